@@ -1,0 +1,967 @@
+/*
+ * dtn_oracle.c -- plain, slow FP64 CPU oracle of the local BIE / walk-on-spheres
+ * Dirichlet-to-Neumann method (Yan, Cai, Zeng, arXiv 1210.1491).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header,
+ * table or constant generator with the CUDA path.
+ *
+ * Every function restates one step of the method in the order the paper gives
+ * it, in double precision, with no blocking, fusion or reordering:
+ *   - Philox4x32-10 counter RNG (Salmon et al., SC'11; not in the paper)
+ *   - Gauss-Legendre rules (Sec. 5.1.2, Eq. bw83/bw85 use them on the hemisphere)
+ *   - distance to the boundary and nearest boundary point (Sec. 2, WOS paragraph)
+ *   - walk on spheres with an epsilon-shell, estimator Eq. bw87
+ *   - whole-sphere Dirichlet Green's function with one Kelvin image (Sec. 4,
+ *     image charge/location as in the text after Eq. bw26)
+ *   - local BIE of the first kind, Eq. bw49-bw51, collocation (Sec. 5.2)
+ *   - dense LU with partial pivoting
+ *   - integral representation Eq. bw03 with the free-space G of Eq. bw05
+ *
+ * Parity status of every function is listed in the test suite; all functions
+ * here are pinned (none is "parity unpinned").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846264338327950288
+
+/* ===================================================================== RNG */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11).  One round: two 32x32->64 products of counter words 0
+ * and 2 with the round multipliers; the new words are
+ *   (hi(M1*x2) ^ x1 ^ k0, lo(M1*x2), hi(M0*x0) ^ x3 ^ k1, lo(M0*x0)),
+ * and the key is bumped by the Weyl constants between rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* 24-bit uniform: the odd integer ((w >> 8) | 1) times 2^-24, in (0,1). */
+double or_u01_24(uint32_t w) { return (double)((w >> 8) | 1u) * 0x1p-24; }
+
+/* 53-bit uniform from two words: the odd integer (hi<<21 | lo>>11) | 1 times 2^-53. */
+double or_u01_53(uint32_t hi, uint32_t lo)
+{
+    uint64_t v = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+    return (double)(v | 1ull) * 0x1p-53;
+}
+
+/* ========================================================= Gauss-Legendre */
+/* n-point Gauss-Legendre rule on [-1,1], nodes ascending.  Newton's method on
+ * P_n evaluated by the three-term recurrence (k+1)P_{k+1} = (2k+1)xP_k - kP_{k-1};
+ * weight 2 / ((1-x^2) P_n'(x)^2). */
+void or_gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(OR_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            if (n == 0) p1 = 1.0;
+            for (int k = 1; k < n; ++k) {
+                double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+                p0 = p1; p1 = p2;
+            }
+            /* p1 = P_n(z), p0 = P_{n-1}(z) */
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) {
+                /* one more evaluation of the derivative at the final node */
+                p0 = 1.0; p1 = z;
+                for (int k = 1; k < n; ++k) {
+                    double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+                    p0 = p1; p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                break;
+            }
+        }
+        /* node i counted from +1 downward; store ascending */
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* ================================================================ geometry */
+/* Domain kinds: 0 ball interior, 1 box interior, 2 box minus boxes. */
+typedef struct {
+    int kind;
+    double center[3], radius;
+    double lo[3], hi[3];
+    int n_boxes;
+    const double *boxes; /* n_boxes x 6: lo xyz, hi xyz */
+} or_geom;
+
+/* Distance from x to the boundary of the region and the nearest boundary point
+ * (the radius of the largest empty sphere of the WOS step, Sec. 2).
+ * Ties take the lowest face / box index; the outer box comes before the wires. */
+double or_distance(const or_geom *g, const double x[3], double nearest[3])
+{
+    if (g->kind == 0) {
+        double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
+        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (r > 0.0) {
+            for (int i = 0; i < 3; ++i) nearest[i] = g->center[i] + g->radius * v[i] / r;
+        } else {
+            nearest[0] = g->center[0]; nearest[1] = g->center[1];
+            nearest[2] = g->center[2] + g->radius;
+        }
+        return g->radius - r;
+    }
+    /* outer box, interior side: face f = 2*axis + side */
+    double best = INFINITY;
+    int bf = 0;
+    for (int f = 0; f < 6; ++f) {
+        int ax = f / 2;
+        double d = (f % 2 == 0) ? x[ax] - g->lo[ax] : g->hi[ax] - x[ax];
+        if (d < best) { best = d; bf = f; }
+    }
+    nearest[0] = x[0]; nearest[1] = x[1]; nearest[2] = x[2];
+    nearest[bf / 2] = (bf % 2 == 0) ? g->lo[bf / 2] : g->hi[bf / 2];
+    if (g->kind == 1) return best;
+    /* obstacle boxes, exterior side: |max(lo - x, 0, x - hi)| */
+    for (int b = 0; b < g->n_boxes; ++b) {
+        const double *lo = g->boxes + 6 * b, *hi = lo + 3;
+        double e[3], s = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            double t = lo[i] - x[i];
+            double u = x[i] - hi[i];
+            e[i] = t > 0.0 ? t : (u > 0.0 ? u : 0.0);
+            s += e[i] * e[i];
+        }
+        double d = sqrt(s);
+        if (d < best) {
+            best = d;
+            for (int i = 0; i < 3; ++i)
+                nearest[i] = x[i] < lo[i] ? lo[i] : (x[i] > hi[i] ? hi[i] : x[i]);
+        }
+    }
+    return best;
+}
+
+/* ============================================================ Dirichlet data */
+typedef struct {
+    int kind;              /* 0 point source, 1 harmonic polynomial (real SH), 2 constant */
+    double x0[3], strength;
+    int lmax;
+    const double *clm;     /* (lmax+1)^2, index l*l + l + m */
+    double center[3], scale;
+    double constant;
+} or_data;
+
+/* Real orthonormal spherical harmonics Y_lm(direction), l <= lmax, index
+ * l*l + l + m, no Condon-Shortley phase:
+ *   m = 0 : N_l0 P_l(cos t)
+ *   m > 0 : sqrt2 N_lm P_l^m(cos t) cos(m p)
+ *   m < 0 : sqrt2 N_l|m| P_l^|m|(cos t) sin(|m| p)
+ * with N_lm = sqrt((2l+1)/(4pi) (l-m)!/(l+m)!).  P_l^m by the recurrences
+ * P_m^m = (2m-1)!! sin^m t,  P_{m+1}^m = (2m+1) cos t P_m^m,
+ * (l-m) P_l^m = (2l-1) cos t P_{l-1}^m - (l+m-1) P_{l-2}^m. */
+void or_real_sh(int lmax, const double dir[3], double *Y)
+{
+    double r = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    double ct = r > 0 ? dir[2] / r : 1.0;
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = atan2(dir[1], dir[0]);
+    for (int m = 0; m <= lmax; ++m) {
+        /* P_m^m */
+        double pmm = 1.0;
+        for (int k = 1; k <= m; ++k) pmm *= (2.0 * k - 1.0) * st;
+        double plm2 = 0.0, plm1 = 0.0;
+        for (int l = m; l <= lmax; ++l) {
+            double p;
+            if (l == m) p = pmm;
+            else if (l == m + 1) p = (2.0 * m + 1.0) * ct * pmm;
+            else p = ((2.0 * l - 1.0) * ct * plm1 - (l + m - 1.0) * plm2) / (double)(l - m);
+            plm2 = plm1; plm1 = p;
+            /* N_lm via the factorial ratio */
+            double ratio = 1.0;
+            for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+            double N = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * ratio);
+            if (m == 0) {
+                Y[l * l + l] = N * p;
+            } else {
+                Y[l * l + l + m] = sqrt(2.0) * N * p * cos(m * ph);
+                Y[l * l + l - m] = sqrt(2.0) * N * p * sin(m * ph);
+            }
+        }
+    }
+}
+
+/* Dirichlet data g(x) (the boundary values of u in Eq. bw01). */
+double or_dirichlet(const or_data *d, const double x[3])
+{
+    if (d->kind == 0) {
+        double v[3] = {x[0] - d->x0[0], x[1] - d->x0[1], x[2] - d->x0[2]};
+        return d->strength / (4.0 * OR_PI * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    }
+    if (d->kind == 1) {
+        double v[3] = {(x[0] - d->center[0]) / d->scale, (x[1] - d->center[1]) / d->scale,
+                       (x[2] - d->center[2]) / d->scale};
+        double rho = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        int nl = (d->lmax + 1) * (d->lmax + 1);
+        double Y[(32 + 1) * (32 + 1)];
+        if (d->lmax > 32) return NAN;
+        or_real_sh(d->lmax, v, Y);
+        (void)nl;
+        double s = 0.0, rl = 1.0;
+        for (int l = 0; l <= d->lmax; ++l) {
+            for (int m = -l; m <= l; ++m) s += d->clm[l * l + l + m] * rl * Y[l * l + l + m];
+            rl *= rho;
+        }
+        return s;
+    }
+    return d->constant;
+}
+
+/* Exact Neumann data n . grad u for the harmonic extension of the data.
+ * Point source: grad of strength/(4 pi |x-x0|).  Harmonic polynomial of degree
+ * lmax: u restricted to the line x + t n is a polynomial of degree <= lmax, so
+ * the central difference of order 2m >= lmax (weights (-1)^(k+1) (m!)^2 /
+ * (k (m-k)! (m+k)!)) is exact for it. */
+double or_neumann_exact(const or_data *d, const double x[3], const double n[3])
+{
+    if (d->kind == 0) {
+        double v[3] = {x[0] - d->x0[0], x[1] - d->x0[1], x[2] - d->x0[2]};
+        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        return -d->strength * (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / (4.0 * OR_PI * r * r * r);
+    }
+    if (d->kind == 1) {
+        int m = (d->lmax + 1) / 2 + 1;
+        double h = 0.125 * d->scale;
+        double mf = 1.0;
+        for (int k = 1; k <= m; ++k) mf *= k;
+        double s = 0.0;
+        for (int k = 1; k <= m; ++k) {
+            double fmk = 1.0, fpk = 1.0;
+            for (int j = 1; j <= m - k; ++j) fmk *= j;
+            for (int j = 1; j <= m + k; ++j) fpk *= j;
+            double wk = ((k % 2) ? 1.0 : -1.0) * mf * mf / (k * fmk * fpk);
+            double xp[3], xm[3];
+            for (int i = 0; i < 3; ++i) { xp[i] = x[i] + k * h * n[i]; xm[i] = x[i] - k * h * n[i]; }
+            s += wk * (or_dirichlet(d, xp) - or_dirichlet(d, xm));
+        }
+        return s / h;
+    }
+    return 0.0;
+}
+
+/* ==================================================================== WOS */
+typedef struct {
+    double eps;          /* absorption shell width */
+    uint64_t seed;       /* Philox key = (seed lo32, seed hi32) */
+    uint64_t max_steps;  /* distance evaluations per walk before a walk is cut */
+    int stream;          /* 0: one Philox call per jump, 53-bit uniforms from words (0,1),(2,3)
+                            1: one Philox call per two jumps, 24-bit uniforms; jump j uses
+                               counter (walk, j>>1, point, patch), words (0,1) if j even, (2,3) if odd */
+    int score;           /* 0: g at the nearest boundary point; 1: the data function at the
+                            absorption point itself (martingale diagnostic) */
+} or_wos_opts;
+
+/* One walk on spheres (Sec. 2): from y, repeat { d = dist(x); stop if d <= eps;
+ * jump to a uniform point of the sphere of radius d about x }.  Returns 1 and the
+ * score when absorbed, 0 when the walk reached max_steps distance evaluations. */
+int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t walk,
+            uint32_t point, uint32_t patch, const or_wos_opts *o, double *score, uint64_t *steps)
+{
+    double x[3] = {y[0], y[1], y[2]};
+    uint32_t key[2] = {(uint32_t)(o->seed & 0xffffffffu), (uint32_t)(o->seed >> 32)};
+    *steps = 0;
+    for (uint64_t j = 0; j < o->max_steps; ++j) {
+        double nb[3];
+        double d = or_distance(g, x, nb);
+        *steps += 1;
+        if (d <= o->eps) {
+            *score = (o->score == 0) ? or_dirichlet(dat, nb) : or_dirichlet(dat, x);
+            return 1;
+        }
+        double u1, u2;
+        uint32_t w[4];
+        if (o->stream == 0) {
+            uint32_t ctr[4] = {walk, (uint32_t)j, point, patch};
+            or_philox4x32_10(ctr, key, w);
+            u1 = or_u01_53(w[0], w[1]);
+            u2 = or_u01_53(w[2], w[3]);
+        } else {
+            uint32_t ctr[4] = {walk, (uint32_t)(j >> 1), point, patch};
+            or_philox4x32_10(ctr, key, w);
+            if ((j & 1) == 0) { u1 = or_u01_24(w[0]); u2 = or_u01_24(w[1]); }
+            else { u1 = or_u01_24(w[2]); u2 = or_u01_24(w[3]); }
+        }
+        /* uniform direction on the unit sphere: z uniform in (-1,1), azimuth uniform */
+        double z = 1.0 - 2.0 * u1;
+        double s = sqrt(fmax(0.0, 1.0 - z * z));
+        double ph = 2.0 * OR_PI * u2;
+        x[0] += d * s * cos(ph);
+        x[1] += d * s * sin(ph);
+        x[2] += d * z;
+    }
+    return 0;
+}
+
+/* Estimator Eq. bw87 at one hemisphere node: sums over walks [w0, w1). */
+void or_wos_point(const or_geom *g, const or_data *dat, const double y[3], uint32_t point,
+                  uint32_t patch, int64_t w0, int64_t w1, const or_wos_opts *o, double *sum,
+                  double *sum2, uint64_t *steps, uint64_t *capped)
+{
+    double s1 = 0.0, s2 = 0.0;
+    uint64_t st = 0, cap = 0;
+    for (int64_t w = w0; w < w1; ++w) {
+        double sc;
+        uint64_t ns;
+        if (or_walk(g, dat, y, (uint32_t)w, point, patch, o, &sc, &ns)) {
+            s1 += sc;
+            s2 += sc * sc;
+        } else {
+            cap += 1;
+        }
+        st += ns;
+    }
+    *sum = s1; *sum2 = s2; *steps = st; *capped = cap;
+}
+
+/* Many nodes at once (OpenMP over nodes; each node is the serial loop above). */
+void or_wos_points(const or_geom *g, const or_data *dat, int64_t n, const double *y,
+                   const uint32_t *point, const uint32_t *patch, const int64_t *walks,
+                   const or_wos_opts *o, double *sum, double *sum2, uint64_t *steps,
+                   uint64_t *capped)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i)
+        or_wos_point(g, dat, y + 3 * i, point[i], patch[i], 0, walks[i], o, sum + i, sum2 + i,
+                     steps + i, capped + i);
+}
+
+/* ================================================================ patches */
+/* Patch kinds: 0 flat disk (S lies in one plane face), 1 spherical cap (S lies
+ * on the boundary sphere of a ball domain).  Local frame (t1, t2, n): n is the
+ * outward normal of the region at c; t1 = normalised projection of the
+ * coordinate axis least aligned with n (lowest index on ties); t2 = n x t1. */
+typedef struct {
+    int kind;
+    double c[3], n[3], t1[3], t2[3];
+    double a;
+    double R, sc[3];   /* cap: sphere radius and centre */
+    double theta_max;  /* hemisphere polar range measured from -n */
+    double umax;       /* panel radial parameter range: a (disk) or psi_max (cap) */
+} or_patch;
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void frame_from_normal(or_patch *p)
+{
+    int ax = 0;
+    for (int i = 1; i < 3; ++i)
+        if (fabs(p->n[i]) < fabs(p->n[ax])) ax = i;
+    double e[3] = {0, 0, 0};
+    e[ax] = 1.0;
+    double en = p->n[ax];
+    double t[3] = {e[0] - en * p->n[0], e[1] - en * p->n[1], e[2] - en * p->n[2]};
+    double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    for (int i = 0; i < 3; ++i) p->t1[i] = t[i] / tn;
+    cross3(p->n, p->t1, p->t2);
+}
+
+/* Returns 0 on success, -1 if the ball about c meets more than one plane face
+ * or the geometry/centre combination is not supported. */
+int or_patch_frame(const or_geom *g, const double c[3], double a, or_patch *p)
+{
+    memset(p, 0, sizeof(*p));
+    for (int i = 0; i < 3; ++i) p->c[i] = c[i];
+    p->a = a;
+    if (g->kind == 0) {
+        double v[3] = {c[0] - g->center[0], c[1] - g->center[1], c[2] - g->center[2]};
+        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (!(a < 2.0 * g->radius) || r == 0.0) return -1;
+        for (int i = 0; i < 3; ++i) { p->n[i] = v[i] / r; p->sc[i] = g->center[i]; }
+        p->kind = 1;
+        p->R = g->radius;
+        /* |y - centre| <= R on the hemisphere  <=>  cos(theta) >= a / (2R) */
+        p->theta_max = acos(a / (2.0 * g->radius));
+        /* geodesic angle of the cap: chord a  <=>  psi = 2 asin(a / 2R) */
+        p->umax = 2.0 * asin(a / (2.0 * g->radius));
+        frame_from_normal(p);
+        return 0;
+    }
+    /* plane faces: find the face containing c */
+    double best = INFINITY;
+    int bw = -2, bf = -1;
+    for (int f = 0; f < 6; ++f) {
+        int ax = f / 2;
+        double d = fabs((f % 2 == 0) ? c[ax] - g->lo[ax] : g->hi[ax] - c[ax]);
+        if (d < best) { best = d; bw = -1; bf = f; }
+    }
+    if (g->kind == 2) {
+        for (int b = 0; b < g->n_boxes; ++b) {
+            const double *lo = g->boxes + 6 * b, *hi = lo + 3;
+            for (int f = 0; f < 6; ++f) {
+                int ax = f / 2;
+                double d = fabs((f % 2 == 0) ? c[ax] - lo[ax] : c[ax] - hi[ax]);
+                /* c must lie within the face rectangle */
+                int in = 1;
+                for (int i = 0; i < 3; ++i)
+                    if (i != ax && (c[i] < lo[i] || c[i] > hi[i])) in = 0;
+                if (in && d < best) { best = d; bw = b; bf = f; }
+            }
+        }
+    }
+    int ax = bf / 2, side = bf % 2;
+    p->n[0] = p->n[1] = p->n[2] = 0.0;
+    if (bw == -1) p->n[ax] = side ? 1.0 : -1.0;   /* outer box: outward of the box */
+    else p->n[ax] = side ? -1.0 : 1.0;            /* obstacle: region normal points into the box */
+    p->kind = 0;
+    p->theta_max = OR_PI / 2.0;
+    p->umax = a;
+    frame_from_normal(p);
+    /* the ball must meet this face only */
+    if (bw == -1) {
+        for (int f = 0; f < 6; ++f) {
+            if (f == bf) continue;
+            int fx = f / 2;
+            double d = (f % 2 == 0) ? c[fx] - g->lo[fx] : g->hi[fx] - c[fx];
+            if (d <= a) return -1;
+        }
+    } else {
+        const double *lo = g->boxes + 6 * bw, *hi = lo + 3;
+        for (int i = 0; i < 3; ++i)
+            if (i != ax && (c[i] - lo[i] <= a || hi[i] - c[i] <= a)) return -1;
+        /* the ball must not reach the opposite face of the same box */
+        if (hi[ax] - lo[ax] <= a) return -1;
+        for (int f = 0; f < 6; ++f) {
+            int fx = f / 2;
+            double d = (f % 2 == 0) ? c[fx] - g->lo[fx] : g->hi[fx] - c[fx];
+            if (d <= a) return -1;
+        }
+    }
+    if (g->kind == 2) {
+        for (int b = 0; b < g->n_boxes; ++b) {
+            if (b == bw) continue;
+            const double *lo = g->boxes + 6 * b, *hi = lo + 3;
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                double t = fmax(fmax(lo[i] - c[i], 0.0), c[i] - hi[i]);
+                s += t * t;
+            }
+            if (sqrt(s) <= a) return -1;
+        }
+    }
+    return 0;
+}
+
+static void local_to_global(const or_patch *p, const double L[3], double y[3])
+{
+    for (int i = 0; i < 3; ++i) y[i] = p->c[i] + L[0] * p->t1[i] + L[1] * p->t2[i] + L[2] * p->n[i];
+}
+
+/* Hemisphere nodes (Eq. bw85 generalised to theta in [0, theta_max]):
+ * theta_i = (theta_max/2)(xi_i + 1), phi_j = pi (xi_j + 1), node index i*nphi + j,
+ * local position a (sin th cos ph, sin th sin ph, -cos th), weight
+ * w_i w_j (theta_max/2) pi a^2 sin th_i (the area element of Eq. bw83). */
+void or_gamma_nodes(const or_patch *p, int nt, int nph, double *Yloc, double *yglob, double *W)
+{
+    double *xt = malloc(sizeof(double) * nt), *wt = malloc(sizeof(double) * nt);
+    double *xp = malloc(sizeof(double) * nph), *wp = malloc(sizeof(double) * nph);
+    or_gauss_legendre(nt, xt, wt);
+    or_gauss_legendre(nph, xp, wp);
+    for (int i = 0; i < nt; ++i) {
+        double th = 0.5 * p->theta_max * (xt[i] + 1.0);
+        for (int j = 0; j < nph; ++j) {
+            double ph = OR_PI * (xp[j] + 1.0);
+            int k = i * nph + j;
+            double L[3] = {p->a * sin(th) * cos(ph), p->a * sin(th) * sin(ph), -p->a * cos(th)};
+            if (Yloc) { Yloc[3 * k] = L[0]; Yloc[3 * k + 1] = L[1]; Yloc[3 * k + 2] = L[2]; }
+            if (yglob) local_to_global(p, L, yglob + 3 * k);
+            W[k] = wt[i] * wp[j] * 0.5 * p->theta_max * OR_PI * p->a * p->a * sin(th);
+        }
+    }
+    free(xt); free(wt); free(xp); free(wp);
+}
+
+/* Point of the patch at parameters (u, v), local coordinates, its unit normal
+ * (local) and the area Jacobian.  Disk: Y = u (cos v, sin v, 0), J = u.
+ * Cap: Y = (R sin u cos v, R sin u sin v, -2R sin^2(u/2)), n = (sin u cos v,
+ * sin u sin v, cos u), J = R^2 sin u. */
+static void patch_point(const or_patch *p, double u, double v, double Y[3], double nl[3], double *J)
+{
+    if (p->kind == 0) {
+        Y[0] = u * cos(v); Y[1] = u * sin(v); Y[2] = 0.0;
+        nl[0] = 0.0; nl[1] = 0.0; nl[2] = 1.0;
+        *J = u;
+    } else {
+        double su = sin(u), cu = cos(u), sh = sin(0.5 * u);
+        Y[0] = p->R * su * cos(v); Y[1] = p->R * su * sin(v); Y[2] = -2.0 * p->R * sh * sh;
+        nl[0] = su * cos(v); nl[1] = su * sin(v); nl[2] = cu;
+        *J = p->R * p->R * su;
+    }
+}
+
+/* Panels: ring r in [0,nr), sector s in [0,ns), index r*ns + s; parameter box
+ * u in [r umax/nr, (r+1) umax/nr], v in [s 2pi/ns, (s+1) 2pi/ns].
+ * Collocation point = the panel's area centroid (disk), or the radial projection
+ * of its area centroid onto the sphere (cap).  prm = (u0, u1, v0, v1, uc, vc). */
+void or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, double *nglob,
+               double *area, double *prm)
+{
+    double du = p->umax / nr, dv = 2.0 * OR_PI / ns;
+    double sinc = sin(0.5 * dv) / (0.5 * dv);
+    for (int r = 0; r < nr; ++r) {
+        for (int s = 0; s < ns; ++s) {
+            int k = r * ns + s;
+            double u0 = r * du, u1 = (r + 1) * du, v0 = s * dv, v1 = (s + 1) * dv;
+            double vc = 0.5 * (v0 + v1), uc, A;
+            if (p->kind == 0) {
+                uc = (2.0 / 3.0) * (u1 * u1 * u1 - u0 * u0 * u0) / (u1 * u1 - u0 * u0) * sinc;
+                A = 0.5 * (u1 * u1 - u0 * u0) * dv;
+            } else {
+                /* centroid direction: polar angle atan2(int sin^2 u du * sinc, int sin u cos u du) */
+                double Is = 0.5 * ((u1 - sin(u1) * cos(u1)) - (u0 - sin(u0) * cos(u0)));
+                double Ic = 0.5 * (sin(u1) * sin(u1) - sin(u0) * sin(u0));
+                uc = atan2(Is * sinc, Ic);
+                A = p->R * p->R * (cos(u0) - cos(u1)) * dv;
+            }
+            double Y[3], nl[3], J;
+            patch_point(p, uc, vc, Y, nl, &J);
+            if (Xloc) { Xloc[3 * k] = Y[0]; Xloc[3 * k + 1] = Y[1]; Xloc[3 * k + 2] = Y[2]; }
+            if (xglob) local_to_global(p, Y, xglob + 3 * k);
+            if (nglob)
+                for (int i = 0; i < 3; ++i)
+                    nglob[3 * k + i] = nl[0] * p->t1[i] + nl[1] * p->t2[i] + nl[2] * p->n[i];
+            area[k] = A;
+            if (prm) {
+                double *q = prm + 6 * k;
+                q[0] = u0; q[1] = u1; q[2] = v0; q[3] = v1; q[4] = uc; q[5] = vc;
+            }
+        }
+    }
+}
+
+/* ======================================================= Green's functions */
+/* Whole-sphere Dirichlet Green's function of B(c,a) in local coordinates
+ * X = x - c, Y = y - c (Sec. 4: free-space term plus one Kelvin image of charge
+ * -a/|Y| at c + a^2 Y/|Y|^2; written symmetrically in X and Y):
+ *   G = (1/4pi) [ 1/|X-Y| - a / sqrt(|X|^2|Y|^2 - 2a^2 X.Y + a^4) ]. */
+double or_green(double a, const double X[3], const double Y[3])
+{
+    double d[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    double yy = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    double xy = X[0] * Y[0] + X[1] * Y[1] + X[2] * Y[2];
+    double Q = xx * yy - 2.0 * a * a * xy + a * a * a * a;
+    return (1.0 / r - a / sqrt(Q)) / (4.0 * OR_PI);
+}
+
+/* grad_Y G = (1/4pi) [ (X-Y)/|X-Y|^3 + a (|X|^2 Y - a^2 X) / Q^{3/2} ]. */
+void or_green_grad_y(double a, const double X[3], const double Y[3], double g[3])
+{
+    double d[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double r3 = r2 * sqrt(r2);
+    double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    double yy = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    double xy = X[0] * Y[0] + X[1] * Y[1] + X[2] * Y[2];
+    double Q = xx * yy - 2.0 * a * a * xy + a * a * a * a;
+    double Q32 = Q * sqrt(Q);
+    for (int i = 0; i < 3; ++i)
+        g[i] = (d[i] / r3 + a * (xx * Y[i] - a * a * X[i]) / Q32) / (4.0 * OR_PI);
+}
+
+/* Poisson kernel of B(c,a): -dG/dn_y on |Y| = a, = (a^2 - |X|^2) / (4 pi a |X-Y|^3)
+ * (the hitting density of Eq. bw21 for the ball). */
+double or_poisson(double a, const double X[3], const double Y[3])
+{
+    double d[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    return (a * a - xx) / (4.0 * OR_PI * a * r2 * sqrt(r2));
+}
+
+/* ============================================== adaptive panel quadrature */
+/* Integrands over a patch panel, in the panel's (u, v) parameters. */
+typedef struct {
+    const or_patch *p;
+    const or_data *dat;
+    int kind;           /* 0: G(X,Y); 1: dG/dn_y(X,Y) (g(y) - g(x)); 2: G(X,Y) q_exact(y);
+                           3: dG/dn_y(X,Y) g(y) */
+    double X[3];
+    double gx;          /* g at the collocation point (kind 1) */
+} quad_ctx;
+
+static double gl10_x[10], gl10_w[10];
+static int gl10_ready = 0;
+
+static void gl10_init(void)
+{
+    if (!gl10_ready) {
+        or_gauss_legendre(10, gl10_x, gl10_w);
+        gl10_ready = 1;
+    }
+}
+
+static double integrand(const quad_ctx *c, double u, double v)
+{
+    double Y[3], nl[3], J;
+    patch_point(c->p, u, v, Y, nl, &J);
+    if (c->kind == 0) return or_green(c->p->a, c->X, Y) * J;
+    double y[3];
+    local_to_global(c->p, Y, y);
+    if (c->kind == 1 || c->kind == 3) {
+        double g[3];
+        or_green_grad_y(c->p->a, c->X, Y, g);
+        double dn = g[0] * nl[0] + g[1] * nl[1] + g[2] * nl[2];
+        double gy = or_dirichlet(c->dat, y);
+        return dn * (c->kind == 1 ? gy - c->gx : gy) * J;
+    }
+    double ng[3];
+    for (int i = 0; i < 3; ++i) ng[i] = nl[0] * c->p->t1[i] + nl[1] * c->p->t2[i] + nl[2] * c->p->n[i];
+    return or_green(c->p->a, c->X, Y) * or_neumann_exact(c->dat, y, ng) * J;
+}
+
+/* Globally adaptive 1-D integration (bisect the segment with the largest error
+ * estimate until the summed estimate is below tol, or a segment budget is
+ * spent).  Rule: 10-point Gauss-Legendre; error estimate of a segment =
+ * |G10(whole) - G10(left) - G10(right)|, value = G10(left) + G10(right). */
+typedef double (*fn1)(void *, double);
+
+static double gl_apply(fn1 f, void *c, double a, double b)
+{
+    double h = 0.5 * (b - a), m = 0.5 * (a + b), s = 0.0;
+    for (int i = 0; i < 10; ++i) s += gl10_w[i] * f(c, m + h * gl10_x[i]);
+    return s * h;
+}
+
+#define OR_MAXSEG 160
+static double gadapt(fn1 f, void *c, double a, double b, double tol)
+{
+    double sa[OR_MAXSEG], sb[OR_MAXSEG], sl[OR_MAXSEG], sr[OR_MAXSEG], se[OR_MAXSEG];
+    double m = 0.5 * (a + b);
+    double w = gl_apply(f, c, a, b);
+    sa[0] = a; sb[0] = b;
+    sl[0] = gl_apply(f, c, a, m); sr[0] = gl_apply(f, c, m, b);
+    se[0] = fabs(sl[0] + sr[0] - w);
+    int ns = 1;
+    for (;;) {
+        double tot = 0.0, mag = 0.0;
+        int worst = 0;
+        for (int i = 0; i < ns; ++i) {
+            tot += se[i];
+            mag += fabs(sl[i]) + fabs(sr[i]);
+            if (se[i] > se[worst]) worst = i;
+        }
+        if (tot <= tol || tot <= 1e-15 * mag || ns + 1 >= OR_MAXSEG) break;
+        /* split the worst segment into its two halves, each refined once */
+        double a0 = sa[worst], b0 = sb[worst], m0 = 0.5 * (a0 + b0);
+        double wl = sl[worst], wr = sr[worst];
+        double q1 = 0.5 * (a0 + m0), q3 = 0.5 * (m0 + b0);
+        double l1 = gl_apply(f, c, a0, q1), r1 = gl_apply(f, c, q1, m0);
+        double l2 = gl_apply(f, c, m0, q3), r2 = gl_apply(f, c, q3, b0);
+        sa[worst] = a0; sb[worst] = m0; sl[worst] = l1; sr[worst] = r1; se[worst] = fabs(l1 + r1 - wl);
+        sa[ns] = m0; sb[ns] = b0; sl[ns] = l2; sr[ns] = r2; se[ns] = fabs(l2 + r2 - wr);
+        ++ns;
+    }
+    double v = 0.0;
+    for (int i = 0; i < ns; ++i) v += sl[i] + sr[i];
+    return v;
+}
+
+/* Nested integration over a parameter box: outer over u, inner over v.  An
+ * inner error d moves the outer integral by at most d (u1 - u0), so the inner
+ * tolerance is a tenth of tol / (u1 - u0). */
+typedef struct { const quad_ctx *q; double u, v0, v1, tol; } box_ctx;
+
+static double box_inner(void *p, double v)
+{
+    box_ctx *b = (box_ctx *)p;
+    return integrand(b->q, b->u, v);
+}
+
+static double box_outer(void *p, double u)
+{
+    box_ctx b = *(box_ctx *)p;
+    b.u = u;
+    return gadapt(box_inner, &b, b.v0, b.v1, b.tol);
+}
+
+static double rect_integral(const quad_ctx *c, double u0, double u1, double v0, double v1, double tol)
+{
+    box_ctx b = {c, 0.0, v0, v1, 0.1 * tol / (u1 - u0)};
+    return gadapt(box_outer, &b, u0, u1, tol);
+}
+
+/* Triangle (S, A, B) in parameter space with the singular point at S, by the
+ * Duffy map p(s,t) = S + s [(A - S) + t (B - A)], Jacobian s |det(A - S, B - A)|:
+ * the factor s cancels the 1/r singularity at S (the local polar transform of
+ * the self panel, Sec. 5.2).  Nested adaptive integration in (s, t). */
+typedef struct {
+    const quad_ctx *q;
+    double S[2], E1[2], E2[2], det;
+    double s, tol;
+} duffy_ctx;
+
+static double duffy_inner(void *p, double t)
+{
+    duffy_ctx *T = (duffy_ctx *)p;
+    double u = T->S[0] + T->s * (T->E1[0] + t * T->E2[0]);
+    double v = T->S[1] + T->s * (T->E1[1] + t * T->E2[1]);
+    return integrand(T->q, u, v) * T->s * T->det;
+}
+
+static double duffy_outer(void *p, double s)
+{
+    duffy_ctx T = *(duffy_ctx *)p;
+    T.s = s;
+    return gadapt(duffy_inner, &T, 0.0, 1.0, T.tol);
+}
+
+static double duffy_triangle(const quad_ctx *c, const double S[2], const double A[2],
+                             const double B[2], double tol)
+{
+    duffy_ctx T;
+    T.q = c;
+    T.S[0] = S[0]; T.S[1] = S[1];
+    T.E1[0] = A[0] - S[0]; T.E1[1] = A[1] - S[1];
+    T.E2[0] = B[0] - A[0]; T.E2[1] = B[1] - A[1];
+    T.det = fabs(T.E1[0] * T.E2[1] - T.E1[1] * T.E2[0]);
+    T.s = 0.0;
+    T.tol = 0.1 * tol;
+    if (T.det == 0.0) return 0.0;
+    return gadapt(duffy_outer, &T, 0.0, 1.0, tol);
+}
+
+/* Exact integral (R9 reading: entries are the integrals themselves) of the
+ * chosen integrand over one panel's parameter box.  If `sing` is given (the
+ * collocation point lies on this panel) the box is cut into four triangles
+ * from the singular parameter point and each is integrated through the Duffy
+ * map.  `rtol` is relative to area / (4 pi max(distance, diameter)). */
+double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const double X[3],
+                         const double prm[6], const double *sing, double rtol)
+{
+    gl10_init();
+    quad_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.p = p; c.dat = dat; c.kind = kind;
+    c.X[0] = X[0]; c.X[1] = X[1]; c.X[2] = X[2];
+    if (kind == 1) {
+        double xg[3];
+        local_to_global(p, X, xg);
+        c.gx = or_dirichlet(dat, xg);
+    }
+    double u0 = prm[0], u1 = prm[1], v0 = prm[2], v1 = prm[3];
+    double Yc[3], nl[3], J;
+    patch_point(p, prm[4], prm[5], Yc, nl, &J);
+    double d = sqrt((X[0] - Yc[0]) * (X[0] - Yc[0]) + (X[1] - Yc[1]) * (X[1] - Yc[1]) +
+                    (X[2] - Yc[2]) * (X[2] - Yc[2]));
+    double diam, area;
+    if (p->kind == 0) {
+        diam = (u1 - u0) + u1 * (v1 - v0);
+        area = 0.5 * (u1 * u1 - u0 * u0) * (v1 - v0);
+    } else {
+        diam = p->R * (u1 - u0) + p->R * sin(u1) * (v1 - v0);
+        area = p->R * p->R * (cos(u0) - cos(u1)) * (v1 - v0);
+    }
+    double tol = rtol * area / (4.0 * OR_PI * (d > diam ? d : diam));
+    if (!sing) return rect_integral(&c, u0, u1, v0, v1, tol);
+    double S[2] = {sing[0], sing[1]};
+    double cor[5][2] = {{u0, v0}, {u1, v0}, {u1, v1}, {u0, v1}, {u0, v0}};
+    double s = 0.0;
+    for (int e = 0; e < 4; ++e) s += duffy_triangle(&c, S, cor[e], cor[e + 1], 0.25 * tol);
+    return s;
+}
+
+/* ================================================================ assembly */
+/* Collocation of the first-kind local BIE, Eq. bw49-bw51, at the panel
+ * collocation points x_i with piecewise-constant Neumann data on the panels:
+ *   A_ij = int_{panel j} G(x_i, y) ds_y.
+ * The right side b of Eq. bw51 is taken with the constant solution subtracted,
+ * as the paper does for its single-point formula (Sec. 3, Eq. bw61-bw68): for
+ * u = 1 (zero Neumann data) Eq. bw51 reads 0 = 1/2 + p.v. int_S dG/dn_y +
+ * int_Gamma dG/dn_y, and subtracting g(x_i) times that identity gives
+ *   b_i = int_S dG/dn_y(x_i, y) (g(y) - g(x_i)) ds_y
+ *         - sum_k W_k P(x_i, y_k) (U_k - g(x_i)),
+ * where the Gamma integral of dG/dn_y u is minus the Poisson-kernel quadrature
+ * over the hemisphere nodes and U_k are the walk estimates of u there.  On a
+ * plane through c both terms of dG/dn_y vanish, so the S integral is zero for
+ * flat patches. */
+void or_assemble(const or_patch *p, const or_data *dat, int nr, int ns, int nt, int nph,
+                 const double *U, double rtol, double *A, double *b)
+{
+    int n = nr * ns, P = nt * nph;
+    double *Xl = malloc(sizeof(double) * 3 * n), *xg = malloc(sizeof(double) * 3 * n);
+    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * 6 * n);
+    double *Yl = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
+    or_panels(p, nr, ns, Xl, xg, NULL, ar, prm);
+    or_gamma_nodes(p, nt, nph, Yl, NULL, W);
+    gl10_init();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; ++i) {
+        double gxi = or_dirichlet(dat, xg + 3 * i);
+        double bi = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double *sing = (i == j) ? prm + 6 * i + 4 : NULL;
+            A[(int64_t)i * n + j] = or_panel_integral(p, dat, 0, Xl + 3 * i, prm + 6 * j, sing, rtol);
+            if (p->kind == 1)
+                bi += or_panel_integral(p, dat, 1, Xl + 3 * i, prm + 6 * j, sing, rtol);
+        }
+        for (int k = 0; k < P; ++k)
+            bi -= W[k] * or_poisson(p->a, Xl + 3 * i, Yl + 3 * k) * (U[k] - gxi);
+        b[i] = bi;
+    }
+    free(Xl); free(xg); free(ar); free(prm); free(Yl); free(W);
+}
+
+/* ======================================================================= LU */
+/* Dense LU with partial pivoting (pivot = first row of maximal |a|), then
+ * forward and back substitution.  A (row-major n x n) and b are overwritten.
+ * Returns 0, or k+1 if the k-th pivot is exactly zero. */
+int or_lu_solve(int n, double *A, double *b, double *x)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(A[(int64_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            double v = fabs(A[(int64_t)i * n + k]);
+            if (v > best) { best = v; piv = i; }
+        }
+        if (best == 0.0) return k + 1;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(int64_t)k * n + j];
+                A[(int64_t)k * n + j] = A[(int64_t)piv * n + j];
+                A[(int64_t)piv * n + j] = t;
+            }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double l = A[(int64_t)i * n + k] / A[(int64_t)k * n + k];
+            A[(int64_t)i * n + k] = l;
+            for (int j = k + 1; j < n; ++j) A[(int64_t)i * n + j] -= l * A[(int64_t)k * n + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < n; ++j) s -= A[(int64_t)i * n + j] * x[j];
+        x[i] = s / A[(int64_t)i * n + i];
+    }
+    return 0;
+}
+
+/* =========================================================== full patch */
+/* Steps 1 and 2 of the BIE-WOS algorithm (Sec. 4) for one patch: walks at the
+ * hemisphere nodes, then assembly and solve.  If U_in is given the walks are
+ * skipped and U_in is used. */
+int or_solve_patch(const or_geom *g, const or_data *dat, const double c[3], double a, int nt,
+                   int nph, int nr, int ns, int64_t walks, uint32_t patch_id,
+                   const or_wos_opts *o, const double *U_in, double rtol, double *U_out,
+                   double *SE_out, uint64_t *steps_out, double *q_out)
+{
+    or_patch p;
+    if (or_patch_frame(g, c, a, &p) != 0) return -1;
+    int P = nt * nph, n = nr * ns;
+    double *U = malloc(sizeof(double) * P);
+    if (U_in) {
+        memcpy(U, U_in, sizeof(double) * P);
+        if (steps_out) *steps_out = 0;
+    } else {
+        double *y = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
+        double *s1 = malloc(sizeof(double) * P), *s2 = malloc(sizeof(double) * P);
+        uint64_t *st = malloc(sizeof(uint64_t) * P), *cp = malloc(sizeof(uint64_t) * P);
+        uint32_t *pt = malloc(sizeof(uint32_t) * P), *pa = malloc(sizeof(uint32_t) * P);
+        int64_t *wk = malloc(sizeof(int64_t) * P);
+        or_gamma_nodes(&p, nt, nph, NULL, y, W);
+        for (int k = 0; k < P; ++k) { pt[k] = (uint32_t)k; pa[k] = patch_id; wk[k] = walks; }
+        or_wos_points(g, dat, P, y, pt, pa, wk, o, s1, s2, st, cp);
+        uint64_t tot = 0;
+        for (int k = 0; k < P; ++k) {
+            double N = (double)(walks - (int64_t)cp[k]);
+            U[k] = s1[k] / N;
+            double var = (s2[k] - N * U[k] * U[k]) / (N * (N - 1.0));
+            if (SE_out) SE_out[k] = sqrt(var > 0 ? var : 0.0);
+            tot += st[k];
+        }
+        if (steps_out) *steps_out = tot;
+        free(y); free(W); free(s1); free(s2); free(st); free(cp); free(pt); free(pa); free(wk);
+    }
+    if (U_out) memcpy(U_out, U, sizeof(double) * P);
+    double *A = malloc(sizeof(double) * n * n), *b = malloc(sizeof(double) * n);
+    or_assemble(&p, dat, nr, ns, nt, nph, U, rtol, A, b);
+    int rc = or_lu_solve(n, A, b, q_out);
+    free(A); free(b); free(U);
+    return rc;
+}
+
+/* ============================================================== potential */
+/* Integral representation Eq. bw03 with G0 = 1/(4pi|x-y|) (Eq. bw05) and the
+ * panel-midpoint rule:
+ *   u(t) = sum_p A_p [ q_p / (4pi|t-y_p|) - g_p n_p.(t-y_p) / (4pi|t-y_p|^3) ]. */
+void or_potential(int64_t np, const double *y, const double *nrm, const double *area,
+                  const double *q, const double *g, int64_t nt, const double *t, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nt; ++i) {
+        double s = 0.0;
+        for (int64_t p = 0; p < np; ++p) {
+            double d[3] = {t[3 * i] - y[3 * p], t[3 * i + 1] - y[3 * p + 1], t[3 * i + 2] - y[3 * p + 2]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double dn = d[0] * nrm[3 * p] + d[1] * nrm[3 * p + 1] + d[2] * nrm[3 * p + 2];
+            s += area[p] * (q[p] / (4.0 * OR_PI * r) - g[p] * dn / (4.0 * OR_PI * r * r * r));
+        }
+        out[i] = s;
+    }
+}
+
+/* Panel ownership for the overlapping-patch cover (Sec. 6): panel of patch p is
+ * kept iff the patch centre nearest to its collocation point is p's (lowest
+ * index on ties).  keep[i] = 1 / 0. */
+void or_owned(int64_t npan, const double *x, const int64_t *owner_patch, int64_t ncent,
+              const double *cent, uint8_t *keep)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npan; ++i) {
+        int64_t best = -1;
+        double bd = INFINITY;
+        for (int64_t c = 0; c < ncent; ++c) {
+            double d[3] = {x[3 * i] - cent[3 * c], x[3 * i + 1] - cent[3 * c + 1], x[3 * i + 2] - cent[3 * c + 2]};
+            double r = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r < bd) { bd = r; best = c; }
+        }
+        keep[i] = (best == owner_patch[i]) ? 1 : 0;
+    }
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,311 @@
+"""Seeded synthetic inputs shared by the tests, the oracle runs and bench.py.
+
+This module holds only input generation (random coefficients, patch-centre
+layouts, wire layouts, target points).  It contains none of the method's
+arithmetic: no Green's functions, no walks, no quadrature, no solves.  Both the
+CUDA path and the oracle consume what it returns.
+
+All host-side randomness uses NumPy's PCG64 with an explicit seed.  The random
+numbers of the walks themselves are not drawn here: both sides generate them
+from the counter-based Philox4x32-10 definition (key = walk seed).
+
+Workload shapes follow the five configurations of the method's GPU study
+(unit-cube single patch, unit-ball full boundary, 200-wire box layout, scaled
+unit ball, serving).  The paper itself uses a planar interface (Sec. 5.1) and a
+sphere of radius 3 (Sec. 5.2); the shapes below keep its parameters where they
+are given (hemisphere Gauss products, patch radius, epsilon-shell).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# geometry kinds (same numeric values as the C ABI enum)
+GEOM_BALL_INTERIOR = 0
+GEOM_BOX_INTERIOR = 1
+GEOM_BOX_MINUS_BOXES = 2
+
+# Dirichlet data kinds
+DATA_POINT_SOURCE = 0
+DATA_HARMONIC_SH = 1
+DATA_CONSTANT = 2
+
+
+@dataclasses.dataclass
+class Geometry:
+    kind: int
+    center: tuple = (0.0, 0.0, 0.0)
+    radius: float = 1.0
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    boxes: np.ndarray | None = None  # (n, 6) float64: lo xyz, hi xyz
+
+    @property
+    def n_boxes(self) -> int:
+        return 0 if self.boxes is None else int(self.boxes.shape[0])
+
+
+@dataclasses.dataclass
+class Dirichlet:
+    kind: int
+    x0: tuple = (0.0, 0.0, 0.0)
+    strength: float = 1.0            # g = strength / (4 pi |x - x0|)
+    lmax: int = 0
+    clm: np.ndarray | None = None    # (lmax+1)^2, index l*l + l + m
+    center: tuple = (0.0, 0.0, 0.0)
+    scale: float = 1.0
+    constant: float = 0.0
+
+
+@dataclasses.dataclass
+class PatchBatch:
+    centers: np.ndarray              # (n, 3) float64, points on the boundary
+    radius: np.ndarray               # (n,) float64
+    n_theta: np.ndarray              # (n,) int32, polar Gauss order on the hemisphere
+    n_phi: np.ndarray                # (n,) int32, azimuthal Gauss order
+    n_rings: np.ndarray              # (n,) int32, panel rings on the patch
+    n_sectors: np.ndarray            # (n,) int32, panel sectors on the patch
+    walks: np.ndarray                # (n,) int64, walks per hemisphere node
+    patch_id_base: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.centers.shape[0])
+
+    def subset(self, idx) -> "PatchBatch":
+        idx = np.asarray(idx)
+        return PatchBatch(self.centers[idx].copy(), self.radius[idx].copy(),
+                          self.n_theta[idx].copy(), self.n_phi[idx].copy(),
+                          self.n_rings[idx].copy(), self.n_sectors[idx].copy(),
+                          self.walks[idx].copy(), self.patch_id_base)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    geometry: Geometry
+    data: Dirichlet
+    batch: PatchBatch
+    epsilon: float = 1e-4
+    seed: int = 0
+    patch_ids: np.ndarray | None = None  # explicit RNG patch ids (default: base + index)
+
+
+def _uniform_batch(centers, a, nt, nph, nr, ns, walks, base=0) -> PatchBatch:
+    n = centers.shape[0]
+    return PatchBatch(
+        centers=np.ascontiguousarray(centers, dtype=np.float64),
+        radius=np.full(n, a, dtype=np.float64),
+        n_theta=np.full(n, nt, dtype=np.int32),
+        n_phi=np.full(n, nph, dtype=np.int32),
+        n_rings=np.full(n, nr, dtype=np.int32),
+        n_sectors=np.full(n, ns, dtype=np.int32),
+        walks=np.full(n, walks, dtype=np.int64),
+        patch_id_base=base,
+    )
+
+
+def fibonacci_sphere(n: int, radius: float = 1.0) -> np.ndarray:
+    """n points on a sphere: z_i = 1 - (2i+1)/n, azimuth i * golden angle."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * (math.pi * (3.0 - math.sqrt(5.0)))
+    return radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def random_clm(lmax: int, seed: int = 0) -> np.ndarray:
+    """c_lm ~ N(0,1), (lmax+1)^2 of them, PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((lmax + 1) ** 2)
+
+
+# ---------------------------------------------------------------- configurations
+
+def cube_single_patch(walks: int = 10_000, n_theta: int = 16, n_phi: int = 16,
+                      n_rings: int = 8, n_sectors: int = 8) -> Workload:
+    """Unit cube interior, point-source data below face z=0, one flat patch.
+
+    x0 = (0.5, 0.5, -0.3), patch centre (0.5, 0.5, 0), a = 0.1, 8x8 panels,
+    16x16 hemisphere nodes, 1e4 walks per node, epsilon = 1e-4, seed 0.
+    """
+    geom = Geometry(GEOM_BOX_INTERIOR, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0))
+    data = Dirichlet(DATA_POINT_SOURCE, x0=(0.5, 0.5, -0.3), strength=1.0)
+    batch = _uniform_batch(np.array([[0.5, 0.5, 0.0]]), 0.1, n_theta, n_phi,
+                           n_rings, n_sectors, walks)
+    return Workload("cube_1patch_a0.1_np64_P256", geom, data, batch)
+
+
+def unit_ball(n_patches: int = 2000, walks: int = 4096, n_theta: int = 16,
+              n_phi: int = 32, n_rings: int = 16, n_sectors: int = 8,
+              lmax: int = 8, a: float = 0.1, seed: int = 0) -> Workload:
+    """Unit ball interior with a random harmonic polynomial as data.
+
+    g = sum_{l<=8} c_lm r^l Y_lm, c_lm ~ N(0,1) (PCG64(seed)); patch centres on a
+    Fibonacci sphere; a = 0.1; 128 panels (16 rings x 8 sectors); 512
+    hemisphere nodes (16 polar x 32 azimuthal); 4096 walks per node.
+    """
+    geom = Geometry(GEOM_BALL_INTERIOR, center=(0.0, 0.0, 0.0), radius=1.0)
+    data = Dirichlet(DATA_HARMONIC_SH, lmax=lmax, clm=random_clm(lmax, seed),
+                     center=(0.0, 0.0, 0.0), scale=1.0)
+    batch = _uniform_batch(fibonacci_sphere(n_patches), a, n_theta, n_phi,
+                           n_rings, n_sectors, walks)
+    name = f"unit_ball_{n_patches}p_np{n_rings * n_sectors}_P{n_theta * n_phi}_W{walks}"
+    return Workload(name, geom, data, batch)
+
+
+def unit_ball_scaled(n_patches: int = 20_000, walks: int = 8192) -> Workload:
+    """Unit-ball study scaled up: 256 panels (16x16), 1024 nodes (32x32), 8192 walks."""
+    return unit_ball(n_patches=n_patches, walks=walks, n_theta=32, n_phi=32,
+                     n_rings=16, n_sectors=16)
+
+
+def wire_layout(n_wires: int = 200, seed: int = 0, outer_lo=(0.0, 0.0, 0.0),
+                outer_hi=(64.0, 64.0, 16.0), gap: float = 0.6,
+                max_tries: int = 200_000) -> np.ndarray:
+    """Axis-aligned wire boxes inside the outer box, by rejection sampling.
+
+    Layer k in {0..3} at z-centre 2 + 4k; x-oriented for even k, y-oriented for
+    odd k; length U[2,20], width and thickness U[0.2,1.0]; gap >= 0.6 to other
+    wires and to the outer box.  Returns (n, 6) float64 rows (lo xyz, hi xyz).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    olo = np.asarray(outer_lo, dtype=np.float64)
+    ohi = np.asarray(outer_hi, dtype=np.float64)
+    boxes: list[np.ndarray] = []
+    tries = 0
+    while len(boxes) < n_wires:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("wire layout: too many rejections")
+        k = len(boxes) % 4
+        length = rng.uniform(2.0, 20.0)
+        width = rng.uniform(0.2, 1.0)
+        thick = rng.uniform(0.2, 1.0)
+        ext = np.array([length, width, thick]) if k % 2 == 0 else np.array([width, length, thick])
+        zc = 2.0 + 4.0 * k
+        cx = rng.uniform(olo[0] + gap + ext[0] / 2, ohi[0] - gap - ext[0] / 2)
+        cy = rng.uniform(olo[1] + gap + ext[1] / 2, ohi[1] - gap - ext[1] / 2)
+        c = np.array([cx, cy, zc])
+        lo, hi = c - ext / 2, c + ext / 2
+        ok = True
+        for b in boxes:
+            sep = np.maximum(b[:3] - hi, lo - b[3:])
+            if np.max(sep) < gap:
+                ok = False
+                break
+        if ok:
+            boxes.append(np.concatenate([lo, hi]))
+    return np.array(boxes, dtype=np.float64)
+
+
+def wire_patch_centers(boxes: np.ndarray, n: int, a: float, seed: int = 1,
+                       margin: float = 1e-9, max_tries: int = 5_000_000,
+                       outer_lo=(0.0, 0.0, 0.0), outer_hi=(64.0, 64.0, 16.0)):
+    """Area-uniform patch centres on wire faces whose ball meets one face only.
+
+    A centre c on face f of wire w is kept when the disk of radius a around c
+    lies inside the face rectangle and no other wire, face or the outer box
+    comes within a of c.  Returns (centres (n,3), wire index (n,), rejected).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ext = boxes[:, 3:] - boxes[:, :3]
+    # face areas: faces 2*axis+side, area = product of the two other extents
+    areas = np.stack([ext[:, 1] * ext[:, 2], ext[:, 1] * ext[:, 2],
+                      ext[:, 0] * ext[:, 2], ext[:, 0] * ext[:, 2],
+                      ext[:, 0] * ext[:, 1], ext[:, 0] * ext[:, 1]], axis=1)
+    flat = areas.reshape(-1)
+    prob = flat / flat.sum()
+    olo = np.asarray(outer_lo)
+    ohi = np.asarray(outer_hi)
+    out, owner = [], []
+    rejected = 0
+    tries = 0
+    while len(out) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("wire patch centres: too many rejections")
+        idx = rng.choice(flat.size, p=prob)
+        w, f = divmod(int(idx), 6)
+        axis, side = divmod(f, 2)
+        lo, hi = boxes[w, :3], boxes[w, 3:]
+        c = rng.uniform(lo, hi)
+        c[axis] = lo[axis] if side == 0 else hi[axis]
+        good = ext[w, axis] > a + margin   # the ball must not reach the opposite face
+        for ax in range(3):
+            if ax == axis:
+                continue
+            if c[ax] - lo[ax] < a + margin or hi[ax] - c[ax] < a + margin:
+                good = False
+        # other wires and the outer box must stay farther than a
+        if good:
+            d_out = np.min(np.minimum(c - olo, ohi - c))
+            if d_out <= a + margin:
+                good = False
+        if good:
+            e = np.maximum(np.maximum(boxes[:, :3] - c, 0.0), c - boxes[:, 3:])
+            d = np.sqrt((e * e).sum(axis=1))
+            d[w] = np.inf
+            if np.min(d) <= a + margin:
+                good = False
+        if not good:
+            rejected += 1
+            continue
+        out.append(c)
+        owner.append(w)
+    return np.array(out), np.array(owner, dtype=np.int64), rejected
+
+
+def wires(n_patches: int = 10_000, walks: int = 2048, a: float = 0.3,
+          seed: int = 0) -> Workload:
+    """200-wire layout in the grounded box [0,64]^2 x [0,16].
+
+    Data: point source at the centre of wire 0 (outside the region).  Patch
+    sizes vary by patch: node orders 16^2, 24^2 or 32^2 and panel counts
+    4x8 .. 16x32, drawn per patch, so that one batch carries uneven systems
+    (32 .. 512 collocation points).
+    """
+    boxes = wire_layout(seed=seed)
+    geom = Geometry(GEOM_BOX_MINUS_BOXES, lo=(0.0, 0.0, 0.0), hi=(64.0, 64.0, 16.0),
+                    boxes=boxes)
+    x0 = tuple(0.5 * (boxes[0, :3] + boxes[0, 3:]))
+    data = Dirichlet(DATA_POINT_SOURCE, x0=x0, strength=1.0)
+    centers, _, _ = wire_patch_centers(boxes, n_patches, a, seed=seed + 1)
+    rng = np.random.Generator(np.random.PCG64(seed + 2))
+    # uneven collocation sizes: rings x sectors in {4..16} x {8..32}
+    rings = rng.choice(np.array([4, 8, 12, 16], dtype=np.int32), size=n_patches)
+    sectors = rng.choice(np.array([8, 16, 24, 32], dtype=np.int32), size=n_patches)
+    nodes = rng.choice(np.array([16, 24, 32], dtype=np.int32), size=n_patches)
+    batch = PatchBatch(centers=centers.astype(np.float64),
+                       radius=np.full(n_patches, a),
+                       n_theta=nodes.copy(), n_phi=nodes.copy(),
+                       n_rings=rings, n_sectors=sectors,
+                       walks=np.full(n_patches, walks, dtype=np.int64))
+    return Workload(f"wires200_{n_patches}p_uneven", geom, data, batch)
+
+
+def targets_in_ball(n: int, radius: float, margin: float, seed: int = 3) -> np.ndarray:
+    """n points uniform in the ball |x| <= radius - margin (PCG64(seed))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = (radius - margin) * rng.uniform(0.0, 1.0, n) ** (1.0 / 3.0)
+    return v * r[:, None]
+
+
+def targets_outside_ball(n: int, radius: float, margin: float, seed: int = 4) -> np.ndarray:
+    """n points in the shell radius+margin <= |x| <= 2 radius."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = rng.uniform(radius + margin, 2.0 * radius, n)
+    return v * r[:, None]
+
+
+def points_in_box(n: int, lo, hi, margin: float, seed: int = 5) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = np.asarray(lo) + margin
+    hi = np.asarray(hi) - margin
+    return rng.uniform(lo, hi, size=(n, 3))
