@@ -1,0 +1,327 @@
+"""Benchmark of the walk-on-spheres / local-BIE DtN hot path on one GB300.
+
+A step is one pass of the whole path over the unit-ball workload (2000 patches
+on a Fibonacci sphere, a = 0.1, 128 panels and 512 hemisphere nodes per patch,
+4096 walks per node, epsilon 1e-4, degree-8 random harmonic data): patch setup,
+walks and their estimates, assembly, batched LU with refinement, the panel
+gather of the patch cover and the potential at 1e5 targets.  Prints one JSON
+line.  `--impl reference` times the FP64 CPU oracle instead, on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "WOS walk-steps/s & DtN patches/s vs plain FP64 path; p50/p99 query latency"
+N_TARGETS = 100_000
+# algorithmic thread-level ALU operations of one FP32 walk-step in the ball
+# region (half a Philox4x32-10 block: 10 rounds x (2 mul.hi + 2 mul.lo + 2 xor3
+# + 2 key adds) / 2 = 40; distance to the sphere 9; shell test 2; two 24-bit
+# uniforms 6; direction (z, s, sincospi) 17; position update 5)
+OPS_PER_STEP = 79
+SM_COUNT = 152
+LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(int(os.environ.get("LOCAL_RANK", "0"))) and parts[0] != "0":
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload():
+    wl = W.unit_ball(n_patches=2000, walks=4096)
+    targets = W.targets_in_ball(N_TARGETS, 1.0, 0.05, seed=3)
+    return wl, targets
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+
+def run_reference(args):
+    import oracle as O
+    wl, targets = make_workload()
+    b = wl.batch
+    o = O.wos_opts(eps=wl.epsilon, seed=wl.seed, stream=O.STREAM_F64)
+    times = []
+    sample = 1   # patches per step: a bounded sample of the same workload
+
+    def one(k):
+        i = k % b.n
+        t0 = time.perf_counter()
+        O.solve_patch(wl.geometry, wl.data, b.centers[i], float(b.radius[i]), int(b.n_theta[i]),
+                      int(b.n_phi[i]), int(b.n_rings[i]), int(b.n_sectors[i]), int(b.walks[i]), i, o,
+                      rtol=1e-12)
+        return time.perf_counter() - t0
+
+    for k in range(args.warmup):
+        one(k)
+    for k in range(args.steps):
+        times.append(one(args.warmup + k))
+    sec = sum(times) / len(times)
+    value = sample / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "patches/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "patches_per_step": sample, "walks_per_node": int(b.walks[0]),
+                   "nodes_per_patch": int(b.n_theta[0] * b.n_phi[0]), "panels_per_patch": int(b.n_rings[0] * b.n_sectors[0])},
+        "cpu_baseline": {"value": value, "unit": "patches/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{sample} patch per step of the 2000-patch unit-ball workload, full walks"},
+        "e2e": {"value": value, "unit": "patches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+
+def cpu_baseline_sample(wl):
+    """The oracle on a bounded sample (2 patches) on this host's cores."""
+    import oracle as O
+    b = wl.batch
+    o = O.wos_opts(eps=wl.epsilon, seed=wl.seed, stream=O.STREAM_F64)
+    t0 = time.perf_counter()
+    steps = 0
+    n = 2
+    for i in range(n):
+        r = O.solve_patch(wl.geometry, wl.data, b.centers[i], float(b.radius[i]), int(b.n_theta[i]),
+                          int(b.n_phi[i]), int(b.n_rings[i]), int(b.n_sectors[i]), int(b.walks[i]), i, o,
+                          rtol=1e-12)
+        steps += r["steps"]
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "patches/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"first {n} patches of the workload, full walks, assembly and solve",
+            "walk_steps_per_s": steps / dt}
+
+
+def run_ours(args):
+    import torch
+    import paper_1210_1491_gb300 as dtn
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl, targets = make_workload()
+    b = wl.batch
+    # replicas only: every rank solves its own copy with its own patch ids
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks, patch_id_base=rank * b.n)
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    prec = dtn.PREC_MIXED if args.prec == "mixed" else dtn.PREC_FP64
+    opts = dtn.solve_opts(prec=prec, epsilon=wl.epsilon, seed=wl.seed, record_stages=True)
+    dev = torch.device("cuda", local)
+    centers = torch.from_numpy(b.centers).to(dev)
+    radius = torch.from_numpy(b.radius).to(dev)
+    tgt = torch.from_numpy(targets).to(dev)
+    res = dtn.alloc_result(hb)
+    owner = torch.from_numpy(np.repeat(np.arange(b.n), int(b.n_rings[0] * b.n_sectors[0]))).to(dev)
+    u_out = torch.empty(N_TARGETS, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    keep = torch.empty(res["neumann"].shape[0], dtype=torch.uint8, device=dev)
+
+    def full_step():
+        dtn.solve_patches(g, centers, radius, hb, opts, result=res)
+        _, kept, nk = dtn.gather_owned(res["colloc_xyz"], owner, centers)
+        dtn.eval_potential(g, res["colloc_xyz"], res["normals"], res["areas"], res["neumann"],
+                           res["dirichlet"], tgt, prec=prec, out=u_out, index=kept, n_index=nk)
+
+    for _ in range(args.warmup):
+        full_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    step_ms, wos_ms, stage = [], [], []
+    walk_steps = 0
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()   # write 256 MB between timed steps: L2 starts cold
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        full_step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = g.stage_times()
+        stage.append(st)
+        wos_ms.append(st[1])
+        walk_steps = int(res["gamma_steps"].sum().item())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * b.n / (ms / 1e3)
+    wos = sum(wos_ms) / len(wos_ms)
+    walk_steps_per_s = world * walk_steps / (wos / 1e3)
+
+    # e2e: host buffers in, host results out, through the same C-ABI calls
+    pin_c = torch.from_numpy(b.centers).pin_memory()
+    pin_r = torch.from_numpy(b.radius).pin_memory()
+    pin_t = torch.from_numpy(targets).pin_memory()
+    out_q = torch.empty(res["neumann"].shape, dtype=torch.float64).pin_memory()
+    out_u = torch.empty(N_TARGETS, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        centers.copy_(pin_c, non_blocking=True)
+        radius.copy_(pin_r, non_blocking=True)
+        tgt.copy_(pin_t, non_blocking=True)
+        full_step()
+        out_q.copy_(res["neumann"], non_blocking=True)
+        out_u.copy_(u_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    h2d = pin_c.numel() * 8 + pin_r.numel() * 8 + pin_t.numel() * 8
+    d2h = out_q.numel() * 8 + out_u.numel() * 8
+
+    # the plain FP64 path, one patch per launch, on a sample of 20 patches
+    o64 = dtn.solve_opts(prec=dtn.PREC_FP64, epsilon=wl.epsilon, seed=wl.seed)
+    nplain = 20
+    hb1 = [dtn.HostBatch(b.n_theta[i:i + 1], b.n_phi[i:i + 1], b.n_rings[i:i + 1], b.n_sectors[i:i + 1],
+                         b.walks[i:i + 1], patch_id_base=i) for i in range(nplain)]
+    r1 = [dtn.alloc_result(h) for h in hb1]
+    dtn.solve_patches(g, centers[0:1], radius[0:1], hb1[0], o64, result=r1[0])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(nplain):
+        dtn.solve_patches(g, centers[i:i + 1], radius[i:i + 1], hb1[i], o64, result=r1[i])
+    e1.record(stream)
+    e1.synchronize()
+    plain = nplain / (e0.elapsed_time(e1) / 1e3)
+
+    peaks = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # Tops/s
+    achieved = walk_steps * OPS_PER_STEP / (wos / 1e3) / 1e12
+    kernels_per_step = 3 + 2 + 1 + 1 + 4 + 1   # setup, walks+finalize, assembly, LU, gather, potential
+    line = {
+        "metric": METRIC, "value": value, "unit": "patches/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == dtn.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "patches": b.n, "nodes_per_patch": int(b.n_theta[0] * b.n_phi[0]),
+                   "panels_per_patch": int(b.n_rings[0] * b.n_sectors[0]), "walks_per_node": int(b.walks[0]),
+                   "epsilon": wl.epsilon, "targets": N_TARGETS, "precision": args.prec,
+                   "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+        "walk_steps_per_s": walk_steps_per_s, "walk_steps_per_step": walk_steps,
+        "stage_ms": {"setup": statistics.mean(s[0] for s in stage), "walks": wos,
+                     "assembly": statistics.mean(s[2] for s in stage), "solve": statistics.mean(s[3] for s in stage),
+                     "gather_and_potential": ms - sum(statistics.mean(s[k] for s in stage) for k in range(4))},
+        "fp64_path": {"value": plain, "unit": "patches/s", "sample": f"{nplain} patches, one patch per launch",
+                      "speedup": value / plain},
+        "roofline": {"bound": "alu", "kernel": "wos_kernel<float, ball>", "achieved": achieved,
+                     "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                     "ops_per_walk_step": OPS_PER_STEP,
+                     "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"},
+        "e2e": {"value": b.n * world / (e2e / 1e3), "unit": "patches/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_sample(wl)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

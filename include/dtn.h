@@ -1,0 +1,293 @@
+/*
+ * dtn.h -- C ABI of the GB300 (sm_103a) local-BIE / walk-on-spheres
+ * Dirichlet-to-Neumann library (method of Yan, Cai and Zeng, arXiv 1210.1491).
+ *
+ * Problem (Sec. 2, Eq. bw01-bw05): the Laplace equation holds in a region D with
+ * Dirichlet data g on its boundary.  For each patch S = boundary of D inside a
+ * ball B(c, a) centred at a boundary point c, the library returns the Neumann
+ * data q = du/dn (n = outward normal of D) on S (Sec. 4, BIE-WOS algorithm):
+ *   step 1: walk-on-spheres estimates U_k of u at the Gauss nodes y_k of the
+ *           hemisphere Gamma = dB inside D (Sec. 2, Eq. bw87, Eq. bw85);
+ *   step 2: collocation solve of the first-kind local BIE (Eq. bw49-bw51) built
+ *           on the whole-sphere Dirichlet Green's function of B (one Kelvin image).
+ * The potential anywhere then follows from the integral representation Eq. bw03.
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" are CUDA device pointers (for instance the data
+ *     pointers of torch tensors on cuda:0); "host" pointers are ordinary memory.
+ *     The caller owns every pointer it passes; host descriptors and host arrays
+ *     are copied before the call returns.  The library owns the geometry object,
+ *     its device copies and its workspaces.
+ *   - Calls taking a `stream` (a cudaStream_t passed as void*, NULL = default
+ *     stream) are asynchronous: argument errors are returned synchronously
+ *     before anything is enqueued; conditions found on the device (unsupported
+ *     patch, capped walks, refinement that did not converge) are written to the
+ *     per-patch status array and counters, which the caller reads after a
+ *     stream synchronisation.  No call aborts, traps or prints.
+ *   - A geometry object may be used from several threads only if the caller
+ *     serialises the calls on it.
+ *   - Arrays of 3-vectors are row-major (x, y, z) per row; matrices row-major.
+ *
+ * Error behaviour: every call returns a dtn_status; DTN_E_CUDA means a CUDA
+ * runtime call failed (dtn_last_cuda_error() gives its code).
+ */
+#ifndef DTN_H
+#define DTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque, library-owned geometry object (region, data, device workspaces). */
+typedef struct dtn_geometry dtn_geometry;
+
+typedef enum {
+    DTN_OK = 0,
+    DTN_E_INVALID_ARG = 1,
+    DTN_E_OUT_OF_MEMORY = 2,
+    DTN_E_CUDA = 3,
+    DTN_E_NOT_CONVERGED = 4,
+    DTN_E_TIMEOUT = 5,
+    DTN_E_UNSUPPORTED = 6,
+    DTN_E_WALK_CAP = 7
+} dtn_status;
+
+/* Region kinds (the solution domain D; walks run inside it). */
+typedef enum {
+    DTN_GEOM_BALL_INTERIOR = 0,    /* |x - center| < radius */
+    DTN_GEOM_BOX_INTERIOR = 1,     /* lo < x < hi */
+    DTN_GEOM_BOX_MINUS_BOXES = 2   /* outer box minus the closed obstacle boxes */
+} dtn_geom_kind;
+
+typedef struct {
+    int32_t kind;                  /* dtn_geom_kind */
+    double center[3];              /* ball */
+    double radius;
+    double lo[3], hi[3];           /* outer box */
+    int32_t n_boxes;               /* obstacle boxes, disjoint, inside the outer box */
+    const double *boxes;           /* host, n_boxes x 6 (lo xyz, hi xyz), copied */
+    double cell_size;              /* obstacle lookup grid cell edge; <= 0 picks one */
+} dtn_geometry_desc;
+
+/* Dirichlet data g on the boundary (Eq. bw01).  Each kind is the trace of a
+ * function harmonic in D, so exact Neumann data exist for testing. */
+typedef enum {
+    DTN_DATA_POINT_SOURCE = 0,     /* g = strength / (4 pi |x - x0|), x0 outside D */
+    DTN_DATA_HARMONIC_SH = 1,      /* g = sum c_lm rho^l Y_lm(dir), rho = |x-center|/scale,
+                                      real orthonormal Y_lm, no Condon-Shortley phase */
+    DTN_DATA_CONSTANT = 2          /* g = constant */
+} dtn_data_kind;
+
+typedef struct {
+    int32_t kind;                  /* dtn_data_kind */
+    double x0[3];
+    double strength;
+    int32_t lmax;                  /* <= 16 */
+    const double *clm;             /* host, (lmax+1)^2 coefficients, index l*l + l + m, copied */
+    double center[3];
+    double scale;
+    double constant;
+} dtn_dirichlet_desc;
+
+typedef enum {
+    DTN_PREC_FP64 = 0,   /* FP64 walks, FP64 assembly, FP64 LU (the plain path) */
+    DTN_PREC_MIXED = 1   /* FP32 walks with FP64 sums; FP32 far-field assembly with FP64
+                            singular / near-singular / rim entries; FP32 LU with FP64-residual
+                            iterative refinement */
+} dtn_precision;
+
+typedef struct {
+    int32_t prec;               /* dtn_precision */
+    double epsilon;             /* absorption shell width (Sec. 2); > 0 */
+    uint64_t seed;              /* Philox key = (seed low 32 bits, seed high 32 bits) */
+    uint64_t max_steps;         /* distance evaluations per walk before it is cut (0 = 1e6) */
+    int32_t max_refine_iters;   /* mixed precision: refinement sweeps (0 = 10) */
+    double refine_tol;          /* stop when |r|_inf <= refine_tol |b|_inf (0 = 1e-12) */
+    int32_t u_provided;         /* 1: skip the walks and read U_k from result->u_gamma_mean */
+    int32_t walk_chunk;         /* walks per warp work item (0 = tuned) */
+    int32_t wos_blocks_per_sm;  /* resident walk blocks per SM (0 = tuned) */
+    int32_t graph_capture;      /* 1: replay the device part as a CUDA graph when the shapes of
+                                   the previous call repeat */
+    int32_t record_stages;      /* 1: record CUDA events between the stages of the call on its
+                                   stream (read them with dtn_stage_times) */
+} dtn_solve_opts;
+
+/* A batch of patches.  Patch p has a ball of radius radius[p] about centers[p]
+ * (a point of the boundary), n_theta[p] x n_phi[p] hemisphere Gauss nodes
+ * (Eq. bw85, theta in [0, theta_max]), n_rings[p] x n_sectors[p] panels on S
+ * and walks_per_point[p] walks per node.  Node k = i*n_phi + j (i polar, j
+ * azimuthal); panel index = ring*n_sectors + sector.  The walks of node k of
+ * patch p use Philox counters (walk, step, k, patch id). */
+typedef struct {
+    int64_t n_patches;
+    const double *centers;          /* device, n_patches x 3 */
+    const double *radius;           /* device, n_patches */
+    const int32_t *n_theta;         /* host, n_patches, 1..64 */
+    const int32_t *n_phi;           /* host, n_patches, 1..64 */
+    const int32_t *n_rings;         /* host, n_patches, >= 1 */
+    const int32_t *n_sectors;       /* host, n_patches, >= 1; rings*sectors <= 1024 */
+    const int64_t *walks_per_point; /* host, n_patches, >= 2 (ignored with u_provided) */
+    uint32_t patch_id_base;         /* RNG patch id of patch p = base + p ... */
+    const uint32_t *patch_ids;      /* ... unless this host array (n_patches) is given */
+} dtn_patch_batch;
+
+/* Outputs (all device; offsets of patch p are the prefix sums of the per-patch
+ * node and panel counts in batch order).  NULL marks an output not wanted,
+ * except where "required" is stated. */
+typedef struct {
+    double *gamma_xyz;       /* gamma_total x 3, hemisphere node positions */
+    double *gamma_w;         /* gamma_total, node weights (area element of Eq. bw83) */
+    double *u_gamma_mean;    /* gamma_total, required: U_k (written; read when u_provided) */
+    double *u_gamma_se;      /* gamma_total, standard error of U_k */
+    uint64_t *gamma_steps;   /* gamma_total, walk-steps (distance evaluations) per node */
+    uint32_t *gamma_capped;  /* gamma_total, walks cut at max_steps (excluded from U_k) */
+    double *colloc_xyz;      /* panels_total x 3, collocation points */
+    double *normals;         /* panels_total x 3, outward normals of D there */
+    double *areas;           /* panels_total */
+    double *dirichlet;       /* panels_total, g at the collocation points */
+    double *neumann;         /* panels_total, required: q = du/dn */
+    double *matrix;          /* sum n_p^2: assembled A (row-major per patch), for checking */
+    double *rhs;             /* panels_total: assembled b, for checking */
+    int32_t *refine_iters;   /* n_patches */
+    double *residual;        /* n_patches, final |b - A q|_inf / |b|_inf */
+    int32_t *patch_status;   /* n_patches, dtn_status per patch */
+} dtn_patch_result;
+
+/* Creates a geometry object (device copies of the region, obstacle lookup
+ * grid).  Errors: DTN_E_INVALID_ARG for a malformed description (radius <= 0,
+ * lo >= hi, obstacle outside the outer box), DTN_E_CUDA / DTN_E_OUT_OF_MEMORY. */
+dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out);
+
+/* Releases the geometry object and every device buffer it owns (synchronises). */
+dtn_status dtn_destroy_geometry(dtn_geometry *geom);
+
+/* Sets the Dirichlet data g of Eq. bw01 (copied to the device). */
+dtn_status dtn_set_dirichlet(dtn_geometry *geom, const dtn_dirichlet_desc *data);
+
+/* Totals of a batch: panels_total = sum rings*sectors, gamma_total = sum
+ * n_theta*n_phi, matrix_total = sum (rings*sectors)^2 (host, synchronous). */
+dtn_status dtn_query_patch_sizes(const dtn_patch_batch *batch, int64_t *panels_total,
+                                 int64_t *gamma_total, int64_t *matrix_total);
+
+/* BIE-WOS algorithm (Sec. 4) for every patch of the batch: patch setup,
+ * walks (Sec. 2, Eq. bw87), assembly of Eq. bw49-bw51 and the collocation
+ * solve.  Asynchronous on `stream`.  Per-patch failures land in patch_status
+ * (DTN_E_UNSUPPORTED: the ball meets more than one plane face, or the centre
+ * is not on the boundary; DTN_E_NOT_CONVERGED: refinement stopped above
+ * refine_tol; DTN_E_WALK_CAP: some walks were cut at max_steps). */
+dtn_status dtn_solve_patches(dtn_geometry *geom, const dtn_patch_batch *batch,
+                             const dtn_solve_opts *opts, dtn_patch_result *result, void *stream);
+
+/* Integral representation Eq. bw03 with the free-space G of Eq. bw05 and the
+ * panel-midpoint rule over n_panels panels:
+ *   u(t) = sum_p area_p [ q_p / (4 pi |t - y_p|) - g_p n_p.(t - y_p) / (4 pi |t - y_p|^3) ].
+ * All arrays device.  dirichlet may be NULL (then g is evaluated from the
+ * data set on geom).  If panel_index (device int64) is given, the sum runs
+ * over panels panel_index[0 .. m) of the arrays, m = *n_index (device int64,
+ * for instance the count written by dtn_gather_owned) or n_panels when n_index
+ * is NULL; otherwise over panels 0 .. n_panels.  prec: DTN_PREC_FP64 (FP64
+ * pairs) or DTN_PREC_MIXED (FP32 pair terms, FP64 per-target accumulation).
+ * Asynchronous. */
+dtn_status dtn_eval_potential(const dtn_geometry *geom, int64_t n_panels, const double *xyz,
+                              const double *normals, const double *areas, const double *neumann,
+                              const double *dirichlet, const int64_t *panel_index,
+                              const int64_t *n_index, int64_t n_targets, const double *targets,
+                              double *u_out, int32_t prec, void *stream);
+
+/* Panel gather for the overlapping-patch cover (Sec. 6: the boundary is covered
+ * by overlapping patches S_i): panel i (of patch owner[i]) is kept iff the
+ * patch centre nearest to its collocation point (FP64 distances, lowest index
+ * on ties) is owner[i]'s.  Writes keep[i] (0/1) and the kept panels' indices,
+ * in input order, to kept_index; *n_kept (device int64) receives their count.
+ * Asynchronous. */
+dtn_status dtn_gather_owned(int64_t n_panels, const double *colloc_xyz, const int64_t *owner,
+                            int64_t n_centers, const double *centers, uint8_t *keep,
+                            int64_t *kept_index, int64_t *n_kept, void *stream);
+
+/* Walk-on-spheres estimates (Sec. 2, Eq. bw87) at arbitrary points of D:
+ * n points y (device n x 3), each with its RNG point id and patch id (device
+ * u32 arrays) and walk count (host int64 array, each in [2, 2^32)).  Outputs
+ * (device, n): mean, standard error (may be NULL), walk-steps per point (may
+ * be NULL), capped walks (may be NULL).  Uses opts->prec, epsilon, seed,
+ * max_steps, walk_chunk, wos_blocks_per_sm.  Returns after the stream has
+ * finished the walks (it synchronises `stream`). */
+dtn_status dtn_wos_points(const dtn_geometry *geom, int64_t n, const double *y,
+                          const uint32_t *point_ids, const uint32_t *patch_ids,
+                          const int64_t *walks, const dtn_solve_opts *opts, double *mean,
+                          double *se, uint64_t *steps, uint32_t *capped, void *stream);
+
+/* Distance to the boundary and nearest boundary point (the WOS sphere radius,
+ * Sec. 2) at n device points; d and nearest are device outputs (n, n x 3).
+ * prec selects FP64 or the FP32 arithmetic the mixed walks use. */
+dtn_status dtn_distance(const dtn_geometry *geom, int64_t n, const double *x, double *d,
+                        double *nearest, int32_t prec, void *stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on n device counters (n x 4 u32) with
+ * key (seed lo32, seed hi32): out (device, n x 4 u32).  The walk kernels use
+ * the same generator; this entry point exposes it for bit-exact checking. */
+dtn_status dtn_philox4x32_10(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out,
+                             void *stream);
+
+/* Dirichlet data g at n device points (FP64). */
+dtn_status dtn_eval_dirichlet(const dtn_geometry *geom, int64_t n, const double *x, double *g,
+                              void *stream);
+
+/* Device time in milliseconds of the stages of the last dtn_solve_patches call
+ * on geom made with record_stages = 1: ms[0] patch setup, ms[1] walks and their
+ * estimates, ms[2] assembly, ms[3] LU and refinement.  Waits for that call's
+ * last event.  DTN_E_INVALID_ARG if no call recorded stages. */
+dtn_status dtn_stage_times(dtn_geometry *geom, float ms[4]);
+
+/* Human-readable name of a status code (static storage). */
+const char *dtn_status_string(dtn_status s);
+
+/* The last failing CUDA runtime error code seen by this library (0 if none). */
+int32_t dtn_last_cuda_error(void);
+
+/* ---------------------------------------------------------------- serving */
+/* Continuous-batching request server (not in the paper: a serving layer over
+ * dtn_solve_patches).  Queries are sets of patches with their own walk
+ * budgets; they are admitted while in-flight slots and workspace memory
+ * allow, run concurrently on separate streams, and complete independently.
+ * Results depend only on the query (its patch ids fix every random number),
+ * so a query gives the same answer alone or in a mix. */
+typedef struct dtn_server dtn_server;
+
+typedef struct {
+    int32_t max_inflight;        /* concurrent batches (streams), >= 1 */
+    int64_t max_batch_patches;   /* patches merged into one launch */
+    int64_t memory_budget;       /* bytes of workspace the server may hold in flight */
+    dtn_solve_opts opts;         /* solve options for every query */
+} dtn_server_config;
+
+/* One query: host arrays, copied at submission.  Node/panel layout as in
+ * dtn_patch_batch. */
+typedef struct {
+    int64_t n_patches;
+    const double *centers;          /* host n x 3 */
+    const double *radius;           /* host n */
+    const int32_t *n_theta, *n_phi, *n_rings, *n_sectors; /* host n */
+    const int64_t *walks_per_point; /* host n */
+    const uint32_t *patch_ids;      /* host n: RNG patch ids */
+} dtn_query;
+
+dtn_status dtn_server_create(dtn_geometry *geom, const dtn_server_config *cfg, dtn_server **out);
+/* Enqueues a query; *ticket identifies it.  Never blocks on the GPU. */
+dtn_status dtn_server_submit(dtn_server *srv, const dtn_query *q, int64_t *ticket);
+/* Non-blocking: *done = 1 once the query has finished; then neumann (host,
+ * its panels_total) and, if not NULL, u_mean (host, its gamma_total) are
+ * filled, and latency_s gets submit-to-completion seconds. */
+dtn_status dtn_server_poll(dtn_server *srv, int64_t ticket, int32_t *done, double *neumann,
+                           double *u_mean, double *latency_s);
+/* Blocks until every submitted query has completed. */
+dtn_status dtn_server_drain(dtn_server *srv);
+dtn_status dtn_server_destroy(dtn_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTN_H */

@@ -1,0 +1,654 @@
+// api.cu -- the C ABI of include/dtn.h: geometry objects, Dirichlet data, the
+// BIE-WOS batch solve (Sec. 4), potential evaluation (Eq. bw03) and the small
+// checking entry points.  Host code only orchestrates; every numerical step
+// runs in the kernels of setup.cu, wos.cu, assemble.cu, lu.cu, potential.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dtn_internal.h"
+
+namespace dtn {
+
+namespace {
+std::atomic<int32_t> g_last_cuda_error{0};
+}
+
+void set_cuda_error(cudaError_t e) { g_last_cuda_error.store((int32_t)e); }
+
+cudaError_t DevBuf::reserve(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) {
+        cudaError_t e = cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (e != cudaSuccess) return e;
+    }
+    const size_t want = std::max<size_t>(n, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return e;
+    }
+    bytes = want;
+    return cudaSuccess;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+dtn_status to_status(cudaError_t e) {
+    if (e == cudaSuccess) return DTN_OK;
+    set_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? DTN_E_OUT_OF_MEMORY : DTN_E_CUDA;
+}
+
+// Lower bound of the distance between two axis-aligned boxes.
+double box_box_dist(const double *alo, const double *ahi, const double *blo, const double *bhi) {
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const double t = std::max({0.0, blo[i] - ahi[i], alo[i] - bhi[i]});
+        s += t * t;
+    }
+    return std::sqrt(s);
+}
+
+// Obstacle lookup grid: every cell lists the boxes whose distance to the cell
+// (grown by a small margin, so that a point filed in a neighbouring cell by
+// rounding is still covered) is at most `listing`, and stores the smallest
+// distance to any box it does not list.
+void build_grid(GeometryHost &h) {
+    const dtn_geometry_desc &d = h.desc;
+    const double ext[3] = {d.hi[0] - d.lo[0], d.hi[1] - d.lo[1], d.hi[2] - d.lo[2]};
+    double cell = d.cell_size > 0 ? d.cell_size : std::max({ext[0], ext[1], ext[2]}) / 64.0;
+    for (int i = 0; i < 3; ++i) {
+        h.gn[i] = std::max(1, (int)std::ceil(ext[i] / cell));
+        h.glo[i] = d.lo[i];
+    }
+    h.cell = cell;
+    const double listing = 2.0 * cell, margin = 1e-3 * cell;
+    const int64_t nc = (int64_t)h.gn[0] * h.gn[1] * h.gn[2];
+    h.cstart.assign(nc + 1, 0);
+    h.citems.clear();
+    h.ccap.assign(nc, 0.f);
+    const int nb = d.n_boxes;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int ix = (int)(c % h.gn[0]), iy = (int)((c / h.gn[0]) % h.gn[1]), iz = (int)(c / ((int64_t)h.gn[0] * h.gn[1]));
+        const double lo[3] = {h.glo[0] + ix * cell - margin, h.glo[1] + iy * cell - margin, h.glo[2] + iz * cell - margin};
+        const double hi[3] = {lo[0] + cell + 2 * margin, lo[1] + cell + 2 * margin, lo[2] + cell + 2 * margin};
+        double cap = 1e30;
+        for (int b = 0; b < nb; ++b) {
+            const double *bl = &h.boxes[6 * b], *bh = bl + 3;
+            const double dd = box_box_dist(lo, hi, bl, bh);
+            if (dd <= listing) h.citems.push_back(b);
+            else cap = std::min(cap, dd);
+        }
+        // FP32 cap rounded down so it never exceeds the true bound
+        float cf = (float)cap;
+        if ((double)cf > cap) cf = std::nextafter(cf, 0.0f);
+        h.ccap[c] = cf;
+        h.cstart[c + 1] = (int)h.citems.size();
+    }
+}
+
+double point_boundary_distance(const dtn_geometry_desc &d, const double *x) {
+    if (d.kind == DTN_GEOM_BALL_INTERIOR) {
+        const double r = std::sqrt((x[0] - d.center[0]) * (x[0] - d.center[0]) + (x[1] - d.center[1]) * (x[1] - d.center[1]) +
+                                   (x[2] - d.center[2]) * (x[2] - d.center[2]));
+        return std::fabs(d.radius - r);
+    }
+    auto box_surface = [](const double *lo, const double *hi, const double *p) {
+        bool inside = true;
+        double s = 0.0, m = 1e300;
+        for (int i = 0; i < 3; ++i) {
+            const double t = std::max({0.0, lo[i] - p[i], p[i] - hi[i]});
+            s += t * t;
+            if (p[i] < lo[i] || p[i] > hi[i]) inside = false;
+            m = std::min({m, p[i] - lo[i], hi[i] - p[i]});
+        }
+        return inside ? m : std::sqrt(s);
+    };
+    double dist = box_surface(d.lo, d.hi, x);
+    if (d.kind == DTN_GEOM_BOX_MINUS_BOXES)
+        for (int b = 0; b < d.n_boxes; ++b) dist = std::min(dist, box_surface(d.boxes + 6 * b, d.boxes + 6 * b + 3, x));
+    return dist;
+}
+
+// |g| bound on the boundary, for the fixed-point scale of the walk sums
+double score_bound(const dtn_geometry_desc &gd, const dtn_dirichlet_desc &dd) {
+    if (dd.kind == DTN_DATA_POINT_SOURCE) {
+        const double dist = point_boundary_distance(gd, dd.x0);
+        return std::fabs(dd.strength) / (4.0 * kPi * std::max(dist, 1e-12));
+    }
+    if (dd.kind == DTN_DATA_HARMONIC_SH) {
+        // farthest boundary point from the data centre
+        double rmax = 0.0;
+        if (gd.kind == DTN_GEOM_BALL_INTERIOR) {
+            rmax = gd.radius + std::sqrt((gd.center[0] - dd.center[0]) * (gd.center[0] - dd.center[0]) +
+                                         (gd.center[1] - dd.center[1]) * (gd.center[1] - dd.center[1]) +
+                                         (gd.center[2] - dd.center[2]) * (gd.center[2] - dd.center[2]));
+        } else {
+            for (int c = 0; c < 8; ++c) {
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    const double v = ((c >> i) & 1 ? gd.hi[i] : gd.lo[i]) - dd.center[i];
+                    s += v * v;
+                }
+                rmax = std::max(rmax, std::sqrt(s));
+            }
+        }
+        const double rho = rmax / dd.scale;
+        double tot = 0.0, rl = 1.0;
+        for (int l = 0; l <= dd.lmax; ++l) {
+            double cs = 0.0;
+            for (int m = -l; m <= l; ++m) cs += std::fabs(dd.clm[l * l + l + m]);
+            tot += rl * cs * std::sqrt((2.0 * l + 1.0) / (4.0 * kPi));
+            rl *= rho;
+        }
+        return tot;
+    }
+    return std::fabs(dd.constant);
+}
+
+dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
+    const int64_t n = b->n_patches;
+    L.n_patches = n;
+    L.gamma_off.assign(n + 1, 0);
+    L.panel_off.assign(n + 1, 0);
+    L.mat_off.assign(n + 1, 0);
+    L.nt.resize(n); L.nph.resize(n); L.nr.resize(n); L.ns.resize(n);
+    L.walks.resize(n); L.pid.resize(n);
+    L.max_panels = 0; L.max_nodes = 0; L.max_walks = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        const int32_t nt = b->n_theta[p], nph = b->n_phi[p], nr = b->n_rings[p], ns = b->n_sectors[p];
+        if (nt < 1 || nt > kMaxGauss || nph < 1 || nph > kMaxGauss || nr < 1 || ns < 1 || (int64_t)nr * ns > 1024)
+            return DTN_E_INVALID_ARG;
+        const int32_t np = nr * ns, P = nt * nph;
+        L.nt[p] = nt; L.nph[p] = nph; L.nr[p] = nr; L.ns[p] = ns;
+        L.walks[p] = b->walks_per_point ? b->walks_per_point[p] : 0;
+        L.pid[p] = b->patch_ids ? b->patch_ids[p] : (uint32_t)(b->patch_id_base + (uint32_t)p);
+        L.gamma_off[p + 1] = L.gamma_off[p] + P;
+        L.panel_off[p + 1] = L.panel_off[p] + np;
+        L.mat_off[p + 1] = L.mat_off[p] + (int64_t)np * np;
+        L.max_panels = std::max(L.max_panels, np);
+        L.max_nodes = std::max(L.max_nodes, P);
+        L.max_walks = std::max(L.max_walks, L.walks[p]);
+    }
+    L.gamma_total = L.gamma_off[n];
+    L.panels_total = L.panel_off[n];
+    L.matrix_total = L.mat_off[n];
+    return DTN_OK;
+}
+
+// Packs the layout arrays (plus chunk bookkeeping of the walks) into one device
+// buffer.  Pageable-memory copies are staged by the runtime before return.
+cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, DevLayout &D,
+                          int64_t &total_chunks, cudaStream_t s) {
+    const int64_t n = L.n_patches;
+    std::vector<int64_t> chunk_off(n + 1, 0);
+    std::vector<int32_t> cpn(n, 1);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t c = (L.walks[p] + chunk - 1) / chunk;
+        cpn[p] = (int32_t)std::max<int64_t>(c, 1);
+        const int64_t nodes = L.gamma_off[p + 1] - L.gamma_off[p];
+        chunk_off[p + 1] = chunk_off[p] + (L.walks[p] > 0 ? nodes * cpn[p] : 0);
+    }
+    total_chunks = chunk_off[n];
+    // byte layout: 5 int64 arrays (n+1 or n), 5 int32 arrays (n), pid (n), frames (n)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const size_t o_goff = off; off = al(off + (n + 1) * 8);
+    const size_t o_poff = off; off = al(off + (n + 1) * 8);
+    const size_t o_moff = off; off = al(off + (n + 1) * 8);
+    const size_t o_walk = off; off = al(off + n * 8);
+    const size_t o_coff = off; off = al(off + (n + 1) * 8);
+    const size_t o_nt = off; off = al(off + n * 4);
+    const size_t o_nph = off; off = al(off + n * 4);
+    const size_t o_nr = off; off = al(off + n * 4);
+    const size_t o_ns = off; off = al(off + n * 4);
+    const size_t o_cpn = off; off = al(off + n * 4);
+    const size_t o_pid = off; off = al(off + n * 4);
+    const size_t host_bytes = off;
+    const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
+    cudaError_t e = g->ws.layout.reserve(off);
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned char> h(host_bytes, 0);
+    std::memcpy(&h[o_goff], L.gamma_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_poff], L.panel_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_moff], L.mat_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_walk], L.walks.data(), n * 8);
+    std::memcpy(&h[o_coff], chunk_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_nt], L.nt.data(), n * 4);
+    std::memcpy(&h[o_nph], L.nph.data(), n * 4);
+    std::memcpy(&h[o_nr], L.nr.data(), n * 4);
+    std::memcpy(&h[o_ns], L.ns.data(), n * 4);
+    std::memcpy(&h[o_cpn], cpn.data(), n * 4);
+    std::memcpy(&h[o_pid], L.pid.data(), n * 4);
+    char *base = g->ws.layout.as<char>();
+    e = cudaMemcpyAsync(base, h.data(), host_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    D.gamma_off = (int64_t *)(base + o_goff);
+    D.panel_off = (int64_t *)(base + o_poff);
+    D.mat_off = (int64_t *)(base + o_moff);
+    D.walks = (int64_t *)(base + o_walk);
+    D.chunk_off = (int64_t *)(base + o_coff);
+    D.nt = (int32_t *)(base + o_nt);
+    D.nph = (int32_t *)(base + o_nph);
+    D.nr = (int32_t *)(base + o_nr);
+    D.ns = (int32_t *)(base + o_ns);
+    D.cpn = (int32_t *)(base + o_cpn);
+    D.pid = (uint32_t *)(base + o_pid);
+    D.frames = (PatchFrame *)(base + o_fr);
+    return cudaSuccess;
+}
+
+int32_t pick_chunk(const dtn_solve_opts *o, int64_t max_walks) {
+    if (o->walk_chunk > 0) return o->walk_chunk;
+    (void)max_walks;
+    return 256;
+}
+
+}  // namespace
+}  // namespace dtn
+
+using namespace dtn;
+
+extern "C" {
+
+const char *dtn_status_string(dtn_status s) {
+    switch (s) {
+        case DTN_OK: return "ok";
+        case DTN_E_INVALID_ARG: return "invalid argument";
+        case DTN_E_OUT_OF_MEMORY: return "out of device memory";
+        case DTN_E_CUDA: return "CUDA runtime error";
+        case DTN_E_NOT_CONVERGED: return "refinement did not converge";
+        case DTN_E_TIMEOUT: return "timed out";
+        case DTN_E_UNSUPPORTED: return "unsupported patch or geometry";
+        case DTN_E_WALK_CAP: return "walks cut at max_steps";
+    }
+    return "unknown status";
+}
+
+int32_t dtn_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out) {
+    if (!desc || !out) return DTN_E_INVALID_ARG;
+    *out = nullptr;
+    const dtn_geometry_desc &d = *desc;
+    if (d.kind == DTN_GEOM_BALL_INTERIOR) {
+        if (!(d.radius > 0)) return DTN_E_INVALID_ARG;
+    } else if (d.kind == DTN_GEOM_BOX_INTERIOR || d.kind == DTN_GEOM_BOX_MINUS_BOXES) {
+        for (int i = 0; i < 3; ++i)
+            if (!(d.hi[i] > d.lo[i])) return DTN_E_INVALID_ARG;
+        if (d.kind == DTN_GEOM_BOX_MINUS_BOXES) {
+            if (d.n_boxes < 0 || (d.n_boxes > 0 && !d.boxes)) return DTN_E_INVALID_ARG;
+            for (int b = 0; b < d.n_boxes; ++b)
+                for (int i = 0; i < 3; ++i) {
+                    const double lo = d.boxes[6 * b + i], hi = d.boxes[6 * b + 3 + i];
+                    if (!(hi > lo) || lo < d.lo[i] || hi > d.hi[i]) return DTN_E_INVALID_ARG;
+                }
+        }
+    } else {
+        return DTN_E_INVALID_ARG;
+    }
+    cudaError_t e = ensure_tables();
+    if (e != cudaSuccess) return to_status(e);
+    dtn_geometry *g = new dtn_geometry();
+    g->host.desc = d;
+    const int nb = d.kind == DTN_GEOM_BOX_MINUS_BOXES ? d.n_boxes : 0;
+    g->host.boxes.assign(d.boxes ? d.boxes : nullptr, d.boxes ? d.boxes + 6 * nb : nullptr);
+    g->host.desc.boxes = g->host.boxes.data();
+    g->host.desc.n_boxes = nb;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    DGeom &dg = g->dg;
+    std::memset(&dg, 0, sizeof(dg));
+    dg.kind = d.kind;
+    for (int i = 0; i < 3; ++i) {
+        dg.c[i] = d.center[i];
+        dg.lo[i] = d.lo[i];
+        dg.hi[i] = d.hi[i];
+    }
+    dg.R = d.radius;
+    dg.nb = nb;
+    dg.gn[0] = dg.gn[1] = dg.gn[2] = 1;
+    dg.cell = 1.0;
+    dg.inv_cell_f = 1.0f;
+    if (d.kind == DTN_GEOM_BOX_MINUS_BOXES) {
+        build_grid(g->host);
+        std::vector<float> bf(g->host.boxes.begin(), g->host.boxes.end());
+        const size_t nbx = std::max<size_t>(g->host.boxes.size(), 1);
+        if ((e = g->d_boxes.reserve(nbx * sizeof(double))) != cudaSuccess ||
+            (e = g->d_boxes_f.reserve(nbx * sizeof(float))) != cudaSuccess ||
+            (e = g->d_cstart.reserve(g->host.cstart.size() * sizeof(int))) != cudaSuccess ||
+            (e = g->d_citems.reserve(std::max<size_t>(g->host.citems.size(), 1) * sizeof(int))) != cudaSuccess ||
+            (e = g->d_ccap.reserve(g->host.ccap.size() * sizeof(float))) != cudaSuccess) {
+            delete g;
+            return to_status(e);
+        }
+        cudaMemcpy(g->d_boxes.p, g->host.boxes.data(), g->host.boxes.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(g->d_boxes_f.p, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(g->d_cstart.p, g->host.cstart.data(), g->host.cstart.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (!g->host.citems.empty())
+            cudaMemcpy(g->d_citems.p, g->host.citems.data(), g->host.citems.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(g->d_ccap.p, g->host.ccap.data(), g->host.ccap.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            delete g;
+            return to_status(e);
+        }
+        dg.boxes = g->d_boxes.as<double>();
+        dg.boxes_f = g->d_boxes_f.as<float>();
+        dg.cstart = g->d_cstart.as<int>();
+        dg.citems = g->d_citems.as<int>();
+        dg.ccap = g->d_ccap.as<float>();
+        for (int i = 0; i < 3; ++i) {
+            dg.gn[i] = g->host.gn[i];
+            dg.glo[i] = g->host.glo[i];
+            dg.glo_f[i] = (float)g->host.glo[i];
+        }
+        dg.cell = g->host.cell;
+        dg.inv_cell_f = (float)(1.0 / g->host.cell);
+    }
+    std::memset(&g->dd, 0, sizeof(g->dd));
+    g->dd.kind = DTN_DATA_CONSTANT;
+    g->dd.inv_scale = 1.0;
+    g->dd.sh = sh_tables_dev();
+    *out = g;
+    return DTN_OK;
+}
+
+dtn_status dtn_destroy_geometry(dtn_geometry *g) {
+    if (!g) return DTN_E_INVALID_ARG;
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&g->d_boxes, &g->d_boxes_f, &g->d_cstart, &g->d_citems, &g->d_ccap, &g->d_clm, &g->d_clm_f,
+                      &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
+                      &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
+                      &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp};
+    for (DevBuf *b : bufs) b->release();
+    for (int k = 0; k < 5; ++k)
+        if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
+    delete g;
+    return DTN_OK;
+}
+
+dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
+    if (!g || !d) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    DData &dd = g->dd;
+    if (d->kind == DTN_DATA_HARMONIC_SH) {
+        if (d->lmax < 0 || d->lmax > kMaxL || !d->clm || !(d->scale > 0)) return DTN_E_INVALID_ARG;
+        const int nc = (d->lmax + 1) * (d->lmax + 1);
+        std::vector<float> cf(d->clm, d->clm + nc);
+        cudaError_t e;
+        if ((e = g->d_clm.reserve(nc * sizeof(double))) != cudaSuccess) return to_status(e);
+        if ((e = g->d_clm_f.reserve(nc * sizeof(float))) != cudaSuccess) return to_status(e);
+        cudaDeviceSynchronize();
+        if ((e = cudaMemcpy(g->d_clm.p, d->clm, nc * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return to_status(e);
+        if ((e = cudaMemcpy(g->d_clm_f.p, cf.data(), nc * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return to_status(e);
+        dd.clm = g->d_clm.as<double>();
+        dd.clm_f = g->d_clm_f.as<float>();
+        dd.lmax = d->lmax;
+    } else if (d->kind != DTN_DATA_POINT_SOURCE && d->kind != DTN_DATA_CONSTANT) {
+        return DTN_E_INVALID_ARG;
+    }
+    dd.kind = d->kind;
+    for (int i = 0; i < 3; ++i) {
+        dd.x0[i] = d->x0[i];
+        dd.ctr[i] = d->center[i];
+    }
+    dd.strength = d->strength;
+    dd.inv_scale = d->kind == DTN_DATA_HARMONIC_SH ? 1.0 / d->scale : 1.0;
+    dd.constant = d->constant;
+    dd.sh = sh_tables_dev();
+    g->score_bound = std::max(score_bound(g->host.desc, *d), 1e-300);
+    g->host.data = *d;
+    if (d->kind == DTN_DATA_HARMONIC_SH) {
+        g->host.clm.assign(d->clm, d->clm + (d->lmax + 1) * (d->lmax + 1));
+        g->host.data.clm = g->host.clm.data();
+    } else {
+        g->host.clm.clear();
+        g->host.data.clm = nullptr;
+    }
+    g->has_data = true;
+    return DTN_OK;
+}
+
+dtn_status dtn_query_patch_sizes(const dtn_patch_batch *b, int64_t *panels_total, int64_t *gamma_total,
+                                 int64_t *matrix_total) {
+    if (!b || b->n_patches < 0) return DTN_E_INVALID_ARG;
+    if (b->n_patches > 0 && (!b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors)) return DTN_E_INVALID_ARG;
+    BatchLayout L;
+    dtn_status st = build_layout(b, L);
+    if (st != DTN_OK) return st;
+    if (panels_total) *panels_total = L.panels_total;
+    if (gamma_total) *gamma_total = L.gamma_total;
+    if (matrix_total) *matrix_total = L.matrix_total;
+    return DTN_OK;
+}
+
+dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dtn_solve_opts *o,
+                             dtn_patch_result *r, void *stream) {
+    if (!g || !b || !o || !r) return DTN_E_INVALID_ARG;
+    if (b->n_patches < 0) return DTN_E_INVALID_ARG;
+    if (b->n_patches == 0) return DTN_OK;
+    if (!b->centers || !b->radius || !b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors) return DTN_E_INVALID_ARG;
+    if (!r->u_gamma_mean || !r->neumann) return DTN_E_INVALID_ARG;
+    if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    if (!o->u_provided) {
+        if (!b->walks_per_point || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
+        for (int64_t p = 0; p < b->n_patches; ++p)
+            if (b->walks_per_point[p] < 2 || b->walks_per_point[p] > 0xFFFFFFFFll) return DTN_E_INVALID_ARG;
+    }
+    if (!g->has_data) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchLayout L;
+    dtn_status st = build_layout(b, L);
+    if (st != DTN_OK) return st;
+    const int32_t chunk = pick_chunk(o, L.max_walks);
+    DevLayout D;
+    int64_t total_chunks = 0;
+    cudaError_t e = upload_layout(g, L, chunk, D, total_chunks, s);
+    if (e != cudaSuccess) return to_status(e);
+    Workspace &W = g->ws;
+    const size_t G = (size_t)L.gamma_total, Pn = (size_t)L.panels_total;
+    if ((e = W.gamma_loc.reserve(G * 3 * 8)) != cudaSuccess || (e = W.gamma_w.reserve(G * 8)) != cudaSuccess ||
+        (e = W.gamma_xyz.reserve(G * 3 * 8)) != cudaSuccess || (e = W.panel_loc.reserve(Pn * 3 * 8)) != cudaSuccess ||
+        (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
+        (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.rhs.reserve(Pn * 8)) != cudaSuccess ||
+        (e = W.se_tmp.reserve(G * 8)) != cudaSuccess)
+        return to_status(e);
+    if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) return to_status(e);
+    double *gxyz = r->gamma_xyz ? r->gamma_xyz : W.gamma_xyz.as<double>();
+    double *gw = r->gamma_w ? r->gamma_w : W.gamma_w.as<double>();
+    double *pg = r->dirichlet ? r->dirichlet : W.panel_g.as<double>();
+    double *A = r->matrix ? r->matrix : W.mat.as<double>();
+    double *rhs = r->rhs ? r->rhs : W.rhs.as<double>();
+    const bool rec = o->record_stages != 0;
+    if (rec) {
+        for (int k = 0; k < 5; ++k)
+            if (!g->stage_ev[k] && (e = cudaEventCreate(&g->stage_ev[k])) != cudaSuccess) return to_status(e);
+        g->stages_recorded = true;
+    }
+    auto mark = [&](int k) -> cudaError_t { return rec ? cudaEventRecord(g->stage_ev[k], s) : cudaSuccess; };
+    if ((e = mark(0)) != cudaSuccess) return to_status(e);
+    // 1. patch setup
+    e = launch_patch_setup(g, L, D, b->centers, b->radius, gxyz, gw, W.gamma_loc.as<double>(), r->colloc_xyz,
+                           r->normals, r->areas, W.panel_loc.as<double>(), W.panel_prm.as<double>(),
+                           W.panel_aux.as<double>(), pg, s);
+    if (e != cudaSuccess) return to_status(e);
+    if ((e = mark(1)) != cudaSuccess) return to_status(e);
+    // 2. walks at the hemisphere nodes (step 1 of the BIE-WOS algorithm)
+    if (!o->u_provided) {
+        WosLaunch w{};
+        w.n_groups = L.n_patches;
+        w.node_off = D.gamma_off;
+        w.walks = D.walks;
+        w.pid = D.pid;
+        w.point_id = nullptr;
+        w.chunk_off = D.chunk_off;
+        w.cpn = D.cpn;
+        w.total_chunks = total_chunks;
+        w.total_nodes = L.gamma_total;
+        w.chunk = chunk;
+        w.max_walks = L.max_walks;
+        w.y = gxyz;
+        w.prec = o->prec;
+        w.eps = o->epsilon;
+        w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
+        w.seed = o->seed;
+        w.blocks_per_sm = o->wos_blocks_per_sm;
+        w.mean = r->u_gamma_mean;
+        w.se = r->u_gamma_se ? r->u_gamma_se : W.se_tmp.as<double>();
+        w.steps = r->gamma_steps;
+        w.capped = r->gamma_capped;
+        if ((e = launch_wos(g, w, s)) != cudaSuccess) return to_status(e);
+    }
+    if ((e = mark(2)) != cudaSuccess) return to_status(e);
+    // 3. assembly of Eq. bw49-bw51 (step 2)
+    e = launch_assemble(g, L, D, o->prec, W.panel_loc.as<double>(), W.panel_prm.as<double>(), W.panel_aux.as<double>(),
+                        pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A, rhs, s);
+    if (e != cudaSuccess) return to_status(e);
+    if ((e = mark(3)) != cudaSuccess) return to_status(e);
+    // 4. collocation solve
+    const int iters = o->max_refine_iters > 0 ? o->max_refine_iters : 10;
+    const double tol = o->refine_tol > 0 ? o->refine_tol : 1e-12;
+    e = launch_lu_solve(g, L, D, o->prec, A, rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
+                        r->patch_status, s);
+    if (e == cudaSuccess) e = mark(4);
+    return to_status(e);
+}
+
+dtn_status dtn_stage_times(dtn_geometry *g, float ms[4]) {
+    if (!g || !ms || !g->stages_recorded) return DTN_E_INVALID_ARG;
+    cudaError_t e = cudaEventSynchronize(g->stage_ev[4]);
+    if (e != cudaSuccess) return to_status(e);
+    for (int k = 0; k < 4; ++k)
+        if ((e = cudaEventElapsedTime(&ms[k], g->stage_ev[k], g->stage_ev[k + 1])) != cudaSuccess) return to_status(e);
+    return DTN_OK;
+}
+
+dtn_status dtn_eval_potential(const dtn_geometry *g, int64_t np, const double *xyz, const double *nrm,
+                              const double *area, const double *q, const double *gv, const int64_t *index,
+                              const int64_t *n_index, int64_t nt, const double *t, double *out, int32_t prec,
+                              void *stream) {
+    if (!g || np < 0 || nt < 0) return DTN_E_INVALID_ARG;
+    if (nt == 0) return DTN_OK;
+    if (!t || !out || (np > 0 && (!xyz || !nrm || !area || !q))) return DTN_E_INVALID_ARG;
+    if (prec != DTN_PREC_FP64 && prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    double *tmp = nullptr;
+    if (!gv && np > 0) {
+        if (!g->has_data) return DTN_E_INVALID_ARG;
+        if ((e = cudaMallocAsync((void **)&tmp, np * sizeof(double), s)) != cudaSuccess) return to_status(e);
+        if ((e = launch_dirichlet(g, np, xyz, tmp, s)) != cudaSuccess) return to_status(e);
+        gv = tmp;
+    }
+    e = launch_potential(np, index, n_index, xyz, nrm, area, q, gv, nt, t, out, prec, g->num_sms, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    return to_status(e);
+}
+
+dtn_status dtn_gather_owned(int64_t np, const double *x, const int64_t *owner, int64_t nc, const double *cent,
+                            uint8_t *keep, int64_t *kept, int64_t *n_kept, void *stream) {
+    if (np < 0 || nc < 0 || !n_kept) return DTN_E_INVALID_ARG;
+    if (np > 0 && (!x || !owner || !keep || !kept || nc == 0 || !cent)) return DTN_E_INVALID_ARG;
+    return to_status(launch_gather(np, x, owner, nc, cent, keep, kept, n_kept, (cudaStream_t)stream));
+}
+
+dtn_status dtn_wos_points(const dtn_geometry *gc, int64_t n, const double *y, const uint32_t *point_ids,
+                          const uint32_t *patch_ids, const int64_t *walks, const dtn_solve_opts *o, double *mean,
+                          double *se, uint64_t *steps, uint32_t *capped, void *stream) {
+    dtn_geometry *g = const_cast<dtn_geometry *>(gc);
+    if (!g || n < 0 || !o) return DTN_E_INVALID_ARG;
+    if (n == 0) return DTN_OK;
+    if (!y || !point_ids || !patch_ids || !walks || !mean || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
+    if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    if (!g->has_data) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t maxw = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (walks[i] < 2 || walks[i] > 0xFFFFFFFFll) return DTN_E_INVALID_ARG;
+        maxw = std::max(maxw, walks[i]);
+    }
+    const int32_t chunk = pick_chunk(o, maxw);
+    std::vector<int64_t> node_off(n + 1), chunk_off(n + 1, 0);
+    std::vector<int32_t> cpn(n);
+    for (int64_t i = 0; i <= n; ++i) node_off[i] = i;
+    for (int64_t i = 0; i < n; ++i) {
+        cpn[i] = (int32_t)((walks[i] + chunk - 1) / chunk);
+        chunk_off[i + 1] = chunk_off[i] + cpn[i];
+    }
+    // device staging: node_off, chunk_off, walks, cpn
+    const size_t bytes = (size_t)(3 * (n + 1)) * 8 + (size_t)n * 4 + 64;
+    cudaError_t e = g->ws.counter.reserve(bytes);
+    if (e != cudaSuccess) return to_status(e);
+    char *base = g->ws.counter.as<char>();
+    int64_t *d_node = (int64_t *)base, *d_chunk = d_node + (n + 1), *d_walks = d_chunk + (n + 1);
+    int32_t *d_cpn = (int32_t *)(d_walks + (n + 1));
+    if ((e = cudaMemcpyAsync(d_node, node_off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_chunk, chunk_off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_walks, walks, n * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_cpn, cpn.data(), n * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return to_status(e);
+    WosLaunch w{};
+    w.n_groups = n;
+    w.node_off = d_node;
+    w.walks = d_walks;
+    w.pid = patch_ids;
+    w.point_id = point_ids;
+    w.chunk_off = d_chunk;
+    w.cpn = d_cpn;
+    w.total_chunks = chunk_off[n];
+    w.total_nodes = n;
+    w.chunk = chunk;
+    w.max_walks = maxw;
+    w.y = y;
+    w.prec = o->prec;
+    w.eps = o->epsilon;
+    w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
+    w.seed = o->seed;
+    w.blocks_per_sm = o->wos_blocks_per_sm;
+    w.mean = mean;
+    if (!se) {
+        if ((e = g->ws.se_tmp.reserve(n * 8)) != cudaSuccess) return to_status(e);
+        se = g->ws.se_tmp.as<double>();
+    }
+    w.se = se;
+    w.steps = steps;
+    w.capped = capped;
+    e = launch_wos(g, w, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
+    return to_status(e);
+}
+
+dtn_status dtn_distance(const dtn_geometry *g, int64_t n, const double *x, double *d, double *nearest, int32_t prec,
+                        void *stream) {
+    if (!g || n < 0 || (n > 0 && !x)) return DTN_E_INVALID_ARG;
+    if (prec != DTN_PREC_FP64 && prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    return to_status(launch_distance(g, n, x, d, nearest, prec, (cudaStream_t)stream));
+}
+
+dtn_status dtn_philox4x32_10(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out, void *stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return DTN_E_INVALID_ARG;
+    return to_status(launch_philox(n, ctr, seed, out, (cudaStream_t)stream));
+}
+
+dtn_status dtn_eval_dirichlet(const dtn_geometry *g, int64_t n, const double *x, double *out, void *stream) {
+    if (!g || n < 0 || (n > 0 && (!x || !out))) return DTN_E_INVALID_ARG;
+    if (!g->has_data) return DTN_E_INVALID_ARG;
+    return to_status(launch_dirichlet(g, n, x, out, (cudaStream_t)stream));
+}
+
+}  // extern "C"

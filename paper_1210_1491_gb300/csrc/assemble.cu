@@ -1,0 +1,337 @@
+// assemble.cu -- collocation matrix and right side of the first-kind local BIE
+// (Eq. bw49-bw51) on piecewise-constant panels, one CTA per collocation row:
+//
+//   A_ij = int_{panel j} G(x_i, y) ds_y                       (single layer, Eq. bw50)
+//   b_i  = int_S dG/dn_y(x_i, y) (g(y) - g(x_i)) ds_y
+//          - sum_k W_k P(x_i, y_k) (U_k - g(x_i))
+//
+// with G the whole-sphere Dirichlet Green's function of the patch ball and P its
+// Poisson kernel.  b is Eq. bw51 with the constant solution subtracted (the
+// identity 1/2 + p.v. int_S dG/dn_y + int_Gamma dG/dn_y = 0 times g(x_i)), the
+// regularisation Sec. 3 applies to its single-point formula (Eq. bw61-bw68).
+// On a plane through the ball centre dG/dn_y vanishes, so disk patches have
+// no S term.
+//
+// Quadrature (per entry, in the panel's (u, v) parameters):
+//   self panel   : four triangles from the collocation point, each through the
+//                  Duffy map (the local polar transform of Sec. 5.2), FP64;
+//   other panels : tensor Gauss-Legendre whose order follows the ratio r of the
+//                  distance from the singular points (x_i and its Kelvin image)
+//                  to the panel centre over the panel radius; below r = 2 the
+//                  parameter box is split into four, recursively.  Mixed
+//                  precision evaluates panels with r >= 2 in FP32 and keeps the
+//                  split (near-singular) cases and the rim image term in FP64.
+#include <cmath>
+
+#include "dtn_internal.h"
+
+namespace dtn {
+
+namespace {
+
+constexpr int kAsmThreads = 128;
+constexpr int kMaxDepth = 10;
+constexpr int kStack = 40;
+
+template <typename T>
+struct Ctx {
+    int kind;
+    T a, R;
+    T X[3], xn;
+    T Xs[3];
+    bool img;
+    bool needD;
+    T gx;
+    T c[3], t1[3], t2[3], n[3];
+    const DData *dat;
+};
+
+template <typename T>
+__device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa, T &sd) {
+    T Y[3], nl[3], J;
+    patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+    const T wj = w * J;
+    sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
+    if (c.needD) {
+        const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+        const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+        const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+        const T gy = dirichlet_eval<T>(*c.dat, yx, yy, yz);
+        sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
+    }
+}
+
+// parameter region: rectangle (u0, du, v0, dv) or Duffy triangle
+// (S_u, S_v, E1_u, E1_v, E2_u, E2_v) mapped from (xi, eta) in [0,1]^2
+struct Region {
+    bool tri;
+    double p[6];
+    double det;
+};
+
+template <typename T>
+__device__ __forceinline__ void map_uv(const Region &R, T xi, T eta, T &u, T &v, T &jac) {
+    if (!R.tri) {
+        u = (T)R.p[0] + xi * (T)R.p[1];
+        v = (T)R.p[2] + eta * (T)R.p[3];
+        jac = (T)(R.p[1] * R.p[3]);
+    } else {
+        u = (T)R.p[0] + xi * ((T)R.p[2] + eta * (T)R.p[4]);
+        v = (T)R.p[1] + xi * ((T)R.p[3] + eta * (T)R.p[5]);
+        jac = xi * (T)R.det;
+    }
+}
+
+template <typename T>
+__device__ void gauss_square(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, int n,
+                             const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
+    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
+    const T hx = (T)0.5 * (x1 - x0), mx = (T)0.5 * (x0 + x1);
+    const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
+    for (int i = 0; i < n; ++i) {
+        const T xi = mx + hx * (T)gx[i];
+        const T wi = (T)gw[i] * hx * he;
+        for (int j = 0; j < n; ++j) {
+            const T eta = me + he * (T)gx[j];
+            T u, v, jac;
+            map_uv<T>(R, xi, eta, u, v, jac);
+            eval_point<T>(c, u, v, wi * (T)gw[j] * jac, sa, sd);
+        }
+    }
+}
+
+// Gauss order from the distance ratio r (0: split further).  FP64 orders aim at
+// 1e-15 relative for a singularity next to the middle of a panel edge, FP32
+// orders at 1e-8.
+__device__ __forceinline__ int order64(double r) {
+    if (r >= 20.0) return 5;
+    if (r >= 10.0) return 6;
+    if (r >= 5.0) return 9;
+    if (r >= 3.0) return 12;
+    if (r >= 2.0) return 20;
+    return 0;
+}
+__device__ __forceinline__ int order32(double r) {
+    if (r >= 20.0) return 3;
+    if (r >= 10.0) return 4;
+    if (r >= 5.0) return 5;
+    if (r >= 3.0) return 7;
+    if (r >= 2.0) return 11;
+    return 0;
+}
+
+// distance ratio of a sub-square: min distance from the singular points to the
+// square's physical centre over the largest centre-to-(corner or edge midpoint)
+// distance
+template <typename T>
+__device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, bool withX) {
+    T uc, vc, jac, Yc[3], nl[3], J;
+    map_uv<T>(R, (T)0.5 * (x0 + x1), (T)0.5 * (e0 + e1), uc, vc, jac);
+    patch_point<T>(c.kind, c.R, uc, vc, Yc, nl, J);
+    T rad = (T)0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            if (a == 1 && b == 1) continue;
+            T u, v, Y[3];
+            map_uv<T>(R, x0 + (T)0.5 * a * (x1 - x0), e0 + (T)0.5 * b * (e1 - e0), u, v, jac);
+            patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+            const T d2 = (Y[0] - Yc[0]) * (Y[0] - Yc[0]) + (Y[1] - Yc[1]) * (Y[1] - Yc[1]) +
+                         (Y[2] - Yc[2]) * (Y[2] - Yc[2]);
+            rad = fmax(rad, sqrt(d2));
+        }
+    T dmin = (T)INFINITY;
+    if (withX) {
+        const T d2 = (c.X[0] - Yc[0]) * (c.X[0] - Yc[0]) + (c.X[1] - Yc[1]) * (c.X[1] - Yc[1]) +
+                     (c.X[2] - Yc[2]) * (c.X[2] - Yc[2]);
+        dmin = sqrt(d2);
+    }
+    if (c.img) {
+        const T d2 = (c.Xs[0] - Yc[0]) * (c.Xs[0] - Yc[0]) + (c.Xs[1] - Yc[1]) * (c.Xs[1] - Yc[1]) +
+                     (c.Xs[2] - Yc[2]) * (c.Xs[2] - Yc[2]);
+        dmin = fmin(dmin, sqrt(d2));
+    }
+    return rad > (T)0 ? dmin / rad : (T)INFINITY;
+}
+
+template <typename T>
+__device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, int min_order,
+                                 const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
+    struct Sq { T x0, x1, e0, e1; int depth; };
+    Sq stack[kStack];
+    int sp = 0;
+    stack[sp++] = Sq{(T)0, (T)1, (T)0, (T)1, 0};
+    while (sp > 0) {
+        const Sq q = stack[--sp];
+        const T r = square_ratio<T>(c, R, q.x0, q.x1, q.e0, q.e1, withX);
+        int n = order64((double)r);
+        if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
+            const T xm = (T)0.5 * (q.x0 + q.x1), em = (T)0.5 * (q.e0 + q.e1);
+            stack[sp++] = Sq{q.x0, xm, q.e0, em, q.depth + 1};
+            stack[sp++] = Sq{xm, q.x1, q.e0, em, q.depth + 1};
+            stack[sp++] = Sq{q.x0, xm, em, q.e1, q.depth + 1};
+            stack[sp++] = Sq{xm, q.x1, em, q.e1, q.depth + 1};
+            continue;
+        }
+        if (n == 0) n = 20;
+        if (n < min_order) n = min_order;
+        gauss_square<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
+    }
+}
+
+template <typename T>
+__device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double gx, const DData *dat) {
+    c.kind = f.kind;
+    c.a = (T)f.a;
+    c.R = (T)f.R;
+    for (int d = 0; d < 3; ++d) {
+        c.X[d] = (T)X[d];
+        c.c[d] = (T)f.c[d]; c.t1[d] = (T)f.t1[d]; c.t2[d] = (T)f.t2[d]; c.n[d] = (T)f.n[d];
+    }
+    const double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    c.xn = (T)sqrt(xx);
+    c.img = xx > 0.0;
+    if (c.img)
+        for (int d = 0; d < 3; ++d) c.Xs[d] = (T)(f.a * f.a * X[d] / xx);
+    c.needD = (f.kind == kCap);
+    c.gx = (T)gx;
+    c.dat = dat;
+}
+
+struct AsmDev {
+    const PatchFrame *frames;
+    const int64_t *panel_off, *gamma_off, *mat_off;
+    const int32_t *ns, *nr;
+    const double *panel_loc, *panel_prm, *panel_aux, *panel_g;
+    const double *gamma_loc, *gamma_w, *U;
+    double *A, *b;
+    DData dat;
+    int64_t n_patches;
+    int prec;
+    const double *glx, *glw;
+};
+
+__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
+    const int64_t row = blockIdx.x;
+    const int64_t p = find_group(P.panel_off, P.n_patches, row);
+    const PatchFrame f = P.frames[p];
+    const int64_t poff = P.panel_off[p];
+    const int n = (int)(P.panel_off[p + 1] - poff);
+    const int i = (int)(row - poff);
+    __shared__ double red[2][kAsmThreads / 32];
+    if (f.status != DTN_OK) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) P.A[P.mat_off[p] + (int64_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+        if (threadIdx.x == 0) P.b[row] = 0.0;
+        return;
+    }
+    const double X[3] = {P.panel_loc[3 * row], P.panel_loc[3 * row + 1], P.panel_loc[3 * row + 2]};
+    const double gx = P.panel_g[row];
+    Ctx<double> c64;
+    make_ctx<double>(c64, f, X, gx, &P.dat);
+    Ctx<float> c32;
+    make_ctx<float>(c32, f, X, gx, &P.dat);
+    double dsum = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t pj = poff + j;
+        const double *prm = P.panel_prm + 6 * pj;
+        double sa = 0.0, sd = 0.0;
+        if (j == i) {
+            // self panel: triangles from the collocation point (uc, vc) to each side
+            const double S[2] = {prm[4], prm[5]};
+            const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
+            const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
+            for (int e = 0; e < 4; ++e) {
+                Region R;
+                R.tri = true;
+                R.p[0] = S[0]; R.p[1] = S[1];
+                R.p[2] = cu[e] - S[0]; R.p[3] = cv[e] - S[1];
+                R.p[4] = cu[e + 1] - cu[e]; R.p[5] = cv[e + 1] - cv[e];
+                R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
+                if (R.det == 0.0) continue;
+                integrate_region<double>(c64, R, false, 16, P.glx, P.glw, sa, sd);
+            }
+        } else {
+            const double *ax = P.panel_aux + 4 * pj;
+            double dmin = sqrt((X[0] - ax[0]) * (X[0] - ax[0]) + (X[1] - ax[1]) * (X[1] - ax[1]) +
+                               (X[2] - ax[2]) * (X[2] - ax[2]));
+            if (c64.img) {
+                const double d2 = (c64.Xs[0] - ax[0]) * (c64.Xs[0] - ax[0]) + (c64.Xs[1] - ax[1]) * (c64.Xs[1] - ax[1]) +
+                                  (c64.Xs[2] - ax[2]) * (c64.Xs[2] - ax[2]);
+                dmin = fmin(dmin, sqrt(d2));
+            }
+            const double r = dmin / ax[3];
+            Region R;
+            R.tri = false;
+            R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
+            R.det = 0.0;
+            if (r >= 2.0) {
+                if (P.prec == DTN_PREC_MIXED) {
+                    float a32 = 0.f, d32 = 0.f;
+                    gauss_square<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
+                    sa = a32; sd = d32;
+                } else {
+                    gauss_square<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
+                }
+            } else {
+                integrate_region<double>(c64, R, true, 0, P.glx, P.glw, sa, sd);
+            }
+        }
+        P.A[P.mat_off[p] + (int64_t)i * n + j] = sa;
+        dsum += sd;
+    }
+    // Gamma term: sum_k W_k P(x_i, y_k) (U_k - g(x_i)), FP64
+    const int64_t goff = P.gamma_off[p];
+    const int nk = (int)(P.gamma_off[p + 1] - goff);
+    double gsum = 0.0;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const int64_t gk = goff + k;
+        const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
+        gsum += P.gamma_w[gk] * poisson_ball<double>(f.a, X, Y) * (P.U[gk] - gx);
+    }
+    double v0 = dsum, v1 = gsum;
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red[0][w] = v0; red[1][w] = v1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = 0; k < kAsmThreads / 32; ++k) { s0 += red[0][k]; s1 += red[1][k]; }
+        P.b[row] = s0 - s1;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
+                            const double *panel_loc, const double *panel_prm, const double *panel_aux,
+                            const double *panel_g, const double *gamma_loc, const double *gamma_w,
+                            const double *U, double *A, double *b, cudaStream_t s) {
+    if (L.panels_total == 0) return cudaSuccess;
+    AsmDev P;
+    P.frames = D.frames;
+    P.panel_off = D.panel_off;
+    P.gamma_off = D.gamma_off;
+    P.mat_off = D.mat_off;
+    P.ns = D.ns;
+    P.nr = D.nr;
+    P.panel_loc = panel_loc;
+    P.panel_prm = panel_prm;
+    P.panel_aux = panel_aux;
+    P.panel_g = panel_g;
+    P.gamma_loc = gamma_loc;
+    P.gamma_w = gamma_w;
+    P.U = U;
+    P.A = A;
+    P.b = b;
+    P.dat = g->dd;
+    P.n_patches = L.n_patches;
+    P.prec = prec;
+    P.glx = gl_x_dev();
+    P.glw = gl_w_dev();
+    assemble_kernel<<<(unsigned)L.panels_total, kAsmThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace dtn

@@ -1,0 +1,355 @@
+// dtn_device.cuh -- device-side building blocks of the walk-on-spheres /
+// local-BIE path: counter RNG, distance to the boundary, Dirichlet data, and
+// the whole-sphere Green's function of the patch ball.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dtn {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxL = 16;                 // highest spherical-harmonic degree
+constexpr int kMaxSmemBoxes = 1024;       // obstacle boxes staged in shared memory
+
+// ------------------------------------------------------------------ RNG
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// products (multipliers D2511F53, CD9E8D57) and xors with the key, the key
+// advancing by the Weyl increments 9E3779B9, BB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniforms in (0,1), never 0 or 1: an odd integer times a power of two.
+__device__ __forceinline__ float u01_24(uint32_t w) {
+    return __uint2float_rn((w >> 8) | 1u) * 0x1p-24f;
+}
+__device__ __forceinline__ double u01_53(uint32_t hi, uint32_t lo) {
+    const unsigned long long v = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
+    return __ull2double_rn(v | 1ull) * 0x1p-53;
+}
+
+// ------------------------------------------------------------------ geometry
+enum GeomKind : int { kBall = 0, kBox = 1, kBoxMinusBoxes = 2 };
+
+struct DGeom {
+    int kind;
+    double c[3], R;          // ball
+    double lo[3], hi[3];     // outer box
+    int nb;                  // obstacle boxes
+    const double *boxes;     // nb x 6
+    const float *boxes_f;    // nb x 6
+    // obstacle lookup grid over the outer box: per cell, the boxes within the
+    // listing distance (CSR) and a lower bound of the distance from the cell to
+    // every box not listed
+    int gn[3];
+    double glo[3], cell;
+    float glo_f[3], inv_cell_f;
+    const int *cstart;
+    const int *citems;
+    const float *ccap;
+};
+
+template <typename T> struct Vec3 { T x, y, z; };
+
+// Distance from x to the boundary, the radius of the largest empty sphere
+// used by one walk step.  For the box-minus-boxes region the obstacle part
+// only looks at the boxes listed for x's grid cell and caps the result at the
+// cell's bound for all others, which is a valid (never larger) radius and
+// exact whenever it is below the bound.  `sb` are the boxes staged in shared
+// memory (kind 2, T = float) or nullptr.
+template <typename T>
+__device__ __forceinline__ T box_interior_dist(const DGeom &g, T x, T y, T z) {
+    T d = x - (T)g.lo[0];
+    d = fmin(d, (T)g.hi[0] - x);
+    d = fmin(d, y - (T)g.lo[1]);
+    d = fmin(d, (T)g.hi[1] - y);
+    d = fmin(d, z - (T)g.lo[2]);
+    d = fmin(d, (T)g.hi[2] - z);
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ T box_exterior_dist(const T *b, T x, T y, T z) {
+    const T ex = fmax(fmax(b[0] - x, (T)0), x - b[3]);
+    const T ey = fmax(fmax(b[1] - y, (T)0), y - b[4]);
+    const T ez = fmax(fmax(b[2] - z, (T)0), z - b[5]);
+    return sqrt(ex * ex + ey * ey + ez * ez);
+}
+
+// Grid cell of a point (FP32 index arithmetic: a point near a cell face may be
+// filed in the neighbouring cell, whose candidate list is built with a margin
+// that covers this).
+template <typename T>
+__device__ __forceinline__ int grid_cell(const DGeom &g, T x, T y, T z) {
+    int ix = (int)floorf(((float)x - g.glo_f[0]) * g.inv_cell_f);
+    int iy = (int)floorf(((float)y - g.glo_f[1]) * g.inv_cell_f);
+    int iz = (int)floorf(((float)z - g.glo_f[2]) * g.inv_cell_f);
+    ix = min(max(ix, 0), g.gn[0] - 1);
+    iy = min(max(iy, 0), g.gn[1] - 1);
+    iz = min(max(iz, 0), g.gn[2] - 1);
+    return (iz * g.gn[1] + iy) * g.gn[0] + ix;
+}
+
+template <typename T, int GK>
+__device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z) {
+    if (GK == kBall) {
+        const T dx = x - (T)g.c[0], dy = y - (T)g.c[1], dz = z - (T)g.c[2];
+        return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
+    } else if (GK == kBox) {
+        return box_interior_dist<T>(g, x, y, z);
+    } else {
+        T d = box_interior_dist<T>(g, x, y, z);
+        const int c = grid_cell<T>(g, x, y, z);
+        d = fmin(d, (T)g.ccap[c]);
+        const int e = g.cstart[c + 1];
+        for (int i = g.cstart[c]; i < e; ++i) {
+            const int b = g.citems[i];
+            const T *bb;
+            T tmp[6];
+            if (sb) {
+                bb = sb + 6 * b;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) tmp[k] = (T)g.boxes[6 * b + k];
+                bb = tmp;
+            }
+            d = fmin(d, box_exterior_dist<T>(bb, x, y, z));
+        }
+        return d;
+    }
+}
+
+// Nearest boundary point (the absorption point whose data are scored), exact
+// over the same candidates; ties take the lowest face index, the outer box
+// before obstacles, and obstacles in index order.
+template <typename T>
+__device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &ny, T &nz) {
+    if (g.kind == kBall) {
+        const T dx = x - (T)g.c[0], dy = y - (T)g.c[1], dz = z - (T)g.c[2];
+        const T r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r > (T)0) {
+            const T s = (T)g.R / r;
+            nx = (T)g.c[0] + s * dx; ny = (T)g.c[1] + s * dy; nz = (T)g.c[2] + s * dz;
+        } else {
+            nx = (T)g.c[0]; ny = (T)g.c[1]; nz = (T)g.c[2] + (T)g.R;
+        }
+        return (T)g.R - r;
+    }
+    const T xs[3] = {x, y, z};
+    T best = (T)INFINITY;
+    int bf = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1;
+        const T d = (f & 1) ? (T)g.hi[ax] - xs[ax] : xs[ax] - (T)g.lo[ax];
+        if (d < best) { best = d; bf = f; }
+    }
+    T p[3] = {x, y, z};
+    p[bf >> 1] = (bf & 1) ? (T)g.hi[bf >> 1] : (T)g.lo[bf >> 1];
+    if (g.kind == kBoxMinusBoxes) {
+        const int c = grid_cell<T>(g, x, y, z);
+        const int e = g.cstart[c + 1];
+        for (int i = g.cstart[c]; i < e; ++i) {
+            const int b = g.citems[i];
+            T bb[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) bb[k] = sb ? sb[6 * b + k] : (T)g.boxes[6 * b + k];
+            const T d = box_exterior_dist<T>(bb, x, y, z);
+            if (d < best) {
+                best = d;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) p[k] = fmin(fmax(xs[k], bb[k]), bb[k + 3]);
+            }
+        }
+    }
+    nx = p[0]; ny = p[1]; nz = p[2];
+    return best;
+}
+
+// ------------------------------------------------------------------ data
+enum DataKind : int { kPointSource = 0, kHarmonicSH = 1, kConstant = 2 };
+
+// normalised associated-Legendre recurrence coefficients, filled at load time:
+// A[l][m] = sqrt((4l^2-1)/(l^2-m^2)), B[l][m] = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)),
+// D[m] = sqrt((2m+1)/(2m))
+struct ShTables {
+    double A[kMaxL + 1][kMaxL + 1], B[kMaxL + 1][kMaxL + 1], D[kMaxL + 1];
+    float Af[kMaxL + 1][kMaxL + 1], Bf[kMaxL + 1][kMaxL + 1], Df[kMaxL + 1];
+};
+
+struct DData {
+    int kind;
+    double x0[3], strength;
+    int lmax;
+    const double *clm;      // (lmax+1)^2
+    const float *clm_f;
+    double ctr[3], inv_scale;
+    double constant;
+    const ShTables *sh;     // device copy of the recurrence tables
+};
+
+template <typename T> __device__ __forceinline__ T sh_A(const ShTables *t, int l, int m);
+template <> __device__ __forceinline__ double sh_A<double>(const ShTables *t, int l, int m) { return t->A[l][m]; }
+template <> __device__ __forceinline__ float sh_A<float>(const ShTables *t, int l, int m) { return t->Af[l][m]; }
+template <typename T> __device__ __forceinline__ T sh_B(const ShTables *t, int l, int m);
+template <> __device__ __forceinline__ double sh_B<double>(const ShTables *t, int l, int m) { return t->B[l][m]; }
+template <> __device__ __forceinline__ float sh_B<float>(const ShTables *t, int l, int m) { return t->Bf[l][m]; }
+template <typename T> __device__ __forceinline__ T sh_D(const ShTables *t, int m);
+template <> __device__ __forceinline__ double sh_D<double>(const ShTables *t, int m) { return t->D[m]; }
+template <> __device__ __forceinline__ float sh_D<float>(const ShTables *t, int m) { return t->Df[m]; }
+template <typename T> __device__ __forceinline__ T clm_at(const DData &d, int i);
+template <> __device__ __forceinline__ double clm_at<double>(const DData &d, int i) { return d.clm[i]; }
+template <> __device__ __forceinline__ float clm_at<float>(const DData &d, int i) { return d.clm_f[i]; }
+
+// sum c_lm rho^l Y_lm(direction) with orthonormal real harmonics (no
+// Condon-Shortley phase), by the normalised Legendre recurrences in m and l
+// and the angle-addition recurrence for cos(m phi), sin(m phi).
+template <typename T>
+__device__ T harmonic_eval(const DData &d, T x, T y, T z) {
+    x = (x - (T)d.ctr[0]) * (T)d.inv_scale;
+    y = (y - (T)d.ctr[1]) * (T)d.inv_scale;
+    z = (z - (T)d.ctr[2]) * (T)d.inv_scale;
+    const T rxy2 = x * x + y * y;
+    const T r = sqrt(rxy2 + z * z);
+    const T y00 = (T)0.28209479177387814;  // 1/sqrt(4 pi)
+    if (r == (T)0) return clm_at<T>(d, 0) * y00;
+    const T rxy = sqrt(rxy2);
+    const T ct = z / r, st = rxy / r;
+    const T cp = rxy > (T)0 ? x / rxy : (T)1, sp = rxy > (T)0 ? y / rxy : (T)0;
+    const T sqrt2 = (T)1.4142135623730951;
+    T acc = (T)0;
+    T pmm = y00, cm = (T)1, sm = (T)0, rm = (T)1;
+    for (int m = 0; m <= d.lmax; ++m) {
+        if (m > 0) {
+            pmm *= sh_D<T>(d.sh, m) * st;
+            const T c2 = cm * cp - sm * sp;
+            sm = sm * cp + cm * sp;
+            cm = c2;
+            rm *= r;
+        }
+        T p1 = pmm, p2 = (T)0, rl = rm;
+        for (int l = m; l <= d.lmax; ++l) {
+            if (l > m) {
+                const T p = sh_A<T>(d.sh, l, m) * (ct * p1 - sh_B<T>(d.sh, l, m) * p2);
+                p2 = p1;
+                p1 = p;
+                rl *= r;
+            }
+            const int base = l * l + l;
+            if (m == 0) {
+                acc += clm_at<T>(d, base) * rl * p1;
+            } else {
+                acc += sqrt2 * rl * p1 * (clm_at<T>(d, base + m) * cm + clm_at<T>(d, base - m) * sm);
+            }
+        }
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T dirichlet_eval(const DData &d, T x, T y, T z) {
+    if (d.kind == kPointSource) {
+        const T dx = x - (T)d.x0[0], dy = y - (T)d.x0[1], dz = z - (T)d.x0[2];
+        return (T)(d.strength / (4.0 * kPi)) / sqrt(dx * dx + dy * dy + dz * dz);
+    } else if (d.kind == kHarmonicSH) {
+        return harmonic_eval<T>(d, x, y, z);
+    }
+    return (T)d.constant;
+}
+
+// ------------------------------------------------------------------ Green's functions
+// Whole-sphere Dirichlet Green's function of B(c, a), local coordinates X = x - c,
+// Y = y - c: free-space term minus the Kelvin image of charge a/|Y| at a^2 Y/|Y|^2,
+//   G = (1/4pi) [ 1/|X - Y| - a / sqrt(Q) ],
+//   Q = |X|^2|Y|^2 - 2a^2 X.Y + a^4 = (a^2 - |X||Y|)^2 + a^2 |X||Y| |Xh - Yh|^2,
+// the second form (no cancellation near the rim) with Xh, Yh unit vectors.
+template <typename T>
+__device__ __forceinline__ T image_q(T a2, const T *X, T xn, const T *Y) {
+    const T yn = sqrt(Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2]);
+    const T p = xn * yn;
+    const T t = a2 - p;
+    if (xn == (T)0 || yn == (T)0) return t * t;
+    // |X|Y| - Y|X||^2 / (|X||Y|) = |X||Y| |Xh - Yh|^2
+    const T ux = X[0] * yn - Y[0] * xn, uy = X[1] * yn - Y[1] * xn, uz = X[2] * yn - Y[2] * xn;
+    return t * t + a2 * (ux * ux + uy * uy + uz * uz) / p;
+}
+
+template <typename T>
+__device__ __forceinline__ T green_ball(T a, const T *X, T xn, const T *Y) {
+    const T dx = X[0] - Y[0], dy = X[1] - Y[1], dz = X[2] - Y[2];
+    const T r = sqrt(dx * dx + dy * dy + dz * dz);
+    const T Q = image_q<T>(a * a, X, xn, Y);
+    return ((T)1 / r - a / sqrt(Q)) * (T)(0.25 / kPi);
+}
+
+// n_y . grad_Y G = (1/4pi) [ n.(X-Y)/|X-Y|^3 + a n.(|X|^2 Y - a^2 X) / Q^{3/2} ]
+template <typename T>
+__device__ __forceinline__ T green_ball_dny(T a, const T *X, T xn, const T *Y, const T *ny) {
+    const T dx = X[0] - Y[0], dy = X[1] - Y[1], dz = X[2] - Y[2];
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T r = sqrt(r2);
+    const T a2 = a * a;
+    const T Q = image_q<T>(a2, X, xn, Y);
+    const T sQ = sqrt(Q);
+    const T xx = xn * xn;
+    const T t1 = (ny[0] * dx + ny[1] * dy + ny[2] * dz) / (r2 * r);
+    const T t2 = a * (xx * (ny[0] * Y[0] + ny[1] * Y[1] + ny[2] * Y[2]) -
+                      a2 * (ny[0] * X[0] + ny[1] * X[1] + ny[2] * X[2])) / (Q * sQ);
+    return (t1 + t2) * (T)(0.25 / kPi);
+}
+
+// Poisson kernel of the ball, -dG/dn_y on |Y| = a: (a^2 - |X|^2) / (4 pi a |X - Y|^3)
+template <typename T>
+__device__ __forceinline__ T poisson_ball(T a, const T *X, const T *Y) {
+    const T dx = X[0] - Y[0], dy = X[1] - Y[1], dz = X[2] - Y[2];
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    return (a * a - xx) / ((T)(4.0 * kPi) * a * r2 * sqrt(r2));
+}
+
+// ------------------------------------------------------------------ patches
+enum PatchKind : int { kDisk = 0, kCap = 1 };
+
+// Local frame of a patch: n = outward normal of D at c; t1 = normalised
+// projection of the coordinate axis least aligned with n (lowest index on
+// ties); t2 = n x t1.
+struct PatchFrame {
+    double c[3], n[3], t1[3], t2[3];
+    double a, R, theta_max, umax;
+    int kind, status;
+};
+
+// point of the patch at parameters (u, v), local coordinates (t1, t2, n),
+// its local unit normal and the area Jacobian.  Disk: Y = u (cos v, sin v, 0),
+// J = u.  Cap (boundary sphere of radius R through c, centre c - R n):
+// Y = (R sin u cos v, R sin u sin v, -2R sin^2(u/2)), J = R^2 sin u.
+template <typename T>
+__device__ __forceinline__ void patch_point(int kind, T R, T u, T v, T *Y, T *nl, T &J) {
+    T sv, cv;
+    sincos(v, &sv, &cv);
+    if (kind == kDisk) {
+        Y[0] = u * cv; Y[1] = u * sv; Y[2] = (T)0;
+        nl[0] = (T)0; nl[1] = (T)0; nl[2] = (T)1;
+        J = u;
+    } else {
+        T su, cu;
+        sincos(u, &su, &cu);
+        const T sh = sin((T)0.5 * u);
+        Y[0] = R * su * cv; Y[1] = R * su * sv; Y[2] = (T)-2 * R * sh * sh;
+        nl[0] = su * cv; nl[1] = su * sv; nl[2] = cu;
+        J = R * R * su;
+    }
+}
+
+}  // namespace dtn

@@ -1,0 +1,183 @@
+// dtn_internal.h -- host-side structures shared by the translation units of
+// the library (geometry object, per-call batch layout, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/dtn.h"
+#include "dtn_device.cuh"
+
+namespace dtn {
+
+// A device buffer that only grows; freed with the geometry object.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Per-call layout of a batch on the device (offsets are prefix sums over
+// patches in batch order).
+struct BatchLayout {
+    int64_t n_patches = 0;
+    int64_t gamma_total = 0, panels_total = 0, matrix_total = 0;
+    int32_t max_panels = 0, max_nodes = 0;
+    int64_t max_walks = 0;
+    std::vector<int64_t> gamma_off, panel_off, mat_off;   // n+1
+    std::vector<int32_t> nt, nph, nr, ns;                 // n
+    std::vector<int64_t> walks;                           // n
+    std::vector<uint32_t> pid;                            // n
+};
+
+// Device copies of one layout (kept in the geometry workspace).
+struct DevLayout {
+    int64_t *gamma_off, *panel_off, *mat_off, *walks, *chunk_off;
+    int32_t *nt, *nph, *nr, *ns, *cpn;
+    uint32_t *pid;
+    PatchFrame *frames;
+};
+
+struct Workspace {
+    DevBuf layout;          // DevLayout arrays
+    DevBuf gamma_loc;       // gamma_total x 3 (local node coordinates)
+    DevBuf gamma_w;         // gamma_total
+    DevBuf gamma_xyz;       // gamma_total x 3
+    DevBuf panel_loc;       // panels_total x 3 (local collocation coordinates)
+    DevBuf panel_prm;       // panels_total x 4 (u0, u1, v0, v1) + (uc, vc)
+    DevBuf panel_aux;       // panels_total x 4: local centre xyz + bounding radius
+    DevBuf panel_g;         // panels_total
+    DevBuf mat;             // matrix_total doubles (assembled A)
+    DevBuf lu32;            // matrix_total floats (LU factors when not in shared memory)
+    DevBuf lu64;            // matrix_total doubles (FP64 LU when not in shared memory)
+    DevBuf rhs;             // panels_total
+    DevBuf acc;             // WOS accumulators: 3 x u64 + u32 per node
+    DevBuf counter;         // work counter(s)
+    DevBuf se_tmp;          // gamma_total (standard errors when not requested)
+};
+
+struct GeometryHost {
+    dtn_geometry_desc desc{};
+    std::vector<double> boxes;
+    // obstacle grid (host copy)
+    int gn[3] = {1, 1, 1};
+    double glo[3] = {0, 0, 0}, cell = 1.0;
+    std::vector<int> cstart, citems;
+    std::vector<float> ccap;
+    // last Dirichlet data set (for cloning geometry objects)
+    dtn_dirichlet_desc data{};
+    std::vector<double> clm;
+};
+
+}  // namespace dtn
+
+struct dtn_geometry {
+    dtn::GeometryHost host;
+    dtn::DGeom dg{};
+    dtn::DData dd{};
+    bool has_data = false;
+    double score_bound = 1.0;          // bound on |g| over the boundary
+    dtn::DevBuf d_boxes, d_boxes_f, d_cstart, d_citems, d_ccap, d_clm, d_clm_f;
+    dtn::Workspace ws;
+    int device = 0;
+    int num_sms = 0;
+    cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool stages_recorded = false;
+    std::mutex mu;
+};
+
+namespace dtn {
+
+// error bookkeeping
+void set_cuda_error(cudaError_t e);
+#define DTN_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) {                              \
+            ::dtn::set_cuda_error(_e);                        \
+            return _e == cudaErrorMemoryAllocation ? DTN_E_OUT_OF_MEMORY : DTN_E_CUDA; \
+        }                                                     \
+    } while (0)
+
+// Gauss-Legendre tables on the device: orders 1..kMaxGauss, order n at offset
+// n(n-1)/2, nodes ascending on [-1, 1].
+constexpr int kMaxGauss = 64;
+cudaError_t ensure_tables();
+const double *gl_x_dev();
+const double *gl_w_dev();
+const ShTables *sh_tables_dev();
+void gauss_legendre_host(int n, double *x, double *w);
+
+// launchers (each enqueues on `s`)
+cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                               const double *centers, const double *radius, double *gamma_xyz,
+                               double *gamma_w, double *gamma_loc, double *colloc, double *normals,
+                               double *areas, double *panel_loc, double *panel_prm, double *panel_aux,
+                               double *panel_g, cudaStream_t s);
+
+struct WosLaunch {
+    int64_t n_groups;
+    const int64_t *node_off;     // n_groups + 1
+    const int64_t *walks;        // per group
+    const uint32_t *pid;         // per group (RNG patch id)
+    const uint32_t *point_id;    // per node or nullptr (then node - node_off[group])
+    const int64_t *chunk_off;    // n_groups + 1
+    const int32_t *cpn;          // chunks per node, per group
+    int64_t total_chunks;
+    int64_t total_nodes;
+    int32_t chunk;
+    int64_t max_walks;
+    const double *y;             // nodes x 3
+    int prec;
+    double eps;
+    uint64_t max_steps, seed;
+    int blocks_per_sm;
+    // outputs
+    double *mean, *se;
+    uint64_t *steps;
+    uint32_t *capped;
+};
+cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s);
+
+cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                            int prec, const double *panel_loc, const double *panel_prm,
+                            const double *panel_aux, const double *panel_g, const double *gamma_loc,
+                            const double *gamma_w, const double *U, double *A, double *b,
+                            cudaStream_t s);
+
+cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
+                            const double *A, const double *b, double *q, int max_iters, double tol,
+                            int32_t *iters, double *resid, int32_t *status, cudaStream_t s);
+
+cudaError_t launch_potential(int64_t np, const int64_t *index, const int64_t *n_index, const double *xyz,
+                             const double *nrm, const double *area, const double *q, const double *g,
+                             int64_t nt, const double *t, double *out, int prec, int num_sms,
+                             cudaStream_t s);
+
+cudaError_t launch_gather(int64_t np, const double *x, const int64_t *owner, int64_t nc,
+                          const double *cent, uint8_t *keep, int64_t *kept, int64_t *n_kept,
+                          cudaStream_t s);
+
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out,
+                          cudaStream_t s);
+cudaError_t launch_distance(const dtn_geometry *g, int64_t n, const double *x, double *d,
+                            double *nearest, int prec, cudaStream_t s);
+cudaError_t launch_dirichlet(const dtn_geometry *g, int64_t n, const double *x, double *out,
+                             cudaStream_t s);
+
+__host__ __device__ inline int64_t find_group(const int64_t *off, int64_t n, int64_t idx) {
+    // largest p in [0, n) with off[p] <= idx
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace dtn

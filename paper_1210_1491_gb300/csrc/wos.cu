@@ -1,0 +1,419 @@
+// wos.cu -- walk on spheres (Sec. 2) with an epsilon shell, estimator Eq. bw87.
+//
+// Persistent kernel, one walk per lane.  Work is a list of chunks (a chunk =
+// up to `chunk` consecutive walks of one node); a warp takes a chunk from a
+// global counter and hands its walks to idle lanes, so a lane whose walk ends
+// starts the next walk without waiting for the rest of the warp (compaction of
+// finished walks).  A lane keeps walking while fewer than `refill` lanes of its
+// warp are idle; then absorbed walks are scored together (their data are
+// evaluated in one pass, not one divergent lane at a time) and idle lanes are
+// refilled.
+//
+// Scores are accumulated as 64-bit fixed-point integers (score * 2^F), per lane
+// while the lane stays on one node and by integer atomics when it moves on, so
+// sums do not depend on scheduling: the estimates are bitwise reproducible.
+//
+// Random numbers: Philox4x32-10 keyed by the seed.  FP64 walks draw one block
+// per jump, counter (walk, j, point, patch), 53-bit uniforms from words (0,1)
+// and (2,3).  FP32 walks draw one block per two jumps, counter
+// (walk, j >> 1, point, patch), 24-bit uniforms from words (0,1) for even j and
+// (2,3) for odd j; each loop iteration of an FP32 walk therefore makes two
+// jumps from one block.
+#include <cmath>
+#include <type_traits>
+
+#include "dtn_internal.h"
+
+namespace dtn {
+
+namespace {
+
+constexpr int kWosThreads = 256;
+
+struct WosDev {
+    DGeom g;
+    DData dat;
+    const double *y;
+    const int64_t *node_off;
+    const int64_t *walks;
+    const uint32_t *pid;
+    const uint32_t *point_id;
+    const int64_t *chunk_off;
+    const int32_t *cpn;
+    int64_t n_groups, total_chunks;
+    int32_t chunk;
+    int32_t refill;
+    unsigned long long *counter;
+    unsigned long long *s1, *s2, *st;
+    unsigned int *cap;
+    int lgM1, lgM2;        // ceil(log2) of the score bound and of its square
+    double eps;
+    uint32_t max_steps;
+    uint32_t k0, k1;
+};
+
+// Fixed-point exponent of a node's sums: |sum over W walks| <= W * bound < 2^61,
+// so F = 61 - ceil(log2 W) - ceil(log2 bound).  It depends only on the node's own
+// walk count, never on the rest of the batch.
+__host__ __device__ __forceinline__ int fixed_exponent(int64_t walks, int lgM) {
+    int lw = 0;
+    while (lw < 63 && ((int64_t)1 << lw) < walks) ++lw;
+    int e = 61 - lw - lgM;
+    return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+}
+
+__device__ __forceinline__ double pow2(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+template <typename T>
+struct LaneAcc {
+    int64_t node = -1;
+    long long a1 = 0, a2 = 0;
+    unsigned long long st = 0;
+    unsigned int cap = 0;
+
+    __device__ __forceinline__ void flush(const WosDev &P) {
+        if (node >= 0) {
+            atomicAdd(P.s1 + node, (unsigned long long)a1);
+            atomicAdd(P.s2 + node, (unsigned long long)a2);
+            atomicAdd(P.st + node, st);
+            if (cap) atomicAdd(P.cap + node, cap);
+        }
+        a1 = 0; a2 = 0; st = 0; cap = 0;
+    }
+};
+
+// one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
+// z uniform in (-1, 1), azimuth 2 pi u2
+__device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t w1, uint32_t w2) {
+    const float u1 = u01_24(w1), u2 = u01_24(w2);
+    const float zz = fmaf(-2.0f, u1, 1.0f);
+    const float s = sqrtf(fmaxf(0.0f, (1.0f - zz) * (1.0f + zz)));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    x = fmaf(d * s, cs, x);
+    y = fmaf(d * s, sn, y);
+    z = fmaf(d, zz, z);
+}
+
+__device__ __forceinline__ void jump(double &x, double &y, double &z, double d, uint4 w) {
+    const double u1 = u01_53(w.x, w.y), u2 = u01_53(w.z, w.w);
+    const double zz = 1.0 - 2.0 * u1;
+    const double s = sqrt(fmax(0.0, 1.0 - zz * zz));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    x += d * s * cs;
+    y += d * s * sn;
+    z += d * zz;
+}
+
+template <typename T, int GK>
+__global__ void __launch_bounds__(kWosThreads) wos_kernel(WosDev P) {
+    extern __shared__ float s_boxes[];
+    const float *sb = nullptr;
+    if (GK == kBoxMinusBoxes && std::is_same<T, float>::value && P.g.nb <= kMaxSmemBoxes) {
+        for (int i = threadIdx.x; i < 6 * P.g.nb; i += blockDim.x) s_boxes[i] = P.g.boxes_f[i];
+        __syncthreads();
+        sb = s_boxes;
+    }
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const T eps = (T)P.eps;
+
+    // warp-uniform chunk state
+    int64_t cnode = -1;
+    int64_t cnext = 0, cend = 0;
+    uint32_t cpid = 0, cpt = 0;
+    double csc1 = 0.0, csc2 = 0.0;
+    bool no_more = false;
+
+    // lane state
+    bool active = false, pending = false;
+    T x = 0, y = 0, z = 0;
+    T nx = 0, ny = 0, nz = 0;
+    uint32_t walk = 0, step = 0, ppid = 0, ppt = 0;
+    double sc1 = 0.0, sc2 = 0.0;
+    LaneAcc<T> acc;
+
+    for (;;) {
+        // score absorbed walks together
+        if (pending) {
+            const T sc = dirichlet_eval<T>(P.dat, nx, ny, nz);
+            const double sd = (double)sc;
+            acc.a1 += __double2ll_rn(sd * sc1);
+            acc.a2 += __double2ll_rn(sd * sd * sc2);
+            pending = false;
+        }
+        // hand out walks to idle lanes
+        unsigned idle = __ballot_sync(FULL, !active);
+        while (idle != 0u && !no_more) {
+            if (cnext >= cend) {
+                unsigned long long c = 0;
+                if (lane == 0) c = atomicAdd(P.counter, 1ull);
+                c = __shfl_sync(FULL, c, 0);
+                if (c >= (unsigned long long)P.total_chunks) {
+                    no_more = true;
+                    break;
+                }
+                const int64_t grp = find_group(P.chunk_off, P.n_groups, (int64_t)c);
+                const int64_t local = (int64_t)c - P.chunk_off[grp];
+                const int64_t cp = P.cpn[grp];
+                const int64_t k = local / cp, j = local - k * cp;
+                cnode = P.node_off[grp] + k;
+                cnext = j * P.chunk;
+                cend = min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
+                cpid = P.pid[grp];
+                csc1 = pow2(fixed_exponent(P.walks[grp], P.lgM1));
+                csc2 = pow2(fixed_exponent(P.walks[grp], P.lgM2));
+                cpt = P.point_id ? P.point_id[cnode] : (uint32_t)k;
+            }
+            const int nidle = __popc(idle);
+            const int take = (int)min((int64_t)nidle, cend - cnext);
+            const int rank = __popc(idle & lt_mask);
+            if (!active && rank < take) {
+                if (acc.node != cnode) {
+                    acc.flush(P);
+                    acc.node = cnode;
+                }
+                walk = (uint32_t)(cnext + rank);
+                step = 0;
+                ppid = cpid;
+                ppt = cpt;
+                sc1 = csc1;
+                sc2 = csc2;
+                x = (T)P.y[3 * cnode];
+                y = (T)P.y[3 * cnode + 1];
+                z = (T)P.y[3 * cnode + 2];
+                active = true;
+            }
+            cnext += take;
+            idle = __ballot_sync(FULL, !active);
+        }
+        if (__ballot_sync(FULL, active) == 0u) break;
+        const int thresh = no_more ? 32 : P.refill;
+        for (;;) {
+            if (active) {
+                if constexpr (std::is_same<T, float>::value) {
+                    // two jumps from one Philox block
+                    const uint4 w = philox4x32_10(make_uint4(walk, step >> 1, ppt, ppid), P.k0, P.k1);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (active) {
+                            const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
+                            ++step;
+                            if (d <= eps) {
+                                geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
+                                acc.st += step;
+                                pending = true;
+                                active = false;
+                            } else if (step >= P.max_steps) {
+                                acc.st += step;
+                                acc.cap += 1;
+                                active = false;
+                            } else {
+                                jump(x, y, z, d, h == 0 ? w.x : w.z, h == 0 ? w.y : w.w);
+                            }
+                        }
+                    }
+                } else {
+                    const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
+                    ++step;
+                    if (d <= eps) {
+                        geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
+                        acc.st += step;
+                        pending = true;
+                        active = false;
+                    } else if (step >= P.max_steps) {
+                        acc.st += step;
+                        acc.cap += 1;
+                        active = false;
+                    } else {
+                        const uint4 w = philox4x32_10(make_uint4(walk, step - 1, ppt, ppid), P.k0, P.k1);
+                        jump(x, y, z, d, w);
+                    }
+                }
+            }
+            if (__popc(__ballot_sync(FULL, !active)) >= thresh) break;
+        }
+    }
+    acc.flush(P);
+}
+
+__global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int64_t *__restrict__ node_off,
+                                    const int64_t *__restrict__ walks, const unsigned long long *__restrict__ s1,
+                                    const unsigned long long *__restrict__ s2,
+                                    const unsigned long long *__restrict__ st,
+                                    const unsigned int *__restrict__ cap, int lgM1, int lgM2,
+                                    double *__restrict__ mean, double *__restrict__ se,
+                                    uint64_t *__restrict__ steps, uint32_t *__restrict__ capped) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    const int64_t grp = find_group(node_off, n_groups, i);
+    const double N = (double)(walks[grp] - (int64_t)cap[i]);
+    const double inv1 = pow2(-fixed_exponent(walks[grp], lgM1));
+    const double inv2 = pow2(-fixed_exponent(walks[grp], lgM2));
+    const double m1 = (double)(long long)s1[i] * inv1 / N;
+    const double e2 = (double)(long long)s2[i] * inv2;
+    const double var = (e2 - N * m1 * m1) / (N * (N - 1.0));
+    mean[i] = m1;
+    if (se) se[i] = sqrt(fmax(var, 0.0));
+    if (steps) steps[i] = st[i];
+    if (capped) capped[i] = cap[i];
+}
+
+template <typename T>
+void *wos_kernel_ptr(int gk) {
+    if (gk == kBall) return (void *)wos_kernel<T, kBall>;
+    if (gk == kBox) return (void *)wos_kernel<T, kBox>;
+    return (void *)wos_kernel<T, kBoxMinusBoxes>;
+}
+
+}  // namespace
+
+cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
+    if (w.total_nodes == 0) return cudaSuccess;
+    cudaError_t e;
+    // accumulators: s1, s2, st (u64) and cap (u32) per node, plus the counter
+    const size_t n = (size_t)w.total_nodes;
+    const size_t bytes = n * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
+    if ((e = g->ws.acc.reserve(bytes)) != cudaSuccess) return e;
+    char *base = g->ws.acc.as<char>();
+    unsigned long long *counter = (unsigned long long *)base;
+    unsigned long long *s1 = (unsigned long long *)(base + 64);
+    unsigned long long *s2 = s1 + n, *st = s2 + n;
+    unsigned int *cap = (unsigned int *)(st + n);
+    if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
+
+    // fixed-point scales follow the bound on |g| (per node walk count on the device)
+    const double M = g->score_bound > 0 ? g->score_bound : 1.0;
+    const int lgM1 = (int)std::ceil(std::log2(M)), lgM2 = (int)std::ceil(std::log2(M * M));
+
+    WosDev P;
+    P.g = g->dg;
+    P.dat = g->dd;
+    P.y = w.y;
+    P.node_off = w.node_off;
+    P.walks = w.walks;
+    P.pid = w.pid;
+    P.point_id = w.point_id;
+    P.chunk_off = w.chunk_off;
+    P.cpn = w.cpn;
+    P.n_groups = w.n_groups;
+    P.total_chunks = w.total_chunks;
+    P.chunk = w.chunk;
+    P.refill = 8;
+    P.counter = counter;
+    P.s1 = s1; P.s2 = s2; P.st = st; P.cap = cap;
+    P.lgM1 = lgM1;
+    P.lgM2 = lgM2;
+    P.eps = w.eps;
+    P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
+    P.k0 = (uint32_t)(w.seed & 0xFFFFFFFFull);
+    P.k1 = (uint32_t)(w.seed >> 32);
+
+    const int gk = g->dg.kind;
+    const bool fp32 = (w.prec == DTN_PREC_MIXED);
+    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
+    const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
+    if (smem > 48 * 1024) {
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+    }
+    const int bps = w.blocks_per_sm > 0 ? w.blocks_per_sm : 4;
+    int64_t blocks = (int64_t)g->num_sms * bps;
+    // no more warps than chunks
+    const int64_t max_blocks = (w.total_chunks + (kWosThreads / 32) - 1) / (kWosThreads / 32);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    void *args[] = {&P};
+    if ((e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kWosThreads), args, smem, s)) != cudaSuccess)
+        return e;
+    const int T = 256;
+    wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
+        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, cap, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- small checks
+
+namespace {
+
+__global__ void philox_kernel(int64_t n, const uint32_t *__restrict__ ctr, uint32_t k0, uint32_t k1,
+                              uint32_t *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, k0, k1);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+template <typename T>
+__global__ void distance_kernel(DGeom g, int64_t n, const double *__restrict__ x, double *__restrict__ d,
+                                double *__restrict__ nb) {
+    extern __shared__ float s_boxes[];
+    const float *sb = nullptr;
+    if (std::is_same<T, float>::value && g.kind == kBoxMinusBoxes && g.nb <= kMaxSmemBoxes) {
+        for (int i = threadIdx.x; i < 6 * g.nb; i += blockDim.x) s_boxes[i] = g.boxes_f[i];
+        __syncthreads();
+        sb = s_boxes;
+    }
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T px = (T)x[3 * i], py = (T)x[3 * i + 1], pz = (T)x[3 * i + 2];
+    T dist;
+    if (g.kind == kBall) dist = geo_dist<T, kBall>(g, (const T *)sb, px, py, pz);
+    else if (g.kind == kBox) dist = geo_dist<T, kBox>(g, (const T *)sb, px, py, pz);
+    else dist = geo_dist<T, kBoxMinusBoxes>(g, (const T *)sb, px, py, pz);
+    if (d) d[i] = (double)dist;
+    if (nb) {
+        T ax, ay, az;
+        geo_nearest<T>(g, (const T *)sb, px, py, pz, ax, ay, az);
+        nb[3 * i] = ax; nb[3 * i + 1] = ay; nb[3 * i + 2] = az;
+    }
+}
+
+__global__ void dirichlet_kernel(DData dat, int64_t n, const double *__restrict__ x, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = dirichlet_eval<double>(dat, x[3 * i], x[3 * i + 1], x[3 * i + 2]);
+}
+
+}  // namespace
+
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int T = 256;
+    philox_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(n, ctr, (uint32_t)(seed & 0xFFFFFFFFull),
+                                                            (uint32_t)(seed >> 32), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_distance(const dtn_geometry *g, int64_t n, const double *x, double *d, double *nearest,
+                            int prec, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int T = 128;
+    const unsigned blocks = (unsigned)((n + T - 1) / T);
+    if (prec == DTN_PREC_MIXED) {
+        const size_t smem = (g->dg.kind == kBoxMinusBoxes && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute((void *)distance_kernel<float>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        distance_kernel<float><<<blocks, T, smem, s>>>(g->dg, n, x, d, nearest);
+    } else {
+        distance_kernel<double><<<blocks, T, 0, s>>>(g->dg, n, x, d, nearest);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dirichlet(const dtn_geometry *g, int64_t n, const double *x, double *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int T = 128;
+    dirichlet_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dd, n, x, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dtn
