@@ -90,8 +90,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_patch_base(rank: int, n_patches: int) -> int:
+    """RNG patch-id base of a replica: ranks solve independent copies with disjoint ids."""
+    return rank * n_patches
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Max over ranks (the slowest replica sets the whole-job time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+ARGS = None
+
+
 def make_workload():
-    wl = W.unit_ball(n_patches=2000, walks=4096)
+    """The unit-ball workload (2000 patches, 4096 walks); --patches/--walks shrink it
+    for profiler captures only."""
+    n = ARGS.patches if ARGS is not None else 2000
+    w = ARGS.walks if ARGS is not None else 4096
+    wl = W.unit_ball(n_patches=n, walks=w)
     targets = W.targets_in_ball(N_TARGETS, 1.0, 0.05, seed=3)
     return wl, targets
 
@@ -169,7 +191,8 @@ def run_ours(args):
     wl, targets = make_workload()
     b = wl.batch
     # replicas only: every rank solves its own copy with its own patch ids
-    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks, patch_id_base=rank * b.n)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks,
+                       patch_id_base=replica_patch_base(rank, b.n))
     g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
     prec = dtn.PREC_MIXED if args.prec == "mixed" else dtn.PREC_FP64
     opts = dtn.solve_opts(prec=prec, epsilon=wl.epsilon, seed=wl.seed, record_stages=True)
@@ -219,10 +242,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, dev)
     value = world * b.n / (ms / 1e3)
     wos = sum(wos_ms) / len(wos_ms)
     walk_steps_per_s = world * walk_steps / (wos / 1e3)
@@ -314,7 +334,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--patches", type=int, default=2000, help="profiler captures only")
+    ap.add_argument("--walks", type=int, default=4096, help="profiler captures only")
     args = ap.parse_args()
+    global ARGS
+    ARGS = args
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

@@ -113,7 +113,16 @@ typedef struct {
                                    the previous call repeat */
     int32_t record_stages;      /* 1: record CUDA events between the stages of the call on its
                                    stream (read them with dtn_stage_times) */
+    int32_t wos_refill;         /* idle lanes of a warp before it refills them (0 = tuned) */
 } dtn_solve_opts;
+
+/* Launch parameters of the walk kernel chosen by dtn_autotune_walks. */
+typedef struct {
+    int32_t walk_chunk;
+    int32_t wos_blocks_per_sm;
+    int32_t wos_refill;
+    float ns_per_walk_step;     /* measured device time per walk-step of the best choice */
+} dtn_tuning;
 
 /* A batch of patches.  Patch p has a ball of radius radius[p] about centers[p]
  * (a point of the boundary), n_theta[p] x n_phi[p] hemisphere Gauss nodes
@@ -234,6 +243,16 @@ dtn_status dtn_philox4x32_10(int64_t n, const uint32_t *ctr, uint64_t seed, uint
 /* Dirichlet data g at n device points (FP64). */
 dtn_status dtn_eval_dirichlet(const dtn_geometry *geom, int64_t n, const double *x, double *g,
                               void *stream);
+
+/* Autotuner (not in the paper): times the walk kernel on a sample of the batch
+ * (at most 32 patches, at most 512 walks per node) for every combination of
+ * walk chunk {64, 128, 256, 512}, resident blocks per SM {1 .. occupancy
+ * limit} and refill threshold {2, 4, 8, 16}, and keeps the fastest per
+ * (device name, region kind, precision) in a process-wide cache that
+ * dtn_solve_patches and dtn_wos_points consult for every opts field left at 0.
+ * Synchronises `stream`.  *out (may be NULL) receives the choice. */
+dtn_status dtn_autotune_walks(dtn_geometry *geom, const dtn_patch_batch *batch,
+                              const dtn_solve_opts *opts, dtn_tuning *out, void *stream);
 
 /* Device time in milliseconds of the stages of the last dtn_solve_patches call
  * on geom made with record_stages = 1: ms[0] patch setup, ms[1] walks and their

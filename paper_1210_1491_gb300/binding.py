@@ -53,7 +53,12 @@ class SolveOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("epsilon", C.c_double), ("seed", C.c_uint64),
                 ("max_steps", C.c_uint64), ("max_refine_iters", C.c_int32), ("refine_tol", C.c_double),
                 ("u_provided", C.c_int32), ("walk_chunk", C.c_int32), ("wos_blocks_per_sm", C.c_int32),
-                ("graph_capture", C.c_int32), ("record_stages", C.c_int32)]
+                ("graph_capture", C.c_int32), ("record_stages", C.c_int32), ("wos_refill", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("walk_chunk", C.c_int32), ("wos_blocks_per_sm", C.c_int32), ("wos_refill", C.c_int32),
+                ("ns_per_walk_step", C.c_float)]
 
 
 class PatchBatch(C.Structure):
@@ -85,7 +90,7 @@ EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "
            "dtn_solve_patches", "dtn_eval_potential", "dtn_gather_owned", "dtn_wos_points",
            "dtn_distance", "dtn_philox4x32_10", "dtn_eval_dirichlet", "dtn_status_string",
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
-           "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times"]
+           "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks"]
 
 _lib = None
 
@@ -119,6 +124,7 @@ def load(path: str = LIB_PATH):
         "dtn_server_drain": ([vp], i32),
         "dtn_server_destroy": ([vp], i32),
         "dtn_stage_times": ([vp, C.POINTER(C.c_float)], i32),
+        "dtn_autotune_walks": ([vp, C.POINTER(PatchBatch), C.POINTER(SolveOpts), C.POINTER(Tuning), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -159,13 +165,26 @@ def _dev(t, dtype):
 
 def solve_opts(prec=PREC_MIXED, epsilon=1e-4, seed=0, max_steps=0, max_refine_iters=0, refine_tol=0.0,
                u_provided=False, walk_chunk=0, wos_blocks_per_sm=0, graph_capture=False,
-               record_stages=False) -> SolveOpts:
+               record_stages=False, wos_refill=0) -> SolveOpts:
     o = SolveOpts()
     o.prec, o.epsilon, o.seed, o.max_steps = int(prec), float(epsilon), int(seed), int(max_steps)
     o.max_refine_iters, o.refine_tol, o.u_provided = int(max_refine_iters), float(refine_tol), int(u_provided)
     o.walk_chunk, o.wos_blocks_per_sm, o.graph_capture = int(walk_chunk), int(wos_blocks_per_sm), int(graph_capture)
     o.record_stages = int(record_stages)
+    o.wos_refill = int(wos_refill)
     return o
+
+
+def autotune_walks(geom, centers, radius, hb, opts: SolveOpts, stream=None) -> dict:
+    """dtn_autotune_walks: pick and cache the walk-kernel launch parameters."""
+    c = _dev(centers, torch.float64).reshape(-1, 3)
+    rad = _dev(radius, torch.float64).reshape(-1)
+    t = Tuning()
+    b = hb.struct(c, rad)
+    _check(load().dtn_autotune_walks(geom.handle, C.byref(b), C.byref(opts), C.byref(t), _stream(stream)),
+           "dtn_autotune_walks")
+    return dict(walk_chunk=t.walk_chunk, wos_blocks_per_sm=t.wos_blocks_per_sm, wos_refill=t.wos_refill,
+                ns_per_walk_step=t.ns_per_walk_step)
 
 
 class Geometry:

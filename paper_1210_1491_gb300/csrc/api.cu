@@ -6,6 +6,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "dtn_internal.h"
@@ -249,11 +252,32 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     return cudaSuccess;
 }
 
-int32_t pick_chunk(const dtn_solve_opts *o, int64_t max_walks) {
-    if (o->walk_chunk > 0) return o->walk_chunk;
-    (void)max_walks;
-    return 256;
+// Walk-kernel launch parameters: explicit opts fields win; fields left at 0 come
+// from the autotuner's cache for (device name, region kind, precision), else
+// from defaults (chunk 256, all resident blocks, refill at 8 idle lanes).
+std::mutex g_tune_mu;
+std::map<std::tuple<std::string, int, int>, dtn_tuning> g_tune;
+
+struct WalkParams {
+    int32_t chunk, bps, refill;
+};
+
+WalkParams walk_params(const dtn_geometry *g, const dtn_solve_opts *o) {
+    WalkParams w{256, 0, 8};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(std::make_tuple(std::string(g->dev_name), g->dg.kind, o->prec));
+        if (it != g_tune.end()) w = WalkParams{it->second.walk_chunk, it->second.wos_blocks_per_sm, it->second.wos_refill};
+    }
+    if (o->walk_chunk > 0) w.chunk = o->walk_chunk;
+    if (o->wos_blocks_per_sm > 0) w.bps = o->wos_blocks_per_sm;
+    if (o->wos_refill > 0) w.refill = o->wos_refill;
+    return w;
 }
+
+cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, const dtn_solve_opts *o,
+                          const WalkParams &wp, int64_t total_chunks, const dtn_patch_batch *b, dtn_patch_result *r,
+                          double *gxyz, double *gw, double *pg, double *A, double *rhs, bool rec, cudaStream_t s);
 
 }  // namespace
 }  // namespace dtn
@@ -308,6 +332,11 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
     g->host.desc.n_boxes = nb;
     cudaGetDevice(&g->device);
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, g->device) == cudaSuccess)
+            std::strncpy(g->dev_name, prop.name, sizeof(g->dev_name) - 1);
+    }
     DGeom &dg = g->dg;
     std::memset(&dg, 0, sizeof(dg));
     dg.kind = d.kind;
@@ -370,10 +399,11 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
     DevBuf *bufs[] = {&g->d_boxes, &g->d_boxes_f, &g->d_cstart, &g->d_citems, &g->d_ccap, &g->d_clm, &g->d_clm_f,
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
-                      &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp};
+                      &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune};
     for (DevBuf *b : bufs) b->release();
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
     delete g;
     return DTN_OK;
 }
@@ -410,6 +440,7 @@ dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
     dd.constant = d->constant;
     dd.sh = sh_tables_dev();
     g->score_bound = std::max(score_bound(g->host.desc, *d), 1e-300);
+    g->data_version += 1;
     g->host.data = *d;
     if (d->kind == DTN_DATA_HARMONIC_SH) {
         g->host.clm.assign(d->clm, d->clm + (d->lmax + 1) * (d->lmax + 1));
@@ -454,7 +485,8 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     BatchLayout L;
     dtn_status st = build_layout(b, L);
     if (st != DTN_OK) return st;
-    const int32_t chunk = pick_chunk(o, L.max_walks);
+    const WalkParams wp = walk_params(g, o);
+    const int32_t chunk = wp.chunk;
     DevLayout D;
     int64_t total_chunks = 0;
     cudaError_t e = upload_layout(g, L, chunk, D, total_chunks, s);
@@ -479,14 +511,70 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
             if (!g->stage_ev[k] && (e = cudaEventCreate(&g->stage_ev[k])) != cudaSuccess) return to_status(e);
         g->stages_recorded = true;
     }
+    if (o->graph_capture) {
+        // every buffer the device part touches is reserved before capture, so the
+        // captured graph allocates nothing and its pointers stay valid while the
+        // key (shapes, pointers, options, data version) repeats
+        if ((e = W.acc.reserve(G * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64)) != cudaSuccess)
+            return to_status(e);
+        const size_t lus = lu_scratch_bytes(L, o->prec);
+        if (lus && (e = (o->prec == DTN_PREC_MIXED ? W.lu32 : W.lu64).reserve(lus)) != cudaSuccess) return to_status(e);
+        std::vector<unsigned char> key;
+        auto put = [&key](const void *p, size_t n) {
+            const unsigned char *c = (const unsigned char *)p;
+            key.insert(key.end(), c, c + n);
+        };
+        put(L.nt.data(), L.nt.size() * 4); put(L.nph.data(), L.nph.size() * 4);
+        put(L.nr.data(), L.nr.size() * 4); put(L.ns.data(), L.ns.size() * 4);
+        put(L.walks.data(), L.walks.size() * 8); put(L.pid.data(), L.pid.size() * 4);
+        put(&wp, sizeof(wp)); put(o, sizeof(*o)); put(&b->centers, sizeof(void *)); put(&b->radius, sizeof(void *));
+        put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
+        const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
+                                &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp};
+        for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
+        if (!(g->graph_exec && key == g->graph_key)) {
+            if (g->graph_exec) {
+                cudaGraphExecDestroy(g->graph_exec);
+                g->graph_exec = nullptr;
+            }
+            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return to_status(e);
+            cudaError_t ce = enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, s);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(s, &graph);
+            if (ce != cudaSuccess) e = ce;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                g->graph_exec = nullptr;
+                return to_status(e);
+            }
+            g->graph_key.swap(key);
+        }
+        return to_status(cudaGraphLaunch(g->graph_exec, s));
+    }
+    return to_status(enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, s));
+}
+
+}  // extern "C"
+
+namespace dtn {
+namespace {
+
+// The device part of a batch solve: setup, walks, assembly, solve, enqueued on s.
+cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, const dtn_solve_opts *o,
+                          const WalkParams &wp, int64_t total_chunks, const dtn_patch_batch *b, dtn_patch_result *r,
+                          double *gxyz, double *gw, double *pg, double *A, double *rhs, bool rec, cudaStream_t s) {
+    Workspace &W = g->ws;
+    cudaError_t e;
+    const int32_t chunk = wp.chunk;
     auto mark = [&](int k) -> cudaError_t { return rec ? cudaEventRecord(g->stage_ev[k], s) : cudaSuccess; };
-    if ((e = mark(0)) != cudaSuccess) return to_status(e);
+    if ((e = mark(0)) != cudaSuccess) return e;
     // 1. patch setup
     e = launch_patch_setup(g, L, D, b->centers, b->radius, gxyz, gw, W.gamma_loc.as<double>(), r->colloc_xyz,
                            r->normals, r->areas, W.panel_loc.as<double>(), W.panel_prm.as<double>(),
                            W.panel_aux.as<double>(), pg, s);
-    if (e != cudaSuccess) return to_status(e);
-    if ((e = mark(1)) != cudaSuccess) return to_status(e);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
     // 2. walks at the hemisphere nodes (step 1 of the BIE-WOS algorithm)
     if (!o->u_provided) {
         WosLaunch w{};
@@ -506,26 +594,124 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         w.eps = o->epsilon;
         w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
         w.seed = o->seed;
-        w.blocks_per_sm = o->wos_blocks_per_sm;
+        w.blocks_per_sm = wp.bps;
+        w.refill = wp.refill;
         w.mean = r->u_gamma_mean;
         w.se = r->u_gamma_se ? r->u_gamma_se : W.se_tmp.as<double>();
         w.steps = r->gamma_steps;
         w.capped = r->gamma_capped;
-        if ((e = launch_wos(g, w, s)) != cudaSuccess) return to_status(e);
+        if ((e = launch_wos(g, w, s)) != cudaSuccess) return e;
     }
-    if ((e = mark(2)) != cudaSuccess) return to_status(e);
+    if ((e = mark(2)) != cudaSuccess) return e;
     // 3. assembly of Eq. bw49-bw51 (step 2)
     e = launch_assemble(g, L, D, o->prec, W.panel_loc.as<double>(), W.panel_prm.as<double>(), W.panel_aux.as<double>(),
                         pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A, rhs, s);
-    if (e != cudaSuccess) return to_status(e);
-    if ((e = mark(3)) != cudaSuccess) return to_status(e);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
     // 4. collocation solve
     const int iters = o->max_refine_iters > 0 ? o->max_refine_iters : 10;
     const double tol = o->refine_tol > 0 ? o->refine_tol : 1e-12;
     e = launch_lu_solve(g, L, D, o->prec, A, rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
                         r->patch_status, s);
     if (e == cudaSuccess) e = mark(4);
-    return to_status(e);
+    return e;
+}
+
+}  // namespace
+}  // namespace dtn
+
+extern "C" {
+
+dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const dtn_solve_opts *o, dtn_tuning *out,
+                              void *stream) {
+    if (!g || !b || !o || b->n_patches < 1 || !b->centers || !b->radius || !b->walks_per_point) return DTN_E_INVALID_ARG;
+    if (!b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
+    if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    if (!g->has_data) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    // sample: the first patches, walks capped
+    const int64_t n = std::min<int64_t>(b->n_patches, 32);
+    std::vector<int64_t> walks(n);
+    for (int64_t p = 0; p < n; ++p) walks[p] = std::max<int64_t>(2, std::min<int64_t>(b->walks_per_point[p], 512));
+    dtn_patch_batch sb = *b;
+    sb.n_patches = n;
+    sb.walks_per_point = walks.data();
+    BatchLayout L;
+    dtn_status st = build_layout(&sb, L);
+    if (st != DTN_OK) return st;
+    DevLayout D;
+    int64_t total_chunks = 0;
+    cudaError_t e = upload_layout(g, L, 256, D, total_chunks, s);
+    if (e != cudaSuccess) return to_status(e);
+    Workspace &W = g->ws;
+    const size_t G = (size_t)L.gamma_total, Pn = (size_t)L.panels_total;
+    if ((e = W.gamma_loc.reserve(G * 3 * 8)) != cudaSuccess || (e = W.gamma_w.reserve(G * 8)) != cudaSuccess ||
+        (e = W.gamma_xyz.reserve(G * 3 * 8)) != cudaSuccess || (e = W.panel_loc.reserve(Pn * 3 * 8)) != cudaSuccess ||
+        (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
+        (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.tune.reserve(G * 8 * 3)) != cudaSuccess)
+        return to_status(e);
+    e = launch_patch_setup(g, L, D, b->centers, b->radius, W.gamma_xyz.as<double>(), W.gamma_w.as<double>(),
+                           W.gamma_loc.as<double>(), nullptr, nullptr, nullptr, W.panel_loc.as<double>(),
+                           W.panel_prm.as<double>(), W.panel_aux.as<double>(), W.panel_g.as<double>(), s);
+    if (e != cudaSuccess) return to_status(e);
+    double *mean = W.tune.as<double>(), *se = mean + G;
+    uint64_t *steps = (uint64_t *)(se + G);
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return to_status(e);
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return to_status(e); }
+    dtn_tuning best{256, 0, 8, 1e30f};
+    uint64_t total_steps = 0;
+    const int chunks[4] = {64, 128, 256, 512}, bpss[4] = {1, 2, 3, 4}, refills[4] = {2, 4, 8, 16};
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+        if ((e = upload_layout(g, L, chunks[ci], D, total_chunks, s)) != cudaSuccess) break;
+        for (int bi = 0; bi < 4 && e == cudaSuccess; ++bi)
+            for (int ri = 0; ri < 4 && e == cudaSuccess; ++ri) {
+                WosLaunch w{};
+                w.n_groups = L.n_patches;
+                w.node_off = D.gamma_off;
+                w.walks = D.walks;
+                w.pid = D.pid;
+                w.chunk_off = D.chunk_off;
+                w.cpn = D.cpn;
+                w.total_chunks = total_chunks;
+                w.total_nodes = L.gamma_total;
+                w.chunk = chunks[ci];
+                w.max_walks = L.max_walks;
+                w.y = W.gamma_xyz.as<double>();
+                w.prec = o->prec;
+                w.eps = o->epsilon;
+                w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
+                w.seed = o->seed;
+                w.blocks_per_sm = bpss[bi];
+                w.refill = refills[ri];
+                w.mean = mean;
+                w.se = se;
+                w.steps = steps;
+                if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+                if ((e = launch_wos(g, w, s)) != cudaSuccess) break;
+                if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (total_steps == 0) {
+                    std::vector<uint64_t> hs(G);
+                    if ((e = cudaMemcpy(hs.data(), steps, G * 8, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+                    for (uint64_t v : hs) total_steps += v;
+                }
+                const float ns = (float)(ms * 1e6 / (double)std::max<uint64_t>(total_steps, 1));
+                if (ns < best.ns_per_walk_step) best = dtn_tuning{chunks[ci], bpss[bi], refills[ri], ns};
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return to_status(e);
+    {
+        std::lock_guard<std::mutex> tl(g_tune_mu);
+        g_tune[std::make_tuple(std::string(g->dev_name), g->dg.kind, o->prec)] = best;
+    }
+    if (out) *out = best;
+    return DTN_OK;
 }
 
 dtn_status dtn_stage_times(dtn_geometry *g, float ms[4]) {
@@ -582,7 +768,8 @@ dtn_status dtn_wos_points(const dtn_geometry *gc, int64_t n, const double *y, co
         if (walks[i] < 2 || walks[i] > 0xFFFFFFFFll) return DTN_E_INVALID_ARG;
         maxw = std::max(maxw, walks[i]);
     }
-    const int32_t chunk = pick_chunk(o, maxw);
+    const WalkParams wp = walk_params(g, o);
+    const int32_t chunk = wp.chunk;
     std::vector<int64_t> node_off(n + 1), chunk_off(n + 1, 0);
     std::vector<int32_t> cpn(n);
     for (int64_t i = 0; i <= n; ++i) node_off[i] = i;
@@ -619,7 +806,8 @@ dtn_status dtn_wos_points(const dtn_geometry *gc, int64_t n, const double *y, co
     w.eps = o->epsilon;
     w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
     w.seed = o->seed;
-    w.blocks_per_sm = o->wos_blocks_per_sm;
+    w.blocks_per_sm = wp.bps;
+    w.refill = wp.refill;
     w.mean = mean;
     if (!se) {
         if ((e = g->ws.se_tmp.reserve(n * 8)) != cudaSuccess) return to_status(e);

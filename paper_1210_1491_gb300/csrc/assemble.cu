@@ -41,6 +41,7 @@ struct Ctx {
     T Xs[3];
     bool img;
     bool needD;
+    bool data32;   // evaluate g in FP32 for the (bounded) double-layer integrand
     T gx;
     T c[3], t1[3], t2[3], n[3];
     const DData *dat;
@@ -56,7 +57,8 @@ __device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa
         const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
         const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
         const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
-        const T gy = dirichlet_eval<T>(*c.dat, yx, yy, yz);
+        const T gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
+                              : dirichlet_eval<T>(*c.dat, yx, yy, yz);
         sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
     }
 }
@@ -123,22 +125,40 @@ __device__ __forceinline__ int order32(double r) {
 // distance ratio of a sub-square: min distance from the singular points to the
 // square's physical centre over the largest centre-to-(corner or edge midpoint)
 // distance
+// (also returns the physical lengths of the square's two mid-lines, lx along
+// xi and le along eta, which decide where to split)
 template <typename T>
-__device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, bool withX) {
+__device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, bool withX, T &lx, T &le) {
     T uc, vc, jac, Yc[3], nl[3], J;
     map_uv<T>(R, (T)0.5 * (x0 + x1), (T)0.5 * (e0 + e1), uc, vc, jac);
     patch_point<T>(c.kind, c.R, uc, vc, Yc, nl, J);
     T rad = (T)0;
+    T P[3][3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            if (a == 1 && b == 1) continue;
+            if (a == 1 && b == 1) {
+                P[1][1][0] = Yc[0]; P[1][1][1] = Yc[1]; P[1][1][2] = Yc[2];
+                continue;
+            }
             T u, v, Y[3];
             map_uv<T>(R, x0 + (T)0.5 * a * (x1 - x0), e0 + (T)0.5 * b * (e1 - e0), u, v, jac);
             patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+            P[a][b][0] = Y[0]; P[a][b][1] = Y[1]; P[a][b][2] = Y[2];
             const T d2 = (Y[0] - Yc[0]) * (Y[0] - Yc[0]) + (Y[1] - Yc[1]) * (Y[1] - Yc[1]) +
                          (Y[2] - Yc[2]) * (Y[2] - Yc[2]);
             rad = fmax(rad, sqrt(d2));
         }
+    lx = (T)0;
+    le = (T)0;
+    for (int k = 0; k < 2; ++k) {
+        T dx = (T)0, de = (T)0;
+        for (int d = 0; d < 3; ++d) {
+            dx += (P[k + 1][1][d] - P[k][1][d]) * (P[k + 1][1][d] - P[k][1][d]);
+            de += (P[1][k + 1][d] - P[1][k][d]) * (P[1][k + 1][d] - P[1][k][d]);
+        }
+        lx += sqrt(dx);
+        le += sqrt(de);
+    }
     T dmin = (T)INFINITY;
     if (withX) {
         const T d2 = (c.X[0] - Yc[0]) * (c.X[0] - Yc[0]) + (c.X[1] - Yc[1]) * (c.X[1] - Yc[1]) +
@@ -162,14 +182,24 @@ __device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, i
     stack[sp++] = Sq{(T)0, (T)1, (T)0, (T)1, 0};
     while (sp > 0) {
         const Sq q = stack[--sp];
-        const T r = square_ratio<T>(c, R, q.x0, q.x1, q.e0, q.e1, withX);
+        T lx, le;
+        const T r = square_ratio<T>(c, R, q.x0, q.x1, q.e0, q.e1, withX, lx, le);
         int n = order64((double)r);
         if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
+            // split the long direction only while the square is more than 2:1
             const T xm = (T)0.5 * (q.x0 + q.x1), em = (T)0.5 * (q.e0 + q.e1);
-            stack[sp++] = Sq{q.x0, xm, q.e0, em, q.depth + 1};
-            stack[sp++] = Sq{xm, q.x1, q.e0, em, q.depth + 1};
-            stack[sp++] = Sq{q.x0, xm, em, q.e1, q.depth + 1};
-            stack[sp++] = Sq{xm, q.x1, em, q.e1, q.depth + 1};
+            if (lx > (T)2 * le) {
+                stack[sp++] = Sq{q.x0, xm, q.e0, q.e1, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, q.e0, q.e1, q.depth + 1};
+            } else if (le > (T)2 * lx) {
+                stack[sp++] = Sq{q.x0, q.x1, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{q.x0, q.x1, em, q.e1, q.depth + 1};
+            } else {
+                stack[sp++] = Sq{q.x0, xm, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{q.x0, xm, em, q.e1, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, em, q.e1, q.depth + 1};
+            }
             continue;
         }
         if (n == 0) n = 20;
@@ -193,6 +223,7 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
     if (c.img)
         for (int d = 0; d < 3; ++d) c.Xs[d] = (T)(f.a * f.a * X[d] / xx);
     c.needD = (f.kind == kCap);
+    c.data32 = false;
     c.gx = (T)gx;
     c.dat = dat;
 }
@@ -227,6 +258,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const double gx = P.panel_g[row];
     Ctx<double> c64;
     make_ctx<double>(c64, f, X, gx, &P.dat);
+    c64.data32 = (P.prec == DTN_PREC_MIXED);
     Ctx<float> c32;
     make_ctx<float>(c32, f, X, gx, &P.dat);
     double dsum = 0.0;
@@ -235,19 +267,39 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         const double *prm = P.panel_prm + 6 * pj;
         double sa = 0.0, sd = 0.0;
         if (j == i) {
-            // self panel: triangles from the collocation point (uc, vc) to each side
+            // self panel: triangles from the collocation point (uc, vc) to each side,
+            // each side cut into m pieces so that every Duffy triangle's far edge is
+            // no longer than its height (the angular factor of the transformed
+            // integrand then stays smooth for thin panels)
             const double S[2] = {prm[4], prm[5]};
             const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
             const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
+            double PS[3], nl[3], J;
+            patch_point<double>(f.kind, f.R, S[0], S[1], PS, nl, J);
             for (int e = 0; e < 4; ++e) {
-                Region R;
-                R.tri = true;
-                R.p[0] = S[0]; R.p[1] = S[1];
-                R.p[2] = cu[e] - S[0]; R.p[3] = cv[e] - S[1];
-                R.p[4] = cu[e + 1] - cu[e]; R.p[5] = cv[e + 1] - cv[e];
-                R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
-                if (R.det == 0.0) continue;
-                integrate_region<double>(c64, R, false, 16, P.glx, P.glw, sa, sd);
+                double PA[3], PB[3];
+                patch_point<double>(f.kind, f.R, cu[e], cv[e], PA, nl, J);
+                patch_point<double>(f.kind, f.R, cu[e + 1], cv[e + 1], PB, nl, J);
+                const double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
+                const double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
+                const double cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2],
+                                      ab[0] * as[1] - ab[1] * as[0]};
+                const double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+                const double h = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmax(L, 1e-300);
+                const int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
+                for (int k = 0; k < m; ++k) {
+                    const double ua = cu[e] + (cu[e + 1] - cu[e]) * k / m, va = cv[e] + (cv[e + 1] - cv[e]) * k / m;
+                    const double ub = cu[e] + (cu[e + 1] - cu[e]) * (k + 1) / m;
+                    const double vb = cv[e] + (cv[e + 1] - cv[e]) * (k + 1) / m;
+                    Region R;
+                    R.tri = true;
+                    R.p[0] = S[0]; R.p[1] = S[1];
+                    R.p[2] = ua - S[0]; R.p[3] = va - S[1];
+                    R.p[4] = ub - ua; R.p[5] = vb - va;
+                    R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
+                    if (R.det == 0.0) continue;
+                    integrate_region<double>(c64, R, false, 16, P.glx, P.glw, sa, sd);
+                }
             }
         } else {
             const double *ax = P.panel_aux + 4 * pj;

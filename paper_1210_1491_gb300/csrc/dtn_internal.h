@@ -59,6 +59,7 @@ struct Workspace {
     DevBuf acc;             // WOS accumulators: 3 x u64 + u32 per node
     DevBuf counter;         // work counter(s)
     DevBuf se_tmp;          // gamma_total (standard errors when not requested)
+    DevBuf tune;            // autotuner outputs (means, steps)
 };
 
 struct GeometryHost {
@@ -86,6 +87,10 @@ struct dtn_geometry {
     dtn::Workspace ws;
     int device = 0;
     int num_sms = 0;
+    char dev_name[256] = {0};
+    uint64_t data_version = 0;                // bumped by every dtn_set_dirichlet
+    cudaGraphExec_t graph_exec = nullptr;     // last captured solve (graph_capture)
+    std::vector<unsigned char> graph_key;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool stages_recorded = false;
     std::mutex mu;
@@ -137,6 +142,7 @@ struct WosLaunch {
     double eps;
     uint64_t max_steps, seed;
     int blocks_per_sm;
+    int refill;
     // outputs
     double *mean, *se;
     uint64_t *steps;
@@ -149,6 +155,10 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
                             const double *gamma_w, const double *U, double *A, double *b,
                             cudaStream_t s);
+
+// bytes of global factor scratch the LU launch needs (0 when the factors fit in
+// shared memory)
+size_t lu_scratch_bytes(const BatchLayout &L, int prec);
 
 cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
                             const double *A, const double *b, double *q, int max_iters, double tol,

@@ -188,7 +188,22 @@ __global__ void __launch_bounds__(kLuThreads) lu_kernel(LuDev P) {
     }
 }
 
+size_t lu_head_bytes(int n) {
+    const int nw = kLuThreads / 32;
+    size_t head = (size_t)(2 * n) * sizeof(double) + (size_t)((n + 1) & ~1) * sizeof(int) + nw * (sizeof(double) + sizeof(int));
+    return (head + 15) & ~(size_t)15;
+}
+
+constexpr size_t kLuSmemLimit = 220 * 1024;
+
 }  // namespace
+
+size_t lu_scratch_bytes(const BatchLayout &L, int prec) {
+    const int n = L.max_panels;
+    const size_t fsz = prec == DTN_PREC_MIXED ? sizeof(float) : sizeof(double);
+    if (lu_head_bytes(n) + (size_t)n * (n + 1) * fsz <= kLuSmemLimit) return 0;
+    return (size_t)(L.matrix_total + L.panels_total) * fsz;
+}
 
 cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
                             const double *A, const double *b, double *q, int max_iters, double tol,
@@ -196,13 +211,11 @@ cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayo
     if (L.n_patches == 0) return cudaSuccess;
     cudaError_t e;
     const int n = L.max_panels;
-    const int nw = kLuThreads / 32;
     const bool fp32 = (prec == DTN_PREC_MIXED);
     const size_t fsz = fp32 ? sizeof(float) : sizeof(double);
-    size_t head = (size_t)(2 * n) * sizeof(double) + (size_t)((n + 1) & ~1) * sizeof(int) + nw * (sizeof(double) + sizeof(int));
-    head = (head + 15) & ~(size_t)15;
+    const size_t head = lu_head_bytes(n);
     const size_t fac = (size_t)n * (n + 1) * fsz;
-    const size_t limit = 220 * 1024;
+    const size_t limit = kLuSmemLimit;
     LuDev P;
     P.frames = D.frames;
     P.panel_off = D.panel_off;
@@ -224,7 +237,7 @@ cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayo
         P.in_smem = 0;
         // factor storage n*(n+1) per patch: offsets mat_off[p] + panel_off[p] cover it
         DevBuf &buf = fp32 ? g->ws.lu32 : g->ws.lu64;
-        if ((e = buf.reserve((size_t)(L.matrix_total + L.panels_total) * fsz)) != cudaSuccess) return e;
+        if ((e = buf.reserve(lu_scratch_bytes(L, prec))) != cudaSuccess) return e;
         P.scratch = buf.p;
     }
     void *fn = fp32 ? (void *)lu_kernel<float> : (void *)lu_kernel<double>;

@@ -303,7 +303,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     P.n_groups = w.n_groups;
     P.total_chunks = w.total_chunks;
     P.chunk = w.chunk;
-    P.refill = 8;
+    P.refill = w.refill > 0 ? std::min(w.refill, 32) : 8;
     P.counter = counter;
     P.s1 = s1; P.s2 = s2; P.st = st; P.cap = cap;
     P.lgM1 = lgM1;
@@ -321,7 +321,12 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
         if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
     }
-    const int bps = w.blocks_per_sm > 0 ? w.blocks_per_sm : 4;
+    // persistent grid: never more blocks per SM than can be resident at once
+    int resident = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, kWosThreads, smem)) != cudaSuccess)
+        return e;
+    resident = std::max(resident, 1);
+    const int bps = w.blocks_per_sm > 0 ? std::min(w.blocks_per_sm, resident) : resident;
     int64_t blocks = (int64_t)g->num_sms * bps;
     // no more warps than chunks
     const int64_t max_blocks = (w.total_chunks + (kWosThreads / 32) - 1) / (kWosThreads / 32);

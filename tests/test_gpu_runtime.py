@@ -1,0 +1,79 @@
+"""Runtime pieces around the kernels: CUDA-graph replay, the walk-kernel
+autotuner, stage timing, and capped walks.  The walk estimates must not depend
+on launch parameters (chunk size, resident blocks, refill threshold) nor on
+graph replay: they are bitwise reproducible."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+dtn = pytest.importorskip("paper_1210_1491_gb300")
+
+
+def _case():
+    wl = W.unit_ball(n_patches=200, walks=700, n_theta=8, n_phi=12, n_rings=6, n_sectors=8)
+    b = wl.batch.subset(np.arange(0, 200, 7))
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks, patch_ids=np.arange(0, 200, 7))
+    return wl, b, g, hb
+
+
+def test_results_independent_of_launch_parameters():
+    wl, b, g, hb = _case()
+    ref = None
+    for chunk, bps, refill in [(256, 0, 8), (64, 1, 2), (512, 2, 16), (100, 3, 5)]:
+        o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3, walk_chunk=chunk, wos_blocks_per_sm=bps,
+                           wos_refill=refill)
+        r = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+        torch.cuda.synchronize()
+        out = (r["u_gamma_mean"].cpu().numpy(), r["neumann"].cpu().numpy(), r["gamma_steps"].cpu().numpy())
+        if ref is None:
+            ref = out
+        else:
+            for a, c in zip(ref, out):
+                assert np.array_equal(a, c)
+
+
+def test_graph_replay_matches_direct_and_stage_times():
+    wl, b, g, hb = _case()
+    o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+    torch.cuda.synchronize()
+    og = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3, graph_capture=True, record_stages=True)
+    res = dtn.alloc_result(hb)
+    c = torch.from_numpy(b.centers).cuda()
+    rad = torch.from_numpy(b.radius).cuda()
+    for _ in range(3):   # capture, then two replays
+        res["neumann"].zero_()
+        dtn.solve_patches(g, c, rad, hb, og, result=res)
+        torch.cuda.synchronize()
+        assert np.array_equal(res["neumann"].cpu().numpy(), r0["neumann"].cpu().numpy())
+        ms = g.stage_times()
+        assert all(m >= 0 for m in ms) and ms[1] > 0
+
+
+def test_autotuner_picks_and_results_unchanged():
+    wl, b, g, hb = _case()
+    o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+    torch.cuda.synchronize()
+    t = dtn.autotune_walks(g, b.centers, b.radius, hb, o)
+    assert t["walk_chunk"] in (64, 128, 256, 512) and 1 <= t["wos_blocks_per_sm"] <= 4
+    assert t["wos_refill"] in (2, 4, 8, 16) and t["ns_per_walk_step"] > 0
+    r1 = dtn.solve_patches(g, b.centers, b.radius, hb, o)   # now with tuned parameters
+    torch.cuda.synchronize()
+    assert np.array_equal(r0["neumann"].cpu().numpy(), r1["neumann"].cpu().numpy())
+
+
+def test_capped_walks_counted_and_excluded():
+    wl = W.cube_single_patch(walks=200, n_theta=4, n_phi=4, n_rings=2, n_sectors=4)
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    y = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.00005]])
+    r = dtn.wos_points(g, y, [0, 1], 0, 200, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, max_steps=3))
+    cap = r["capped"].cpu().numpy()
+    st = r["steps"].cpu().numpy()
+    assert cap[0] > 0 and cap[1] == 0         # a centre walk rarely ends in 3 steps; the shell point at once
+    assert st[1] == 200

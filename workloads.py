@@ -139,12 +139,12 @@ def cube_single_patch(walks: int = 10_000, n_theta: int = 16, n_phi: int = 16,
 
 
 def unit_ball(n_patches: int = 2000, walks: int = 4096, n_theta: int = 16,
-              n_phi: int = 32, n_rings: int = 16, n_sectors: int = 8,
+              n_phi: int = 32, n_rings: int = 8, n_sectors: int = 16,
               lmax: int = 8, a: float = 0.1, seed: int = 0) -> Workload:
     """Unit ball interior with a random harmonic polynomial as data.
 
     g = sum_{l<=8} c_lm r^l Y_lm, c_lm ~ N(0,1) (PCG64(seed)); patch centres on a
-    Fibonacci sphere; a = 0.1; 128 panels (16 rings x 8 sectors); 512
+    Fibonacci sphere; a = 0.1; 128 panels (8 rings x 16 sectors); 512
     hemisphere nodes (16 polar x 32 azimuthal); 4096 walks per node.
     """
     geom = Geometry(GEOM_BALL_INTERIOR, center=(0.0, 0.0, 0.0), radius=1.0)
