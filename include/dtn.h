@@ -133,7 +133,8 @@ typedef struct {
 typedef struct {
     int64_t n_patches;
     const double *centers;          /* device, n_patches x 3 */
-    const double *radius;           /* device, n_patches */
+    const double *radius;           /* host, n_patches (a patch-shape parameter, like the
+                                       ring and sector counts) */
     const int32_t *n_theta;         /* host, n_patches, 1..64 */
     const int32_t *n_phi;           /* host, n_patches, 1..64 */
     const int32_t *n_rings;         /* host, n_patches, >= 1 */
@@ -183,7 +184,12 @@ dtn_status dtn_query_patch_sizes(const dtn_patch_batch *batch, int64_t *panels_t
 
 /* BIE-WOS algorithm (Sec. 4) for every patch of the batch: patch setup,
  * walks (Sec. 2, Eq. bw87), assembly of Eq. bw49-bw51 and the collocation
- * solve.  Asynchronous on `stream`.  Per-patch failures land in patch_status
+ * solve.  Asynchronous on `stream`.  The matrix A of Eq. bw50 depends only on
+ * the patch shape (region kind, a, sphere radius, rings, sectors) expressed in
+ * the patch frame; in DTN_PREC_MIXED the patches of one shape share one FP64
+ * A (assembled with the FP64 rules) and one FP32 factorisation, and each patch
+ * gets its own right side and FP64-residual refinement.  DTN_PREC_FP64 (the
+ * plain path) assembles and factors every patch separately.  Per-patch failures land in patch_status
  * (DTN_E_UNSUPPORTED: the ball meets more than one plane face, or the centre
  * is not on the boundary; DTN_E_NOT_CONVERGED: refinement stopped above
  * refine_tol; DTN_E_WALK_CAP: some walks were cut at max_steps). */

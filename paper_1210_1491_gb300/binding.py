@@ -163,6 +163,13 @@ def _dev(t, dtype):
     return torch.as_tensor(t).to(device="cuda", dtype=dtype).contiguous()
 
 
+def _host_f64(t):
+    """Host float64 array (per-patch shape parameters live on the host)."""
+    if isinstance(t, torch.Tensor):
+        t = t.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1))
+
+
 def solve_opts(prec=PREC_MIXED, epsilon=1e-4, seed=0, max_steps=0, max_refine_iters=0, refine_tol=0.0,
                u_provided=False, walk_chunk=0, wos_blocks_per_sm=0, graph_capture=False,
                record_stages=False, wos_refill=0) -> SolveOpts:
@@ -178,7 +185,7 @@ def solve_opts(prec=PREC_MIXED, epsilon=1e-4, seed=0, max_steps=0, max_refine_it
 def autotune_walks(geom, centers, radius, hb, opts: SolveOpts, stream=None) -> dict:
     """dtn_autotune_walks: pick and cache the walk-kernel launch parameters."""
     c = _dev(centers, torch.float64).reshape(-1, 3)
-    rad = _dev(radius, torch.float64).reshape(-1)
+    rad = _host_f64(radius)
     t = Tuning()
     b = hb.struct(c, rad)
     _check(load().dtn_autotune_walks(geom.handle, C.byref(b), C.byref(opts), C.byref(t), _stream(stream)),
@@ -266,11 +273,11 @@ class HostBatch:
         self.base = int(patch_id_base)
         self.n = int(self.nt.shape[0])
 
-    def struct(self, centers_dev, radius_dev) -> PatchBatch:
+    def struct(self, centers_dev, radius_host) -> PatchBatch:
         b = PatchBatch()
         b.n_patches = self.n
         b.centers = _ptr(centers_dev)
-        b.radius = _ptr(radius_dev)
+        b.radius = _ptr(radius_host)
         b.n_theta, b.n_phi = _ptr(self.nt), _ptr(self.nph)
         b.n_rings, b.n_sectors = _ptr(self.nr), _ptr(self.ns)
         b.walks_per_point = _ptr(self.walks)
@@ -318,7 +325,7 @@ def solve_patches(geom: Geometry, centers, radius, hb: HostBatch, opts: SolveOpt
                   stream=None, **alloc_kw):
     """dtn_solve_patches on device tensors; returns the result dict of tensors."""
     c = _dev(centers, torch.float64).reshape(-1, 3)
-    rad = _dev(radius, torch.float64).reshape(-1)
+    rad = _host_f64(radius)
     if result is None:
         result = alloc_result(hb, **alloc_kw)
     b = hb.struct(c, rad)

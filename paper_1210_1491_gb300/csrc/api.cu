@@ -167,14 +167,31 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
     L.panel_off.assign(n + 1, 0);
     L.mat_off.assign(n + 1, 0);
     L.nt.resize(n); L.nph.resize(n); L.nr.resize(n); L.ns.resize(n);
-    L.walks.resize(n); L.pid.resize(n);
+    L.walks.resize(n); L.pid.resize(n); L.radius.assign(n, 0.0);
+    L.group_of.assign(n, 0);
+    L.rep.clear();
     L.max_panels = 0; L.max_nodes = 0; L.max_walks = 0;
+    std::map<std::tuple<uint64_t, int32_t, int32_t>, int64_t> groups;
     for (int64_t p = 0; p < n; ++p) {
         const int32_t nt = b->n_theta[p], nph = b->n_phi[p], nr = b->n_rings[p], ns = b->n_sectors[p];
         if (nt < 1 || nt > kMaxGauss || nph < 1 || nph > kMaxGauss || nr < 1 || ns < 1 || (int64_t)nr * ns > 1024)
             return DTN_E_INVALID_ARG;
         const int32_t np = nr * ns, P = nt * nph;
         L.nt[p] = nt; L.nph[p] = nph; L.nr[p] = nr; L.ns[p] = ns;
+        if (b->radius) {
+            const double a = b->radius[p];
+            if (!(a > 0.0) || !std::isfinite(a)) return DTN_E_INVALID_ARG;
+            L.radius[p] = a;
+        }
+        uint64_t abits;
+        std::memcpy(&abits, &L.radius[p], sizeof(abits));
+        auto key = std::make_tuple(abits, nr, ns);
+        auto it = groups.find(key);
+        if (it == groups.end()) {
+            it = groups.emplace(key, (int64_t)L.rep.size()).first;
+            L.rep.push_back(p);
+        }
+        L.group_of[p] = it->second;
         L.walks[p] = b->walks_per_point ? b->walks_per_point[p] : 0;
         L.pid[p] = b->patch_ids ? b->patch_ids[p] : (uint32_t)(b->patch_id_base + (uint32_t)p);
         L.gamma_off[p + 1] = L.gamma_off[p] + P;
@@ -187,6 +204,19 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
     L.gamma_total = L.gamma_off[n];
     L.panels_total = L.panel_off[n];
     L.matrix_total = L.mat_off[n];
+    L.n_groups = (int64_t)L.rep.size();
+    L.grows_off.assign(L.n_groups + 1, 0);
+    L.gmat_off.assign(L.n_groups + 1, 0);
+    L.gfac_off.assign(L.n_groups + 1, 0);
+    for (int64_t k = 0; k < L.n_groups; ++k) {
+        const int64_t np = (int64_t)L.nr[L.rep[k]] * L.ns[L.rep[k]];
+        L.grows_off[k + 1] = L.grows_off[k] + np;
+        L.gmat_off[k + 1] = L.gmat_off[k] + np * np;
+        L.gfac_off[k + 1] = L.gfac_off[k] + np * (np + 1);
+    }
+    L.grows_total = L.grows_off[L.n_groups];
+    L.gmat_total = L.gmat_off[L.n_groups];
+    L.gfac_total = L.gfac_off[L.n_groups];
     return DTN_OK;
 }
 
@@ -218,6 +248,13 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     const size_t o_ns = off; off = al(off + n * 4);
     const size_t o_cpn = off; off = al(off + n * 4);
     const size_t o_pid = off; off = al(off + n * 4);
+    const size_t o_rad = off; off = al(off + n * 8);
+    const int64_t ng = L.n_groups;
+    const size_t o_gof = off; off = al(off + n * 8);
+    const size_t o_rep = off; off = al(off + ng * 8);
+    const size_t o_grow = off; off = al(off + (ng + 1) * 8);
+    const size_t o_gmat = off; off = al(off + (ng + 1) * 8);
+    const size_t o_gfac = off; off = al(off + (ng + 1) * 8);
     const size_t host_bytes = off;
     const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
     cudaError_t e = g->ws.layout.reserve(off);
@@ -234,6 +271,12 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     std::memcpy(&h[o_ns], L.ns.data(), n * 4);
     std::memcpy(&h[o_cpn], cpn.data(), n * 4);
     std::memcpy(&h[o_pid], L.pid.data(), n * 4);
+    std::memcpy(&h[o_rad], L.radius.data(), n * 8);
+    std::memcpy(&h[o_gof], L.group_of.data(), n * 8);
+    std::memcpy(&h[o_rep], L.rep.data(), ng * 8);
+    std::memcpy(&h[o_grow], L.grows_off.data(), (ng + 1) * 8);
+    std::memcpy(&h[o_gmat], L.gmat_off.data(), (ng + 1) * 8);
+    std::memcpy(&h[o_gfac], L.gfac_off.data(), (ng + 1) * 8);
     char *base = g->ws.layout.as<char>();
     e = cudaMemcpyAsync(base, h.data(), host_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
@@ -248,6 +291,12 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     D.ns = (int32_t *)(base + o_ns);
     D.cpn = (int32_t *)(base + o_cpn);
     D.pid = (uint32_t *)(base + o_pid);
+    D.radius = (double *)(base + o_rad);
+    D.group_of = (int64_t *)(base + o_gof);
+    D.rep = (int64_t *)(base + o_rep);
+    D.grows_off = (int64_t *)(base + o_grow);
+    D.gmat_off = (int64_t *)(base + o_gmat);
+    D.gfac_off = (int64_t *)(base + o_gfac);
     D.frames = (PatchFrame *)(base + o_fr);
     return cudaSuccess;
 }
@@ -399,11 +448,13 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
     DevBuf *bufs[] = {&g->d_boxes, &g->d_boxes_f, &g->d_cstart, &g->d_citems, &g->d_ccap, &g->d_clm, &g->d_clm_f,
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
-                      &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune};
+                      &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
+                      &g->ws.gfac, &g->ws.gpiv};
     for (DevBuf *b : bufs) b->release();
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
     if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
     return DTN_OK;
 }
@@ -499,7 +550,15 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.rhs.reserve(Pn * 8)) != cudaSuccess ||
         (e = W.se_tmp.reserve(G * 8)) != cudaSuccess)
         return to_status(e);
-    if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) return to_status(e);
+    const bool shared = (o->prec == DTN_PREC_MIXED);
+    if (shared) {
+        if ((e = W.gmat.reserve((size_t)L.gmat_total * 8)) != cudaSuccess ||
+            (e = W.gfac.reserve(lu_shared_scratch_bytes(L))) != cudaSuccess ||
+            (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess)
+            return to_status(e);
+    } else if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) {
+        return to_status(e);
+    }
     double *gxyz = r->gamma_xyz ? r->gamma_xyz : W.gamma_xyz.as<double>();
     double *gw = r->gamma_w ? r->gamma_w : W.gamma_w.as<double>();
     double *pg = r->dirichlet ? r->dirichlet : W.panel_g.as<double>();
@@ -517,8 +576,8 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         // key (shapes, pointers, options, data version) repeats
         if ((e = W.acc.reserve(G * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64)) != cudaSuccess)
             return to_status(e);
-        const size_t lus = lu_scratch_bytes(L, o->prec);
-        if (lus && (e = (o->prec == DTN_PREC_MIXED ? W.lu32 : W.lu64).reserve(lus)) != cudaSuccess) return to_status(e);
+        const size_t lus = shared ? 0 : lu_scratch_bytes(L, o->prec);
+        if (lus && (e = W.lu64.reserve(lus)) != cudaSuccess) return to_status(e);
         std::vector<unsigned char> key;
         auto put = [&key](const void *p, size_t n) {
             const unsigned char *c = (const unsigned char *)p;
@@ -527,20 +586,27 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(L.nt.data(), L.nt.size() * 4); put(L.nph.data(), L.nph.size() * 4);
         put(L.nr.data(), L.nr.size() * 4); put(L.ns.data(), L.ns.size() * 4);
         put(L.walks.data(), L.walks.size() * 8); put(L.pid.data(), L.pid.size() * 4);
-        put(&wp, sizeof(wp)); put(o, sizeof(*o)); put(&b->centers, sizeof(void *)); put(&b->radius, sizeof(void *));
+        put(L.radius.data(), L.radius.size() * 8);
+        put(&wp, sizeof(wp)); put(o, sizeof(*o)); put(&b->centers, sizeof(void *));
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
-                                &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp};
+                                &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
+                                &W.gmat, &W.gfac, &W.gpiv};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
                 cudaGraphExecDestroy(g->graph_exec);
                 g->graph_exec = nullptr;
             }
-            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return to_status(e);
-            cudaError_t ce = enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, s);
+            // capture on a private stream (the legacy default stream cannot be
+            // captured); the graph is then launched on the caller's stream
+            if (!g->cap_stream && (e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+                return to_status(e);
+            if ((e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+                return to_status(e);
+            cudaError_t ce = enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, g->cap_stream);
             cudaGraph_t graph = nullptr;
-            e = cudaStreamEndCapture(s, &graph);
+            e = cudaStreamEndCapture(g->cap_stream, &graph);
             if (ce != cudaSuccess) e = ce;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph_exec, graph, 0);
             if (graph) cudaGraphDestroy(graph);
@@ -570,7 +636,7 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     auto mark = [&](int k) -> cudaError_t { return rec ? cudaEventRecord(g->stage_ev[k], s) : cudaSuccess; };
     if ((e = mark(0)) != cudaSuccess) return e;
     // 1. patch setup
-    e = launch_patch_setup(g, L, D, b->centers, b->radius, gxyz, gw, W.gamma_loc.as<double>(), r->colloc_xyz,
+    e = launch_patch_setup(g, L, D, b->centers, gxyz, gw, W.gamma_loc.as<double>(), r->colloc_xyz,
                            r->normals, r->areas, W.panel_loc.as<double>(), W.panel_prm.as<double>(),
                            W.panel_aux.as<double>(), pg, s);
     if (e != cudaSuccess) return e;
@@ -604,15 +670,32 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     }
     if ((e = mark(2)) != cudaSuccess) return e;
     // 3. assembly of Eq. bw49-bw51 (step 2)
-    e = launch_assemble(g, L, D, o->prec, W.panel_loc.as<double>(), W.panel_prm.as<double>(), W.panel_aux.as<double>(),
-                        pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A, rhs, s);
+    const double *pl = W.panel_loc.as<double>(), *pp = W.panel_prm.as<double>(), *pa = W.panel_aux.as<double>();
+    const bool shared = (o->prec == DTN_PREC_MIXED);
+    if (shared) {
+        // one matrix per patch shape, FP64 rules; the right sides per patch
+        double *gA = W.gmat.as<double>();
+        e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                            gA, rhs, s);
+        if (e == cudaSuccess)
+            e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                                gA, rhs, s);
+        if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
+    } else {
+        e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,
+                            rhs, s);
+    }
     if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
     // 4. collocation solve
     const int iters = o->max_refine_iters > 0 ? o->max_refine_iters : 10;
     const double tol = o->refine_tol > 0 ? o->refine_tol : 1e-12;
-    e = launch_lu_solve(g, L, D, o->prec, A, rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
-                        r->patch_status, s);
+    if (shared)
+        e = launch_lu_shared(g, L, D, W.gmat.as<double>(), rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
+                             r->patch_status, s);
+    else
+        e = launch_lu_solve(g, L, D, o->prec, A, rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
+                            r->patch_status, s);
     if (e == cudaSuccess) e = mark(4);
     return e;
 }
@@ -651,7 +734,7 @@ dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const d
         (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
         (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.tune.reserve(G * 8 * 3)) != cudaSuccess)
         return to_status(e);
-    e = launch_patch_setup(g, L, D, b->centers, b->radius, W.gamma_xyz.as<double>(), W.gamma_w.as<double>(),
+    e = launch_patch_setup(g, L, D, b->centers, W.gamma_xyz.as<double>(), W.gamma_w.as<double>(),
                            W.gamma_loc.as<double>(), nullptr, nullptr, nullptr, W.panel_loc.as<double>(),
                            W.panel_prm.as<double>(), W.panel_aux.as<double>(), W.panel_g.as<double>(), s);
     if (e != cudaSuccess) return to_status(e);

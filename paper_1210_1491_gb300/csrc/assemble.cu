@@ -32,6 +32,7 @@ namespace {
 constexpr int kAsmThreads = 128;
 constexpr int kMaxDepth = 10;
 constexpr int kStack = 40;
+constexpr int kMaxRule = 20;   // highest Gauss order the rules below use
 
 template <typename T>
 struct Ctx {
@@ -42,6 +43,7 @@ struct Ctx {
     bool img;
     bool needD;
     bool data32;   // evaluate g in FP32 for the (bounded) double-layer integrand
+    bool needA;    // accumulate the single-layer entry
     T gx;
     T c[3], t1[3], t2[3], n[3];
     const DData *dat;
@@ -52,7 +54,7 @@ __device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa
     T Y[3], nl[3], J;
     patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
     const T wj = w * J;
-    sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
+    if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
     if (c.needD) {
         const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
         const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
@@ -98,6 +100,50 @@ __device__ void gauss_square(const Ctx<T> &c, const Region &R, T x0, T x1, T e0,
             T u, v, jac;
             map_uv<T>(R, xi, eta, u, v, jac);
             eval_point<T>(c, u, v, wi * (T)gw[j] * jac, sa, sd);
+        }
+    }
+}
+
+// The same rule on a rectangle of the parameter box.  The map is separable, so
+// the sines and cosines of u and of v are taken once per Gauss line.
+template <typename T>
+__device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, int n,
+                           const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
+    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
+    const T hx = (T)0.5 * (x1 - x0), mx = (T)0.5 * (x0 + x1);
+    const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
+    const T du = (T)R.p[1], dv = (T)R.p[3];
+    const T jac = du * dv;
+    T cvs[kMaxRule], svs[kMaxRule];
+    for (int j = 0; j < n; ++j) {
+        const T v = (T)R.p[2] + (me + he * (T)gx[j]) * dv;
+        sincos(v, &svs[j], &cvs[j]);
+    }
+    for (int i = 0; i < n; ++i) {
+        const T u = (T)R.p[0] + (mx + hx * (T)gx[i]) * du;
+        const T wi = (T)gw[i] * hx * he * jac;
+        T ru, rz, nu, nz, J;
+        if (c.kind == kDisk) {
+            ru = u; rz = (T)0; nu = (T)0; nz = (T)1; J = u;
+        } else {
+            T su, cu;
+            sincos(u, &su, &cu);
+            const T sh = sin((T)0.5 * u);
+            ru = c.R * su; rz = (T)-2 * c.R * sh * sh; nu = su; nz = cu; J = c.R * c.R * su;
+        }
+        for (int j = 0; j < n; ++j) {
+            const T Y[3] = {ru * cvs[j], ru * svs[j], rz};
+            const T wj = wi * (T)gw[j] * J;
+            if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
+            if (c.needD) {
+                const T nl[3] = {nu * cvs[j], nu * svs[j], nz};
+                const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+                const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+                const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+                const T gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
+                                      : dirichlet_eval<T>(*c.dat, yx, yy, yz);
+                sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
+            }
         }
     }
 }
@@ -184,7 +230,7 @@ __device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, i
         const Sq q = stack[--sp];
         T lx, le;
         const T r = square_ratio<T>(c, R, q.x0, q.x1, q.e0, q.e1, withX, lx, le);
-        int n = order64((double)r);
+        int n = sizeof(T) == 8 ? order64((double)r) : order32((double)r);
         if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
             // split the long direction only while the square is more than 2:1
             const T xm = (T)0.5 * (q.x0 + q.x1), em = (T)0.5 * (q.e0 + q.e1);
@@ -202,9 +248,10 @@ __device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, i
             }
             continue;
         }
-        if (n == 0) n = 20;
+        if (n == 0) n = sizeof(T) == 8 ? 20 : 11;
         if (n < min_order) n = min_order;
-        gauss_square<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
+        if (R.tri) gauss_square<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
+        else gauss_rect<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
     }
 }
 
@@ -224,6 +271,7 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
         for (int d = 0; d < 3; ++d) c.Xs[d] = (T)(f.a * f.a * X[d] / xx);
     c.needD = (f.kind == kCap);
     c.data32 = false;
+    c.needA = true;
     c.gx = (T)gx;
     c.dat = dat;
 }
@@ -231,26 +279,91 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
 struct AsmDev {
     const PatchFrame *frames;
     const int64_t *panel_off, *gamma_off, *mat_off;
-    const int32_t *ns, *nr;
+    const int64_t *grows_off, *rep, *gmat_off;
+    int64_t n_groups;
     const double *panel_loc, *panel_prm, *panel_aux, *panel_g;
     const double *gamma_loc, *gamma_w, *U;
     double *A, *b;
     DData dat;
     int64_t n_patches;
     int prec;
+    int mode;
     const double *glx, *glw;
 };
 
+// self panel: triangles from the collocation point (uc, vc) to each side, each
+// side cut into m pieces so that every Duffy triangle's far edge is no longer
+// than its height (the angular factor of the transformed integrand then stays
+// smooth for thin panels)
+template <typename T>
+__device__ void self_panel(const Ctx<T> &c, const PatchFrame &f, const double *prm, int min_order,
+                           const double *glx, const double *glw, T &sa, T &sd) {
+    const double S[2] = {prm[4], prm[5]};
+    const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
+    const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
+    double PS[3], nl[3], J;
+    patch_point<double>(f.kind, f.R, S[0], S[1], PS, nl, J);
+    for (int e = 0; e < 4; ++e) {
+        double PA[3], PB[3];
+        patch_point<double>(f.kind, f.R, cu[e], cv[e], PA, nl, J);
+        patch_point<double>(f.kind, f.R, cu[e + 1], cv[e + 1], PB, nl, J);
+        const double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
+        const double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
+        const double cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2], ab[0] * as[1] - ab[1] * as[0]};
+        const double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+        const double h = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmax(L, 1e-300);
+        const int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
+        for (int k = 0; k < m; ++k) {
+            const double ua = cu[e] + (cu[e + 1] - cu[e]) * k / m, va = cv[e] + (cv[e + 1] - cv[e]) * k / m;
+            const double ub = cu[e] + (cu[e + 1] - cu[e]) * (k + 1) / m;
+            const double vb = cv[e] + (cv[e + 1] - cv[e]) * (k + 1) / m;
+            Region R;
+            R.tri = true;
+            R.p[0] = S[0]; R.p[1] = S[1];
+            R.p[2] = ua - S[0]; R.p[3] = va - S[1];
+            R.p[4] = ub - ua; R.p[5] = vb - va;
+            R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
+            if (R.det == 0.0) continue;
+            integrate_region<T>(c, R, false, min_order, glx, glw, sa, sd);
+        }
+    }
+}
+
+// distance ratio of panel j (its bounding sphere) to the singular points of row X
+__device__ __forceinline__ double panel_ratio(const Ctx<double> &c, const double *X, const double *ax) {
+    double dmin = sqrt((X[0] - ax[0]) * (X[0] - ax[0]) + (X[1] - ax[1]) * (X[1] - ax[1]) + (X[2] - ax[2]) * (X[2] - ax[2]));
+    if (c.img) {
+        const double d2 = (c.Xs[0] - ax[0]) * (c.Xs[0] - ax[0]) + (c.Xs[1] - ax[1]) * (c.Xs[1] - ax[1]) +
+                          (c.Xs[2] - ax[2]) * (c.Xs[2] - ax[2]);
+        dmin = fmin(dmin, sqrt(d2));
+    }
+    return dmin / ax[3];
+}
+
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
-    const int64_t row = blockIdx.x;
-    const int64_t p = find_group(P.panel_off, P.n_patches, row);
+    int64_t p, row;
+    int n, i;
+    double *Arow = nullptr;
+    if (P.mode == 1) {
+        const int64_t grp = find_group(P.grows_off, P.n_groups, (int64_t)blockIdx.x);
+        i = (int)(blockIdx.x - P.grows_off[grp]);
+        p = P.rep[grp];
+        n = (int)(P.grows_off[grp + 1] - P.grows_off[grp]);
+        row = P.panel_off[p] + i;
+        Arow = P.A + P.gmat_off[grp] + (int64_t)i * n;
+    } else {
+        row = blockIdx.x;
+        p = find_group(P.panel_off, P.n_patches, row);
+        n = (int)(P.panel_off[p + 1] - P.panel_off[p]);
+        i = (int)(row - P.panel_off[p]);
+        if (P.mode == 0) Arow = P.A + P.mat_off[p] + (int64_t)i * n;
+    }
     const PatchFrame f = P.frames[p];
     const int64_t poff = P.panel_off[p];
-    const int n = (int)(P.panel_off[p + 1] - poff);
-    const int i = (int)(row - poff);
     __shared__ double red[2][kAsmThreads / 32];
-    if (f.status != DTN_OK) {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) P.A[P.mat_off[p] + (int64_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+    if (P.mode != 1 && f.status != DTN_OK) {
+        if (Arow)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) Arow[j] = (i == j) ? 1.0 : 0.0;
         if (threadIdx.x == 0) P.b[row] = 0.0;
         return;
     }
@@ -259,77 +372,59 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     Ctx<double> c64;
     make_ctx<double>(c64, f, X, gx, &P.dat);
     c64.data32 = (P.prec == DTN_PREC_MIXED);
+    if (P.mode == 1) c64.needD = false;
     Ctx<float> c32;
     make_ctx<float>(c32, f, X, gx, &P.dat);
+    c32.data32 = true;
+    if (P.mode == 2) c32.needA = false;
     double dsum = 0.0;
+    const bool doD = (P.mode != 1) && (f.kind == kCap);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int64_t pj = poff + j;
         const double *prm = P.panel_prm + 6 * pj;
+        if (P.mode == 2) {
+            // double layer only, bounded integrand, FP32 rules
+            if (!doD) break;
+            float a32 = 0.f, d32 = 0.f;
+            if (j == i) {
+                self_panel<float>(c32, f, prm, 8, P.glx, P.glw, a32, d32);
+            } else {
+                const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
+                Region R;
+                R.tri = false;
+                R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
+                R.det = 0.0;
+                if (r >= 2.0) gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
+                else integrate_region<float>(c32, R, true, 0, P.glx, P.glw, a32, d32);
+            }
+            dsum += (double)d32;
+            continue;
+        }
         double sa = 0.0, sd = 0.0;
         if (j == i) {
-            // self panel: triangles from the collocation point (uc, vc) to each side,
-            // each side cut into m pieces so that every Duffy triangle's far edge is
-            // no longer than its height (the angular factor of the transformed
-            // integrand then stays smooth for thin panels)
-            const double S[2] = {prm[4], prm[5]};
-            const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
-            const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
-            double PS[3], nl[3], J;
-            patch_point<double>(f.kind, f.R, S[0], S[1], PS, nl, J);
-            for (int e = 0; e < 4; ++e) {
-                double PA[3], PB[3];
-                patch_point<double>(f.kind, f.R, cu[e], cv[e], PA, nl, J);
-                patch_point<double>(f.kind, f.R, cu[e + 1], cv[e + 1], PB, nl, J);
-                const double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
-                const double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
-                const double cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2],
-                                      ab[0] * as[1] - ab[1] * as[0]};
-                const double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
-                const double h = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmax(L, 1e-300);
-                const int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
-                for (int k = 0; k < m; ++k) {
-                    const double ua = cu[e] + (cu[e + 1] - cu[e]) * k / m, va = cv[e] + (cv[e + 1] - cv[e]) * k / m;
-                    const double ub = cu[e] + (cu[e + 1] - cu[e]) * (k + 1) / m;
-                    const double vb = cv[e] + (cv[e + 1] - cv[e]) * (k + 1) / m;
-                    Region R;
-                    R.tri = true;
-                    R.p[0] = S[0]; R.p[1] = S[1];
-                    R.p[2] = ua - S[0]; R.p[3] = va - S[1];
-                    R.p[4] = ub - ua; R.p[5] = vb - va;
-                    R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
-                    if (R.det == 0.0) continue;
-                    integrate_region<double>(c64, R, false, 16, P.glx, P.glw, sa, sd);
-                }
-            }
+            self_panel<double>(c64, f, prm, 16, P.glx, P.glw, sa, sd);
         } else {
-            const double *ax = P.panel_aux + 4 * pj;
-            double dmin = sqrt((X[0] - ax[0]) * (X[0] - ax[0]) + (X[1] - ax[1]) * (X[1] - ax[1]) +
-                               (X[2] - ax[2]) * (X[2] - ax[2]));
-            if (c64.img) {
-                const double d2 = (c64.Xs[0] - ax[0]) * (c64.Xs[0] - ax[0]) + (c64.Xs[1] - ax[1]) * (c64.Xs[1] - ax[1]) +
-                                  (c64.Xs[2] - ax[2]) * (c64.Xs[2] - ax[2]);
-                dmin = fmin(dmin, sqrt(d2));
-            }
-            const double r = dmin / ax[3];
+            const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
             Region R;
             R.tri = false;
             R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
             R.det = 0.0;
             if (r >= 2.0) {
-                if (P.prec == DTN_PREC_MIXED) {
+                if (P.mode == 0 && P.prec == DTN_PREC_MIXED) {
                     float a32 = 0.f, d32 = 0.f;
-                    gauss_square<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
+                    gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
                     sa = a32; sd = d32;
                 } else {
-                    gauss_square<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
+                    gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
                 }
             } else {
                 integrate_region<double>(c64, R, true, 0, P.glx, P.glw, sa, sd);
             }
         }
-        P.A[P.mat_off[p] + (int64_t)i * n + j] = sa;
+        Arow[j] = sa;
         dsum += sd;
     }
+    if (P.mode == 1) return;
     // Gamma term: sum_k W_k P(x_i, y_k) (U_k - g(x_i)), FP64
     const int64_t goff = P.gamma_off[p];
     const int nk = (int)(P.gamma_off[p + 1] - goff);
@@ -354,20 +449,34 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     }
 }
 
+__global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat_off,
+                              const int64_t *__restrict__ group_of, const int64_t *__restrict__ gmat_off,
+                              const double *__restrict__ gA, double *__restrict__ A) {
+    const int64_t p = blockIdx.y;
+    if (p >= n_patches) return;
+    const int64_t len = mat_off[p + 1] - mat_off[p];
+    const double *src = gA + gmat_off[group_of[p]];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x)
+        A[mat_off[p] + k] = src[k];
+}
+
 }  // namespace
 
-cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
+cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
                             const double *U, double *A, double *b, cudaStream_t s) {
-    if (L.panels_total == 0) return cudaSuccess;
+    const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
+    if (rows == 0) return cudaSuccess;
     AsmDev P;
     P.frames = D.frames;
     P.panel_off = D.panel_off;
     P.gamma_off = D.gamma_off;
     P.mat_off = D.mat_off;
-    P.ns = D.ns;
-    P.nr = D.nr;
+    P.grows_off = D.grows_off;
+    P.rep = D.rep;
+    P.gmat_off = D.gmat_off;
+    P.n_groups = L.n_groups;
     P.panel_loc = panel_loc;
     P.panel_prm = panel_prm;
     P.panel_aux = panel_aux;
@@ -380,9 +489,17 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.dat = g->dd;
     P.n_patches = L.n_patches;
     P.prec = prec;
+    P.mode = mode;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
-    assemble_kernel<<<(unsigned)L.panels_total, kAsmThreads, 0, s>>>(P);
+    assemble_kernel<<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA, double *A,
+                                   cudaStream_t s) {
+    if (L.n_patches == 0) return cudaSuccess;
+    expand_kernel<<<dim3(8, (unsigned)L.n_patches), 256, 0, s>>>(L.n_patches, D.mat_off, D.group_of, D.gmat_off, gA, A);
     return cudaGetLastError();
 }
 

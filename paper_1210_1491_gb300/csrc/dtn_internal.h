@@ -33,6 +33,14 @@ struct BatchLayout {
     std::vector<int32_t> nt, nph, nr, ns;                 // n
     std::vector<int64_t> walks;                           // n
     std::vector<uint32_t> pid;                            // n
+    std::vector<double> radius;                           // n
+    // shape groups (patches with equal radius, rings and sectors): the matrix of
+    // Eq. bw50 in the patch frame is the same for all members
+    int64_t n_groups = 0;
+    std::vector<int64_t> group_of;                        // n
+    std::vector<int64_t> rep;                             // n_groups: first member
+    std::vector<int64_t> grows_off, gmat_off, gfac_off;   // n_groups + 1
+    int64_t grows_total = 0, gmat_total = 0, gfac_total = 0;
 };
 
 // Device copies of one layout (kept in the geometry workspace).
@@ -40,6 +48,8 @@ struct DevLayout {
     int64_t *gamma_off, *panel_off, *mat_off, *walks, *chunk_off;
     int32_t *nt, *nph, *nr, *ns, *cpn;
     uint32_t *pid;
+    double *radius;
+    int64_t *group_of, *rep, *grows_off, *gmat_off, *gfac_off;
     PatchFrame *frames;
 };
 
@@ -60,6 +70,9 @@ struct Workspace {
     DevBuf counter;         // work counter(s)
     DevBuf se_tmp;          // gamma_total (standard errors when not requested)
     DevBuf tune;            // autotuner outputs (means, steps)
+    DevBuf gmat;            // shared matrices, one per shape group (FP64)
+    DevBuf gfac;            // shared FP32 factors, n(n+1) per group
+    DevBuf gpiv;            // shared pivots, n per group
 };
 
 struct GeometryHost {
@@ -90,6 +103,7 @@ struct dtn_geometry {
     char dev_name[256] = {0};
     uint64_t data_version = 0;                // bumped by every dtn_set_dirichlet
     cudaGraphExec_t graph_exec = nullptr;     // last captured solve (graph_capture)
+    cudaStream_t cap_stream = nullptr;        // private stream used for capture
     std::vector<unsigned char> graph_key;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool stages_recorded = false;
@@ -120,7 +134,7 @@ void gauss_legendre_host(int n, double *x, double *w);
 
 // launchers (each enqueues on `s`)
 cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
-                               const double *centers, const double *radius, double *gamma_xyz,
+                               const double *centers, double *gamma_xyz,
                                double *gamma_w, double *gamma_loc, double *colloc, double *normals,
                                double *areas, double *panel_loc, double *panel_prm, double *panel_aux,
                                double *panel_g, cudaStream_t s);
@@ -150,11 +164,18 @@ struct WosLaunch {
 };
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s);
 
+// mode 0: per patch, A and b (FP64 rules, or FP32 far field in mixed precision);
+// mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off;
+// mode 2: b only, per patch (mixed precision rules for the double layer)
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
-                            int prec, const double *panel_loc, const double *panel_prm,
+                            int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
                             const double *gamma_w, const double *U, double *A, double *b,
                             cudaStream_t s);
+
+// copies each patch's group matrix into its own block (mat_off) for checking
+cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA,
+                                   double *A, cudaStream_t s);
 
 // bytes of global factor scratch the LU launch needs (0 when the factors fit in
 // shared memory)
@@ -163,6 +184,13 @@ size_t lu_scratch_bytes(const BatchLayout &L, int prec);
 cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec,
                             const double *A, const double *b, double *q, int max_iters, double tol,
                             int32_t *iters, double *resid, int32_t *status, cudaStream_t s);
+
+// shared-matrix path: FP32 factors of every group matrix, then one solve with
+// FP64-residual refinement per patch against its group's matrix and factors
+cudaError_t launch_lu_shared(dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                             const double *gA, const double *b, double *q, int max_iters, double tol,
+                             int32_t *iters, double *resid, int32_t *status, cudaStream_t s);
+size_t lu_shared_scratch_bytes(const BatchLayout &L);
 
 cudaError_t launch_potential(int64_t np, const int64_t *index, const int64_t *n_index, const double *xyz,
                              const double *nrm, const double *area, const double *q, const double *g,

@@ -129,7 +129,7 @@ dtn_status launch_batch(dtn_server *S, Slot &sl, const std::vector<int64_t> &tic
     dtn_patch_batch b{};
     b.n_patches = n;
     b.centers = sl.d_centers.as<double>();
-    b.radius = sl.d_radius.as<double>();
+    b.radius = sl.h_radius.p;   // per-patch shape parameter: host array
     b.n_theta = sl.nt.data();
     b.n_phi = sl.nph.data();
     b.n_rings = sl.nr.data();

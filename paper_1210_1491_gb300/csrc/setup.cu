@@ -280,13 +280,13 @@ __global__ void panels_kernel(DData dat, int64_t n_patches, int64_t total, const
 }  // namespace
 
 cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
-                               const double *centers, const double *radius, double *gamma_xyz,
+                               const double *centers, double *gamma_xyz,
                                double *gamma_w, double *gamma_loc, double *colloc, double *normals,
                                double *areas, double *panel_loc, double *panel_prm, double *panel_aux,
                                double *panel_g, cudaStream_t s) {
     const int T = 128;
     const int64_t n = L.n_patches;
-    patch_frame_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dg, n, centers, radius, D.frames);
+    patch_frame_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dg, n, centers, D.radius, D.frames);
     if (L.gamma_total > 0)
         gamma_nodes_kernel<<<(unsigned)((L.gamma_total + T - 1) / T), T, 0, s>>>(
             n, L.gamma_total, D.gamma_off, D.nt, D.nph, D.frames, gl_x_dev(), gl_w_dev(), gamma_xyz,

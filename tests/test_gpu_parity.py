@@ -208,11 +208,13 @@ def test_assembly_and_solve_parity_given_U(which):
             Ao, bo = O.assemble(pf, wl.data, nr, ns, nt, nph, U[p * P:(p + 1) * P], rtol=1e-13)
             A = _np(res["matrix"])[p * n * n:(p + 1) * n * n].reshape(n, n)
             b = _np(res["rhs"])[p * n:(p + 1) * n]
+            # the matrix uses the FP64 rules in both modes (mixed precision shares one
+            # matrix per patch shape); entries agree to ~1e-12 of the largest
+            assert np.max(np.abs(A - Ao)) <= 1e-11 * np.max(np.abs(Ao))
             if prec == dtn.PREC_FP64:
-                assert np.max(np.abs(A - Ao)) <= 1e-12 * np.max(np.abs(Ao))
                 assert np.max(np.abs(b - bo)) <= 1e-11 * np.max(np.abs(bo))
             else:
-                assert np.max(np.abs(A - Ao)) <= 1e-6 * np.max(np.abs(Ao))
+                assert np.max(np.abs(b - bo)) <= 1e-6 * np.max(np.abs(bo))
             qo = np.linalg.solve(Ao, bo)
             q = _np(res["neumann"])[p * n:(p + 1) * n]
             rel = np.linalg.norm(q - qo) / np.linalg.norm(qo)
