@@ -262,8 +262,10 @@ dtn_status dtn_autotune_walks(dtn_geometry *geom, const dtn_patch_batch *batch,
 
 /* Device time in milliseconds of the stages of the last dtn_solve_patches call
  * on geom made with record_stages = 1: ms[0] patch setup, ms[1] walks and their
- * estimates, ms[2] assembly, ms[3] LU and refinement.  Waits for that call's
- * last event.  DTN_E_INVALID_ARG if no call recorded stages. */
+ * estimates, ms[2] assembly, ms[3] LU and refinement.  A call replayed as a
+ * CUDA graph (graph_capture) is timed as a whole in ms[0], with ms[1..3] = 0.
+ * Waits for that call's last event.  DTN_E_INVALID_ARG if no call recorded
+ * stages. */
 dtn_status dtn_stage_times(dtn_geometry *geom, float ms[4]);
 
 /* Human-readable name of a status code (static storage). */

@@ -50,6 +50,7 @@ namespace {
 dtn_status to_status(cudaError_t e) {
     if (e == cudaSuccess) return DTN_OK;
     set_cuda_error(e);
+    cudaGetLastError();   // do not leave a non-sticky error for the caller's next CUDA call
     return e == cudaErrorMemoryAllocation ? DTN_E_OUT_OF_MEMORY : DTN_E_CUDA;
 }
 
@@ -449,7 +450,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
-                      &g->ws.gfac, &g->ws.gpiv};
+                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gpre};
     for (DevBuf *b : bufs) b->release();
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
@@ -554,7 +555,9 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     if (shared) {
         if ((e = W.gmat.reserve((size_t)L.gmat_total * 8)) != cudaSuccess ||
             (e = W.gfac.reserve(lu_shared_scratch_bytes(L))) != cudaSuccess ||
-            (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess)
+            (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess ||
+            (g->dg.kind == kBall &&
+             (e = W.gpre.reserve((size_t)L.panels_total * kGprePerPanel * sizeof(float))) != cudaSuccess))
             return to_status(e);
     } else if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) {
         return to_status(e);
@@ -591,7 +594,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                                 &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
-                                &W.gmat, &W.gfac, &W.gpiv};
+                                &W.gmat, &W.gfac, &W.gpiv, &W.gpre};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
@@ -604,7 +607,10 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
                 return to_status(e);
             if ((e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
                 return to_status(e);
-            cudaError_t ce = enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, g->cap_stream);
+            // (stage events are not recorded inside the graph: the whole replay is
+            // timed instead, see below)
+            cudaError_t ce = enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, false,
+                                           g->cap_stream);
             cudaGraph_t graph = nullptr;
             e = cudaStreamEndCapture(g->cap_stream, &graph);
             if (ce != cudaSuccess) e = ce;
@@ -616,7 +622,14 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
             }
             g->graph_key.swap(key);
         }
-        return to_status(cudaGraphLaunch(g->graph_exec, s));
+        // a replay is timed as a whole: stage 0 spans the graph, stages 1-3 are empty
+        if (rec && (e = cudaEventRecord(g->stage_ev[0], s)) != cudaSuccess) return to_status(e);
+        e = cudaGraphLaunch(g->graph_exec, s);
+        if (e == cudaSuccess && rec) {
+            e = cudaEventRecord(g->stage_ev[1], s);
+            for (int k = 2; k < 5 && e == cudaSuccess; ++k) e = cudaEventRecord(g->stage_ev[k], s);
+        }
+        return to_status(e);
     }
     return to_status(enqueue_solve(g, L, D, o, wp, total_chunks, b, r, gxyz, gw, pg, A, rhs, rec, s));
 }
@@ -676,14 +689,14 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         // one matrix per patch shape, FP64 rules; the right sides per patch
         double *gA = W.gmat.as<double>();
         e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                            gA, rhs, s);
+                            gA, rhs, nullptr, s);
         if (e == cudaSuccess)
             e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                                gA, rhs, s);
+                                gA, rhs, W.gpre.as<float>(), s);
         if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
     } else {
         e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,
-                            rhs, s);
+                            rhs, nullptr, s);
     }
     if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;

@@ -33,6 +33,9 @@ constexpr int kAsmThreads = 128;
 constexpr int kMaxDepth = 10;
 constexpr int kStack = 40;
 constexpr int kMaxRule = 20;   // highest Gauss order the rules below use
+// fixed double-layer rules of the right side (mixed precision): per panel an
+// 8x8 Gauss rule (64 points) and the same rule on its four quarters (256)
+constexpr int kPreCoarse = 64, kPrePerPanel = 320, kPreN = 8;
 
 template <typename T>
 struct Ctx {
@@ -108,7 +111,8 @@ __device__ void gauss_square(const Ctx<T> &c, const Region &R, T x0, T x1, T e0,
 // the sines and cosines of u and of v are taken once per Gauss line.
 template <typename T>
 __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, int n,
-                           const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
+                           const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd,
+                           const float *__restrict__ gpre = nullptr) {
     const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
     const T hx = (T)0.5 * (x1 - x0), mx = (T)0.5 * (x0 + x1);
     const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
@@ -137,11 +141,16 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
             if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
             if (c.needD) {
                 const T nl[3] = {nu * cvs[j], nu * svs[j], nz};
-                const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
-                const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
-                const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
-                const T gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
-                                      : dirichlet_eval<T>(*c.dat, yx, yy, yz);
+                T gy;
+                if (gpre) {
+                    gy = (T)gpre[i * n + j];   // data precomputed at this rule's points
+                } else {
+                    const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+                    const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+                    const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+                    gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
+                                  : dirichlet_eval<T>(*c.dat, yx, yy, yz);
+                }
                 sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
             }
         }
@@ -289,6 +298,7 @@ struct AsmDev {
     int prec;
     int mode;
     const double *glx, *glw;
+    const float *gpre;    // mode 2: data at the fixed per-panel rules
 };
 
 // self panel: triangles from the collocation point (uc, vc) to each side, each
@@ -383,19 +393,30 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         const int64_t pj = poff + j;
         const double *prm = P.panel_prm + 6 * pj;
         if (P.mode == 2) {
-            // double layer only, bounded integrand, FP32 rules
+            // double layer only: the integrand (g(y) - g(x_i)) dG/dn_y is bounded,
+            // so fixed 8x8 rules with the data precomputed per patch (whole panel
+            // when the panel is far, its four quarters when near) and a Duffy rule
+            // on the self panel, all FP32
             if (!doD) break;
             float a32 = 0.f, d32 = 0.f;
             if (j == i) {
-                self_panel<float>(c32, f, prm, 8, P.glx, P.glw, a32, d32);
+                self_panel<float>(c32, f, prm, 6, P.glx, P.glw, a32, d32);
             } else {
                 const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
                 Region R;
                 R.tri = false;
                 R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
                 R.det = 0.0;
-                if (r >= 2.0) gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
-                else integrate_region<float>(c32, R, true, 0, P.glx, P.glw, a32, d32);
+                const float *gp = P.gpre + pj * kPrePerPanel;
+                if (r >= 2.0) {
+                    gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, kPreN, P.glx, P.glw, a32, d32, gp);
+                } else {
+                    for (int s = 0; s < 4; ++s) {
+                        const float x0 = 0.5f * (s & 1), e0 = 0.5f * (s >> 1);
+                        gauss_rect<float>(c32, R, x0, x0 + 0.5f, e0, e0 + 0.5f, kPreN, P.glx, P.glw, a32, d32,
+                                          gp + kPreCoarse + kPreCoarse * s);
+                    }
+                }
             }
             dsum += (double)d32;
             continue;
@@ -449,6 +470,41 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     }
 }
 
+// Data g at the fixed per-panel rules of the double-layer term (cap patches):
+// points 0..63 the 8x8 Gauss rule on the panel, points 64..319 the same rule on
+// each quarter of the panel (quarter s = 2 e + x of the parameter box).  One
+// thread per point; the row kernels read these values instead of evaluating
+// the harmonic data again for every collocation row.
+__global__ void panel_gpre_kernel(DData dat, int64_t n_patches, int64_t total, const int64_t *__restrict__ panel_off,
+                                  const PatchFrame *__restrict__ frames, const double *__restrict__ panel_prm,
+                                  const double *__restrict__ glx, float *__restrict__ out) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int64_t pj = idx / kPrePerPanel;
+    const int q = (int)(idx - pj * kPrePerPanel);
+    const int64_t p = find_group(panel_off, n_patches, pj);
+    const PatchFrame &f = frames[p];
+    const double *prm = panel_prm + 6 * pj;
+    double x0 = 0.0, x1 = 1.0, e0 = 0.0, e1 = 1.0;
+    int k = q;
+    if (q >= kPreCoarse) {
+        const int s = (q - kPreCoarse) / kPreCoarse;
+        k = (q - kPreCoarse) % kPreCoarse;
+        x0 = 0.5 * (s & 1); x1 = x0 + 0.5;
+        e0 = 0.5 * (s >> 1); e1 = e0 + 0.5;
+    }
+    const int i = k / kPreN, j = k % kPreN;
+    const double *gx = glx + kPreN * (kPreN - 1) / 2;
+    const double u = prm[0] + (0.5 * (x0 + x1) + 0.5 * (x1 - x0) * gx[i]) * (prm[1] - prm[0]);
+    const double v = prm[2] + (0.5 * (e0 + e1) + 0.5 * (e1 - e0) * gx[j]) * (prm[3] - prm[2]);
+    double Y[3], nl[3], J;
+    patch_point<double>(f.kind, f.R, u, v, Y, nl, J);
+    const double y0 = f.c[0] + Y[0] * f.t1[0] + Y[1] * f.t2[0] + Y[2] * f.n[0];
+    const double y1 = f.c[1] + Y[0] * f.t1[1] + Y[1] * f.t2[1] + Y[2] * f.n[1];
+    const double y2 = f.c[2] + Y[0] * f.t1[2] + Y[1] * f.t2[2] + Y[2] * f.n[2];
+    out[idx] = dirichlet_eval<float>(dat, (float)y0, (float)y1, (float)y2);
+}
+
 __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat_off,
                               const int64_t *__restrict__ group_of, const int64_t *__restrict__ gmat_off,
                               const double *__restrict__ gA, double *__restrict__ A) {
@@ -465,7 +521,7 @@ __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
-                            const double *U, double *A, double *b, cudaStream_t s) {
+                            const double *U, double *A, double *b, float *gpre, cudaStream_t s) {
     const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
     if (rows == 0) return cudaSuccess;
     AsmDev P;
@@ -492,9 +548,19 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.mode = mode;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
+    P.gpre = gpre;
+    if (mode == 2 && g->dg.kind == kBall) {
+        // data at the fixed double-layer rules, once per patch
+        const int64_t total = L.panels_total * kPrePerPanel;
+        const int T = 256;
+        panel_gpre_kernel<<<(unsigned)((total + T - 1) / T), T, 0, s>>>(g->dd, L.n_patches, total, D.panel_off,
+                                                                        D.frames, panel_prm, P.glx, gpre);
+    }
     assemble_kernel<<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
+
+cudaError_t upload_sh_assemble(const ShTables &t) { return upload_sh_tables_here(t); }
 
 cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA, double *A,
                                    cudaStream_t s) {

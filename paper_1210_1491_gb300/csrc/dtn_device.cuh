@@ -105,7 +105,13 @@ template <typename T, int GK>
 __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z) {
     if (GK == kBall) {
         const T dx = x - (T)g.c[0], dy = y - (T)g.c[1], dz = z - (T)g.c[2];
-        return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
+        if constexpr (sizeof(T) == 4) {
+            // SFU reciprocal square root: |x| to a few FP32 ulps
+            const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
+            return (float)g.R - r2 * rsqrtf(r2);
+        } else {
+            return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
+        }
     } else if (GK == kBox) {
         return box_interior_dist<T>(g, x, y, z);
     } else {
@@ -199,15 +205,25 @@ struct DData {
     const ShTables *sh;     // device copy of the recurrence tables
 };
 
-template <typename T> __device__ __forceinline__ T sh_A(const ShTables *t, int l, int m);
-template <> __device__ __forceinline__ double sh_A<double>(const ShTables *t, int l, int m) { return t->A[l][m]; }
-template <> __device__ __forceinline__ float sh_A<float>(const ShTables *t, int l, int m) { return t->Af[l][m]; }
-template <typename T> __device__ __forceinline__ T sh_B(const ShTables *t, int l, int m);
-template <> __device__ __forceinline__ double sh_B<double>(const ShTables *t, int l, int m) { return t->B[l][m]; }
-template <> __device__ __forceinline__ float sh_B<float>(const ShTables *t, int l, int m) { return t->Bf[l][m]; }
-template <typename T> __device__ __forceinline__ T sh_D(const ShTables *t, int m);
-template <> __device__ __forceinline__ double sh_D<double>(const ShTables *t, int m) { return t->D[m]; }
-template <> __device__ __forceinline__ float sh_D<float>(const ShTables *t, int m) { return t->Df[m]; }
+// The recurrence coefficients live in constant memory: every index (l, m) is the
+// same across a warp, so reads are broadcasts with no load latency.  Each
+// translation unit has its own copy (no relocatable device code), filled by its
+// upload function at table set-up.
+static __constant__ ShTables c_sh;
+
+static inline cudaError_t upload_sh_tables_here(const ShTables &t) {
+    return cudaMemcpyToSymbol(c_sh, &t, sizeof(t));
+}
+
+template <typename T> __device__ __forceinline__ T sh_A(const ShTables *, int l, int m);
+template <> __device__ __forceinline__ double sh_A<double>(const ShTables *, int l, int m) { return c_sh.A[l][m]; }
+template <> __device__ __forceinline__ float sh_A<float>(const ShTables *, int l, int m) { return c_sh.Af[l][m]; }
+template <typename T> __device__ __forceinline__ T sh_B(const ShTables *, int l, int m);
+template <> __device__ __forceinline__ double sh_B<double>(const ShTables *, int l, int m) { return c_sh.B[l][m]; }
+template <> __device__ __forceinline__ float sh_B<float>(const ShTables *, int l, int m) { return c_sh.Bf[l][m]; }
+template <typename T> __device__ __forceinline__ T sh_D(const ShTables *, int m);
+template <> __device__ __forceinline__ double sh_D<double>(const ShTables *, int m) { return c_sh.D[m]; }
+template <> __device__ __forceinline__ float sh_D<float>(const ShTables *, int m) { return c_sh.Df[m]; }
 template <typename T> __device__ __forceinline__ T clm_at(const DData &d, int i);
 template <> __device__ __forceinline__ double clm_at<double>(const DData &d, int i) { return d.clm[i]; }
 template <> __device__ __forceinline__ float clm_at<float>(const DData &d, int i) { return d.clm_f[i]; }

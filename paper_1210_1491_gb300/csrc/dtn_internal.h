@@ -73,6 +73,7 @@ struct Workspace {
     DevBuf gmat;            // shared matrices, one per shape group (FP64)
     DevBuf gfac;            // shared FP32 factors, n(n+1) per group
     DevBuf gpiv;            // shared pivots, n per group
+    DevBuf gpre;            // data at the fixed double-layer rules (cap patches)
 };
 
 struct GeometryHost {
@@ -130,6 +131,9 @@ cudaError_t ensure_tables();
 const double *gl_x_dev();
 const double *gl_w_dev();
 const ShTables *sh_tables_dev();
+// per-unit constant-memory copies of the harmonic recurrence tables
+cudaError_t upload_sh_wos(const ShTables &t);
+cudaError_t upload_sh_assemble(const ShTables &t);
 void gauss_legendre_host(int n, double *x, double *w);
 
 // launchers (each enqueues on `s`)
@@ -171,7 +175,9 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
                             int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
                             const double *gamma_w, const double *U, double *A, double *b,
-                            cudaStream_t s);
+                            float *gpre, cudaStream_t s);
+// floats of data the mode-2 assembly precomputes per panel (cap patches)
+constexpr int64_t kGprePerPanel = 320;
 
 // copies each patch's group matrix into its own block (mat_off) for checking
 cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA,

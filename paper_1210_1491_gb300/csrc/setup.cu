@@ -84,6 +84,9 @@ cudaError_t ensure_tables() {
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(g_sh, &t, sizeof(t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
+    if ((e = upload_sh_tables_here(t)) != cudaSuccess) return e;
+    if ((e = upload_sh_wos(t)) != cudaSuccess) return e;
+    if ((e = upload_sh_assemble(t)) != cudaSuccess) return e;
     g_tab_ready = true;
     return cudaSuccess;
 }

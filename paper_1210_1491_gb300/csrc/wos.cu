@@ -86,12 +86,17 @@ struct LaneAcc {
 
 // one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
 // z uniform in (-1, 1), azimuth 2 pi u2
+// FP32 walks: the azimuth 2 pi u2 is reduced to (-pi, pi] (the same angle mod
+// 2 pi) and taken by the SFU sine/cosine; s = sqrt(1 - z^2) by the SFU
+// reciprocal square root (1 - z^2 >= 4 * 2^-24 > 0 for the 24-bit uniforms).
 __device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t w1, uint32_t w2) {
     const float u1 = u01_24(w1), u2 = u01_24(w2);
     const float zz = fmaf(-2.0f, u1, 1.0f);
-    const float s = sqrtf(fmaxf(0.0f, (1.0f - zz) * (1.0f + zz)));
+    const float t = (1.0f - zz) * (1.0f + zz);
+    const float s = t * rsqrtf(t);
+    const float a = 6.2831853071795865f * (u2 > 0.5f ? u2 - 1.0f : u2);
     float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
+    __sincosf(a, &sn, &cs);
     x = fmaf(d * s, cs, x);
     y = fmaf(d * s, sn, y);
     z = fmaf(d, zz, z);
@@ -109,7 +114,7 @@ __device__ __forceinline__ void jump(double &x, double &y, double &z, double d, 
 }
 
 template <typename T, int GK>
-__global__ void __launch_bounds__(kWosThreads) wos_kernel(WosDev P) {
+__global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
     extern __shared__ float s_boxes[];
     const float *sb = nullptr;
     if (GK == kBoxMinusBoxes && std::is_same<T, float>::value && P.g.nb <= kMaxSmemBoxes) {
@@ -132,14 +137,16 @@ __global__ void __launch_bounds__(kWosThreads) wos_kernel(WosDev P) {
     // lane state
     bool active = false, pending = false;
     T x = 0, y = 0, z = 0;
-    T nx = 0, ny = 0, nz = 0;
     uint32_t walk = 0, step = 0, ppid = 0, ppt = 0;
     double sc1 = 0.0, sc2 = 0.0;
     LaneAcc<T> acc;
 
     for (;;) {
-        // score absorbed walks together
+        // absorbed walks keep their absorption point until here: project it onto
+        // the boundary and score the data there, all pending lanes together
         if (pending) {
+            T nx, ny, nz;
+            geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
             const T sc = dirichlet_eval<T>(P.dat, nx, ny, nz);
             const double sd = (double)sc;
             acc.a1 += __double2ll_rn(sd * sc1);
@@ -204,7 +211,6 @@ __global__ void __launch_bounds__(kWosThreads) wos_kernel(WosDev P) {
                             const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                             ++step;
                             if (d <= eps) {
-                                geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
                                 acc.st += step;
                                 pending = true;
                                 active = false;
@@ -221,7 +227,6 @@ __global__ void __launch_bounds__(kWosThreads) wos_kernel(WosDev P) {
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     ++step;
                     if (d <= eps) {
-                        geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
                         acc.st += step;
                         pending = true;
                         active = false;
@@ -340,6 +345,8 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
         w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, cap, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
     return cudaGetLastError();
 }
+
+cudaError_t upload_sh_wos(const ShTables &t) { return upload_sh_tables_here(t); }
 
 // ---------------------------------------------------------------- small checks
 

@@ -336,12 +336,14 @@ def test_potential_parity():
     u64 = _np(dtn.eval_potential(g, y, nrm, ar, q, gv, t, prec=dtn.PREC_FP64))
     u32 = _np(dtn.eval_potential(g, y, nrm, ar, q, gv, t, prec=dtn.PREC_MIXED))
     assert np.linalg.norm(u64 - ref) <= 1e-12 * np.linalg.norm(ref)
-    # FP32 pair terms: each term carries a relative error of a few FP32 units, so
-    # the bound is a multiple of eps32 times the sum of |terms| per target
+    # FP32 pair terms: positions are FP32 offsets from a tile origin (|offset| <= 4
+    # here), so t - y carries an absolute error of a few eps32 * 4 and a term's
+    # relative error is at most ~ eps32 (8 + 48 / r); the bound sums that over the
+    # terms of each target
     d = t[:, None, :] - y[None]
     r = np.linalg.norm(d, axis=2)
     terms = np.abs(ar * q / (4 * np.pi * r)) + np.abs(ar * gv * np.einsum("tpk,pk->tp", d, nrm) / (4 * np.pi * r ** 3))
-    bound = 16 * np.finfo(np.float32).eps * terms.sum(axis=1)
+    bound = (np.finfo(np.float32).eps * terms * (8 + 48 / r)).sum(axis=1)
     assert np.all(np.abs(u32 - ref) <= bound)
     # smooth data (a harmonic potential from a patch cover) reaches 1e-6 relative
     assert np.linalg.norm(u32 - ref) <= 1e-4 * np.linalg.norm(ref)

@@ -51,8 +51,8 @@ def test_graph_replay_matches_direct_and_stage_times():
         dtn.solve_patches(g, c, rad, hb, og, result=res)
         torch.cuda.synchronize()
         assert np.array_equal(res["neumann"].cpu().numpy(), r0["neumann"].cpu().numpy())
-        ms = g.stage_times()
-        assert all(m >= 0 for m in ms) and ms[1] > 0
+        ms = g.stage_times()   # a replay is timed as a whole in ms[0]
+        assert all(m >= 0 for m in ms) and ms[0] > 0
 
 
 def test_autotuner_picks_and_results_unchanged():
