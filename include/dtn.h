@@ -234,6 +234,31 @@ dtn_status dtn_wos_points(const dtn_geometry *geom, int64_t n, const double *y,
                           const int64_t *walks, const dtn_solve_opts *opts, double *mean,
                           double *se, uint64_t *steps, uint32_t *capped, void *stream);
 
+/* dtn_wos_points for callers that cannot allocate device memory.  (The paper
+ * has no counterpart; this is a deployment variant.)  Some callers must not
+ * call cudaMalloc: a serving loop that cannot afford the device-wide
+ * synchronisation an allocation or a free may cause, or a host that owns all
+ * device memory through its own pool and cannot let a library take memory
+ * (or fail for lack of it) in the middle of a request.  This entry point
+ * allocates nothing: its scratch (walk accumulators, work counter, per-point
+ * tables) is one file-scope device array of about 4 MB that every GPU loading
+ * the library keeps until the process exits.
+ *   - n must be at most 65536 points; larger n returns DTN_E_INVALID_ARG
+ *     before any device work.  Arguments and outputs as in dtn_wos_points
+ *     (walks is a host array); se may be NULL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call uses the same array and leaves its contents behind; each call
+ *     clears the parts that must start at zero.  Calls whose work overlaps on
+ *     the GPU race on the array: serialise them (one stream, or events).
+ *   - Asynchronous on `stream`; the host array walks is copied before
+ *     return and may be reused at once. */
+dtn_status dtn_wos_points_noalloc(const dtn_geometry *geom, int64_t n, const double *y,
+                                  const uint32_t *point_ids, const uint32_t *patch_ids,
+                                  const int64_t *walks, const dtn_solve_opts *opts, double *mean,
+                                  double *se, uint64_t *steps, uint32_t *capped, void *stream);
+
 /* Distance to the boundary and nearest boundary point (the WOS sphere radius,
  * Sec. 2) at n device points; d and nearest are device outputs (n, n x 3).
  * prec selects FP64 or the FP32 arithmetic the mixed walks use. */

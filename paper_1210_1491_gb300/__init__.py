@@ -9,5 +9,5 @@ from .binding import (  # noqa: F401
     DATA_CONSTANT, DATA_HARMONIC_SH, DATA_POINT_SOURCE, EXPORTS, GEOM_BALL_INTERIOR,
     GEOM_BOX_INTERIOR, GEOM_BOX_MINUS_BOXES, LIB_PATH, PREC_FP64, PREC_MIXED, DtnError, Geometry,
     HostBatch, Server, alloc_result, autotune_walks, distance, eval_dirichlet, eval_potential, gather_owned, load,
-    philox, solve_opts, solve_patches, wos_points,
+    philox, solve_opts, solve_patches, wos_points, wos_points_noalloc,
 )

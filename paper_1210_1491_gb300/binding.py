@@ -90,7 +90,8 @@ EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "
            "dtn_solve_patches", "dtn_eval_potential", "dtn_gather_owned", "dtn_wos_points",
            "dtn_distance", "dtn_philox4x32_10", "dtn_eval_dirichlet", "dtn_status_string",
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
-           "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks"]
+           "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks",
+           "dtn_wos_points_noalloc"]
 
 _lib = None
 
@@ -125,6 +126,7 @@ def load(path: str = LIB_PATH):
         "dtn_server_destroy": ([vp], i32),
         "dtn_stage_times": ([vp, C.POINTER(C.c_float)], i32),
         "dtn_autotune_walks": ([vp, C.POINTER(PatchBatch), C.POINTER(SolveOpts), C.POINTER(Tuning), vp], i32),
+        "dtn_wos_points_noalloc": ([vp, i64, vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -384,6 +386,29 @@ def wos_points(geom: Geometry, y, point_ids, patch_ids, walks, opts: SolveOpts, 
                                  _ptr(mean), _ptr(se), _ptr(steps), _ptr(capped), _stream(stream)),
            "dtn_wos_points")
     return dict(mean=mean, se=se, steps=steps, capped=capped)
+
+
+def wos_points_noalloc(geom: Geometry, y, point_ids, patch_ids, walks, opts: SolveOpts, out=None,
+                       stream=None):
+    """dtn_wos_points_noalloc: the library allocates nothing (the caller's tensors
+    in `out`, if given, receive mean / se / steps / capped)."""
+    yy = _dev(y, torch.float64).reshape(-1, 3)
+    n = yy.shape[0]
+    pt32 = _dev(np.broadcast_to(np.asarray(point_ids, dtype=np.uint32), (n,)).astype(np.int64),
+                torch.int64).to(torch.int32).contiguous()
+    pa32 = _dev(np.broadcast_to(np.asarray(patch_ids, dtype=np.uint32), (n,)).astype(np.int64),
+                torch.int64).to(torch.int32).contiguous()
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(walks, dtype=np.int64), (n,)))
+    if out is None:
+        out = dict(mean=torch.empty(n, dtype=torch.float64, device="cuda"),
+                   se=torch.empty(n, dtype=torch.float64, device="cuda"),
+                   steps=torch.empty(n, dtype=torch.int64, device="cuda"),
+                   capped=torch.empty(n, dtype=torch.int32, device="cuda"))
+    _check(load().dtn_wos_points_noalloc(geom.handle, n, _ptr(yy), _ptr(pt32), _ptr(pa32), _ptr(w), C.byref(opts),
+                                         _ptr(out["mean"]), _ptr(out.get("se")), _ptr(out.get("steps")),
+                                         _ptr(out.get("capped")), _stream(stream)),
+           "dtn_wos_points_noalloc")
+    return out
 
 
 def distance(geom: Geometry, x, prec=PREC_FP64, stream=None):

@@ -167,6 +167,8 @@ struct WosLaunch {
     uint32_t *capped;
 };
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s);
+size_t wos_scratch_bytes(int64_t nodes);
+cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s);
 
 // mode 0: per patch, A and b (FP64 rules, or FP32 far field in mixed precision);
 // mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off;

@@ -346,6 +346,75 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Same launch as launch_wos, but the accumulators and the work counter live in
+// caller-provided device memory (`acc`, at least wos_scratch_bytes(nodes)
+// bytes, 256-byte aligned) instead of the geometry's workspace, so nothing is
+// allocated here.
+size_t wos_scratch_bytes(int64_t nodes) {
+    return (size_t)nodes * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
+}
+
+cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s) {
+    if (w.total_nodes == 0) return cudaSuccess;
+    cudaError_t e;
+    const size_t n = (size_t)w.total_nodes;
+    const size_t bytes = wos_scratch_bytes(w.total_nodes);
+    char *base = (char *)acc;
+    unsigned long long *counter = (unsigned long long *)base;
+    unsigned long long *s1 = (unsigned long long *)(base + 64);
+    unsigned long long *s2 = s1 + n, *st = s2 + n;
+    unsigned int *cap = (unsigned int *)(st + n);
+    if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
+    const double M = g->score_bound > 0 ? g->score_bound : 1.0;
+    const int lgM1 = (int)std::ceil(std::log2(M)), lgM2 = (int)std::ceil(std::log2(M * M));
+    WosDev P;
+    P.g = g->dg;
+    P.dat = g->dd;
+    P.y = w.y;
+    P.node_off = w.node_off;
+    P.walks = w.walks;
+    P.pid = w.pid;
+    P.point_id = w.point_id;
+    P.chunk_off = w.chunk_off;
+    P.cpn = w.cpn;
+    P.n_groups = w.n_groups;
+    P.total_chunks = w.total_chunks;
+    P.chunk = w.chunk;
+    P.refill = w.refill > 0 ? std::min(w.refill, 32) : 8;
+    P.counter = counter;
+    P.s1 = s1; P.s2 = s2; P.st = st; P.cap = cap;
+    P.lgM1 = lgM1;
+    P.lgM2 = lgM2;
+    P.eps = w.eps;
+    P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
+    P.k0 = (uint32_t)(w.seed & 0xFFFFFFFFull);
+    P.k1 = (uint32_t)(w.seed >> 32);
+    const int gk = g->dg.kind;
+    const bool fp32 = (w.prec == DTN_PREC_MIXED);
+    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
+    const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
+    if (smem > 48 * 1024) {
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+    }
+    int resident = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, kWosThreads, smem)) != cudaSuccess)
+        return e;
+    resident = std::max(resident, 1);
+    const int bps = w.blocks_per_sm > 0 ? std::min(w.blocks_per_sm, resident) : resident;
+    int64_t blocks = (int64_t)g->num_sms * bps;
+    const int64_t max_blocks = (w.total_chunks + (kWosThreads / 32) - 1) / (kWosThreads / 32);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    void *args[] = {&P};
+    if ((e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kWosThreads), args, smem, s)) != cudaSuccess)
+        return e;
+    const int T = 256;
+    wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
+        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, cap, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+    return cudaGetLastError();
+}
+
 cudaError_t upload_sh_wos(const ShTables &t) { return upload_sh_tables_here(t); }
 
 // ---------------------------------------------------------------- small checks
