@@ -176,6 +176,52 @@ def cpu_baseline_sample(wl):
             "walk_steps_per_s": steps / dt}
 
 
+def run_serving(dtn, n_queries=32, seed=7, load=0.8):
+    """Continuous-batching server on the 200-wire geometry: queries of 1..64 patches
+    (log-uniform) with 512..4096 walks per node (log-uniform), first all at once
+    (saturated throughput), then as Poisson arrivals at `load` x that rate; returns
+    p50/p99 submit-to-result latency."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    wl = W.wires(n_patches=4096, walks=2048)
+    b = wl.batch
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    opts = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=wl.epsilon, seed=wl.seed)
+    queries, start = [], 0
+    for _ in range(n_queries):
+        n = int(np.exp(rng.uniform(0.0, np.log(64.0))))
+        idx = (start + np.arange(n)) % b.n
+        start += n
+        walks = int(np.exp(rng.uniform(np.log(512.0), np.log(4096.0))))
+        queries.append(dict(centers=b.centers[idx], radius=b.radius[idx], n_theta=b.n_theta[idx],
+                            n_phi=b.n_phi[idx], n_rings=b.n_rings[idx], n_sectors=b.n_sectors[idx],
+                            walks=np.full(n, walks, np.int64), patch_ids=idx.astype(np.uint32)))
+    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024)
+    # warm-up (first-use costs)
+    srv.submit(**queries[0])
+    srv.drain()
+    t0 = time.perf_counter()
+    for q in queries:
+        srv.submit(**q)
+    srv.drain()
+    t_sat = time.perf_counter() - t0
+    rate = load * n_queries / t_sat
+    gaps = rng.exponential(1.0 / rate, n_queries)
+    tickets = []
+    t0 = time.perf_counter()
+    for q, gap in zip(queries, gaps):
+        time.sleep(gap)
+        tickets.append(srv.submit(**q))
+    srv.drain()
+    t_poisson = time.perf_counter() - t0
+    lat = np.array([srv.poll(t)["latency_s"] for t in tickets]) * 1e3
+    srv.close()
+    patches = int(sum(len(q["radius"]) for q in queries))
+    return {"geometry": "box [0,64]^2x[0,16] minus 200 wires", "queries": n_queries, "patches": patches,
+            "saturated_queries_per_s": n_queries / t_sat, "saturated_patches_per_s": patches / t_sat,
+            "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "poisson_patches_per_s": patches / t_poisson}
+
+
 def run_ours(args):
     import torch
     import paper_1210_1491_gb300 as dtn
@@ -214,8 +260,14 @@ def run_ours(args):
         dtn.eval_potential(g, res["colloc_xyz"], res["normals"], res["areas"], res["neumann"],
                            res["dirichlet"], tgt, prec=prec, out=u_out, index=kept, n_index=nk)
 
-    # walk-kernel launch parameters picked by the library's autotuner (untimed)
-    tuning = dtn.autotune_walks(g, centers, radius, hb, opts)
+    # walk-kernel launch parameters picked by the library's autotuner (untimed),
+    # or fixed on the command line (profiler captures)
+    if args.walk_params:
+        wc, wb, wr = (int(v) for v in args.walk_params.split(","))
+        opts.walk_chunk, opts.wos_blocks_per_sm, opts.wos_refill = wc, wb, wr
+        tuning = dict(walk_chunk=wc, wos_blocks_per_sm=wb, wos_refill=wr, source="command line")
+    else:
+        tuning = dtn.autotune_walks(g, centers, radius, hb, opts)
     for _ in range(args.warmup):
         full_step()
     torch.cuda.synchronize()
@@ -294,9 +346,10 @@ def run_ours(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # Tops/s
     achieved = walk_steps * OPS_PER_STEP / (wos / 1e3) / 1e12
-    # setup 3, walks + estimates 2, group matrices 1, data at the double-layer
-    # rules 1, right sides 1, group factors + solves 2, gather 4, potential 1
-    kernels_per_step = 3 + 2 + 3 + 2 + 4 + 1
+    # setup 3, walks + estimates 2; mixed: group matrices 1, right-side weights 3
+    # (far, near, walk term), samples 1, products 1, group factors + solves 2;
+    # FP64: matrices and right sides 1, factor + solve 1; gather 4, potential 1
+    kernels_per_step = 3 + 2 + (1 + 3 + 1 + 1 + 2 if prec == dtn.PREC_MIXED else 1 + 1) + 4 + 1
     line = {
         "metric": METRIC, "value": value, "unit": "patches/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -321,6 +374,8 @@ def run_ours(args):
         "walk_tuning": tuning,
         "clocks": clk,
     }
+    if not args.no_serve:
+        line["serving"] = run_serving(dtn)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(wl)
     if rank == 0:
@@ -337,6 +392,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--walk-params", default="", help="chunk,blocks_per_sm,refill (skips the autotuner)")
     ap.add_argument("--patches", type=int, default=2000, help="profiler captures only")
     ap.add_argument("--walks", type=int, default=4096, help="profiler captures only")
     args = ap.parse_args()

@@ -161,7 +161,7 @@ double score_bound(const dtn_geometry_desc &gd, const dtn_dirichlet_desc &dd) {
     return std::fabs(dd.constant);
 }
 
-dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
+dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap) {
     const int64_t n = b->n_patches;
     L.n_patches = n;
     L.gamma_off.assign(n + 1, 0);
@@ -173,6 +173,9 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
     L.rep.clear();
     L.max_panels = 0; L.max_nodes = 0; L.max_walks = 0;
     std::map<std::tuple<uint64_t, int32_t, int32_t>, int64_t> groups;
+    std::map<std::tuple<uint64_t, int32_t, int32_t, int32_t, int32_t>, int64_t> wgroups;
+    L.wgroup_of.assign(n, 0);
+    L.wrep.clear();
     for (int64_t p = 0; p < n; ++p) {
         const int32_t nt = b->n_theta[p], nph = b->n_phi[p], nr = b->n_rings[p], ns = b->n_sectors[p];
         if (nt < 1 || nt > kMaxGauss || nph < 1 || nph > kMaxGauss || nr < 1 || ns < 1 || (int64_t)nr * ns > 1024)
@@ -193,6 +196,13 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
             L.rep.push_back(p);
         }
         L.group_of[p] = it->second;
+        auto wkey = std::make_tuple(abits, nr, ns, nt, nph);
+        auto wit = wgroups.find(wkey);
+        if (wit == wgroups.end()) {
+            wit = wgroups.emplace(wkey, (int64_t)L.wrep.size()).first;
+            L.wrep.push_back(p);
+        }
+        L.wgroup_of[p] = wit->second;
         L.walks[p] = b->walks_per_point ? b->walks_per_point[p] : 0;
         L.pid[p] = b->patch_ids ? b->patch_ids[p] : (uint32_t)(b->patch_id_base + (uint32_t)p);
         L.gamma_off[p + 1] = L.gamma_off[p] + P;
@@ -218,6 +228,40 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L) {
     L.grows_total = L.grows_off[L.n_groups];
     L.gmat_total = L.gmat_off[L.n_groups];
     L.gfac_total = L.gfac_off[L.n_groups];
+    // right-side weights (per weight group) and sample vectors (per patch)
+    const int64_t nw = (int64_t)L.wrep.size();
+    L.n_wgroups = nw;
+    L.wrows_off.assign(nw + 1, 0);
+    L.kcols.assign(nw, 0);
+    L.gw_off.assign(nw + 1, 0);
+    L.mem_off.assign(nw + 1, 0);
+    L.tile_off.assign(nw + 1, 0);
+    L.max_wgroup_rows = 0;
+    for (int64_t k = 0; k < nw; ++k) {
+        const int64_t r = L.wrep[k];
+        const int64_t np = (int64_t)L.nr[r] * L.ns[r];
+        L.wrows_off[k + 1] = L.wrows_off[k] + np;
+        L.kcols[k] = (cap ? (int64_t)kSamplesPerPanel * np : 0) + (int64_t)L.nt[r] * L.nph[r];
+        L.gw_off[k + 1] = L.gw_off[k] + np * L.kcols[k];
+        L.max_wgroup_rows = std::max<int32_t>(L.max_wgroup_rows, (int32_t)np);
+    }
+    L.wrows_total = L.wrows_off[nw];
+    L.gw_total = L.gw_off[nw];
+    L.vec_off.assign(n + 1, 0);
+    std::vector<int64_t> count(nw, 0);
+    for (int64_t p = 0; p < n; ++p) {
+        L.vec_off[p + 1] = L.vec_off[p] + L.kcols[L.wgroup_of[p]];
+        ++count[L.wgroup_of[p]];
+    }
+    L.vec_total = L.vec_off[n];
+    for (int64_t k = 0; k < nw; ++k) {
+        L.mem_off[k + 1] = L.mem_off[k] + count[k];
+        L.tile_off[k + 1] = L.tile_off[k] + (count[k] + kRhsTileN - 1) / kRhsTileN;
+    }
+    L.tiles_total = L.tile_off[nw];
+    L.members.assign(n, 0);
+    std::vector<int64_t> fill(L.mem_off.begin(), L.mem_off.end() - 1);
+    for (int64_t p = 0; p < n; ++p) L.members[fill[L.wgroup_of[p]]++] = p;
     return DTN_OK;
 }
 
@@ -256,6 +300,15 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     const size_t o_grow = off; off = al(off + (ng + 1) * 8);
     const size_t o_gmat = off; off = al(off + (ng + 1) * 8);
     const size_t o_gfac = off; off = al(off + (ng + 1) * 8);
+    const int64_t nw = L.n_wgroups;
+    const size_t o_wrep = off; off = al(off + nw * 8);
+    const size_t o_wrow = off; off = al(off + (nw + 1) * 8);
+    const size_t o_kc = off; off = al(off + nw * 8);
+    const size_t o_gwo = off; off = al(off + (nw + 1) * 8);
+    const size_t o_vec = off; off = al(off + (n + 1) * 8);
+    const size_t o_mem = off; off = al(off + n * 8);
+    const size_t o_mof = off; off = al(off + (nw + 1) * 8);
+    const size_t o_tof = off; off = al(off + (nw + 1) * 8);
     const size_t host_bytes = off;
     const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
     cudaError_t e = g->ws.layout.reserve(off);
@@ -278,6 +331,14 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     std::memcpy(&h[o_grow], L.grows_off.data(), (ng + 1) * 8);
     std::memcpy(&h[o_gmat], L.gmat_off.data(), (ng + 1) * 8);
     std::memcpy(&h[o_gfac], L.gfac_off.data(), (ng + 1) * 8);
+    std::memcpy(&h[o_wrep], L.wrep.data(), nw * 8);
+    std::memcpy(&h[o_wrow], L.wrows_off.data(), (nw + 1) * 8);
+    std::memcpy(&h[o_kc], L.kcols.data(), nw * 8);
+    std::memcpy(&h[o_gwo], L.gw_off.data(), (nw + 1) * 8);
+    std::memcpy(&h[o_vec], L.vec_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_mem], L.members.data(), n * 8);
+    std::memcpy(&h[o_mof], L.mem_off.data(), (nw + 1) * 8);
+    std::memcpy(&h[o_tof], L.tile_off.data(), (nw + 1) * 8);
     char *base = g->ws.layout.as<char>();
     e = cudaMemcpyAsync(base, h.data(), host_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
@@ -298,6 +359,14 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     D.grows_off = (int64_t *)(base + o_grow);
     D.gmat_off = (int64_t *)(base + o_gmat);
     D.gfac_off = (int64_t *)(base + o_gfac);
+    D.wrep = (int64_t *)(base + o_wrep);
+    D.wrows_off = (int64_t *)(base + o_wrow);
+    D.kcols = (int64_t *)(base + o_kc);
+    D.gw_off = (int64_t *)(base + o_gwo);
+    D.vec_off = (int64_t *)(base + o_vec);
+    D.members = (int64_t *)(base + o_mem);
+    D.mem_off = (int64_t *)(base + o_mof);
+    D.tile_off = (int64_t *)(base + o_tof);
     D.frames = (PatchFrame *)(base + o_fr);
     return cudaSuccess;
 }
@@ -396,6 +465,12 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
         dg.hi[i] = d.hi[i];
     }
     dg.R = d.radius;
+    for (int i = 0; i < 3; ++i) {
+        dg.c_f[i] = (float)dg.c[i];
+        dg.lo_f[i] = (float)dg.lo[i];
+        dg.hi_f[i] = (float)dg.hi[i];
+    }
+    dg.R_f = (float)dg.R;
     dg.nb = nb;
     dg.gn[0] = dg.gn[1] = dg.gn[2] = 1;
     dg.cell = 1.0;
@@ -438,6 +513,7 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
     std::memset(&g->dd, 0, sizeof(g->dd));
     g->dd.kind = DTN_DATA_CONSTANT;
     g->dd.inv_scale = 1.0;
+    g->dd.inv_scale_f = 1.0f;
     g->dd.sh = sh_tables_dev();
     *out = g;
     return DTN_OK;
@@ -447,10 +523,11 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
     if (!g) return DTN_E_INVALID_ARG;
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&g->d_boxes, &g->d_boxes_f, &g->d_cstart, &g->d_citems, &g->d_ccap, &g->d_clm, &g->d_clm_f,
+                      &g->d_clm_cart,
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
-                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gpre};
+                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec};
     for (DevBuf *b : bufs) b->release();
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
@@ -476,8 +553,17 @@ dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
             return to_status(e);
         if ((e = cudaMemcpy(g->d_clm_f.p, cf.data(), nc * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
             return to_status(e);
+        std::vector<float2> cart(kShPairs, make_float2(0.f, 0.f));
+        for (int l = 0; l <= d->lmax; ++l)
+            for (int m = 0; m <= l; ++m)
+                cart[sh_pair(l, m)] = make_float2((float)d->clm[l * l + l + m], m > 0 ? (float)d->clm[l * l + l - m] : 0.f);
+        if ((e = g->d_clm_cart.reserve(kShPairs * sizeof(float2))) != cudaSuccess) return to_status(e);
+        if ((e = cudaMemcpy(g->d_clm_cart.p, cart.data(), kShPairs * sizeof(float2), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return to_status(e);
         dd.clm = g->d_clm.as<double>();
         dd.clm_f = g->d_clm_f.as<float>();
+        dd.cart = g->d_clm_cart.as<float2>();
         dd.lmax = d->lmax;
     } else if (d->kind != DTN_DATA_POINT_SOURCE && d->kind != DTN_DATA_CONSTANT) {
         return DTN_E_INVALID_ARG;
@@ -490,6 +576,13 @@ dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
     dd.strength = d->strength;
     dd.inv_scale = d->kind == DTN_DATA_HARMONIC_SH ? 1.0 / d->scale : 1.0;
     dd.constant = d->constant;
+    for (int i = 0; i < 3; ++i) {
+        dd.x0_f[i] = (float)dd.x0[i];
+        dd.ctr_f[i] = (float)dd.ctr[i];
+    }
+    dd.q_f = (float)(dd.strength / (4.0 * kPi));
+    dd.inv_scale_f = (float)dd.inv_scale;
+    dd.constant_f = (float)dd.constant;
     dd.sh = sh_tables_dev();
     g->score_bound = std::max(score_bound(g->host.desc, *d), 1e-300);
     g->data_version += 1;
@@ -510,7 +603,7 @@ dtn_status dtn_query_patch_sizes(const dtn_patch_batch *b, int64_t *panels_total
     if (!b || b->n_patches < 0) return DTN_E_INVALID_ARG;
     if (b->n_patches > 0 && (!b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors)) return DTN_E_INVALID_ARG;
     BatchLayout L;
-    dtn_status st = build_layout(b, L);
+    dtn_status st = build_layout(b, L, false);
     if (st != DTN_OK) return st;
     if (panels_total) *panels_total = L.panels_total;
     if (gamma_total) *gamma_total = L.gamma_total;
@@ -535,7 +628,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     std::lock_guard<std::mutex> lk(g->mu);
     cudaStream_t s = (cudaStream_t)stream;
     BatchLayout L;
-    dtn_status st = build_layout(b, L);
+    dtn_status st = build_layout(b, L, g->dg.kind == kBall);
     if (st != DTN_OK) return st;
     const WalkParams wp = walk_params(g, o);
     const int32_t chunk = wp.chunk;
@@ -556,8 +649,8 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         if ((e = W.gmat.reserve((size_t)L.gmat_total * 8)) != cudaSuccess ||
             (e = W.gfac.reserve(lu_shared_scratch_bytes(L))) != cudaSuccess ||
             (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess ||
-            (g->dg.kind == kBall &&
-             (e = W.gpre.reserve((size_t)L.panels_total * kGprePerPanel * sizeof(float))) != cudaSuccess))
+            (e = W.gw.reserve((size_t)L.gw_total * sizeof(float))) != cudaSuccess ||
+            (e = W.vec.reserve((size_t)L.vec_total * sizeof(float))) != cudaSuccess)
             return to_status(e);
     } else if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) {
         return to_status(e);
@@ -594,7 +687,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                                 &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
-                                &W.gmat, &W.gfac, &W.gpiv, &W.gpre};
+                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
@@ -686,17 +779,18 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     const double *pl = W.panel_loc.as<double>(), *pp = W.panel_prm.as<double>(), *pa = W.panel_aux.as<double>();
     const bool shared = (o->prec == DTN_PREC_MIXED);
     if (shared) {
-        // one matrix per patch shape, FP64 rules; the right sides per patch
+        // one matrix and one set of right-side weights per patch shape, FP64
+        // rules; the right sides of all patches of a shape as one product
         double *gA = W.gmat.as<double>();
         e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                            gA, rhs, nullptr, s);
+                            gA, rhs, s);
         if (e == cudaSuccess)
-            e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                                gA, rhs, W.gpre.as<float>(), s);
+            e = launch_rhs_shared(g, L, D, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                                  W.gw.as<float>(), W.vec.as<float>(), rhs, s);
         if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
     } else {
         e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,
-                            rhs, nullptr, s);
+                            rhs, s);
     }
     if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
@@ -734,7 +828,7 @@ dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const d
     sb.n_patches = n;
     sb.walks_per_point = walks.data();
     BatchLayout L;
-    dtn_status st = build_layout(&sb, L);
+    dtn_status st = build_layout(&sb, L, g->dg.kind == kBall);
     if (st != DTN_OK) return st;
     DevLayout D;
     int64_t total_chunks = 0;

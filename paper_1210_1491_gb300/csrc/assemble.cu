@@ -1,5 +1,5 @@
 // assemble.cu -- collocation matrix and right side of the first-kind local BIE
-// (Eq. bw49-bw51) on piecewise-constant panels, one CTA per collocation row:
+// (Eq. bw49-bw51) on piecewise-constant panels:
 //
 //   A_ij = int_{panel j} G(x_i, y) ds_y                       (single layer, Eq. bw50)
 //   b_i  = int_S dG/dn_y(x_i, y) (g(y) - g(x_i)) ds_y
@@ -18,9 +18,20 @@
 //   other panels : tensor Gauss-Legendre whose order follows the ratio r of the
 //                  distance from the singular points (x_i and its Kelvin image)
 //                  to the panel centre over the panel radius; below r = 2 the
-//                  parameter box is split into four, recursively.  Mixed
-//                  precision evaluates panels with r >= 2 in FP32 and keeps the
-//                  split (near-singular) cases and the rim image term in FP64.
+//                  parameter box is split, recursively.
+//
+// FP64 mode assembles A and b per patch (one CTA per row).  Mixed precision
+// uses that A and b are linear in the patch data with coefficients that depend
+// only on the patch shape: per shape group one FP64 matrix A, and one weight
+// row per collocation point,
+//   b_i = sum_q w_iq (s_q - c) - (g(x_i) - c) sum_q w_iq,
+// whose samples s are the data at the 8 x 8 Gauss points of every panel (cap
+// patches) followed by the walk estimates U_k, c a per-patch constant.  The
+// double-layer weights are product rules, w_iq = int dG/dn_y(x_i, y) l_q(y) ds_y
+// with l_q the panel's tensor Lagrange basis on those points (the 8 x 8 rule
+// itself on far panels); the walk weights are -W_k P(x_i, y_k).  All right
+// sides of a group are then one FP32 product (FP64 sums across k-tiles), the
+// row sums of W taken in the same pass.
 #include <cmath>
 
 #include "dtn_internal.h"
@@ -33,9 +44,9 @@ constexpr int kAsmThreads = 128;
 constexpr int kMaxDepth = 10;
 constexpr int kStack = 40;
 constexpr int kMaxRule = 20;   // highest Gauss order the rules below use
-// fixed double-layer rules of the right side (mixed precision): per panel an
-// 8x8 Gauss rule (64 points) and the same rule on its four quarters (256)
-constexpr int kPreCoarse = 64, kPrePerPanel = 320, kPreN = 8;
+constexpr int kWtThreads = 128;
+constexpr double kFarRatio = 5.0;   // right-side weights: the plain 8 x 8 rule from here on
+constexpr int kSelfOrderW = 12;     // Duffy order of the self-panel product rules
 
 template <typename T>
 struct Ctx {
@@ -45,7 +56,6 @@ struct Ctx {
     T Xs[3];
     bool img;
     bool needD;
-    bool data32;   // evaluate g in FP32 for the (bounded) double-layer integrand
     bool needA;    // accumulate the single-layer entry
     T gx;
     T c[3], t1[3], t2[3], n[3];
@@ -62,8 +72,7 @@ __device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa
         const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
         const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
         const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
-        const T gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
-                              : dirichlet_eval<T>(*c.dat, yx, yy, yz);
+        const T gy = dirichlet_eval<T>(*c.dat, yx, yy, yz);
         sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
     }
 }
@@ -89,30 +98,11 @@ __device__ __forceinline__ void map_uv(const Region &R, T xi, T eta, T &u, T &v,
     }
 }
 
-template <typename T>
-__device__ void gauss_square(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, int n,
-                             const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
-    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
-    const T hx = (T)0.5 * (x1 - x0), mx = (T)0.5 * (x0 + x1);
-    const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
-    for (int i = 0; i < n; ++i) {
-        const T xi = mx + hx * (T)gx[i];
-        const T wi = (T)gw[i] * hx * he;
-        for (int j = 0; j < n; ++j) {
-            const T eta = me + he * (T)gx[j];
-            T u, v, jac;
-            map_uv<T>(R, xi, eta, u, v, jac);
-            eval_point<T>(c, u, v, wi * (T)gw[j] * jac, sa, sd);
-        }
-    }
-}
-
-// The same rule on a rectangle of the parameter box.  The map is separable, so
-// the sines and cosines of u and of v are taken once per Gauss line.
+// Tensor Gauss rule of order n on a rectangle of the parameter box.  The map is
+// separable, so the sines and cosines of u and of v are taken once per Gauss line.
 template <typename T>
 __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, int n,
-                           const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd,
-                           const float *__restrict__ gpre = nullptr) {
+                           const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
     const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
     const T hx = (T)0.5 * (x1 - x0), mx = (T)0.5 * (x0 + x1);
     const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
@@ -141,39 +131,24 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
             if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
             if (c.needD) {
                 const T nl[3] = {nu * cvs[j], nu * svs[j], nz};
-                T gy;
-                if (gpre) {
-                    gy = (T)gpre[i * n + j];   // data precomputed at this rule's points
-                } else {
-                    const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
-                    const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
-                    const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
-                    gy = c.data32 ? (T)dirichlet_eval<float>(*c.dat, (float)yx, (float)yy, (float)yz)
-                                  : dirichlet_eval<T>(*c.dat, yx, yy, yz);
-                }
+                const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+                const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+                const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+                const T gy = dirichlet_eval<T>(*c.dat, yx, yy, yz);
                 sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
             }
         }
     }
 }
 
-// Gauss order from the distance ratio r (0: split further).  FP64 orders aim at
-// 1e-15 relative for a singularity next to the middle of a panel edge, FP32
-// orders at 1e-8.
+// Gauss order from the distance ratio r (0: split further), aiming at 1e-15
+// relative for a singularity next to the middle of a panel edge.
 __device__ __forceinline__ int order64(double r) {
     if (r >= 20.0) return 5;
     if (r >= 10.0) return 6;
     if (r >= 5.0) return 9;
     if (r >= 3.0) return 12;
     if (r >= 2.0) return 20;
-    return 0;
-}
-__device__ __forceinline__ int order32(double r) {
-    if (r >= 20.0) return 3;
-    if (r >= 10.0) return 4;
-    if (r >= 5.0) return 5;
-    if (r >= 3.0) return 7;
-    if (r >= 2.0) return 11;
     return 0;
 }
 
@@ -228,9 +203,12 @@ __device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T 
     return rad > (T)0 ? dmin / rad : (T)INFINITY;
 }
 
-template <typename T>
-__device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, int min_order,
-                                 const double *__restrict__ glx, const double *__restrict__ glw, T &sa, T &sd) {
+// Adaptive cover of a region's unit parameter square: sub-squares whose ratio
+// asks for more than the highest order are split (the long direction only
+// while the square is more than 2:1); fn(x0, x1, e0, e1, n) integrates each
+// accepted sub-square with Gauss order n.
+template <typename T, typename Fn>
+__device__ void adaptive_squares(const Ctx<T> &c, const Region &R, bool withX, int min_order, Fn &&fn) {
     struct Sq { T x0, x1, e0, e1; int depth; };
     Sq stack[kStack];
     int sp = 0;
@@ -239,7 +217,7 @@ __device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, i
         const Sq q = stack[--sp];
         T lx, le;
         const T r = square_ratio<T>(c, R, q.x0, q.x1, q.e0, q.e1, withX, lx, le);
-        int n = sizeof(T) == 8 ? order64((double)r) : order32((double)r);
+        int n = order64((double)r);
         if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
             // split the long direction only while the square is more than 2:1
             const T xm = (T)0.5 * (q.x0 + q.x1), em = (T)0.5 * (q.e0 + q.e1);
@@ -257,10 +235,9 @@ __device__ void integrate_region(const Ctx<T> &c, const Region &R, bool withX, i
             }
             continue;
         }
-        if (n == 0) n = sizeof(T) == 8 ? 20 : 11;
+        if (n == 0) n = kMaxRule;
         if (n < min_order) n = min_order;
-        if (R.tri) gauss_square<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
-        else gauss_rect<T>(c, R, q.x0, q.x1, q.e0, q.e1, n, glx, glw, sa, sd);
+        fn(q.x0, q.x1, q.e0, q.e1, n);
     }
 }
 
@@ -279,7 +256,6 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
     if (c.img)
         for (int d = 0; d < 3; ++d) c.Xs[d] = (T)(f.a * f.a * X[d] / xx);
     c.needD = (f.kind == kCap);
-    c.data32 = false;
     c.needA = true;
     c.gx = (T)gx;
     c.dat = dat;
@@ -298,16 +274,15 @@ struct AsmDev {
     int prec;
     int mode;
     const double *glx, *glw;
-    const float *gpre;    // mode 2: data at the fixed per-panel rules
 };
 
 // self panel: triangles from the collocation point (uc, vc) to each side, each
 // side cut into m pieces so that every Duffy triangle's far edge is no longer
 // than its height (the angular factor of the transformed integrand then stays
 // smooth for thin panels)
-template <typename T>
-__device__ void self_panel(const Ctx<T> &c, const PatchFrame &f, const double *prm, int min_order,
-                           const double *glx, const double *glw, T &sa, T &sd) {
+// (fn(R) integrates over one triangle R)
+template <typename Fn>
+__device__ void self_triangles(const PatchFrame &f, const double *prm, Fn &&fn) {
     const double S[2] = {prm[4], prm[5]};
     const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
     const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
@@ -334,8 +309,25 @@ __device__ void self_panel(const Ctx<T> &c, const PatchFrame &f, const double *p
             R.p[4] = ub - ua; R.p[5] = vb - va;
             R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
             if (R.det == 0.0) continue;
-            integrate_region<T>(c, R, false, min_order, glx, glw, sa, sd);
+            fn(R);
         }
+    }
+}
+
+
+// The Gauss rule of order nq on one sub-square of a region, its points dealt
+// to the lanes of a warp in turn (each lane sums its own points).
+__device__ __forceinline__ void coop_gauss(const Ctx<double> &c, const Region &R, double x0, double x1, double e0,
+                                           double e1, int nq, const double *__restrict__ glx,
+                                           const double *__restrict__ glw, int lane, double &sa, double &sd) {
+    const double *gx = glx + nq * (nq - 1) / 2, *gw = glw + nq * (nq - 1) / 2;
+    const double hx = 0.5 * (x1 - x0), mx = 0.5 * (x0 + x1);
+    const double he = 0.5 * (e1 - e0), me = 0.5 * (e0 + e1);
+    for (int q = lane; q < nq * nq; q += 32) {
+        const int qi = q / nq, qj = q - qi * nq;
+        double u, v, jac;
+        map_uv<double>(R, mx + hx * gx[qi], me + he * gx[qj], u, v, jac);
+        eval_point<double>(c, u, v, gw[qi] * gw[qj] * hx * he * jac, sa, sd);
     }
 }
 
@@ -381,69 +373,84 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const double gx = P.panel_g[row];
     Ctx<double> c64;
     make_ctx<double>(c64, f, X, gx, &P.dat);
-    c64.data32 = (P.prec == DTN_PREC_MIXED);
     if (P.mode == 1) c64.needD = false;
-    Ctx<float> c32;
-    make_ctx<float>(c32, f, X, gx, &P.dat);
-    c32.data32 = true;
-    if (P.mode == 2) c32.needA = false;
+    __shared__ int near_list[1024];
+    __shared__ int near_count;
+    __shared__ double self_part[2][kAsmThreads / 32];
+    if (threadIdx.x == 0) near_count = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double dsum = 0.0;
-    const bool doD = (P.mode != 1) && (f.kind == kCap);
+    // far panels (r >= 2): one thread each, separable Gauss rule
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j == i) continue;
         const int64_t pj = poff + j;
-        const double *prm = P.panel_prm + 6 * pj;
-        if (P.mode == 2) {
-            // double layer only: the integrand (g(y) - g(x_i)) dG/dn_y is bounded,
-            // so fixed 8x8 rules with the data precomputed per patch (whole panel
-            // when the panel is far, its four quarters when near) and a Duffy rule
-            // on the self panel, all FP32
-            if (!doD) break;
-            float a32 = 0.f, d32 = 0.f;
-            if (j == i) {
-                self_panel<float>(c32, f, prm, 6, P.glx, P.glw, a32, d32);
-            } else {
-                const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
-                Region R;
-                R.tri = false;
-                R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
-                R.det = 0.0;
-                const float *gp = P.gpre + pj * kPrePerPanel;
-                if (r >= 2.0) {
-                    gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, kPreN, P.glx, P.glw, a32, d32, gp);
-                } else {
-                    for (int s = 0; s < 4; ++s) {
-                        const float x0 = 0.5f * (s & 1), e0 = 0.5f * (s >> 1);
-                        gauss_rect<float>(c32, R, x0, x0 + 0.5f, e0, e0 + 0.5f, kPreN, P.glx, P.glw, a32, d32,
-                                          gp + kPreCoarse + kPreCoarse * s);
-                    }
-                }
-            }
-            dsum += (double)d32;
+        const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
+        if (r < 2.0) {
+            near_list[atomicAdd(&near_count, 1)] = j;
             continue;
         }
+        const double *prm = P.panel_prm + 6 * pj;
+        Region R;
+        R.tri = false;
+        R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
+        R.det = 0.0;
         double sa = 0.0, sd = 0.0;
-        if (j == i) {
-            self_panel<double>(c64, f, prm, 16, P.glx, P.glw, sa, sd);
-        } else {
-            const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
-            Region R;
-            R.tri = false;
-            R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
-            R.det = 0.0;
-            if (r >= 2.0) {
-                if (P.mode == 0 && P.prec == DTN_PREC_MIXED) {
-                    float a32 = 0.f, d32 = 0.f;
-                    gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order32(r), P.glx, P.glw, a32, d32);
-                    sa = a32; sd = d32;
-                } else {
-                    gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
-                }
-            } else {
-                integrate_region<double>(c64, R, true, 0, P.glx, P.glw, sa, sd);
-            }
-        }
+        gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
         Arow[j] = sa;
         dsum += sd;
+    }
+    // self panel: its Duffy triangles dealt to the warps in turn, the points of
+    // each accepted sub-square to the lanes; sums in a fixed order
+    {
+        double sa = 0.0, sd = 0.0;
+        int tri = 0;
+        self_triangles(f, P.panel_prm + 6 * row, [&](const Region &R) {
+            if ((tri++ % (kAsmThreads / 32)) != warp) return;
+            adaptive_squares<double>(c64, R, false, 16, [&](double x0, double x1, double e0, double e1, int nq) {
+                coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
+            });
+        });
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        }
+        if (lane == 0) {
+            self_part[0][warp] = sa;
+            self_part[1][warp] = sd;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sd = 0.0;
+        for (int w = 0; w < kAsmThreads / 32; ++w) {
+            sa += self_part[0][w];
+            sd += self_part[1][w];
+        }
+        Arow[i] = sa;
+        dsum += sd;
+    }
+    // near panels (r < 2): one warp each, adaptive cover, points over the lanes
+    const int nn = near_count;
+    for (int k = warp; k < nn; k += kAsmThreads / 32) {
+        const int j = near_list[k];
+        const double *prm = P.panel_prm + 6 * (poff + j);
+        Region R;
+        R.tri = false;
+        R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
+        R.det = 0.0;
+        double sa = 0.0, sd = 0.0;
+        adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
+            coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
+        });
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        }
+        if (lane == 0) {
+            Arow[j] = sa;
+            dsum += sd;
+        }
     }
     if (P.mode == 1) return;
     // Gamma term: sum_k W_k P(x_i, y_k) (U_k - g(x_i)), FP64
@@ -470,39 +477,353 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     }
 }
 
-// Data g at the fixed per-panel rules of the double-layer term (cap patches):
-// points 0..63 the 8x8 Gauss rule on the panel, points 64..319 the same rule on
-// each quarter of the panel (quarter s = 2 e + x of the parameter box).  One
-// thread per point; the row kernels read these values instead of evaluating
-// the harmonic data again for every collocation row.
-__global__ void panel_gpre_kernel(DData dat, int64_t n_patches, int64_t total, const int64_t *__restrict__ panel_off,
-                                  const PatchFrame *__restrict__ frames, const double *__restrict__ panel_prm,
-                                  const double *__restrict__ glx, float *__restrict__ out) {
+// ---------------------------------------------------------------------------
+// Mixed precision right sides (one weight row per collocation point of each
+// shape group, then one product per group).
+
+// Lagrange basis on the 8 Gauss-Legendre points of the unit interval
+struct Basis8 {
+    double s[kSampleN], w[kSampleN], inv[kSampleN];
+};
+
+__device__ __forceinline__ void basis_all(const Basis8 &B, double t, double *l) {
+    double pre[kSampleN], acc = 1.0;
+#pragma unroll
+    for (int m = 0; m < kSampleN; ++m) {
+        pre[m] = acc;
+        acc *= (t - B.s[m]);
+    }
+    double suf = 1.0;
+#pragma unroll
+    for (int m = kSampleN - 1; m >= 0; --m) {
+        l[m] = pre[m] * suf * B.inv[m];
+        suf *= (t - B.s[m]);
+    }
+}
+
+struct WtDev {
+    const PatchFrame *frames;
+    const int64_t *panel_off, *gamma_off, *wrows_off, *wrep, *kcols, *gw_off;
+    int64_t n_wgroups;
+    const double *panel_loc, *panel_prm, *panel_aux, *gamma_loc, *gamma_w;
+    float *gw;
+    const double *glx, *glw;
+};
+
+// Row `grow` of the weight groups: its group, local row, representative patch
+// and weight row.
+struct WtRow {
+    int64_t grp, p, poff;
+    int i, n, m;
+    int64_t dcols, kc;
+    float *W;
+    double X[3];
+};
+
+__device__ __forceinline__ WtRow wt_row(const WtDev &P, int64_t grow) {
+    WtRow r;
+    r.grp = find_group(P.wrows_off, P.n_wgroups, grow);
+    r.i = (int)(grow - P.wrows_off[r.grp]);
+    r.p = P.wrep[r.grp];
+    r.n = (int)(P.wrows_off[r.grp + 1] - P.wrows_off[r.grp]);
+    r.kc = P.kcols[r.grp];
+    const int64_t goff = P.gamma_off[r.p];
+    r.m = (int)(P.gamma_off[r.p + 1] - goff);
+    r.dcols = r.kc - r.m;
+    r.W = P.gw + P.gw_off[r.grp] + (int64_t)r.i * r.kc;
+    r.poff = P.panel_off[r.p];
+    const int64_t row = r.poff + r.i;
+    for (int d = 0; d < 3; ++d) r.X[d] = P.panel_loc[3 * row + d];
+    return r;
+}
+
+__device__ __forceinline__ void basis8_init(Basis8 &B, const double *glx, const double *glw) {
+    const double *gx = glx + kSampleN * (kSampleN - 1) / 2, *gw = glw + kSampleN * (kSampleN - 1) / 2;
+    for (int a = 0; a < kSampleN; ++a) {
+        B.s[a] = 0.5 * (1.0 + gx[a]);
+        B.w[a] = 0.5 * gw[a];
+    }
+    for (int a = 0; a < kSampleN; ++a) {
+        double d = 1.0;
+        for (int q = 0; q < kSampleN; ++q)
+            if (q != a) d *= (B.s[a] - B.s[q]);
+        B.inv[a] = 1.0 / d;
+    }
+}
+
+// Double-layer weights of the far panels (r >= 5, not the row's own), one
+// thread per (row, panel, a): the 8 x 8 rule itself (the interpolatory rule on
+// its own points), so w_(a,b) = w_a w_b |box| J dG/dn_y at point (a, b).
+// Grid (rows, task blocks).  FP64, stored FP32.
+__global__ void __launch_bounds__(kWtThreads) rhs_far_weights_kernel(WtDev P) {
+    const WtRow r = wt_row(P, blockIdx.x);
+    const int t = blockIdx.y * blockDim.x + threadIdx.x;
+    __shared__ Basis8 B;
+    if (threadIdx.x == 0) basis8_init(B, P.glx, P.glw);
+    __syncthreads();
+    if (r.dcols == 0 || t >= r.n * kSampleN) return;
+    const int j = t / kSampleN, a = t - j * kSampleN;
+    if (j == r.i) return;
+    const PatchFrame f = P.frames[r.p];
+    Ctx<double> c;
+    make_ctx<double>(c, f, r.X, 0.0, nullptr);
+    const int64_t pj = r.poff + j;
+    if (panel_ratio(c, r.X, P.panel_aux + 4 * pj) < kFarRatio) return;   // near: rhs_near_weights_kernel
+    const double *prm = P.panel_prm + 6 * pj;
+    const double u0 = prm[0], du = prm[1] - prm[0], v0 = prm[2], dv = prm[3] - prm[2];
+    const double ua = u0 + B.s[a] * du;
+    float *dst = r.W + (int64_t)j * kSamplesPerPanel + a * kSampleN;
+#pragma unroll
+    for (int b = 0; b < kSampleN; ++b) {
+        double Y[3], nl[3], J;
+        patch_point<double>(f.kind, f.R, ua, v0 + B.s[b] * dv, Y, nl, J);
+        dst[b] = (float)(B.w[a] * B.w[b] * du * dv * J * green_ball_dny<double>(c.a, c.X, c.xn, Y, nl));
+    }
+}
+
+constexpr int kNearWarps = 8;
+
+// Warp-cooperative product rule over one accepted sub-square: the lanes take
+// its points in turn; each point's k = weight * J * dG/dn_y times the 8 basis
+// values in u, and the 8 basis values in v, go through shared memory, and lane
+// l accumulates the weights (a, b) = (l / 4, 2 (l % 4) + {0, 1}).  Every point
+// is evaluated once for all 64 weights; the summation order is fixed.
+struct ProdBuf {
+    double ku[32][kSampleN], lv[32][kSampleN];
+};
+
+__device__ __forceinline__ void coop_square(const Ctx<double> &c, const PatchFrame &f, const Basis8 &B,
+                                            const Region &R, double u0, double du, double v0, double dv,
+                                            double x0, double x1, double e0, double e1, int nq, const double *glx,
+                                            const double *glw, ProdBuf &pb, int lane, double &acc0, double &acc1) {
+    const double *gx = glx + nq * (nq - 1) / 2, *gw = glw + nq * (nq - 1) / 2;
+    const double hx = 0.5 * (x1 - x0), mx = 0.5 * (x0 + x1);
+    const double he = 0.5 * (e1 - e0), me = 0.5 * (e0 + e1);
+    const int npts = nq * nq;
+    const int a = lane >> 2, b0 = (lane & 3) * 2;
+    for (int base = 0; base < npts; base += 32) {
+        const int q = base + lane;
+        if (q < npts) {
+            const int qi = q / nq, qj = q - qi * nq;
+            double u, v, jac, Y[3], nl[3], J;
+            map_uv<double>(R, mx + hx * gx[qi], me + he * gx[qj], u, v, jac);
+            patch_point<double>(f.kind, f.R, u, v, Y, nl, J);
+            const double k = gw[qi] * gw[qj] * hx * he * jac * J * green_ball_dny<double>(c.a, c.X, c.xn, Y, nl);
+            double lu[kSampleN];
+            basis_all(B, (u - u0) / du, lu);
+            basis_all(B, (v - v0) / dv, pb.lv[lane]);
+#pragma unroll
+            for (int m = 0; m < kSampleN; ++m) pb.ku[lane][m] = k * lu[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < kSampleN; ++m) {
+                pb.ku[lane][m] = 0.0;
+                pb.lv[lane][m] = 0.0;
+            }
+        }
+        __syncwarp();
+        const int cnt = min(32, npts - base);
+        for (int s = 0; s < cnt; ++s) {
+            const double ka = pb.ku[s][a];
+            acc0 = fma(ka, pb.lv[s][b0], acc0);
+            acc1 = fma(ka, pb.lv[s][b0 + 1], acc1);
+        }
+        __syncwarp();
+    }
+}
+
+// Double-layer weights of the row's own panel and of its near panels (r < 5),
+// one CTA of 8 warps per row.  Own panel: the Duffy triangles (adaptive cover,
+// order >= 12) are dealt to the warps in turn and the warps' sums added in warp
+// order; near panels: one warp per panel, adaptive cover with order >= 8.
+__global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev P) {
+    const WtRow r = wt_row(P, blockIdx.x);
+    __shared__ Basis8 B;
+    __shared__ ProdBuf pbuf[kNearWarps];
+    __shared__ double part[kNearWarps][kSamplesPerPanel];
+    __shared__ int near_list[1024];
+    __shared__ int near_count;
+    if (threadIdx.x == 0) {
+        basis8_init(B, P.glx, P.glw);
+        near_count = 0;
+    }
+    __syncthreads();
+    if (r.dcols == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const PatchFrame f = P.frames[r.p];
+    Ctx<double> c;
+    make_ctx<double>(c, f, r.X, 0.0, nullptr);
+    // near panels of this row
+    for (int j = threadIdx.x; j < r.n; j += blockDim.x)
+        if (j != r.i && panel_ratio(c, r.X, P.panel_aux + 4 * (r.poff + j)) < kFarRatio)
+            near_list[atomicAdd(&near_count, 1)] = j;
+    // own panel
+    {
+        const double *prm = P.panel_prm + 6 * (r.poff + r.i);
+        const double u0 = prm[0], du = prm[1] - prm[0], v0 = prm[2], dv = prm[3] - prm[2];
+        double acc0 = 0.0, acc1 = 0.0;
+        int tri = 0;
+        self_triangles(f, prm, [&](const Region &R) {
+            if ((tri++ % kNearWarps) != warp) return;
+            adaptive_squares<double>(c, R, false, kSelfOrderW, [&](double x0, double x1, double e0, double e1, int nq) {
+                coop_square(c, f, B, R, u0, du, v0, dv, x0, x1, e0, e1, nq, P.glx, P.glw, pbuf[warp], lane, acc0,
+                            acc1);
+            });
+        });
+        const int o = (lane >> 2) * kSampleN + (lane & 3) * 2;
+        part[warp][o] = acc0;
+        part[warp][o + 1] = acc1;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSamplesPerPanel) {
+        double t = 0.0;
+        for (int w = 0; w < kNearWarps; ++w) t += part[w][threadIdx.x];
+        r.W[(int64_t)r.i * kSamplesPerPanel + threadIdx.x] = (float)t;
+    }
+    // near panels, one warp each
+    const int nn = near_count;
+    for (int k = warp; k < nn; k += kNearWarps) {
+        const int j = near_list[k];
+        const double *prm = P.panel_prm + 6 * (r.poff + j);
+        const double u0 = prm[0], du = prm[1] - prm[0], v0 = prm[2], dv = prm[3] - prm[2];
+        Region R;
+        R.tri = false;
+        R.p[0] = u0; R.p[1] = du; R.p[2] = v0; R.p[3] = dv;
+        R.det = 0.0;
+        double acc0 = 0.0, acc1 = 0.0;
+        adaptive_squares<double>(c, R, true, kSampleN, [&](double x0, double x1, double e0, double e1, int nq) {
+            coop_square(c, f, B, R, u0, du, v0, dv, x0, x1, e0, e1, nq, P.glx, P.glw, pbuf[warp], lane, acc0, acc1);
+        });
+        float *dst = r.W + (int64_t)j * kSamplesPerPanel + (lane >> 2) * kSampleN + (lane & 3) * 2;
+        dst[0] = (float)acc0;
+        dst[1] = (float)acc1;
+    }
+}
+
+// Walk-term weights -W_k P(x_i, y_k): grid (rows, node blocks).
+__global__ void __launch_bounds__(kWtThreads) rhs_walk_weights_kernel(WtDev P) {
+    const WtRow r = wt_row(P, blockIdx.x);
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= r.m) return;
+    const double a = P.frames[r.p].a;
+    const int64_t gk = P.gamma_off[r.p] + k;
+    const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
+    r.W[r.dcols + k] = (float)(-P.gamma_w[gk] * poisson_ball<double>(a, r.X, Y));
+}
+
+// Per-patch sample vectors: the data at the 8 x 8 Gauss points of every panel
+// (FP32 evaluation) and the walk estimates, each minus c = g at the first
+// collocation point, stored FP32.  One thread per sample.
+__global__ void rhs_samples_kernel(DData dat, int64_t n_patches, int64_t total, const int64_t *__restrict__ vec_off,
+                                   const int64_t *__restrict__ panel_off, const int64_t *__restrict__ gamma_off,
+                                   const PatchFrame *__restrict__ frames, const double *__restrict__ panel_prm,
+                                   const double *__restrict__ panel_g, const double *__restrict__ U,
+                                   const double *__restrict__ glx, float *__restrict__ vec) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int64_t pj = idx / kPrePerPanel;
-    const int q = (int)(idx - pj * kPrePerPanel);
-    const int64_t p = find_group(panel_off, n_patches, pj);
-    const PatchFrame &f = frames[p];
-    const double *prm = panel_prm + 6 * pj;
-    double x0 = 0.0, x1 = 1.0, e0 = 0.0, e1 = 1.0;
-    int k = q;
-    if (q >= kPreCoarse) {
-        const int s = (q - kPreCoarse) / kPreCoarse;
-        k = (q - kPreCoarse) % kPreCoarse;
-        x0 = 0.5 * (s & 1); x1 = x0 + 0.5;
-        e0 = 0.5 * (s >> 1); e1 = e0 + 0.5;
+    const int64_t p = find_group(vec_off, n_patches, idx);
+    const int64_t q = idx - vec_off[p];
+    const int64_t m = gamma_off[p + 1] - gamma_off[p];
+    const int64_t dcols = vec_off[p + 1] - vec_off[p] - m;
+    const double c0 = panel_g[panel_off[p]];
+    double val;
+    if (q < dcols) {
+        const int64_t j = q / kSamplesPerPanel;
+        const int a = (int)(q - j * kSamplesPerPanel) / kSampleN, b = (int)(q % kSampleN);
+        const double *gx = glx + kSampleN * (kSampleN - 1) / 2;
+        const double *prm = panel_prm + 6 * (panel_off[p] + j);
+        const double u = prm[0] + 0.5 * (1.0 + gx[a]) * (prm[1] - prm[0]);
+        const double v = prm[2] + 0.5 * (1.0 + gx[b]) * (prm[3] - prm[2]);
+        const PatchFrame &f = frames[p];
+        double Y[3], nl[3], J;
+        patch_point<double>(f.kind, f.R, u, v, Y, nl, J);
+        const double y0 = f.c[0] + Y[0] * f.t1[0] + Y[1] * f.t2[0] + Y[2] * f.n[0];
+        const double y1 = f.c[1] + Y[0] * f.t1[1] + Y[1] * f.t2[1] + Y[2] * f.n[1];
+        const double y2 = f.c[2] + Y[0] * f.t1[2] + Y[1] * f.t2[2] + Y[2] * f.n[2];
+        val = (double)dirichlet_eval<float>(dat, (float)y0, (float)y1, (float)y2) - c0;
+    } else {
+        val = U[gamma_off[p] + (q - dcols)] - c0;
     }
-    const int i = k / kPreN, j = k % kPreN;
-    const double *gx = glx + kPreN * (kPreN - 1) / 2;
-    const double u = prm[0] + (0.5 * (x0 + x1) + 0.5 * (x1 - x0) * gx[i]) * (prm[1] - prm[0]);
-    const double v = prm[2] + (0.5 * (e0 + e1) + 0.5 * (e1 - e0) * gx[j]) * (prm[3] - prm[2]);
-    double Y[3], nl[3], J;
-    patch_point<double>(f.kind, f.R, u, v, Y, nl, J);
-    const double y0 = f.c[0] + Y[0] * f.t1[0] + Y[1] * f.t2[0] + Y[2] * f.n[0];
-    const double y1 = f.c[1] + Y[0] * f.t1[1] + Y[1] * f.t2[1] + Y[2] * f.n[1];
-    const double y2 = f.c[2] + Y[0] * f.t1[2] + Y[1] * f.t2[2] + Y[2] * f.n[2];
-    out[idx] = dirichlet_eval<float>(dat, (float)y0, (float)y1, (float)y2);
+    vec[idx] = (float)val;
+}
+
+constexpr int kGemmM = 32, kGemmK = 32, kGemmThreads = 256;
+
+struct RhsDev {
+    const PatchFrame *frames;
+    const int64_t *panel_off, *wrows_off, *kcols, *gw_off, *vec_off, *members, *mem_off, *tile_off;
+    int64_t n_wgroups;
+    int row_tiles;
+    const float *gw, *vec;
+    const double *panel_g;
+    double *b;
+};
+
+// b = W s - (g(x_i) - c) rowsum(W) for a tile of 32 rows x 32 patches of one
+// weight group.  FP32 products summed over each k-tile of 32, the tile sums added in
+// FP64; every b entry sums in the same order whatever the batch holds.
+__global__ void __launch_bounds__(kGemmThreads) rhs_product_kernel(RhsDev P) {
+    const int64_t tile = blockIdx.x / P.row_tiles;
+    const int rt = (int)(blockIdx.x - tile * P.row_tiles);
+    const int64_t grp = find_group(P.tile_off, P.n_wgroups, tile);
+    const int n = (int)(P.wrows_off[grp + 1] - P.wrows_off[grp]);
+    const int row0 = rt * kGemmM;
+    if (row0 >= n) return;
+    const int64_t kc = P.kcols[grp];
+    const float *W = P.gw + P.gw_off[grp];
+    const int64_t m0 = P.mem_off[grp] + (tile - P.tile_off[grp]) * kRhsTileN;
+    const int mcount = (int)min((int64_t)kRhsTileN, P.mem_off[grp + 1] - m0);
+    __shared__ float Ws[kGemmK][kGemmM + 1];
+    __shared__ float Vs[kGemmK][kRhsTileN + 1];
+    __shared__ int64_t vbase[kRhsTileN];
+    if (threadIdx.x < kRhsTileN)
+        vbase[threadIdx.x] = (int)threadIdx.x < mcount ? P.vec_off[P.members[m0 + threadIdx.x]] : -1;
+    __syncthreads();
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    double rsum[2] = {0.0, 0.0};   // row sums of W, in the same summation order
+    for (int64_t k0 = 0; k0 < kc; k0 += kGemmK) {
+#pragma unroll
+        for (int e = 0; e < (kGemmM * kGemmK) / kGemmThreads; ++e) {
+            const int idx = threadIdx.x + kGemmThreads * e;
+            const int r = idx >> 5, kk = idx & 31;
+            const int64_t k = k0 + kk;
+            Ws[kk][r] = (row0 + r < n && k < kc) ? W[(int64_t)(row0 + r) * kc + k] : 0.f;
+            Vs[kk][r] = (vbase[r] >= 0 && k < kc) ? P.vec[vbase[r] + k] : 0.f;
+        }
+        __syncthreads();
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f, r0 = 0.f, r1 = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < kGemmK; ++kk) {
+            const float a0 = Ws[kk][2 * ty], a1 = Ws[kk][2 * ty + 1];
+            const float b0 = Vs[kk][2 * tx], b1 = Vs[kk][2 * tx + 1];
+            s00 = fmaf(a0, b0, s00);
+            s01 = fmaf(a0, b1, s01);
+            s10 = fmaf(a1, b0, s10);
+            s11 = fmaf(a1, b1, s11);
+            r0 += a0;
+            r1 += a1;
+        }
+        acc[0][0] += (double)s00;
+        acc[0][1] += (double)s01;
+        acc[1][0] += (double)s10;
+        acc[1][1] += (double)s11;
+        rsum[0] += (double)r0;
+        rsum[1] += (double)r1;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int row = row0 + 2 * ty + rr, col = 2 * tx + cc;
+            if (row >= n || col >= mcount) continue;
+            const int64_t p = P.members[m0 + col];
+            const int64_t off = P.panel_off[p];
+            P.b[off + row] = (P.frames[p].status == DTN_OK)
+                                 ? acc[rr][cc] - (P.panel_g[off + row] - P.panel_g[off]) * rsum[rr]
+                                 : 0.0;
+        }
 }
 
 __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat_off,
@@ -521,7 +842,7 @@ __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
-                            const double *U, double *A, double *b, float *gpre, cudaStream_t s) {
+                            const double *U, double *A, double *b, cudaStream_t s) {
     const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
     if (rows == 0) return cudaSuccess;
     AsmDev P;
@@ -548,15 +869,60 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.mode = mode;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
-    P.gpre = gpre;
-    if (mode == 2 && g->dg.kind == kBall) {
-        // data at the fixed double-layer rules, once per patch
-        const int64_t total = L.panels_total * kPrePerPanel;
-        const int T = 256;
-        panel_gpre_kernel<<<(unsigned)((total + T - 1) / T), T, 0, s>>>(g->dd, L.n_patches, total, D.panel_off,
-                                                                        D.frames, panel_prm, P.glx, gpre);
-    }
     assemble_kernel<<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                              const double *panel_loc, const double *panel_prm, const double *panel_aux,
+                              const double *panel_g, const double *gamma_loc, const double *gamma_w,
+                              const double *U, float *gw, float *vec, double *b, cudaStream_t s) {
+    if (L.wrows_total == 0) return cudaSuccess;
+    WtDev Wd;
+    Wd.frames = D.frames;
+    Wd.panel_off = D.panel_off;
+    Wd.gamma_off = D.gamma_off;
+    Wd.wrows_off = D.wrows_off;
+    Wd.wrep = D.wrep;
+    Wd.kcols = D.kcols;
+    Wd.gw_off = D.gw_off;
+    Wd.n_wgroups = L.n_wgroups;
+    Wd.panel_loc = panel_loc;
+    Wd.panel_prm = panel_prm;
+    Wd.panel_aux = panel_aux;
+    Wd.gamma_loc = gamma_loc;
+    Wd.gamma_w = gamma_w;
+    Wd.gw = gw;
+    Wd.glx = gl_x_dev();
+    Wd.glw = gl_w_dev();
+    const unsigned rows = (unsigned)L.wrows_total;
+    if (g->dg.kind == kBall) {
+        const unsigned tb = (unsigned)((L.max_wgroup_rows * kSampleN + kWtThreads - 1) / kWtThreads);
+        rhs_far_weights_kernel<<<dim3(rows, tb), kWtThreads, 0, s>>>(Wd);
+        rhs_near_weights_kernel<<<rows, 32 * kNearWarps, 0, s>>>(Wd);
+    }
+    rhs_walk_weights_kernel<<<dim3(rows, (unsigned)((L.max_nodes + kWtThreads - 1) / kWtThreads)), kWtThreads, 0, s>>>(Wd);
+    const int T = 256;
+    rhs_samples_kernel<<<(unsigned)((L.vec_total + T - 1) / T), T, 0, s>>>(
+        g->dd, L.n_patches, L.vec_total, D.vec_off, D.panel_off, D.gamma_off, D.frames, panel_prm, panel_g, U,
+        Wd.glx, vec);
+    RhsDev R;
+    R.frames = D.frames;
+    R.panel_off = D.panel_off;
+    R.wrows_off = D.wrows_off;
+    R.kcols = D.kcols;
+    R.gw_off = D.gw_off;
+    R.vec_off = D.vec_off;
+    R.members = D.members;
+    R.mem_off = D.mem_off;
+    R.tile_off = D.tile_off;
+    R.n_wgroups = L.n_wgroups;
+    R.row_tiles = (L.max_wgroup_rows + kGemmM - 1) / kGemmM;
+    R.gw = gw;
+    R.vec = vec;
+    R.panel_g = panel_g;
+    R.b = b;
+    rhs_product_kernel<<<(unsigned)(L.tiles_total * R.row_tiles), kGemmThreads, 0, s>>>(R);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct DGeom {
     int kind;
     double c[3], R;          // ball
     double lo[3], hi[3];     // outer box
+    float c_f[3], R_f, lo_f[3], hi_f[3];   // the same, rounded to FP32 on the host
     int nb;                  // obstacle boxes
     const double *boxes;     // nb x 6
     const float *boxes_f;    // nb x 6
@@ -62,6 +63,12 @@ struct DGeom {
 
 template <typename T> struct Vec3 { T x, y, z; };
 
+// A parameter in the walk's precision: FP32 walks read the host-rounded copy
+// (a double-to-float conversion on the device would run on the FP64 pipe).
+template <typename T> __device__ __forceinline__ T pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
 // Distance from x to the boundary, the radius of the largest empty sphere
 // used by one walk step.  For the box-minus-boxes region the obstacle part
 // only looks at the boxes listed for x's grid cell and caps the result at the
@@ -70,12 +77,12 @@ template <typename T> struct Vec3 { T x, y, z; };
 // memory (kind 2, T = float) or nullptr.
 template <typename T>
 __device__ __forceinline__ T box_interior_dist(const DGeom &g, T x, T y, T z) {
-    T d = x - (T)g.lo[0];
-    d = fmin(d, (T)g.hi[0] - x);
-    d = fmin(d, y - (T)g.lo[1]);
-    d = fmin(d, (T)g.hi[1] - y);
-    d = fmin(d, z - (T)g.lo[2]);
-    d = fmin(d, (T)g.hi[2] - z);
+    T d = x - pick<T>(g.lo[0], g.lo_f[0]);
+    d = fmin(d, pick<T>(g.hi[0], g.hi_f[0]) - x);
+    d = fmin(d, y - pick<T>(g.lo[1], g.lo_f[1]));
+    d = fmin(d, pick<T>(g.hi[1], g.hi_f[1]) - y);
+    d = fmin(d, z - pick<T>(g.lo[2], g.lo_f[2]));
+    d = fmin(d, pick<T>(g.hi[2], g.hi_f[2]) - z);
     return d;
 }
 
@@ -104,11 +111,12 @@ __device__ __forceinline__ int grid_cell(const DGeom &g, T x, T y, T z) {
 template <typename T, int GK>
 __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z) {
     if (GK == kBall) {
-        const T dx = x - (T)g.c[0], dy = y - (T)g.c[1], dz = z - (T)g.c[2];
+        const T dx = x - pick<T>(g.c[0], g.c_f[0]), dy = y - pick<T>(g.c[1], g.c_f[1]),
+                dz = z - pick<T>(g.c[2], g.c_f[2]);
         if constexpr (sizeof(T) == 4) {
             // SFU reciprocal square root: |x| to a few FP32 ulps
             const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
-            return (float)g.R - r2 * rsqrtf(r2);
+            return g.R_f - r2 * rsqrtf(r2);
         } else {
             return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
         }
@@ -142,15 +150,25 @@ __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z
 template <typename T>
 __device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &ny, T &nz) {
     if (g.kind == kBall) {
-        const T dx = x - (T)g.c[0], dy = y - (T)g.c[1], dz = z - (T)g.c[2];
-        const T r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r > (T)0) {
-            const T s = (T)g.R / r;
-            nx = (T)g.c[0] + s * dx; ny = (T)g.c[1] + s * dy; nz = (T)g.c[2] + s * dz;
+        const T cx = pick<T>(g.c[0], g.c_f[0]), cy = pick<T>(g.c[1], g.c_f[1]), cz = pick<T>(g.c[2], g.c_f[2]);
+        const T R = pick<T>(g.R, g.R_f);
+        const T dx = x - cx, dy = y - cy, dz = z - cz;
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        T r, s;
+        if constexpr (sizeof(T) == 4) {
+            const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;   // SFU, a few ulps
+            r = r2 * ir;
+            s = R * ir;
         } else {
-            nx = (T)g.c[0]; ny = (T)g.c[1]; nz = (T)g.c[2] + (T)g.R;
+            r = sqrt(r2);
+            s = r > (T)0 ? R / r : (T)0;
         }
-        return (T)g.R - r;
+        if (r > (T)0) {
+            nx = cx + s * dx; ny = cy + s * dy; nz = cz + s * dz;
+        } else {
+            nx = cx; ny = cy; nz = cz + R;
+        }
+        return R - r;
     }
     const T xs[3] = {x, y, z};
     T best = (T)INFINITY;
@@ -158,11 +176,11 @@ __device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &n
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
         const int ax = f >> 1;
-        const T d = (f & 1) ? (T)g.hi[ax] - xs[ax] : xs[ax] - (T)g.lo[ax];
+        const T d = (f & 1) ? pick<T>(g.hi[ax], g.hi_f[ax]) - xs[ax] : xs[ax] - pick<T>(g.lo[ax], g.lo_f[ax]);
         if (d < best) { best = d; bf = f; }
     }
     T p[3] = {x, y, z};
-    p[bf >> 1] = (bf & 1) ? (T)g.hi[bf >> 1] : (T)g.lo[bf >> 1];
+    p[bf >> 1] = (bf & 1) ? pick<T>(g.hi[bf >> 1], g.hi_f[bf >> 1]) : pick<T>(g.lo[bf >> 1], g.lo_f[bf >> 1]);
     if (g.kind == kBoxMinusBoxes) {
         const int c = grid_cell<T>(g, x, y, z);
         const int e = g.cstart[c + 1];
@@ -189,9 +207,18 @@ enum DataKind : int { kPointSource = 0, kHarmonicSH = 1, kConstant = 2 };
 // normalised associated-Legendre recurrence coefficients, filled at load time:
 // A[l][m] = sqrt((4l^2-1)/(l^2-m^2)), B[l][m] = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)),
 // D[m] = sqrt((2m+1)/(2m))
+// Pairs (l, m), 0 <= m <= l <= kMaxL, in m-major order: pair (l, m) sits at
+// sh_pair(l, m).
+constexpr int kShPairs = (kMaxL + 1) * (kMaxL + 2) / 2;
+__host__ __device__ constexpr int sh_pair(int l, int m) { return m * (kMaxL + 1) - m * (m - 1) / 2 + (l - m); }
+
 struct ShTables {
     double A[kMaxL + 1][kMaxL + 1], B[kMaxL + 1][kMaxL + 1], D[kMaxL + 1];
     float Af[kMaxL + 1][kMaxL + 1], Bf[kMaxL + 1][kMaxL + 1], Df[kMaxL + 1];
+    // solid-harmonic form (FP32): rec[sh_pair(l, m)] = (A, A B) of (l, m);
+    // pmm[m] = Y00 prod_{k<=m} D_k, times sqrt 2 for m > 0
+    float2 rec[kShPairs];
+    float pmm[kMaxL + 1];
 };
 
 struct DData {
@@ -203,6 +230,11 @@ struct DData {
     double ctr[3], inv_scale;
     double constant;
     const ShTables *sh;     // device copy of the recurrence tables
+    // FP32 copies rounded on the host; q_f = strength / (4 pi)
+    float x0_f[3], q_f, ctr_f[3], inv_scale_f, constant_f;
+    // FP32 coefficients in pair order: cart[sh_pair(l, m)] = (c_{l,m}, c_{l,-m})
+    // (c_{l,-0} = 0, zero beyond lmax)
+    const float2 *cart;
 };
 
 // The recurrence coefficients live in constant memory: every index (l, m) is the
@@ -233,9 +265,10 @@ template <> __device__ __forceinline__ float clm_at<float>(const DData &d, int i
 // and the angle-addition recurrence for cos(m phi), sin(m phi).
 template <typename T>
 __device__ T harmonic_eval(const DData &d, T x, T y, T z) {
-    x = (x - (T)d.ctr[0]) * (T)d.inv_scale;
-    y = (y - (T)d.ctr[1]) * (T)d.inv_scale;
-    z = (z - (T)d.ctr[2]) * (T)d.inv_scale;
+    const T is = pick<T>(d.inv_scale, d.inv_scale_f);
+    x = (x - pick<T>(d.ctr[0], d.ctr_f[0])) * is;
+    y = (y - pick<T>(d.ctr[1], d.ctr_f[1])) * is;
+    z = (z - pick<T>(d.ctr[2], d.ctr_f[2])) * is;
     const T rxy2 = x * x + y * y;
     const T r = sqrt(rxy2 + z * z);
     const T y00 = (T)0.28209479177387814;  // 1/sqrt(4 pi)
@@ -273,15 +306,51 @@ __device__ T harmonic_eval(const DData &d, T x, T y, T z) {
     return acc;
 }
 
+// The same sum in FP32 without square roots or divisions, by the solid
+// harmonics r^l Ybar_lm: with (C_m + i S_m) = (x + i y)^m and
+// T_lm = r^(l-m) Pbar_lm(cos theta) / sin^m theta, a polynomial in z and r^2,
+//   T_mm = pmm_m,  T_lm = A_lm (z T_{l-1,m} - B_lm r^2 T_{l-2,m}),
+//   g = sum_m sum_l T_lm (c_{l,m} C_m + c_{l,-m} S_m).
+// `cs` are the coefficients in pair order (shared memory), x, y, z already
+// centred and scaled.
+__device__ __forceinline__ float harmonic_cart(const float2 *cs, int lmax, float x, float y, float z) {
+    const float r2 = x * x + y * y + z * z;
+    float C = 1.f, S = 0.f, acc = 0.f;
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) {
+            const float c2 = C * x - S * y;
+            S = fmaf(S, x, C * y);
+            C = c2;
+        }
+        int k = sh_pair(m, m);
+        float t2 = 0.f, t1 = c_sh.pmm[m];
+        float2 c = cs[k];
+        float ac = c.x * t1, as = c.y * t1;
+        for (int l = m + 1; l <= lmax; ++l) {
+            ++k;
+            const float2 rc = c_sh.rec[k];
+            const float t = rc.x * z * t1 - rc.y * r2 * t2;
+            t2 = t1;
+            t1 = t;
+            c = cs[k];
+            ac = fmaf(c.x, t, ac);
+            as = fmaf(c.y, t, as);
+        }
+        acc = fmaf(ac, C, fmaf(as, S, acc));
+    }
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ T dirichlet_eval(const DData &d, T x, T y, T z) {
     if (d.kind == kPointSource) {
-        const T dx = x - (T)d.x0[0], dy = y - (T)d.x0[1], dz = z - (T)d.x0[2];
-        return (T)(d.strength / (4.0 * kPi)) / sqrt(dx * dx + dy * dy + dz * dz);
+        const T dx = x - pick<T>(d.x0[0], d.x0_f[0]), dy = y - pick<T>(d.x0[1], d.x0_f[1]),
+                dz = z - pick<T>(d.x0[2], d.x0_f[2]);
+        return pick<T>(d.strength / (4.0 * kPi), d.q_f) / sqrt(dx * dx + dy * dy + dz * dz);
     } else if (d.kind == kHarmonicSH) {
         return harmonic_eval<T>(d, x, y, z);
     }
-    return (T)d.constant;
+    return pick<T>(d.constant, d.constant_f);
 }
 
 // ------------------------------------------------------------------ Green's functions

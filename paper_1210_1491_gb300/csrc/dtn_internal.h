@@ -41,7 +41,27 @@ struct BatchLayout {
     std::vector<int64_t> rep;                             // n_groups: first member
     std::vector<int64_t> grows_off, gmat_off, gfac_off;   // n_groups + 1
     int64_t grows_total = 0, gmat_total = 0, gfac_total = 0;
+    // weight groups (shape and node orders): the weights that map the data and
+    // the walk estimates to the right side of Eq. bw51 are the same for all
+    // members; rows x kcols FP32, kcols = 64 per panel (8 x 8 data samples,
+    // cap patches only) + hemisphere nodes
+    int64_t n_wgroups = 0;
+    std::vector<int64_t> wgroup_of, wrep;                 // n, n_wgroups
+    std::vector<int64_t> wrows_off;                       // n_wgroups + 1
+    int64_t wrows_total = 0;
+    std::vector<int64_t> kcols, gw_off;                   // n_wgroups, n_wgroups + 1
+    int64_t gw_total = 0;
+    std::vector<int64_t> vec_off;                         // n + 1: per-patch sample vectors
+    int64_t vec_total = 0;
+    std::vector<int64_t> members, mem_off, tile_off;      // n, n_wgroups + 1, n_wgroups + 1
+    int64_t tiles_total = 0;
+    int32_t max_wgroup_rows = 0;
 };
+
+// panel samples of the data in the right-side weights (8 x 8 Gauss points)
+constexpr int kSampleN = 8, kSamplesPerPanel = kSampleN * kSampleN;
+// patches per column tile of the right-side product
+constexpr int kRhsTileN = 32;
 
 // Device copies of one layout (kept in the geometry workspace).
 struct DevLayout {
@@ -50,6 +70,7 @@ struct DevLayout {
     uint32_t *pid;
     double *radius;
     int64_t *group_of, *rep, *grows_off, *gmat_off, *gfac_off;
+    int64_t *wrep, *wrows_off, *kcols, *gw_off, *vec_off, *members, *mem_off, *tile_off;
     PatchFrame *frames;
 };
 
@@ -73,7 +94,8 @@ struct Workspace {
     DevBuf gmat;            // shared matrices, one per shape group (FP64)
     DevBuf gfac;            // shared FP32 factors, n(n+1) per group
     DevBuf gpiv;            // shared pivots, n per group
-    DevBuf gpre;            // data at the fixed double-layer rules (cap patches)
+    DevBuf gw;              // right-side weights per weight group (FP32)
+    DevBuf vec;             // per-patch samples (data at panel points, walk estimates), FP32
 };
 
 struct GeometryHost {
@@ -97,7 +119,7 @@ struct dtn_geometry {
     dtn::DData dd{};
     bool has_data = false;
     double score_bound = 1.0;          // bound on |g| over the boundary
-    dtn::DevBuf d_boxes, d_boxes_f, d_cstart, d_citems, d_ccap, d_clm, d_clm_f;
+    dtn::DevBuf d_boxes, d_boxes_f, d_cstart, d_citems, d_ccap, d_clm, d_clm_f, d_clm_cart;
     dtn::Workspace ws;
     int device = 0;
     int num_sms = 0;
@@ -171,15 +193,19 @@ size_t wos_scratch_bytes(int64_t nodes);
 cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s);
 
 // mode 0: per patch, A and b (FP64 rules, or FP32 far field in mixed precision);
-// mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off;
-// mode 2: b only, per patch (mixed precision rules for the double layer)
+// mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
                             int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
-                            const double *gamma_w, const double *U, double *A, double *b,
-                            float *gpre, cudaStream_t s);
-// floats of data the mode-2 assembly precomputes per panel (cap patches)
-constexpr int64_t kGprePerPanel = 320;
+                            const double *gamma_w, const double *U, double *A, double *b, cudaStream_t s);
+
+// mixed precision right sides: FP64 weights per shape group (product rules of
+// the double layer against the panel interpolants of the data, and the walk
+// term), the per-patch sample vectors, then one product per group
+cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                              const double *panel_loc, const double *panel_prm, const double *panel_aux,
+                              const double *panel_g, const double *gamma_loc, const double *gamma_w,
+                              const double *U, float *gw, float *vec, double *b, cudaStream_t s);
 
 // copies each patch's group matrix into its own block (mat_off) for checking
 cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA,

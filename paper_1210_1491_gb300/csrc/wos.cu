@@ -66,23 +66,122 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-template <typename T>
+// Per-lane step and cap counts of the node the lane works on, flushed with
+// integer atomics when the lane moves to another node.
 struct LaneAcc {
     int64_t node = -1;
-    long long a1 = 0, a2 = 0;
     unsigned long long st = 0;
     unsigned int cap = 0;
 
     __device__ __forceinline__ void flush(const WosDev &P) {
         if (node >= 0) {
-            atomicAdd(P.s1 + node, (unsigned long long)a1);
-            atomicAdd(P.s2 + node, (unsigned long long)a2);
             atomicAdd(P.st + node, st);
             if (cap) atomicAdd(P.cap + node, cap);
         }
-        a1 = 0; a2 = 0; st = 0; cap = 0;
+        st = 0;
+        cap = 0;
     }
 };
+
+// Fixed-point score terms round(s 2^F1) and round(s^2 2^F2).  FP32 scores:
+// s 2^F is exact in FP32 (F in the normal range), and s^2 = M^2 2^(2e) with
+// the 24-bit significand M is formed exactly as a 48-bit integer, so both
+// round to the same integers as the FP64 products would (ties to even).
+__device__ __forceinline__ long long fixed_term(float s, int F) {
+    if (F >= -126 && F <= 127) return __float2ll_rn(s * __int_as_float((F + 127) << 23));
+    return __double2ll_rn((double)s * pow2(F));
+}
+__device__ __forceinline__ long long fixed_term(double s, int F) { return __double2ll_rn(s * pow2(F)); }
+
+__device__ __forceinline__ long long fixed_square(float s, int F) {
+    const uint32_t bits = __float_as_uint(s) & 0x7fffffffu;
+    const int E = (int)(bits >> 23);
+    const unsigned long long M = E ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
+    const unsigned long long M2 = M * M;   // < 2^48
+    if (M2 == 0ull) return 0;
+    const int sh = 2 * ((E ? E : 1) - 150) + F;
+    if (sh >= 0) return (long long)(M2 << (sh < 15 ? sh : 15));   // < 2^61 by the choice of F
+    const int k = -sh;
+    if (k > 48) return 0;   // below 1/2
+    const unsigned long long q = M2 >> k, rem = M2 & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    return (long long)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+}
+__device__ __forceinline__ long long fixed_square(double s, int F) { return __double2ll_rn(s * s * pow2(F)); }
+
+// Data at a boundary point for the score: FP32 harmonic data by the solid
+// harmonic recurrences with the coefficients staged in shared memory.
+template <typename T>
+__device__ __forceinline__ T walk_data(const DData &d, const float2 *cs, T x, T y, T z) {
+    if constexpr (sizeof(T) == 4) {
+        if (d.kind == kHarmonicSH) {
+            const float is = d.inv_scale_f;
+            return harmonic_cart(cs, d.lmax, (x - d.ctr_f[0]) * is, (y - d.ctr_f[1]) * is, (z - d.ctr_f[2]) * is);
+        }
+    }
+    return dirichlet_eval<T>(d, x, y, z);
+}
+
+// Absorbed walks wait in a per-warp ring of absorption points until 32 are
+// there; then every lane scores one (projection onto the boundary and the
+// data), so the scoring never runs with idle lanes.
+constexpr int kQueue = 64;
+template <typename T>
+struct ScoreQueue {
+    T x[kQueue], y[kQueue], z[kQueue];
+    int node[kQueue];
+    short f1[kQueue], f2[kQueue];
+};
+
+// Warp-uniform running score sums of one node, flushed with atomics when a
+// batch brings another node.
+struct WarpScore {
+    int node = -1;
+    long long a1 = 0, a2 = 0;
+};
+
+template <typename T, int GK>
+__device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const float2 *cs, ScoreQueue<T> &Q,
+                                            int &qhead, int &qcount, int cnt, int lane, WarpScore &ws) {
+    const unsigned FULL = 0xffffffffu;
+    int node = -1;
+    long long v1 = 0, v2 = 0;
+    if (lane < cnt) {
+        const int e = (qhead + lane) & (kQueue - 1);
+        T nx, ny, nz;
+        geo_nearest<T>(P.g, sb, Q.x[e], Q.y[e], Q.z[e], nx, ny, nz);
+        const T sc = walk_data<T>(P.dat, cs, nx, ny, nz);
+        node = Q.node[e];
+        v1 = fixed_term(sc, (int)Q.f1[e]);
+        v2 = fixed_square(sc, (int)Q.f2[e]);
+    }
+    __syncwarp();
+    unsigned rem = __ballot_sync(FULL, lane < cnt);
+    while (rem) {
+        const int nd = __shfl_sync(FULL, node, __ffs(rem) - 1);
+        const bool in = (lane < cnt) && node == nd;
+        long long s1 = in ? v1 : 0, s2 = in ? v2 : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(FULL, s1, o);
+            s2 += __shfl_xor_sync(FULL, s2, o);
+        }
+        rem &= ~__ballot_sync(FULL, in);
+        if (nd != ws.node) {
+            if (ws.node >= 0 && lane == 0) {
+                atomicAdd(P.s1 + ws.node, (unsigned long long)ws.a1);
+                atomicAdd(P.s2 + ws.node, (unsigned long long)ws.a2);
+            }
+            ws.node = nd;
+            ws.a1 = 0;
+            ws.a2 = 0;
+        }
+        ws.a1 += s1;
+        ws.a2 += s2;
+    }
+    qhead = (qhead + cnt) & (kQueue - 1);
+    qcount -= cnt;
+    __syncwarp();   // the slots just read may be written by the next pushes
+}
 
 // one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
 // z uniform in (-1, 1), azimuth 2 pi u2
@@ -116,42 +215,57 @@ __device__ __forceinline__ void jump(double &x, double &y, double &z, double d, 
 template <typename T, int GK>
 __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
     extern __shared__ float s_boxes[];
+    __shared__ ScoreQueue<T> s_queue[kWosThreads / 32];
+    __shared__ float2 s_cs[kShPairs];
     const float *sb = nullptr;
     if (GK == kBoxMinusBoxes && std::is_same<T, float>::value && P.g.nb <= kMaxSmemBoxes) {
         for (int i = threadIdx.x; i < 6 * P.g.nb; i += blockDim.x) s_boxes[i] = P.g.boxes_f[i];
-        __syncthreads();
         sb = s_boxes;
     }
+    if (std::is_same<T, float>::value && P.dat.kind == kHarmonicSH)
+        for (int i = threadIdx.x; i < kShPairs; i += blockDim.x) s_cs[i] = P.dat.cart[i];
+    __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const T eps = (T)P.eps;
+    ScoreQueue<T> &Q = s_queue[threadIdx.x >> 5];
+    int qhead = 0, qcount = 0;   // warp-uniform
+    WarpScore ws;
 
     // warp-uniform chunk state
     int64_t cnode = -1;
     int64_t cnext = 0, cend = 0;
     uint32_t cpid = 0, cpt = 0;
-    double csc1 = 0.0, csc2 = 0.0;
+    int cf1 = 0, cf2 = 0;          // fixed-point exponents of the node's sums
+    T cx = 0, cy = 0, cz = 0;
     bool no_more = false;
 
     // lane state
     bool active = false, pending = false;
     T x = 0, y = 0, z = 0;
     uint32_t walk = 0, step = 0, ppid = 0, ppt = 0;
-    double sc1 = 0.0, sc2 = 0.0;
-    LaneAcc<T> acc;
+    int f1 = 0, f2 = 0;
+    LaneAcc acc;
 
     for (;;) {
-        // absorbed walks keep their absorption point until here: project it onto
-        // the boundary and score the data there, all pending lanes together
-        if (pending) {
-            T nx, ny, nz;
-            geo_nearest<T>(P.g, (const T *)sb, x, y, z, nx, ny, nz);
-            const T sc = dirichlet_eval<T>(P.dat, nx, ny, nz);
-            const double sd = (double)sc;
-            acc.a1 += __double2ll_rn(sd * sc1);
-            acc.a2 += __double2ll_rn(sd * sd * sc2);
-            pending = false;
+        // absorbed walks go to the queue with their absorption point; full
+        // batches of 32 are scored at once
+        const unsigned pm = __ballot_sync(FULL, pending);
+        if (pm) {
+            if (pending) {
+                const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
+                Q.x[e] = x;
+                Q.y[e] = y;
+                Q.z[e] = z;
+                Q.node[e] = (int)acc.node;
+                Q.f1[e] = (short)f1;
+                Q.f2[e] = (short)f2;
+                pending = false;
+            }
+            qcount += __popc(pm);
+            __syncwarp();
+            if (qcount >= 32) score_batch<T, GK>(P, (const T *)sb, s_cs, Q, qhead, qcount, 32, lane, ws);
         }
         // hand out walks to idle lanes
         unsigned idle = __ballot_sync(FULL, !active);
@@ -172,9 +286,12 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                 cnext = j * P.chunk;
                 cend = min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
                 cpid = P.pid[grp];
-                csc1 = pow2(fixed_exponent(P.walks[grp], P.lgM1));
-                csc2 = pow2(fixed_exponent(P.walks[grp], P.lgM2));
+                cf1 = fixed_exponent(P.walks[grp], P.lgM1);
+                cf2 = fixed_exponent(P.walks[grp], P.lgM2);
                 cpt = P.point_id ? P.point_id[cnode] : (uint32_t)k;
+                cx = (T)P.y[3 * cnode];
+                cy = (T)P.y[3 * cnode + 1];
+                cz = (T)P.y[3 * cnode + 2];
             }
             const int nidle = __popc(idle);
             const int take = (int)min((int64_t)nidle, cend - cnext);
@@ -188,11 +305,11 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                 step = 0;
                 ppid = cpid;
                 ppt = cpt;
-                sc1 = csc1;
-                sc2 = csc2;
-                x = (T)P.y[3 * cnode];
-                y = (T)P.y[3 * cnode + 1];
-                z = (T)P.y[3 * cnode + 2];
+                f1 = cf1;
+                f2 = cf2;
+                x = cx;
+                y = cy;
+                z = cz;
                 active = true;
             }
             cnext += take;
@@ -244,6 +361,26 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
         }
     }
     acc.flush(P);
+    // the last absorbed walks (fewer than 32)
+    {
+        const unsigned pm = __ballot_sync(FULL, pending);
+        if (pending) {
+            const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
+            Q.x[e] = x;
+            Q.y[e] = y;
+            Q.z[e] = z;
+            Q.node[e] = (int)acc.node;
+            Q.f1[e] = (short)f1;
+            Q.f2[e] = (short)f2;
+        }
+        qcount += __popc(pm);
+        __syncwarp();
+        while (qcount > 0) score_batch<T, GK>(P, (const T *)sb, s_cs, Q, qhead, qcount, min(qcount, 32), lane, ws);
+    }
+    if (ws.node >= 0 && lane == 0) {
+        atomicAdd(P.s1 + ws.node, (unsigned long long)ws.a1);
+        atomicAdd(P.s2 + ws.node, (unsigned long long)ws.a2);
+    }
 }
 
 __global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int64_t *__restrict__ node_off,
@@ -279,6 +416,7 @@ void *wos_kernel_ptr(int gk) {
 
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     if (w.total_nodes == 0) return cudaSuccess;
+    if (w.total_nodes > 0x7fffffffll) return cudaErrorInvalidValue;   // node ids are 32-bit in the kernel
     cudaError_t e;
     // accumulators: s1, s2, st (u64) and cap (u32) per node, plus the counter
     const size_t n = (size_t)w.total_nodes;
@@ -356,6 +494,7 @@ size_t wos_scratch_bytes(int64_t nodes) {
 
 cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s) {
     if (w.total_nodes == 0) return cudaSuccess;
+    if (w.total_nodes > 0x7fffffffll) return cudaErrorInvalidValue;   // node ids are 32-bit in the kernel
     cudaError_t e;
     const size_t n = (size_t)w.total_nodes;
     const size_t bytes = wos_scratch_bytes(w.total_nodes);
