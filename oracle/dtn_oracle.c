@@ -104,7 +104,9 @@ void or_gauss_legendre(int n, double *x, double *w)
 }
 
 /* ================================================================ geometry */
-/* Domain kinds: 0 ball interior, 1 box interior, 2 box minus boxes. */
+/* Domain kinds: 0 ball interior, 1 box interior, 2 box minus boxes, 3 half space
+ * z > center[2] (an exterior-type region: a walk that leaves the truncation
+ * sphere of radius `radius` about `center` has gone to infinity, Sec. 4.1.3). */
 typedef struct {
     int kind;
     double center[3], radius;
@@ -118,6 +120,10 @@ typedef struct {
  * Ties take the lowest face / box index; the outer box comes before the wires. */
 double or_distance(const or_geom *g, const double x[3], double nearest[3])
 {
+    if (g->kind == 3) {
+        nearest[0] = x[0]; nearest[1] = x[1]; nearest[2] = g->center[2];
+        return x[2] - g->center[2];
+    }
     if (g->kind == 0) {
         double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
         double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -283,7 +289,9 @@ typedef struct {
 
 /* One walk on spheres (Sec. 2): from y, repeat { d = dist(x); stop if d <= eps;
  * jump to a uniform point of the sphere of radius d about x }.  Returns 1 and the
- * score when absorbed, 0 when the walk reached max_steps distance evaluations. */
+ * score when absorbed, 0 when the walk reached max_steps distance evaluations.
+ * Half space: before each distance evaluation, a walk outside the truncation
+ * sphere has gone to infinity and scores 0 (the solution vanishes there). */
 int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t walk,
             uint32_t point, uint32_t patch, const or_wos_opts *o, double *score, uint64_t *steps)
 {
@@ -292,6 +300,13 @@ int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t wa
     *steps = 0;
     for (uint64_t j = 0; j < o->max_steps; ++j) {
         double nb[3];
+        if (g->kind == 3) {
+            double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
+            if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] > g->radius * g->radius) {
+                *score = 0.0;
+                return 1;
+            }
+        }
         double d = or_distance(g, x, nb);
         *steps += 1;
         if (d <= o->eps) {
@@ -408,6 +423,16 @@ int or_patch_frame(const or_geom *g, const double c[3], double a, or_patch *p)
         p->theta_max = acos(a / (2.0 * g->radius));
         /* geodesic angle of the cap: chord a  <=>  psi = 2 asin(a / 2R) */
         p->umax = 2.0 * asin(a / (2.0 * g->radius));
+        frame_from_normal(p);
+        return 0;
+    }
+    if (g->kind == 3) {
+        /* the plane z = center[2]; the region lies above it */
+        if (!(fabs(c[2] - g->center[2]) <= 1e-9 * fmax(1.0, fabs(g->center[2])))) return -1;
+        p->n[0] = 0.0; p->n[1] = 0.0; p->n[2] = -1.0;
+        p->kind = 0;
+        p->theta_max = OR_PI / 2.0;
+        p->umax = a;
         frame_from_normal(p);
         return 0;
     }
@@ -916,6 +941,78 @@ int or_solve_patch(const or_geom *g, const or_data *dat, const double c[3], doub
     int rc = or_lu_solve(n, A, b, q_out);
     free(A); free(b); free(U);
     return rc;
+}
+
+/* ======================================================= single point */
+/* Neumann data at one point x of a flat boundary piece, Sec. 4.1 (Eq. bw64):
+ *   q(x) = Sigma1' + Sigma2',
+ *   Sigma1' = - int_Gamma d2g/dn_x dn_y (u(y) - g(x)) ds_y        (Eq. bw65)
+ *           ~ - sum_ij W_ij (3 cos th_i / (2 pi a^3)) (U_ij - g(x))  (Eq. bw83, bw85)
+ * with the hemisphere nodes and weights of or_gamma_nodes (theta_max = pi/2), the
+ * normal second derivative of the half-ball Green's function on Gamma being
+ * 3 cos th / (2 pi a^3); U_ij are WOS estimates (Eq. bw87) or given values;
+ *   Sigma2' = -(1/2pi) int_{S_a minus disk(x, delta)} (1/rho^3 - 1/a^3) (g(y) - g(x)) ds_y
+ * (Eq. bw68 with the small disk of Eq. bw73-bw82 removed, an O(delta) error),
+ * by the ng2 x ng2 Gauss rule in polar coordinates about x: rho in [delta, a],
+ * angle in [0, 2 pi], ds = rho drho dangle.
+ * out: Sigma1', Sigma2', q, standard error of Sigma1'.  U_in (ng1^2 values) or NULL
+ * to run `walks` walks per node (node k = i*ng1 + j is the RNG point id, `patch`
+ * the RNG patch id).  U_out (ng1^2) receives the node values if not NULL.
+ * Returns 0, or -1 if x is not on a supported flat piece. */
+int or_single_point(const or_geom *g, const or_data *dat, const double x[3], double a, int ng1,
+                    int ng2, double delta, int64_t walks, uint32_t patch, const or_wos_opts *o,
+                    const double *U_in, double out[4], double *U_out)
+{
+    or_patch p;
+    if (or_patch_frame(g, x, a, &p) != 0 || p.kind != 0) return -1;
+    const int nn = ng1 * ng1;
+    double *Yl = malloc(sizeof(double) * 3 * nn), *yg = malloc(sizeof(double) * 3 * nn);
+    double *W = malloc(sizeof(double) * nn), *U = malloc(sizeof(double) * nn);
+    double *SE = malloc(sizeof(double) * nn);
+    or_gamma_nodes(&p, ng1, ng1, Yl, yg, W);
+    if (U_in) {
+        for (int k = 0; k < nn; ++k) { U[k] = U_in[k]; SE[k] = 0.0; }
+    } else {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int k = 0; k < nn; ++k) {
+            double s1, s2;
+            uint64_t st, cap;
+            or_wos_point(g, dat, yg + 3 * k, (uint32_t)k, patch, 0, walks, o, &s1, &s2, &st, &cap);
+            double N = (double)(walks - (int64_t)cap);
+            U[k] = s1 / N;
+            double var = (s2 - N * U[k] * U[k]) / (N * (N - 1.0));
+            SE[k] = sqrt(fmax(var, 0.0));
+        }
+    }
+    const double gx = or_dirichlet(dat, x);
+    double s1 = 0.0, v1 = 0.0;
+    for (int k = 0; k < nn; ++k) {
+        double cth = -Yl[3 * k + 2] / a;
+        double wk = W[k] * 3.0 * cth / (2.0 * OR_PI * a * a * a);
+        s1 -= wk * (U[k] - gx);
+        v1 += wk * wk * SE[k] * SE[k];
+    }
+    double *xr = malloc(sizeof(double) * ng2), *wr = malloc(sizeof(double) * ng2);
+    or_gauss_legendre(ng2, xr, wr);
+    double s2 = 0.0;
+    for (int i = 0; i < ng2; ++i) {
+        double rho = delta + 0.5 * (a - delta) * (xr[i] + 1.0);
+        double wrho = 0.5 * (a - delta) * wr[i];
+        for (int j = 0; j < ng2; ++j) {
+            double ang = OR_PI * (xr[j] + 1.0);
+            double L[3] = {rho * cos(ang), rho * sin(ang), 0.0};
+            double y[3];
+            local_to_global(&p, L, y);
+            s2 += wrho * OR_PI * wr[j] * rho * (1.0 / (rho * rho * rho) - 1.0 / (a * a * a)) *
+                  (or_dirichlet(dat, y) - gx);
+        }
+    }
+    s2 *= -1.0 / (2.0 * OR_PI);
+    out[0] = s1; out[1] = s2; out[2] = s1 + s2; out[3] = sqrt(v1);
+    if (U_out)
+        for (int k = 0; k < nn; ++k) U_out[k] = U[k];
+    free(Yl); free(yg); free(W); free(U); free(SE); free(xr); free(wr);
+    return 0;
 }
 
 /* ============================================================== potential */

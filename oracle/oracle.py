@@ -99,6 +99,10 @@ def lib():
         L.or_potential.argtypes = [C.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_int64,
                                    _f64p, _f64p]
         L.or_owned.argtypes = [C.c_int64, _f64p, _i64p, C.c_int64, _f64p, _u8p]
+        L.or_single_point.argtypes = [C.POINTER(OrGeom), C.POINTER(OrData), _f64p, C.c_double, C.c_int,
+                                      C.c_int, C.c_double, C.c_int64, C.c_uint32, C.POINTER(OrWosOpts),
+                                      C.c_void_p, _f64p, C.c_void_p]
+        L.or_single_point.restype = C.c_int
         L.or_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -360,3 +364,26 @@ def num_threads() -> int:
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]
+
+
+def single_point(geom, data, x, a, ng1, ng2, delta, walks=0, patch=0, opts=None, U_in=None):
+    """or_single_point: Neumann data at one point of a flat boundary piece by
+    Sigma1' + Sigma2' (Sec. 4.1, Eq. bw64-bw88).  Returns dict(sigma1, sigma2, q,
+    se, U) or None if x is not on a supported flat piece."""
+    og, k1 = make_geom(geom)
+    od, k2 = make_data(data)
+    o = opts if opts is not None else wos_opts()
+    nn = ng1 * ng1
+    U = np.zeros(nn)
+    out = np.zeros(4)
+    uin = None
+    if U_in is not None:
+        uin = np.ascontiguousarray(U_in, dtype=np.float64)
+        assert uin.shape == (nn,)
+    rc = lib().or_single_point(C.byref(og), C.byref(od), np.ascontiguousarray(x, dtype=np.float64), float(a),
+                               int(ng1), int(ng2), float(delta), int(walks), int(patch), C.byref(o),
+                               None if uin is None else uin.ctypes.data_as(C.c_void_p), out,
+                               U.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        return None
+    return dict(sigma1=out[0], sigma2=out[1], q=out[2], se=out[3], U=U)

@@ -26,6 +26,7 @@ import numpy as np
 GEOM_BALL_INTERIOR = 0
 GEOM_BOX_INTERIOR = 1
 GEOM_BOX_MINUS_BOXES = 2
+GEOM_HALF_SPACE = 3
 
 # Dirichlet data kinds
 DATA_POINT_SOURCE = 0
@@ -284,6 +285,17 @@ def wires(n_patches: int = 10_000, walks: int = 2048, a: float = 0.3,
                        n_rings=rings, n_sectors=sectors,
                        walks=np.full(n_patches, walks, dtype=np.int64))
     return Workload(f"wires200_{n_patches}p_uneven", geom, data, batch)
+
+
+def half_space_charge(depth: float = 1.0, truncation: float = 1e5) -> tuple:
+    """The planar-interface problem of Sec. 4.1.3 (Test 1): the region z > 0
+    above the plane z = 0, a unit point charge at (0, 0, -depth) below it, so
+    u = 1 / |x - (0, 0, -depth)| (point-source data of strength 4 pi); walks
+    that leave the sphere of radius `truncation` about the origin have gone
+    to infinity.  Returns (Geometry, Dirichlet)."""
+    geom = Geometry(GEOM_HALF_SPACE, center=(0.0, 0.0, 0.0), radius=truncation)
+    data = Dirichlet(DATA_POINT_SOURCE, x0=(0.0, 0.0, -depth), strength=4.0 * np.pi)
+    return geom, data
 
 
 def targets_in_ball(n: int, radius: float, margin: float, seed: int = 3) -> np.ndarray:
