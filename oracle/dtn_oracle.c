@@ -104,15 +104,19 @@ void or_gauss_legendre(int n, double *x, double *w)
 }
 
 /* ================================================================ geometry */
-/* Domain kinds: 0 ball interior, 1 box interior, 2 box minus boxes, 3 half space
- * z > center[2] (an exterior-type region: a walk that leaves the truncation
- * sphere of radius `radius` about `center` has gone to infinity, Sec. 4.1.3). */
+/* Domain kinds: 0 ball interior, 1 box interior, 2 box minus boxes, and two
+ * unbounded regions where a walk that leaves the truncation sphere of radius
+ * `truncation` about `center` has gone to infinity (Sec. 4.1.3): 3 the half
+ * space z > center[2]; 4 space outside the thin disk of radius `radius` about
+ * `center` in the plane z = center[2] (Test 4); 5 space outside the sphere of
+ * radius `radius` about `center` (Sec. 5.2, the R = 3 sphere). */
 typedef struct {
     int kind;
     double center[3], radius;
     double lo[3], hi[3];
     int n_boxes;
     const double *boxes; /* n_boxes x 6: lo xyz, hi xyz */
+    double truncation;
 } or_geom;
 
 /* Distance from x to the boundary of the region and the nearest boundary point
@@ -123,6 +127,29 @@ double or_distance(const or_geom *g, const double x[3], double nearest[3])
     if (g->kind == 3) {
         nearest[0] = x[0]; nearest[1] = x[1]; nearest[2] = g->center[2];
         return x[2] - g->center[2];
+    }
+    if (g->kind == 5) {
+        double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
+        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (r > 0.0) {
+            for (int i = 0; i < 3; ++i) nearest[i] = g->center[i] + g->radius * v[i] / r;
+        } else {
+            nearest[0] = g->center[0]; nearest[1] = g->center[1];
+            nearest[2] = g->center[2] + g->radius;
+        }
+        return r - g->radius;
+    }
+    if (g->kind == 4) {
+        double dx = x[0] - g->center[0], dy = x[1] - g->center[1], dz = x[2] - g->center[2];
+        double r = sqrt(dx * dx + dy * dy);
+        nearest[2] = g->center[2];
+        if (r <= g->radius) {
+            nearest[0] = x[0]; nearest[1] = x[1];
+            return fabs(dz);
+        }
+        nearest[0] = g->center[0] + g->radius * dx / r;
+        nearest[1] = g->center[1] + g->radius * dy / r;
+        return sqrt((r - g->radius) * (r - g->radius) + dz * dz);
     }
     if (g->kind == 0) {
         double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
@@ -290,8 +317,9 @@ typedef struct {
 /* One walk on spheres (Sec. 2): from y, repeat { d = dist(x); stop if d <= eps;
  * jump to a uniform point of the sphere of radius d about x }.  Returns 1 and the
  * score when absorbed, 0 when the walk reached max_steps distance evaluations.
- * Half space: before each distance evaluation, a walk outside the truncation
- * sphere has gone to infinity and scores 0 (the solution vanishes there). */
+ * Unbounded regions (kinds 3, 4, 5): before each distance evaluation, a walk
+ * outside the truncation sphere has gone to infinity and scores 0 (the
+ * solution vanishes there). */
 int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t walk,
             uint32_t point, uint32_t patch, const or_wos_opts *o, double *score, uint64_t *steps)
 {
@@ -300,9 +328,9 @@ int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t wa
     *steps = 0;
     for (uint64_t j = 0; j < o->max_steps; ++j) {
         double nb[3];
-        if (g->kind == 3) {
+        if (g->kind >= 3) {
             double v[3] = {x[0] - g->center[0], x[1] - g->center[1], x[2] - g->center[2]};
-            if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] > g->radius * g->radius) {
+            if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] > g->truncation * g->truncation) {
                 *score = 0.0;
                 return 1;
             }
@@ -379,7 +407,8 @@ typedef struct {
     int kind;
     double c[3], n[3], t1[3], t2[3];
     double a;
-    double R, sc[3];   /* cap: sphere radius and centre */
+    double R, sc[3];   /* cap: signed sphere radius (the sphere's centre is at c - R n:
+                          R > 0 for a ball region, R < 0 outside a sphere) and centre */
     double theta_max;  /* hemisphere polar range measured from -n */
     double umax;       /* panel radial parameter range: a (disk) or psi_max (cap) */
 } or_patch;
@@ -426,13 +455,33 @@ int or_patch_frame(const or_geom *g, const double c[3], double a, or_patch *p)
         frame_from_normal(p);
         return 0;
     }
-    if (g->kind == 3) {
-        /* the plane z = center[2]; the region lies above it */
+    if (g->kind == 3 || g->kind == 4) {
+        /* the plane z = center[2] (half space: the region lies above it; thin
+         * disk: the top face, with the ball's slice of the plane inside the disk) */
         if (!(fabs(c[2] - g->center[2]) <= 1e-9 * fmax(1.0, fabs(g->center[2])))) return -1;
+        if (g->kind == 4) {
+            double dx = c[0] - g->center[0], dy = c[1] - g->center[1];
+            if (!(sqrt(dx * dx + dy * dy) + a < g->radius)) return -1;
+        }
         p->n[0] = 0.0; p->n[1] = 0.0; p->n[2] = -1.0;
         p->kind = 0;
         p->theta_max = OR_PI / 2.0;
         p->umax = a;
+        frame_from_normal(p);
+        return 0;
+    }
+    if (g->kind == 5) {
+        /* outside a sphere: the outward normal of the region points into the
+         * sphere, whose centre lies at c + R_sphere n, i.e. signed R = -R_sphere */
+        double v[3] = {c[0] - g->center[0], c[1] - g->center[1], c[2] - g->center[2]};
+        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (!(a < 2.0 * g->radius) || !(fabs(r - g->radius) <= 1e-9 * g->radius)) return -1;
+        for (int i = 0; i < 3; ++i) { p->n[i] = -v[i] / r; p->sc[i] = g->center[i]; }
+        p->kind = 1;
+        p->R = -g->radius;
+        /* |y - centre| >= R on the hemisphere  <=>  cos(theta) >= -a / (2R) */
+        p->theta_max = OR_PI - acos(a / (2.0 * g->radius));
+        p->umax = 2.0 * asin(a / (2.0 * g->radius));
         frame_from_normal(p);
         return 0;
     }
@@ -809,7 +858,7 @@ double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const 
         diam = (u1 - u0) + u1 * (v1 - v0);
         area = 0.5 * (u1 * u1 - u0 * u0) * (v1 - v0);
     } else {
-        diam = p->R * (u1 - u0) + p->R * sin(u1) * (v1 - v0);
+        diam = fabs(p->R) * ((u1 - u0) + sin(u1) * (v1 - v0));
         area = p->R * p->R * (cos(u0) - cos(u1)) * (v1 - v0);
     }
     double tol = rtol * area / (4.0 * OR_PI * (d > diam ? d : diam));

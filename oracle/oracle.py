@@ -24,7 +24,7 @@ _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 class OrGeom(C.Structure):
     _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("radius", C.c_double),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n_boxes", C.c_int),
-                ("boxes", C.POINTER(C.c_double))]
+                ("boxes", C.POINTER(C.c_double)), ("truncation", C.c_double)]
 
 
 class OrData(C.Structure):
@@ -126,6 +126,7 @@ def make_geom(g) -> tuple:
     og.radius = float(g.radius)
     og.lo[:] = list(map(float, g.lo))
     og.hi[:] = list(map(float, g.hi))
+    og.truncation = float(getattr(g, "truncation", 0.0))
     if g.boxes is not None and len(g.boxes):
         b = np.ascontiguousarray(g.boxes, dtype=np.float64)
         k.refs.append(b)
@@ -363,9 +364,6 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
-__all__ = [n for n in dir() if not n.startswith("_")]
-
-
 def single_point(geom, data, x, a, ng1, ng2, delta, walks=0, patch=0, opts=None, U_in=None):
     """or_single_point: Neumann data at one point of a flat boundary piece by
     Sigma1' + Sigma2' (Sec. 4.1, Eq. bw64-bw88).  Returns dict(sigma1, sigma2, q,
@@ -387,3 +385,6 @@ def single_point(geom, data, x, a, ng1, ng2, delta, walks=0, patch=0, opts=None,
     if rc != 0:
         return None
     return dict(sigma1=out[0], sigma2=out[1], q=out[2], se=out[3], U=U)
+
+
+__all__ = [n for n in dir() if not n.startswith("_")]

@@ -17,7 +17,7 @@ Q_EXACT = 0.71554   # Table 1, analytic solution (printed to 5 digits)
 
 
 def _golden():
-    t1, t2, sec = [], [], None
+    t1, t2, t4, sec = [], [], [], None
     with open(os.path.join(GOLDEN, "paper_single_point_sigma.txt")) as f:
         for line in f:
             line = line.split("#")[0].strip()
@@ -27,8 +27,8 @@ def _golden():
                 sec = line.split("]")[0][1:]
                 continue
             v = [float(t) for t in line.split()]
-            (t1 if sec == "table1" else t2).append(v)
-    return t1, t2
+            {"table1": t1, "table2": t2, "test4": t4}[sec].append(v)
+    return t1, t2, t4
 
 
 def _exact_nodes(geom, data, a, ng1):
@@ -50,7 +50,7 @@ def test_half_space_distance_and_frame():
 
 def test_sigma2_matches_table1():
     g, d = W.half_space_charge()
-    t1, _ = _golden()
+    t1, _, _ = _golden()
     for a, s2 in t1:
         r = O.single_point(g, d, X, a, 4, 20, 1e-6 * a, U_in=np.zeros(16))
         assert abs(r["sigma2"] - s2) <= 1e-6, (a, r["sigma2"], s2)
@@ -62,7 +62,7 @@ def test_sigma2_table2_delta_and_order():
     a / (a - delta)); at delta/a <= 1e-4 the two agree to the printed digits.
     The O(delta) trend of Eq. bw82 holds for the rule as written."""
     g, d = W.half_space_charge()
-    _, t2 = _golden()
+    _, t2, _ = _golden()
     a = 0.5
     for row in t2:
         da = row[0]
@@ -79,7 +79,7 @@ def test_sigma2_table2_delta_and_order():
 
 def test_exact_hemisphere_values_recover_analytic_neumann():
     g, d = W.half_space_charge()
-    t1, _ = _golden()
+    t1, _, _ = _golden()
     for a, _ in t1:
         U = _exact_nodes(g, d, a, 20)
         r = O.single_point(g, d, X, a, 20, 20, 1e-6 * a, U_in=U)
@@ -120,3 +120,67 @@ def test_walks_in_half_space_within_4se_of_exact():
                        O.wos_opts(eps=1e-5))
     mean, se = O.wos_estimates(res, walks)
     assert np.all(np.abs(mean - U[:6]) <= 4 * se + 1e-4)
+
+
+def _disk_potential(p, b=1.0):
+    """Potential of the thin disk of radius b at potential 1 (oblate spheroidal
+    solution): u = (2/pi) asin(2b / (r1 + r2)), r1,2 = distances to the rim
+    circle's nearest and farthest points in the meridian plane."""
+    p = np.atleast_2d(p)
+    r = np.hypot(p[:, 0], p[:, 1])
+    r1 = np.hypot(r - b, p[:, 2])
+    r2 = np.hypot(r + b, p[:, 2])
+    return (2.0 / math.pi) * np.arcsin(np.minimum(1.0, 2.0 * b / (r1 + r2)))
+
+
+def test_thin_disk_closed_form_is_the_solution():
+    """The closed form used below: 1 on the disk, harmonic off it (finite
+    differences), decays like 2b/(pi |x|), and its normal derivative on the disk
+    is the analytic density of Test 4."""
+    on = np.array([[0.3, 0.2, 0.0], [-0.9, 0.0, 0.0]])
+    assert np.allclose(_disk_potential(on), 1.0, atol=1e-12)
+    h = 1e-3
+    for x in ([0.4, 0.3, 0.5], [1.5, -0.2, 0.1], [0.0, 0.0, 2.0]):
+        x = np.array(x)
+        lap = sum(_disk_potential(x + h * e)[0] + _disk_potential(x - h * e)[0] for e in np.eye(3)) \
+            - 6 * _disk_potential(x)[0]
+        assert abs(lap / h ** 2) < 1e-4
+    far = np.array([[0.0, 0.0, 1e4]])
+    assert abs(_disk_potential(far)[0] * 1e4 - 2.0 / math.pi) < 1e-6
+    _, _, t4 = _golden()
+    b, a, xr, sig = t4[0]
+    def fd(dz):   # one-sided difference quotient of -du/dz on the top face
+        return (1.0 - _disk_potential([[xr, 0.0, dz]])[0]) / dz
+    dudn = 2.0 * fd(5e-5) - fd(1e-4)   # Richardson: the O(dz) term cancels
+    assert abs(dudn - sig) < 1e-5, dudn
+    assert abs(2.0 / (math.pi * math.sqrt(b * b - xr * xr)) - sig) < 1e-6
+
+
+def test_thin_disk_distance_and_frame():
+    g, _ = W.thin_disk()
+    pts = np.array([[0.3, 0.4, 0.2], [3.0, 4.0, 1.0], [0.0, -2.0, -0.5]])
+    d, nb = O.distance(g, pts)
+    assert np.allclose(d, [0.2, math.hypot(4.0, 1.0), math.hypot(1.0, 0.5)], atol=1e-15)
+    assert np.allclose(nb, [[0.3, 0.4, 0.0], [0.6, 0.8, 0.0], [0.0, -1.0, 0.0]], atol=1e-15)
+    assert O.patch_frame(g, [-0.5, 0.0, 0.0], 0.4) is not None
+    assert O.single_point(g, W.Dirichlet(W.DATA_CONSTANT, constant=1.0), [-0.5, 0, 0], 0.6, 4, 4, 1e-6,
+                          U_in=np.zeros(16)) is None   # the ball's slice leaves the disk
+
+
+def test_thin_disk_exact_hemisphere_values_and_walks():
+    """Test 4: with the exact potential on the hemisphere the rule gives the
+    analytic density (Sigma2' = 0 for constant data); walks that either reach the
+    disk or leave the truncation sphere give Sigma1' within 4 standard errors."""
+    g, d = W.thin_disk()
+    _, _, t4 = _golden()
+    b, a, xr, sig = t4[0]
+    x = np.array([xr, 0.0, 0.0])
+    pf = O.patch_frame(g, x, a)
+    _, yg, _ = O.gamma_nodes(pf, 20, 20)
+    r = O.single_point(g, d, x, a, 20, 20, 1e-6 * a, U_in=_disk_potential(yg.reshape(-1, 3), b))
+    assert abs(r["sigma2"]) < 1e-15
+    assert abs(r["q"] - sig) < 2e-4 * sig, r["q"]
+    _, yg6, _ = O.gamma_nodes(pf, 6, 6)
+    r0 = O.single_point(g, d, x, a, 6, 6, 1e-6 * a, U_in=_disk_potential(yg6.reshape(-1, 3), b))
+    rw = O.single_point(g, d, x, a, 6, 6, 1e-6 * a, walks=300, patch=5, opts=O.wos_opts(eps=1e-5))
+    assert rw["se"] > 0 and abs(rw["sigma1"] - r0["sigma1"]) <= 4 * rw["se"] + 1e-4

@@ -27,6 +27,8 @@ GEOM_BALL_INTERIOR = 0
 GEOM_BOX_INTERIOR = 1
 GEOM_BOX_MINUS_BOXES = 2
 GEOM_HALF_SPACE = 3
+GEOM_DISK_EXTERIOR = 4
+GEOM_BALL_EXTERIOR = 5
 
 # Dirichlet data kinds
 DATA_POINT_SOURCE = 0
@@ -42,6 +44,7 @@ class Geometry:
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (1.0, 1.0, 1.0)
     boxes: np.ndarray | None = None  # (n, 6) float64: lo xyz, hi xyz
+    truncation: float = 0.0          # unbounded regions: radius of the truncation sphere
 
     @property
     def n_boxes(self) -> int:
@@ -293,8 +296,31 @@ def half_space_charge(depth: float = 1.0, truncation: float = 1e5) -> tuple:
     u = 1 / |x - (0, 0, -depth)| (point-source data of strength 4 pi); walks
     that leave the sphere of radius `truncation` about the origin have gone
     to infinity.  Returns (Geometry, Dirichlet)."""
-    geom = Geometry(GEOM_HALF_SPACE, center=(0.0, 0.0, 0.0), radius=truncation)
+    geom = Geometry(GEOM_HALF_SPACE, center=(0.0, 0.0, 0.0), truncation=truncation)
     data = Dirichlet(DATA_POINT_SOURCE, x0=(0.0, 0.0, -depth), strength=4.0 * np.pi)
+    return geom, data
+
+
+def sphere_exterior(n_patches: int = 64, R: float = 3.0, a: float = 1.0, walks: int = 1000,
+                    n_theta: int = 16, n_phi: int = 32, n_rings: int = 8, n_sectors: int = 16,
+                    truncation: float = 1e5) -> Workload:
+    """Sec. 5.2: the DtN map on the sphere of radius R = 3 seen from outside,
+    with unit potential on the sphere and u = 0 at infinity (u = R/|x|, exact
+    Neumann data along the outward normal of the region, which points into the
+    sphere: q = 1/R); patch centres on a Fibonacci sphere, a = 1, cap patches."""
+    geom = Geometry(GEOM_BALL_EXTERIOR, center=(0.0, 0.0, 0.0), radius=R, truncation=truncation)
+    data = Dirichlet(DATA_CONSTANT, constant=1.0)
+    batch = _uniform_batch(fibonacci_sphere(n_patches, R), a, n_theta, n_phi, n_rings, n_sectors, walks)
+    return Workload("sphere_exterior_R3", geom, data, batch, epsilon=1e-4, seed=0)
+
+
+def thin_disk(b: float = 1.0, truncation: float = 1e5) -> tuple:
+    """Test 4 of Sec. 4.1.3: space outside the thin disk of radius b in the plane
+    z = 0 about the origin, the disk held at potential 1 (constant data), u = 0
+    at infinity; walks that leave the sphere of radius `truncation` have gone
+    to infinity.  Returns (Geometry, Dirichlet)."""
+    geom = Geometry(GEOM_DISK_EXTERIOR, center=(0.0, 0.0, 0.0), radius=b, truncation=truncation)
+    data = Dirichlet(DATA_CONSTANT, constant=1.0)
     return geom, data
 
 
