@@ -27,11 +27,15 @@ import workloads as W  # noqa: E402
 
 METRIC = "WOS walk-steps/s & DtN patches/s vs plain FP64 path; p50/p99 query latency"
 N_TARGETS = 100_000
-# algorithmic thread-level ALU operations of one FP32 walk-step in the ball
-# region (half a Philox4x32-10 block: 10 rounds x (2 mul.hi + 2 mul.lo + 2 xor3
-# + 2 key adds) / 2 = 40; distance to the sphere 9; shell test 2; two 24-bit
-# uniforms 6; direction (z, s, sincospi) 17; position update 5)
-OPS_PER_STEP = 79
+# algorithmic thread-level ALU operations of the FP32 walk in the ball region.
+# Per step: half a Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 xor3 +
+# 2 key adds) / 2 = 30), two 24-bit uniforms 8, direction (z, 1 - z^2, sqrt,
+# azimuth reduction and sincos) 11, distance to the sphere 9, shell test and
+# step count 2, position update 4: 64.  Per walk: the score, projection onto the
+# sphere 8 + degree-8 harmonic data by solid-harmonic recurrences (45 (l, m)
+# pairs x 5 + 9 x 4) 261 + fixed-point terms 11: 280.
+OPS_PER_STEP = 64
+OPS_PER_WALK = 280
 SM_COUNT = 152
 LANES_PER_SM = 128
 
@@ -176,26 +180,39 @@ def cpu_baseline_sample(wl):
             "walk_steps_per_s": steps / dt}
 
 
-def run_serving(dtn, n_queries=32, seed=7, load=0.8):
-    """Continuous-batching server on the 200-wire geometry: queries of 1..64 patches
-    (log-uniform) with 512..4096 walks per node (log-uniform), first all at once
-    (saturated throughput), then as Poisson arrivals at `load` x that rate; returns
-    p50/p99 submit-to-result latency."""
+def run_serving(dtn, n_queries=32, seed=7, load=0.8, n_targets=100_000):
+    """Continuous-batching server on the 200-wire geometry (resident on the device).
+
+    Each query asks for the Neumann data at 1..4096 boundary points (log-uniform),
+    served by wire-face patches taken in turn until their panels cover that many
+    points, with 1024..16384 walks per hemisphere point (log-uniform).  The queries
+    are submitted first all at once (saturated throughput), then as Poisson
+    arrivals at `load` x that rate (p50/p99 submit-to-result latency), with an
+    8 GB device-memory admission budget.  Then the potential at 10^5 targets
+    outside the wires, by the integral representation over all served panels."""
+    import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     wl = W.wires(n_patches=4096, walks=2048)
     b = wl.batch
     g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
     opts = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=wl.epsilon, seed=wl.seed)
-    queries, start = [], 0
+    panels = (b.n_rings * b.n_sectors).astype(np.int64)
+    queries, start, points = [], 0, 0
     for _ in range(n_queries):
-        n = int(np.exp(rng.uniform(0.0, np.log(64.0))))
-        idx = (start + np.arange(n)) % b.n
-        start += n
-        walks = int(np.exp(rng.uniform(np.log(512.0), np.log(4096.0))))
+        want = int(np.exp(rng.uniform(0.0, np.log(4096.0))))
+        idx = []
+        got = 0
+        while got < want:
+            idx.append(start % b.n)
+            got += int(panels[start % b.n])
+            start += 1
+        idx = np.asarray(idx)
+        points += want
+        walks = int(np.exp(rng.uniform(np.log(1024.0), np.log(16384.0))))
         queries.append(dict(centers=b.centers[idx], radius=b.radius[idx], n_theta=b.n_theta[idx],
                             n_phi=b.n_phi[idx], n_rings=b.n_rings[idx], n_sectors=b.n_sectors[idx],
-                            walks=np.full(n, walks, np.int64), patch_ids=idx.astype(np.uint32)))
-    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024)
+                            walks=np.full(len(idx), walks, np.int64), patch_ids=idx.astype(np.uint32)))
+    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, memory_budget=8 << 30)
     # warm-up (first-use costs)
     srv.submit(**queries[0])
     srv.drain()
@@ -213,13 +230,88 @@ def run_serving(dtn, n_queries=32, seed=7, load=0.8):
         tickets.append(srv.submit(**q))
     srv.drain()
     t_poisson = time.perf_counter() - t0
-    lat = np.array([srv.poll(t)["latency_s"] for t in tickets]) * 1e3
+    served = [srv.poll(t) for t in tickets]
+    lat = np.array([r["latency_s"] for r in served]) * 1e3
     srv.close()
-    patches = int(sum(len(q["radius"]) for q in queries))
-    return {"geometry": "box [0,64]^2x[0,16] minus 200 wires", "queries": n_queries, "patches": patches,
-            "saturated_queries_per_s": n_queries / t_sat, "saturated_patches_per_s": patches / t_sat,
+    # potential at targets outside the wires, over every served panel: the panel
+    # geometry and data of the served patches (no walks), their served Neumann data
+    allq = {k: np.concatenate([q[k] for q in queries]) for k in queries[0]}
+    hb = dtn.HostBatch(allq["n_theta"], allq["n_phi"], allq["n_rings"], allq["n_sectors"], allq["walks"],
+                       patch_ids=allq["patch_ids"])
+    geo = dtn.alloc_result(hb)
+    geo["u_gamma_mean"].zero_()
+    dtn.solve_patches(g, allq["centers"], allq["radius"], hb, dtn.solve_opts(prec=dtn.PREC_MIXED, u_provided=True),
+                      result=geo)
+    q_served = torch.from_numpy(np.concatenate([r["neumann"] for r in served])).cuda()
+    boxes = np.asarray(wl.geometry.boxes)
+    tg = W.points_in_box(4 * n_targets, (0.0, 0.0, 0.0), (64.0, 64.0, 16.0), 0.05, seed=11)
+    outside = np.ones(len(tg), bool)
+    for bx in boxes:
+        outside &= ~np.all((tg >= bx[:3] - 0.05) & (tg <= bx[3:] + 0.05), axis=1)
+    tgt = torch.from_numpy(np.ascontiguousarray(tg[outside][:n_targets])).cuda()
+    u_t = torch.empty(tgt.shape[0], dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(3):
+        if k == 2:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        dtn.eval_potential(g, geo["colloc_xyz"], geo["normals"], geo["areas"], q_served, geo["dirichlet"], tgt,
+                           prec=dtn.PREC_MIXED, out=u_t)
+    e1.record(stream)
+    e1.synchronize()
+    pot_ms = e0.elapsed_time(e1)
+    n_pan = int(q_served.shape[0])
+    return {"geometry": "box [0,64]^2x[0,16] minus 200 wires", "queries": n_queries, "points": points,
+            "patches": int(len(allq["radius"])), "panels": n_pan,
+            "walks_per_node": "1024..16384 log-uniform per query",
+            "saturated_queries_per_s": n_queries / t_sat, "saturated_patches_per_s": len(allq["radius"]) / t_sat,
             "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "poisson_patches_per_s": patches / t_poisson}
+            "poisson_queries_per_s": n_queries / t_poisson,
+            "potential": {"targets": int(tgt.shape[0]), "panels": n_pan, "ms": pot_ms,
+                          "targets_per_s": tgt.shape[0] / (pot_ms / 1e3),
+                          "pair_terms_per_s": tgt.shape[0] * n_pan / (pot_ms / 1e3)}}
+
+
+def run_single_point(dtn, n_points=256, ng=20, walks=1000):
+    """The single-point method (Sec. 4.1) on the paper's two flat-boundary tests,
+    20 x 20 hemisphere and ring rules, 1000 walks per node (4e5 paths per point,
+    as in Tables 1 and 5), epsilon 1e-5, FP32 walks.  Test 1: the half space
+    above z = 0 with a unit charge at depth 1, a = 0.5, exact q = 0.71554 on the
+    circle of radius 0.5.  Test 4: outside the thin disk of radius 1 at potential
+    1, a = 0.4, exact density 0.735105 on the circle of radius 0.5 (the paper
+    times one point: 1218 s of CPU for 4e5 paths).  Device time of one call with
+    CUDA events, for n_points points on that circle and for the single point."""
+    import torch
+    ang = 2 * np.pi * np.arange(n_points) / n_points
+    circle = np.stack([0.5 * np.cos(ang), 0.5 * np.sin(ang), np.zeros(n_points)], 1)
+    opts = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-5, seed=0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, (geom, data), a, exact in (("test1_half_space", W.half_space_charge(), 0.5, 0.71554),
+                                         ("test4_thin_disk", W.thin_disk(), 0.4, 0.735105)):
+        g = dtn.Geometry.from_spec(geom).set_data_spec(data)
+        res = {"a": a, "exact": exact}
+        for tag, pts in (("points", circle), ("one_point", np.array([[-0.5, 0.0, 0.0]]))):
+            xd = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+            for k in range(3):
+                if k == 2:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                r = dtn.single_point_neumann(g, xd, a, ng, ng, 1e-6 * a, walks, opts)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            q = r["q"].cpu().numpy()
+            se = r["se"].cpu().numpy()
+            paths = len(pts) * ng * ng * walks
+            res[tag] = {"n": len(pts), "ms": ms, "paths_per_s": paths / (ms / 1e3),
+                        "q_mean": float(q.mean()), "rel_err_of_mean": float(q.mean() / exact - 1.0),
+                        "mean_se": float(se.mean()), "max_abs_z": float(np.max(np.abs(q - exact) / se))}
+        out[name] = res
+    out["setup"] = f"{ng}x{ng} hemisphere and ring rules, {walks} walks per node, eps 1e-5, FP32 walks, delta 1e-6 a"
+    return out
 
 
 def run_ours(args):
@@ -345,7 +437,8 @@ def run_ours(args):
     peaks = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # Tops/s
-    achieved = walk_steps * OPS_PER_STEP / (wos / 1e3) / 1e12
+    n_walks = int(np.sum(b.walks * (b.n_theta * b.n_phi)))
+    achieved = (walk_steps * OPS_PER_STEP + n_walks * OPS_PER_WALK) / (wos / 1e3) / 1e12
     # setup 3, walks + estimates 2; mixed: group matrices 1, right-side weights 3
     # (far, near, walk term), samples 1, products 1, group factors + solves 2;
     # FP64: matrices and right sides 1, factor + solve 1; gather 4, potential 1
@@ -366,7 +459,7 @@ def run_ours(args):
                       "speedup": value / plain},
         "roofline": {"bound": "alu", "kernel": "wos_kernel<float, ball>", "achieved": achieved,
                      "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
-                     "ops_per_walk_step": OPS_PER_STEP,
+                     "ops_per_walk_step": OPS_PER_STEP, "ops_per_walk": OPS_PER_WALK, "walks": n_walks,
                      "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"},
         "e2e": {"value": b.n * world / (e2e / 1e3), "unit": "patches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -376,6 +469,7 @@ def run_ours(args):
     }
     if not args.no_serve:
         line["serving"] = run_serving(dtn)
+        line["single_point"] = run_single_point(dtn)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(wl)
     if rank == 0:

@@ -59,17 +59,23 @@ typedef enum {
 typedef enum {
     DTN_GEOM_BALL_INTERIOR = 0,    /* |x - center| < radius */
     DTN_GEOM_BOX_INTERIOR = 1,     /* lo < x < hi */
-    DTN_GEOM_BOX_MINUS_BOXES = 2   /* outer box minus the closed obstacle boxes */
+    DTN_GEOM_BOX_MINUS_BOXES = 2,  /* outer box minus the closed obstacle boxes */
+    /* unbounded regions (Sec. 4.1.3): a walk that leaves the truncation sphere of
+       radius `truncation` about `center` has gone to infinity and scores 0 */
+    DTN_GEOM_HALF_SPACE = 3,       /* z > center[2] */
+    DTN_GEOM_DISK_EXTERIOR = 4     /* space outside the thin disk of radius `radius`
+                                      about `center` in the plane z = center[2] */
 } dtn_geom_kind;
 
 typedef struct {
     int32_t kind;                  /* dtn_geom_kind */
-    double center[3];              /* ball */
-    double radius;
+    double center[3];              /* ball; half space: a point of the plane; disk */
+    double radius;                 /* ball; disk */
     double lo[3], hi[3];           /* outer box */
     int32_t n_boxes;               /* obstacle boxes, disjoint, inside the outer box */
     const double *boxes;           /* host, n_boxes x 6 (lo xyz, hi xyz), copied */
     double cell_size;              /* obstacle lookup grid cell edge; <= 0 picks one */
+    double truncation;             /* unbounded regions: truncation radius (> radius) */
 } dtn_geometry_desc;
 
 /* Dirichlet data g on the boundary (Eq. bw01).  Each kind is the trace of a
@@ -233,6 +239,34 @@ dtn_status dtn_wos_points(const dtn_geometry *geom, int64_t n, const double *y,
                           const uint32_t *point_ids, const uint32_t *patch_ids,
                           const int64_t *walks, const dtn_solve_opts *opts, double *mean,
                           double *se, uint64_t *steps, uint32_t *capped, void *stream);
+
+/* Neumann data at single points of a flat boundary piece by the BIE-WOS formula
+ * of Sec. 4.1, Eq. bw64: q(x) = Sigma1' + Sigma2', where
+ *   Sigma1' = - sum_ij W_ij (3 cos th_i / (2 pi a^3)) (U_ij - g(x))   (Eq. bw65, bw83)
+ * over the ng1 x ng1 Gauss nodes th_i = (pi/4)(xi_i + 1), ph_j = pi (xi_j + 1)
+ * of the hemisphere of radius a about x (Eq. bw85), U_ij the walk estimates
+ * there (Eq. bw87, walks[i] walks per node), and
+ *   Sigma2' = -(1/2pi) int (1/rho^3 - 1/a^3) (g(y) - g(x)) ds_y      (Eq. bw68, bw82)
+ * over the annulus delta <= rho <= a of the plane about x, by the ng2 x ng2
+ * Gauss rule in (rho, angle).  The error of leaving out the disk of radius
+ * delta is O(delta) (Eq. bw81).
+ *   x: device n x 3 points, each on a plane face (box, box minus boxes, half
+ *      space; thin disk: its top face z = center[2], the side z > center[2], with
+ *      the ball's slice of the plane inside the disk) with the ball of radius a
+ *      meeting that face only; q = ∂u/∂n with n the outward normal of D.
+ *   walks: host int64 n, each in [2, 2^32); RNG point id = node index i*ng1 + j,
+ *      patch id = patch_id_base + point index (as dtn_wos_points).
+ *   ng1, ng2 in [1, 64]; 0 <= delta < a.
+ *   Outputs, device, n values each: q (required); sigma1, sigma2, se (standard
+ *      error of Sigma1'), status (DTN_OK, or DTN_E_UNSUPPORTED when x is not on
+ *      a supported flat piece, then q = 0) may be NULL; U (n x ng1^2 node
+ *      estimates) may be NULL.
+ *   Uses opts->prec, epsilon, seed, max_steps and the walk launch fields.
+ *   Asynchronous on `stream`; argument errors are returned before any work. */
+dtn_status dtn_single_point_neumann(dtn_geometry *geom, int64_t n, const double *x, double a, int32_t ng1,
+                                    int32_t ng2, double delta, const int64_t *walks, uint32_t patch_id_base,
+                                    const dtn_solve_opts *opts, double *sigma1, double *sigma2, double *q,
+                                    double *se, int32_t *status, double *U, void *stream);
 
 /* dtn_wos_points for callers that cannot allocate device memory.  (The paper
  * has no counterpart; this is a deployment variant.)  Some callers must not

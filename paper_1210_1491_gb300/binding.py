@@ -21,6 +21,8 @@ PREC_MIXED = 1
 GEOM_BALL_INTERIOR = 0
 GEOM_BOX_INTERIOR = 1
 GEOM_BOX_MINUS_BOXES = 2
+GEOM_HALF_SPACE = 3
+GEOM_DISK_EXTERIOR = 4
 
 DATA_POINT_SOURCE = 0
 DATA_HARMONIC_SH = 1
@@ -40,7 +42,7 @@ class DtnError(RuntimeError):
 class GeometryDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("center", C.c_double * 3), ("radius", C.c_double),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n_boxes", C.c_int32),
-                ("boxes", C.POINTER(C.c_double)), ("cell_size", C.c_double)]
+                ("boxes", C.POINTER(C.c_double)), ("cell_size", C.c_double), ("truncation", C.c_double)]
 
 
 class DirichletDesc(C.Structure):
@@ -91,7 +93,7 @@ EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "
            "dtn_distance", "dtn_philox4x32_10", "dtn_eval_dirichlet", "dtn_status_string",
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
            "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks",
-           "dtn_wos_points_noalloc"]
+           "dtn_wos_points_noalloc", "dtn_single_point_neumann"]
 
 _lib = None
 
@@ -127,6 +129,8 @@ def load(path: str = LIB_PATH):
         "dtn_stage_times": ([vp, C.POINTER(C.c_float)], i32),
         "dtn_autotune_walks": ([vp, C.POINTER(PatchBatch), C.POINTER(SolveOpts), C.POINTER(Tuning), vp], i32),
         "dtn_wos_points_noalloc": ([vp, i64, vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, vp, vp, vp], i32),
+        "dtn_single_point_neumann": ([vp, i64, vp, dbl, i32, i32, dbl, vp, C.c_uint32, C.POINTER(SolveOpts),
+                                      vp, vp, vp, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -200,7 +204,7 @@ class Geometry:
     """dtn_create_geometry / dtn_set_dirichlet / dtn_destroy_geometry."""
 
     def __init__(self, kind, center=(0, 0, 0), radius=1.0, lo=(0, 0, 0), hi=(1, 1, 1), boxes=None,
-                 cell_size=0.0):
+                 cell_size=0.0, truncation=0.0):
         L = load()
         d = GeometryDesc()
         d.kind = int(kind)
@@ -214,6 +218,7 @@ class Geometry:
             d.n_boxes = int(self._boxes.shape[0])
             d.boxes = self._boxes.ctypes.data_as(C.POINTER(C.c_double))
         d.cell_size = float(cell_size)
+        d.truncation = float(truncation)
         h = C.c_void_p()
         _check(L.dtn_create_geometry(C.byref(d), C.byref(h)), "dtn_create_geometry")
         self.handle = h
@@ -221,8 +226,8 @@ class Geometry:
 
     @classmethod
     def from_spec(cls, g, cell_size=0.0):
-        """From any object with kind/center/radius/lo/hi/boxes attributes."""
-        return cls(g.kind, g.center, g.radius, g.lo, g.hi, g.boxes, cell_size)
+        """From any object with kind/center/radius/lo/hi/boxes (and truncation) attributes."""
+        return cls(g.kind, g.center, g.radius, g.lo, g.hi, g.boxes, cell_size, getattr(g, "truncation", 0.0))
 
     def set_dirichlet(self, kind, x0=(0, 0, 0), strength=1.0, lmax=0, clm=None, center=(0, 0, 0),
                       scale=1.0, constant=0.0):
@@ -364,7 +369,7 @@ def gather_owned(colloc_xyz, owner, centers, stream=None):
     c = _dev(centers, torch.float64).reshape(-1, 3)
     keep = torch.empty(x.shape[0], dtype=torch.uint8, device="cuda")
     kept = torch.empty(x.shape[0], dtype=torch.int64, device="cuda")
-    nk = torch.zeros(1, dtype=torch.int64, device="cuda")
+    nk = torch.empty(1, dtype=torch.int64, device="cuda")   # written by the library
     _check(load().dtn_gather_owned(x.shape[0], _ptr(x), _ptr(o), c.shape[0], _ptr(c), _ptr(keep), _ptr(kept),
                                    _ptr(nk), _stream(stream)), "dtn_gather_owned")
     return keep, kept, nk
@@ -408,6 +413,29 @@ def wos_points_noalloc(geom: Geometry, y, point_ids, patch_ids, walks, opts: Sol
                                          _ptr(out["mean"]), _ptr(out.get("se")), _ptr(out.get("steps")),
                                          _ptr(out.get("capped")), _stream(stream)),
            "dtn_wos_points_noalloc")
+    return out
+
+
+def single_point_neumann(geom: Geometry, x, a, ng1, ng2, delta, walks, opts: SolveOpts, patch_id_base=0,
+                         want_nodes=False, stream=None):
+    """dtn_single_point_neumann: q = Sigma1' + Sigma2' at points x (n x 3) of flat
+    boundary pieces -> dict of device tensors (sigma1, sigma2, q, se, status, U)."""
+    xx = _dev(x, torch.float64).reshape(-1, 3)
+    n = xx.shape[0]
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(walks, dtype=np.int64), (n,)))
+    out = dict(sigma1=torch.empty(n, dtype=torch.float64, device="cuda"),
+               sigma2=torch.empty(n, dtype=torch.float64, device="cuda"),
+               q=torch.empty(n, dtype=torch.float64, device="cuda"),
+               se=torch.empty(n, dtype=torch.float64, device="cuda"),
+               status=torch.empty(n, dtype=torch.int32, device="cuda"))
+    if want_nodes:
+        out["U"] = torch.empty(n * int(ng1) * int(ng1), dtype=torch.float64, device="cuda")
+    _check(load().dtn_single_point_neumann(geom.handle, n, _ptr(xx), float(a), int(ng1), int(ng2), float(delta),
+                                           _ptr(w), int(patch_id_base), C.byref(opts), _ptr(out["sigma1"]),
+                                           _ptr(out["sigma2"]), _ptr(out["q"]), _ptr(out["se"]),
+                                           _ptr(out["status"]), _ptr(out.get("U")), _stream(stream)),
+           "dtn_single_point_neumann")
+    out["_keep"] = (xx, w)
     return out
 
 

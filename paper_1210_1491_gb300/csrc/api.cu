@@ -103,6 +103,11 @@ void build_grid(GeometryHost &h) {
 }
 
 double point_boundary_distance(const dtn_geometry_desc &d, const double *x) {
+    if (d.kind == DTN_GEOM_HALF_SPACE) return std::fabs(x[2] - d.center[2]);
+    if (d.kind == DTN_GEOM_DISK_EXTERIOR) {
+        const double r = std::hypot(x[0] - d.center[0], x[1] - d.center[1]), z = x[2] - d.center[2];
+        return r <= d.radius ? std::fabs(z) : std::hypot(r - d.radius, z);
+    }
     if (d.kind == DTN_GEOM_BALL_INTERIOR) {
         const double r = std::sqrt((x[0] - d.center[0]) * (x[0] - d.center[0]) + (x[1] - d.center[1]) * (x[1] - d.center[1]) +
                                    (x[2] - d.center[2]) * (x[2] - d.center[2]));
@@ -134,8 +139,10 @@ double score_bound(const dtn_geometry_desc &gd, const dtn_dirichlet_desc &dd) {
     if (dd.kind == DTN_DATA_HARMONIC_SH) {
         // farthest boundary point from the data centre
         double rmax = 0.0;
-        if (gd.kind == DTN_GEOM_BALL_INTERIOR) {
-            rmax = gd.radius + std::sqrt((gd.center[0] - dd.center[0]) * (gd.center[0] - dd.center[0]) +
+        if (gd.kind == DTN_GEOM_BALL_INTERIOR || gd.kind == DTN_GEOM_HALF_SPACE ||
+            gd.kind == DTN_GEOM_DISK_EXTERIOR) {
+            // (unbounded regions: the scored points lie within the truncation sphere)
+            rmax = (gd.kind == DTN_GEOM_BALL_INTERIOR ? gd.radius : gd.truncation) + std::sqrt((gd.center[0] - dd.center[0]) * (gd.center[0] - dd.center[0]) +
                                          (gd.center[1] - dd.center[1]) * (gd.center[1] - dd.center[1]) +
                                          (gd.center[2] - dd.center[2]) * (gd.center[2] - dd.center[2]));
         } else {
@@ -427,6 +434,10 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
     const dtn_geometry_desc &d = *desc;
     if (d.kind == DTN_GEOM_BALL_INTERIOR) {
         if (!(d.radius > 0)) return DTN_E_INVALID_ARG;
+    } else if (d.kind == DTN_GEOM_HALF_SPACE) {
+        if (!(d.truncation > 0)) return DTN_E_INVALID_ARG;
+    } else if (d.kind == DTN_GEOM_DISK_EXTERIOR) {
+        if (!(d.radius > 0) || !(d.truncation > d.radius)) return DTN_E_INVALID_ARG;
     } else if (d.kind == DTN_GEOM_BOX_INTERIOR || d.kind == DTN_GEOM_BOX_MINUS_BOXES) {
         for (int i = 0; i < 3; ++i)
             if (!(d.hi[i] > d.lo[i])) return DTN_E_INVALID_ARG;
@@ -471,6 +482,8 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
         dg.hi_f[i] = (float)dg.hi[i];
     }
     dg.R_f = (float)dg.R;
+    dg.trunc = d.truncation;
+    dg.trunc_f = (float)d.truncation;
     dg.nb = nb;
     dg.gn[0] = dg.gn[1] = dg.gn[2] = 1;
     dg.cell = 1.0;
@@ -527,7 +540,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
-                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec};
+                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp};
     for (DevBuf *b : bufs) b->release();
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
@@ -1009,6 +1022,97 @@ dtn_status dtn_wos_points(const dtn_geometry *gc, int64_t n, const double *y, co
     e = launch_wos(g, w, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors go out of scope
     return to_status(e);
+}
+
+dtn_status dtn_single_point_neumann(dtn_geometry *g, int64_t n, const double *x, double a, int32_t ng1, int32_t ng2,
+                                    double delta, const int64_t *walks, uint32_t patch_id_base,
+                                    const dtn_solve_opts *o, double *sigma1, double *sigma2, double *q, double *se,
+                                    int32_t *status, double *U, void *stream) {
+    if (!g || n < 0 || !o) return DTN_E_INVALID_ARG;
+    if (n == 0) return DTN_OK;
+    if (!x || !walks || !q || !(a > 0) || !(delta >= 0) || !(delta < a)) return DTN_E_INVALID_ARG;
+    if (ng1 < 1 || ng1 > kMaxGauss || ng2 < 1 || ng2 > kMaxGauss || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
+    if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    if (!g->has_data) return DTN_E_INVALID_ARG;
+    int64_t maxw = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (walks[i] < 2 || walks[i] > 0xFFFFFFFFll) return DTN_E_INVALID_ARG;
+        maxw = std::max(maxw, walks[i]);
+    }
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    const WalkParams wp = walk_params(g, o);
+    const int32_t chunk = wp.chunk;
+    const int64_t nn = (int64_t)ng1 * ng1, nodes = n * nn;
+    // walk layout: one group per point, its ng1^2 nodes
+    std::vector<int64_t> node_off(n + 1), chunk_off(n + 1, 0), wv(walks, walks + n);
+    std::vector<int32_t> cpn(n);
+    std::vector<uint32_t> pid(n);
+    std::vector<double> rad(n, a);
+    for (int64_t i = 0; i <= n; ++i) node_off[i] = i * nn;
+    for (int64_t i = 0; i < n; ++i) {
+        cpn[i] = (int32_t)((walks[i] + chunk - 1) / chunk);
+        chunk_off[i + 1] = chunk_off[i] + nn * cpn[i];
+        pid[i] = patch_id_base + (uint32_t)i;
+    }
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const size_t o_node = off; off = al(off + (n + 1) * 8);
+    const size_t o_chunk = off; off = al(off + (n + 1) * 8);
+    const size_t o_walk = off; off = al(off + n * 8);
+    const size_t o_cpn = off; off = al(off + n * 4);
+    const size_t o_pid = off; off = al(off + n * 4);
+    const size_t o_rad = off; off = al(off + n * 8);
+    const size_t host_bytes = off;
+    const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
+    const size_t o_y = off; off = al(off + nodes * 24);
+    const size_t o_wk = off; off = al(off + nodes * 8);
+    const size_t o_U = off; off = al(off + nodes * 8);
+    const size_t o_SE = off; off = al(off + nodes * 8);
+    cudaError_t e = g->ws.sp.reserve(off);
+    if (e != cudaSuccess) return to_status(e);
+    std::vector<unsigned char> h(host_bytes, 0);
+    std::memcpy(&h[o_node], node_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_chunk], chunk_off.data(), (n + 1) * 8);
+    std::memcpy(&h[o_walk], wv.data(), n * 8);
+    std::memcpy(&h[o_cpn], cpn.data(), n * 4);
+    std::memcpy(&h[o_pid], pid.data(), n * 4);
+    std::memcpy(&h[o_rad], rad.data(), n * 8);
+    char *base = g->ws.sp.as<char>();
+    if ((e = cudaMemcpyAsync(base, h.data(), host_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return to_status(e);
+    PatchFrame *frames = (PatchFrame *)(base + o_fr);
+    double *y = (double *)(base + o_y), *wk = (double *)(base + o_wk);
+    double *Ud = U ? U : (double *)(base + o_U);
+    double *SEd = (double *)(base + o_SE);
+    if ((e = launch_patch_frames(g, n, x, (const double *)(base + o_rad), frames, s)) != cudaSuccess ||
+        (e = launch_sp_nodes(n, ng1, frames, y, wk, s)) != cudaSuccess)
+        return to_status(e);
+    WosLaunch w{};
+    w.n_groups = n;
+    w.node_off = (const int64_t *)(base + o_node);
+    w.walks = (const int64_t *)(base + o_walk);
+    w.pid = (const uint32_t *)(base + o_pid);
+    w.point_id = nullptr;   // node index within the point
+    w.chunk_off = (const int64_t *)(base + o_chunk);
+    w.cpn = (const int32_t *)(base + o_cpn);
+    w.total_chunks = chunk_off[n];
+    w.total_nodes = nodes;
+    w.chunk = chunk;
+    w.max_walks = maxw;
+    w.y = y;
+    w.prec = o->prec;
+    w.eps = o->epsilon;
+    w.max_steps = o->max_steps ? o->max_steps : 1000000ull;
+    w.seed = o->seed;
+    w.blocks_per_sm = wp.bps;
+    w.refill = wp.refill;
+    w.mean = Ud;
+    w.se = SEd;
+    w.steps = nullptr;
+    w.capped = nullptr;
+    if ((e = launch_wos(g, w, s)) != cudaSuccess) return to_status(e);
+    return to_status(launch_sp_sigma(g, n, ng1, ng2, delta, frames, wk, Ud, SEd, sigma1, sigma2, q, se, status, s));
 }
 
 dtn_status dtn_distance(const dtn_geometry *g, int64_t n, const double *x, double *d, double *nearest, int32_t prec,

@@ -19,13 +19,25 @@ constexpr int kMaxSmemBoxes = 1024;       // obstacle boxes staged in shared mem
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // one 32 x 32 -> 64-bit product per multiplier gives both halves
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same generator with the ten round keys (k0 + r 9E3779B9, k1 + r BB67AE85)
+// given: from kernel parameters they are constant-bank operands of the xors.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r],
+                       (uint32_t)p0);
     }
     return c;
 }
@@ -40,13 +52,15 @@ __device__ __forceinline__ double u01_53(uint32_t hi, uint32_t lo) {
 }
 
 // ------------------------------------------------------------------ geometry
-enum GeomKind : int { kBall = 0, kBox = 1, kBoxMinusBoxes = 2 };
+enum GeomKind : int { kBall = 0, kBox = 1, kBoxMinusBoxes = 2, kHalfSpace = 3, kDiskExterior = 4 };
 
 struct DGeom {
     int kind;
     double c[3], R;          // ball
     double lo[3], hi[3];     // outer box
     float c_f[3], R_f, lo_f[3], hi_f[3];   // the same, rounded to FP32 on the host
+    double trunc;            // unbounded regions: truncation radius
+    float trunc_f;
     int nb;                  // obstacle boxes
     const double *boxes;     // nb x 6
     const float *boxes_f;    // nb x 6
@@ -120,6 +134,15 @@ __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z
         } else {
             return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
         }
+    } else if (GK == kHalfSpace) {
+        return z - pick<T>(g.c[2], g.c_f[2]);
+    } else if (GK == kDiskExterior) {
+        const T dx = x - pick<T>(g.c[0], g.c_f[0]), dy = y - pick<T>(g.c[1], g.c_f[1]),
+                dz = z - pick<T>(g.c[2], g.c_f[2]);
+        const T b = pick<T>(g.R, g.R_f);
+        const T r = sqrt(dx * dx + dy * dy);
+        if (r <= b) return fabs(dz);
+        return sqrt((r - b) * (r - b) + dz * dz);
     } else if (GK == kBox) {
         return box_interior_dist<T>(g, x, y, z);
     } else {
@@ -144,11 +167,40 @@ __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z
     }
 }
 
+// Unbounded regions: outside the truncation sphere a walk has gone to infinity.
+template <typename T>
+__device__ __forceinline__ bool geo_escaped(const DGeom &g, T x, T y, T z) {
+    const T dx = x - pick<T>(g.c[0], g.c_f[0]), dy = y - pick<T>(g.c[1], g.c_f[1]), dz = z - pick<T>(g.c[2], g.c_f[2]);
+    const T R = pick<T>(g.trunc, g.trunc_f);
+    return dx * dx + dy * dy + dz * dz > R * R;
+}
+
 // Nearest boundary point (the absorption point whose data are scored), exact
 // over the same candidates; ties take the lowest face index, the outer box
 // before obstacles, and obstacles in index order.
 template <typename T>
 __device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &ny, T &nz) {
+    if (g.kind == kHalfSpace) {
+        nx = x;
+        ny = y;
+        nz = pick<T>(g.c[2], g.c_f[2]);
+        return z - nz;
+    }
+    if (g.kind == kDiskExterior) {
+        const T cx = pick<T>(g.c[0], g.c_f[0]), cy = pick<T>(g.c[1], g.c_f[1]), cz = pick<T>(g.c[2], g.c_f[2]);
+        const T b = pick<T>(g.R, g.R_f);
+        const T dx = x - cx, dy = y - cy, dz = z - cz;
+        const T r = sqrt(dx * dx + dy * dy);
+        nz = cz;
+        if (r <= b) {
+            nx = x;
+            ny = y;
+            return fabs(dz);
+        }
+        nx = cx + b * dx / r;
+        ny = cy + b * dy / r;
+        return sqrt((r - b) * (r - b) + dz * dz);
+    }
     if (g.kind == kBall) {
         const T cx = pick<T>(g.c[0], g.c_f[0]), cy = pick<T>(g.c[1], g.c_f[1]), cz = pick<T>(g.c[2], g.c_f[2]);
         const T R = pick<T>(g.R, g.R_f);
@@ -333,6 +385,38 @@ __device__ __forceinline__ float harmonic_cart(const float2 *cs, int lmax, float
             t2 = t1;
             t1 = t;
             c = cs[k];
+            ac = fmaf(c.x, t, ac);
+            as = fmaf(c.y, t, as);
+        }
+        acc = fmaf(ac, C, fmaf(as, S, acc));
+    }
+    return acc;
+}
+
+// The same with the degree fixed at compile time (coefficients beyond the
+// data's lmax are zero in the pair table): every loop unrolls, so the
+// recurrence constants are immediate constant-bank operands.
+template <int L>
+__device__ __forceinline__ float harmonic_cart_fixed(const float2 *cs, float x, float y, float z) {
+    const float r2 = x * x + y * y + z * z;
+    float C = 1.f, S = 0.f, acc = 0.f;
+#pragma unroll
+    for (int m = 0; m <= L; ++m) {
+        if (m > 0) {
+            const float c2 = C * x - S * y;
+            S = fmaf(S, x, C * y);
+            C = c2;
+        }
+        float t2 = 0.f, t1 = c_sh.pmm[m];
+        float2 c = cs[sh_pair(m, m)];
+        float ac = c.x * t1, as = c.y * t1;
+#pragma unroll
+        for (int l = m + 1; l <= L; ++l) {
+            const float2 rc = c_sh.rec[sh_pair(l, m)];
+            const float t = rc.x * z * t1 - rc.y * r2 * t2;
+            t2 = t1;
+            t1 = t;
+            c = cs[sh_pair(l, m)];
             ac = fmaf(c.x, t, ac);
             as = fmaf(c.y, t, as);
         }

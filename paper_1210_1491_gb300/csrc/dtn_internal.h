@@ -96,6 +96,7 @@ struct Workspace {
     DevBuf gpiv;            // shared pivots, n per group
     DevBuf gw;              // right-side weights per weight group (FP32)
     DevBuf vec;             // per-patch samples (data at panel points, walk estimates), FP32
+    DevBuf sp;              // single-point method: frames, nodes, weights, estimates, walk layout
 };
 
 struct GeometryHost {
@@ -164,6 +165,16 @@ cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, cons
                                double *gamma_w, double *gamma_loc, double *colloc, double *normals,
                                double *areas, double *panel_loc, double *panel_prm, double *panel_aux,
                                double *panel_g, cudaStream_t s);
+
+cudaError_t launch_patch_frames(const dtn_geometry *g, int64_t n, const double *centers, const double *radius,
+                                PatchFrame *frames, cudaStream_t s);
+
+// single-point method (Sec. 4.1): hemisphere nodes with their Sigma1' weights,
+// then the two sums per point
+cudaError_t launch_sp_nodes(int64_t n, int ng1, const PatchFrame *frames, double *y, double *wk, cudaStream_t s);
+cudaError_t launch_sp_sigma(const dtn_geometry *g, int64_t n, int ng1, int ng2, double delta, const PatchFrame *frames,
+                            const double *wk, const double *U, const double *SE, double *sigma1, double *sigma2,
+                            double *q, double *se, int32_t *status, cudaStream_t s);
 
 struct WosLaunch {
     int64_t n_groups;

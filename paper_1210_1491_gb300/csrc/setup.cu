@@ -133,7 +133,17 @@ __global__ void patch_frame_kernel(DGeom g, int64_t n, const double *__restrict_
     f.status = DTN_OK;
     f.R = 0.0;
     if (!(a > 0.0)) f.status = DTN_E_INVALID_ARG;
-    if (g.kind == kBall) {
+    if (g.kind == kHalfSpace || g.kind == kDiskExterior) {
+        // the plane z = c_z (half space: the region above it; thin disk: its top
+        // face, with the ball's slice of the plane inside the disk)
+        if (!(fabs(c[2] - g.c[2]) <= 1e-9 * fmax(1.0, fabs(g.c[2])))) f.status = DTN_E_UNSUPPORTED;
+        if (g.kind == kDiskExterior && !(sqrt((c[0] - g.c[0]) * (c[0] - g.c[0]) + (c[1] - g.c[1]) * (c[1] - g.c[1])) + a < g.R))
+            f.status = DTN_E_UNSUPPORTED;
+        f.n[0] = 0.0; f.n[1] = 0.0; f.n[2] = -1.0;
+        f.kind = kDisk;
+        f.theta_max = 0.5 * kPi;
+        f.umax = a;
+    } else if (g.kind == kBall) {
         const double v[3] = {c[0] - g.c[0], c[1] - g.c[1], c[2] - g.c[2]};
         const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         if (!(fabs(r - g.R) <= 1e-9 * g.R) || !(a < 2.0 * g.R)) f.status = DTN_E_UNSUPPORTED;
@@ -288,6 +298,14 @@ __global__ void panels_kernel(DData dat, int64_t n_patches, int64_t total, const
 }
 
 }  // namespace
+
+cudaError_t launch_patch_frames(const dtn_geometry *g, int64_t n, const double *centers, const double *radius,
+                                PatchFrame *frames, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int T = 128;
+    patch_frame_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dg, n, centers, radius, frames);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
                                const double *centers, double *gamma_xyz,

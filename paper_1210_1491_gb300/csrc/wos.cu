@@ -49,8 +49,19 @@ struct WosDev {
     int lgM1, lgM2;        // ceil(log2) of the score bound and of its square
     double eps;
     uint32_t max_steps;
-    uint32_t k0, k1;
+    uint32_t rk0[10], rk1[10];   // Philox round keys from the seed
 };
+
+// the round keys of Philox4x32-10 for a 64-bit seed
+inline void philox_round_keys(uint64_t seed, uint32_t *rk0, uint32_t *rk1) {
+    uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk0[r] = k0;
+        rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // Fixed-point exponent of a node's sums: |sum over W walks| <= W * bound < 2^61,
 // so F = 61 - ceil(log2 W) - ceil(log2 bound).  It depends only on the node's own
@@ -115,7 +126,10 @@ __device__ __forceinline__ T walk_data(const DData &d, const float2 *cs, T x, T 
     if constexpr (sizeof(T) == 4) {
         if (d.kind == kHarmonicSH) {
             const float is = d.inv_scale_f;
-            return harmonic_cart(cs, d.lmax, (x - d.ctr_f[0]) * is, (y - d.ctr_f[1]) * is, (z - d.ctr_f[2]) * is);
+            const float xs = (x - d.ctr_f[0]) * is, ys = (y - d.ctr_f[1]) * is, zs = (z - d.ctr_f[2]) * is;
+            if (d.lmax <= 4) return harmonic_cart_fixed<4>(cs, xs, ys, zs);
+            if (d.lmax <= 8) return harmonic_cart_fixed<8>(cs, xs, ys, zs);
+            return harmonic_cart(cs, d.lmax, xs, ys, zs);
         }
     }
     return dirichlet_eval<T>(d, x, y, z);
@@ -191,7 +205,7 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 __device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t w1, uint32_t w2) {
     const float u1 = u01_24(w1), u2 = u01_24(w2);
     const float zz = fmaf(-2.0f, u1, 1.0f);
-    const float t = (1.0f - zz) * (1.0f + zz);
+    const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
     const float s = t * rsqrtf(t);
     const float a = 6.2831853071795865f * (u2 > 0.5f ? u2 - 1.0f : u2);
     float sn, cs;
@@ -321,9 +335,13 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
             if (active) {
                 if constexpr (std::is_same<T, float>::value) {
                     // two jumps from one Philox block
-                    const uint4 w = philox4x32_10(make_uint4(walk, step >> 1, ppt, ppid), P.k0, P.k1);
+                    const uint4 w = philox4x32_10_rk(make_uint4(walk, step >> 1, ppt, ppid), P.rk0, P.rk1);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
+                        if (active && (GK == kHalfSpace || GK == kDiskExterior) && geo_escaped<T>(P.g, x, y, z)) {
+                            acc.st += step;   // gone to infinity: scores 0
+                            active = false;
+                        }
                         if (active) {
                             const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                             ++step;
@@ -340,6 +358,9 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                             }
                         }
                     }
+                } else if ((GK == kHalfSpace || GK == kDiskExterior) && geo_escaped<T>(P.g, x, y, z)) {
+                    acc.st += step;   // gone to infinity: scores 0
+                    active = false;
                 } else {
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     ++step;
@@ -352,7 +373,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                         acc.cap += 1;
                         active = false;
                     } else {
-                        const uint4 w = philox4x32_10(make_uint4(walk, step - 1, ppt, ppid), P.k0, P.k1);
+                        const uint4 w = philox4x32_10_rk(make_uint4(walk, step - 1, ppt, ppid), P.rk0, P.rk1);
                         jump(x, y, z, d, w);
                     }
                 }
@@ -409,6 +430,8 @@ template <typename T>
 void *wos_kernel_ptr(int gk) {
     if (gk == kBall) return (void *)wos_kernel<T, kBall>;
     if (gk == kBox) return (void *)wos_kernel<T, kBox>;
+    if (gk == kHalfSpace) return (void *)wos_kernel<T, kHalfSpace>;
+    if (gk == kDiskExterior) return (void *)wos_kernel<T, kDiskExterior>;
     return (void *)wos_kernel<T, kBoxMinusBoxes>;
 }
 
@@ -453,8 +476,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     P.lgM2 = lgM2;
     P.eps = w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
-    P.k0 = (uint32_t)(w.seed & 0xFFFFFFFFull);
-    P.k1 = (uint32_t)(w.seed >> 32);
+    philox_round_keys(w.seed, P.rk0, P.rk1);
 
     const int gk = g->dg.kind;
     const bool fp32 = (w.prec == DTN_PREC_MIXED);
@@ -526,8 +548,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
     P.lgM2 = lgM2;
     P.eps = w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
-    P.k0 = (uint32_t)(w.seed & 0xFFFFFFFFull);
-    P.k1 = (uint32_t)(w.seed >> 32);
+    philox_round_keys(w.seed, P.rk0, P.rk1);
     const int gk = g->dg.kind;
     const bool fp32 = (w.prec == DTN_PREC_MIXED);
     void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
@@ -585,6 +606,8 @@ __global__ void distance_kernel(DGeom g, int64_t n, const double *__restrict__ x
     T dist;
     if (g.kind == kBall) dist = geo_dist<T, kBall>(g, (const T *)sb, px, py, pz);
     else if (g.kind == kBox) dist = geo_dist<T, kBox>(g, (const T *)sb, px, py, pz);
+    else if (g.kind == kHalfSpace) dist = geo_dist<T, kHalfSpace>(g, (const T *)sb, px, py, pz);
+    else if (g.kind == kDiskExterior) dist = geo_dist<T, kDiskExterior>(g, (const T *)sb, px, py, pz);
     else dist = geo_dist<T, kBoxMinusBoxes>(g, (const T *)sb, px, py, pz);
     if (d) d[i] = (double)dist;
     if (nb) {
