@@ -63,8 +63,9 @@ typedef enum {
     /* unbounded regions (Sec. 4.1.3): a walk that leaves the truncation sphere of
        radius `truncation` about `center` has gone to infinity and scores 0 */
     DTN_GEOM_HALF_SPACE = 3,       /* z > center[2] */
-    DTN_GEOM_DISK_EXTERIOR = 4     /* space outside the thin disk of radius `radius`
+    DTN_GEOM_DISK_EXTERIOR = 4,    /* space outside the thin disk of radius `radius`
                                       about `center` in the plane z = center[2] */
+    DTN_GEOM_BALL_EXTERIOR = 5     /* |x - center| > radius */
 } dtn_geom_kind;
 
 typedef struct {

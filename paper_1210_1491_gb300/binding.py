@@ -23,6 +23,7 @@ GEOM_BOX_INTERIOR = 1
 GEOM_BOX_MINUS_BOXES = 2
 GEOM_HALF_SPACE = 3
 GEOM_DISK_EXTERIOR = 4
+GEOM_BALL_EXTERIOR = 5
 
 DATA_POINT_SOURCE = 0
 DATA_HARMONIC_SH = 1

@@ -108,7 +108,7 @@ double point_boundary_distance(const dtn_geometry_desc &d, const double *x) {
         const double r = std::hypot(x[0] - d.center[0], x[1] - d.center[1]), z = x[2] - d.center[2];
         return r <= d.radius ? std::fabs(z) : std::hypot(r - d.radius, z);
     }
-    if (d.kind == DTN_GEOM_BALL_INTERIOR) {
+    if (d.kind == DTN_GEOM_BALL_INTERIOR || d.kind == DTN_GEOM_BALL_EXTERIOR) {
         const double r = std::sqrt((x[0] - d.center[0]) * (x[0] - d.center[0]) + (x[1] - d.center[1]) * (x[1] - d.center[1]) +
                                    (x[2] - d.center[2]) * (x[2] - d.center[2]));
         return std::fabs(d.radius - r);
@@ -140,7 +140,7 @@ double score_bound(const dtn_geometry_desc &gd, const dtn_dirichlet_desc &dd) {
         // farthest boundary point from the data centre
         double rmax = 0.0;
         if (gd.kind == DTN_GEOM_BALL_INTERIOR || gd.kind == DTN_GEOM_HALF_SPACE ||
-            gd.kind == DTN_GEOM_DISK_EXTERIOR) {
+            gd.kind == DTN_GEOM_DISK_EXTERIOR || gd.kind == DTN_GEOM_BALL_EXTERIOR) {
             // (unbounded regions: the scored points lie within the truncation sphere)
             rmax = (gd.kind == DTN_GEOM_BALL_INTERIOR ? gd.radius : gd.truncation) + std::sqrt((gd.center[0] - dd.center[0]) * (gd.center[0] - dd.center[0]) +
                                          (gd.center[1] - dd.center[1]) * (gd.center[1] - dd.center[1]) +
@@ -436,7 +436,7 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
         if (!(d.radius > 0)) return DTN_E_INVALID_ARG;
     } else if (d.kind == DTN_GEOM_HALF_SPACE) {
         if (!(d.truncation > 0)) return DTN_E_INVALID_ARG;
-    } else if (d.kind == DTN_GEOM_DISK_EXTERIOR) {
+    } else if (d.kind == DTN_GEOM_DISK_EXTERIOR || d.kind == DTN_GEOM_BALL_EXTERIOR) {
         if (!(d.radius > 0) || !(d.truncation > d.radius)) return DTN_E_INVALID_ARG;
     } else if (d.kind == DTN_GEOM_BOX_INTERIOR || d.kind == DTN_GEOM_BOX_MINUS_BOXES) {
         for (int i = 0; i < 3; ++i)
@@ -641,7 +641,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     std::lock_guard<std::mutex> lk(g->mu);
     cudaStream_t s = (cudaStream_t)stream;
     BatchLayout L;
-    dtn_status st = build_layout(b, L, g->dg.kind == kBall);
+    dtn_status st = build_layout(b, L, g->dg.kind == kBall || g->dg.kind == kBallExterior);
     if (st != DTN_OK) return st;
     const WalkParams wp = walk_params(g, o);
     const int32_t chunk = wp.chunk;
@@ -841,7 +841,7 @@ dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const d
     sb.n_patches = n;
     sb.walks_per_point = walks.data();
     BatchLayout L;
-    dtn_status st = build_layout(&sb, L, g->dg.kind == kBall);
+    dtn_status st = build_layout(&sb, L, g->dg.kind == kBall || g->dg.kind == kBallExterior);
     if (st != DTN_OK) return st;
     DevLayout D;
     int64_t total_chunks = 0;

@@ -896,7 +896,7 @@ cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const
     Wd.glx = gl_x_dev();
     Wd.glw = gl_w_dev();
     const unsigned rows = (unsigned)L.wrows_total;
-    if (g->dg.kind == kBall) {
+    if (g->dg.kind == kBall || g->dg.kind == kBallExterior) {
         const unsigned tb = (unsigned)((L.max_wgroup_rows * kSampleN + kWtThreads - 1) / kWtThreads);
         rhs_far_weights_kernel<<<dim3(rows, tb), kWtThreads, 0, s>>>(Wd);
         rhs_near_weights_kernel<<<rows, 32 * kNearWarps, 0, s>>>(Wd);

@@ -52,7 +52,10 @@ __device__ __forceinline__ double u01_53(uint32_t hi, uint32_t lo) {
 }
 
 // ------------------------------------------------------------------ geometry
-enum GeomKind : int { kBall = 0, kBox = 1, kBoxMinusBoxes = 2, kHalfSpace = 3, kDiskExterior = 4 };
+enum GeomKind : int { kBall = 0, kBox = 1, kBoxMinusBoxes = 2, kHalfSpace = 3, kDiskExterior = 4, kBallExterior = 5 };
+
+// regions whose walks can leave for infinity (through the truncation sphere)
+__host__ __device__ constexpr bool unbounded(int gk) { return gk == 3 || gk == 4 || gk == 5; }
 
 struct DGeom {
     int kind;
@@ -124,16 +127,18 @@ __device__ __forceinline__ int grid_cell(const DGeom &g, T x, T y, T z) {
 
 template <typename T, int GK>
 __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z) {
-    if (GK == kBall) {
+    if (GK == kBall || GK == kBallExterior) {
         const T dx = x - pick<T>(g.c[0], g.c_f[0]), dy = y - pick<T>(g.c[1], g.c_f[1]),
                 dz = z - pick<T>(g.c[2], g.c_f[2]);
+        T r;
         if constexpr (sizeof(T) == 4) {
             // SFU reciprocal square root: |x| to a few FP32 ulps
             const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
-            return g.R_f - r2 * rsqrtf(r2);
+            r = r2 * rsqrtf(r2);
         } else {
-            return (T)g.R - sqrt(dx * dx + dy * dy + dz * dz);
+            r = sqrt(dx * dx + dy * dy + dz * dz);
         }
+        return GK == kBall ? pick<T>(g.R, g.R_f) - r : r - pick<T>(g.R, g.R_f);
     } else if (GK == kHalfSpace) {
         return z - pick<T>(g.c[2], g.c_f[2]);
     } else if (GK == kDiskExterior) {
@@ -201,7 +206,7 @@ __device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &n
         ny = cy + b * dy / r;
         return sqrt((r - b) * (r - b) + dz * dz);
     }
-    if (g.kind == kBall) {
+    if (g.kind == kBall || g.kind == kBallExterior) {
         const T cx = pick<T>(g.c[0], g.c_f[0]), cy = pick<T>(g.c[1], g.c_f[1]), cz = pick<T>(g.c[2], g.c_f[2]);
         const T R = pick<T>(g.R, g.R_f);
         const T dx = x - cx, dy = y - cy, dz = z - cz;
@@ -220,7 +225,7 @@ __device__ T geo_nearest(const DGeom &g, const T *sb, T x, T y, T z, T &nx, T &n
         } else {
             nx = cx; ny = cy; nz = cz + R;
         }
-        return R - r;
+        return g.kind == kBall ? R - r : r - R;
     }
     const T xs[3] = {x, y, z};
     T best = (T)INFINITY;

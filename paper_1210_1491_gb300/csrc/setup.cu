@@ -143,6 +143,18 @@ __global__ void patch_frame_kernel(DGeom g, int64_t n, const double *__restrict_
         f.kind = kDisk;
         f.theta_max = 0.5 * kPi;
         f.umax = a;
+    } else if (g.kind == kBallExterior) {
+        // outside a sphere: the region's outward normal points into the sphere,
+        // whose centre lies at c + R n; the cap takes the signed radius -R
+        const double v[3] = {c[0] - g.c[0], c[1] - g.c[1], c[2] - g.c[2]};
+        const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (!(fabs(r - g.R) <= 1e-9 * g.R) || !(a < 2.0 * g.R)) f.status = DTN_E_UNSUPPORTED;
+        const double rr = r > 0.0 ? r : 1.0;
+        for (int i = 0; i < 3; ++i) f.n[i] = -v[i] / rr;
+        f.kind = kCap;
+        f.R = -g.R;
+        f.theta_max = kPi - acos(fmin(1.0, a / (2.0 * g.R)));
+        f.umax = 2.0 * asin(fmin(1.0, a / (2.0 * g.R)));
     } else if (g.kind == kBall) {
         const double v[3] = {c[0] - g.c[0], c[1] - g.c[1], c[2] - g.c[2]};
         const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                     const uint4 w = philox4x32_10_rk(make_uint4(walk, step >> 1, ppt, ppid), P.rk0, P.rk1);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        if (active && (GK == kHalfSpace || GK == kDiskExterior) && geo_escaped<T>(P.g, x, y, z)) {
+                        if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                             acc.st += step;   // gone to infinity: scores 0
                             active = false;
                         }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                             }
                         }
                     }
-                } else if ((GK == kHalfSpace || GK == kDiskExterior) && geo_escaped<T>(P.g, x, y, z)) {
+                } else if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                     acc.st += step;   // gone to infinity: scores 0
                     active = false;
                 } else {
@@ -432,6 +432,7 @@ void *wos_kernel_ptr(int gk) {
     if (gk == kBox) return (void *)wos_kernel<T, kBox>;
     if (gk == kHalfSpace) return (void *)wos_kernel<T, kHalfSpace>;
     if (gk == kDiskExterior) return (void *)wos_kernel<T, kDiskExterior>;
+    if (gk == kBallExterior) return (void *)wos_kernel<T, kBallExterior>;
     return (void *)wos_kernel<T, kBoxMinusBoxes>;
 }
 
@@ -608,6 +609,7 @@ __global__ void distance_kernel(DGeom g, int64_t n, const double *__restrict__ x
     else if (g.kind == kBox) dist = geo_dist<T, kBox>(g, (const T *)sb, px, py, pz);
     else if (g.kind == kHalfSpace) dist = geo_dist<T, kHalfSpace>(g, (const T *)sb, px, py, pz);
     else if (g.kind == kDiskExterior) dist = geo_dist<T, kDiskExterior>(g, (const T *)sb, px, py, pz);
+    else if (g.kind == kBallExterior) dist = geo_dist<T, kBallExterior>(g, (const T *)sb, px, py, pz);
     else dist = geo_dist<T, kBoxMinusBoxes>(g, (const T *)sb, px, py, pz);
     if (d) d[i] = (double)dist;
     if (nb) {
