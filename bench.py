@@ -28,13 +28,14 @@ import workloads as W  # noqa: E402
 METRIC = "WOS walk-steps/s & DtN patches/s vs plain FP64 path; p50/p99 query latency"
 N_TARGETS = 100_000
 # algorithmic thread-level ALU operations of the FP32 walk in the ball region.
-# Per step: half a Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 xor3 +
-# 2 key adds) / 2 = 30), two 24-bit uniforms 8, direction (z, 1 - z^2, sqrt,
-# azimuth reduction and sincos) 11, distance to the sphere 9, shell test and
-# step count 2, position update 4: 64.  Per walk: the score, projection onto the
-# sphere 8 + degree-8 harmonic data by solid-harmonic recurrences (45 (l, m)
-# pairs x 5 + 9 x 4) 261 + fixed-point terms 11: 280.
-OPS_PER_STEP = 64
+# Per step: a third of a Philox4x32-10 block (10 rounds x (2 wide multiplies +
+# 2 xor3 + 2 key adds) / 3 = 20) and of its split into six 21-bit fields
+# (10 / 3 = 3), two uniforms 6, direction (z, 1 - z^2, sqrt, azimuth reduction
+# and sincos) 11, distance to the sphere 9, shell test and step count 2,
+# position update 4: 55.  Per walk: the score, projection onto the sphere 8 +
+# degree-8 harmonic data by solid-harmonic recurrences (45 (l, m) pairs x 5 +
+# 9 x 4) 261 + fixed-point terms 11: 280.
+OPS_PER_STEP = 55
 OPS_PER_WALK = 280
 SM_COUNT = 152
 LANES_PER_SM = 128

@@ -56,8 +56,19 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* 24-bit uniform: the odd integer ((w >> 8) | 1) times 2^-24, in (0,1). */
-double or_u01_24(uint32_t w) { return (double)((w >> 8) | 1u) * 0x1p-24; }
+/* 21-bit uniform: the odd integer 2f + 1 times 2^-22, in (0,1), for a 21-bit
+ * field f of a Philox block. */
+double or_u01_21(uint32_t f) { return (double)(2u * (f & 0x1fffffu) + 1u) * 0x1p-22; }
+
+/* The six 21-bit fields of one Philox block w[0..3]: the top 21 bits of each
+ * word, then the low 11 bits of w[0] with the low 10 bits of w[1] above them,
+ * and the same of w[2], w[3]. */
+void or_fields21(const uint32_t w[4], uint32_t f[6])
+{
+    for (int i = 0; i < 4; ++i) f[i] = w[i] >> 11;
+    f[4] = (w[0] & 0x7ffu) | ((w[1] & 0x3ffu) << 11);
+    f[5] = (w[2] & 0x7ffu) | ((w[3] & 0x3ffu) << 11);
+}
 
 /* 53-bit uniform from two words: the odd integer (hi<<21 | lo>>11) | 1 times 2^-53. */
 double or_u01_53(uint32_t hi, uint32_t lo)
@@ -308,8 +319,9 @@ typedef struct {
     uint64_t seed;       /* Philox key = (seed lo32, seed hi32) */
     uint64_t max_steps;  /* distance evaluations per walk before a walk is cut */
     int stream;          /* 0: one Philox call per jump, 53-bit uniforms from words (0,1),(2,3)
-                            1: one Philox call per two jumps, 24-bit uniforms; jump j uses
-                               counter (walk, j>>1, point, patch), words (0,1) if j even, (2,3) if odd */
+                            1: one Philox call per three jumps, 21-bit uniforms; jump j uses
+                               counter (walk, j/3, point, patch) and fields (2m, 2m+1), m = j%3,
+                               of or_fields21 */
     int score;           /* 0: g at the nearest boundary point; 1: the data function at the
                             absorption point itself (martingale diagnostic) */
 } or_wos_opts;
@@ -349,10 +361,13 @@ int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t wa
             u1 = or_u01_53(w[0], w[1]);
             u2 = or_u01_53(w[2], w[3]);
         } else {
-            uint32_t ctr[4] = {walk, (uint32_t)(j >> 1), point, patch};
+            uint32_t ctr[4] = {walk, (uint32_t)(j / 3), point, patch};
             or_philox4x32_10(ctr, key, w);
-            if ((j & 1) == 0) { u1 = or_u01_24(w[0]); u2 = or_u01_24(w[1]); }
-            else { u1 = or_u01_24(w[2]); u2 = or_u01_24(w[3]); }
+            uint32_t f[6];
+            or_fields21(w, f);
+            int m = (int)(j % 3);
+            u1 = or_u01_21(f[2 * m]);
+            u2 = or_u01_21(f[2 * m + 1]);
         }
         /* uniform direction on the unit sphere: z uniform in (-1,1), azimuth uniform */
         double z = 1.0 - 2.0 * u1;

@@ -46,7 +46,7 @@ class OrPatch(C.Structure):
 
 
 STREAM_F64 = 0   # one Philox call per jump, 53-bit uniforms
-STREAM_F32 = 1   # one Philox call per two jumps, 24-bit uniforms
+STREAM_F32 = 1   # one Philox call per three jumps, 21-bit uniforms
 
 
 def lib():
@@ -55,8 +55,9 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
-        L.or_u01_24.argtypes = [C.c_uint32]
-        L.or_u01_24.restype = C.c_double
+        L.or_u01_21.argtypes = [C.c_uint32]
+        L.or_u01_21.restype = C.c_double
+        L.or_fields21.argtypes = [_u32p, _u32p]
         L.or_u01_53.argtypes = [C.c_uint32, C.c_uint32]
         L.or_u01_53.restype = C.c_double
         L.or_gauss_legendre.argtypes = [C.c_int, _f64p, _f64p]
@@ -170,8 +171,16 @@ def philox(ctr, key) -> np.ndarray:
     return out
 
 
-def u01_24(w: int) -> float:
-    return lib().or_u01_24(int(w) & 0xFFFFFFFF)
+def u01_21(f: int) -> float:
+    return lib().or_u01_21(int(f) & 0xFFFFFFFF)
+
+
+def fields21(w) -> np.ndarray:
+    """or_fields21: the six 21-bit fields of one Philox block."""
+    ww = np.ascontiguousarray(w, dtype=np.uint32)
+    f = np.zeros(6, dtype=np.uint32)
+    lib().or_fields21(ww, f)
+    return f
 
 
 def u01_53(hi: int, lo: int) -> float:

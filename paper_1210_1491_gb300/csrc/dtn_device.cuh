@@ -43,9 +43,6 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk0, 
 }
 
 // Uniforms in (0,1), never 0 or 1: an odd integer times a power of two.
-__device__ __forceinline__ float u01_24(uint32_t w) {
-    return __uint2float_rn((w >> 8) | 1u) * 0x1p-24f;
-}
 __device__ __forceinline__ double u01_53(uint32_t hi, uint32_t lo) {
     const unsigned long long v = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
     return __ull2double_rn(v | 1ull) * 0x1p-53;

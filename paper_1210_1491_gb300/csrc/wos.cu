@@ -15,10 +15,12 @@
 //
 // Random numbers: Philox4x32-10 keyed by the seed.  FP64 walks draw one block
 // per jump, counter (walk, j, point, patch), 53-bit uniforms from words (0,1)
-// and (2,3).  FP32 walks draw one block per two jumps, counter
-// (walk, j >> 1, point, patch), 24-bit uniforms from words (0,1) for even j and
-// (2,3) for odd j; each loop iteration of an FP32 walk therefore makes two
-// jumps from one block.
+// and (2,3).  FP32 walks draw one block per three jumps, counter
+// (walk, j / 3, point, patch): the block's six 21-bit fields (the top 21 bits
+// of each word, then the low 11 bits of words 0 and 2 with the low 10 bits of
+// words 1 and 3 above them) give the uniforms (2f + 1) 2^-22 of jump j % 3
+// from fields (2 (j % 3), 2 (j % 3) + 1); each loop iteration of an FP32 walk
+// makes three jumps from one block.
 #include <cmath>
 #include <type_traits>
 
@@ -199,11 +201,12 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 
 // one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
 // z uniform in (-1, 1), azimuth 2 pi u2
-// FP32 walks: the azimuth 2 pi u2 is reduced to (-pi, pi] (the same angle mod
-// 2 pi) and taken by the SFU sine/cosine; s = sqrt(1 - z^2) by the SFU
-// reciprocal square root (1 - z^2 >= 4 * 2^-24 > 0 for the 24-bit uniforms).
-__device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t w1, uint32_t w2) {
-    const float u1 = u01_24(w1), u2 = u01_24(w2);
+// FP32 walks: uniforms (2f + 1) 2^-22 from 21-bit fields; the azimuth 2 pi u2 is
+// reduced to (-pi, pi] (the same angle mod 2 pi) and taken by the SFU
+// sine/cosine; s = sqrt(1 - z^2) by the SFU reciprocal square root
+// (1 - z^2 >= 2^-20 > 0 for these uniforms).
+__device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
+    const float u1 = __uint2float_rn(2u * f1 + 1u) * 0x1p-22f, u2 = __uint2float_rn(2u * f2 + 1u) * 0x1p-22f;
     const float zz = fmaf(-2.0f, u1, 1.0f);
     const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
     const float s = t * rsqrtf(t);
@@ -334,10 +337,13 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
         for (;;) {
             if (active) {
                 if constexpr (std::is_same<T, float>::value) {
-                    // two jumps from one Philox block
-                    const uint4 w = philox4x32_10_rk(make_uint4(walk, step >> 1, ppt, ppid), P.rk0, P.rk1);
+                    // three jumps from one Philox block
+                    const uint4 w = philox4x32_10_rk(make_uint4(walk, step / 3u, ppt, ppid), P.rk0, P.rk1);
+                    const uint32_t f[6] = {w.x >> 11, w.y >> 11, w.z >> 11, w.w >> 11,
+                                           (w.x & 0x7ffu) | ((w.y & 0x3ffu) << 11),
+                                           (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
+                    for (int h = 0; h < 3; ++h) {
                         if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                             acc.st += step;   // gone to infinity: scores 0
                             active = false;
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                                 acc.cap += 1;
                                 active = false;
                             } else {
-                                jump(x, y, z, d, h == 0 ? w.x : w.z, h == 0 ? w.y : w.w);
+                                jump(x, y, z, d, f[2 * h], f[2 * h + 1]);
                             }
                         }
                     }

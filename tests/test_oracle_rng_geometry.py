@@ -34,16 +34,37 @@ def test_philox_known_answers(ctr, key, out):
 
 
 def test_uniform_conversions_open_interval_and_grid():
-    assert O.u01_24(0) == 2.0 ** -24
-    assert O.u01_24(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    assert O.u01_21(0) == 2.0 ** -22
+    assert O.u01_21(0x1FFFFF) == 1.0 - 2.0 ** -22
     assert O.u01_53(0, 0) == 2.0 ** -53
     assert O.u01_53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
     rng = np.random.default_rng(1)
-    for w in rng.integers(0, 2 ** 32, 200):
-        u = O.u01_24(int(w))
-        k = u * 2 ** 24
-        assert 0.0 < u < 1.0 and k == int(k) and int(k) % 2 == 1
-        assert int(k) >> 1 == int(w) >> 9
+    for f in rng.integers(0, 2 ** 21, 200):
+        u = O.u01_21(int(f))
+        k = u * 2 ** 22
+        assert 0.0 < u < 1.0 and k == int(k) and int(k) == 2 * int(f) + 1
+
+
+def test_fields21_use_every_bit_once():
+    """The six 21-bit fields of a Philox block are disjoint: together they take
+    126 of its 128 bits, all but bit 10 of words 1 and 3."""
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        w = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        f = O.fields21(w)
+        assert np.all(f < 2 ** 21)
+        assert [int(v) for v in f[:4]] == [int(x) >> 11 for x in w]
+        assert int(f[4]) == (int(w[0]) & 0x7FF) | ((int(w[1]) & 0x3FF) << 11)
+        assert int(f[5]) == (int(w[2]) & 0x7FF) | ((int(w[3]) & 0x3FF) << 11)
+    # flipping any bit outside bit 10 of words 1 and 3 changes exactly one field
+    w = np.zeros(4, dtype=np.uint32)
+    base = O.fields21(w)
+    for i in range(4):
+        for b in range(32):
+            v = w.copy()
+            v[i] = np.uint32(1 << b)
+            changed = int(np.sum(O.fields21(v) != base))
+            assert changed == (0 if (i in (1, 3) and b == 10) else 1), (i, b)
     # the uniforms built from Philox words are uniform: KS test on 20000 draws
     us = [O.u01_53(*O.philox([i, 7, 3, 1], [0, 0])[:2]) for i in range(20000)]
     from scipy.stats import kstest
