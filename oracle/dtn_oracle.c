@@ -693,6 +693,125 @@ double or_poisson(double a, const double X[3], const double Y[3])
     return (a * a - xx) / (4.0 * OR_PI * a * r2 * sqrt(r2));
 }
 
+/* Second normal derivative d2G/dn_x dn_y of the Green's function above (R1),
+ * for unit normals nx at X and ny at Y (the kernel of Eq. bw53 and bw59):
+ *   (1/4pi) [ nx.ny / r^3 - 3 (D.nx)(D.ny) / r^5
+ *             + a ( (2 (X.nx)(Y.ny) - a^2 nx.ny) Q^{-3/2}
+ *                   - 3 (|X|^2 Y.ny - a^2 X.ny)(|Y|^2 X.nx - a^2 Y.nx) Q^{-5/2} ) ],
+ * D = X - Y, r = |D|, Q = |X|^2 |Y|^2 - 2 a^2 X.Y + a^4. */
+double or_green_dnn(double a, const double X[3], const double nx[3], const double Y[3], const double ny[3])
+{
+    double D[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
+    double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2], r = sqrt(r2);
+    double Dnx = D[0] * nx[0] + D[1] * nx[1] + D[2] * nx[2];
+    double Dny = D[0] * ny[0] + D[1] * ny[1] + D[2] * ny[2];
+    double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+    double XX = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    double YY = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    double XY = X[0] * Y[0] + X[1] * Y[1] + X[2] * Y[2];
+    double Xnx = X[0] * nx[0] + X[1] * nx[1] + X[2] * nx[2];
+    double Yny = Y[0] * ny[0] + Y[1] * ny[1] + Y[2] * ny[2];
+    double Xny = X[0] * ny[0] + X[1] * ny[1] + X[2] * ny[2];
+    double Ynx = Y[0] * nx[0] + Y[1] * nx[1] + Y[2] * nx[2];
+    double Q = XX * YY - 2.0 * a * a * XY + a * a * a * a;
+    double sq = sqrt(Q);
+    double fr = nn / (r2 * r) - 3.0 * Dnx * Dny / (r2 * r2 * r);
+    double im = a * ((2.0 * Xnx * Yny - a * a * nn) / (Q * sq) -
+                     3.0 * (XX * Yny - a * a * Xny) * (YY * Xnx - a * a * Ynx) / (Q * Q * sq));
+    return (fr + im) / (4.0 * OR_PI);
+}
+
+/* Second-kind local BIE (Eq. bw55-bw59) on a flat (disk) patch.  For x and y
+ * in the plane of S, which passes through the ball centre, X.n = Y.n = 0 and
+ * (X - Y).n = 0, so dG/dn_x vanishes there: D = 0 and Eq. bw55 reads
+ * q(x) = 2 b(x).  b is regularised with the constant solution (for u = 1,
+ * q = 0: 0 = - int_Gamma K - p.f. int_S K), so at each collocation point
+ *   q_i = - 2 sum_k W_k K(x_i, y_k) (U_k - g(x_i))
+ *         - 2 p.v. int_S K(x_i, y) (g(y) - g(x_i)) ds_y,
+ * K = d2G/dn_x dn_y, which on S is (1/4pi) (1/rho^3 - a^3 Q^{-3/2}).  The
+ * linear Taylor term t(y) = grad_S g(x_i).(y - x_i) is taken out of the S
+ * integral: its free-space part is exact, p.v. int_S (y - x)/rho^3 ds =
+ * - oint_{dS} nu / rho dl (divergence theorem in the plane, nu the outward unit
+ * normal of the disk's rim), by ng2 Gauss points on the rim; the rest
+ * (g - g(x_i) - t) K and t times the image part are integrated in polar
+ * coordinates about x_i, angle by ng2 Gauss points on [0, 2 pi], rho by ng2
+ * on [0, rho_max(angle)].  grad_S g by central differences (h = 1e-5 a) along
+ * t1, t2.  U: the hemisphere values at the nodes of or_gamma_nodes(p, nt, nph).
+ * Returns -1 unless p is a disk patch. */
+int or_second_kind_flat(const or_patch *p, const or_data *dat, int nt, int nph, int nr, int ns,
+                        const double *U, int ng2, double *q)
+{
+    if (p->kind != 0) return -1;
+    const int P = nt * nph, n = nr * ns;
+    const double a = p->a;
+    double *Yl = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
+    double *Xl = malloc(sizeof(double) * 3 * n), *ar = malloc(sizeof(double) * n);
+    double *xg = malloc(sizeof(double) * 3 * n);
+    double *gx = malloc(sizeof(double) * ng2), *gw = malloc(sizeof(double) * ng2);
+    or_gamma_nodes(p, nt, nph, Yl, NULL, W);
+    or_panels(p, nr, ns, Xl, xg, NULL, ar, NULL);
+    or_gauss_legendre(ng2, gx, gw);
+    const double ez[3] = {0.0, 0.0, 1.0};
+    for (int i = 0; i < n; ++i) {
+        const double *X = Xl + 3 * i;
+        double xglob[3];
+        local_to_global(p, X, xglob);
+        const double gxi = or_dirichlet(dat, xglob);
+        /* Gamma term; the outward normal of the hemisphere is Y / a */
+        double sg = 0.0;
+        for (int k = 0; k < P; ++k) {
+            const double *Y = Yl + 3 * k;
+            double ny[3] = {Y[0] / a, Y[1] / a, Y[2] / a};
+            sg += W[k] * or_green_dnn(a, X, ez, Y, ny) * (U[k] - gxi);
+        }
+        /* tangential gradient of the data at x_i */
+        double grad[2];
+        const double h = 1e-5 * a;
+        for (int d = 0; d < 2; ++d) {
+            double Lp[3] = {X[0], X[1], 0.0}, Lm[3] = {X[0], X[1], 0.0}, yp[3], ym[3];
+            Lp[d] += h; Lm[d] -= h;
+            local_to_global(p, Lp, yp);
+            local_to_global(p, Lm, ym);
+            grad[d] = (or_dirichlet(dat, yp) - or_dirichlet(dat, ym)) / (2.0 * h);
+        }
+        /* S term: polar coordinates about x_i, rho_max from |X + rho e| = a */
+        double ss = 0.0;
+        const double xx = X[0] * X[0] + X[1] * X[1];
+        for (int j = 0; j < ng2; ++j) {
+            const double ph = OR_PI * (gx[j] + 1.0), wph = OR_PI * gw[j];
+            const double e[2] = {cos(ph), sin(ph)};
+            const double xe = X[0] * e[0] + X[1] * e[1];
+            const double rmax = -xe + sqrt(xe * xe + a * a - xx);
+            for (int l = 0; l < ng2; ++l) {
+                const double rho = 0.5 * rmax * (gx[l] + 1.0), w = wph * 0.5 * rmax * gw[l];
+                const double L[3] = {X[0] + rho * e[0], X[1] + rho * e[1], 0.0};
+                double yglob[3];
+                local_to_global(p, L, yglob);
+                const double t = rho * (grad[0] * e[0] + grad[1] * e[1]);
+                const double XX = xx, YY = L[0] * L[0] + L[1] * L[1], XY = X[0] * L[0] + X[1] * L[1];
+                const double Q = XX * YY - 2.0 * a * a * XY + a * a * a * a;
+                const double img = a * a * a / (Q * sqrt(Q));
+                /* (g - g(x) - t)(1/rho^3 - img) + t (- img), times the area element rho */
+                ss += w * rho * ((or_dirichlet(dat, yglob) - gxi - t) * (1.0 / (rho * rho * rho) - img) - t * img);
+            }
+        }
+        /* p.v. int_S (y - x)/rho^3 ds = - oint nu / rho dl over the rim |Y| = a */
+        double pv[2] = {0.0, 0.0};
+        for (int j = 0; j < ng2; ++j) {
+            const double th = OR_PI * (gx[j] + 1.0), w = OR_PI * gw[j] * a;
+            const double nu[2] = {cos(th), sin(th)};
+            const double dy[2] = {a * nu[0] - X[0], a * nu[1] - X[1]};
+            const double rr = sqrt(dy[0] * dy[0] + dy[1] * dy[1]);
+            pv[0] -= w * nu[0] / rr;
+            pv[1] -= w * nu[1] / rr;
+        }
+        ss += grad[0] * pv[0] + grad[1] * pv[1];
+        q[i] = -2.0 * sg - 2.0 * ss / (4.0 * OR_PI);
+    }
+    free(Yl); free(W); free(Xl); free(ar); free(xg); free(gx); free(gw);
+    return 0;
+}
+
 /* ============================================== adaptive panel quadrature */
 /* Integrands over a patch panel, in the panel's (u, v) parameters. */
 typedef struct {

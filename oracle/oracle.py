@@ -104,6 +104,11 @@ def lib():
                                       C.c_int, C.c_double, C.c_int64, C.c_uint32, C.POINTER(OrWosOpts),
                                       C.c_void_p, _f64p, C.c_void_p]
         L.or_single_point.restype = C.c_int
+        L.or_green_dnn.argtypes = [C.c_double, _f64p, _f64p, _f64p, _f64p]
+        L.or_green_dnn.restype = C.c_double
+        L.or_second_kind_flat.argtypes = [C.POINTER(OrPatch), C.POINTER(OrData), C.c_int, C.c_int, C.c_int,
+                                          C.c_int, _f64p, C.c_int, _f64p]
+        L.or_second_kind_flat.restype = C.c_int
         L.or_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -394,6 +399,25 @@ def single_point(geom, data, x, a, ng1, ng2, delta, walks=0, patch=0, opts=None,
     if rc != 0:
         return None
     return dict(sigma1=out[0], sigma2=out[1], q=out[2], se=out[3], U=U)
+
+
+
+def green_dnn(a, X, nx, Y, ny) -> float:
+    """or_green_dnn: d2G/dn_x dn_y of the whole-sphere Dirichlet Green's function."""
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    return lib().or_green_dnn(float(a), f(X), f(nx), f(Y), f(ny))
+
+
+def second_kind_flat(p: OrPatch, data, nt, nph, nr, ns, U, ng2=20) -> np.ndarray:
+    """or_second_kind_flat: Neumann data of a disk patch by the second-kind
+    local BIE (Eq. bw55-bw59), hemisphere values U at or_gamma_nodes(p, nt, nph)."""
+    od, keep = make_data(data)
+    q = np.zeros(nr * ns)
+    rc = lib().or_second_kind_flat(C.byref(p), C.byref(od), int(nt), int(nph), int(nr), int(ns),
+                                   np.ascontiguousarray(U, dtype=np.float64), int(ng2), q)
+    if rc != 0:
+        raise ValueError("second-kind rows need a disk patch")
+    return q
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]
