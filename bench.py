@@ -37,6 +37,10 @@ N_TARGETS = 100_000
 # 9 x 4) 261 + fixed-point terms 11: 280.
 OPS_PER_STEP = 55
 OPS_PER_WALK = 280
+# DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
+# per-node sums): ncu capture of the 64-patch case, 1,638,400 bytes for 32,768
+# nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
+DRAM_BYTES_PER_NODE = 1638400 / 32768
 SM_COUNT = 152
 LANES_PER_SM = 128
 
@@ -459,7 +463,9 @@ def run_ours(args):
         "fp64_path": {"value": plain, "unit": "patches/s", "sample": f"{nplain} patches, one patch per launch",
                       "speedup": value / plain},
         "roofline": {"bound": "alu", "kernel": "wos_kernel<float, ball>", "achieved": achieved,
-                     "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                     "traffic": DRAM_BYTES_PER_NODE * int(np.sum(b.n_theta * b.n_phi)),
+                     "traffic_basis": "ncu dram bytes of the 64-patch capture, scaled by hemisphere nodes",
                      "ops_per_walk_step": OPS_PER_STEP, "ops_per_walk": OPS_PER_WALK, "walks": n_walks,
                      "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"},
         "e2e": {"value": b.n * world / (e2e / 1e3), "unit": "patches/s", "h2d_bytes_per_step": h2d,

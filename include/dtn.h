@@ -121,6 +121,10 @@ typedef struct {
     int32_t record_stages;      /* 1: record CUDA events between the stages of the call on its
                                    stream (read them with dtn_stage_times) */
     int32_t wos_refill;         /* idle lanes of a warp before it refills them (0 = tuned) */
+    int32_t bie_kind;           /* 0: first-kind local BIE (Eq. bw49-bw51, collocation solve);
+                                   1: second-kind local BIE (Eq. bw55-bw59), disk patches only:
+                                   there the double-layer operator vanishes and q = 2b */
+    int32_t ring_order;         /* second kind: Gauss order of the polar rules on S (0 = 20) */
 } dtn_solve_opts;
 
 /* Launch parameters of the walk kernel chosen by dtn_autotune_walks. */

@@ -56,7 +56,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("epsilon", C.c_double), ("seed", C.c_uint64),
                 ("max_steps", C.c_uint64), ("max_refine_iters", C.c_int32), ("refine_tol", C.c_double),
                 ("u_provided", C.c_int32), ("walk_chunk", C.c_int32), ("wos_blocks_per_sm", C.c_int32),
-                ("graph_capture", C.c_int32), ("record_stages", C.c_int32), ("wos_refill", C.c_int32)]
+                ("graph_capture", C.c_int32), ("record_stages", C.c_int32), ("wos_refill", C.c_int32),
+                ("bie_kind", C.c_int32), ("ring_order", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -179,13 +180,14 @@ def _host_f64(t):
 
 def solve_opts(prec=PREC_MIXED, epsilon=1e-4, seed=0, max_steps=0, max_refine_iters=0, refine_tol=0.0,
                u_provided=False, walk_chunk=0, wos_blocks_per_sm=0, graph_capture=False,
-               record_stages=False, wos_refill=0) -> SolveOpts:
+               record_stages=False, wos_refill=0, bie_kind=0, ring_order=0) -> SolveOpts:
     o = SolveOpts()
     o.prec, o.epsilon, o.seed, o.max_steps = int(prec), float(epsilon), int(seed), int(max_steps)
     o.max_refine_iters, o.refine_tol, o.u_provided = int(max_refine_iters), float(refine_tol), int(u_provided)
     o.walk_chunk, o.wos_blocks_per_sm, o.graph_capture = int(walk_chunk), int(wos_blocks_per_sm), int(graph_capture)
     o.record_stages = int(record_stages)
     o.wos_refill = int(wos_refill)
+    o.bie_kind, o.ring_order = int(bie_kind), int(ring_order)
     return o
 
 

@@ -632,6 +632,10 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     if (!b->centers || !b->radius || !b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors) return DTN_E_INVALID_ARG;
     if (!r->u_gamma_mean || !r->neumann) return DTN_E_INVALID_ARG;
     if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
+    if (o->bie_kind != 0 && o->bie_kind != 1) return DTN_E_INVALID_ARG;
+    if (o->ring_order < 0 || o->ring_order > kMaxGauss) return DTN_E_INVALID_ARG;
+    // the second-kind rows are written for flat patches (the double layer vanishes there)
+    if (o->bie_kind == 1 && (g->dg.kind == kBall || g->dg.kind == kBallExterior)) return DTN_E_UNSUPPORTED;
     if (!o->u_provided) {
         if (!b->walks_per_point || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
         for (int64_t p = 0; p < b->n_patches; ++p)
@@ -788,6 +792,15 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         if ((e = launch_wos(g, w, s)) != cudaSuccess) return e;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
+    // 3-4. second kind (Eq. bw55-bw59, disk patches): q = 2b row by row, no system
+    if (o->bie_kind == 1) {
+        e = launch_second_kind(g, L, D, W.panel_loc.as<double>(), pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                               o->ring_order > 0 ? o->ring_order : 20, r->neumann, r->rhs, r->refine_iters,
+                               r->residual, r->patch_status, s);
+        if (e == cudaSuccess) e = mark(3);
+        if (e == cudaSuccess) e = mark(4);
+        return e;
+    }
     // 3. assembly of Eq. bw49-bw51 (step 2)
     const double *pl = W.panel_loc.as<double>(), *pp = W.panel_prm.as<double>(), *pa = W.panel_aux.as<double>();
     const bool shared = (o->prec == DTN_PREC_MIXED);

@@ -205,8 +205,14 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 // reduced to (-pi, pi] (the same angle mod 2 pi) and taken by the SFU
 // sine/cosine; s = sqrt(1 - z^2) by the SFU reciprocal square root
 // (1 - z^2 >= 2^-20 > 0 for these uniforms).
+__device__ __forceinline__ float u01_21(uint32_t f) {
+    // 1 + (2f + 1) 2^-22 built in the significand (4f + 2 < 2^23), minus 1 exactly:
+    // (2f + 1) 2^-22 with an integer add and an FP32 add, no conversion
+    return __uint_as_float(0x3F800002u + 4u * f) - 1.0f;
+}
+
 __device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
-    const float u1 = __uint2float_rn(2u * f1 + 1u) * 0x1p-22f, u2 = __uint2float_rn(2u * f2 + 1u) * 0x1p-22f;
+    const float u1 = u01_21(f1), u2 = u01_21(f2);
     const float zz = fmaf(-2.0f, u1, 1.0f);
     const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
     const float s = t * rsqrtf(t);
