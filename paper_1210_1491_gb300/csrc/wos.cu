@@ -354,21 +354,23 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                             acc.st += step;   // gone to infinity: scores 0
                             active = false;
                         }
-                        if (active) {
-                            const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
-                            ++step;
-                            if (d <= eps) {
-                                acc.st += step;
-                                pending = true;
-                                active = false;
-                            } else if (step >= P.max_steps) {
-                                acc.st += step;
-                                acc.cap += 1;
-                                active = false;
-                            } else {
-                                jump(x, y, z, d, f[2 * h], f[2 * h + 1]);
-                            }
-                        }
+                        // branch-free step: every lane evaluates, active lanes that
+                        // go on move (the lanes stay converged through the block)
+                        const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
+                        const uint32_t st1 = step + 1u;
+                        const bool absorbed = active && d <= eps;
+                        const bool cut = active && !absorbed && st1 >= P.max_steps;
+                        const bool go = active && !absorbed && !cut;
+                        T nx = x, ny = y, nz = z;
+                        jump(nx, ny, nz, d, f[2 * h], f[2 * h + 1]);
+                        x = go ? nx : x;
+                        y = go ? ny : y;
+                        z = go ? nz : z;
+                        step = active ? st1 : step;
+                        acc.st += (absorbed || cut) ? (unsigned long long)st1 : 0ull;
+                        acc.cap += cut ? 1u : 0u;
+                        pending = pending || absorbed;
+                        active = go;
                     }
                 } else if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                     acc.st += step;   // gone to infinity: scores 0
