@@ -80,3 +80,51 @@ def test_wire_patches_vs_oracle():
         rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], 0.3, 8, 8, 4, 8, 0, 0, O.wos_opts(), U_in=U[sl],
                            rtol=1e-11)
         assert np.linalg.norm(q[p * 32:(p + 1) * 32] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4
+
+
+def test_precision_study_scaled_unit_ball():
+    """The precision study on the scaled unit ball (2e4 patches, 256 panels,
+    1024 nodes x 8192 walks): FP32 walks with FP64 sums and the FP32 shared
+    factors with FP64-residual refinement over all patches in one call; the
+    all-FP64 path (FP64 walks, FP64 assembly and LU, one patch per call) on a
+    sample; both against the exact Neumann data and against the oracle's solve
+    with their own node values.  Prints the per-patch relative L2 errors."""
+    wl = W.unit_ball_scaled()
+    b = wl.batch
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks)
+    r = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=wl.epsilon,
+                                                                     seed=wl.seed))
+    torch.cuda.synchronize()
+    assert np.all(r["patch_status"].cpu().numpy() == 0)
+    P, n = 1024, 256
+    q = r["neumann"].cpu().numpy()
+    x = r["colloc_xyz"].cpu().numpy()
+    nrm = r["normals"].cpu().numpy()
+    U = r["u_gamma_mean"].cpu().numpy()
+    iters = r["refine_iters"].cpu().numpy()
+    assert iters.max() <= 10
+    sample = (0, 7777, 19999)
+    errs_mixed, errs_fp64 = [], []
+    for p in sample:
+        sl = slice(p * n, (p + 1) * n)
+        inner = np.linalg.norm(x[sl] - b.centers[p], axis=1) < 0.07
+        qe = O.neumann_exact(wl.data, x[sl], nrm[sl])
+        errs_mixed.append(np.linalg.norm((q[sl] - qe)[inner]) / np.linalg.norm(qe[inner]))
+        # the oracle's collocation solve with the GPU's node values
+        rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], 0.1, 32, 32, 16, 16, 0, 0, O.wos_opts(),
+                           U_in=U[p * P:(p + 1) * P], rtol=1e-10)
+        assert np.linalg.norm(q[sl] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4
+        # the all-FP64 path on the same patch (its own FP64 walks)
+        h1 = dtn.HostBatch(b.n_theta[p:p + 1], b.n_phi[p:p + 1], b.n_rings[p:p + 1], b.n_sectors[p:p + 1],
+                           b.walks[p:p + 1], patch_id_base=p)
+        r64 = dtn.solve_patches(g, b.centers[p:p + 1], b.radius[p:p + 1], h1,
+                                dtn.solve_opts(prec=dtn.PREC_FP64, epsilon=wl.epsilon, seed=wl.seed))
+        torch.cuda.synchronize()
+        q64 = r64["neumann"].cpu().numpy()
+        errs_fp64.append(np.linalg.norm((q64 - qe)[inner]) / np.linalg.norm(qe[inner]))
+    print("precision study rel-L2 (r < 0.7a) mixed:", errs_mixed, "fp64:", errs_fp64)
+    # both paths sit at the Monte Carlo + discretisation level, and neither is
+    # systematically worse than the other by more than that level
+    assert max(errs_mixed) < 0.05 and max(errs_fp64) < 0.05
+    assert np.mean(errs_mixed) < 2.0 * np.mean(errs_fp64) + 0.01
