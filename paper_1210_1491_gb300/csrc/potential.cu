@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(kPotThreads) potential_mixed_kernel(
     const double *__restrict__ xyz, const double *__restrict__ nrm,
     const double *__restrict__ area, const double *__restrict__ q, const double *__restrict__ g,
     int64_t nt, const double *__restrict__ t, double *__restrict__ out) {
-    __shared__ float sx[kTile], sy[kTile], sz[kTile], snx[kTile], sny[kTile], snz[kTile], saq[kTile], sag[kTile];
+    // a panel as two float4 (offset from the tile origin with area q / 4pi, normal
+    // with area g / 4pi): two shared-memory loads per pair term
+    __shared__ float4 s_pa[kTile], s_pb[kTile];
     __shared__ double s_org[3];
     const int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = it < nt;
@@ -41,27 +43,24 @@ __global__ void __launch_bounds__(kPotThreads) potential_mixed_kernel(
             s_org[0] = xyz[3 * p0]; s_org[1] = xyz[3 * p0 + 1]; s_org[2] = xyz[3 * p0 + 2];
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < kTile; k += blockDim.x) {
-            if (k < cnt) {
-                const int64_t pp = index ? index[base + k] : base + k;
-                sx[k] = (float)(xyz[3 * pp] - s_org[0]);
-                sy[k] = (float)(xyz[3 * pp + 1] - s_org[1]);
-                sz[k] = (float)(xyz[3 * pp + 2] - s_org[2]);
-                snx[k] = (float)nrm[3 * pp]; sny[k] = (float)nrm[3 * pp + 1]; snz[k] = (float)nrm[3 * pp + 2];
-                saq[k] = (float)(area[pp] * q[pp]) * inv4pi;
-                sag[k] = (float)(area[pp] * g[pp]) * inv4pi;
-            }
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const int64_t pp = index ? index[base + k] : base + k;
+            s_pa[k] = make_float4((float)(xyz[3 * pp] - s_org[0]), (float)(xyz[3 * pp + 1] - s_org[1]),
+                                  (float)(xyz[3 * pp + 2] - s_org[2]), (float)(area[pp] * q[pp]) * inv4pi);
+            s_pb[k] = make_float4((float)nrm[3 * pp], (float)nrm[3 * pp + 1], (float)nrm[3 * pp + 2],
+                                  (float)(area[pp] * g[pp]) * inv4pi);
         }
         __syncthreads();
         const float ox = (float)(tx - s_org[0]), oy = (float)(ty - s_org[1]), oz = (float)(tz - s_org[2]);
         float s = 0.0f;
 #pragma unroll 4
         for (int k = 0; k < cnt; ++k) {
-            const float dx = ox - sx[k], dy = oy - sy[k], dz = oz - sz[k];
+            const float4 pa = s_pa[k], pb = s_pb[k];
+            const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float ri = rsqrtf(r2);
-            const float dn = fmaf(dx, snx[k], fmaf(dy, sny[k], dz * snz[k]));
-            s += ri * fmaf(-sag[k] * dn, ri * ri, saq[k]);
+            const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+            s += ri * fmaf(-pb.w * dn, ri * ri, pa.w);
         }
         acc += (double)s;
     }
@@ -110,21 +109,52 @@ __global__ void __launch_bounds__(kGatherThreads) owner_kernel(int64_t np, const
                                                              const int64_t *__restrict__ owner, int64_t nc,
                                                              const double *__restrict__ cent,
                                                              uint8_t *__restrict__ keep) {
+    // Two passes over the centres (staged in shared memory): the FP32 minimum of
+    // the squared distances, then the FP64 decision (lowest index on ties) among
+    // the centres whose FP32 squared distance is within twice the FP32 error
+    // bound of that minimum, so the FP64 minimum is always a candidate.  Bound:
+    // each FP32 difference is off by at most dl = 4 u M (u = 2^-24, M the size
+    // of the coordinates involved), so a squared distance d^2 by at most
+    // 2 sqrt(3) d dl + 3 dl^2 + 4 u d^2.
     __shared__ double sc[3 * kGatherThreads];
+    __shared__ float sf[3 * kGatherThreads];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = i < np;
     const double px = valid ? x[3 * i] : 0.0, py = valid ? x[3 * i + 1] : 0.0, pz = valid ? x[3 * i + 2] : 0.0;
+    const float fx = (float)px, fy = (float)py, fz = (float)pz;
+    float fbest = INFINITY;
+    for (int64_t base = 0; base < nc; base += kGatherThreads) {
+        const int cnt = (int)min((int64_t)kGatherThreads, nc - base);
+        __syncthreads();
+        for (int k = threadIdx.x; k < 3 * cnt; k += blockDim.x) sf[k] = (float)cent[3 * base + k];
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const float dx = fx - sf[3 * k], dy = fy - sf[3 * k + 1], dz = fz - sf[3 * k + 2];
+            fbest = fminf(fbest, dx * dx + dy * dy + dz * dz);
+        }
+    }
+    const float D = sqrtf(fbest);
+    const float M = fmaxf(fmaxf(fabsf(fx), fabsf(fy)), fabsf(fz)) + 2.0f * D;
+    const float dl = 4.0f * 0x1p-24f * M;
+    const float thr = fbest + 2.0f * (3.5f * D * dl + 3.0f * dl * dl + 4.0f * 0x1p-24f * fbest) + 1e-30f;
     double best = INFINITY;
     int64_t bi = -1;
     for (int64_t base = 0; base < nc; base += kGatherThreads) {
         const int cnt = (int)min((int64_t)kGatherThreads, nc - base);
         __syncthreads();
-        for (int k = threadIdx.x; k < 3 * cnt; k += blockDim.x) sc[k] = cent[3 * base + k];
+        for (int k = threadIdx.x; k < 3 * cnt; k += blockDim.x) {
+            const double c = cent[3 * base + k];
+            sc[k] = c;
+            sf[k] = (float)c;
+        }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
-            const double dx = px - sc[3 * k], dy = py - sc[3 * k + 1], dz = pz - sc[3 * k + 2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 < best) { best = d2; bi = base + k; }
+            const float dx = fx - sf[3 * k], dy = fy - sf[3 * k + 1], dz = fz - sf[3 * k + 2];
+            if (dx * dx + dy * dy + dz * dz <= thr) {
+                const double ex = px - sc[3 * k], ey = py - sc[3 * k + 1], ez = pz - sc[3 * k + 2];
+                const double d2 = ex * ex + ey * ey + ez * ez;
+                if (d2 < best) { best = d2; bi = base + k; }
+            }
         }
     }
     if (valid) keep[i] = (bi == owner[i]) ? 1 : 0;
