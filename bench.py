@@ -41,6 +41,9 @@ OPS_PER_WALK = 280
 # per-node sums): ncu capture of the 64-patch case, 1,638,400 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
 DRAM_BYTES_PER_NODE = 1638400 / 32768
+# the same capture's issue-slot utilisation and active lanes per warp instruction
+NCU_ISSUE_ACTIVE = 0.761
+NCU_LANES_PER_INST = 28.96
 SM_COUNT = 152
 LANES_PER_SM = 128
 
@@ -58,7 +61,8 @@ class ClockSampler:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"dtn_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -466,6 +470,7 @@ def run_ours(args):
                      "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
                      "traffic": DRAM_BYTES_PER_NODE * int(np.sum(b.n_theta * b.n_phi)),
                      "traffic_basis": "ncu dram bytes of the 64-patch capture, scaled by hemisphere nodes",
+                     "ncu_issue_slots_busy": NCU_ISSUE_ACTIVE, "ncu_active_lanes_per_inst": NCU_LANES_PER_INST,
                      "ops_per_walk_step": OPS_PER_STEP, "ops_per_walk": OPS_PER_WALK, "walks": n_walks,
                      "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"},
         "e2e": {"value": b.n * world / (e2e / 1e3), "unit": "patches/s", "h2d_bytes_per_step": h2d,
