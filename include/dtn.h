@@ -223,6 +223,57 @@ dtn_status dtn_eval_potential(const dtn_geometry *geom, int64_t n_panels, const 
                               const int64_t *n_index, int64_t n_targets, const double *targets,
                               double *u_out, int32_t prec, void *stream);
 
+/* Options of the fast multipole evaluation (dtn_eval_potential_fmm). */
+typedef struct {
+    int32_t order;          /* expansion order P, 1 .. 16 */
+    int32_t leaf_sources;   /* a source cell holding more panels is split, 1 .. 4096 */
+    int32_t leaf_targets;   /* a target cell holding more targets is split, 1 .. 4096 */
+    int32_t max_level;      /* deepest octree level, 1 .. 21 */
+    double theta;           /* acceptance (r_T + r_S) < theta |z - c|, r the cell half-diagonal; (0, 1) */
+} dtn_fmm_opts;
+
+/* What one evaluation did (counts; written when the pointer is not NULL). */
+typedef struct {
+    int64_t source_cells, target_cells;   /* octree cells, all levels */
+    int64_t m2l_pairs, p2p_pairs;         /* accepted cell pairs and leaf pairs */
+    int64_t p2p_terms;                    /* direct pair terms (sum of leaf-pair products) */
+    int32_t source_levels, target_levels; /* levels including the root */
+    int32_t traversal_passes;             /* level-synchronous traversal passes */
+    int32_t restarts;                     /* traversals restarted after a list grew */
+} dtn_fmm_stats;
+
+/* The same sum as dtn_eval_potential (Eq. bw03 with the free-space G of
+ * Eq. bw05, panel-midpoint rule) by the fast multipole method of Greengard and
+ * Rokhlin, the evaluation Sec. 6 names for the potential after the patch
+ * solves.  Panel p is a charge area_p q_p / 4pi and a dipole
+ * -area_p g_p n_p / 4pi at its collocation point.  Sources and targets get
+ * adaptive octrees over one bounding cube; a dual-tree traversal sends each
+ * (target cell, source cell) pair with (r_T + r_S) < theta |z - c| (r the cell
+ * half-diagonals, z and c their centres) through multipole-to-local
+ * translation with expansions of order P in solid harmonics, and leaf pairs
+ * that fail the test through the direct pair sum.  The far-field error of a
+ * pair falls like theta^(P+1).  Expansions and pair terms are FP32, centre
+ * differences and per-target sums FP64.
+ *   Arrays as in dtn_eval_potential (device; dirichlet may be NULL: g from the
+ *   data set on geom; panel_index / n_index select panels the same way, and
+ *   panel_index must hold at least that many entries).  An index outside
+ *   [0, n_panels) is found on the device before any panel is read and gives
+ *   DTN_E_INVALID_ARG.
+ *   n_panels and n_targets below 2^31.  A target that coincides with a panel
+ *   point gets an infinite value, as in the direct sum.
+ *   opts: required; stats: may be NULL.
+ * Synchronises `stream` (the octrees and the traversal are built level by
+ * level with host-side counts); the result is complete when the call returns
+ * DTN_OK.  The workspace is owned by geom and reused; calls on one geom must
+ * be serialised.  Errors: DTN_E_INVALID_ARG for options out of range or
+ * missing arrays, DTN_E_CUDA / DTN_E_OUT_OF_MEMORY. */
+dtn_status dtn_eval_potential_fmm(dtn_geometry *geom, int64_t n_panels, const double *xyz,
+                                  const double *normals, const double *areas, const double *neumann,
+                                  const double *dirichlet, const int64_t *panel_index,
+                                  const int64_t *n_index, int64_t n_targets, const double *targets,
+                                  double *u_out, const dtn_fmm_opts *opts, dtn_fmm_stats *stats,
+                                  void *stream);
+
 /* Panel gather for the overlapping-patch cover (Sec. 6: the boundary is covered
  * by overlapping patches S_i): panel i (of patch owner[i]) is kept iff the
  * patch centre nearest to its collocation point (FP64 distances, lowest index

@@ -1218,6 +1218,28 @@ void or_potential(int64_t np, const double *y, const double *nrm, const double *
     }
 }
 
+/* Majorants of the sum above, per target: b0 = sum_p |A_p q_p| / (4pi|t-y_p|)
+ * and b1 = sum_p |A_p g_p| / (4pi|t-y_p|^2) (the charge and dipole magnitudes
+ * over the first and second power of the distance).  They scale the error
+ * bound of an approximate evaluation (a multipole expansion) of or_potential. */
+void or_potential_majorants(int64_t np, const double *y, const double *area, const double *q,
+                            const double *g, int64_t nt, const double *t, double *b0, double *b1)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nt; ++i) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int64_t p = 0; p < np; ++p) {
+            double d[3] = {t[3 * i] - y[3 * p], t[3 * i + 1] - y[3 * p + 1], t[3 * i + 2] - y[3 * p + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double r = sqrt(r2);
+            s0 += fabs(area[p] * q[p]) / (4.0 * OR_PI * r);
+            s1 += fabs(area[p] * g[p]) / (4.0 * OR_PI * r2);
+        }
+        b0[i] = s0;
+        b1[i] = s1;
+    }
+}
+
 /* Panel ownership for the overlapping-patch cover (Sec. 6): panel of patch p is
  * kept iff the patch centre nearest to its collocation point is p's (lowest
  * index on ties).  keep[i] = 1 / 0. */

@@ -99,6 +99,8 @@ def lib():
         L.or_solve_patch.restype = C.c_int
         L.or_potential.argtypes = [C.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p, C.c_int64,
                                    _f64p, _f64p]
+        L.or_potential_majorants.argtypes = [C.c_int64, _f64p, _f64p, _f64p, _f64p, C.c_int64, _f64p,
+                                             _f64p, _f64p]
         L.or_owned.argtypes = [C.c_int64, _f64p, _i64p, C.c_int64, _f64p, _u8p]
         L.or_single_point.argtypes = [C.POINTER(OrGeom), C.POINTER(OrData), _f64p, C.c_double, C.c_int,
                                       C.c_int, C.c_double, C.c_int64, C.c_uint32, C.POINTER(OrWosOpts),
@@ -364,6 +366,18 @@ def potential(y, normals, area, q, g, targets) -> np.ndarray:
                        np.ascontiguousarray(q, dtype=np.float64),
                        np.ascontiguousarray(g, dtype=np.float64), len(t), t, out)
     return out
+
+
+def potential_majorants(y, area, q, g, targets) -> tuple:
+    """(b0, b1) per target: sum |A q| / (4 pi r) and sum |A g| / (4 pi r^2)."""
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+    b0 = np.zeros(len(t))
+    b1 = np.zeros(len(t))
+    lib().or_potential_majorants(len(y), y, np.ascontiguousarray(area, dtype=np.float64),
+                                 np.ascontiguousarray(q, dtype=np.float64),
+                                 np.ascontiguousarray(g, dtype=np.float64), len(t), t, b0, b1)
+    return b0, b1
 
 
 def owned(x, owner_patch, centers) -> np.ndarray:

@@ -90,12 +90,26 @@ class Query(C.Structure):
                 ("n_sectors", C.c_void_p), ("walks_per_point", C.c_void_p), ("patch_ids", C.c_void_p)]
 
 
+class FmmOpts(C.Structure):
+    _fields_ = [("order", C.c_int32), ("leaf_sources", C.c_int32), ("leaf_targets", C.c_int32),
+                ("max_level", C.c_int32), ("theta", C.c_double)]
+
+
+class FmmStats(C.Structure):
+    _fields_ = [("source_cells", C.c_int64), ("target_cells", C.c_int64), ("m2l_pairs", C.c_int64),
+                ("p2p_pairs", C.c_int64), ("p2p_terms", C.c_int64), ("source_levels", C.c_int32),
+                ("target_levels", C.c_int32), ("traversal_passes", C.c_int32), ("restarts", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "dtn_query_patch_sizes",
            "dtn_solve_patches", "dtn_eval_potential", "dtn_gather_owned", "dtn_wos_points",
            "dtn_distance", "dtn_philox4x32_10", "dtn_eval_dirichlet", "dtn_status_string",
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
            "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks",
-           "dtn_wos_points_noalloc", "dtn_single_point_neumann"]
+           "dtn_wos_points_noalloc", "dtn_single_point_neumann", "dtn_eval_potential_fmm"]
 
 _lib = None
 
@@ -133,6 +147,8 @@ def load(path: str = LIB_PATH):
         "dtn_wos_points_noalloc": ([vp, i64, vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, vp, vp, vp], i32),
         "dtn_single_point_neumann": ([vp, i64, vp, dbl, i32, i32, dbl, vp, C.c_uint32, C.POINTER(SolveOpts),
                                       vp, vp, vp, vp, vp, vp, vp], i32),
+        "dtn_eval_potential_fmm": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, C.POINTER(FmmOpts),
+                                    C.POINTER(FmmStats), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -356,13 +372,43 @@ def eval_potential(geom: Geometry, xyz, normals, areas, neumann, dirichlet, targ
     t = _dev(targets, torch.float64).reshape(-1, 3)
     if out is None:
         out = torch.empty(t.shape[0], dtype=torch.float64, device="cuda")
-    idx = None if index is None else _dev(index, torch.int64)
+    idx = None if index is None else _dev(index, torch.int64).reshape(-1)
     cnt = None if n_index is None else _dev(n_index, torch.int64)
+    if idx is not None and cnt is None and idx.numel() < x.shape[0]:
+        raise ValueError("index without n_index must hold one entry per panel array row")
     _check(load().dtn_eval_potential(geom.handle, x.shape[0], _ptr(x), _ptr(n), _ptr(a), _ptr(q), _ptr(g),
                                      _ptr(idx), _ptr(cnt), t.shape[0], _ptr(t), _ptr(out), int(prec),
                                      _stream(stream)),
            "dtn_eval_potential")
     return out
+
+
+def fmm_opts(order=10, theta=0.5, leaf_sources=64, leaf_targets=64, max_level=20) -> FmmOpts:
+    return FmmOpts(int(order), int(leaf_sources), int(leaf_targets), int(max_level), float(theta))
+
+
+def eval_potential_fmm(geom: Geometry, xyz, normals, areas, neumann, dirichlet, targets, opts: FmmOpts = None,
+                       out=None, stream=None, index=None, n_index=None, want_stats=False):
+    """dtn_eval_potential_fmm: the sum of eval_potential by the fast multipole method."""
+    x = _dev(xyz, torch.float64).reshape(-1, 3)
+    n = _dev(normals, torch.float64).reshape(-1, 3)
+    a = _dev(areas, torch.float64).reshape(-1)
+    q = _dev(neumann, torch.float64).reshape(-1)
+    g = None if dirichlet is None else _dev(dirichlet, torch.float64).reshape(-1)
+    t = _dev(targets, torch.float64).reshape(-1, 3)
+    if out is None:
+        out = torch.empty(t.shape[0], dtype=torch.float64, device="cuda")
+    idx = None if index is None else _dev(index, torch.int64).reshape(-1)
+    cnt = None if n_index is None else _dev(n_index, torch.int64)
+    if idx is not None and cnt is None and idx.numel() < x.shape[0]:
+        raise ValueError("index without n_index must hold one entry per panel array row")
+    o = opts if opts is not None else fmm_opts()
+    st = FmmStats()
+    _check(load().dtn_eval_potential_fmm(geom.handle, x.shape[0], _ptr(x), _ptr(n), _ptr(a), _ptr(q), _ptr(g),
+                                         _ptr(idx), _ptr(cnt), t.shape[0], _ptr(t), _ptr(out), C.byref(o),
+                                         C.byref(st), _stream(stream)),
+           "dtn_eval_potential_fmm")
+    return (out, st.as_dict()) if want_stats else out
 
 
 def gather_owned(colloc_xyz, owner, centers, stream=None):

@@ -45,14 +45,14 @@ void DevBuf::release() {
     bytes = 0;
 }
 
-namespace {
-
 dtn_status to_status(cudaError_t e) {
     if (e == cudaSuccess) return DTN_OK;
     set_cuda_error(e);
     cudaGetLastError();   // do not leave a non-sticky error for the caller's next CUDA call
     return e == cudaErrorMemoryAllocation ? DTN_E_OUT_OF_MEMORY : DTN_E_CUDA;
 }
+
+namespace {
 
 // Lower bound of the distance between two axis-aligned boxes.
 double box_box_dist(const double *alo, const double *ahi, const double *blo, const double *bhi) {
@@ -542,6 +542,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
                       &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp};
     for (DevBuf *b : bufs) b->release();
+    fmm_release(g);
     for (int k = 0; k < 5; ++k)
         if (g->stage_ev[k]) cudaEventDestroy(g->stage_ev[k]);
     if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);

@@ -127,6 +127,7 @@ struct dtn_geometry {
     char dev_name[256] = {0};
     uint64_t data_version = 0;                // bumped by every dtn_set_dirichlet
     cudaGraphExec_t graph_exec = nullptr;     // last captured solve (graph_capture)
+    void *fmm_ws = nullptr;                   // fast multipole workspace (fmm.cu)
     cudaStream_t cap_stream = nullptr;        // private stream used for capture
     std::vector<unsigned char> graph_key;
     cudaEvent_t stage_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -258,6 +259,14 @@ cudaError_t launch_distance(const dtn_geometry *g, int64_t n, const double *x, d
                             double *nearest, int prec, cudaStream_t s);
 cudaError_t launch_dirichlet(const dtn_geometry *g, int64_t n, const double *x, double *out,
                              cudaStream_t s);
+
+// fast multipole evaluation (fmm.cu)
+cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const double *xyz, const double *nrm,
+                         const double *area, const double *q, const double *gv, const int64_t *index, int64_t nt,
+                         const double *t, double *out, const dtn_fmm_opts &o, dtn_fmm_stats *st, bool *bad_index,
+                         cudaStream_t s);
+void fmm_release(dtn_geometry *g);
+dtn_status to_status(cudaError_t e);
 
 __host__ __device__ inline int64_t find_group(const int64_t *off, int64_t n, int64_t idx) {
     // largest p in [0, n) with off[p] <= idx

@@ -1,0 +1,985 @@
+// fmm.cu -- fast multipole evaluation of the integral representation Eq. bw03
+// (Sec. 6: once the patches have their Neumann data, the potential anywhere is
+// one application of the fast multipole method of Greengard and Rokhlin to the
+// panel sources).
+//
+// Sources.  Panel p is a charge c_p = area_p q_p / 4pi and a dipole
+// d_p = -area_p g_p n_p / 4pi at its collocation point y_p, so that
+//   u(t) = sum_p [ c_p / |t - y_p| + d_p.(t - y_p) / |t - y_p|^3 ],
+// the panel-midpoint sum of the direct kernels in potential.cu.
+//
+// Expansions.  Complex solid harmonics
+//   R_n^m(x) = r^n P_n^m(cos th) e^{i m ph} / (n+m)!,
+//   S_n^m(x) = (n-m)! P_n^m(cos th) e^{i m ph} / r^{n+1},
+// P_n^m without the Condon-Shortley phase and A_n^{-m} = (-1)^m conj(A_n^m), so
+// that 1/|x - y| = sum_{n,|m|<=n} S_n^m(x) conj(R_n^m(y)) for |y| < |x|.  The
+// fields are real, so every expansion obeys the same symmetry and only m >= 0
+// is stored ((P+1)(P+2)/2 coefficients, index n(n+1)/2 + m).  With centres c
+// (multipole) and z (local) the operators follow from the addition theorems
+// R_n^m(a + b) = sum_{k,l} R_k^l(a) R_{n-k}^{m-l}(b) and
+//   S_n^m(a + b) = sum_{k,l} (-1)^k conj(R_k^l(b)) S_{n+k}^{m+l}(a):
+//   P2M  M_n^m = sum_p conj(c_p R_n^m(v) + d_p.grad R_n^m(v)),  v = y_p - c,
+//        grad: (dx + i dy)/2 R_{n-1}^{m-1} - (dx - i dy)/2 R_{n-1}^{m+1} + dz R_{n-1}^m
+//   M2M  M'_n^m = sum_{k,l} conj(R_k^l(c - c')) M_{n-k}^{m-l}
+//   M2L  L_n^m = (-1)^{n+m} sum_{j,k} S_{j+n}^{k-m}(z - c) M_j^k
+//   L2L  L'_k^l = sum_{n>=k,m} L_n^m R_{n-k}^{m-l}(z' - z)
+//   L2P  u(t) = sum_{n,m} R_n^m(t - z) L_n^m
+// Each expansion is stored scaled by its cell's half-width h (M / h^n, L h^n),
+// which keeps every FP32 coefficient of order one.
+//
+// Trees and traversal.  Sources and targets get separate adaptive octrees over
+// one bounding cube: points sorted by 63-bit Morton keys, a cell split while it
+// holds more than the leaf size (cells in level order, the children of a cell
+// contiguous).  A dual-tree traversal, level-synchronous on the GPU, sorts every
+// (target cell, source cell) pair into an M2L pair when (r_T + r_S) < theta |z - c|
+// (r = half-diagonal), a P2P pair when both are leaves, and otherwise splits the
+// larger cell.  Each target point then receives every source exactly once,
+// through one M2L (plus the L2L chain below it) or one P2P pair.
+//
+// Precision: expansions and pair terms in FP32, centre differences in FP64,
+// per-target sums in FP64 (the source and target offsets of a P2P pair are
+// taken from the target leaf's centre, so their difference keeps its digits).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dtn_internal.h"
+
+namespace dtn {
+
+namespace {
+
+constexpr int kFmmMaxOrder = 16;
+constexpr int kMortonBits = 21;
+constexpr int kNcMax = (kFmmMaxOrder + 1) * (kFmmMaxOrder + 2) / 2;               // 153
+constexpr int kNsMax = (2 * kFmmMaxOrder + 1) * (2 * kFmmMaxOrder + 2) / 2;       // 561
+constexpr int kOwnMax = (kNcMax + 31) / 32;                                        // outputs per lane
+constexpr int kCellWarps = 4;                                                      // warps per CTA
+constexpr int kBboxBlocks = 256;
+
+struct FCell {
+    double c[3];            // centre
+    uint64_t key;           // Morton prefix, 3 bits per level
+    int32_t start, count;   // points [start, start + count) in Morton order
+    int32_t child, nchild;  // first child (next level, contiguous); -1 for a leaf
+    int32_t level, pad;
+};
+
+__host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+__device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a += b c
+__device__ inline void cmac(float2 &a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+// a += conj(b) c
+__device__ inline void cmac_cb(float2 &a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+
+// (n, m) of the stored coefficient idx = n(n+1)/2 + m
+__device__ inline void tri_nm(int idx, int &n, int &m) {
+    n = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+    while (tri(n + 1, 0) <= idx) ++n;
+    while (tri(n, 0) > idx) --n;
+    m = idx - tri(n, 0);
+}
+
+// Column m (R_m^m .. R_P^m) of the regular harmonics at v, into tab[tri(n, m)]:
+//   R_m^m = (x + i y)^m / (2^m m!),  R_{m+1}^m = z R_m^m,
+//   R_n^m = ((2n-1) z R_{n-1}^m - r^2 R_{n-2}^m) / ((n+m)(n-m)).
+__device__ inline void regular_column(float2 *tab, int m, int P, float x, float y, float z) {
+    const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+    float2 rmm = make_float2(1.0f, 0.0f);
+    for (int k = 1; k <= m; ++k) rmm = cscale(cmul(rmm, make_float2(x, y)), 0.5f / (float)k);
+    if (m > P) return;
+    tab[tri(m, m)] = rmm;
+    float2 a = make_float2(0.0f, 0.0f), b = rmm;
+    for (int n = m + 1; n <= P; ++n) {
+        const float inv = 1.0f / (float)((n + m) * (n - m));
+        const float2 c = make_float2(((2 * n - 1) * z * b.x - r2 * a.x) * inv, ((2 * n - 1) * z * b.y - r2 * a.y) * inv);
+        tab[tri(n, m)] = c;
+        a = b;
+        b = c;
+    }
+}
+
+// Column m (S_m^m .. S_N^m) of the singular harmonics at v:
+//   S_0^0 = 1/r,  S_m^m = (2m-1) (x + i y) / r^2 S_{m-1}^{m-1},  S_{m+1}^m = (2m+1) z / r^2 S_m^m,
+//   S_n^m = ((2n-1) z S_{n-1}^m - (n+m-1)(n-m-1) S_{n-2}^m) / r^2.
+__device__ inline void singular_column(float2 *tab, int m, int N, float x, float y, float z) {
+    const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+    const float ir2 = 1.0f / r2;
+    float2 smm = make_float2(rsqrtf(r2), 0.0f);
+    for (int k = 1; k <= m; ++k) smm = cscale(cmul(smm, make_float2(x, y)), (float)(2 * k - 1) * ir2);
+    tab[tri(m, m)] = smm;
+    float2 a = make_float2(0.0f, 0.0f), b = smm;
+    for (int n = m + 1; n <= N; ++n) {
+        const float f = (float)((n + m - 1) * (n - m - 1));
+        const float2 c = make_float2(((2 * n - 1) * z * b.x - f * a.x) * ir2, ((2 * n - 1) * z * b.y - f * a.y) * ir2);
+        tab[tri(n, m)] = c;
+        a = b;
+        b = c;
+    }
+}
+
+// A_n^m for any |m| <= n from the stored m >= 0 half
+__device__ inline float2 sym_get(const float2 *tab, int n, int m) {
+    if (m >= 0) return tab[tri(n, m)];
+    const float2 v = tab[tri(n, -m)];
+    return ((-m) & 1) ? make_float2(-v.x, v.y) : make_float2(v.x, -v.y);
+}
+
+// ------------------------------------------------------------------ tree build
+
+// Bounding box partials per block; an index outside [0, n_total) sets *bad and
+// is skipped (it is never dereferenced).
+__global__ void fmm_bbox_kernel(int64_t n, const double *__restrict__ x, const int64_t *__restrict__ index,
+                                int64_t n_total, double *__restrict__ part, int *__restrict__ bad) {
+    __shared__ double red[6][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = index ? index[i] : i;
+        if (p < 0 || p >= n_total) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        for (int a = 0; a < 3; ++a) {
+            const double v = x[3 * p + a];
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        red[a][threadIdx.x] = lo[a];
+        red[3 + a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) {
+                red[a][threadIdx.x] = fmin(red[a][threadIdx.x], red[a][threadIdx.x + o]);
+                red[3 + a][threadIdx.x] = fmax(red[3 + a][threadIdx.x], red[3 + a][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__device__ inline uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ inline uint32_t quantise(double v, double lo, double scale) {
+    const double q = floor((v - lo) * scale);
+    return (uint32_t)fmin(fmax(q, 0.0), (double)((1u << kMortonBits) - 1));
+}
+
+// key = interleaved (x, y, z) bits, x most significant; val = the point's id
+__global__ void fmm_morton_kernel(int64_t n, const double *__restrict__ x, const int64_t *__restrict__ index,
+                                  double lx, double ly, double lz, double scale, uint64_t *__restrict__ key,
+                                  int32_t *__restrict__ val) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = index ? index[i] : i;
+    key[i] = spread21(quantise(x[3 * p], lx, scale)) << 2 | spread21(quantise(x[3 * p + 1], ly, scale)) << 1 |
+             spread21(quantise(x[3 * p + 2], lz, scale));
+    val[i] = (int32_t)p;
+}
+
+// One thread per (cell of this level, octant): the run of the cell's points
+// whose next Morton digit is the octant (points are sorted, so within a cell
+// the digit is non-decreasing).
+__global__ void fmm_split_kernel(const FCell *__restrict__ cells, int64_t c0, int64_t nc,
+                                 const uint64_t *__restrict__ keys, int ncrit, int max_level,
+                                 int32_t *__restrict__ flag, int32_t *__restrict__ lo, int32_t *__restrict__ hi) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 8 * nc) return;
+    const FCell &cell = cells[c0 + i / 8];
+    const int d = (int)(i % 8);
+    if (cell.count <= ncrit || cell.level >= max_level) {
+        flag[i] = 0;
+        return;
+    }
+    const int shift = 3 * (kMortonBits - cell.level - 1);
+    const int s0 = cell.start, s1 = cell.start + cell.count;
+    auto lower = [&](int dd) {
+        int a = s0, b = s1;
+        while (a < b) {
+            const int mid = (a + b) >> 1;
+            if ((int)((keys[mid] >> shift) & 7u) < dd) a = mid + 1;
+            else b = mid;
+        }
+        return a;
+    };
+    const int l = lower(d), h = (d == 7) ? s1 : lower(d + 1);
+    flag[i] = h > l ? 1 : 0;
+    lo[i] = l;
+    hi[i] = h;
+}
+
+__global__ void fmm_emit_kernel(FCell *__restrict__ cells, int64_t c0, int64_t nc, int64_t c_next,
+                                const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                                const int32_t *__restrict__ lo, const int32_t *__restrict__ hi, double h_child) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 8 * nc) return;
+    const int64_t p = c0 + i / 8;
+    const int d = (int)(i % 8);
+    if (d == 0) {
+        int cnt = 0;
+        for (int k = 0; k < 8; ++k) cnt += flag[i + k];
+        cells[p].child = cnt ? (int32_t)(c_next + pos[i]) : -1;
+        cells[p].nchild = cnt;
+    }
+    if (!flag[i]) return;
+    FCell ch;
+    ch.c[0] = cells[p].c[0] + ((d & 4) ? h_child : -h_child);
+    ch.c[1] = cells[p].c[1] + ((d & 2) ? h_child : -h_child);
+    ch.c[2] = cells[p].c[2] + ((d & 1) ? h_child : -h_child);
+    ch.key = cells[p].key << 3 | (uint64_t)d;
+    ch.start = lo[i];
+    ch.count = hi[i] - lo[i];
+    ch.child = -1;
+    ch.nchild = 0;
+    ch.level = cells[p].level + 1;
+    ch.pad = 0;
+    cells[c_next + pos[i]] = ch;
+}
+
+// sources in Morton order: FP64 position, (dipole, charge) as float4
+__global__ void fmm_source_kernel(int64_t n, const int32_t *__restrict__ val, const double *__restrict__ xyz,
+                                  const double *__restrict__ nrm, const double *__restrict__ area,
+                                  const double *__restrict__ q, const double *__restrict__ g,
+                                  double *__restrict__ spos, float4 *__restrict__ sdat) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = val[i];
+    const double inv4pi = 0.25 / kPi;
+    const double c = area[p] * q[p] * inv4pi, dd = -area[p] * g[p] * inv4pi;
+    spos[3 * i] = xyz[3 * p];
+    spos[3 * i + 1] = xyz[3 * p + 1];
+    spos[3 * i + 2] = xyz[3 * p + 2];
+    sdat[i] = make_float4((float)(dd * nrm[3 * p]), (float)(dd * nrm[3 * p + 1]), (float)(dd * nrm[3 * p + 2]),
+                          (float)c);
+}
+
+// ------------------------------------------------------------------ upward pass
+
+struct FmmShared {
+    float2 tab[kNsMax];   // R or S table
+    float2 exp[kNcMax];   // a staged expansion
+};
+
+// P2M: one warp per source leaf; the warp builds each source's regular table
+// (lane m computes column m) and every lane accumulates the coefficients it owns.
+__global__ void __launch_bounds__(32 * kCellWarps) fmm_p2m_kernel(
+    const FCell *__restrict__ cells, int64_t ncell, const double *__restrict__ spos,
+    const float4 *__restrict__ sdat, double half_w0, int P, float2 *__restrict__ M) {
+    __shared__ FmmShared sh[kCellWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ci = blockIdx.x * (int64_t)kCellWarps + wid;
+    if (ci >= ncell) return;
+    const FCell cell = cells[ci];
+    if (cell.child >= 0) return;
+    const int nc = tri(P + 1, 0);
+    const double h = ldexp(half_w0, -cell.level);
+    const float ih = (float)(1.0 / h);
+    float2 acc[kOwnMax];
+    int on[kOwnMax], om[kOwnMax];
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r) {
+        acc[r] = make_float2(0.0f, 0.0f);
+        const int idx = lane + 32 * r;
+        if (idx < nc) tri_nm(idx, on[r], om[r]);
+        else on[r] = om[r] = 0;
+    }
+    float2 *tab = sh[wid].tab;
+    for (int s = cell.start; s < cell.start + cell.count; ++s) {
+        const float vx = (float)((spos[3 * s] - cell.c[0]) / h), vy = (float)((spos[3 * s + 1] - cell.c[1]) / h),
+                    vz = (float)((spos[3 * s + 2] - cell.c[2]) / h);
+        const float4 sd = sdat[s];
+        __syncwarp();
+        if (lane <= P) regular_column(tab, lane, P, vx, vy, vz);
+        __syncwarp();
+        const float dx = sd.x * ih, dy = sd.y * ih, dz = sd.z * ih, c = sd.w;
+        const float2 dp = make_float2(0.5f * dx, 0.5f * dy);    // (dx + i dy) / 2
+        const float2 dm = make_float2(0.5f * dx, -0.5f * dy);   // (dx - i dy) / 2
+#pragma unroll
+        for (int r = 0; r < kOwnMax; ++r) {
+            if (lane + 32 * r >= nc) break;
+            const int n = on[r], m = om[r];
+            float2 t = cscale(tab[tri(n, m)], c);
+            if (n >= 1) {
+                // R_{n-1}^{m-1} (m = 0: -conj(R_{n-1}^1)), R_{n-1}^{m+1}, R_{n-1}^m
+                float2 rm1 = make_float2(0.0f, 0.0f);
+                if (m >= 1) rm1 = tab[tri(n - 1, m - 1)];
+                else if (n - 1 >= 1) { const float2 v = tab[tri(n - 1, 1)]; rm1 = make_float2(-v.x, v.y); }
+                if (m - 1 <= n - 1) cmac(t, dp, rm1);
+                if (m + 1 <= n - 1) { const float2 v = tab[tri(n - 1, m + 1)]; cmac(t, make_float2(-dm.x, -dm.y), v); }
+                if (m <= n - 1) { const float2 v = tab[tri(n - 1, m)]; t.x = fmaf(dz, v.x, t.x); t.y = fmaf(dz, v.y, t.y); }
+            }
+            acc[r] = cadd(acc[r], cconj(t));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r)
+        if (lane + 32 * r < nc) M[ci * nc + lane + 32 * r] = acc[r];
+}
+
+// M2M for the split cells of one level: M'_n^m = sum conj(R_k^l(d)) 2^{-(n-k)} M_{n-k}^{m-l},
+// d = (child centre - parent centre) / h_parent.
+__global__ void __launch_bounds__(32 * kCellWarps) fmm_m2m_kernel(
+    const FCell *__restrict__ cells, int64_t c0, int64_t ncell, double half_w0, int P, float2 *__restrict__ M) {
+    __shared__ FmmShared sh[kCellWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ci = c0 + blockIdx.x * (int64_t)kCellWarps + wid;
+    if (ci >= c0 + ncell) return;
+    const FCell cell = cells[ci];
+    if (cell.child < 0) return;
+    const int nc = tri(P + 1, 0);
+    const double h = ldexp(half_w0, -cell.level);
+    float2 acc[kOwnMax];
+    int on[kOwnMax], om[kOwnMax];
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r) {
+        acc[r] = make_float2(0.0f, 0.0f);
+        const int idx = lane + 32 * r;
+        if (idx < nc) tri_nm(idx, on[r], om[r]);
+        else on[r] = om[r] = 0;
+    }
+    float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
+    for (int k = 0; k < cell.nchild; ++k) {
+        const int64_t cc = cell.child + k;
+        const float dx = (float)((cells[cc].c[0] - cell.c[0]) / h), dy = (float)((cells[cc].c[1] - cell.c[1]) / h),
+                    dz = (float)((cells[cc].c[2] - cell.c[2]) / h);
+        __syncwarp();
+        if (lane <= P) regular_column(tab, lane, P, dx, dy, dz);
+        for (int e = lane; e < nc; e += 32) ex[e] = M[cc * nc + e];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kOwnMax; ++r) {
+            if (lane + 32 * r >= nc) break;
+            const int n = on[r], m = om[r];
+            float2 s = make_float2(0.0f, 0.0f);
+            for (int kk = 0; kk <= n; ++kk) {
+                const int nn = n - kk;
+                const float sc = ldexpf(1.0f, -nn);
+                const int l0 = max(-kk, m - nn), l1 = min(kk, m + nn);
+                for (int l = l0; l <= l1; ++l) {
+                    const float2 rv = sym_get(tab, kk, l);
+                    const float2 mv = sym_get(ex, nn, m - l);
+                    cmac_cb(s, cscale(rv, sc), mv);
+                }
+            }
+            acc[r] = cadd(acc[r], s);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r)
+        if (lane + 32 * r < nc) M[ci * nc + lane + 32 * r] = acc[r];
+}
+
+// ------------------------------------------------------------------ traversal
+
+struct DttCounters {
+    unsigned long long next, m2l, p2p, p2p_terms, overflow;
+};
+
+__global__ void fmm_dtt_kernel(const int2 *__restrict__ front, int64_t nf, const FCell *__restrict__ tc,
+                               const FCell *__restrict__ sc, double r0, double theta2, int2 *__restrict__ next,
+                               int64_t cap_next, uint64_t *__restrict__ m2l, int64_t cap_m2l,
+                               uint64_t *__restrict__ p2p, int64_t cap_p2p, DttCounters *__restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const int2 pr = front[i];
+    const FCell &T = tc[pr.x];
+    const FCell &S = sc[pr.y];
+    const double rt = ldexp(r0, -T.level), rs = ldexp(r0, -S.level);
+    const double dx = T.c[0] - S.c[0], dy = T.c[1] - S.c[1], dz = T.c[2] - S.c[2];
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    const bool tleaf = T.child < 0, sleaf = S.child < 0;
+    if ((rt + rs) * (rt + rs) < theta2 * d2) {
+        const unsigned long long k = atomicAdd(&cnt->m2l, 1ull);
+        if ((int64_t)k < cap_m2l) m2l[k] = (uint64_t)(uint32_t)pr.x << 32 | (uint32_t)pr.y;
+        else cnt->overflow = 1;
+    } else if (tleaf && sleaf) {
+        const unsigned long long k = atomicAdd(&cnt->p2p, 1ull);
+        atomicAdd(&cnt->p2p_terms, (unsigned long long)T.count * (unsigned long long)S.count);
+        if ((int64_t)k < cap_p2p) p2p[k] = (uint64_t)(uint32_t)pr.x << 32 | (uint32_t)pr.y;
+        else cnt->overflow = 1;
+    } else {
+        const bool split_t = sleaf || (!tleaf && rt >= rs);
+        const int first = split_t ? T.child : S.child, nch = split_t ? T.nchild : S.nchild;
+        const unsigned long long k = atomicAdd(&cnt->next, (unsigned long long)nch);
+        if ((int64_t)(k + nch) <= cap_next) {
+            for (int c = 0; c < nch; ++c)
+                next[k + c] = split_t ? make_int2(first + c, pr.y) : make_int2(pr.x, first + c);
+        } else {
+            cnt->overflow = 1;
+        }
+    }
+}
+
+// CSR offsets of a list of (target << 32 | source) keys sorted ascending
+__global__ void fmm_csr_kernel(int64_t ncell, const uint64_t *__restrict__ keys, int64_t n, int64_t *__restrict__ off) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t > ncell) return;
+    const uint64_t want = (uint64_t)t << 32;
+    int64_t a = 0, b = n;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (keys[mid] < want) a = mid + 1;
+        else b = mid;
+    }
+    off[t] = a;
+}
+
+// ------------------------------------------------------------------ downward pass
+
+// M2L: one warp per target cell, over its sorted source list.  Lanes build the
+// singular table at (z - c)/rho to degree 2P (lane m: columns m and m + 32),
+// stage the source's scaled expansion, and accumulate the coefficients they own:
+//   L_n^m = (-1)^{n+m} (h_T/rho)^n / rho sum_j sum_k S_{j+n}^{k-m} (h_S/rho)^j M_j^k,
+// rho = max(h_T, h_S); the k < 0 half enters as (-1)^m conj(sum_{k>0} M_j^k S_{j+n}^{m+k}).
+// Writes L for every cell (zero for an empty list).
+__global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
+    const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
+    const uint64_t *__restrict__ list, double half_w0, int P, const float2 *__restrict__ M, float2 *__restrict__ L) {
+    __shared__ FmmShared sh[kCellWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ti = blockIdx.x * (int64_t)kCellWarps + wid;
+    if (ti >= ntc) return;
+    const FCell T = tc[ti];
+    const int nc = tri(P + 1, 0);
+    float2 acc[kOwnMax];
+    int on[kOwnMax], om[kOwnMax];
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r) {
+        acc[r] = make_float2(0.0f, 0.0f);
+        const int idx = lane + 32 * r;
+        if (idx < nc) tri_nm(idx, on[r], om[r]);
+        else on[r] = om[r] = 0;
+    }
+    float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
+    const int64_t e0 = off[ti], e1 = off[ti + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int64_t si = (int64_t)(uint32_t)(list[e] & 0xffffffffu);
+        const FCell &S = sc[si];
+        const int lt = T.level, ls = S.level;
+        const int lr = min(lt, ls);                    // rho = h at the coarser level
+        const double rho = ldexp(half_w0, -lr);
+        const float vx = (float)((T.c[0] - S.c[0]) / rho), vy = (float)((T.c[1] - S.c[1]) / rho),
+                    vz = (float)((T.c[2] - S.c[2]) / rho);
+        const int bt = lt - lr, bs = ls - lr;          // h_T / rho = 2^-bt, h_S / rho = 2^-bs
+        __syncwarp();
+        for (int m = lane; m <= 2 * P; m += 32) singular_column(tab, m, 2 * P, vx, vy, vz);
+        for (int q = lane; q < nc; q += 32) {
+            int n, m;
+            tri_nm(q, n, m);
+            const float2 v = M[si * nc + q];
+            ex[q] = make_float2(ldexpf(v.x, -n * bs), ldexpf(v.y, -n * bs));
+        }
+        __syncwarp();
+        const float irho = (float)(1.0 / rho);
+#pragma unroll
+        for (int r = 0; r < kOwnMax; ++r) {
+            if (lane + 32 * r >= nc) break;
+            const int n = on[r], m = om[r];
+            float2 s = make_float2(0.0f, 0.0f), t = make_float2(0.0f, 0.0f);
+            for (int j = 0; j <= P; ++j) {
+                const float2 *Sj = tab + tri(j + n, 0);
+                const float2 *Mj = ex + tri(j, 0);
+                // k in [0, min(j, m-1)]: S_{j+n}^{k-m} = (-1)^{m-k} conj(S_{j+n}^{m-k})
+                const int kk = min(j, m - 1);
+                for (int k = 0; k <= kk; ++k) {
+                    const float2 sv = Sj[m - k];
+                    const float2 c = ((m - k) & 1) ? make_float2(-sv.x, sv.y) : make_float2(sv.x, -sv.y);
+                    cmac(s, c, Mj[k]);
+                }
+                // k in [m, j]: S_{j+n}^{k-m}
+                for (int k = m; k <= j; ++k) cmac(s, Sj[k - m], Mj[k]);
+                // k' in [1, j]: M_j^{k'} S_{j+n}^{m+k'}
+                for (int k = 1; k <= j; ++k) cmac(t, Mj[k], Sj[m + k]);
+            }
+            // s + (-1)^m conj(t), times (-1)^{n+m} (h_T/rho)^n / rho
+            const float sg = (m & 1) ? -1.0f : 1.0f;
+            float2 v = make_float2(s.x + sg * t.x, s.y - sg * t.y);
+            const float f = ldexpf(((n + m) & 1) ? -irho : irho, -n * bt);
+            acc[r] = make_float2(fmaf(f, v.x, acc[r].x), fmaf(f, v.y, acc[r].y));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kOwnMax; ++r)
+        if (lane + 32 * r < nc) L[ti * nc + lane + 32 * r] = acc[r];
+}
+
+// L2L for the cells of one level (parent complete): L'_k^l += 2^-k sum_{n>=k,m} L_n^m R_{n-k}^{m-l}(d),
+// d = (child centre - parent centre) / h_parent.  The root has no parent.
+__global__ void __launch_bounds__(32 * kCellWarps) fmm_l2l_kernel(
+    const FCell *__restrict__ tc, int64_t c0, int64_t ncell, const int32_t *__restrict__ parent, double half_w0,
+    int P, float2 *__restrict__ L) {
+    __shared__ FmmShared sh[kCellWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ci = c0 + blockIdx.x * (int64_t)kCellWarps + wid;
+    if (ci >= c0 + ncell) return;
+    const int64_t pi = parent[ci];
+    const FCell &C = tc[ci];
+    const FCell &Pp = tc[pi];
+    const int nc = tri(P + 1, 0);
+    const double h = ldexp(half_w0, -Pp.level);
+    const float dx = (float)((C.c[0] - Pp.c[0]) / h), dy = (float)((C.c[1] - Pp.c[1]) / h),
+                dz = (float)((C.c[2] - Pp.c[2]) / h);
+    float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
+    if (lane <= P) regular_column(tab, lane, P, dx, dy, dz);
+    for (int q = lane; q < nc; q += 32) ex[q] = L[pi * nc + q];
+    __syncwarp();
+    for (int q = lane; q < nc; q += 32) {
+        int k, l;
+        tri_nm(q, k, l);
+        float2 s = make_float2(0.0f, 0.0f);
+        for (int n = k; n <= P; ++n) {
+            const int d = n - k;
+            const int m0 = max(-n, l - d), m1 = min(n, l + d);
+            for (int m = m0; m <= m1; ++m) cmac(s, sym_get(ex, n, m), sym_get(tab, d, m - l));
+        }
+        const float sc = ldexpf(1.0f, -k);
+        L[ci * nc + q] = make_float2(fmaf(sc, s.x, L[ci * nc + q].x), fmaf(sc, s.y, L[ci * nc + q].y));
+    }
+}
+
+__global__ void fmm_parent_kernel(const FCell *__restrict__ tc, int64_t ncell, int32_t *__restrict__ parent) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ncell) return;
+    if (i == 0) parent[0] = -1;
+    const FCell &c = tc[i];
+    for (int k = 0; k < c.nchild; ++k) parent[c.child + k] = (int32_t)i;
+}
+
+// Target leaves: one warp per leaf, a lane per target.  L2P by the regular
+// recurrence at (t - z)/h with the leaf's local expansion in shared memory, then
+// P2P over the leaf's source leaves (staged 32 at a time as FP32 offsets from
+// the target leaf's centre); FP64 sum per target.
+__global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
+    const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
+    const uint64_t *__restrict__ list, const int32_t *__restrict__ tval, const double *__restrict__ targets,
+    const double *__restrict__ spos, const float4 *__restrict__ sdat, double half_w0, int P,
+    const float2 *__restrict__ L, double *__restrict__ out) {
+    __shared__ float2 sl[kCellWarps][kNcMax];
+    __shared__ float4 sa[kCellWarps][32], sb[kCellWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ti = blockIdx.x * (int64_t)kCellWarps + wid;
+    if (ti >= ntc) return;
+    const FCell T = tc[ti];
+    if (T.child >= 0) return;
+    const int nc = tri(P + 1, 0);
+    for (int q = lane; q < nc; q += 32) sl[wid][q] = L[ti * nc + q];
+    const double h = ldexp(half_w0, -T.level);
+    const int64_t e0 = off[ti], e1 = off[ti + 1];
+    for (int tb = T.start; tb < T.start + T.count; tb += 32) {
+        const int it = tb + lane;
+        const bool valid = it < T.start + T.count;
+        const int32_t id = valid ? tval[it] : 0;
+        const double ex = valid ? targets[3 * id] - T.c[0] : 0.0, ey = valid ? targets[3 * id + 1] - T.c[1] : 0.0,
+                     ez = valid ? targets[3 * id + 2] - T.c[2] : 0.0;
+        __syncwarp();
+        // L2P: u = sum_n [R_n^0 L_n^0 + 2 Re sum_{m>0} R_n^m L_n^m]
+        const float x = (float)(ex / h), y = (float)(ey / h), z = (float)(ez / h);
+        const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+        float far = 0.0f;
+        float2 rmm = make_float2(1.0f, 0.0f);
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) rmm = cscale(cmul(rmm, make_float2(x, y)), 0.5f / (float)m);
+            const float wgt = m ? 2.0f : 1.0f;
+            float2 a = make_float2(0.0f, 0.0f), b = rmm;
+            float part = b.x * sl[wid][tri(m, m)].x - b.y * sl[wid][tri(m, m)].y;
+            for (int n = m + 1; n <= P; ++n) {
+                const float inv = 1.0f / (float)((n + m) * (n - m));
+                const float2 c = make_float2(((2 * n - 1) * z * b.x - r2 * a.x) * inv,
+                                             ((2 * n - 1) * z * b.y - r2 * a.y) * inv);
+                const float2 lv = sl[wid][tri(n, m)];
+                part = fmaf(c.x, lv.x, fmaf(-c.y, lv.y, part));
+                a = b;
+                b = c;
+            }
+            far = fmaf(wgt, part, far);
+        }
+        double acc = (double)far;
+        // P2P
+        const float ox = (float)ex, oy = (float)ey, oz = (float)ez;
+        for (int64_t e = e0; e < e1; ++e) {
+            const FCell &S = sc[(uint32_t)(list[e] & 0xffffffffu)];
+            float part = 0.0f;
+            for (int sbase = S.start; sbase < S.start + S.count; sbase += 32) {
+                const int cnt = min(32, S.start + S.count - sbase);
+                __syncwarp();
+                if (lane < cnt) {
+                    const int s = sbase + lane;
+                    const float4 d = sdat[s];
+                    sa[wid][lane] = make_float4((float)(spos[3 * s] - T.c[0]), (float)(spos[3 * s + 1] - T.c[1]),
+                                                (float)(spos[3 * s + 2] - T.c[2]), d.w);
+                    sb[wid][lane] = make_float4(d.x, d.y, d.z, 0.0f);
+                }
+                __syncwarp();
+                for (int k = 0; k < cnt; ++k) {
+                    const float4 pa = sa[wid][k], pb = sb[wid][k];
+                    const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
+                    const float rr = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float ri = rsqrtf(rr);
+                    const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+                    part += ri * fmaf(dn, ri * ri, pa.w);
+                }
+            }
+            acc += (double)part;
+        }
+        if (valid) out[id] = acc;
+    }
+}
+
+__global__ void fmm_zero_kernel(int64_t n, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = 0.0;
+}
+
+inline int64_t nblk(int64_t n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+struct FmmWorkspace {
+    DevBuf part, kin, kout, vin, sval, tval, flag, pos, lo, hi, cub, scell, tcell, tparent;
+    DevBuf spos, sdat, M, L, front, next, m2l, m2l_s, p2p, p2p_s, m2l_off, p2p_off, cnt, gtmp;
+    DttCounters *host_cnt = nullptr;   // pinned
+    int64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;
+};
+
+void fmm_release(dtn_geometry *g) {
+    FmmWorkspace *w = static_cast<FmmWorkspace *>(g->fmm_ws);
+    if (!w) return;
+    DevBuf *bufs[] = {&w->part, &w->kin, &w->kout, &w->vin, &w->sval, &w->tval, &w->flag, &w->pos, &w->lo,
+                      &w->hi, &w->cub, &w->scell, &w->tcell, &w->tparent, &w->spos, &w->sdat, &w->M, &w->L,
+                      &w->front, &w->next, &w->m2l, &w->m2l_s, &w->p2p, &w->p2p_s, &w->m2l_off, &w->p2p_off,
+                      &w->cnt, &w->gtmp};
+    for (DevBuf *b : bufs) b->release();
+    if (w->host_cnt) cudaFreeHost(w->host_cnt);
+    delete w;
+    g->fmm_ws = nullptr;
+}
+
+namespace {
+
+#define FMM_TRY(x)                                   \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return e_;            \
+    } while (0)
+
+// grow a buffer keeping its first `keep` bytes (stream-ordered copy)
+cudaError_t grow_keep(DevBuf &b, size_t need, size_t keep, cudaStream_t s) {
+    if (need <= b.bytes && b.p) return cudaSuccess;
+    void *np = nullptr;
+    const size_t want = std::max(need, b.bytes * 3 / 2);
+    FMM_TRY(cudaMalloc(&np, want));
+    if (b.p && keep) FMM_TRY(cudaMemcpyAsync(np, b.p, keep, cudaMemcpyDeviceToDevice, s));
+    FMM_TRY(cudaStreamSynchronize(s));
+    b.release();
+    b.p = np;
+    b.bytes = want;
+    return cudaSuccess;
+}
+
+struct TreeInfo {
+    std::vector<int64_t> level_off;   // cells of level l: [level_off[l], level_off[l+1])
+    int64_t ncell = 0, nleaf = 0;
+};
+
+// Sorts the points by Morton key and builds the cells level by level.
+cudaError_t build_tree(FmmWorkspace &w, DevBuf &cells, DevBuf &val_out, int64_t n, const double *x,
+                       const int64_t *index, const double lo[3], double width, int ncrit, int max_level,
+                       TreeInfo &ti, cudaStream_t s) {
+    const double scale = std::ldexp(1.0, kMortonBits) / width;
+    FMM_TRY(w.kin.reserve(n * 8));
+    FMM_TRY(w.kout.reserve(n * 8));
+    FMM_TRY(w.vin.reserve(n * 4));
+    FMM_TRY(val_out.reserve(n * 4));
+    fmm_morton_kernel<<<nblk(n, 256), 256, 0, s>>>(n, x, index, lo[0], lo[1], lo[2], scale, w.kin.as<uint64_t>(),
+                                                    w.vin.as<int32_t>());
+    FMM_TRY(cudaGetLastError());
+    size_t tb = 0;
+    FMM_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, w.kin.as<uint64_t>(), w.kout.as<uint64_t>(),
+                                            w.vin.as<int32_t>(), val_out.as<int32_t>(), (int)n, 0, 3 * kMortonBits, s));
+    FMM_TRY(w.cub.reserve(tb));
+    FMM_TRY(cub::DeviceRadixSort::SortPairs(w.cub.p, tb, w.kin.as<uint64_t>(), w.kout.as<uint64_t>(),
+                                            w.vin.as<int32_t>(), val_out.as<int32_t>(), (int)n, 0, 3 * kMortonBits, s));
+    const uint64_t *keys = w.kout.as<uint64_t>();
+    // root
+    FCell root{};
+    root.c[0] = lo[0] + 0.5 * width;
+    root.c[1] = lo[1] + 0.5 * width;
+    root.c[2] = lo[2] + 0.5 * width;
+    root.key = 0;
+    root.start = 0;
+    root.count = (int32_t)n;
+    root.child = -1;
+    root.nchild = 0;
+    root.level = 0;
+    FMM_TRY(grow_keep(cells, sizeof(FCell) * 1024, 0, s));
+    FMM_TRY(cudaMemcpyAsync(cells.p, &root, sizeof(FCell), cudaMemcpyHostToDevice, s));
+    ti.level_off.assign({0, 1});
+    for (int l = 0; l < max_level; ++l) {
+        const int64_t c0 = ti.level_off[l], nc = ti.level_off[l + 1] - c0;
+        if (nc == 0) break;
+        FMM_TRY(w.flag.reserve(8 * nc * 4));
+        FMM_TRY(w.pos.reserve(8 * nc * 4));
+        FMM_TRY(w.lo.reserve(8 * nc * 4));
+        FMM_TRY(w.hi.reserve(8 * nc * 4));
+        fmm_split_kernel<<<nblk(8 * nc, 256), 256, 0, s>>>(cells.as<FCell>(), c0, nc, keys, ncrit, max_level,
+                                                            w.flag.as<int32_t>(), w.lo.as<int32_t>(),
+                                                            w.hi.as<int32_t>());
+        FMM_TRY(cudaGetLastError());
+        size_t sb = 0;
+        FMM_TRY(cub::DeviceScan::ExclusiveSum(nullptr, sb, w.flag.as<int32_t>(), w.pos.as<int32_t>(), (int)(8 * nc), s));
+        FMM_TRY(w.cub.reserve(std::max(sb, w.cub.bytes)));
+        FMM_TRY(cub::DeviceScan::ExclusiveSum(w.cub.p, sb, w.flag.as<int32_t>(), w.pos.as<int32_t>(), (int)(8 * nc), s));
+        int32_t tail[2];
+        FMM_TRY(cudaMemcpyAsync(&tail[0], w.pos.as<int32_t>() + 8 * nc - 1, 4, cudaMemcpyDeviceToHost, s));
+        FMM_TRY(cudaMemcpyAsync(&tail[1], w.flag.as<int32_t>() + 8 * nc - 1, 4, cudaMemcpyDeviceToHost, s));
+        FMM_TRY(cudaStreamSynchronize(s));
+        const int64_t total = (int64_t)tail[0] + tail[1];
+        const int64_t c_next = c0 + nc;
+        FMM_TRY(grow_keep(cells, sizeof(FCell) * (c_next + std::max<int64_t>(total, 1)), sizeof(FCell) * c_next, s));
+        const double h_child = std::ldexp(width, -(l + 2));
+        fmm_emit_kernel<<<nblk(8 * nc, 256), 256, 0, s>>>(cells.as<FCell>(), c0, nc, c_next, w.flag.as<int32_t>(),
+                                                           w.pos.as<int32_t>(), w.lo.as<int32_t>(),
+                                                           w.hi.as<int32_t>(), h_child);
+        FMM_TRY(cudaGetLastError());
+        if (total == 0) break;
+        ti.level_off.push_back(c_next + total);
+    }
+    ti.ncell = ti.level_off.back();
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const double *xyz, const double *nrm,
+                         const double *area, const double *q, const double *gv, const int64_t *index, int64_t nt,
+                         const double *t, double *out, const dtn_fmm_opts &o, dtn_fmm_stats *st, bool *bad_index,
+                         cudaStream_t s) {
+    *bad_index = false;
+    if (!g->fmm_ws) g->fmm_ws = new FmmWorkspace();
+    FmmWorkspace &w = *static_cast<FmmWorkspace *>(g->fmm_ws);
+    if (!w.host_cnt) FMM_TRY(cudaMallocHost((void **)&w.host_cnt, sizeof(DttCounters)));
+    dtn_fmm_stats stats{};
+    if (np == 0) {
+        fmm_zero_kernel<<<nblk(nt, 256), 256, 0, s>>>(nt, out);
+        FMM_TRY(cudaGetLastError());
+        if (st) *st = stats;
+        return cudaSuccess;
+    }
+    // bounding cube of sources and targets
+    const size_t part_bytes = 2 * kBboxBlocks * 6 * sizeof(double);
+    FMM_TRY(w.part.reserve(part_bytes + 16));
+    int *d_bad = reinterpret_cast<int *>(w.part.as<char>() + part_bytes);
+    FMM_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    fmm_bbox_kernel<<<kBboxBlocks, 256, 0, s>>>(np, xyz, index, np_total, w.part.as<double>(), d_bad);
+    fmm_bbox_kernel<<<kBboxBlocks, 256, 0, s>>>(nt, t, nullptr, nt, w.part.as<double>() + kBboxBlocks * 6, d_bad);
+    FMM_TRY(cudaGetLastError());
+    std::vector<double> part(2 * kBboxBlocks * 6 + 2);
+    FMM_TRY(cudaMemcpyAsync(part.data(), w.part.p, part_bytes + 16, cudaMemcpyDeviceToHost, s));
+    FMM_TRY(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<const int *>(part.data() + 2 * kBboxBlocks * 6)) {
+        *bad_index = true;
+        return cudaSuccess;
+    }
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < 2 * kBboxBlocks; ++b)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], part[6 * b + a]);
+            hi[a] = std::max(hi[a], part[6 * b + 3 + a]);
+        }
+    double width = 0.0;
+    for (int a = 0; a < 3; ++a) width = std::max(width, hi[a] - lo[a]);
+    if (!std::isfinite(width)) return cudaErrorInvalidValue;
+    width = width * (1.0 + 1e-9) + 1e-300;
+    for (int a = 0; a < 3; ++a) lo[a] -= 0.5 * (width - (hi[a] - lo[a]));   // centre the cube on the box
+    const double half_w0 = 0.5 * width, r0 = std::sqrt(3.0) * half_w0;
+
+    // trees
+    TreeInfo st_s, st_t;
+    FMM_TRY(build_tree(w, w.scell, w.sval, np, xyz, index, lo, width, o.leaf_sources, o.max_level, st_s, s));
+    FMM_TRY(w.spos.reserve(np * 24));
+    FMM_TRY(w.sdat.reserve(np * 16));
+    fmm_source_kernel<<<nblk(np, 256), 256, 0, s>>>(np, w.sval.as<int32_t>(), xyz, nrm, area, q, gv,
+                                                     w.spos.as<double>(), w.sdat.as<float4>());
+    FMM_TRY(cudaGetLastError());
+    FMM_TRY(build_tree(w, w.tcell, w.tval, nt, t, nullptr, lo, width, o.leaf_targets, o.max_level, st_t, s));
+    const int64_t nsc = st_s.ncell, ntc = st_t.ncell;
+    const int P = o.order, nc = tri(P + 1, 0);
+
+    // upward pass
+    FMM_TRY(w.M.reserve(nsc * nc * sizeof(float2)));
+    fmm_p2m_kernel<<<nblk(nsc, kCellWarps), 32 * kCellWarps, 0, s>>>(w.scell.as<FCell>(), nsc, w.spos.as<double>(),
+                                                                     w.sdat.as<float4>(), half_w0, P,
+                                                                     w.M.as<float2>());
+    FMM_TRY(cudaGetLastError());
+    for (int l = (int)st_s.level_off.size() - 2; l >= 0; --l) {
+        const int64_t c0 = st_s.level_off[l], n = st_s.level_off[l + 1] - c0;
+        fmm_m2m_kernel<<<nblk(n, kCellWarps), 32 * kCellWarps, 0, s>>>(w.scell.as<FCell>(), c0, n, half_w0, P,
+                                                                       w.M.as<float2>());
+        FMM_TRY(cudaGetLastError());
+    }
+
+    // dual-tree traversal
+    // list capacities from the tree sizes (grown and the traversal restarted on overflow)
+    w.cap_front = std::max(w.cap_front, 32 * (nsc + ntc) + 4096);
+    w.cap_m2l = std::max(w.cap_m2l, 256 * ntc + 4096);
+    w.cap_p2p = std::max(w.cap_p2p, 64 * ntc + 4096);
+    int64_t n_m2l = 0, n_p2p = 0;
+    int passes = 0, restarts = 0;
+    for (;;) {
+        FMM_TRY(w.front.reserve(w.cap_front * sizeof(int2)));
+        FMM_TRY(w.next.reserve(w.cap_front * sizeof(int2)));
+        FMM_TRY(w.m2l.reserve(w.cap_m2l * 8));
+        FMM_TRY(w.p2p.reserve(w.cap_p2p * 8));
+        FMM_TRY(w.cnt.reserve(sizeof(DttCounters)));
+        FMM_TRY(cudaMemsetAsync(w.cnt.p, 0, sizeof(DttCounters), s));
+        const int2 root = make_int2(0, 0);
+        FMM_TRY(cudaMemcpyAsync(w.front.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
+        int64_t nf = 1;
+        bool overflow = false;
+        passes = 0;
+        while (nf > 0) {
+            FMM_TRY(cudaMemsetAsync(w.cnt.p, 0, sizeof(unsigned long long), s));   // next = 0
+            fmm_dtt_kernel<<<nblk(nf, 256), 256, 0, s>>>(
+                w.front.as<int2>(), nf, w.tcell.as<FCell>(), w.scell.as<FCell>(), r0, o.theta * o.theta,
+                w.next.as<int2>(), w.cap_front, w.m2l.as<uint64_t>(), w.cap_m2l, w.p2p.as<uint64_t>(), w.cap_p2p,
+                w.cnt.as<DttCounters>());
+            FMM_TRY(cudaGetLastError());
+            FMM_TRY(cudaMemcpyAsync(w.host_cnt, w.cnt.p, sizeof(DttCounters), cudaMemcpyDeviceToHost, s));
+            FMM_TRY(cudaStreamSynchronize(s));
+            ++passes;
+            const DttCounters c = *w.host_cnt;
+            if (c.overflow) {
+                overflow = true;
+                if ((int64_t)c.next > w.cap_front) w.cap_front = 2 * (int64_t)c.next;
+                if ((int64_t)c.m2l >= w.cap_m2l) w.cap_m2l = 2 * (int64_t)c.m2l;
+                if ((int64_t)c.p2p >= w.cap_p2p) w.cap_p2p = 2 * (int64_t)c.p2p;
+                break;
+            }
+            std::swap(w.front, w.next);
+            nf = (int64_t)c.next;
+            n_m2l = (int64_t)c.m2l;
+            n_p2p = (int64_t)c.p2p;
+            stats.p2p_terms = (int64_t)c.p2p_terms;
+        }
+        if (!overflow) break;
+        ++restarts;
+    }
+    // sort both lists by target and build their offsets
+    FMM_TRY(w.m2l_s.reserve(std::max<int64_t>(n_m2l, 1) * 8));
+    FMM_TRY(w.p2p_s.reserve(std::max<int64_t>(n_p2p, 1) * 8));
+    {
+        size_t tb1 = 0, tb2 = 0;
+        FMM_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb1, w.m2l.as<uint64_t>(), w.m2l_s.as<uint64_t>(), (int)n_m2l, 0, 64, s));
+        FMM_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb2, w.p2p.as<uint64_t>(), w.p2p_s.as<uint64_t>(), (int)n_p2p, 0, 64, s));
+        FMM_TRY(w.cub.reserve(std::max(std::max(tb1, tb2), w.cub.bytes)));
+        size_t tb = w.cub.bytes;
+        FMM_TRY(cub::DeviceRadixSort::SortKeys(w.cub.p, tb, w.m2l.as<uint64_t>(), w.m2l_s.as<uint64_t>(), (int)n_m2l, 0, 64, s));
+        tb = w.cub.bytes;
+        FMM_TRY(cub::DeviceRadixSort::SortKeys(w.cub.p, tb, w.p2p.as<uint64_t>(), w.p2p_s.as<uint64_t>(), (int)n_p2p, 0, 64, s));
+    }
+    FMM_TRY(w.m2l_off.reserve((ntc + 1) * 8));
+    FMM_TRY(w.p2p_off.reserve((ntc + 1) * 8));
+    fmm_csr_kernel<<<nblk(ntc + 1, 256), 256, 0, s>>>(ntc, w.m2l_s.as<uint64_t>(), n_m2l, w.m2l_off.as<int64_t>());
+    fmm_csr_kernel<<<nblk(ntc + 1, 256), 256, 0, s>>>(ntc, w.p2p_s.as<uint64_t>(), n_p2p, w.p2p_off.as<int64_t>());
+    FMM_TRY(cudaGetLastError());
+
+    // downward pass
+    FMM_TRY(w.L.reserve(ntc * nc * sizeof(float2)));
+    fmm_m2l_kernel<<<nblk(ntc, kCellWarps), 32 * kCellWarps, 0, s>>>(
+        w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.m2l_off.as<int64_t>(), w.m2l_s.as<uint64_t>(), half_w0, P,
+        w.M.as<float2>(), w.L.as<float2>());
+    FMM_TRY(cudaGetLastError());
+    FMM_TRY(w.tparent.reserve(ntc * 4));
+    fmm_parent_kernel<<<nblk(ntc, 256), 256, 0, s>>>(w.tcell.as<FCell>(), ntc, w.tparent.as<int32_t>());
+    FMM_TRY(cudaGetLastError());
+    for (size_t l = 1; l + 1 < st_t.level_off.size(); ++l) {
+        const int64_t c0 = st_t.level_off[l], n = st_t.level_off[l + 1] - c0;
+        fmm_l2l_kernel<<<nblk(n, kCellWarps), 32 * kCellWarps, 0, s>>>(w.tcell.as<FCell>(), c0, n,
+                                                                       w.tparent.as<int32_t>(), half_w0, P,
+                                                                       w.L.as<float2>());
+        FMM_TRY(cudaGetLastError());
+    }
+    fmm_leaf_kernel<<<nblk(ntc, kCellWarps), 32 * kCellWarps, 0, s>>>(
+        w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.p2p_off.as<int64_t>(), w.p2p_s.as<uint64_t>(),
+        w.tval.as<int32_t>(), t, w.spos.as<double>(), w.sdat.as<float4>(), half_w0, P, w.L.as<float2>(), out);
+    FMM_TRY(cudaGetLastError());
+
+    if (st) {
+        stats.source_cells = nsc;
+        stats.target_cells = ntc;
+        stats.source_levels = (int32_t)st_s.level_off.size() - 1;
+        stats.target_levels = (int32_t)st_t.level_off.size() - 1;
+        stats.m2l_pairs = n_m2l;
+        stats.p2p_pairs = n_p2p;
+        stats.traversal_passes = passes;
+        stats.restarts = restarts;
+        *st = stats;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace dtn
+
+extern "C" dtn_status dtn_eval_potential_fmm(dtn_geometry *g, int64_t np, const double *xyz, const double *nrm,
+                                             const double *area, const double *q, const double *gv,
+                                             const int64_t *index, const int64_t *n_index, int64_t nt,
+                                             const double *t, double *out, const dtn_fmm_opts *o,
+                                             dtn_fmm_stats *st, void *stream) {
+    using namespace dtn;
+    if (!g || !o || np < 0 || nt < 0) return DTN_E_INVALID_ARG;
+    if (o->order < 1 || o->order > kFmmMaxOrder || !(o->theta > 0.0 && o->theta < 1.0) || o->leaf_sources < 1 ||
+        o->leaf_sources > 4096 || o->leaf_targets < 1 || o->leaf_targets > 4096 || o->max_level < 1 ||
+        o->max_level > kMortonBits)
+        return DTN_E_INVALID_ARG;
+    if (np >= (int64_t)1 << 31 || nt >= (int64_t)1 << 31) return DTN_E_INVALID_ARG;
+    if (st) *st = dtn_fmm_stats{};
+    if (nt == 0) return DTN_OK;
+    if (!t || !out || (np > 0 && (!xyz || !nrm || !area || !q))) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    int64_t n = np;
+    if (index && n_index) {
+        if ((e = cudaMemcpyAsync(&n, n_index, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return to_status(e);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return to_status(e);
+        if (n < 0 || n > np) return DTN_E_INVALID_ARG;
+    }
+    if (!gv && n > 0) {
+        if (!g->has_data) return DTN_E_INVALID_ARG;
+        if (!g->fmm_ws) g->fmm_ws = new FmmWorkspace();
+        FmmWorkspace &w = *static_cast<FmmWorkspace *>(g->fmm_ws);
+        if ((e = w.gtmp.reserve(np * sizeof(double))) != cudaSuccess) return to_status(e);
+        if ((e = launch_dirichlet(g, np, xyz, w.gtmp.as<double>(), s)) != cudaSuccess) return to_status(e);
+        gv = w.gtmp.as<double>();
+    }
+    bool bad = false;
+    e = fmm_evaluate(g, n, np, xyz, nrm, area, q, gv, index, nt, t, out, *o, st, &bad, s);
+    if (e == cudaSuccess && bad) return DTN_E_INVALID_ARG;
+    return to_status(e);
+}

@@ -61,13 +61,9 @@ cudaError_t scratch_on_current_device(void **out) {
     return cudaSuccess;
 }
 
-dtn_status to_status(cudaError_t e) {
-    if (e == cudaSuccess) return DTN_OK;
-    dtn::set_cuda_error(e);
-    return e == cudaErrorMemoryAllocation ? DTN_E_OUT_OF_MEMORY : DTN_E_CUDA;
-}
-
 }  // namespace
+
+using dtn::to_status;
 
 extern "C" dtn_status dtn_wos_points_noalloc(const dtn_geometry *gc, int64_t n, const double *y,
                                              const uint32_t *point_ids, const uint32_t *patch_ids,

@@ -347,3 +347,45 @@ def points_in_box(n: int, lo, hi, margin: float, seed: int = 5) -> np.ndarray:
     lo = np.asarray(lo) + margin
     hi = np.asarray(hi) - margin
     return rng.uniform(lo, hi, size=(n, 3))
+
+
+# ---------------------------------------------------------------- panel sets for the potential
+
+def sphere_panels(n: int, radius: float = 1.0) -> tuple:
+    """n equal-area panels of a sphere: collocation points on the Fibonacci
+    lattice, outward normals, area 4 pi radius^2 / n each.  Returns (xyz,
+    normals, areas)."""
+    y = fibonacci_sphere(n, radius)
+    return y, y / radius, np.full(n, 4.0 * math.pi * radius * radius / n)
+
+
+def box_surface_panels(boxes: np.ndarray, h: float) -> tuple:
+    """Square panels of side about h on the six faces of every box (rows lo, hi)
+    with outward normals and areas.  Returns (xyz, normals, areas)."""
+    xs, ns, ar = [], [], []
+    for lo, hi in zip(boxes[:, :3], boxes[:, 3:]):
+        for axis in range(3):
+            u, v = [a for a in range(3) if a != axis]
+            nu = max(1, int(round((hi[u] - lo[u]) / h)))
+            nv = max(1, int(round((hi[v] - lo[v]) / h)))
+            du, dv = (hi[u] - lo[u]) / nu, (hi[v] - lo[v]) / nv
+            cu = lo[u] + du * (np.arange(nu) + 0.5)
+            cv = lo[v] + dv * (np.arange(nv) + 0.5)
+            gu, gv = np.meshgrid(cu, cv, indexing="ij")
+            for side, val in ((-1.0, lo[axis]), (1.0, hi[axis])):
+                p = np.empty((nu * nv, 3))
+                p[:, axis] = val
+                p[:, u] = gu.ravel()
+                p[:, v] = gv.ravel()
+                nrm = np.zeros((nu * nv, 3))
+                nrm[:, axis] = side
+                xs.append(p)
+                ns.append(nrm)
+                ar.append(np.full(nu * nv, du * dv))
+    return np.concatenate(xs), np.concatenate(ns), np.concatenate(ar)
+
+
+def panel_values(n: int, seed: int = 11) -> tuple:
+    """Seeded N(0, 1) Neumann and Dirichlet values for n panels (PCG64(seed))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(n), rng.standard_normal(n)
