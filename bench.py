@@ -323,6 +323,47 @@ def run_single_point(dtn, n_points=256, ng=20, walks=1000):
     return out
 
 
+def run_potential_fmm(dtn, n_panels=1_000_000, n_targets=1_000_000, order=10, theta=0.5, direct=True):
+    """Potential by the fast multipole method (Sec. 6) against the direct sum:
+    n_panels equal-area panels of the unit sphere (Fibonacci lattice) with
+    seeded N(0, 1) Neumann and Dirichlet values, n_targets uniform targets in
+    the ball, all resident on the device.  Wall time of one call (the FMM
+    synchronises: its trees and traversal are built level by level), best of 3
+    after 2 warm-up calls; the direct FP32-pair sum is timed once with CUDA events."""
+    import torch
+    y, nrm, ar = W.sphere_panels(n_panels)
+    q, g = W.panel_values(n_panels)
+    t = W.targets_in_ball(n_targets, 1.0, 0.0, seed=4)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (y, nrm, ar, q, g, t)]
+    geom = dtn.Geometry(dtn.GEOM_BALL_INTERIOR, radius=1.0).set_dirichlet(dtn.DATA_CONSTANT, constant=0.0)
+    o = dtn.fmm_opts(order=order, theta=theta)
+    times = []
+    for k in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, st = dtn.eval_potential_fmm(geom, *dev, opts=o, want_stats=True)
+        torch.cuda.synchronize()
+        if k >= 2:
+            times.append(time.perf_counter() - t0)
+    fmm_s = min(times)
+    out = {"panels": n_panels, "targets": n_targets, "order": order, "theta": theta,
+           "leaf_sources": o.leaf_sources, "leaf_targets": o.leaf_targets, "fmm_ms": fmm_s * 1e3,
+           "pair_terms_per_s_equivalent": n_panels * n_targets / fmm_s, "stats": st,
+           "data": "synthetic: Fibonacci-sphere panels, N(0,1) values, uniform targets in the ball"}
+    if direct:
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ud = dtn.eval_potential(geom, *dev, prec=dtn.PREC_MIXED)
+        e1.record(stream)
+        e1.synchronize()
+        direct_s = e0.elapsed_time(e1) / 1e3
+        out.update({"direct_ms": direct_s * 1e3, "speedup_vs_direct": direct_s / fmm_s,
+                    "rel_l2_vs_direct": float((u - ud).norm() / ud.norm())})
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1210_1491_gb300 as dtn
@@ -482,6 +523,7 @@ def run_ours(args):
     if not args.no_serve:
         line["serving"] = run_serving(dtn)
         line["single_point"] = run_single_point(dtn)
+        line["potential_fmm"] = run_potential_fmm(dtn)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(wl)
     if rank == 0:
@@ -502,9 +544,16 @@ def main():
     ap.add_argument("--walk-params", default="", help="chunk,blocks_per_sm,refill (skips the autotuner)")
     ap.add_argument("--patches", type=int, default=2000, help="profiler captures only")
     ap.add_argument("--walks", type=int, default=4096, help="profiler captures only")
+    ap.add_argument("--fmm-only", action="store_true", help="only the fast multipole leg (profiler captures)")
+    ap.add_argument("--fmm-panels", type=int, default=1_000_000, help="panels = targets of --fmm-only")
+    ap.add_argument("--no-direct", action="store_true", help="--fmm-only without the direct sum")
     args = ap.parse_args()
     global ARGS
     ARGS = args
+    if args.fmm_only:
+        import paper_1210_1491_gb300 as dtn
+        print(json.dumps(run_potential_fmm(dtn, args.fmm_panels, args.fmm_panels, direct=not args.no_direct)))
+        return
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

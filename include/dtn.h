@@ -229,7 +229,7 @@ typedef struct {
     int32_t leaf_sources;   /* a source cell holding more panels is split, 1 .. 4096 */
     int32_t leaf_targets;   /* a target cell holding more targets is split, 1 .. 4096 */
     int32_t max_level;      /* deepest octree level, 1 .. 21 */
-    double theta;           /* acceptance (r_T + r_S) < theta |z - c|, r the cell half-diagonal; (0, 1) */
+    double theta;           /* acceptance (r_T + r_S) < theta |z - c|, r the cells' point radii; (0, 1) */
 } dtn_fmm_opts;
 
 /* What one evaluation did (counts; written when the pointer is not NULL). */
@@ -248,8 +248,9 @@ typedef struct {
  * solves.  Panel p is a charge area_p q_p / 4pi and a dipole
  * -area_p g_p n_p / 4pi at its collocation point.  Sources and targets get
  * adaptive octrees over one bounding cube; a dual-tree traversal sends each
- * (target cell, source cell) pair with (r_T + r_S) < theta |z - c| (r the cell
- * half-diagonals, z and c their centres) through multipole-to-local
+ * (target cell, source cell) pair with (r_T + r_S) < theta |z - c| (z and c the
+ * cell centres, r the radii of balls about them that hold the cells' points)
+ * through multipole-to-local
  * translation with expansions of order P in solid harmonics, and leaf pairs
  * that fail the test through the direct pair sum.  The far-field error of a
  * pair falls like theta^(P+1).  Expansions and pair terms are FP32, centre

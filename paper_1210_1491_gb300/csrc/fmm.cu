@@ -32,8 +32,9 @@
 // holds more than the leaf size (cells in level order, the children of a cell
 // contiguous).  A dual-tree traversal, level-synchronous on the GPU, sorts every
 // (target cell, source cell) pair into an M2L pair when (r_T + r_S) < theta |z - c|
-// (r = half-diagonal), a P2P pair when both are leaves, and otherwise splits the
-// larger cell.  Each target point then receives every source exactly once,
+// (r the radius about the cell centre of a ball holding the cell's points: exact
+// for leaves, bounded through the children above), a P2P pair when both are
+// leaves, and otherwise splits the larger cell.  Each target point then receives every source exactly once,
 // through one M2L (plus the L2L chain below it) or one P2P pair.
 //
 // Precision: expansions and pair terms in FP32, centre differences in FP64,
@@ -62,6 +63,7 @@ constexpr int kBboxBlocks = 256;
 
 struct FCell {
     double c[3];            // centre
+    double r;               // radius about c of a ball holding the cell's points
     uint64_t key;           // Morton prefix, 3 bits per level
     int32_t start, count;   // points [start, start + count) in Morton order
     int32_t child, nchild;  // first child (next level, contiguous); -1 for a leaf
@@ -257,6 +259,7 @@ __global__ void fmm_emit_kernel(FCell *__restrict__ cells, int64_t c0, int64_t n
     ch.nchild = 0;
     ch.level = cells[p].level + 1;
     ch.pad = 0;
+    ch.r = 0.0;
     cells[c_next + pos[i]] = ch;
 }
 
@@ -277,6 +280,32 @@ __global__ void fmm_source_kernel(int64_t n, const int32_t *__restrict__ val, co
                           (float)c);
 }
 
+// Cell radii, one level at a time from the deepest: a leaf takes the largest
+// distance of its points from its centre (FP64, points through the optional
+// id list), a split cell max over children of |c_child - c| + r_child.
+__global__ void fmm_radius_kernel(FCell *__restrict__ cells, int64_t c0, int64_t ncell,
+                                  const double *__restrict__ x, const int32_t *__restrict__ ids) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ncell) return;
+    FCell &C = cells[c0 + i];
+    double r2 = 0.0, r = 0.0;
+    if (C.child < 0) {
+        for (int k = C.start; k < C.start + C.count; ++k) {
+            const int64_t p = ids ? ids[k] : k;
+            const double dx = x[3 * p] - C.c[0], dy = x[3 * p + 1] - C.c[1], dz = x[3 * p + 2] - C.c[2];
+            r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+        }
+        r = sqrt(r2);
+    } else {
+        for (int k = 0; k < C.nchild; ++k) {
+            const FCell &D = cells[C.child + k];
+            const double dx = D.c[0] - C.c[0], dy = D.c[1] - C.c[1], dz = D.c[2] - C.c[2];
+            r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz) + D.r);
+        }
+    }
+    C.r = r;
+}
+
 // ------------------------------------------------------------------ upward pass
 
 struct FmmShared {
@@ -286,9 +315,11 @@ struct FmmShared {
 
 // P2M: one warp per source leaf; the warp builds each source's regular table
 // (lane m computes column m) and every lane accumulates the coefficients it owns.
+// Also writes each source's FP32 offset from its leaf centre with its charge
+// (srel), the form the leaf-pair sums read.
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_p2m_kernel(
     const FCell *__restrict__ cells, int64_t ncell, const double *__restrict__ spos,
-    const float4 *__restrict__ sdat, double half_w0, int P, float2 *__restrict__ M) {
+    const float4 *__restrict__ sdat, double half_w0, int P, float2 *__restrict__ M, float4 *__restrict__ srel) {
     __shared__ FmmShared sh[kCellWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t ci = blockIdx.x * (int64_t)kCellWarps + wid;
@@ -308,6 +339,9 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_p2m_kernel(
         else on[r] = om[r] = 0;
     }
     float2 *tab = sh[wid].tab;
+    for (int s = cell.start + lane; s < cell.start + cell.count; s += 32)
+        srel[s] = make_float4((float)(spos[3 * s] - cell.c[0]), (float)(spos[3 * s + 1] - cell.c[1]),
+                              (float)(spos[3 * s + 2] - cell.c[2]), sdat[s].w);
     for (int s = cell.start; s < cell.start + cell.count; ++s) {
         const float vx = (float)((spos[3 * s] - cell.c[0]) / h), vy = (float)((spos[3 * s + 1] - cell.c[1]) / h),
                     vz = (float)((spos[3 * s + 2] - cell.c[2]) / h);
@@ -399,37 +433,78 @@ struct DttCounters {
     unsigned long long next, m2l, p2p, p2p_terms, overflow;
 };
 
+// One thread per frontier pair; appends are aggregated per warp (one atomic per
+// list per warp, offsets by warp prefix sums).
 __global__ void fmm_dtt_kernel(const int2 *__restrict__ front, int64_t nf, const FCell *__restrict__ tc,
-                               const FCell *__restrict__ sc, double r0, double theta2, int2 *__restrict__ next,
+                               const FCell *__restrict__ sc, double theta2, int2 *__restrict__ next,
                                int64_t cap_next, uint64_t *__restrict__ m2l, int64_t cap_m2l,
                                uint64_t *__restrict__ p2p, int64_t cap_p2p, DttCounters *__restrict__ cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    const int2 pr = front[i];
-    const FCell &T = tc[pr.x];
-    const FCell &S = sc[pr.y];
-    const double rt = ldexp(r0, -T.level), rs = ldexp(r0, -S.level);
-    const double dx = T.c[0] - S.c[0], dy = T.c[1] - S.c[1], dz = T.c[2] - S.c[2];
-    const double d2 = dx * dx + dy * dy + dz * dz;
-    const bool tleaf = T.child < 0, sleaf = S.child < 0;
-    if ((rt + rs) * (rt + rs) < theta2 * d2) {
-        const unsigned long long k = atomicAdd(&cnt->m2l, 1ull);
-        if ((int64_t)k < cap_m2l) m2l[k] = (uint64_t)(uint32_t)pr.x << 32 | (uint32_t)pr.y;
-        else cnt->overflow = 1;
-    } else if (tleaf && sleaf) {
-        const unsigned long long k = atomicAdd(&cnt->p2p, 1ull);
-        atomicAdd(&cnt->p2p_terms, (unsigned long long)T.count * (unsigned long long)S.count);
-        if ((int64_t)k < cap_p2p) p2p[k] = (uint64_t)(uint32_t)pr.x << 32 | (uint32_t)pr.y;
-        else cnt->overflow = 1;
-    } else {
-        const bool split_t = sleaf || (!tleaf && rt >= rs);
-        const int first = split_t ? T.child : S.child, nch = split_t ? T.nchild : S.nchild;
-        const unsigned long long k = atomicAdd(&cnt->next, (unsigned long long)nch);
-        if ((int64_t)(k + nch) <= cap_next) {
-            for (int c = 0; c < nch; ++c)
-                next[k + c] = split_t ? make_int2(first + c, pr.y) : make_int2(pr.x, first + c);
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < nf;
+    int2 pr = make_int2(0, 0);
+    int kind = -1;   // 0 M2L, 1 P2P, 2 split
+    int first = 0, nch = 0;
+    bool split_t = false;
+    unsigned long long terms = 0;
+    if (valid) {
+        pr = front[i];
+        const FCell &T = tc[pr.x];
+        const FCell &S = sc[pr.y];
+        const double rt = T.r, rs = S.r;
+        const double dx = T.c[0] - S.c[0], dy = T.c[1] - S.c[1], dz = T.c[2] - S.c[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        const bool tleaf = T.child < 0, sleaf = S.child < 0;
+        if ((rt + rs) * (rt + rs) < theta2 * d2) {
+            kind = 0;
+        } else if (tleaf && sleaf) {
+            kind = 1;
+            terms = (unsigned long long)T.count * (unsigned long long)S.count;
         } else {
-            cnt->overflow = 1;
+            kind = 2;
+            split_t = sleaf || (!tleaf && rt >= rs);
+            first = split_t ? T.child : S.child;
+            nch = split_t ? T.nchild : S.nchild;
+        }
+    }
+    const uint64_t key = (uint64_t)(uint32_t)pr.x << 32 | (uint32_t)pr.y;
+    // M2L and P2P: one slot each
+    for (int k = 0; k < 2; ++k) {
+        const unsigned mask = __ballot_sync(0xffffffffu, kind == k);
+        if (!mask) continue;
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(k == 0 ? &cnt->m2l : &cnt->p2p, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (kind == k) {
+            const int64_t slot = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+            if (slot < (k == 0 ? cap_m2l : cap_p2p)) (k == 0 ? m2l : p2p)[slot] = key;
+            else cnt->overflow = 1;
+        }
+    }
+    // P2P pair terms (statistics)
+    unsigned long long tsum = terms;
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    if (lane == 0 && tsum) atomicAdd(&cnt->p2p_terms, tsum);
+    // splits: nch slots each, warp prefix sum
+    int incl = nch;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&cnt->next, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (nch) {
+            const int64_t at = (int64_t)base + incl - nch;
+            if (at + nch <= cap_next) {
+                for (int c = 0; c < nch; ++c)
+                    next[at + c] = split_t ? make_int2(first + c, pr.y) : make_int2(pr.x, first + c);
+            } else {
+                cnt->overflow = 1;
+            }
         }
     }
 }
@@ -450,81 +525,166 @@ __global__ void fmm_csr_kernel(int64_t ncell, const uint64_t *__restrict__ keys,
 
 // ------------------------------------------------------------------ downward pass
 
-// M2L: one warp per target cell, over its sorted source list.  Lanes build the
-// singular table at (z - c)/rho to degree 2P (lane m: columns m and m + 32),
-// stage the source's scaled expansion, and accumulate the coefficients they own:
-//   L_n^m = (-1)^{n+m} (h_T/rho)^n / rho sum_j sum_k S_{j+n}^{k-m} (h_S/rho)^j M_j^k,
-// rho = max(h_T, h_S); the k < 0 half enters as (-1)^m conj(sum_{k>0} M_j^k S_{j+n}^{m+k}).
-// Writes L for every cell (zero for an empty list).
+// M2L: one warp per target cell, over its sorted source list.  For each source
+// the warp writes the singular harmonics at (z - c)/rho to degree 2P and the
+// source's scaled multipole coefficients as full tables (orders -N..N at index
+// N^2 + N + l, the negative orders from the symmetry), so that every output is
+// the same branch-free sum
+//   L_n^m += (-1)^{n+m} (h_T/rho)^n / rho sum_j sum_{k=-j}^{j} S_{j+n}^{k-m} (h_S/rho)^j M_j^k,
+// rho = max(h_T, h_S), contiguous in k in both tables.  A lane owns three
+// outputs (n, m0), (n, m0+1), (n, m0+2): walking k upwards, the S value loaded
+// for (n, m0) at k serves (n, m0+1) at k+1 and (n, m0+2) at k+2, so each step
+// loads one S value and one (broadcast) M value for three complex products.
+// Outputs past m = n are computed on in-bounds padding and dropped.  Writes L
+// for every cell (zero for an empty list).
+constexpr int kM2lBlock = 3;
+constexpr int kM2lTasksMax = 2;   // rounds of 32 lanes: sum_n ceil((n+1)/3) <= 64 for P <= 16
+constexpr int kSPad = 2;          // entries before the S table (k - m0 - 2 >= -2 - N)
+
+struct M2lShared {
+    float2 s[kSPad + (2 * kFmmMaxOrder + 1) * (2 * kFmmMaxOrder + 1)];
+    float2 m[(kFmmMaxOrder + 1) * (kFmmMaxOrder + 1)];
+};
+
+// task t -> (n, m0): n ascending, m0 = 0, 3, 6, ... <= n; false past the last
+__device__ inline bool m2l_task(int t, int P, int &n, int &m0) {
+    for (n = 0; n <= P; ++n) {
+        const int c = (n + kM2lBlock) / kM2lBlock;
+        if (t < c) {
+            m0 = kM2lBlock * t;
+            return true;
+        }
+        t -= c;
+    }
+    return false;
+}
+
+// Persistent warps: each takes the next target cell from *queue (L is zeroed
+// before the launch, so cells without M2L pairs are skipped).
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
-    const uint64_t *__restrict__ list, double half_w0, int P, const float2 *__restrict__ M, float2 *__restrict__ L) {
-    __shared__ FmmShared sh[kCellWarps];
+    const uint64_t *__restrict__ list, double half_w0, int P, const float2 *__restrict__ M, float2 *__restrict__ L,
+    unsigned long long *__restrict__ queue) {
+    __shared__ M2lShared sh[kCellWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t ti = blockIdx.x * (int64_t)kCellWarps + wid;
-    if (ti >= ntc) return;
-    const FCell T = tc[ti];
     const int nc = tri(P + 1, 0);
-    float2 acc[kOwnMax];
-    int on[kOwnMax], om[kOwnMax];
+    int tn[kM2lTasksMax], tm[kM2lTasksMax];
+    bool tv[kM2lTasksMax];
 #pragma unroll
-    for (int r = 0; r < kOwnMax; ++r) {
-        acc[r] = make_float2(0.0f, 0.0f);
-        const int idx = lane + 32 * r;
-        if (idx < nc) tri_nm(idx, on[r], om[r]);
-        else on[r] = om[r] = 0;
+    for (int r = 0; r < kM2lTasksMax; ++r) {
+        tv[r] = m2l_task(lane + 32 * r, P, tn[r], tm[r]);
+        if (!tv[r]) tn[r] = tm[r] = 0;
     }
-    float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
+    const bool round2 = __any_sync(0xffffffffu, tv[1]);
+    float2 *S = sh[wid].s + kSPad, *Mf = sh[wid].m;
+    if (lane < kSPad) sh[wid].s[lane] = make_float2(0.0f, 0.0f);
+    for (;;) {
+    unsigned long long qi = 0;
+    if (lane == 0) qi = atomicAdd(queue, 1ull);
+    const int64_t ti = (int64_t)__shfl_sync(0xffffffffu, qi, 0);
+    if (ti >= ntc) break;
     const int64_t e0 = off[ti], e1 = off[ti + 1];
+    if (e0 == e1) continue;
+    const FCell T = tc[ti];
+    float2 acc[kM2lTasksMax][kM2lBlock];
+#pragma unroll
+    for (int r = 0; r < kM2lTasksMax; ++r)
+#pragma unroll
+        for (int d = 0; d < kM2lBlock; ++d) acc[r][d] = make_float2(0.0f, 0.0f);
     for (int64_t e = e0; e < e1; ++e) {
         const int64_t si = (int64_t)(uint32_t)(list[e] & 0xffffffffu);
-        const FCell &S = sc[si];
-        const int lt = T.level, ls = S.level;
-        const int lr = min(lt, ls);                    // rho = h at the coarser level
-        const double rho = ldexp(half_w0, -lr);
-        const float vx = (float)((T.c[0] - S.c[0]) / rho), vy = (float)((T.c[1] - S.c[1]) / rho),
-                    vz = (float)((T.c[2] - S.c[2]) / rho);
-        const int bt = lt - lr, bs = ls - lr;          // h_T / rho = 2^-bt, h_S / rho = 2^-bs
+        const FCell &Sc = sc[si];
+        const int lt = T.level, ls = Sc.level;
+        const int lr = min(lt, ls);
+        const double irho = ldexp(1.0 / half_w0, lr);
+        const float vx = (float)((T.c[0] - Sc.c[0]) * irho), vy = (float)((T.c[1] - Sc.c[1]) * irho),
+                    vz = (float)((T.c[2] - Sc.c[2]) * irho);
+        const int bt = lt - lr, bs = ls - lr;
         __syncwarp();
-        for (int m = lane; m <= 2 * P; m += 32) singular_column(tab, m, 2 * P, vx, vy, vz);
+        for (int m = lane; m <= 2 * P; m += 32) {
+            // column m of S, both signs of the order
+            const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+            const float ir2 = 1.0f / r2;
+            float2 smm = make_float2(rsqrtf(r2), 0.0f);
+            for (int k = 1; k <= m; ++k) smm = cscale(cmul(smm, make_float2(vx, vy)), (float)(2 * k - 1) * ir2);
+            const float sg = (m & 1) ? -1.0f : 1.0f;
+            float2 a = make_float2(0.0f, 0.0f), b = smm;
+            for (int n = m; n <= 2 * P; ++n) {
+                if (n > m) {
+                    const float f = (float)((n + m - 1) * (n - m - 1));
+                    const float2 c = make_float2(((2 * n - 1) * vz * b.x - f * a.x) * ir2,
+                                                 ((2 * n - 1) * vz * b.y - f * a.y) * ir2);
+                    a = b;
+                    b = c;
+                }
+                S[n * n + n + m] = b;
+                if (m) S[n * n + n - m] = make_float2(sg * b.x, -sg * b.y);
+            }
+        }
         for (int q = lane; q < nc; q += 32) {
             int n, m;
             tri_nm(q, n, m);
             const float2 v = M[si * nc + q];
-            ex[q] = make_float2(ldexpf(v.x, -n * bs), ldexpf(v.y, -n * bs));
+            const float2 w = make_float2(ldexpf(v.x, -n * bs), ldexpf(v.y, -n * bs));
+            const float sg = (m & 1) ? -1.0f : 1.0f;
+            Mf[n * n + n + m] = w;
+            if (m) Mf[n * n + n - m] = make_float2(sg * w.x, -sg * w.y);
         }
         __syncwarp();
-        const float irho = (float)(1.0 / rho);
+        const float fr = (float)irho;
 #pragma unroll
-        for (int r = 0; r < kOwnMax; ++r) {
-            if (lane + 32 * r >= nc) break;
-            const int n = on[r], m = om[r];
-            float2 s = make_float2(0.0f, 0.0f), t = make_float2(0.0f, 0.0f);
+        for (int r = 0; r < kM2lTasksMax; ++r) {
+            if (r == 1 && !round2) break;
+            const int n = tn[r], m0 = tm[r];
+            float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0;
             for (int j = 0; j <= P; ++j) {
-                const float2 *Sj = tab + tri(j + n, 0);
-                const float2 *Mj = ex + tri(j, 0);
-                // k in [0, min(j, m-1)]: S_{j+n}^{k-m} = (-1)^{m-k} conj(S_{j+n}^{m-k})
-                const int kk = min(j, m - 1);
-                for (int k = 0; k <= kk; ++k) {
-                    const float2 sv = Sj[m - k];
-                    const float2 c = ((m - k) & 1) ? make_float2(-sv.x, sv.y) : make_float2(sv.x, -sv.y);
-                    cmac(s, c, Mj[k]);
+                const float2 *mr = Mf + j * j + j;
+                const int N = j + n;
+                const float2 *sr = S + N * N + N - m0;   // S_N^{k - m0} at sr[k]
+                float2 w1 = sr[-j - 1], w2 = sr[-j - 2];
+                int k = -j;
+                for (; k + 2 <= j; k += 3) {   // three steps with the window rotated in registers
+                    const float2 m0v = mr[k], m1v = mr[k + 1], m2v = mr[k + 2];
+                    const float2 v0 = sr[k], v1 = sr[k + 1], v2 = sr[k + 2];
+                    cmac(p0, v0, m0v);
+                    cmac(p1, w1, m0v);
+                    cmac(p2, w2, m0v);
+                    cmac(p0, v1, m1v);
+                    cmac(p1, v0, m1v);
+                    cmac(p2, w1, m1v);
+                    cmac(p0, v2, m2v);
+                    cmac(p1, v1, m2v);
+                    cmac(p2, v0, m2v);
+                    w2 = v1;
+                    w1 = v2;
                 }
-                // k in [m, j]: S_{j+n}^{k-m}
-                for (int k = m; k <= j; ++k) cmac(s, Sj[k - m], Mj[k]);
-                // k' in [1, j]: M_j^{k'} S_{j+n}^{m+k'}
-                for (int k = 1; k <= j; ++k) cmac(t, Mj[k], Sj[m + k]);
+                for (; k <= j; ++k) {
+                    const float2 mv = mr[k];
+                    const float2 v = sr[k];
+                    cmac(p0, v, mv);
+                    cmac(p1, w1, mv);
+                    cmac(p2, w2, mv);
+                    w2 = w1;
+                    w1 = v;
+                }
             }
-            // s + (-1)^m conj(t), times (-1)^{n+m} (h_T/rho)^n / rho
-            const float sg = (m & 1) ? -1.0f : 1.0f;
-            float2 v = make_float2(s.x + sg * t.x, s.y - sg * t.y);
-            const float f = ldexpf(((n + m) & 1) ? -irho : irho, -n * bt);
-            acc[r] = make_float2(fmaf(f, v.x, acc[r].x), fmaf(f, v.y, acc[r].y));
+            const float2 pr[kM2lBlock] = {p0, p1, p2};
+#pragma unroll
+            for (int d = 0; d < kM2lBlock; ++d) {
+                const int m = m0 + d;
+                const float f = ldexpf(((n + m) & 1) ? -fr : fr, -n * bt);
+                acc[r][d] = make_float2(fmaf(f, pr[d].x, acc[r][d].x), fmaf(f, pr[d].y, acc[r][d].y));
+            }
         }
     }
 #pragma unroll
-    for (int r = 0; r < kOwnMax; ++r)
-        if (lane + 32 * r < nc) L[ti * nc + lane + 32 * r] = acc[r];
+    for (int r = 0; r < kM2lTasksMax; ++r) {
+        if (!tv[r]) continue;
+#pragma unroll
+        for (int d = 0; d < kM2lBlock; ++d)
+            if (tm[r] + d <= tn[r]) L[ti * nc + tri(tn[r], tm[r] + d)] = acc[r][d];
+    }
+    }
 }
 
 // L2L for the cells of one level (parent complete): L'_k^l += 2^-k sum_{n>=k,m} L_n^m R_{n-k}^{m-l}(d),
@@ -569,83 +729,147 @@ __global__ void fmm_parent_kernel(const FCell *__restrict__ tc, int64_t ncell, i
     for (int k = 0; k < c.nchild; ++k) parent[c.child + k] = (int32_t)i;
 }
 
-// Target leaves: one warp per leaf, a lane per target.  L2P by the regular
-// recurrence at (t - z)/h with the leaf's local expansion in shared memory, then
-// P2P over the leaf's source leaves (staged 32 at a time as FP32 offsets from
-// the target leaf's centre); FP64 sum per target.
+// Target leaves: persistent warps take cells from *queue and skip non-leaves.
+// Per leaf, first L2P, a lane per target, by the
+// regular recurrence at (t - z)/h with the leaf's local expansion in shared
+// memory.  Then the direct sum over the leaf's source leaves: the warp takes the
+// source leaves 32 at a time (their counts, a warp prefix sum and the FP32
+// offsets c_S - z from FP64 centres), stages their sources in chunks of
+// kP2pChunk as FP32 offsets from the target leaf's centre, and a target's terms
+// are split over lpt lanes (the largest power of two with lpt x targets <= 32),
+// combined by shuffles at the end.  FP32 chunk sums, FP64 per target.
+constexpr int kP2pChunk = 128;
+
+struct LeafShared {
+    float2 l[kNcMax];
+    float4 a[kP2pChunk], b[kP2pChunk];
+    int pre[33], start[32];
+    float dc[32][3];
+    float far[32];
+};
+
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
     const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
     const uint64_t *__restrict__ list, const int32_t *__restrict__ tval, const double *__restrict__ targets,
-    const double *__restrict__ spos, const float4 *__restrict__ sdat, double half_w0, int P,
-    const float2 *__restrict__ L, double *__restrict__ out) {
-    __shared__ float2 sl[kCellWarps][kNcMax];
-    __shared__ float4 sa[kCellWarps][32], sb[kCellWarps][32];
+    const float4 *__restrict__ srel, const float4 *__restrict__ sdat, double half_w0, int P,
+    const float2 *__restrict__ L, double *__restrict__ out, unsigned long long *__restrict__ queue) {
+    __shared__ LeafShared sh[kCellWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t ti = blockIdx.x * (int64_t)kCellWarps + wid;
-    if (ti >= ntc) return;
-    const FCell T = tc[ti];
-    if (T.child >= 0) return;
+    LeafShared &S = sh[wid];
     const int nc = tri(P + 1, 0);
-    for (int q = lane; q < nc; q += 32) sl[wid][q] = L[ti * nc + q];
+    for (;;) {
+    unsigned long long qi = 0;
+    if (lane == 0) qi = atomicAdd(queue, 1ull);
+    const int64_t ti = (int64_t)__shfl_sync(0xffffffffu, qi, 0);
+    if (ti >= ntc) break;
+    const FCell T = tc[ti];
+    if (T.child >= 0) continue;
+    __syncwarp();
+    for (int q = lane; q < nc; q += 32) S.l[q] = L[ti * nc + q];
+    __syncwarp();
     const double h = ldexp(half_w0, -T.level);
     const int64_t e0 = off[ti], e1 = off[ti + 1];
     for (int tb = T.start; tb < T.start + T.count; tb += 32) {
-        const int it = tb + lane;
-        const bool valid = it < T.start + T.count;
-        const int32_t id = valid ? tval[it] : 0;
-        const double ex = valid ? targets[3 * id] - T.c[0] : 0.0, ey = valid ? targets[3 * id + 1] - T.c[1] : 0.0,
-                     ez = valid ? targets[3 * id + 2] - T.c[2] : 0.0;
+        const int nt = min(32, T.start + T.count - tb);
         __syncwarp();
-        // L2P: u = sum_n [R_n^0 L_n^0 + 2 Re sum_{m>0} R_n^m L_n^m]
-        const float x = (float)(ex / h), y = (float)(ey / h), z = (float)(ez / h);
-        const float r2 = fmaf(x, x, fmaf(y, y, z * z));
-        float far = 0.0f;
-        float2 rmm = make_float2(1.0f, 0.0f);
-        for (int m = 0; m <= P; ++m) {
-            if (m > 0) rmm = cscale(cmul(rmm, make_float2(x, y)), 0.5f / (float)m);
-            const float wgt = m ? 2.0f : 1.0f;
-            float2 a = make_float2(0.0f, 0.0f), b = rmm;
-            float part = b.x * sl[wid][tri(m, m)].x - b.y * sl[wid][tri(m, m)].y;
-            for (int n = m + 1; n <= P; ++n) {
-                const float inv = 1.0f / (float)((n + m) * (n - m));
-                const float2 c = make_float2(((2 * n - 1) * z * b.x - r2 * a.x) * inv,
-                                             ((2 * n - 1) * z * b.y - r2 * a.y) * inv);
-                const float2 lv = sl[wid][tri(n, m)];
-                part = fmaf(c.x, lv.x, fmaf(-c.y, lv.y, part));
-                a = b;
-                b = c;
+        // L2P, a lane per target
+        if (lane < nt) {
+            const int32_t id = tval[tb + lane];
+            const float x = (float)((targets[3 * id] - T.c[0]) / h), y = (float)((targets[3 * id + 1] - T.c[1]) / h),
+                        z = (float)((targets[3 * id + 2] - T.c[2]) / h);
+            const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+            float far = 0.0f;
+            float2 rmm = make_float2(1.0f, 0.0f);
+            for (int m = 0; m <= P; ++m) {
+                if (m > 0) rmm = cscale(cmul(rmm, make_float2(x, y)), 0.5f / (float)m);
+                float2 a = make_float2(0.0f, 0.0f), b = rmm;
+                float part = b.x * S.l[tri(m, m)].x - b.y * S.l[tri(m, m)].y;
+                for (int n = m + 1; n <= P; ++n) {
+                    const float inv = 1.0f / (float)((n + m) * (n - m));
+                    const float2 c = make_float2(((2 * n - 1) * z * b.x - r2 * a.x) * inv,
+                                                 ((2 * n - 1) * z * b.y - r2 * a.y) * inv);
+                    const float2 lv = S.l[tri(n, m)];
+                    part = fmaf(c.x, lv.x, fmaf(-c.y, lv.y, part));
+                    a = b;
+                    b = c;
+                }
+                far = fmaf(m ? 2.0f : 1.0f, part, far);
             }
-            far = fmaf(wgt, part, far);
+            S.far[lane] = far;
         }
-        double acc = (double)far;
-        // P2P
-        const float ox = (float)ex, oy = (float)ey, oz = (float)ez;
-        for (int64_t e = e0; e < e1; ++e) {
-            const FCell &S = sc[(uint32_t)(list[e] & 0xffffffffu)];
-            float part = 0.0f;
-            for (int sbase = S.start; sbase < S.start + S.count; sbase += 32) {
-                const int cnt = min(32, S.start + S.count - sbase);
+        // near field: lane = (target tt, slice) with lpt lanes per target
+        int lpt = 1;
+        while (lpt * 2 * nt <= 32) lpt *= 2;
+        const int tt = lane / lpt, slice = lane % lpt;
+        const bool tvalid = tt < nt;
+        const int32_t id = tval[tb + (tvalid ? tt : 0)];
+        const float ox = (float)(targets[3 * id] - T.c[0]), oy = (float)(targets[3 * id + 1] - T.c[1]),
+                    oz = (float)(targets[3 * id + 2] - T.c[2]);
+        double acc = 0.0;
+        for (int64_t g0 = e0; g0 < e1; g0 += 32) {
+            const int ng = (int)min((int64_t)32, e1 - g0);
+            int cntv = 0;
+            __syncwarp();
+            if (lane < ng) {
+                const FCell &C = sc[(uint32_t)(list[g0 + lane] & 0xffffffffu)];
+                cntv = C.count;
+                S.start[lane] = C.start;
+                S.dc[lane][0] = (float)(C.c[0] - T.c[0]);
+                S.dc[lane][1] = (float)(C.c[1] - T.c[1]);
+                S.dc[lane][2] = (float)(C.c[2] - T.c[2]);
+            }
+            int incl = cntv;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            S.pre[lane + 1] = incl;
+            if (lane == 0) S.pre[0] = 0;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int cb = 0; cb < total; cb += kP2pChunk) {
+                const int cn = min(kP2pChunk, total - cb);
                 __syncwarp();
-                if (lane < cnt) {
-                    const int s = sbase + lane;
-                    const float4 d = sdat[s];
-                    sa[wid][lane] = make_float4((float)(spos[3 * s] - T.c[0]), (float)(spos[3 * s + 1] - T.c[1]),
-                                                (float)(spos[3 * s + 2] - T.c[2]), d.w);
-                    sb[wid][lane] = make_float4(d.x, d.y, d.z, 0.0f);
+                for (int i = lane; i < cn; i += 32) {
+                    const int gidx = cb + i;
+                    int lo = 0, hi = ng;   // pair p with pre[p] <= gidx < pre[p+1]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.pre[mid] <= gidx) lo = mid;
+                        else hi = mid;
+                    }
+                    const int src = S.start[lo] + gidx - S.pre[lo];
+                    const float4 a = srel[src];
+                    S.a[i] = make_float4(a.x + S.dc[lo][0], a.y + S.dc[lo][1], a.z + S.dc[lo][2], a.w);
+                    S.b[i] = sdat[src];
                 }
                 __syncwarp();
-                for (int k = 0; k < cnt; ++k) {
-                    const float4 pa = sa[wid][k], pb = sb[wid][k];
+                float part0 = 0.0f, part1 = 0.0f;
+                int k = slice;
+                for (; k + lpt < cn; k += 2 * lpt) {
+                    const float4 pa = S.a[k], pb = S.b[k], qa = S.a[k + lpt], qb = S.b[k + lpt];
                     const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
-                    const float rr = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float ri = rsqrtf(rr);
+                    const float ex2 = ox - qa.x, ey2 = oy - qa.y, ez2 = oz - qa.z;
+                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    const float rj = rsqrtf(fmaf(ex2, ex2, fmaf(ey2, ey2, ez2 * ez2)));
                     const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
-                    part += ri * fmaf(dn, ri * ri, pa.w);
+                    const float en = fmaf(ex2, qb.x, fmaf(ey2, qb.y, ez2 * qb.z));
+                    part0 += ri * fmaf(dn, ri * ri, pa.w);
+                    part1 += rj * fmaf(en, rj * rj, qa.w);
                 }
+                if (k < cn) {
+                    const float4 pa = S.a[k], pb = S.b[k];
+                    const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
+                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+                    part0 += ri * fmaf(dn, ri * ri, pa.w);
+                }
+                acc += (double)part0 + (double)part1;
             }
-            acc += (double)part;
         }
-        if (valid) out[id] = acc;
+        for (int o = 1; o < lpt; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __syncwarp();
+        if (tvalid && slice == 0) out[id] = acc + (double)S.far[tt];
+    }
     }
 }
 
@@ -662,18 +886,19 @@ inline int64_t nblk(int64_t n, int t) { return (n + t - 1) / t; }
 
 struct FmmWorkspace {
     DevBuf part, kin, kout, vin, sval, tval, flag, pos, lo, hi, cub, scell, tcell, tparent;
-    DevBuf spos, sdat, M, L, front, next, m2l, m2l_s, p2p, p2p_s, m2l_off, p2p_off, cnt, gtmp;
+    DevBuf spos, sdat, srel, M, L, front, next, m2l, m2l_s, p2p, p2p_s, m2l_off, p2p_off, cnt, gtmp, queue;
     DttCounters *host_cnt = nullptr;   // pinned
     int64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;
+    int64_t grid_m2l = 0, grid_leaf = 0;   // persistent grids (resident CTAs x SMs)
 };
 
 void fmm_release(dtn_geometry *g) {
     FmmWorkspace *w = static_cast<FmmWorkspace *>(g->fmm_ws);
     if (!w) return;
     DevBuf *bufs[] = {&w->part, &w->kin, &w->kout, &w->vin, &w->sval, &w->tval, &w->flag, &w->pos, &w->lo,
-                      &w->hi, &w->cub, &w->scell, &w->tcell, &w->tparent, &w->spos, &w->sdat, &w->M, &w->L,
+                      &w->hi, &w->cub, &w->scell, &w->tcell, &w->tparent, &w->spos, &w->sdat, &w->srel, &w->M, &w->L,
                       &w->front, &w->next, &w->m2l, &w->m2l_s, &w->p2p, &w->p2p_s, &w->m2l_off, &w->p2p_off,
-                      &w->cnt, &w->gtmp};
+                      &w->cnt, &w->gtmp, &w->queue};
     for (DevBuf *b : bufs) b->release();
     if (w->host_cnt) cudaFreeHost(w->host_cnt);
     delete w;
@@ -817,7 +1042,7 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
     if (!std::isfinite(width)) return cudaErrorInvalidValue;
     width = width * (1.0 + 1e-9) + 1e-300;
     for (int a = 0; a < 3; ++a) lo[a] -= 0.5 * (width - (hi[a] - lo[a]));   // centre the cube on the box
-    const double half_w0 = 0.5 * width, r0 = std::sqrt(3.0) * half_w0;
+    const double half_w0 = 0.5 * width;
 
     // trees
     TreeInfo st_s, st_t;
@@ -828,14 +1053,24 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
                                                      w.spos.as<double>(), w.sdat.as<float4>());
     FMM_TRY(cudaGetLastError());
     FMM_TRY(build_tree(w, w.tcell, w.tval, nt, t, nullptr, lo, width, o.leaf_targets, o.max_level, st_t, s));
+    for (int l = (int)st_s.level_off.size() - 2; l >= 0; --l) {
+        const int64_t c0 = st_s.level_off[l], n = st_s.level_off[l + 1] - c0;
+        fmm_radius_kernel<<<nblk(n, 128), 128, 0, s>>>(w.scell.as<FCell>(), c0, n, w.spos.as<double>(), nullptr);
+    }
+    for (int l = (int)st_t.level_off.size() - 2; l >= 0; --l) {
+        const int64_t c0 = st_t.level_off[l], n = st_t.level_off[l + 1] - c0;
+        fmm_radius_kernel<<<nblk(n, 128), 128, 0, s>>>(w.tcell.as<FCell>(), c0, n, t, w.tval.as<int32_t>());
+    }
+    FMM_TRY(cudaGetLastError());
     const int64_t nsc = st_s.ncell, ntc = st_t.ncell;
     const int P = o.order, nc = tri(P + 1, 0);
 
     // upward pass
     FMM_TRY(w.M.reserve(nsc * nc * sizeof(float2)));
+    FMM_TRY(w.srel.reserve(np * 16));
     fmm_p2m_kernel<<<nblk(nsc, kCellWarps), 32 * kCellWarps, 0, s>>>(w.scell.as<FCell>(), nsc, w.spos.as<double>(),
                                                                      w.sdat.as<float4>(), half_w0, P,
-                                                                     w.M.as<float2>());
+                                                                     w.M.as<float2>(), w.srel.as<float4>());
     FMM_TRY(cudaGetLastError());
     for (int l = (int)st_s.level_off.size() - 2; l >= 0; --l) {
         const int64_t c0 = st_s.level_off[l], n = st_s.level_off[l + 1] - c0;
@@ -866,7 +1101,7 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
         while (nf > 0) {
             FMM_TRY(cudaMemsetAsync(w.cnt.p, 0, sizeof(unsigned long long), s));   // next = 0
             fmm_dtt_kernel<<<nblk(nf, 256), 256, 0, s>>>(
-                w.front.as<int2>(), nf, w.tcell.as<FCell>(), w.scell.as<FCell>(), r0, o.theta * o.theta,
+                w.front.as<int2>(), nf, w.tcell.as<FCell>(), w.scell.as<FCell>(), o.theta * o.theta,
                 w.next.as<int2>(), w.cap_front, w.m2l.as<uint64_t>(), w.cap_m2l, w.p2p.as<uint64_t>(), w.cap_p2p,
                 w.cnt.as<DttCounters>());
             FMM_TRY(cudaGetLastError());
@@ -911,9 +1146,20 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
 
     // downward pass
     FMM_TRY(w.L.reserve(ntc * nc * sizeof(float2)));
-    fmm_m2l_kernel<<<nblk(ntc, kCellWarps), 32 * kCellWarps, 0, s>>>(
+    FMM_TRY(w.queue.reserve(2 * sizeof(unsigned long long)));
+    unsigned long long *queue = w.queue.as<unsigned long long>();
+    FMM_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s));
+    FMM_TRY(cudaMemsetAsync(w.L.p, 0, ntc * nc * sizeof(float2), s));
+    if (w.grid_m2l == 0) {
+        int per_sm = 0;
+        FMM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_m2l_kernel, 32 * kCellWarps, 0));
+        w.grid_m2l = std::max(1, per_sm) * g->num_sms;
+        FMM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_leaf_kernel, 32 * kCellWarps, 0));
+        w.grid_leaf = std::max(1, per_sm) * g->num_sms;
+    }
+    fmm_m2l_kernel<<<(int)std::min<int64_t>(w.grid_m2l, nblk(ntc, kCellWarps)), 32 * kCellWarps, 0, s>>>(
         w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.m2l_off.as<int64_t>(), w.m2l_s.as<uint64_t>(), half_w0, P,
-        w.M.as<float2>(), w.L.as<float2>());
+        w.M.as<float2>(), w.L.as<float2>(), queue);
     FMM_TRY(cudaGetLastError());
     FMM_TRY(w.tparent.reserve(ntc * 4));
     fmm_parent_kernel<<<nblk(ntc, 256), 256, 0, s>>>(w.tcell.as<FCell>(), ntc, w.tparent.as<int32_t>());
@@ -925,9 +1171,10 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
                                                                        w.L.as<float2>());
         FMM_TRY(cudaGetLastError());
     }
-    fmm_leaf_kernel<<<nblk(ntc, kCellWarps), 32 * kCellWarps, 0, s>>>(
+    fmm_leaf_kernel<<<(int)std::min<int64_t>(w.grid_leaf, nblk(ntc, kCellWarps)), 32 * kCellWarps, 0, s>>>(
         w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.p2p_off.as<int64_t>(), w.p2p_s.as<uint64_t>(),
-        w.tval.as<int32_t>(), t, w.spos.as<double>(), w.sdat.as<float4>(), half_w0, P, w.L.as<float2>(), out);
+        w.tval.as<int32_t>(), t, w.srel.as<float4>(), w.sdat.as<float4>(), half_w0, P, w.L.as<float2>(), out,
+        queue + 1);
     FMM_TRY(cudaGetLastError());
 
     if (st) {
