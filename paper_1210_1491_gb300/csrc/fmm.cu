@@ -280,30 +280,32 @@ __global__ void fmm_source_kernel(int64_t n, const int32_t *__restrict__ val, co
                           (float)c);
 }
 
-// Cell radii, one level at a time from the deepest: a leaf takes the largest
-// distance of its points from its centre (FP64, points through the optional
-// id list), a split cell max over children of |c_child - c| + r_child.
+// Cell radii, one level at a time from the deepest, a warp per cell: a leaf
+// takes the largest distance of its points from its centre (FP64, points
+// through the optional id list), a split cell max over children of
+// |c_child - c| + r_child.
 __global__ void fmm_radius_kernel(FCell *__restrict__ cells, int64_t c0, int64_t ncell,
                                   const double *__restrict__ x, const int32_t *__restrict__ ids) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= ncell) return;
     FCell &C = cells[c0 + i];
-    double r2 = 0.0, r = 0.0;
+    double r = 0.0;
     if (C.child < 0) {
-        for (int k = C.start; k < C.start + C.count; ++k) {
+        double r2 = 0.0;
+        for (int k = C.start + lane; k < C.start + C.count; k += 32) {
             const int64_t p = ids ? ids[k] : k;
             const double dx = x[3 * p] - C.c[0], dy = x[3 * p + 1] - C.c[1], dz = x[3 * p + 2] - C.c[2];
             r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
         }
         r = sqrt(r2);
-    } else {
-        for (int k = 0; k < C.nchild; ++k) {
-            const FCell &D = cells[C.child + k];
-            const double dx = D.c[0] - C.c[0], dy = D.c[1] - C.c[1], dz = D.c[2] - C.c[2];
-            r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz) + D.r);
-        }
+    } else if (lane < C.nchild) {
+        const FCell &D = cells[C.child + lane];
+        const double dx = D.c[0] - C.c[0], dy = D.c[1] - C.c[1], dz = D.c[2] - C.c[2];
+        r = sqrt(dx * dx + dy * dy + dz * dz) + D.r;
     }
-    C.r = r;
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) C.r = r;
 }
 
 // ------------------------------------------------------------------ upward pass
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_p2m_kernel(
     const FCell cell = cells[ci];
     if (cell.child >= 0) return;
     const int nc = tri(P + 1, 0);
-    const double h = ldexp(half_w0, -cell.level);
-    const float ih = (float)(1.0 / h);
+    const double ihd = ldexp(1.0 / half_w0, cell.level);   // 1/h, a power-of-two scaling of 1/half_w0
+    const float ih = (float)ihd;
     float2 acc[kOwnMax];
     int on[kOwnMax], om[kOwnMax];
 #pragma unroll
@@ -342,31 +344,41 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_p2m_kernel(
     for (int s = cell.start + lane; s < cell.start + cell.count; s += 32)
         srel[s] = make_float4((float)(spos[3 * s] - cell.c[0]), (float)(spos[3 * s + 1] - cell.c[1]),
                               (float)(spos[3 * s + 2] - cell.c[2]), sdat[s].w);
-    for (int s = cell.start; s < cell.start + cell.count; ++s) {
-        const float vx = (float)((spos[3 * s] - cell.c[0]) / h), vy = (float)((spos[3 * s + 1] - cell.c[1]) / h),
-                    vz = (float)((spos[3 * s + 2] - cell.c[2]) / h);
-        const float4 sd = sdat[s];
+    // G sources per pass: lane group g = lane / (P+1) builds source g's table, lane m = lane % (P+1) its column
+    const int G = min(32 / (P + 1), kNsMax / nc);
+    const int grp = lane / (P + 1), col = lane % (P + 1);
+    for (int s0 = cell.start; s0 < cell.start + cell.count; s0 += G) {
+        const int ng = min(G, cell.start + cell.count - s0);
         __syncwarp();
-        if (lane <= P) regular_column(tab, lane, P, vx, vy, vz);
+        if (grp < ng) {
+            const int s = s0 + grp;
+            const float vx = (float)((spos[3 * s] - cell.c[0]) * ihd), vy = (float)((spos[3 * s + 1] - cell.c[1]) * ihd),
+                        vz = (float)((spos[3 * s + 2] - cell.c[2]) * ihd);
+            regular_column(tab + grp * nc, col, P, vx, vy, vz);
+        }
         __syncwarp();
-        const float dx = sd.x * ih, dy = sd.y * ih, dz = sd.z * ih, c = sd.w;
-        const float2 dp = make_float2(0.5f * dx, 0.5f * dy);    // (dx + i dy) / 2
-        const float2 dm = make_float2(0.5f * dx, -0.5f * dy);   // (dx - i dy) / 2
+        for (int g = 0; g < ng; ++g) {
+            const float2 *tg = tab + g * nc;
+            const float4 sd = sdat[s0 + g];
+            const float dx = sd.x * ih, dy = sd.y * ih, dz = sd.z * ih, c = sd.w;
+            const float2 dp = make_float2(0.5f * dx, 0.5f * dy);    // (dx + i dy) / 2
+            const float2 dm = make_float2(0.5f * dx, -0.5f * dy);   // (dx - i dy) / 2
 #pragma unroll
-        for (int r = 0; r < kOwnMax; ++r) {
-            if (lane + 32 * r >= nc) break;
-            const int n = on[r], m = om[r];
-            float2 t = cscale(tab[tri(n, m)], c);
-            if (n >= 1) {
-                // R_{n-1}^{m-1} (m = 0: -conj(R_{n-1}^1)), R_{n-1}^{m+1}, R_{n-1}^m
-                float2 rm1 = make_float2(0.0f, 0.0f);
-                if (m >= 1) rm1 = tab[tri(n - 1, m - 1)];
-                else if (n - 1 >= 1) { const float2 v = tab[tri(n - 1, 1)]; rm1 = make_float2(-v.x, v.y); }
-                if (m - 1 <= n - 1) cmac(t, dp, rm1);
-                if (m + 1 <= n - 1) { const float2 v = tab[tri(n - 1, m + 1)]; cmac(t, make_float2(-dm.x, -dm.y), v); }
-                if (m <= n - 1) { const float2 v = tab[tri(n - 1, m)]; t.x = fmaf(dz, v.x, t.x); t.y = fmaf(dz, v.y, t.y); }
+            for (int r = 0; r < kOwnMax; ++r) {
+                if (lane + 32 * r >= nc) break;
+                const int n = on[r], m = om[r];
+                float2 t = cscale(tg[tri(n, m)], c);
+                if (n >= 1) {
+                    // R_{n-1}^{m-1} (m = 0: -conj(R_{n-1}^1)), R_{n-1}^{m+1}, R_{n-1}^m
+                    float2 rm1 = make_float2(0.0f, 0.0f);
+                    if (m >= 1) rm1 = tg[tri(n - 1, m - 1)];
+                    else if (n - 1 >= 1) { const float2 v = tg[tri(n - 1, 1)]; rm1 = make_float2(-v.x, v.y); }
+                    cmac(t, dp, rm1);
+                    if (m + 1 <= n - 1) { const float2 v = tg[tri(n - 1, m + 1)]; cmac(t, make_float2(-dm.x, -dm.y), v); }
+                    if (m <= n - 1) { const float2 v = tg[tri(n - 1, m)]; t.x = fmaf(dz, v.x, t.x); t.y = fmaf(dz, v.y, t.y); }
+                }
+                acc[r] = cadd(acc[r], cconj(t));
             }
-            acc[r] = cadd(acc[r], cconj(t));
         }
     }
 #pragma unroll
@@ -385,7 +397,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2m_kernel(
     const FCell cell = cells[ci];
     if (cell.child < 0) return;
     const int nc = tri(P + 1, 0);
-    const double h = ldexp(half_w0, -cell.level);
+    const double ihd = ldexp(1.0 / half_w0, cell.level);
     float2 acc[kOwnMax];
     int on[kOwnMax], om[kOwnMax];
 #pragma unroll
@@ -398,8 +410,8 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2m_kernel(
     float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
     for (int k = 0; k < cell.nchild; ++k) {
         const int64_t cc = cell.child + k;
-        const float dx = (float)((cells[cc].c[0] - cell.c[0]) / h), dy = (float)((cells[cc].c[1] - cell.c[1]) / h),
-                    dz = (float)((cells[cc].c[2] - cell.c[2]) / h);
+        const float dx = (float)((cells[cc].c[0] - cell.c[0]) * ihd), dy = (float)((cells[cc].c[1] - cell.c[1]) * ihd),
+                    dz = (float)((cells[cc].c[2] - cell.c[2]) * ihd);
         __syncwarp();
         if (lane <= P) regular_column(tab, lane, P, dx, dy, dz);
         for (int e = lane; e < nc; e += 32) ex[e] = M[cc * nc + e];
@@ -578,6 +590,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     const bool round2 = __any_sync(0xffffffffu, tv[1]);
     float2 *S = sh[wid].s + kSPad, *Mf = sh[wid].m;
     if (lane < kSPad) sh[wid].s[lane] = make_float2(0.0f, 0.0f);
+    const double ihw = 1.0 / half_w0;
     for (;;) {
     unsigned long long qi = 0;
     if (lane == 0) qi = atomicAdd(queue, 1ull);
@@ -596,7 +609,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
         const FCell &Sc = sc[si];
         const int lt = T.level, ls = Sc.level;
         const int lr = min(lt, ls);
-        const double irho = ldexp(1.0 / half_w0, lr);
+        const double irho = ldexp(ihw, lr);
         const float vx = (float)((T.c[0] - Sc.c[0]) * irho), vy = (float)((T.c[1] - Sc.c[1]) * irho),
                     vz = (float)((T.c[2] - Sc.c[2]) * irho);
         const int bt = lt - lr, bs = ls - lr;
@@ -700,9 +713,9 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_l2l_kernel(
     const FCell &C = tc[ci];
     const FCell &Pp = tc[pi];
     const int nc = tri(P + 1, 0);
-    const double h = ldexp(half_w0, -Pp.level);
-    const float dx = (float)((C.c[0] - Pp.c[0]) / h), dy = (float)((C.c[1] - Pp.c[1]) / h),
-                dz = (float)((C.c[2] - Pp.c[2]) / h);
+    const double ihd = ldexp(1.0 / half_w0, Pp.level);
+    const float dx = (float)((C.c[0] - Pp.c[0]) * ihd), dy = (float)((C.c[1] - Pp.c[1]) * ihd),
+                dz = (float)((C.c[2] - Pp.c[2]) * ihd);
     float2 *tab = sh[wid].tab, *ex = sh[wid].exp;
     if (lane <= P) regular_column(tab, lane, P, dx, dy, dz);
     for (int q = lane; q < nc; q += 32) ex[q] = L[pi * nc + q];
@@ -767,7 +780,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
     __syncwarp();
     for (int q = lane; q < nc; q += 32) S.l[q] = L[ti * nc + q];
     __syncwarp();
-    const double h = ldexp(half_w0, -T.level);
+    const double ihd = ldexp(1.0 / half_w0, T.level);
     const int64_t e0 = off[ti], e1 = off[ti + 1];
     for (int tb = T.start; tb < T.start + T.count; tb += 32) {
         const int nt = min(32, T.start + T.count - tb);
@@ -775,8 +788,8 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
         // L2P, a lane per target
         if (lane < nt) {
             const int32_t id = tval[tb + lane];
-            const float x = (float)((targets[3 * id] - T.c[0]) / h), y = (float)((targets[3 * id + 1] - T.c[1]) / h),
-                        z = (float)((targets[3 * id + 2] - T.c[2]) / h);
+            const float x = (float)((targets[3 * id] - T.c[0]) * ihd), y = (float)((targets[3 * id + 1] - T.c[1]) * ihd),
+                        z = (float)((targets[3 * id + 2] - T.c[2]) * ihd);
             const float r2 = fmaf(x, x, fmaf(y, y, z * z));
             float far = 0.0f;
             float2 rmm = make_float2(1.0f, 0.0f);
@@ -1055,11 +1068,11 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
     FMM_TRY(build_tree(w, w.tcell, w.tval, nt, t, nullptr, lo, width, o.leaf_targets, o.max_level, st_t, s));
     for (int l = (int)st_s.level_off.size() - 2; l >= 0; --l) {
         const int64_t c0 = st_s.level_off[l], n = st_s.level_off[l + 1] - c0;
-        fmm_radius_kernel<<<nblk(n, 128), 128, 0, s>>>(w.scell.as<FCell>(), c0, n, w.spos.as<double>(), nullptr);
+        fmm_radius_kernel<<<nblk(32 * n, 128), 128, 0, s>>>(w.scell.as<FCell>(), c0, n, w.spos.as<double>(), nullptr);
     }
     for (int l = (int)st_t.level_off.size() - 2; l >= 0; --l) {
         const int64_t c0 = st_t.level_off[l], n = st_t.level_off[l + 1] - c0;
-        fmm_radius_kernel<<<nblk(n, 128), 128, 0, s>>>(w.tcell.as<FCell>(), c0, n, t, w.tval.as<int32_t>());
+        fmm_radius_kernel<<<nblk(32 * n, 128), 128, 0, s>>>(w.tcell.as<FCell>(), c0, n, t, w.tval.as<int32_t>());
     }
     FMM_TRY(cudaGetLastError());
     const int64_t nsc = st_s.ncell, ntc = st_t.ncell;
