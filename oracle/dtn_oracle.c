@@ -818,9 +818,12 @@ typedef struct {
     const or_patch *p;
     const or_data *dat;
     int kind;           /* 0: G(X,Y); 1: dG/dn_y(X,Y) (g(y) - g(x)); 2: G(X,Y) q_exact(y);
-                           3: dG/dn_y(X,Y) g(y) */
+                           3: dG/dn_y(X,Y) g(y); 4: K(X,Y) (g(y) - l(Y)) + dG/dn_x(X,Y) a.n_y;
+                           5: dG/dn_x(X,Y) (second kind, see or_second_kind) */
     double X[3];
-    double gx;          /* g at the collocation point (kind 1) */
+    double gx;          /* g at the collocation point (kinds 1, 4) */
+    double nx[3];       /* normal at X (kinds 4, 5) */
+    double ga[3];       /* tangential gradient of g at X, l(Y) = gx + ga.(Y - X) (kind 4) */
 } quad_ctx;
 
 static double gl10_x[10], gl10_w[10];
@@ -839,6 +842,19 @@ static double integrand(const quad_ctx *c, double u, double v)
     double Y[3], nl[3], J;
     patch_point(c->p, u, v, Y, nl, &J);
     if (c->kind == 0) return or_green(c->p->a, c->X, Y) * J;
+    if (c->kind == 4 || c->kind == 5) {
+        /* dG/dn_x(X, Y) = n_x . grad_X G(X, Y) = n_x . (grad_y G)(Y, X), G symmetric */
+        double gX[3];
+        or_green_grad_y(c->p->a, Y, c->X, gX);
+        const double dnx = gX[0] * c->nx[0] + gX[1] * c->nx[1] + gX[2] * c->nx[2];
+        if (c->kind == 5) return dnx * J;
+        double y[3];
+        local_to_global(c->p, Y, y);
+        const double l = c->gx + c->ga[0] * (Y[0] - c->X[0]) + c->ga[1] * (Y[1] - c->X[1]) +
+                         c->ga[2] * (Y[2] - c->X[2]);
+        const double an = c->ga[0] * nl[0] + c->ga[1] * nl[1] + c->ga[2] * nl[2];
+        return (or_green_dnn(c->p->a, c->X, c->nx, Y, nl) * (or_dirichlet(c->dat, y) - l) + dnx * an) * J;
+    }
     double y[3];
     local_to_global(c->p, Y, y);
     if (c->kind == 1 || c->kind == 3) {
@@ -969,10 +985,11 @@ static double duffy_triangle(const quad_ctx *c, const double S[2], const double 
  * collocation point lies on this panel) the box is cut into four triangles
  * from the singular parameter point and each is integrated through the Duffy
  * map.  `rtol` is relative to area / (4 pi max(distance, diameter)). */
+static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *sing, double rtol);
+
 double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const double X[3],
                          const double prm[6], const double *sing, double rtol)
 {
-    gl10_init();
     quad_ctx c;
     memset(&c, 0, sizeof(c));
     c.p = p; c.dat = dat; c.kind = kind;
@@ -982,6 +999,14 @@ double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const 
         local_to_global(p, X, xg);
         c.gx = or_dirichlet(dat, xg);
     }
+    return panel_integral_ctx(c, prm, sing, rtol);
+}
+
+static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *sing, double rtol)
+{
+    gl10_init();
+    const or_patch *p = c.p;
+    const double *X = c.X;
     double u0 = prm[0], u1 = prm[1], v0 = prm[2], v1 = prm[3];
     double Yc[3], nl[3], J;
     patch_point(p, prm[4], prm[5], Yc, nl, &J);
@@ -1000,6 +1025,57 @@ double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const 
     double S[2] = {sing[0], sing[1]};
     double cor[5][2] = {{u0, v0}, {u1, v0}, {u1, v1}, {u0, v1}, {u0, v0}};
     double s = 0.0;
+    if (c.kind == 4 || c.kind == 5) {
+        /* Second-kind integrands: bounded and smooth in the Duffy variables, but
+         * next to the corner s = 0 rounding dominates them (g - l is O(r^2)
+         * against g = O(1), divided by r^3; n_x.(x - y) is O(r^2) from
+         * components of size r), so an adaptive split toward s = 0 would chase
+         * rounding.  A fixed Gauss rule of order
+         * 40 x 40 per triangle keeps its points at s >= 1e-3; each triangle's
+         * far edge is cut into pieces no longer than its height. */
+        enum { NQ = 40 };
+        static double gx40[NQ], gw40[NQ];
+        static int ready = 0;
+#pragma omp critical(or_gl40)
+        if (!ready) { or_gauss_legendre(NQ, gx40, gw40); ready = 1; }
+        double PS[3], nn[3], Jd;
+        patch_point(p, S[0], S[1], PS, nn, &Jd);
+        for (int e = 0; e < 4; ++e) {
+          /* the far edge cut into m pieces no longer than the triangle's height */
+          double PA[3], PB[3];
+          patch_point(p, cor[e][0], cor[e][1], PA, nn, &Jd);
+          patch_point(p, cor[e + 1][0], cor[e + 1][1], PB, nn, &Jd);
+          double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
+          double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
+          double cr[3];
+          cross3(ab, as, cr);
+          double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+          double hh = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / (L > 0 ? L : 1.0);
+          int m = (int)ceil(L / (hh > 0 ? hh : 1.0));
+          if (m < 1) m = 1;
+          if (m > 64) m = 64;
+          for (int piece = 0; piece < m; ++piece) {
+            double A0[2] = {cor[e][0] + (cor[e + 1][0] - cor[e][0]) * piece / m,
+                            cor[e][1] + (cor[e + 1][1] - cor[e][1]) * piece / m};
+            double B0[2] = {cor[e][0] + (cor[e + 1][0] - cor[e][0]) * (piece + 1) / m,
+                            cor[e][1] + (cor[e + 1][1] - cor[e][1]) * (piece + 1) / m};
+            double E1[2] = {A0[0] - S[0], A0[1] - S[1]};
+            double E2[2] = {B0[0] - A0[0], B0[1] - A0[1]};
+            double det = fabs(E1[0] * E2[1] - E1[1] * E2[0]);
+            if (det == 0.0) continue;
+            for (int i = 0; i < NQ; ++i) {
+                double sv = 0.5 * (gx40[i] + 1.0);
+                for (int j = 0; j < NQ; ++j) {
+                    double tv = 0.5 * (gx40[j] + 1.0);
+                    double u = S[0] + sv * (E1[0] + tv * E2[0]);
+                    double v = S[1] + sv * (E1[1] + tv * E2[1]);
+                    s += 0.25 * gw40[i] * gw40[j] * integrand(&c, u, v) * sv * det;
+                }
+            }
+          }
+        }
+        return s;
+    }
     for (int e = 0; e < 4; ++e) s += duffy_triangle(&c, S, cor[e], cor[e + 1], 0.25 * tol);
     return s;
 }
@@ -1043,6 +1119,89 @@ void or_assemble(const or_patch *p, const or_data *dat, int nr, int ns, int nt, 
         b[i] = bi;
     }
     free(Xl); free(xg); free(ar); free(prm); free(Yl); free(W);
+}
+
+/* ============================================= second kind, any patch */
+/* Second-kind local BIE (Eq. bw55-bw59) on a disk or cap patch, collocated at
+ * the panel collocation points with piecewise-constant Neumann data:
+ *   (1/2) q_i - sum_j D_ij q_j = b_i,   D_ij = int_{panel j} dG/dn_x(x_i, y) ds_y.
+ * The Hadamard finite part in b (Eq. bw59) is regularised with the harmonic
+ * function l_i(y) = g(x_i) + a_i.(y - x_i), a_i the tangential gradient of g
+ * at x_i (central differences, h = 1e-5 a, along the two unit tangents of the
+ * patch there): Eq. bw55 holds for l_i itself, whose Neumann data is a_i.n_y
+ * and a_i.n_x = 0, so
+ *   p.f. int_S K l_i = - int_Gamma K l_i + D[a_i.n](x_i),
+ * and
+ *   b_i = - sum_k W_k K(x_i, y_k) (U_k - l_i(y_k))
+ *         - int_S [ K(x_i, y) (g(y) - l_i(y)) + dG/dn_x(x_i, y) a_i.n_y ] ds_y,
+ * K = d2G/dn_x dn_y; g - l_i = O(|y - x_i|^2) on S, so every integrand is
+ * O(1/|y - x_i|) and the self panel goes through the Duffy map.  Entries by
+ * the adaptive rules of or_panel_integral (relative tolerance rtol).  A (n x n,
+ * row-major) and b are written when not NULL; q receives the solution.  U: the
+ * hemisphere values at the nodes of or_gamma_nodes(p, nt, nph).  Returns the
+ * status of the LU solve. */
+int or_lu_solve(int n, double *A, double *b, double *x);
+
+int or_second_kind(const or_patch *p, const or_data *dat, int nt, int nph, int nr, int ns, const double *U,
+                   double rtol, double *A_out, double *b_out, double *q)
+{
+    const int n = nr * ns, P = nt * nph;
+    const double a = p->a;
+    double *Xl = malloc(sizeof(double) * 3 * n), *xg = malloc(sizeof(double) * 3 * n);
+    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * 6 * n);
+    double *Yl = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
+    double *A = malloc(sizeof(double) * (size_t)n * n), *b = malloc(sizeof(double) * n);
+    or_panels(p, nr, ns, Xl, xg, NULL, ar, prm);
+    or_gamma_nodes(p, nt, nph, Yl, NULL, W);
+    gl10_init();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; ++i) {
+        const double *X = Xl + 3 * i;
+        double Yc[3], nx[3], J;
+        patch_point(p, prm[6 * i + 4], prm[6 * i + 5], Yc, nx, &J);
+        /* unit tangents at the collocation point: along u and along v */
+        const double uc = prm[6 * i + 4], vc = prm[6 * i + 5];
+        double e1[3], e2[3] = {-sin(vc), cos(vc), 0.0};
+        if (p->kind == 0) { e1[0] = cos(vc); e1[1] = sin(vc); e1[2] = 0.0; }
+        else { e1[0] = cos(uc) * cos(vc); e1[1] = cos(uc) * sin(vc); e1[2] = -sin(uc); }
+        const double h = 1e-5 * a;
+        double ga[3] = {0.0, 0.0, 0.0};
+        const double *ev[2] = {e1, e2};
+        for (int d = 0; d < 2; ++d) {
+            double Lp[3], Lm[3], yp[3], ym[3];
+            for (int k = 0; k < 3; ++k) { Lp[k] = X[k] + h * ev[d][k]; Lm[k] = X[k] - h * ev[d][k]; }
+            local_to_global(p, Lp, yp);
+            local_to_global(p, Lm, ym);
+            const double dg = (or_dirichlet(dat, yp) - or_dirichlet(dat, ym)) / (2.0 * h);
+            for (int k = 0; k < 3; ++k) ga[k] += dg * ev[d][k];
+        }
+        quad_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.p = p; c.dat = dat;
+        for (int k = 0; k < 3; ++k) { c.X[k] = X[k]; c.nx[k] = nx[k]; c.ga[k] = ga[k]; }
+        c.gx = or_dirichlet(dat, xg + 3 * i);
+        double bi = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double *sing = (i == j) ? prm + 6 * i + 4 : NULL;
+            c.kind = 5;
+            const double dij = panel_integral_ctx(c, prm + 6 * j, sing, rtol);
+            A[(int64_t)i * n + j] = (i == j ? 0.5 : 0.0) - dij;
+            c.kind = 4;
+            bi -= panel_integral_ctx(c, prm + 6 * j, sing, rtol);
+        }
+        for (int k = 0; k < P; ++k) {
+            const double *Y = Yl + 3 * k;
+            const double ny[3] = {Y[0] / a, Y[1] / a, Y[2] / a};
+            const double l = c.gx + ga[0] * (Y[0] - X[0]) + ga[1] * (Y[1] - X[1]) + ga[2] * (Y[2] - X[2]);
+            bi -= W[k] * or_green_dnn(a, X, nx, Y, ny) * (U[k] - l);
+        }
+        b[i] = bi;
+    }
+    if (A_out) memcpy(A_out, A, sizeof(double) * (size_t)n * n);
+    if (b_out) memcpy(b_out, b, sizeof(double) * n);
+    int st = or_lu_solve(n, A, b, q);
+    free(Xl); free(xg); free(ar); free(prm); free(Yl); free(W); free(A); free(b);
+    return st;
 }
 
 /* ======================================================================= LU */

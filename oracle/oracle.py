@@ -111,6 +111,9 @@ def lib():
         L.or_second_kind_flat.argtypes = [C.POINTER(OrPatch), C.POINTER(OrData), C.c_int, C.c_int, C.c_int,
                                           C.c_int, _f64p, C.c_int, _f64p]
         L.or_second_kind_flat.restype = C.c_int
+        L.or_second_kind.argtypes = [C.POINTER(OrPatch), C.POINTER(OrData), C.c_int, C.c_int, C.c_int, C.c_int,
+                                     _f64p, C.c_double, C.c_void_p, C.c_void_p, _f64p]
+        L.or_second_kind.restype = C.c_int
         L.or_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -432,6 +435,27 @@ def second_kind_flat(p: OrPatch, data, nt, nph, nr, ns, U, ng2=20) -> np.ndarray
     if rc != 0:
         raise ValueError("second-kind rows need a disk patch")
     return q
+
+
+def second_kind(p: OrPatch, data, nt, nph, nr, ns, U, rtol=1e-10, want_system=False):
+    """or_second_kind: Neumann data of a disk or cap patch by the second-kind
+    local BIE (Eq. bw55-bw59) with the harmonic-linear regularisation of the
+    finite part; hemisphere values U at or_gamma_nodes(p, nt, nph).  With
+    want_system also returns (A, b) of (1/2 I - D) q = b.  rtol: the adaptive
+    panel rules' relative tolerance; below ~1e-11 the rules next to x_i chase
+    the rounding of g - l (O(r^2) against g = O(1)) and slow down."""
+    od, keep = make_data(data)
+    n = nr * ns
+    q = np.zeros(n)
+    A = np.zeros((n, n)) if want_system else None
+    b = np.zeros(n) if want_system else None
+    rc = lib().or_second_kind(C.byref(p), C.byref(od), int(nt), int(nph), int(nr), int(ns),
+                              np.ascontiguousarray(U, dtype=np.float64), float(rtol),
+                              None if A is None else A.ctypes.data_as(C.c_void_p),
+                              None if b is None else b.ctypes.data_as(C.c_void_p), q)
+    if rc != 0:
+        raise ValueError(f"or_second_kind: LU status {rc}")
+    return (q, A, b) if want_system else q
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]

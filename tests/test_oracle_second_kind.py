@@ -58,3 +58,92 @@ def test_exact_hemisphere_values_give_the_neumann_data():
         q = O.second_kind_flat(pf, wl.data, nt, 2 * nt, 8, 8, U, ng2=20)
         rel = np.abs(q - qe) / np.abs(qe)
         assert rel[inner].max() <= bound, (nt, rel[inner].max())
+
+
+# ----------------------------------------------------------------- any patch (cap or disk)
+# or_second_kind: (1/2 I - D) q = b with D_ij = int_{panel j} dG/dn_x(x_i, y) ds_y and the
+# finite part regularised by the harmonic function l_i = g(x_i) + grad_S g(x_i).(y - x_i).
+
+def _ball_cap(i=3, a=0.1):
+    wl = W.unit_ball(n_patches=20)
+    return wl, O.patch_frame(wl.geometry, wl.batch.centers[i], a)
+
+
+def test_general_constant_solution_gives_zero():
+    _, pf = _ball_cap()
+    const = W.Dirichlet(W.DATA_CONSTANT, constant=2.0)
+    q = O.second_kind(pf, const, 16, 32, 4, 8, np.full(16 * 32, 2.0))
+    assert np.max(np.abs(q)) < 1e-12
+
+
+def test_general_rows_agree_with_flat_rows_on_a_disk():
+    """Two regularisations of the linear Taylor term (the exact rim integral of
+    the flat rows, the identity for the harmonic l_i here) give the same inner
+    rows."""
+    wc = W.cube_single_patch()
+    pd = O.patch_frame(wc.geometry, wc.batch.centers[0], 0.1)
+    _, yg, _ = O.gamma_nodes(pd, 16, 32)
+    U = O.dirichlet(wc.data, yg.reshape(-1, 3))
+    pan = O.panels(pd, 8, 8)
+    inner = np.linalg.norm(pan["Xloc"][:, :2], axis=1) < 0.07
+    qf = O.second_kind_flat(pd, wc.data, 16, 32, 8, 8, U, ng2=48)
+    qg = O.second_kind(pd, wc.data, 16, 32, 8, 8, U, rtol=1e-10)
+    assert np.max(np.abs(qg - qf)[inner]) <= 5e-4 * np.max(np.abs(qf))
+
+
+def test_cap_exact_hemisphere_values_give_the_neumann_data():
+    """Harmonic data r^l Y_lm on the unit ball (exact Neumann data
+    sum l c_lm Y_lm): with the exact solution at the hemisphere nodes the cap
+    rows match it inside r < 0.7a to 1e-3 of max|q|, and the system is well
+    conditioned (cond ~ 1)."""
+    wl, pf = _ball_cap()
+    nr, ns, nt, nph = 4, 8, 16, 32
+    _, yg, _ = O.gamma_nodes(pf, nt, nph)
+    U = O.dirichlet(wl.data, yg.reshape(-1, 3))
+    pan = O.panels(pf, nr, ns)
+    qe = O.neumann_exact(wl.data, pan["x"], pan["normal"])
+    q, A, b = O.second_kind(pf, wl.data, nt, nph, nr, ns, U, want_system=True)
+    inner = np.linalg.norm(pan["Xloc"][:, :2], axis=1) < 0.07
+    scale = np.max(np.abs(qe))
+    assert np.max(np.abs(q - qe)[inner]) <= 1e-3 * scale
+    assert np.max(np.abs(q - qe)) <= 0.1 * scale
+    assert np.linalg.cond(A) < 1.2
+
+
+
+def _cap_point(pf, u, v):
+    R = pf.R
+    return np.array([R * np.sin(u) * np.cos(v), R * np.sin(u) * np.sin(v), -2 * R * np.sin(0.5 * u) ** 2])
+
+
+def test_double_layer_row_sums_match_a_geodesic_polar_rule():
+    """sum_j D_ij = int_S dG/dn_x(x_i, y) ds_y (the panels' constant basis sums
+    to one).  Brute force: geodesic polar coordinates (sigma, phi) about x_i on
+    the sphere, the cap's edge at sigma_max(phi) from spherical trigonometry,
+    48 x 48 Gauss points; the integrand is bounded there (the 1/r of dG/dn_x
+    on a sphere against the Jacobian R^2 sin sigma)."""
+    wl, pf = _ball_cap(a=0.15)
+    nr, ns = 2, 4
+    q, A, b = O.second_kind(pf, wl.data, 4, 8, nr, ns, np.zeros(32), want_system=True)
+    D = 0.5 * np.eye(nr * ns) - A
+    pan = O.panels(pf, nr, ns)
+    R, a = pf.R, pf.a
+    o = np.array([0.0, 0.0, -R])                        # sphere centre, local frame
+    x, w = np.polynomial.legendre.leggauss(48)
+    for i in range(nr * ns):
+        X = pan["Xloc"][i]
+        p = (X - o) / R
+        nx = p                                         # outward unit normal at X
+        e1 = np.cross(p, [0.0, 1.0, 0.0]); e1 /= np.linalg.norm(e1)
+        e2 = np.cross(p, e1)
+        tot = 0.0
+        for phi, wp in zip(np.pi * (x + 1), np.pi * w):
+            d = np.cos(phi) * e1 + np.sin(phi) * e2
+            A0, B0 = p[2], d[2]
+            C0 = np.hypot(A0, B0)
+            smax = np.arctan2(B0, A0) + np.arccos(np.cos(pf.umax) / C0)
+            for sg, ws in zip(0.5 * smax * (x + 1), 0.5 * smax * w):
+                Y = o + R * (np.cos(sg) * p + np.sin(sg) * d)
+                dnx = float(np.dot(O.green_grad_y(a, Y, X), nx))
+                tot += wp * ws * dnx * R * R * np.sin(sg)
+        assert abs(D[i].sum() - tot) <= 1e-9 * max(1.0, abs(tot)), (i, D[i].sum(), tot)
