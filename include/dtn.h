@@ -122,9 +122,14 @@ typedef struct {
                                    stream (read them with dtn_stage_times) */
     int32_t wos_refill;         /* idle lanes of a warp before it refills them (0 = tuned) */
     int32_t bie_kind;           /* 0: first-kind local BIE (Eq. bw49-bw51, collocation solve);
-                                   1: second-kind local BIE (Eq. bw55-bw59), disk patches only:
-                                   there the double-layer operator vanishes and q = 2b */
-    int32_t ring_order;         /* second kind: Gauss order of the polar rules on S (0 = 20) */
+                                   1: second-kind local BIE (Eq. bw55-bw59).  Disk patches: the
+                                   double-layer operator vanishes and q = 2b row by row.  Cap
+                                   patches: (1/2 I - D) q = b with D_ij the integral of dG/dn_x
+                                   over panel j, the finite part of b regularised by the harmonic
+                                   l = g(x) + grad_S g(x).(y - x); FP64 rules for D and b (D per
+                                   patch shape in DTN_PREC_MIXED, solved with FP32 factors and
+                                   FP64 refinement) */
+    int32_t ring_order;         /* second kind on disks: Gauss order of the polar rules on S (0 = 20) */
 } dtn_solve_opts;
 
 /* Launch parameters of the walk kernel chosen by dtn_autotune_walks. */

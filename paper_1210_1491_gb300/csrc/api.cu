@@ -636,7 +636,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     if (o->bie_kind != 0 && o->bie_kind != 1) return DTN_E_INVALID_ARG;
     if (o->ring_order < 0 || o->ring_order > kMaxGauss) return DTN_E_INVALID_ARG;
     // the second-kind rows are written for flat patches (the double layer vanishes there)
-    if (o->bie_kind == 1 && (g->dg.kind == kBall || g->dg.kind == kBallExterior)) return DTN_E_UNSUPPORTED;
+
     if (!o->u_provided) {
         if (!b->walks_per_point || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
         for (int64_t p = 0; p < b->n_patches; ++p)
@@ -793,8 +793,9 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         if ((e = launch_wos(g, w, s)) != cudaSuccess) return e;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
-    // 3-4. second kind (Eq. bw55-bw59, disk patches): q = 2b row by row, no system
-    if (o->bie_kind == 1) {
+    const bool caps = (g->dg.kind == kBall || g->dg.kind == kBallExterior);
+    // 3-4. second kind (Eq. bw55-bw59) on disk patches: q = 2b row by row, no system
+    if (o->bie_kind == 1 && !caps) {
         e = launch_second_kind(g, L, D, W.panel_loc.as<double>(), pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                o->ring_order > 0 ? o->ring_order : 20, r->neumann, r->rhs, r->refine_iters,
                                r->residual, r->patch_status, s);
@@ -805,7 +806,22 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     // 3. assembly of Eq. bw49-bw51 (step 2)
     const double *pl = W.panel_loc.as<double>(), *pp = W.panel_prm.as<double>(), *pa = W.panel_aux.as<double>();
     const bool shared = (o->prec == DTN_PREC_MIXED);
-    if (shared) {
+    if (o->bie_kind == 1) {
+        // second kind on cap patches: (1/2 I - D) q = b.  Mixed precision: D per
+        // shape group (FP64 rules), every row's right side with the FP64 rules,
+        // FP32 group factors with FP64 refinement; FP64: per patch.
+        if (shared) {
+            e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                                W.gmat.as<double>(), rhs, s, 1);
+            if (e == cudaSuccess)
+                e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw,
+                                    r->u_gamma_mean, nullptr, rhs, s, 1);
+            if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, W.gmat.as<double>(), r->matrix, s);
+        } else {
+            e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,
+                                rhs, s, 1);
+        }
+    } else if (shared) {
         // one matrix and one set of right-side weights per patch shape, FP64
         // rules; the right sides of all patches of a shape as one product
         double *gA = W.gmat.as<double>();

@@ -60,13 +60,41 @@ struct Ctx {
     T gx;
     T c[3], t1[3], t2[3], n[3];
     const DData *dat;
+    // second kind (Eq. bw55-bw59): A accumulates dG/dn_x, D the regularised
+    // right-side integrand K (g - l) + dG/dn_x a.n_y, l(Y) = gx + ga.(Y - X)
+    bool sk;
+    T nx[3], ga[3];
 };
+
+// One quadrature point of the second-kind integrands (FP64 only).
+__device__ __forceinline__ void sk_point(const Ctx<double> &c, const double *Y, const double *nl, double wj,
+                                         double &sa, double &sd) {
+    const double yn = sqrt(Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2]);
+    // dG/dn_x(X, Y) = n_x . grad_X G(X, Y) = n_x . (grad_y G)(Y, X): G is symmetric
+    const double dnx = green_ball_dny<double>(c.a, Y, yn, c.X, c.nx);
+    if (c.needA) sa += wj * dnx;
+    if (c.needD) {
+        const double yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+        const double yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+        const double yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+        const double l = c.gx + c.ga[0] * (Y[0] - c.X[0]) + c.ga[1] * (Y[1] - c.X[1]) + c.ga[2] * (Y[2] - c.X[2]);
+        const double an = c.ga[0] * nl[0] + c.ga[1] * nl[1] + c.ga[2] * nl[2];
+        sd += wj * (green_ball_dnn(c.a, c.X, c.nx, Y, nl) * (dirichlet_eval<double>(*c.dat, yx, yy, yz) - l) +
+                    dnx * an);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void sk_point(const Ctx<T> &, const T *, const T *, T, T &, T &) {}
 
 template <typename T>
 __device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa, T &sd) {
     T Y[3], nl[3], J;
     patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
     const T wj = w * J;
+    if (c.sk) {
+        sk_point(c, Y, nl, wj, sa, sd);
+        return;
+    }
     if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
     if (c.needD) {
         const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
@@ -128,6 +156,11 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
         for (int j = 0; j < n; ++j) {
             const T Y[3] = {ru * cvs[j], ru * svs[j], rz};
             const T wj = wi * (T)gw[j] * J;
+            if (c.sk) {
+                const T nl[3] = {nu * cvs[j], nu * svs[j], nz};
+                sk_point(c, Y, nl, wj, sa, sd);
+                continue;
+            }
             if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
             if (c.needD) {
                 const T nl[3] = {nu * cvs[j], nu * svs[j], nz};
@@ -259,6 +292,7 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
     c.needA = true;
     c.gx = (T)gx;
     c.dat = dat;
+    c.sk = false;
 }
 
 struct AsmDev {
@@ -272,7 +306,8 @@ struct AsmDev {
     DData dat;
     int64_t n_patches;
     int prec;
-    int mode;
+    int mode;   // 0 matrix and right side per patch, 1 matrix per shape group, 2 right side only
+    int sk;     // second-kind system (1/2 I - D) q = b instead of Eq. bw49-bw51
     const double *glx, *glw;
 };
 
@@ -342,6 +377,9 @@ __device__ __forceinline__ double panel_ratio(const Ctx<double> &c, const double
     return dmin / ax[3];
 }
 
+// SK: the second-kind system (a separate instance, so the first-kind code
+// carries none of its branches).
+template <bool SK>
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     int64_t p, row;
     int n, i;
@@ -377,8 +415,43 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     __shared__ int near_list[1024];
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
+    __shared__ double sk_grad[2];
+    double e1[3] = {0.0, 0.0, 0.0}, e2[3] = {0.0, 0.0, 0.0};
+    if (SK) {
+        // normal at the collocation point and unit tangents along u and v there
+        const double uc = P.panel_prm[6 * row + 4], vc = P.panel_prm[6 * row + 5];
+        double Yc[3], nl[3], J;
+        patch_point<double>(f.kind, f.R, uc, vc, Yc, nl, J);
+        double su, cu, sv, cv;
+        sincos(uc, &su, &cu);
+        sincos(vc, &sv, &cv);
+        if (f.kind == kDisk) { e1[0] = cv; e1[1] = sv; e1[2] = 0.0; }
+        else { e1[0] = cu * cv; e1[1] = cu * sv; e1[2] = -su; }
+        e2[0] = -sv; e2[1] = cv; e2[2] = 0.0;
+        c64.sk = true;
+        c64.needA = (P.mode != 2);
+        c64.needD = (P.mode != 1);
+        for (int d = 0; d < 3; ++d) c64.nx[d] = nl[d];
+        if (threadIdx.x < 2) {
+            // tangential derivative of the data by central differences, h = 1e-5 a
+            const double h = 1e-5 * f.a;
+            const double *e = threadIdx.x == 0 ? e1 : e2;
+            double gp[3], gm[3];
+            for (int d = 0; d < 3; ++d) {
+                const double lp[3] = {X[0] + h * e[0], X[1] + h * e[1], X[2] + h * e[2]};
+                const double lm[3] = {X[0] - h * e[0], X[1] - h * e[1], X[2] - h * e[2]};
+                gp[d] = f.c[d] + lp[0] * f.t1[d] + lp[1] * f.t2[d] + lp[2] * f.n[d];
+                gm[d] = f.c[d] + lm[0] * f.t1[d] + lm[1] * f.t2[d] + lm[2] * f.n[d];
+            }
+            sk_grad[threadIdx.x] = (dirichlet_eval<double>(P.dat, gp[0], gp[1], gp[2]) -
+                                    dirichlet_eval<double>(P.dat, gm[0], gm[1], gm[2])) / (2.0 * h);
+        }
+    }
     if (threadIdx.x == 0) near_count = 0;
     __syncthreads();
+    if (SK)
+        for (int d = 0; d < 3; ++d) c64.ga[d] = sk_grad[0] * e1[d] + sk_grad[1] * e2[d];
+    const double dsign = SK ? -1.0 : 1.0;   // second kind: A = 1/2 I - D
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double dsum = 0.0;
     // far panels (r >= 2): one thread each, separable Gauss rule
@@ -397,7 +470,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
         gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
-        Arow[j] = sa;
+        if (Arow) Arow[j] = dsign * sa;
         dsum += sd;
     }
     // self panel: its Duffy triangles dealt to the warps in turn, the points of
@@ -427,7 +500,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             sa += self_part[0][w];
             sd += self_part[1][w];
         }
-        Arow[i] = sa;
+        if (Arow) Arow[i] = SK ? 0.5 - sa : sa;
         dsum += sd;
     }
     // near panels (r < 2): one warp each, adaptive cover, points over the lanes
@@ -448,7 +521,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             sd += __shfl_xor_sync(0xffffffffu, sd, o);
         }
         if (lane == 0) {
-            Arow[j] = sa;
+            if (Arow) Arow[j] = dsign * sa;
             dsum += sd;
         }
     }
@@ -460,7 +533,14 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         const int64_t gk = goff + k;
         const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
-        gsum += P.gamma_w[gk] * poisson_ball<double>(f.a, X, Y) * (P.U[gk] - gx);
+        if (SK) {
+            // second kind: sum_k W_k K(x_i, y_k) (U_k - l(y_k)), K = d2G/dn_x dn_y, n_y = Y / a
+            const double ny[3] = {Y[0] / f.a, Y[1] / f.a, Y[2] / f.a};
+            const double l = gx + c64.ga[0] * (Y[0] - X[0]) + c64.ga[1] * (Y[1] - X[1]) + c64.ga[2] * (Y[2] - X[2]);
+            gsum += P.gamma_w[gk] * green_ball_dnn(f.a, X, c64.nx, Y, ny) * (P.U[gk] - l);
+        } else {
+            gsum += P.gamma_w[gk] * poisson_ball<double>(f.a, X, Y) * (P.U[gk] - gx);
+        }
     }
     double v0 = dsum, v1 = gsum;
     for (int o = 16; o > 0; o >>= 1) {
@@ -473,7 +553,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0;
         for (int k = 0; k < kAsmThreads / 32; ++k) { s0 += red[0][k]; s1 += red[1][k]; }
-        P.b[row] = s0 - s1;
+        P.b[row] = SK ? -s0 - s1 : s0 - s1;
     }
 }
 
@@ -842,7 +922,7 @@ __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
-                            const double *U, double *A, double *b, cudaStream_t s) {
+                            const double *U, double *A, double *b, cudaStream_t s, int sk) {
     const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
     if (rows == 0) return cudaSuccess;
     AsmDev P;
@@ -867,9 +947,11 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.n_patches = L.n_patches;
     P.prec = prec;
     P.mode = mode;
+    P.sk = sk;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
-    assemble_kernel<<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    if (sk) assemble_kernel<true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    else assemble_kernel<false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -480,6 +480,33 @@ __device__ __forceinline__ T green_ball_dny(T a, const T *X, T xn, const T *Y, c
     return (t1 + t2) * (T)(0.25 / kPi);
 }
 
+// d2G/dn_x dn_y of the whole-sphere Dirichlet Green's function of B(c, a), local
+// coordinates, unit normals nx at X and ny at Y (the kernel of Eq. bw53, bw59):
+//   (1/4pi) [ nx.ny/r^3 - 3 (D.nx)(D.ny)/r^5 + a ( (2 (X.nx)(Y.ny) - a^2 nx.ny) Q^-3/2
+//             - 3 (|X|^2 Y.ny - a^2 X.ny)(|Y|^2 X.nx - a^2 Y.nx) Q^-5/2 ) ],  D = X - Y
+__device__ __forceinline__ double green_ball_dnn(double a, const double *X, const double *nx, const double *Y,
+                                                 const double *ny) {
+    const double D[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
+    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2], r = sqrt(r2);
+    const double Dnx = D[0] * nx[0] + D[1] * nx[1] + D[2] * nx[2];
+    const double Dny = D[0] * ny[0] + D[1] * ny[1] + D[2] * ny[2];
+    const double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
+    const double XX = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+    const double YY = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+    const double XY = X[0] * Y[0] + X[1] * Y[1] + X[2] * Y[2];
+    const double Xnx = X[0] * nx[0] + X[1] * nx[1] + X[2] * nx[2];
+    const double Yny = Y[0] * ny[0] + Y[1] * ny[1] + Y[2] * ny[2];
+    const double Xny = X[0] * ny[0] + X[1] * ny[1] + X[2] * ny[2];
+    const double Ynx = Y[0] * nx[0] + Y[1] * nx[1] + Y[2] * nx[2];
+    const double a2 = a * a;
+    const double Q = XX * YY - 2.0 * a2 * XY + a2 * a2;
+    const double sq = sqrt(Q);
+    const double fr = nn / (r2 * r) - 3.0 * Dnx * Dny / (r2 * r2 * r);
+    const double im = a * ((2.0 * Xnx * Yny - a2 * nn) / (Q * sq) -
+                           3.0 * (XX * Yny - a2 * Xny) * (YY * Xnx - a2 * Ynx) / (Q * Q * sq));
+    return (fr + im) / (4.0 * kPi);
+}
+
 // Poisson kernel of the ball, -dG/dn_y on |Y| = a: (a^2 - |X|^2) / (4 pi a |X - Y|^3)
 template <typename T>
 __device__ __forceinline__ T poisson_ball(T a, const T *X, const T *Y) {

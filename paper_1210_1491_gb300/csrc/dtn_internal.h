@@ -209,7 +209,8 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
                             int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
-                            const double *gamma_w, const double *U, double *A, double *b, cudaStream_t s);
+                            const double *gamma_w, const double *U, double *A, double *b, cudaStream_t s,
+                            int sk = 0);
 
 // mixed precision right sides: FP64 weights per shape group (product rules of
 // the double layer against the panel interpolants of the data, and the walk

@@ -23,31 +23,6 @@ namespace {
 
 constexpr int kSkThreads = 128;
 
-// d2G/dn_x dn_y of the whole-sphere Dirichlet Green's function of B(c, a), local
-// coordinates, unit normals nx at X and ny at Y
-__device__ __forceinline__ double green_dnn(double a, const double *X, const double *nx, const double *Y,
-                                            const double *ny) {
-    const double D[3] = {X[0] - Y[0], X[1] - Y[1], X[2] - Y[2]};
-    const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2], r = sqrt(r2);
-    const double Dnx = D[0] * nx[0] + D[1] * nx[1] + D[2] * nx[2];
-    const double Dny = D[0] * ny[0] + D[1] * ny[1] + D[2] * ny[2];
-    const double nn = nx[0] * ny[0] + nx[1] * ny[1] + nx[2] * ny[2];
-    const double XX = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
-    const double YY = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
-    const double XY = X[0] * Y[0] + X[1] * Y[1] + X[2] * Y[2];
-    const double Xnx = X[0] * nx[0] + X[1] * nx[1] + X[2] * nx[2];
-    const double Yny = Y[0] * ny[0] + Y[1] * ny[1] + Y[2] * ny[2];
-    const double Xny = X[0] * ny[0] + X[1] * ny[1] + X[2] * ny[2];
-    const double Ynx = Y[0] * nx[0] + Y[1] * nx[1] + Y[2] * nx[2];
-    const double a2 = a * a;
-    const double Q = XX * YY - 2.0 * a2 * XY + a2 * a2;
-    const double sq = sqrt(Q);
-    const double fr = nn / (r2 * r) - 3.0 * Dnx * Dny / (r2 * r2 * r);
-    const double im = a * ((2.0 * Xnx * Yny - a2 * nn) / (Q * sq) -
-                           3.0 * (XX * Yny - a2 * Xny) * (YY * Xnx - a2 * Ynx) / (Q * Q * sq));
-    return (fr + im) / (4.0 * kPi);
-}
-
 struct SkDev {
     const PatchFrame *frames;
     const int64_t *panel_off, *gamma_off;
@@ -117,7 +92,7 @@ __global__ void __launch_bounds__(kSkThreads) second_kind_kernel(SkDev P) {
         const int64_t gk = goff + k;
         const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
         const double ny[3] = {Y[0] / a, Y[1] / a, Y[2] / a};
-        sg += P.gamma_w[gk] * green_dnn(a, X, ez, Y, ny) * (P.U[gk] - gxi);
+        sg += P.gamma_w[gk] * green_ball_dnn(a, X, ez, Y, ny) * (P.U[gk] - gxi);
     }
     __syncthreads();
     const double g0 = grad[0], g1 = grad[1];
