@@ -126,10 +126,12 @@ typedef struct {
                                    double-layer operator vanishes and q = 2b row by row.  Cap
                                    patches: (1/2 I - D) q = b with D_ij the integral of dG/dn_x
                                    over panel j, the finite part of b regularised by the harmonic
-                                   l = g(x) + grad_S g(x).(y - x); FP64 rules for D and b (D per
-                                   patch shape in DTN_PREC_MIXED, solved with FP32 factors and
-                                   FP64 refinement) */
-    int32_t ring_order;         /* second kind on disks: Gauss order of the polar rules on S (0 = 20) */
+                                   l = g(x) + grad_S g(x).(y - x).  DTN_PREC_FP64: D and b by the
+                                   panel rules per patch.  DTN_PREC_MIXED: D per patch shape, b by
+                                   a geodesic polar rule about each collocation point, FP32
+                                   factors with FP64 refinement */
+    int32_t ring_order;         /* second kind: Gauss order of the polar rules on S
+                                   (0 = 20 on disks, 32 on caps) */
 } dtn_solve_opts;
 
 /* Launch parameters of the walk kernel chosen by dtn_autotune_walks. */

@@ -808,14 +808,15 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     const bool shared = (o->prec == DTN_PREC_MIXED);
     if (o->bie_kind == 1) {
         // second kind on cap patches: (1/2 I - D) q = b.  Mixed precision: D per
-        // shape group (FP64 rules), every row's right side with the FP64 rules,
-        // FP32 group factors with FP64 refinement; FP64: per patch.
+        // shape group (FP64 rules), every row's right side by the geodesic polar
+        // rule about its collocation point, FP32 group factors with FP64
+        // refinement; FP64: matrix and right side per patch with the panel rules.
         if (shared) {
             e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                 W.gmat.as<double>(), rhs, s, 1);
             if (e == cudaSuccess)
-                e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw,
-                                    r->u_gamma_mean, nullptr, rhs, s, 1);
+                e = launch_second_kind_cap_rhs(g, L, D, pl, pp, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                                               o->ring_order > 0 ? o->ring_order : 32, rhs, s);
             if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, W.gmat.as<double>(), r->matrix, s);
         } else {
             e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,

@@ -94,6 +94,8 @@ cudaError_t ensure_tables() {
     if ((e = upload_sh_tables_here(t)) != cudaSuccess) return e;
     if ((e = upload_sh_wos(t)) != cudaSuccess) return e;
     if ((e = upload_sh_assemble(t)) != cudaSuccess) return e;
+    if ((e = upload_sh_second_kind(t)) != cudaSuccess) return e;
+    if ((e = upload_sh_single_point(t)) != cudaSuccess) return e;
     g_tab_ready = true;
     return cudaSuccess;
 }

@@ -122,3 +122,7 @@ cudaError_t launch_sp_sigma(const dtn_geometry *g, int64_t n, int ng1, int ng2, 
 }
 
 }  // namespace dtn
+
+namespace dtn {
+cudaError_t upload_sh_single_point(const ShTables &t) { return upload_sh_tables_here(t); }
+}  // namespace dtn
