@@ -368,6 +368,31 @@ def run_potential_fmm(dtn, n_panels=1_000_000, n_targets=1_000_000, order=10, th
     return out
 
 
+def run_second_kind(dtn, g, centers, radius, hb, opts_kw):
+    """The unit-ball workload solved with the second-kind local BIE (Eq. bw55-bw59,
+    cap patches: (1/2 I - D) q = b, mixed precision): device time of the
+    solve call (walks, assembly, solve) with CUDA events, best of 2 after one
+    warm-up."""
+    import torch
+    stream = torch.cuda.current_stream()
+    res = dtn.alloc_result(hb)
+    opts = dtn.solve_opts(bie_kind=1, **opts_kw)
+    best = None
+    for k in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dtn.solve_patches(g, centers, radius, hb, opts, result=res)
+        e1.record(stream)
+        e1.synchronize()
+        if k:
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+    n = int(centers.shape[0])
+    return {"patches": n, "ms": best, "patches_per_s": n / (best / 1e3),
+            "status_ok": bool((res["patch_status"] == 0).all().item()),
+            "setup": "unit-ball workload, second-kind BIE on the caps, mixed precision"}
+
+
 def run_ours(args):
     import torch
     import paper_1210_1491_gb300 as dtn
@@ -528,6 +553,8 @@ def run_ours(args):
         line["serving"] = run_serving(dtn)
         line["single_point"] = run_single_point(dtn)
         line["potential_fmm"] = run_potential_fmm(dtn)
+        line["second_kind"] = run_second_kind(dtn, g, centers, radius, hb,
+                                              dict(prec=prec, epsilon=wl.epsilon, seed=wl.seed))
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(wl)
     if rank == 0:
