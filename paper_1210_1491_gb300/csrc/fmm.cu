@@ -81,6 +81,11 @@ __device__ inline void cmac(float2 &a, float2 b, float2 c) {
     a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
     a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
 }
+// a += s c, s real
+__device__ inline void rmac(float2 &a, float s, float2 c) {
+    a.x = fmaf(s, c.x, a.x);
+    a.y = fmaf(s, c.y, a.y);
+}
 // a += conj(b) c
 __device__ inline void cmac_cb(float2 &a, float2 b, float2 c) {
     a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
@@ -537,24 +542,27 @@ __global__ void fmm_csr_kernel(int64_t ncell, const uint64_t *__restrict__ keys,
 
 // ------------------------------------------------------------------ downward pass
 
-// M2L: one warp per target cell, over its sorted source list.  For each source
-// the warp writes the singular harmonics at (z - c)/rho to degree 2P and the
-// source's scaled multipole coefficients as full tables (orders -N..N at index
-// N^2 + N + l, the negative orders from the symmetry), so that every output is
-// the same branch-free sum
-//   L_n^m += (-1)^{n+m} (h_T/rho)^n / rho sum_j sum_{k=-j}^{j} S_{j+n}^{k-m} (h_S/rho)^j M_j^k,
-// rho = max(h_T, h_S), contiguous in k in both tables.  A lane owns three
-// outputs (n, m0), (n, m0+1), (n, m0+2): walking k upwards, the S value loaded
-// for (n, m0) at k serves (n, m0+1) at k+1 and (n, m0+2) at k+2, so each step
-// loads one S value and one (broadcast) M value for three complex products.
-// Outputs past m = n are computed on in-bounds padding and dropped.  Writes L
-// for every cell (zero for an empty list).
+// M2L: one warp per target cell, over its sorted source list.  With phi the
+// azimuth of v = (z - c)/rho, S_N^l(v) = e^{i l phi} s_N^l where s are the
+// singular harmonics at (|v_xy|, 0, v_z), which are real; so
+//   L_n^m += (-1)^{n+m} (h_T/rho)^n / rho e^{-i m phi}
+//            sum_j sum_{k=-j}^{j} s_{j+n}^{k-m} (h_S/rho)^j M_j^k e^{i k phi},
+// rho = max(h_T, h_S): a real table times the turned coefficients (half the
+// multiply-adds of the complex sum).  For each source the warp writes s to
+// degree 2P and the turned, scaled coefficients as full tables (orders -N..N at
+// index N^2 + N + l, the negative orders from the symmetries), contiguous in k.
+// A lane owns three outputs (n, m0), (n, m0+1), (n, m0+2): walking k upwards,
+// the s value loaded for (n, m0) at k serves (n, m0+1) at k+1 and (n, m0+2) at
+// k+2, so each step loads one s value and one (broadcast) M value for three
+// real-by-complex products.  Outputs past m = n are computed on in-bounds
+// padding and dropped.  L is zeroed before the launch; cells without pairs are
+// skipped.
 constexpr int kM2lBlock = 3;
 constexpr int kM2lTasksMax = 2;   // rounds of 32 lanes: sum_n ceil((n+1)/3) <= 64 for P <= 16
 constexpr int kSPad = 2;          // entries before the S table (k - m0 - 2 >= -2 - N)
 
 struct M2lShared {
-    float2 s[kSPad + (2 * kFmmMaxOrder + 1) * (2 * kFmmMaxOrder + 1)];
+    float s[kSPad + (2 * kFmmMaxOrder + 1) * (2 * kFmmMaxOrder + 1)];
     float2 m[(kFmmMaxOrder + 1) * (kFmmMaxOrder + 1)];
 };
 
@@ -588,8 +596,9 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
         if (!tv[r]) tn[r] = tm[r] = 0;
     }
     const bool round2 = __any_sync(0xffffffffu, tv[1]);
-    float2 *S = sh[wid].s + kSPad, *Mf = sh[wid].m;
-    if (lane < kSPad) sh[wid].s[lane] = make_float2(0.0f, 0.0f);
+    float *S = sh[wid].s + kSPad;
+    float2 *Mf = sh[wid].m;
+    if (lane < kSPad) sh[wid].s[lane] = 0.0f;
     const double ihw = 1.0 / half_w0;
     for (;;) {
     unsigned long long qi = 0;
@@ -613,32 +622,36 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
         const float vx = (float)((T.c[0] - Sc.c[0]) * irho), vy = (float)((T.c[1] - Sc.c[1]) * irho),
                     vz = (float)((T.c[2] - Sc.c[2]) * irho);
         const int bt = lt - lr, bs = ls - lr;
+        // azimuth of z - c taken out: S_N^l(v) = e^{i l phi} s_N^l with s the (real)
+        // singular harmonics at (rho_xy, 0, vz); the source's coefficients are
+        // turned by e^{i k phi} and each output by e^{-i m phi}
+        const float rxy = sqrtf(fmaf(vx, vx, vy * vy));
+        const float2 eph = rxy > 0.0f ? make_float2(vx / rxy, vy / rxy) : make_float2(1.0f, 0.0f);
         __syncwarp();
         for (int m = lane; m <= 2 * P; m += 32) {
-            // column m of S, both signs of the order
-            const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+            // column m of s, both signs of the order (s_N^{-m} = (-1)^m s_N^m)
+            const float r2 = fmaf(rxy, rxy, vz * vz);
             const float ir2 = 1.0f / r2;
-            float2 smm = make_float2(rsqrtf(r2), 0.0f);
-            for (int k = 1; k <= m; ++k) smm = cscale(cmul(smm, make_float2(vx, vy)), (float)(2 * k - 1) * ir2);
+            float smm = rsqrtf(r2);
+            for (int k = 1; k <= m; ++k) smm *= (float)(2 * k - 1) * rxy * ir2;
             const float sg = (m & 1) ? -1.0f : 1.0f;
-            float2 a = make_float2(0.0f, 0.0f), b = smm;
+            float a = 0.0f, b = smm;
             for (int n = m; n <= 2 * P; ++n) {
                 if (n > m) {
-                    const float f = (float)((n + m - 1) * (n - m - 1));
-                    const float2 c = make_float2(((2 * n - 1) * vz * b.x - f * a.x) * ir2,
-                                                 ((2 * n - 1) * vz * b.y - f * a.y) * ir2);
+                    const float c = ((2 * n - 1) * vz * b - (float)((n + m - 1) * (n - m - 1)) * a) * ir2;
                     a = b;
                     b = c;
                 }
                 S[n * n + n + m] = b;
-                if (m) S[n * n + n - m] = make_float2(sg * b.x, -sg * b.y);
+                if (m) S[n * n + n - m] = sg * b;
             }
         }
         for (int q = lane; q < nc; q += 32) {
             int n, m;
             tri_nm(q, n, m);
             const float2 v = M[si * nc + q];
-            const float2 w = make_float2(ldexpf(v.x, -n * bs), ldexpf(v.y, -n * bs));
+            float2 w = make_float2(ldexpf(v.x, -n * bs), ldexpf(v.y, -n * bs));
+            for (int k = 0; k < m; ++k) w = cmul(w, eph);
             const float sg = (m & 1) ? -1.0f : 1.0f;
             Mf[n * n + n + m] = w;
             if (m) Mf[n * n + n - m] = make_float2(sg * w.x, -sg * w.y);
@@ -653,40 +666,46 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
             for (int j = 0; j <= P; ++j) {
                 const float2 *mr = Mf + j * j + j;
                 const int N = j + n;
-                const float2 *sr = S + N * N + N - m0;   // S_N^{k - m0} at sr[k]
-                float2 w1 = sr[-j - 1], w2 = sr[-j - 2];
+                const float *sr = S + N * N + N - m0;   // s_N^{k - m0} at sr[k]
+                float w1 = sr[-j - 1], w2 = sr[-j - 2];
                 int k = -j;
                 for (; k + 2 <= j; k += 3) {   // three steps with the window rotated in registers
                     const float2 m0v = mr[k], m1v = mr[k + 1], m2v = mr[k + 2];
-                    const float2 v0 = sr[k], v1 = sr[k + 1], v2 = sr[k + 2];
-                    cmac(p0, v0, m0v);
-                    cmac(p1, w1, m0v);
-                    cmac(p2, w2, m0v);
-                    cmac(p0, v1, m1v);
-                    cmac(p1, v0, m1v);
-                    cmac(p2, w1, m1v);
-                    cmac(p0, v2, m2v);
-                    cmac(p1, v1, m2v);
-                    cmac(p2, v0, m2v);
+                    const float v0 = sr[k], v1 = sr[k + 1], v2 = sr[k + 2];
+                    rmac(p0, v0, m0v);
+                    rmac(p1, w1, m0v);
+                    rmac(p2, w2, m0v);
+                    rmac(p0, v1, m1v);
+                    rmac(p1, v0, m1v);
+                    rmac(p2, w1, m1v);
+                    rmac(p0, v2, m2v);
+                    rmac(p1, v1, m2v);
+                    rmac(p2, v0, m2v);
                     w2 = v1;
                     w1 = v2;
                 }
                 for (; k <= j; ++k) {
                     const float2 mv = mr[k];
-                    const float2 v = sr[k];
-                    cmac(p0, v, mv);
-                    cmac(p1, w1, mv);
-                    cmac(p2, w2, mv);
+                    const float v = sr[k];
+                    rmac(p0, v, mv);
+                    rmac(p1, w1, mv);
+                    rmac(p2, w2, mv);
                     w2 = w1;
                     w1 = v;
                 }
             }
             const float2 pr[kM2lBlock] = {p0, p1, p2};
+            // e^{-i m phi} for m = m0, m0 + 1, m0 + 2
+            float2 em = make_float2(1.0f, 0.0f);
+            const float2 ec = cconj(eph);
+            for (int k = 0; k < m0; ++k) em = cmul(em, ec);
 #pragma unroll
             for (int d = 0; d < kM2lBlock; ++d) {
                 const int m = m0 + d;
                 const float f = ldexpf(((n + m) & 1) ? -fr : fr, -n * bt);
-                acc[r][d] = make_float2(fmaf(f, pr[d].x, acc[r][d].x), fmaf(f, pr[d].y, acc[r][d].y));
+                const float2 t = cmul(pr[d], em);
+                acc[r][d] = make_float2(fmaf(f, t.x, acc[r][d].x), fmaf(f, t.y, acc[r][d].y));
+                em = cmul(em, ec);
             }
         }
     }

@@ -223,3 +223,34 @@ def test_fmm_full_size_sampled():
     ref = O.potential(y, nrm, ar, q, g, t[sample])
     b0, b1 = _abs_sums(y, ar, q, g, t[sample])
     assert np.all(np.abs(u[sample] - ref) <= _tolerance(b0, b1, 10, 0.5))
+
+
+@pytest.mark.parametrize("order,theta,ls,lt,ml", [
+    (1, 0.3, 16, 16, 20),      # lowest order: the bound is loose, the traversal the same
+    (16, 0.7, 64, 64, 20),     # highest order
+    (6, 0.05, 8, 8, 20),       # theta near 0: almost every pair is a leaf pair
+    (12, 0.95, 32, 32, 20),    # theta near 1: the slowest convergence the acceptance allows
+    (8, 0.5, 1, 1, 20),        # one point per leaf (deep trees)
+    (8, 0.5, 4096, 4096, 20),  # one leaf each: a single leaf pair
+    (8, 0.5, 8, 8, 1),         # max_level 1: leaves of any size at level 1
+])
+def test_fmm_option_extremes(order, theta, ls, lt, ml):
+    # two clusters of panels (one dense) and targets around and between them
+    y1, n1, a1 = W.sphere_panels(3000, radius=0.2)
+    y2, n2, a2 = W.sphere_panels(800, radius=1.0)
+    y = np.concatenate([y1 + np.array([0.6, 0.0, 0.0]), y2])
+    nrm = np.concatenate([n1, n2])
+    ar = np.concatenate([a1, a2])
+    q, g = W.panel_values(len(y), seed=21)
+    t = np.concatenate([W.targets_in_ball(700, 1.0, 0.05, seed=22),
+                        W.targets_outside_ball(300, 1.0, 0.1, seed=23)])
+    ref = O.potential(y, nrm, ar, q, g, t)
+    b0, b1 = _abs_sums(y, ar, q, g, t)
+    o = dtn.fmm_opts(order=order, theta=theta, leaf_sources=ls, leaf_targets=lt, max_level=ml)
+    u, st = dtn.eval_potential_fmm(_geom(), y, nrm, ar, q, g, t, opts=o, want_stats=True)
+    u = _np(u)
+    assert np.all(np.isfinite(u))
+    assert np.all(np.abs(u - ref) <= _tolerance(b0, b1, order, theta))
+    assert st["source_levels"] <= ml + 1 and st["target_levels"] <= ml + 1
+    if ls == 4096:
+        assert st["m2l_pairs"] == 0 and st["p2p_pairs"] == 1
