@@ -198,8 +198,6 @@ __global__ void __launch_bounds__(kSkThreads) second_kind_cap_rhs_kernel(SkDev P
     const double cmax = cos(f.umax);
     const int n2 = P.ng2;
     const double *gx = P.glx + n2 * (n2 - 1) / 2, *gw = P.glw + n2 * (n2 - 1) / 2;
-    const double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
-    (void)xx;
     double ss = 0.0;
     for (int k = threadIdx.x; k < n2 * n2; k += blockDim.x) {
         const int j = k / n2, l = k - j * n2;
