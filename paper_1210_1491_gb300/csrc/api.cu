@@ -667,9 +667,12 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         if ((e = W.gmat.reserve((size_t)L.gmat_total * 8)) != cudaSuccess ||
             (e = W.gfac.reserve(lu_shared_scratch_bytes(L))) != cudaSuccess ||
             (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess ||
-            (e = W.gw.reserve((size_t)L.gw_total * sizeof(float))) != cudaSuccess ||
-            (e = W.vec.reserve((size_t)L.vec_total * sizeof(float))) != cudaSuccess)
+            (e = W.gw.reserve((size_t)L.gw_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)))) !=
+                cudaSuccess ||
+            (e = W.vec.reserve((size_t)L.vec_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)))) !=
+                cudaSuccess)
             return to_status(e);
+
     } else if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) {
         return to_status(e);
     }
@@ -808,15 +811,17 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     const bool shared = (o->prec == DTN_PREC_MIXED);
     if (o->bie_kind == 1) {
         // second kind on cap patches: (1/2 I - D) q = b.  Mixed precision: D per
-        // shape group (FP64 rules), every row's right side by the geodesic polar
-        // rule about its collocation point, FP32 group factors with FP64
+        // shape group (FP64 rules), the right sides by the geodesic polar rule
+        // about each collocation point folded into FP64 weights per weight group
+        // and one FP64 product per patch, FP32 group factors with FP64
         // refinement; FP64: matrix and right side per patch with the panel rules.
         if (shared) {
             e = launch_assemble(g, L, D, o->prec, 1, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                 W.gmat.as<double>(), rhs, s, 1);
             if (e == cudaSuccess)
-                e = launch_second_kind_cap_rhs(g, L, D, pl, pp, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                                               o->ring_order > 0 ? o->ring_order : 32, rhs, s);
+                e = launch_second_kind_cap_rhs_shared(g, L, D, pl, pp, W.gamma_loc.as<double>(), gw,
+                                                      r->u_gamma_mean, o->ring_order > 0 ? o->ring_order : 32,
+                                                      W.gw.as<double>(), W.vec.as<double>(), rhs, s);
             if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, W.gmat.as<double>(), r->matrix, s);
         } else {
             e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,

@@ -227,10 +227,10 @@ cudaError_t launch_second_kind(const dtn_geometry *g, const BatchLayout &L, cons
                                const double *panel_loc, const double *panel_g, const double *gamma_loc,
                                const double *gamma_w, const double *U, int ng2, double *q, double *b,
                                int32_t *iters, double *resid, int32_t *status, cudaStream_t s);
-cudaError_t launch_second_kind_cap_rhs(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
-                                       const double *panel_loc, const double *panel_prm, const double *panel_g,
-                                       const double *gamma_loc, const double *gamma_w, const double *U, int ng,
-                                       double *b, cudaStream_t s);
+cudaError_t launch_second_kind_cap_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
+                                              const double *panel_loc, const double *panel_prm,
+                                              const double *gamma_loc, const double *gamma_w, const double *U,
+                                              int ng, double *W, double *vec, double *b, cudaStream_t s);
 
 // copies each patch's group matrix into its own block (mat_off) for checking
 cudaError_t launch_expand_matrices(const BatchLayout &L, const DevLayout &D, const double *gA,

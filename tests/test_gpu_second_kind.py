@@ -81,9 +81,11 @@ def test_cap_system_matches_oracle_with_exact_values(case):
     against the oracle (adaptive rules at rtol 1e-10, 40-point Duffy rule on the
     self panel): each panel integral agrees to ~1e-10 of the row's scale, so q
     to n_p x 1.5e-10 of max|q| (n_p panels summed per row).  Mixed precision
-    takes the right side by a geodesic polar rule of order 32 about x_i, which
-    converges geometrically (order 20: 2e-6, 32: 4e-8, 48: 4e-10 of max|b| on a
-    unit-ball cap): 1e-6 of max|q|.  Closed forms:
+    takes the right side by a geodesic polar rule of order 32 about x_i (order
+    20: 2e-6, 32: 4e-8, 48: 4e-10 of max|b| on a unit-ball cap) applied to the
+    data interpolated on each panel from its 8 x 8 samples (degree 7 per
+    direction; on these coarse 4 x 8 panels a few 1e-7 of max|q|): 1e-6 of
+    max|q|.  Closed forms:
     harmonic data on the unit ball (inner rows 1e-3 of max|q|), unit potential
     on the R = 3 sphere seen from outside (q = 1/R, 5e-3 inside r < 0.7a)."""
     if case == "ball":
@@ -117,7 +119,8 @@ def test_cap_system_matches_oracle_with_exact_values(case):
 
 def test_cap_second_kind_with_walks_against_the_oracle_and_the_first_kind():
     """200 unit-ball caps of the bench shape with 4096 walks per node: the GPU's
-    second-kind solve (mixed precision: polar right sides, 1e-6 as above)
+    second-kind solve (mixed precision: polar rule on the interpolated data,
+    1e-6 as above)
     against the oracle's on the GPU's own node values (sampled patches), and the
     Neumann error against the closed form
     over whole patches no larger than the first kind's (the better-conditioned
