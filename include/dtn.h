@@ -128,8 +128,10 @@ typedef struct {
                                    over panel j, the finite part of b regularised by the harmonic
                                    l = g(x) + grad_S g(x).(y - x).  DTN_PREC_FP64: D and b by the
                                    panel rules per patch.  DTN_PREC_MIXED: D per patch shape, b by
-                                   a geodesic polar rule about each collocation point, FP32
-                                   factors with FP64 refinement */
+                                   a geodesic polar rule about each collocation point over the
+                                   data interpolated on the panels (FP64 weights per patch shape,
+                                   one FP64 product per patch), FP32 factors with FP64
+                                   refinement */
     int32_t ring_order;         /* second kind: Gauss order of the polar rules on S
                                    (0 = 20 on disks, 32 on caps) */
 } dtn_solve_opts;
