@@ -40,10 +40,10 @@ OPS_PER_WALK = 280
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
 # per-node sums): ncu capture of the 64-patch case, 1,638,400 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
-DRAM_BYTES_PER_NODE = 1638400 / 32768
+DRAM_BYTES_PER_NODE = 1659136 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
-NCU_ISSUE_ACTIVE = 0.761
-NCU_LANES_PER_INST = 28.96
+NCU_ISSUE_ACTIVE = 0.734        # ncu, same capture: issue slots busy
+NCU_LANES_PER_INST = 28.94      # ncu, same capture: active lanes per warp instruction
 SM_COUNT = 152
 LANES_PER_SM = 128
 
