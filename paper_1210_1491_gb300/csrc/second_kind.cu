@@ -464,8 +464,19 @@ cudaError_t launch_second_kind_cap_rhs_shared(const dtn_geometry *g, const Batch
     P.b = b;
     const int nq = ng * ng;
     const size_t smem = (size_t)nq * 8 + (size_t)((nq + 1) / 2) * 8 + 2 * (size_t)nq * 8;
-    cudaError_t e = cudaFuncSetAttribute(sk_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the largest ring order's table, set once (outside any stream capture that follows)
+    static bool smem_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!smem_set[dev]) {
+        const size_t smax = (size_t)kMaxGauss * kMaxGauss * 8 * 4;
+        if ((e = cudaFuncSetAttribute(sk_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax)) !=
+            cudaSuccess)
+            return e;
+        smem_set[dev] = true;
+    }
     sk_weights_kernel<<<(unsigned)L.wrows_total, kSkWThreads, smem, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sk_samples_kernel<<<(unsigned)((L.vec_total + 255) / 256), 256, 0, s>>>(P, L.vec_total);

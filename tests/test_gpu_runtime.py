@@ -55,6 +55,25 @@ def test_graph_replay_matches_direct_and_stage_times():
         assert all(m >= 0 for m in ms) and ms[0] > 0
 
 
+def test_graph_replay_second_kind_caps():
+    """The second-kind path on caps (group weights, samples, product, group LU)
+    captured and replayed: bit-equal to the direct call."""
+    wl, b, g, hb = _case()
+    o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3, bie_kind=1)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+    torch.cuda.synchronize()
+    og = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3, bie_kind=1, graph_capture=True)
+    res = dtn.alloc_result(hb)
+    c = torch.from_numpy(b.centers).cuda()
+    rad = torch.from_numpy(b.radius).cuda()
+    for _ in range(3):   # capture, then two replays
+        res["neumann"].zero_()
+        dtn.solve_patches(g, c, rad, hb, og, result=res)
+        torch.cuda.synchronize()
+        assert np.array_equal(res["neumann"].cpu().numpy(), r0["neumann"].cpu().numpy())
+    assert np.all(res["patch_status"].cpu().numpy() == 0)
+
+
 def test_autotuner_picks_and_results_unchanged():
     wl, b, g, hb = _case()
     o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3)
