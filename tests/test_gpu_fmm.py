@@ -254,3 +254,22 @@ def test_fmm_option_extremes(order, theta, ls, lt, ml):
     assert st["source_levels"] <= ml + 1 and st["target_levels"] <= ml + 1
     if ls == 4096:
         assert st["m2l_pairs"] == 0 and st["p2p_pairs"] == 1
+
+
+def test_fmm_wires_full_size_sampled():
+    # 2.1e6 square panels on the faces of the 200-wire layout (h = 0.05) and 1e6
+    # targets in the outer box: deep, uneven source trees (9 levels); 600
+    # sampled targets against the oracle within the bound
+    boxes = W.wire_layout(200)
+    y, nrm, ar = W.box_surface_panels(boxes, 0.05)
+    q, g = W.panel_values(len(y), seed=5)
+    t = W.points_in_box(1_000_000, (0, 0, 0), (64, 64, 16), 0.0, seed=6)
+    dev = [torch.tensor(a, device="cuda") for a in (y, nrm, ar, q, g, t)]
+    o = dtn.fmm_opts(order=10, theta=0.6, leaf_sources=128, leaf_targets=64)
+    u, st = dtn.eval_potential_fmm(_geom(), *dev, opts=o, want_stats=True)
+    u = _np(u)
+    assert st["source_levels"] >= 8 and st["m2l_pairs"] > 10 ** 6
+    sample = np.random.default_rng(2).choice(len(t), 600, replace=False)
+    ref = O.potential(y, nrm, ar, q, g, t[sample])
+    b0, b1 = _abs_sums(y, ar, q, g, t[sample])
+    assert np.all(np.abs(u[sample] - ref) <= _tolerance(b0, b1, 10, 0.6))
