@@ -581,10 +581,15 @@ __device__ inline bool m2l_task(int t, int P, int &n, int &m0) {
 
 // Persistent warps: each takes the next target cell from *queue (L is zeroed
 // before the launch, so cells without M2L pairs are skipped).
+// PT > 0: the order is the compile-time PT (the j and k loops unroll fully;
+// instantiated for P = 8 and 10, where one round of lanes holds all outputs);
+// PT = 0: the runtime order P.
+template <int PT>
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
     const uint64_t *__restrict__ list, double half_w0, int P, const float2 *__restrict__ M, float2 *__restrict__ L,
     unsigned long long *__restrict__ queue) {
+    if (PT > 0) P = PT;
     __shared__ M2lShared sh[kCellWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nc = tri(P + 1, 0);
@@ -663,6 +668,25 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
             if (r == 1 && !round2) break;
             const int n = tn[r], m0 = tm[r];
             float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0;
+            if constexpr (PT > 0) {
+#pragma unroll
+                for (int j = 0; j <= PT; ++j) {
+                    const float2 *mr = Mf + j * j + j;
+                    const int N = j + n;
+                    const float *sr = S + N * N + N - m0;
+                    float w1 = sr[-j - 1], w2 = sr[-j - 2];
+#pragma unroll
+                    for (int k = -j; k <= j; ++k) {
+                        const float2 mv = mr[k];
+                        const float v = sr[k];
+                        rmac(p0, v, mv);
+                        rmac(p1, w1, mv);
+                        rmac(p2, w2, mv);
+                        w2 = w1;
+                        w1 = v;
+                    }
+                }
+            } else
             for (int j = 0; j <= P; ++j) {
                 const float2 *mr = Mf + j * j + j;
                 const int N = j + n;
@@ -1184,14 +1208,18 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
     FMM_TRY(cudaMemsetAsync(w.L.p, 0, ntc * nc * sizeof(float2), s));
     if (w.grid_m2l == 0) {
         int per_sm = 0;
-        FMM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_m2l_kernel, 32 * kCellWarps, 0));
+        FMM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_m2l_kernel<0>, 32 * kCellWarps, 0));
         w.grid_m2l = std::max(1, per_sm) * g->num_sms;
         FMM_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fmm_leaf_kernel, 32 * kCellWarps, 0));
         w.grid_leaf = std::max(1, per_sm) * g->num_sms;
     }
-    fmm_m2l_kernel<<<(int)std::min<int64_t>(w.grid_m2l, nblk(ntc, kCellWarps)), 32 * kCellWarps, 0, s>>>(
-        w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.m2l_off.as<int64_t>(), w.m2l_s.as<uint64_t>(), half_w0, P,
-        w.M.as<float2>(), w.L.as<float2>(), queue);
+    {
+        const int grid = (int)std::min<int64_t>(w.grid_m2l, nblk(ntc, kCellWarps));
+        auto kern = P == 8 ? fmm_m2l_kernel<8> : P == 10 ? fmm_m2l_kernel<10> : fmm_m2l_kernel<0>;
+        kern<<<grid, 32 * kCellWarps, 0, s>>>(w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.m2l_off.as<int64_t>(),
+                                              w.m2l_s.as<uint64_t>(), half_w0, P, w.M.as<float2>(),
+                                              w.L.as<float2>(), queue);
+    }
     FMM_TRY(cudaGetLastError());
     FMM_TRY(w.tparent.reserve(ntc * 4));
     fmm_parent_kernel<<<nblk(ntc, 256), 256, 0, s>>>(w.tcell.as<FCell>(), ntc, w.tparent.as<int32_t>());
