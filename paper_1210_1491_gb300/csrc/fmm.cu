@@ -801,7 +801,7 @@ struct LeafShared {
     float4 a[kP2pChunk], b[kP2pChunk];
     int pre[33], start[32];
     float dc[32][3];
-    float far[32];
+    float far[64];
 };
 
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
@@ -825,12 +825,12 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
     __syncwarp();
     const double ihd = ldexp(1.0 / half_w0, T.level);
     const int64_t e0 = off[ti], e1 = off[ti + 1];
-    for (int tb = T.start; tb < T.start + T.count; tb += 32) {
-        const int nt = min(32, T.start + T.count - tb);
+    for (int tb = T.start; tb < T.start + T.count; tb += 64) {
+        const int nt = min(64, T.start + T.count - tb);
         __syncwarp();
-        // L2P, a lane per target
-        if (lane < nt) {
-            const int32_t id = tval[tb + lane];
+        // L2P, a lane per target (two rounds of lanes for more than 32 targets)
+        for (int tt = lane; tt < nt; tt += 32) {
+            const int32_t id = tval[tb + tt];
             const float x = (float)((targets[3 * id] - T.c[0]) * ihd), y = (float)((targets[3 * id + 1] - T.c[1]) * ihd),
                         z = (float)((targets[3 * id + 2] - T.c[2]) * ihd);
             const float r2 = fmaf(x, x, fmaf(y, y, z * z));
@@ -851,17 +851,24 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
                 }
                 far = fmaf(m ? 2.0f : 1.0f, part, far);
             }
-            S.far[lane] = far;
+            S.far[tt] = far;
         }
-        // near field: lane = (target tt, slice) with lpt lanes per target
+        // near field: more than 32 targets, two per lane (targets lane and
+        // lane + 32, one staged source serving both); else lanes (target tt,
+        // slice) with lpt lanes per target
+        const bool two = nt > 32;
         int lpt = 1;
-        while (lpt * 2 * nt <= 32) lpt *= 2;
-        const int tt = lane / lpt, slice = lane % lpt;
-        const bool tvalid = tt < nt;
+        if (!two)
+            while (lpt * 2 * nt <= 32) lpt *= 2;
+        const int tt = two ? lane : lane / lpt, slice = two ? 0 : lane % lpt;
+        const bool tvalid = tt < nt, tvalid1 = two && lane + 32 < nt;
         const int32_t id = tval[tb + (tvalid ? tt : 0)];
+        const int32_t id1 = tval[tb + (tvalid1 ? lane + 32 : 0)];
         const float ox = (float)(targets[3 * id] - T.c[0]), oy = (float)(targets[3 * id + 1] - T.c[1]),
                     oz = (float)(targets[3 * id + 2] - T.c[2]);
-        double acc = 0.0;
+        const float qx = (float)(targets[3 * id1] - T.c[0]), qy = (float)(targets[3 * id1 + 1] - T.c[1]),
+                    qz = (float)(targets[3 * id1 + 2] - T.c[2]);
+        double acc = 0.0, acc1 = 0.0;
         for (int64_t g0 = e0; g0 < e1; g0 += 32) {
             const int ng = (int)min((int64_t)32, e1 - g0);
             int cntv = 0;
@@ -900,31 +907,48 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_leaf_kernel(
                 }
                 __syncwarp();
                 float part0 = 0.0f, part1 = 0.0f;
-                int k = slice;
-                for (; k + lpt < cn; k += 2 * lpt) {
-                    const float4 pa = S.a[k], pb = S.b[k], qa = S.a[k + lpt], qb = S.b[k + lpt];
-                    const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
-                    const float ex2 = ox - qa.x, ey2 = oy - qa.y, ez2 = oz - qa.z;
-                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    const float rj = rsqrtf(fmaf(ex2, ex2, fmaf(ey2, ey2, ez2 * ez2)));
-                    const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
-                    const float en = fmaf(ex2, qb.x, fmaf(ey2, qb.y, ez2 * qb.z));
-                    part0 += ri * fmaf(dn, ri * ri, pa.w);
-                    part1 += rj * fmaf(en, rj * rj, qa.w);
+                if (two) {
+                    for (int k = 0; k < cn; ++k) {
+                        const float4 pa = S.a[k], pb = S.b[k];
+                        const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
+                        const float ex2 = qx - pa.x, ey2 = qy - pa.y, ez2 = qz - pa.z;
+                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                        const float rj = rsqrtf(fmaf(ex2, ex2, fmaf(ey2, ey2, ez2 * ez2)));
+                        const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+                        const float en = fmaf(ex2, pb.x, fmaf(ey2, pb.y, ez2 * pb.z));
+                        part0 += ri * fmaf(dn, ri * ri, pa.w);
+                        part1 += rj * fmaf(en, rj * rj, pa.w);
+                    }
+                    acc += (double)part0;
+                    acc1 += (double)part1;
+                } else {
+                    int k = slice;
+                    for (; k + lpt < cn; k += 2 * lpt) {
+                        const float4 pa = S.a[k], pb = S.b[k], qa = S.a[k + lpt], qb = S.b[k + lpt];
+                        const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
+                        const float ex2 = ox - qa.x, ey2 = oy - qa.y, ez2 = oz - qa.z;
+                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                        const float rj = rsqrtf(fmaf(ex2, ex2, fmaf(ey2, ey2, ez2 * ez2)));
+                        const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+                        const float en = fmaf(ex2, qb.x, fmaf(ey2, qb.y, ez2 * qb.z));
+                        part0 += ri * fmaf(dn, ri * ri, pa.w);
+                        part1 += rj * fmaf(en, rj * rj, qa.w);
+                    }
+                    if (k < cn) {
+                        const float4 pa = S.a[k], pb = S.b[k];
+                        const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
+                        const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                        const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
+                        part0 += ri * fmaf(dn, ri * ri, pa.w);
+                    }
+                    acc += (double)part0 + (double)part1;
                 }
-                if (k < cn) {
-                    const float4 pa = S.a[k], pb = S.b[k];
-                    const float dx = ox - pa.x, dy = oy - pa.y, dz = oz - pa.z;
-                    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                    const float dn = fmaf(dx, pb.x, fmaf(dy, pb.y, dz * pb.z));
-                    part0 += ri * fmaf(dn, ri * ri, pa.w);
-                }
-                acc += (double)part0 + (double)part1;
             }
         }
         for (int o = 1; o < lpt; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         __syncwarp();
         if (tvalid && slice == 0) out[id] = acc + (double)S.far[tt];
+        if (tvalid1) out[id1] = acc1 + (double)S.far[lane + 32];
     }
     }
 }
