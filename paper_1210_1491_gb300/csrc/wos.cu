@@ -366,9 +366,9 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                         x = go ? nx : x;
                         y = go ? ny : y;
                         z = go ? nz : z;
-                        step = active ? st1 : step;
-                        acc.st += (absorbed || cut) ? (unsigned long long)st1 : 0ull;
-                        acc.cap += cut ? 1u : 0u;
+                        step = st1;   // an idle lane's count is reset when it is refilled
+                        if (absorbed || cut) acc.st += st1;
+                        if (cut) acc.cap += 1u;
                         pending = pending || absorbed;
                         active = go;
                     }
