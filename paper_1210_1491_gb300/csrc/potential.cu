@@ -9,6 +9,7 @@
 // FP32 offsets from an FP64 tile origin (so differences of nearby points keep
 // their digits whatever the coordinates' magnitude), evaluates pair terms in
 // FP32, sums a tile in FP32 and adds tile sums in FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "dtn_internal.h"
@@ -34,9 +35,12 @@ __global__ void __launch_bounds__(kPotThreads) potential_mixed_kernel(
     const double tx = valid ? t[3 * it] : 0.0, ty = valid ? t[3 * it + 1] : 0.0, tz = valid ? t[3 * it + 2] : 0.0;
     double acc = 0.0;
     const float inv4pi = (float)(0.25 / kPi);
+    // split y of gridDim.y takes tiles [y0, y1) of the panel list
     const int64_t np = n_index ? *n_index : np_host;
-    for (int64_t base = 0; base < np; base += kTile) {
-        const int cnt = (int)min((int64_t)kTile, np - base);
+    const int64_t ntiles = (np + kTile - 1) / kTile, per = (ntiles + gridDim.y - 1) / gridDim.y;
+    const int64_t pend = min(np, (blockIdx.y + 1) * per * kTile);
+    for (int64_t base = blockIdx.y * per * kTile; base < pend; base += kTile) {
+        const int cnt = (int)min((int64_t)kTile, pend - base);
         __syncthreads();
         if (threadIdx.x == 0) {
             const int64_t p0 = index ? index[base] : base;
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(kPotThreads) potential_mixed_kernel(
         }
         acc += (double)s;
     }
-    if (valid) out[it] = acc;
+    if (valid) out[blockIdx.y * nt + it] = acc;
 }
 
 __global__ void __launch_bounds__(kPotThreads) potential_fp64_kernel(
@@ -79,8 +83,10 @@ __global__ void __launch_bounds__(kPotThreads) potential_fp64_kernel(
     double acc = 0.0;
     const double inv4pi = 0.25 / kPi;
     const int64_t np = n_index ? *n_index : np_host;
-    for (int64_t base = 0; base < np; base += kTile) {
-        const int cnt = (int)min((int64_t)kTile, np - base);
+    const int64_t ntiles = (np + kTile - 1) / kTile, per = (ntiles + gridDim.y - 1) / gridDim.y;
+    const int64_t pend = min(np, (blockIdx.y + 1) * per * kTile);
+    for (int64_t base = blockIdx.y * per * kTile; base < pend; base += kTile) {
+        const int cnt = (int)min((int64_t)kTile, pend - base);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int64_t pp = index ? index[base + k] : base + k;
@@ -98,7 +104,16 @@ __global__ void __launch_bounds__(kPotThreads) potential_fp64_kernel(
             acc += saq[k] / r - sag[k] * dn / (r2 * r);
         }
     }
-    if (valid) out[it] = acc;
+    if (valid) out[blockIdx.y * nt + it] = acc;
+}
+
+// out[i] = sum over the splits of part[y nt + i], in split order
+__global__ void potential_reduce_kernel(int64_t nt, int ns, const double *__restrict__ part, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    double s = 0.0;
+    for (int y = 0; y < ns; ++y) s += part[y * nt + i];
+    out[i] = s;
 }
 
 // ---------------------------------------------------------------- panel gather
@@ -221,14 +236,29 @@ __global__ void scatter_kernel(int64_t n, const uint8_t *__restrict__ keep, cons
 cudaError_t launch_potential(int64_t np, const int64_t *index, const int64_t *n_index, const double *xyz,
                              const double *nrm, const double *area, const double *q, const double *g, int64_t nt,
                              const double *t, double *out, int prec, int num_sms, cudaStream_t s) {
-    (void)num_sms;
     if (nt == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((nt + kPotThreads - 1) / kPotThreads);
+    // split the panel list across CTAs when the targets alone fill less than the
+    // GPU (8 resident CTAs of 256 threads per SM); partial sums reduced in split order
+    const int64_t want = (int64_t)num_sms * 8;
+    int ns = (int)std::min<int64_t>(8, std::max<int64_t>(1, want / std::max<unsigned>(blocks, 1u)));
+    ns = (int)std::min<int64_t>(ns, std::max<int64_t>(1, (np + kTile - 1) / kTile));
+    double *part = out;
+    cudaError_t e;
+    if (ns > 1 && (e = cudaMallocAsync((void **)&part, (size_t)ns * nt * sizeof(double), s)) != cudaSuccess)
+        return e;
+    const dim3 grid(blocks, (unsigned)ns);
     if (prec == DTN_PREC_MIXED)
-        potential_mixed_kernel<<<blocks, kPotThreads, 0, s>>>(np, index, n_index, xyz, nrm, area, q, g, nt, t, out);
+        potential_mixed_kernel<<<grid, kPotThreads, 0, s>>>(np, index, n_index, xyz, nrm, area, q, g, nt, t, part);
     else
-        potential_fp64_kernel<<<blocks, kPotThreads, 0, s>>>(np, index, n_index, xyz, nrm, area, q, g, nt, t, out);
-    return cudaGetLastError();
+        potential_fp64_kernel<<<grid, kPotThreads, 0, s>>>(np, index, n_index, xyz, nrm, area, q, g, nt, t, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ns > 1) {
+        potential_reduce_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(nt, ns, part, out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaFreeAsync(part, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_gather(int64_t np, const double *x, const int64_t *owner, int64_t nc, const double *cent,
