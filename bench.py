@@ -38,11 +38,11 @@ N_TARGETS = 100_000
 OPS_PER_STEP = 55
 OPS_PER_WALK = 280
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
-# per-node sums): ncu capture of the 64-patch case, 1,638,400 bytes for 32,768
+# per-node sums): ncu capture of the 64-patch case, 1,642,752 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
-DRAM_BYTES_PER_NODE = 1659136 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
+DRAM_BYTES_PER_NODE = 1642752 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
-NCU_ISSUE_ACTIVE = 0.734        # ncu, same capture: issue slots busy
+NCU_ISSUE_ACTIVE = 0.736        # ncu, same capture: issue slots busy
 NCU_LANES_PER_INST = 28.94      # ncu, same capture: active lanes per warp instruction
 SM_COUNT = 152
 LANES_PER_SM = 128
@@ -521,7 +521,11 @@ def run_ours(args):
     # setup 3, walks + estimates 2; mixed: group matrices 1, right-side weights 3
     # (far, near, walk term), samples 1, products 1, group factors + solves 2;
     # FP64: matrices and right sides 1, factor + solve 1; gather 4, potential 1
-    kernels_per_step = 3 + 2 + (1 + 3 + 1 + 1 + 2 if prec == dtn.PREC_MIXED else 1 + 1) + 4 + 1
+    # the potential adds a split-order reduction when the targets alone fill fewer than
+    # 8 CTAs of 256 threads per SM (its panel list is then split across CTAs)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pot_reduce = 1 if sms * 8 // ((N_TARGETS + 255) // 256) > 1 else 0
+    kernels_per_step = 3 + 2 + (1 + 3 + 1 + 1 + 2 if prec == dtn.PREC_MIXED else 1 + 1) + 4 + 1 + pot_reduce
     line = {
         "metric": METRIC, "value": value, "unit": "patches/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
