@@ -130,7 +130,8 @@ __device__ __forceinline__ T geo_dist(const DGeom &g, const T *sb, T x, T y, T z
         T r;
         if constexpr (sizeof(T) == 4) {
             // SFU reciprocal square root: |x| to a few FP32 ulps
-            const float r2 = fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f);
+            // the 1e-30 keeps r2 > 0 at the centre (below half an ulp of any other r2)
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-30f)));
             r = r2 * rsqrtf(r2);
         } else {
             r = sqrt(dx * dx + dy * dy + dz * dz);

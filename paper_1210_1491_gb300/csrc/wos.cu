@@ -50,6 +50,7 @@ struct WosDev {
     unsigned int *cap;
     int lgM1, lgM2;        // ceil(log2) of the score bound and of its square
     double eps;
+    float eps_f;           // eps rounded to FP32 on the host (FP32 walks)
     uint32_t max_steps;
     uint32_t rk0[10], rk1[10];   // Philox round keys from the seed
 };
@@ -97,12 +98,23 @@ struct LaneAcc {
 };
 
 // Fixed-point score terms round(s 2^F1) and round(s^2 2^F2).  FP32 scores:
-// s 2^F is exact in FP32 (F in the normal range), and s^2 = M^2 2^(2e) with
-// the 24-bit significand M is formed exactly as a 48-bit integer, so both
-// round to the same integers as the FP64 products would (ties to even).
+// s = M 2^e with the 24-bit significand M, so s 2^F and s^2 2^F = M^2 2^(2e+F)
+// are formed exactly from integers (M, or M^2 < 2^48) and shifts, and round to
+// the same integers as the FP64 products would (ties to even).  Integer only:
+// conversions to or from 64-bit types would run on the FP64 pipe.
 __device__ __forceinline__ long long fixed_term(float s, int F) {
-    if (F >= -126 && F <= 127) return __float2ll_rn(s * __int_as_float((F + 127) << 23));
-    return __double2ll_rn((double)s * pow2(F));
+    const uint32_t u = __float_as_uint(s), bits = u & 0x7fffffffu;
+    const int E = (int)(bits >> 23);
+    const uint32_t M = E ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);   // < 2^24
+    const int sh = (E ? E : 1) - 150 + F;
+    // right shift by k with ties to even (k = 25 already leaves less than 1/2), or
+    // left shift by l (M 2^l = |s| 2^F < 2^61 by the choice of F; the cap only
+    // keeps the shift defined)
+    const int k = min(max(-sh, 0), 25), l = min(max(sh, 0), 62);
+    const uint32_t q = M >> k, rem = M & ((1u << k) - 1u), half = (1u << k) >> 1;
+    const uint32_t up = (k > 0 && (rem > half || (rem == half && (q & 1u)))) ? 1u : 0u;
+    const long long v = (long long)((unsigned long long)(q + up) << l);
+    return (u >> 31) ? -v : v;
 }
 __device__ __forceinline__ long long fixed_term(double s, int F) { return __double2ll_rn(s * pow2(F)); }
 
@@ -200,11 +212,11 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 }
 
 // one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
-// z uniform in (-1, 1), azimuth 2 pi u2
-// FP32 walks: uniforms (2f + 1) 2^-22 from 21-bit fields; the azimuth 2 pi u2 is
-// reduced to (-pi, pi] (the same angle mod 2 pi) and taken by the SFU
+// z uniform in (-1, 1), azimuth uniform over a full turn
+// FP32 walks: uniforms (2f + 1) 2^-22 from 21-bit fields; the azimuth is taken as
+// 2 pi (u2 - 1/2), already in (-pi, pi) (u2 - 1/2 is formed exactly), by the SFU
 // sine/cosine; s = sqrt(1 - z^2) by the SFU reciprocal square root
-// (1 - z^2 >= 2^-20 > 0 for these uniforms).
+// (1 - z^2 >= 2^-20 > 0 for these uniforms).  d = 0 leaves x unchanged.
 __device__ __forceinline__ float u01_21(uint32_t f) {
     // 1 + (2f + 1) 2^-22 built in the significand (4f + 2 < 2^23), minus 1 exactly:
     // (2f + 1) 2^-22 with an integer add and an FP32 add, no conversion
@@ -212,13 +224,13 @@ __device__ __forceinline__ float u01_21(uint32_t f) {
 }
 
 __device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
-    const float u1 = u01_21(f1), u2 = u01_21(f2);
+    const float u1 = u01_21(f1);
+    const float h2 = __uint_as_float(0x3F800002u + 4u * f2) - 1.5f;   // u2 - 1/2, exact
     const float zz = fmaf(-2.0f, u1, 1.0f);
     const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
     const float s = t * rsqrtf(t);
-    const float a = 6.2831853071795865f * (u2 > 0.5f ? u2 - 1.0f : u2);
     float sn, cs;
-    __sincosf(a, &sn, &cs);
+    __sincosf(6.2831853071795865f * h2, &sn, &cs);
     x = fmaf(d * s, cs, x);
     y = fmaf(d * s, sn, y);
     z = fmaf(d, zz, z);
@@ -251,7 +263,9 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const T eps = (T)P.eps;
+    // FP32 walks take the host-rounded copy: a double-to-float conversion here
+    // would run on the FP64 pipe, and the compiler may redo it inside the loop
+    const T eps = pick<T>(P.eps, P.eps_f);
     ScoreQueue<T> &Q = s_queue[threadIdx.x >> 5];
     int qhead = 0, qcount = 0;   // warp-uniform
     WarpScore ws;
@@ -320,6 +334,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
             const int take = (int)min((int64_t)nidle, cend - cnext);
             const int rank = __popc(idle & lt_mask);
             if (!active && rank < take) {
+                acc.st += step;   // the length of the lane's previous walk (0 before the first)
                 if (acc.node != cnode) {
                     acc.flush(P);
                     acc.node = cnode;
@@ -350,40 +365,30 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                                            (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
 #pragma unroll
                     for (int h = 0; h < 3; ++h) {
-                        if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
-                            acc.st += step;   // gone to infinity: scores 0
-                            active = false;
-                        }
-                        // branch-free step: every lane evaluates, active lanes that
-                        // go on move (the lanes stay converged through the block)
+                        if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z))
+                            active = false;   // gone to infinity: scores 0
+                        // branch-free step: every lane evaluates; the lanes that do not
+                        // go on jump by 0 (the lanes stay converged through the block)
                         const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                         const uint32_t st1 = step + 1u;
                         const bool absorbed = active && d <= eps;
                         const bool cut = active && !absorbed && st1 >= P.max_steps;
                         const bool go = active && !absorbed && !cut;
-                        T nx = x, ny = y, nz = z;
-                        jump(nx, ny, nz, d, f[2 * h], f[2 * h + 1]);
-                        x = go ? nx : x;
-                        y = go ? ny : y;
-                        z = go ? nz : z;
-                        step = st1;   // an idle lane's count is reset when it is refilled
-                        if (absorbed || cut) acc.st += st1;
+                        jump(x, y, z, go ? d : (T)0, f[2 * h], f[2 * h + 1]);
+                        step = active ? st1 : step;   // a finished walk's length stays until refill
                         if (cut) acc.cap += 1u;
                         pending = pending || absorbed;
                         active = go;
                     }
                 } else if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
-                    acc.st += step;   // gone to infinity: scores 0
-                    active = false;
+                    active = false;   // gone to infinity: scores 0
                 } else {
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     ++step;
                     if (d <= eps) {
-                        acc.st += step;
                         pending = true;
                         active = false;
                     } else if (step >= P.max_steps) {
-                        acc.st += step;
                         acc.cap += 1;
                         active = false;
                     } else {
@@ -395,6 +400,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
             if (__popc(__ballot_sync(FULL, !active)) >= thresh) break;
         }
     }
+    acc.st += step;   // the lane's last walk
     acc.flush(P);
     // the last absorbed walks (fewer than 32)
     {
@@ -490,6 +496,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     P.lgM1 = lgM1;
     P.lgM2 = lgM2;
     P.eps = w.eps;
+    P.eps_f = (float)w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
     philox_round_keys(w.seed, P.rk0, P.rk1);
 
@@ -562,6 +569,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
     P.lgM1 = lgM1;
     P.lgM2 = lgM2;
     P.eps = w.eps;
+    P.eps_f = (float)w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
     philox_round_keys(w.seed, P.rk0, P.rk1);
     const int gk = g->dg.kind;
