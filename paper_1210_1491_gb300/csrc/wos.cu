@@ -30,7 +30,7 @@ namespace dtn {
 
 namespace {
 
-constexpr int kWosThreads = 256;
+constexpr int kWosThreads = 128;
 
 struct WosDev {
     DGeom g;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void jump(double &x, double &y, double &z, double d, 
 }
 
 template <typename T, int GK>
-__global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
+__global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     extern __shared__ float s_boxes[];
     __shared__ ScoreQueue<T> s_queue[kWosThreads / 32];
     __shared__ float2 s_cs[kShPairs];
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
 
     // warp-uniform chunk state
     int64_t cnode = -1;
-    int64_t cnext = 0, cend = 0;
+    uint32_t cnext = 0, cend = 0;   // walk indices of the node (at most 2^32 - 1 walks)
     uint32_t cpid = 0, cpt = 0;
     int cf1 = 0, cf2 = 0;          // fixed-point exponents of the node's sums
     T cx = 0, cy = 0, cz = 0;
@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                 const int64_t cp = P.cpn[grp];
                 const int64_t k = local / cp, j = local - k * cp;
                 cnode = P.node_off[grp] + k;
-                cnext = j * P.chunk;
-                cend = min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
+                cnext = (uint32_t)(j * P.chunk);
+                cend = (uint32_t)min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
                 cpid = P.pid[grp];
                 cf1 = fixed_exponent(P.walks[grp], P.lgM1);
                 cf2 = fixed_exponent(P.walks[grp], P.lgM2);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                 cz = (T)P.y[3 * cnode + 2];
             }
             const int nidle = __popc(idle);
-            const int take = (int)min((int64_t)nidle, cend - cnext);
+            const int take = (int)min((uint32_t)nidle, cend - cnext);
             const int rank = __popc(idle & lt_mask);
             if (!active && rank < take) {
                 acc.st += step;   // the length of the lane's previous walk (0 before the first)
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                     acc.flush(P);
                     acc.node = cnode;
                 }
-                walk = (uint32_t)(cnext + rank);
+                walk = cnext + (uint32_t)rank;
                 step = 0;
                 ppid = cpid;
                 ppt = cpt;
@@ -350,37 +350,38 @@ __global__ void __launch_bounds__(kWosThreads, 3) wos_kernel(WosDev P) {
                 z = cz;
                 active = true;
             }
-            cnext += take;
+            cnext += (uint32_t)take;
             idle = __ballot_sync(FULL, !active);
         }
         if (__ballot_sync(FULL, active) == 0u) break;
         const int thresh = no_more ? 32 : P.refill;
         for (;;) {
-            if (active) {
-                if constexpr (std::is_same<T, float>::value) {
-                    // three jumps from one Philox block
-                    const uint4 w = philox4x32_10_rk(make_uint4(walk, step / 3u, ppt, ppid), P.rk0, P.rk1);
-                    const uint32_t f[6] = {w.x >> 11, w.y >> 11, w.z >> 11, w.w >> 11,
-                                           (w.x & 0x7ffu) | ((w.y & 0x3ffu) << 11),
-                                           (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
+            if constexpr (std::is_same<T, float>::value) {
+                // three jumps from one Philox block; idle lanes run it too and
+                // jump by 0, so the block needs no branch around it
+                const uint4 w = philox4x32_10_rk(make_uint4(walk, step / 3u, ppt, ppid), P.rk0, P.rk1);
+                const uint32_t f[6] = {w.x >> 11, w.y >> 11, w.z >> 11, w.w >> 11,
+                                       (w.x & 0x7ffu) | ((w.y & 0x3ffu) << 11),
+                                       (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
 #pragma unroll
-                    for (int h = 0; h < 3; ++h) {
-                        if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z))
-                            active = false;   // gone to infinity: scores 0
-                        // branch-free step: every lane evaluates; the lanes that do not
-                        // go on jump by 0 (the lanes stay converged through the block)
-                        const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
-                        const uint32_t st1 = step + 1u;
-                        const bool absorbed = active && d <= eps;
-                        const bool cut = active && !absorbed && st1 >= P.max_steps;
-                        const bool go = active && !absorbed && !cut;
-                        jump(x, y, z, go ? d : (T)0, f[2 * h], f[2 * h + 1]);
-                        step = active ? st1 : step;   // a finished walk's length stays until refill
-                        if (cut) acc.cap += 1u;
-                        pending = pending || absorbed;
-                        active = go;
-                    }
-                } else if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
+                for (int h = 0; h < 3; ++h) {
+                    if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z))
+                        active = false;   // gone to infinity: scores 0
+                    // branch-free step: every lane evaluates; the lanes that do not
+                    // go on jump by 0 (the lanes stay converged through the block)
+                    const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
+                    const uint32_t st1 = step + 1u;
+                    const bool absorbed = active && d <= eps;
+                    const bool cut = active && !absorbed && st1 >= P.max_steps;
+                    const bool go = active && !absorbed && !cut;
+                    jump(x, y, z, go ? d : (T)0, f[2 * h], f[2 * h + 1]);
+                    step = active ? st1 : step;   // a finished walk's length stays until refill
+                    if (cut) acc.cap += 1u;
+                    pending = pending || absorbed;
+                    active = go;
+                }
+            } else if (active) {
+                if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                     active = false;   // gone to infinity: scores 0
                 } else {
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);

@@ -24,7 +24,7 @@ def _case():
 def test_results_independent_of_launch_parameters():
     wl, b, g, hb = _case()
     ref = None
-    for chunk, bps, refill in [(256, 0, 8), (64, 1, 2), (512, 2, 16), (100, 3, 5)]:
+    for chunk, bps, refill in [(256, 0, 8), (64, 1, 2), (512, 5, 16), (100, 7, 5)]:
         o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3, walk_chunk=chunk, wos_blocks_per_sm=bps,
                            wos_refill=refill)
         r = dtn.solve_patches(g, b.centers, b.radius, hb, o)
@@ -80,8 +80,8 @@ def test_autotuner_picks_and_results_unchanged():
     r0 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
     torch.cuda.synchronize()
     t = dtn.autotune_walks(g, b.centers, b.radius, hb, o)
-    assert t["walk_chunk"] in (64, 128, 256, 512) and 1 <= t["wos_blocks_per_sm"] <= 4
-    assert t["wos_refill"] in (2, 4, 8, 16) and t["ns_per_walk_step"] > 0
+    assert t["walk_chunk"] in (64, 128, 256, 512) and 4 <= t["wos_blocks_per_sm"] <= 7
+    assert t["wos_refill"] in (4, 8, 12, 16) and t["ns_per_walk_step"] > 0
     r1 = dtn.solve_patches(g, b.centers, b.radius, hb, o)   # now with tuned parameters
     torch.cuda.synchronize()
     assert np.array_equal(r0["neumann"].cpu().numpy(), r1["neumann"].cpu().numpy())
