@@ -47,7 +47,7 @@ struct WosDev {
     int32_t refill;
     unsigned long long *counter;
     unsigned long long *s1, *s2, *st;
-    unsigned int *cap;
+    unsigned int *done;    // per node: walks that ended by absorption or escape
     int lgM1, lgM2;        // ceil(log2) of the score bound and of its square
     double eps;
     float eps_f;           // eps rounded to FP32 on the host (FP32 walks)
@@ -80,20 +80,21 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Per-lane step and cap counts of the node the lane works on, flushed with
-// integer atomics when the lane moves to another node.
+// Per-lane step and escape counts of the node the lane works on, flushed with
+// integer atomics when the lane moves to another node.  Absorbed walks are
+// counted where they are scored; a node's walks cut at max_steps are the rest.
 struct LaneAcc {
     int64_t node = -1;
     unsigned long long st = 0;
-    unsigned int cap = 0;
+    unsigned int esc = 0;
 
     __device__ __forceinline__ void flush(const WosDev &P) {
         if (node >= 0) {
             atomicAdd(P.st + node, st);
-            if (cap) atomicAdd(P.cap + node, cap);
+            if (esc) atomicAdd(P.done + node, esc);
         }
         st = 0;
-        cap = 0;
+        esc = 0;
     }
 };
 
@@ -165,6 +166,7 @@ struct ScoreQueue {
 struct WarpScore {
     int node = -1;
     long long a1 = 0, a2 = 0;
+    unsigned int n = 0;   // walks scored
 };
 
 template <typename T, int GK>
@@ -193,18 +195,22 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
             s1 += __shfl_xor_sync(FULL, s1, o);
             s2 += __shfl_xor_sync(FULL, s2, o);
         }
-        rem &= ~__ballot_sync(FULL, in);
+        const unsigned inm = __ballot_sync(FULL, in);
+        rem &= ~inm;
         if (nd != ws.node) {
             if (ws.node >= 0 && lane == 0) {
                 atomicAdd(P.s1 + ws.node, (unsigned long long)ws.a1);
                 atomicAdd(P.s2 + ws.node, (unsigned long long)ws.a2);
+                atomicAdd(P.done + ws.node, ws.n);
             }
             ws.node = nd;
             ws.a1 = 0;
             ws.a2 = 0;
+            ws.n = 0;
         }
         ws.a1 += s1;
         ws.a2 += s2;
+        ws.n += __popc(inm);
     }
     qhead = (qhead + cnt) & (kQueue - 1);
     qcount -= cnt;
@@ -365,24 +371,26 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                                        (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
-                    if (active && unbounded(GK) && geo_escaped<T>(P.g, x, y, z))
+                    if (unbounded(GK) && active && geo_escaped<T>(P.g, x, y, z)) {
                         active = false;   // gone to infinity: scores 0
+                        acc.esc += 1u;
+                    }
                     // branch-free step: every lane evaluates; the lanes that do not
                     // go on jump by 0 (the lanes stay converged through the block)
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     const uint32_t st1 = step + 1u;
                     const bool absorbed = active && d <= eps;
-                    const bool cut = active && !absorbed && st1 >= P.max_steps;
-                    const bool go = active && !absorbed && !cut;
+                    // a walk neither absorbed nor going on is cut at max_steps
+                    const bool go = active && !absorbed && st1 < P.max_steps;
                     jump(x, y, z, go ? d : (T)0, f[2 * h], f[2 * h + 1]);
                     step = active ? st1 : step;   // a finished walk's length stays until refill
-                    if (cut) acc.cap += 1u;
                     pending = pending || absorbed;
                     active = go;
                 }
             } else if (active) {
                 if (unbounded(GK) && geo_escaped<T>(P.g, x, y, z)) {
                     active = false;   // gone to infinity: scores 0
+                    acc.esc += 1u;
                 } else {
                     const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     ++step;
@@ -390,8 +398,7 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                         pending = true;
                         active = false;
                     } else if (step >= P.max_steps) {
-                        acc.cap += 1;
-                        active = false;
+                        active = false;   // cut
                     } else {
                         const uint4 w = philox4x32_10_rk(make_uint4(walk, step - 1, ppt, ppid), P.rk0, P.rk1);
                         jump(x, y, z, d, w);
@@ -422,6 +429,7 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     if (ws.node >= 0 && lane == 0) {
         atomicAdd(P.s1 + ws.node, (unsigned long long)ws.a1);
         atomicAdd(P.s2 + ws.node, (unsigned long long)ws.a2);
+        atomicAdd(P.done + ws.node, ws.n);
     }
 }
 
@@ -429,13 +437,13 @@ __global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int
                                     const int64_t *__restrict__ walks, const unsigned long long *__restrict__ s1,
                                     const unsigned long long *__restrict__ s2,
                                     const unsigned long long *__restrict__ st,
-                                    const unsigned int *__restrict__ cap, int lgM1, int lgM2,
+                                    const unsigned int *__restrict__ done, int lgM1, int lgM2,
                                     double *__restrict__ mean, double *__restrict__ se,
                                     uint64_t *__restrict__ steps, uint32_t *__restrict__ capped) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_nodes) return;
     const int64_t grp = find_group(node_off, n_groups, i);
-    const double N = (double)(walks[grp] - (int64_t)cap[i]);
+    const double N = (double)done[i];   // walks not cut at max_steps
     const double inv1 = pow2(-fixed_exponent(walks[grp], lgM1));
     const double inv2 = pow2(-fixed_exponent(walks[grp], lgM2));
     const double m1 = (double)(long long)s1[i] * inv1 / N;
@@ -444,7 +452,7 @@ __global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int
     mean[i] = m1;
     if (se) se[i] = sqrt(fmax(var, 0.0));
     if (steps) steps[i] = st[i];
-    if (capped) capped[i] = cap[i];
+    if (capped) capped[i] = (uint32_t)(walks[grp] - (int64_t)done[i]);
 }
 
 template <typename T>
@@ -463,7 +471,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     if (w.total_nodes == 0) return cudaSuccess;
     if (w.total_nodes > 0x7fffffffll) return cudaErrorInvalidValue;   // node ids are 32-bit in the kernel
     cudaError_t e;
-    // accumulators: s1, s2, st (u64) and cap (u32) per node, plus the counter
+    // accumulators: s1, s2, st (u64) and done (u32) per node, plus the counter
     const size_t n = (size_t)w.total_nodes;
     const size_t bytes = n * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
     if ((e = g->ws.acc.reserve(bytes)) != cudaSuccess) return e;
@@ -471,7 +479,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     unsigned long long *counter = (unsigned long long *)base;
     unsigned long long *s1 = (unsigned long long *)(base + 64);
     unsigned long long *s2 = s1 + n, *st = s2 + n;
-    unsigned int *cap = (unsigned int *)(st + n);
+    unsigned int *done = (unsigned int *)(st + n);
     if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
 
     // fixed-point scales follow the bound on |g| (per node walk count on the device)
@@ -493,7 +501,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     P.chunk = w.chunk;
     P.refill = w.refill > 0 ? std::min(w.refill, 32) : 8;
     P.counter = counter;
-    P.s1 = s1; P.s2 = s2; P.st = st; P.cap = cap;
+    P.s1 = s1; P.s2 = s2; P.st = st; P.done = done;
     P.lgM1 = lgM1;
     P.lgM2 = lgM2;
     P.eps = w.eps;
@@ -525,7 +533,7 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
         return e;
     const int T = 256;
     wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
-        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, cap, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
     return cudaGetLastError();
 }
 
@@ -547,7 +555,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
     unsigned long long *counter = (unsigned long long *)base;
     unsigned long long *s1 = (unsigned long long *)(base + 64);
     unsigned long long *s2 = s1 + n, *st = s2 + n;
-    unsigned int *cap = (unsigned int *)(st + n);
+    unsigned int *done = (unsigned int *)(st + n);
     if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
     const double M = g->score_bound > 0 ? g->score_bound : 1.0;
     const int lgM1 = (int)std::ceil(std::log2(M)), lgM2 = (int)std::ceil(std::log2(M * M));
@@ -566,7 +574,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
     P.chunk = w.chunk;
     P.refill = w.refill > 0 ? std::min(w.refill, 32) : 8;
     P.counter = counter;
-    P.s1 = s1; P.s2 = s2; P.st = st; P.cap = cap;
+    P.s1 = s1; P.s2 = s2; P.st = st; P.done = done;
     P.lgM1 = lgM1;
     P.lgM2 = lgM2;
     P.eps = w.eps;
@@ -595,7 +603,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
         return e;
     const int T = 256;
     wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
-        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, cap, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
     return cudaGetLastError();
 }
 

@@ -34,9 +34,12 @@ def test_distance_and_walks_vs_exact():
     do, _ = O.distance(wl.geometry, pts)
     assert np.allclose(_np(d), do, rtol=1e-14, atol=1e-15)
     y = np.array([[0.0, 0.0, 3.4], [2.2, 2.2, 0.5], [0.0, -4.5, 1.0]])
-    r = dtn.wos_points(g, y, np.arange(3), 1, 4000, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3))
     exact = R / np.linalg.norm(y, axis=1)
-    assert np.all(np.abs(_np(r["mean"]) - exact) <= 4 * _np(r["se"]) + 1e-3)
+    for prec in (dtn.PREC_MIXED, dtn.PREC_FP64):
+        r = dtn.wos_points(g, y, np.arange(3), 1, 4000, dtn.solve_opts(prec=prec, epsilon=1e-4, seed=3))
+        # escaped walks score 0 and count in the mean; none is cut at max_steps
+        assert np.all(_np(r["capped"]) == 0)
+        assert np.all(np.abs(_np(r["mean"]) - exact) <= 4 * _np(r["se"]) + 1e-3)
 
 
 def test_assembly_and_solve_parity_given_exact_values():

@@ -91,8 +91,11 @@ def test_capped_walks_counted_and_excluded():
     wl = W.cube_single_patch(walks=200, n_theta=4, n_phi=4, n_rings=2, n_sectors=4)
     g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
     y = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.00005]])
-    r = dtn.wos_points(g, y, [0, 1], 0, 200, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, max_steps=3))
-    cap = r["capped"].cpu().numpy()
-    st = r["steps"].cpu().numpy()
-    assert cap[0] > 0 and cap[1] == 0         # a centre walk rarely ends in 3 steps; the shell point at once
-    assert st[1] == 200
+    for prec in (dtn.PREC_MIXED, dtn.PREC_FP64):
+        r = dtn.wos_points(g, y, [0, 1], 0, 200, dtn.solve_opts(prec=prec, epsilon=1e-4, max_steps=3))
+        cap = r["capped"].cpu().numpy()
+        st = r["steps"].cpu().numpy()
+        assert cap[0] > 0 and cap[1] == 0         # a centre walk rarely ends in 3 steps; the shell point at once
+        assert st[1] == 200
+        # a cut walk made exactly 3 steps, every other one 1 to 3
+        assert 3 * cap[0] + (200 - cap[0]) <= st[0] <= 600
