@@ -567,10 +567,20 @@ dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
             return to_status(e);
         if ((e = cudaMemcpy(g->d_clm_f.p, cf.data(), nc * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
             return to_status(e);
+        // FP32 pair table of the walk scoring: coefficients times the scale alpha_lm
+        // of the recurrence T_lm = alpha_lm Q_lm (see harmonic_cart), formed in FP64
+        // and rounded once
         std::vector<float2> cart(kShPairs, make_float2(0.f, 0.f));
-        for (int l = 0; l <= d->lmax; ++l)
-            for (int m = 0; m <= l; ++m)
-                cart[sh_pair(l, m)] = make_float2((float)d->clm[l * l + l + m], m > 0 ? (float)d->clm[l * l + l - m] : 0.f);
+        double pmm = 0.28209479177387814;   // Y00 = 1 / sqrt(4 pi)
+        for (int m = 0; m <= d->lmax; ++m) {
+            if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+            double alpha = m > 0 ? std::sqrt(2.0) * pmm : pmm;
+            for (int l = m; l <= d->lmax; ++l) {
+                if (l > m) alpha *= std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+                cart[sh_pair(l, m)] = make_float2((float)(alpha * d->clm[l * l + l + m]),
+                                                  m > 0 ? (float)(alpha * d->clm[l * l + l - m]) : 0.f);
+            }
+        }
         if ((e = g->d_clm_cart.reserve(kShPairs * sizeof(float2))) != cudaSuccess) return to_status(e);
         if ((e = cudaMemcpy(g->d_clm_cart.p, cart.data(), kShPairs * sizeof(float2), cudaMemcpyHostToDevice)) !=
             cudaSuccess)

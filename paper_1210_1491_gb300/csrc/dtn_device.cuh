@@ -270,10 +270,9 @@ __host__ __device__ constexpr int sh_pair(int l, int m) { return m * (kMaxL + 1)
 struct ShTables {
     double A[kMaxL + 1][kMaxL + 1], B[kMaxL + 1][kMaxL + 1], D[kMaxL + 1];
     float Af[kMaxL + 1][kMaxL + 1], Bf[kMaxL + 1][kMaxL + 1], Df[kMaxL + 1];
-    // solid-harmonic form (FP32): rec[sh_pair(l, m)] = (A, A B) of (l, m);
-    // pmm[m] = Y00 prod_{k<=m} D_k, times sqrt 2 for m > 0
-    float2 rec[kShPairs];
-    float pmm[kMaxL + 1];
+    // scaled solid-harmonic recurrence (FP32): beta[sh_pair(l, m)] = B_lm / A_{l-1,m}
+    // for l >= m + 2, else 0
+    float beta[kShPairs];
 };
 
 struct DData {
@@ -287,8 +286,8 @@ struct DData {
     const ShTables *sh;     // device copy of the recurrence tables
     // FP32 copies rounded on the host; q_f = strength / (4 pi)
     float x0_f[3], q_f, ctr_f[3], inv_scale_f, constant_f;
-    // FP32 coefficients in pair order: cart[sh_pair(l, m)] = (c_{l,m}, c_{l,-m})
-    // (c_{l,-0} = 0, zero beyond lmax)
+    // FP32 coefficients in pair order times the recurrence scale alpha_lm:
+    // cart[sh_pair(l, m)] = alpha_lm (c_{l,m}, c_{l,-m}) (c_{l,-0} = 0, zero beyond lmax)
     const float2 *cart;
 };
 
@@ -366,8 +365,12 @@ __device__ T harmonic_eval(const DData &d, T x, T y, T z) {
 // T_lm = r^(l-m) Pbar_lm(cos theta) / sin^m theta, a polynomial in z and r^2,
 //   T_mm = pmm_m,  T_lm = A_lm (z T_{l-1,m} - B_lm r^2 T_{l-2,m}),
 //   g = sum_m sum_l T_lm (c_{l,m} C_m + c_{l,-m} S_m).
-// `cs` are the coefficients in pair order (shared memory), x, y, z already
-// centred and scaled.
+// The recurrence runs scaled: T_lm = alpha_lm Q_lm with alpha_mm = pmm_m and
+// alpha_lm = A_lm alpha_{l-1,m}, so Q_mm = 1 and
+//   Q_lm = z Q_{l-1,m} - beta_lm r^2 Q_{l-2,m},  beta_lm = B_lm / A_{l-1,m},
+// and the pair table holds alpha_lm (c_{l,m}, c_{l,-m}) (three operations per
+// term for the recurrence instead of four, none for the diagonal).
+// `cs` is that table (shared memory), x, y, z already centred and scaled.
 __device__ __forceinline__ float harmonic_cart(const float2 *cs, int lmax, float x, float y, float z) {
     const float r2 = x * x + y * y + z * z;
     float C = 1.f, S = 0.f, acc = 0.f;
@@ -378,18 +381,17 @@ __device__ __forceinline__ float harmonic_cart(const float2 *cs, int lmax, float
             C = c2;
         }
         int k = sh_pair(m, m);
-        float t2 = 0.f, t1 = c_sh.pmm[m];
+        float q2 = 0.f, q1 = 1.f;
         float2 c = cs[k];
-        float ac = c.x * t1, as = c.y * t1;
+        float ac = c.x, as = c.y;
         for (int l = m + 1; l <= lmax; ++l) {
             ++k;
-            const float2 rc = c_sh.rec[k];
-            const float t = rc.x * z * t1 - rc.y * r2 * t2;
-            t2 = t1;
-            t1 = t;
+            const float q = fmaf(z, q1, -c_sh.beta[k] * r2 * q2);
+            q2 = q1;
+            q1 = q;
             c = cs[k];
-            ac = fmaf(c.x, t, ac);
-            as = fmaf(c.y, t, as);
+            ac = fmaf(c.x, q, ac);
+            as = fmaf(c.y, q, as);
         }
         acc = fmaf(ac, C, fmaf(as, S, acc));
     }
@@ -410,18 +412,17 @@ __device__ __forceinline__ float harmonic_cart_fixed(const float2 *cs, float x, 
             S = fmaf(S, x, C * y);
             C = c2;
         }
-        float t2 = 0.f, t1 = c_sh.pmm[m];
+        float q2 = 0.f, q1 = 1.f;
         float2 c = cs[sh_pair(m, m)];
-        float ac = c.x * t1, as = c.y * t1;
+        float ac = c.x, as = c.y;
 #pragma unroll
         for (int l = m + 1; l <= L; ++l) {
-            const float2 rc = c_sh.rec[sh_pair(l, m)];
-            const float t = rc.x * z * t1 - rc.y * r2 * t2;
-            t2 = t1;
-            t1 = t;
+            const float q = fmaf(z, q1, -c_sh.beta[sh_pair(l, m)] * r2 * q2);
+            q2 = q1;
+            q1 = q;
             c = cs[sh_pair(l, m)];
-            ac = fmaf(c.x, t, ac);
-            as = fmaf(c.y, t, as);
+            ac = fmaf(c.x, q, ac);
+            as = fmaf(c.y, q, as);
         }
         acc = fmaf(ac, C, fmaf(as, S, acc));
     }

@@ -80,13 +80,8 @@ cudaError_t ensure_tables() {
         t.D[m] = std::sqrt((2.0 * m + 1.0) / (2.0 * m));
         t.Df[m] = (float)t.D[m];
     }
-    double pm = 0.28209479177387814;   // 1 / sqrt(4 pi)
-    for (int m = 0; m <= kMaxL; ++m) {
-        if (m > 0) pm *= t.D[m];
-        t.pmm[m] = (float)(m > 0 ? std::sqrt(2.0) * pm : pm);
-        for (int l = m; l <= kMaxL; ++l)
-            t.rec[sh_pair(l, m)] = make_float2((float)t.A[l][m], (float)(t.A[l][m] * t.B[l][m]));
-    }
+    for (int m = 0; m <= kMaxL; ++m)
+        for (int l = m + 2; l <= kMaxL; ++l) t.beta[sh_pair(l, m)] = (float)(t.B[l][m] / t.A[l - 1][m]);
     e = cudaMalloc(&g_sh, sizeof(ShTables));
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(g_sh, &t, sizeof(t), cudaMemcpyHostToDevice);

@@ -57,3 +57,25 @@ def test_single_point_ring_rule_with_harmonic_data():
                         opts=O.wos_opts(eps=1e-5, seed=3, stream=O.STREAM_F64))
     assert int(_np(r["status"])[0]) == 0
     assert abs(_np(r["sigma2"])[0] - ro["sigma2"]) <= 1e-12 * max(1.0, abs(ro["sigma2"]))
+
+
+@pytest.mark.parametrize("lmax", [3, 8, 12])
+def test_fp32_walk_scoring_of_harmonic_data(lmax):
+    """Walks that start inside the epsilon shell of the unit ball end on their first
+    step and score the data at the radial projection of the start point: the FP32
+    scoring (solid-harmonic recurrence over the FP32 pair table) against the
+    oracle's FP64 harmonic, for the degree-4, degree-8 and general-degree forms."""
+    geom = W.Geometry(W.GEOM_BALL_INTERIOR, center=(0.0, 0.0, 0.0), radius=1.0)
+    data = W.Dirichlet(W.DATA_HARMONIC_SH, lmax=lmax, clm=W.random_clm(lmax, 5), center=(0.1, -0.2, 0.05),
+                       scale=1.3)
+    g = dtn.Geometry.from_spec(geom).set_data_spec(data)
+    rng = np.random.default_rng(11)
+    u = rng.normal(size=(300, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    y = (1.0 - 5e-5) * u
+    for prec in (dtn.PREC_MIXED, dtn.PREC_FP64):
+        r = dtn.wos_points(g, y, np.arange(300), 0, 4, dtn.solve_opts(prec=prec, epsilon=1e-4, seed=1))
+        assert np.all(_np(r["steps"]) == 4) and np.all(_np(r["capped"]) == 0)
+        ref = O.dirichlet(data, u)
+        err = np.max(np.abs(_np(r["mean"]) - ref)) / np.max(np.abs(ref))
+        assert err <= (3e-5 if prec == dtn.PREC_MIXED else 1e-12), (prec, err)
