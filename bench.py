@@ -30,13 +30,14 @@ N_TARGETS = 100_000
 # algorithmic thread-level ALU operations of the FP32 walk in the ball region.
 # Per step: a third of a Philox4x32-10 block (10 rounds x (2 wide multiplies +
 # 2 xor3 + 2 key adds) / 3 = 20) and of its split into six 21-bit fields
-# (10 / 3 = 3), two uniforms 6, direction (z, 1 - z^2, sqrt, azimuth reduction
-# and sincos) 11, distance to the sphere 9, shell test and step count 2,
-# position update 4: 55.  Per walk: the score, projection onto the sphere 8 +
-# degree-8 harmonic data by solid-harmonic recurrences (45 (l, m) pairs x 5 +
-# 9 x 4) 261 + fixed-point terms 11: 280.
-OPS_PER_STEP = 55
-OPS_PER_WALK = 280
+# (10 / 3 = 3), two uniforms 6, direction (z, 1 - z^2, sqrt, azimuth and
+# sincos) 8, distance to the sphere 9, shell test and step count 2, position
+# update 4: 52.  Per walk: the score, projection onto the sphere 8 + degree-8
+# harmonic data by the scaled solid-harmonic recurrence (36 off-diagonal (l, m)
+# pairs x (3 recurrence + 2 accumulate) + 9 x 4 for the powers (x + iy)^m and
+# the per-m sums) 216 + fixed-point terms 11: 235.
+OPS_PER_STEP = 52
+OPS_PER_WALK = 235
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
 # per-node sums): ncu capture of the 64-patch case, 1,655,808 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes

@@ -253,6 +253,19 @@ __device__ __forceinline__ void jump(double &x, double &y, double &z, double d, 
     z += d * zz;
 }
 
+// Ball regions, FP32, position relative to the centre: distance to the sphere
+// and the escape test of the exterior region
+template <int GK>
+__device__ __forceinline__ float ball_dist_rel(const DGeom &g, float x, float y, float z) {
+    // the 1e-30 keeps r2 > 0 at the centre (below half an ulp of any other r2)
+    const float r2 = fmaf(x, x, fmaf(y, y, fmaf(z, z, 1e-30f)));
+    const float r = r2 * rsqrtf(r2);   // SFU reciprocal square root: |x| to a few FP32 ulps
+    return GK == kBall ? g.R_f - r : r - g.R_f;
+}
+__device__ __forceinline__ bool ball_escaped_rel(const DGeom &g, float x, float y, float z) {
+    return x * x + y * y + z * z > g.trunc_f * g.trunc_f;
+}
+
 template <typename T, int GK>
 __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     extern __shared__ float s_boxes[];
@@ -273,6 +286,12 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     // would run on the FP64 pipe, and the compiler may redo it inside the loop
     const T eps = pick<T>(P.eps, P.eps_f);
     ScoreQueue<T> &Q = s_queue[threadIdx.x >> 5];
+    // FP32 walks in a ball region keep positions relative to the centre: the
+    // distance then needs no subtraction; absorption points get the centre back
+    // when they are queued for scoring
+    constexpr bool kRel = std::is_same<T, float>::value && (GK == kBall || GK == kBallExterior);
+    const T ox = kRel ? pick<T>(P.g.c[0], P.g.c_f[0]) : (T)0, oy = kRel ? pick<T>(P.g.c[1], P.g.c_f[1]) : (T)0,
+            oz = kRel ? pick<T>(P.g.c[2], P.g.c_f[2]) : (T)0;
     int qhead = 0, qcount = 0;   // warp-uniform
     WarpScore ws;
 
@@ -298,9 +317,9 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
         if (pm) {
             if (pending) {
                 const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
-                Q.x[e] = x;
-                Q.y[e] = y;
-                Q.z[e] = z;
+                Q.x[e] = x + ox;
+                Q.y[e] = y + oy;
+                Q.z[e] = z + oz;
                 Q.node[e] = (int)acc.node;
                 Q.f1[e] = (short)f1;
                 Q.f2[e] = (short)f2;
@@ -332,9 +351,9 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                 cf1 = fixed_exponent(P.walks[grp], P.lgM1);
                 cf2 = fixed_exponent(P.walks[grp], P.lgM2);
                 cpt = P.point_id ? P.point_id[cnode] : (uint32_t)k;
-                cx = (T)P.y[3 * cnode];
-                cy = (T)P.y[3 * cnode + 1];
-                cz = (T)P.y[3 * cnode + 2];
+                cx = (T)(P.y[3 * cnode] - (kRel ? P.g.c[0] : 0.0));
+                cy = (T)(P.y[3 * cnode + 1] - (kRel ? P.g.c[1] : 0.0));
+                cz = (T)(P.y[3 * cnode + 2] - (kRel ? P.g.c[2] : 0.0));
             }
             const int nidle = __popc(idle);
             const int take = (int)min((uint32_t)nidle, cend - cnext);
@@ -371,13 +390,13 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                                        (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
-                    if (unbounded(GK) && active && geo_escaped<T>(P.g, x, y, z)) {
+                    if (unbounded(GK) && active && (kRel ? ball_escaped_rel(P.g, x, y, z) : geo_escaped<T>(P.g, x, y, z))) {
                         active = false;   // gone to infinity: scores 0
                         acc.esc += 1u;
                     }
                     // branch-free step: every lane evaluates; the lanes that do not
                     // go on jump by 0 (the lanes stay converged through the block)
-                    const T d = geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
+                    const T d = kRel ? ball_dist_rel<GK>(P.g, x, y, z) : geo_dist<T, GK>(P.g, (const T *)sb, x, y, z);
                     const uint32_t st1 = step + 1u;
                     const bool absorbed = active && d <= eps;
                     // a walk neither absorbed nor going on is cut at max_steps
@@ -415,9 +434,9 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
         const unsigned pm = __ballot_sync(FULL, pending);
         if (pending) {
             const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
-            Q.x[e] = x;
-            Q.y[e] = y;
-            Q.z[e] = z;
+            Q.x[e] = x + ox;
+            Q.y[e] = y + oy;
+            Q.z[e] = z + oz;
             Q.node[e] = (int)acc.node;
             Q.f1[e] = (short)f1;
             Q.f2[e] = (short)f2;
