@@ -30,21 +30,22 @@ N_TARGETS = 100_000
 # algorithmic thread-level ALU operations of the FP32 walk in the ball region.
 # Per step: a third of a Philox4x32-10 block (10 rounds x (2 wide multiplies +
 # 2 xor3 + 2 key adds) / 3 = 20) and of its split into six 21-bit fields
-# (10 / 3 = 3), two uniforms 6, direction (z, 1 - z^2, sqrt, azimuth and
-# sincos) 8, distance to the sphere 9, shell test and step count 2, position
-# update 4: 52.  Per walk: the score, projection onto the sphere 8 + degree-8
+# (10 / 3 = 3), two uniforms (one integer add each) 2, direction (z, 1 - z^2,
+# sqrt, azimuth and sincos) 8, distance to the sphere from the centre-relative
+# position (|x|^2, sqrt, R - |x|) 6, shell test and step count 2, position
+# update 4: 45.  Per walk: the score, projection onto the sphere 8 + degree-8
 # harmonic data by the scaled solid-harmonic recurrence (36 off-diagonal (l, m)
 # pairs x (3 recurrence + 2 accumulate) + 9 x 4 for the powers (x + iy)^m and
 # the per-m sums) 216 + fixed-point terms 11: 235.
-OPS_PER_STEP = 52
+OPS_PER_STEP = 45
 OPS_PER_WALK = 235
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
-# per-node sums): ncu capture of the 64-patch case, 1,655,808 bytes for 32,768
+# per-node sums): ncu capture of the 64-patch case, 1,769,216 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
-DRAM_BYTES_PER_NODE = 1655808 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
+DRAM_BYTES_PER_NODE = 1769216 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
-NCU_ISSUE_ACTIVE = 0.741        # ncu, same capture: issue slots busy
-NCU_LANES_PER_INST = 30.94      # ncu, same capture: active lanes per warp instruction
+NCU_ISSUE_ACTIVE = 0.719        # ncu, same capture: issue slots busy
+NCU_LANES_PER_INST = 30.66      # ncu, same capture: active lanes per warp instruction
 SM_COUNT = 152
 LANES_PER_SM = 128
 

@@ -219,24 +219,20 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 
 // one jump of the walk from x by d in the direction drawn from uniforms (u1, u2):
 // z uniform in (-1, 1), azimuth uniform over a full turn
-// FP32 walks: uniforms (2f + 1) 2^-22 from 21-bit fields; the azimuth is taken as
-// 2 pi (u2 - 1/2), already in (-pi, pi) (u2 - 1/2 is formed exactly), by the SFU
+// FP32 walks: uniforms u = (2f + 1) 2^-22 from 21-bit fields, held as v = 1 + u
+// built in the significand (4f + 2 < 2^23: an integer add, no conversion);
+// z = 1 - 2 u1 = 3 - 2 v1 exactly; the azimuth 2 pi (u2 - 1/2) = 2 pi v2 - 3 pi,
+// in (-pi, pi) up to one rounding (a constant shift of the angle), by the SFU
 // sine/cosine; s = sqrt(1 - z^2) by the SFU reciprocal square root
 // (1 - z^2 >= 2^-20 > 0 for these uniforms).  d = 0 leaves x unchanged.
-__device__ __forceinline__ float u01_21(uint32_t f) {
-    // 1 + (2f + 1) 2^-22 built in the significand (4f + 2 < 2^23), minus 1 exactly:
-    // (2f + 1) 2^-22 with an integer add and an FP32 add, no conversion
-    return __uint_as_float(0x3F800002u + 4u * f) - 1.0f;
-}
-
 __device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
-    const float u1 = u01_21(f1);
-    const float h2 = __uint_as_float(0x3F800002u + 4u * f2) - 1.5f;   // u2 - 1/2, exact
-    const float zz = fmaf(-2.0f, u1, 1.0f);
+    constexpr float kTwoPi = 6.2831853071795865f, kAz0 = 1.5f * kTwoPi;
+    const float v1 = __uint_as_float(0x3F800002u + 4u * f1), v2 = __uint_as_float(0x3F800002u + 4u * f2);
+    const float zz = fmaf(-2.0f, v1, 3.0f);
     const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
     const float s = t * rsqrtf(t);
     float sn, cs;
-    __sincosf(6.2831853071795865f * h2, &sn, &cs);
+    __sincosf(fmaf(kTwoPi, v2, -kAz0), &sn, &cs);
     x = fmaf(d * s, cs, x);
     y = fmaf(d * s, sn, y);
     z = fmaf(d, zz, z);
