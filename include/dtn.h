@@ -115,7 +115,7 @@ typedef struct {
     double refine_tol;          /* stop when |r|_inf <= refine_tol |b|_inf (0 = 1e-12) */
     int32_t u_provided;         /* 1: skip the walks and read U_k from result->u_gamma_mean */
     int32_t walk_chunk;         /* walks per warp work item (0 = tuned) */
-    int32_t wos_blocks_per_sm;  /* resident walk blocks per SM (0 = tuned) */
+    int32_t wos_blocks_per_sm;  /* resident 128-thread walk blocks per SM (0 = tuned) */
     int32_t graph_capture;      /* 1: replay the device part as a CUDA graph when the shapes of
                                    the previous call repeat */
     int32_t record_stages;      /* 1: record CUDA events between the stages of the call on its
@@ -377,8 +377,9 @@ dtn_status dtn_eval_dirichlet(const dtn_geometry *geom, int64_t n, const double 
 
 /* Autotuner (not in the paper): times the walk kernel on a sample of the batch
  * (at most 32 patches, at most 512 walks per node) for every combination of
- * walk chunk {64, 128, 256, 512}, resident blocks per SM {1 .. occupancy
- * limit} and refill threshold {2, 4, 8, 16}, and keeps the fastest per
+ * walk chunk {64, 128, 256, 512}, resident 128-thread blocks per SM
+ * {4, 5, 6, 7} (each capped at the occupancy limit) and refill threshold
+ * {4, 8, 12, 16}, and keeps the fastest per
  * (device name, region kind, precision) in a process-wide cache that
  * dtn_solve_patches and dtn_wos_points consult for every opts field left at 0.
  * Synchronises `stream`.  *out (may be NULL) receives the choice. */
