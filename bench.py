@@ -40,12 +40,12 @@ N_TARGETS = 100_000
 OPS_PER_STEP = 45
 OPS_PER_WALK = 235
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
-# per-node sums): ncu capture of the 64-patch case, 1,769,216 bytes for 32,768
+# per-node sums): ncu capture of the 64-patch case, 1,768,704 bytes for 32,768
 # nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
-DRAM_BYTES_PER_NODE = 1769216 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
+DRAM_BYTES_PER_NODE = 1768704 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
-NCU_ISSUE_ACTIVE = 0.719        # ncu, same capture: issue slots busy
-NCU_LANES_PER_INST = 30.66      # ncu, same capture: active lanes per warp instruction
+NCU_ISSUE_ACTIVE = 0.727        # ncu, same capture: issue slots busy
+NCU_LANES_PER_INST = 30.73      # ncu, same capture: active lanes per warp instruction
 SM_COUNT = 152
 LANES_PER_SM = 128
 

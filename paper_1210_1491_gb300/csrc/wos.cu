@@ -84,7 +84,7 @@ __device__ __forceinline__ double pow2(int e) {
 // integer atomics when the lane moves to another node.  Absorbed walks are
 // counted where they are scored; a node's walks cut at max_steps are the rest.
 struct LaneAcc {
-    int64_t node = -1;
+    int node = -1;   // node ids are 32-bit in the kernel
     unsigned long long st = 0;
     unsigned int esc = 0;
 
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     WarpScore ws;
 
     // warp-uniform chunk state
-    int64_t cnode = -1;
+    int cnode = -1;
     uint32_t cnext = 0, cend = 0;   // walk indices of the node (at most 2^32 - 1 walks)
     uint32_t cpid = 0, cpt = 0;
     int cf1 = 0, cf2 = 0;          // fixed-point exponents of the node's sums
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                 Q.x[e] = x + ox;
                 Q.y[e] = y + oy;
                 Q.z[e] = z + oz;
-                Q.node[e] = (int)acc.node;
+                Q.node[e] = acc.node;
                 Q.f1[e] = (short)f1;
                 Q.f2[e] = (short)f2;
                 pending = false;
@@ -340,16 +340,17 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                 const int64_t local = (int64_t)c - P.chunk_off[grp];
                 const int64_t cp = P.cpn[grp];
                 const int64_t k = local / cp, j = local - k * cp;
-                cnode = P.node_off[grp] + k;
+                cnode = (int)(P.node_off[grp] + k);
                 cnext = (uint32_t)(j * P.chunk);
                 cend = (uint32_t)min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
                 cpid = P.pid[grp];
                 cf1 = fixed_exponent(P.walks[grp], P.lgM1);
                 cf2 = fixed_exponent(P.walks[grp], P.lgM2);
                 cpt = P.point_id ? P.point_id[cnode] : (uint32_t)k;
-                cx = (T)(P.y[3 * cnode] - (kRel ? P.g.c[0] : 0.0));
-                cy = (T)(P.y[3 * cnode + 1] - (kRel ? P.g.c[1] : 0.0));
-                cz = (T)(P.y[3 * cnode + 2] - (kRel ? P.g.c[2] : 0.0));
+                const double *yc = P.y + 3 * (int64_t)cnode;
+                cx = (T)(yc[0] - (kRel ? P.g.c[0] : 0.0));
+                cy = (T)(yc[1] - (kRel ? P.g.c[1] : 0.0));
+                cz = (T)(yc[2] - (kRel ? P.g.c[2] : 0.0));
             }
             const int nidle = __popc(idle);
             const int take = (int)min((uint32_t)nidle, cend - cnext);
@@ -372,9 +373,13 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                 active = true;
             }
             cnext += (uint32_t)take;
+            if (take == nidle) {   // every idle lane has a walk
+                idle = 0u;
+                break;
+            }
             idle = __ballot_sync(FULL, !active);
         }
-        if (__ballot_sync(FULL, active) == 0u) break;
+        if (idle == FULL) break;   // no lane active and no walk left
         const int thresh = no_more ? 32 : P.refill;
         for (;;) {
             if constexpr (std::is_same<T, float>::value) {
@@ -433,7 +438,7 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
             Q.x[e] = x + ox;
             Q.y[e] = y + oy;
             Q.z[e] = z + oz;
-            Q.node[e] = (int)acc.node;
+            Q.node[e] = acc.node;
             Q.f1[e] = (short)f1;
             Q.f2[e] = (short)f2;
         }
