@@ -9,9 +9,11 @@
 // evaluated in one pass, not one divergent lane at a time) and idle lanes are
 // refilled.
 //
-// Scores are accumulated as 64-bit fixed-point integers (score * 2^F), per lane
-// while the lane stays on one node and by integer atomics when it moves on, so
-// sums do not depend on scheduling: the estimates are bitwise reproducible.
+// Scores are accumulated as 64-bit fixed-point integers (score * 2^F) per warp
+// and node, together with the number of walks scored; steps and escapes per
+// lane and node; all flushed by integer atomics when the node changes, so sums
+// do not depend on scheduling: the estimates are bitwise reproducible.  A
+// node's walks cut at max_steps are those neither scored nor escaped.
 //
 // Random numbers: Philox4x32-10 keyed by the seed.  FP64 walks draw one block
 // per jump, counter (walk, j, point, patch), 53-bit uniforms from words (0,1)
