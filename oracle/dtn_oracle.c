@@ -326,6 +326,29 @@ typedef struct {
                             absorption point itself (martingale diagnostic) */
 } or_wos_opts;
 
+/* Uniform direction on the unit sphere from two uniforms (Sec. 2: the next
+ * point of a walk is uniform on the sphere of radius d): z = 1 - 2 u1 is
+ * uniform in (-1, 1) and the azimuth is uniform over a full turn, by
+ * Archimedes' hat-box theorem.  Stream 0 takes the azimuth 2 pi u2 in (0, 2 pi);
+ * stream 1 takes 2 pi (u2 - 1/2) in (-pi, pi), the same uniform law shifted by
+ * half a turn (reading R3: the form the FP32 walks use, where u2 - 1/2 is exact
+ * and needs no range reduction). */
+static void direction_parts(double u1, double u2, int stream, double *z, double *s, double *ph)
+{
+    *z = 1.0 - 2.0 * u1;
+    *s = sqrt(fmax(0.0, 1.0 - *z * *z));
+    *ph = (stream == 0) ? 2.0 * OR_PI * u2 : 2.0 * OR_PI * (u2 - 0.5);
+}
+
+void or_direction(double u1, double u2, int stream, double om[3])
+{
+    double z, s, ph;
+    direction_parts(u1, u2, stream, &z, &s, &ph);
+    om[0] = s * cos(ph);
+    om[1] = s * sin(ph);
+    om[2] = z;
+}
+
 /* One walk on spheres (Sec. 2): from y, repeat { d = dist(x); stop if d <= eps;
  * jump to a uniform point of the sphere of radius d about x }.  Returns 1 and the
  * score when absorbed, 0 when the walk reached max_steps distance evaluations.
@@ -369,10 +392,8 @@ int or_walk(const or_geom *g, const or_data *dat, const double y[3], uint32_t wa
             u1 = or_u01_21(f[2 * m]);
             u2 = or_u01_21(f[2 * m + 1]);
         }
-        /* uniform direction on the unit sphere: z uniform in (-1,1), azimuth uniform */
-        double z = 1.0 - 2.0 * u1;
-        double s = sqrt(fmax(0.0, 1.0 - z * z));
-        double ph = 2.0 * OR_PI * u2;
+        double z, s, ph;
+        direction_parts(u1, u2, o->stream, &z, &s, &ph);
         x[0] += d * s * cos(ph);
         x[1] += d * s * sin(ph);
         x[2] += d * z;
@@ -987,6 +1008,17 @@ static double duffy_triangle(const quad_ctx *c, const double S[2], const double 
  * map.  `rtol` is relative to area / (4 pi max(distance, diameter)). */
 static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *sing, double rtol);
 
+/* Gauss order per direction of the self-panel rule of the second-kind
+ * integrands (see panel_integral_ctx).  Set before calls, not during them. */
+static int sk_self_order = 20;
+
+int or_set_sk_self_order(int n)
+{
+    int old = sk_self_order;
+    if (n >= 4 && n <= 64) sk_self_order = n;
+    return old;
+}
+
 double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const double X[3],
                          const double prm[6], const double *sing, double rtol)
 {
@@ -1030,14 +1062,16 @@ static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *
          * next to the corner s = 0 rounding dominates them (g - l is O(r^2)
          * against g = O(1), divided by r^3; n_x.(x - y) is O(r^2) from
          * components of size r), so an adaptive split toward s = 0 would chase
-         * rounding.  A fixed Gauss rule of order
-         * 40 x 40 per triangle keeps its points at s >= 1e-3; each triangle's
-         * far edge is cut into pieces no longer than its height. */
-        enum { NQ = 40 };
-        static double gx40[NQ], gw40[NQ];
-        static int ready = 0;
-#pragma omp critical(or_gl40)
-        if (!ready) { or_gauss_legendre(NQ, gx40, gw40); ready = 1; }
+         * rounding, and so does a high-order rule, whose first nodes sit close
+         * to s = 0 (the rounding error of a node grows like 1/s^2).  A fixed
+         * Gauss rule of order sk_self_order (default 20) per direction and
+         * triangle; each triangle's far edge is cut into pieces no longer than
+         * its height.  On cap and disk patches the orders 12 ... 24 agree to a
+         * few 1e-12 of |q| (the smooth integrand has converged), while 40 and
+         * 80 move q by 1e-11 ... 1e-10 (rounding at their first nodes). */
+        const int NQ = sk_self_order;
+        double gxs[64], gws[64];
+        or_gauss_legendre(NQ, gxs, gws);
         double PS[3], nn[3], Jd;
         patch_point(p, S[0], S[1], PS, nn, &Jd);
         for (int e = 0; e < 4; ++e) {
@@ -1064,12 +1098,12 @@ static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *
             double det = fabs(E1[0] * E2[1] - E1[1] * E2[0]);
             if (det == 0.0) continue;
             for (int i = 0; i < NQ; ++i) {
-                double sv = 0.5 * (gx40[i] + 1.0);
+                double sv = 0.5 * (gxs[i] + 1.0);
                 for (int j = 0; j < NQ; ++j) {
-                    double tv = 0.5 * (gx40[j] + 1.0);
+                    double tv = 0.5 * (gxs[j] + 1.0);
                     double u = S[0] + sv * (E1[0] + tv * E2[0]);
                     double v = S[1] + sv * (E1[1] + tv * E2[1]);
-                    s += 0.25 * gw40[i] * gw40[j] * integrand(&c, u, v) * sv * det;
+                    s += 0.25 * gws[i] * gws[j] * integrand(&c, u, v) * sv * det;
                 }
             }
           }

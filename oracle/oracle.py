@@ -60,6 +60,9 @@ def lib():
         L.or_fields21.argtypes = [_u32p, _u32p]
         L.or_u01_53.argtypes = [C.c_uint32, C.c_uint32]
         L.or_u01_53.restype = C.c_double
+        L.or_direction.argtypes = [C.c_double, C.c_double, C.c_int, _f64p]
+        L.or_set_sk_self_order.argtypes = [C.c_int]
+        L.or_set_sk_self_order.restype = C.c_int
         L.or_gauss_legendre.argtypes = [C.c_int, _f64p, _f64p]
         L.or_distance.argtypes = [C.POINTER(OrGeom), _f64p, _f64p]
         L.or_distance.restype = C.c_double
@@ -195,6 +198,13 @@ def fields21(w) -> np.ndarray:
 
 def u01_53(hi: int, lo: int) -> float:
     return lib().or_u01_53(int(hi) & 0xFFFFFFFF, int(lo) & 0xFFFFFFFF)
+
+
+def direction(u1: float, u2: float, stream: int) -> np.ndarray:
+    """or_direction: the unit jump direction of a walk from two uniforms."""
+    om = np.zeros(3)
+    lib().or_direction(float(u1), float(u2), int(stream), om)
+    return om
 
 
 def gauss_legendre(n: int):
@@ -435,6 +445,12 @@ def second_kind_flat(p: OrPatch, data, nt, nph, nr, ns, U, ng2=20) -> np.ndarray
     if rc != 0:
         raise ValueError("second-kind rows need a disk patch")
     return q
+
+
+def set_sk_self_order(n: int) -> int:
+    """Gauss order per direction of the second kind's self-panel rule (default
+    20); returns the previous order."""
+    return int(lib().or_set_sk_self_order(int(n)))
 
 
 def second_kind(p: OrPatch, data, nt, nph, nr, ns, U, rtol=1e-10, want_system=False):

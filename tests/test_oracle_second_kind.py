@@ -147,3 +147,31 @@ def test_double_layer_row_sums_match_a_geodesic_polar_rule():
                 dnx = float(np.dot(O.green_grad_y(a, Y, X), nx))
                 tot += wp * ws * dnx * R * R * np.sin(sg)
         assert abs(D[i].sum() - tot) <= 1e-9 * max(1.0, abs(tot)), (i, D[i].sum(), tot)
+
+
+def test_self_panel_rule_has_converged():
+    """The second kind's self-panel integrals (Duffy triangles, a fixed Gauss
+    rule of order m per direction): the integrand is smooth in the Duffy
+    variables, so the orders 12 ... 24 must agree to the rounding floor.  q at
+    order 20 (the default) is within 2e-11 (relative L2) of q at 12, 16 and 24,
+    on a unit-ball cap and on the R = 3 sphere seen from outside."""
+    cases = []
+    wl, pf = _ball_cap()
+    cases.append((wl, pf, lambda y: O.dirichlet(wl.data, y)))
+    we = W.sphere_exterior(n_patches=2, walks=2)
+    pe = O.patch_frame(we.geometry, we.batch.centers[0], 1.0)
+    cases.append((we, pe, lambda y: 3.0 / np.linalg.norm(y, axis=1)))
+    assert O.set_sk_self_order(20) == 20
+    try:
+        for wl_, pf_, u in cases:
+            _, yg, _ = O.gamma_nodes(pf_, 16, 32)
+            U = u(yg.reshape(-1, 3))
+            qs = {}
+            for m in (12, 16, 20, 24):
+                O.set_sk_self_order(m)
+                qs[m] = O.second_kind(pf_, wl_.data, 16, 32, 4, 8, U)
+            ref = qs[20]
+            for m in (12, 16, 24):
+                assert np.linalg.norm(qs[m] - ref) <= 2e-11 * np.linalg.norm(ref), m
+    finally:
+        O.set_sk_self_order(20)
