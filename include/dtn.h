@@ -170,8 +170,11 @@ typedef struct {
 typedef struct {
     double *gamma_xyz;       /* gamma_total x 3, hemisphere node positions */
     double *gamma_w;         /* gamma_total, node weights (area element of Eq. bw83) */
-    double *u_gamma_mean;    /* gamma_total, required: U_k (written; read when u_provided) */
-    double *u_gamma_se;      /* gamma_total, standard error of U_k */
+    double *u_gamma_mean;    /* gamma_total, required: U_k (written; read when u_provided).
+                                A node whose walks were all cut at max_steps has no
+                                estimate: NaN (its patch gets DTN_E_WALK_CAP) */
+    double *u_gamma_se;      /* gamma_total, standard error of U_k (+inf when fewer than two
+                                of the node's walks were kept) */
     uint64_t *gamma_steps;   /* gamma_total, walk-steps (distance evaluations) per node */
     uint32_t *gamma_capped;  /* gamma_total, walks cut at max_steps (excluded from U_k) */
     double *colloc_xyz;      /* panels_total x 3, collocation points */
@@ -183,7 +186,9 @@ typedef struct {
     double *rhs;             /* panels_total: assembled b, for checking */
     int32_t *refine_iters;   /* n_patches */
     double *residual;        /* n_patches, final |b - A q|_inf / |b|_inf */
-    int32_t *patch_status;   /* n_patches, dtn_status per patch */
+    int32_t *patch_status;   /* n_patches, dtn_status per patch: DTN_E_UNSUPPORTED (no solve),
+                                else DTN_E_WALK_CAP (walks of the patch were cut at max_steps),
+                                else DTN_E_NOT_CONVERGED, else DTN_OK */
 } dtn_patch_result;
 
 /* Creates a geometry object (device copies of the region, obstacle lookup
@@ -352,6 +357,8 @@ dtn_status dtn_single_point_neumann(dtn_geometry *geom, int64_t n, const double 
  *   - Every call uses the same array and leaves its contents behind; each call
  *     clears the parts that must start at zero.  Calls whose work overlaps on
  *     the GPU race on the array: serialise them (one stream, or events).
+ *   - The device current at the call must be the geometry's device
+ *     (DTN_E_INVALID_ARG otherwise).
  *   - Asynchronous on `stream`; the host array walks is copied before
  *     return and may be reused at once. */
 dtn_status dtn_wos_points_noalloc(const dtn_geometry *geom, int64_t n, const double *y,
@@ -371,12 +378,30 @@ dtn_status dtn_distance(const dtn_geometry *geom, int64_t n, const double *x, do
 dtn_status dtn_philox4x32_10(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out,
                              void *stream);
 
+/* The draws of the FP32 (DTN_PREC_MIXED) walks for n Philox blocks, computed
+ * by the walk kernel's own device functions, for bit-exact checking.  Walk
+ * jump j uses the block with counter (walk, j / 3, point, patch) and its
+ * fields 2m and 2m + 1, m = j mod 3 (the walk on spheres of Sec. 2 draws a
+ * uniform direction per jump; the generator is not in the paper).
+ *   ctr: device, n x 4 u32 counters; key = (seed lo32, seed hi32).
+ *   fields: device, n x 6 u32 (may be NULL): the 21-bit fields, the top 21 bits
+ *     of each word, then (w0 & 0x7ff) | (w1 & 0x3ff) << 11 and the same of w2, w3.
+ *   uniforms: device, n x 6 float (may be NULL): u = (2 f + 1) 2^-22, exact.
+ *   directions: device, n x 3 x 3 float (may be NULL): per jump m the unit
+ *     vector (s cos ph, s sin ph, z), z = 1 - 2 u_{2m}, s = sqrt(1 - z^2),
+ *     ph = 2 pi (u_{2m+1} - 1/2), with the walk kernel's FP32 sine, cosine and
+ *     square root (a few 1e-7 from the exact values).
+ * At least one output must be given.  Asynchronous; DTN_E_INVALID_ARG for
+ * n < 0 or missing arrays. */
+dtn_status dtn_philox_fields21(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *fields,
+                               float *uniforms, float *directions, void *stream);
+
 /* Dirichlet data g at n device points (FP64). */
 dtn_status dtn_eval_dirichlet(const dtn_geometry *geom, int64_t n, const double *x, double *g,
                               void *stream);
 
 /* Autotuner (not in the paper): times the walk kernel on a sample of the batch
- * (at most 32 patches, at most 512 walks per node) for every combination of
+ * (its first 96 patches at most, at most 4096 walks per node) for every combination of
  * walk chunk {64, 128, 256, 512}, resident 128-thread blocks per SM
  * {4, 5, 6, 7} (each capped at the occupancy limit) and refill threshold
  * {4, 8, 12, 16}, and keeps the fastest per

@@ -10,5 +10,5 @@ from .binding import (  # noqa: F401
     GEOM_BOX_INTERIOR, GEOM_BALL_EXTERIOR, GEOM_BOX_MINUS_BOXES, GEOM_DISK_EXTERIOR, GEOM_HALF_SPACE, LIB_PATH, PREC_FP64, PREC_MIXED, DtnError, Geometry,
     HostBatch, Server, alloc_result, autotune_walks, distance, eval_dirichlet, eval_potential, eval_potential_fmm,
     fmm_opts, gather_owned, load,
-    philox, single_point_neumann, solve_opts, solve_patches, wos_points, wos_points_noalloc,
+    philox, philox_fields21, single_point_neumann, solve_opts, solve_patches, wos_points, wos_points_noalloc,
 )

@@ -109,7 +109,8 @@ EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "
            "dtn_distance", "dtn_philox4x32_10", "dtn_eval_dirichlet", "dtn_status_string",
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
            "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks",
-           "dtn_wos_points_noalloc", "dtn_single_point_neumann", "dtn_eval_potential_fmm"]
+           "dtn_wos_points_noalloc", "dtn_single_point_neumann", "dtn_eval_potential_fmm",
+           "dtn_philox_fields21"]
 
 _lib = None
 
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH):
         "dtn_wos_points": ([vp, i64, vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, vp, vp, vp], i32),
         "dtn_distance": ([vp, i64, vp, vp, vp, i32, vp], i32),
         "dtn_philox4x32_10": ([i64, vp, u64, vp, vp], i32),
+        "dtn_philox_fields21": ([i64, vp, u64, vp, vp, vp, vp], i32),
         "dtn_eval_dirichlet": ([vp, i64, vp, vp, vp], i32),
         "dtn_status_string": ([i32], C.c_char_p),
         "dtn_last_cuda_error": ([], i32),
@@ -507,6 +509,20 @@ def philox(ctr, seed: int, stream=None):
     _check(load().dtn_philox4x32_10(c.shape[0], _ptr(cd), int(seed), _ptr(out), _stream(stream)),
            "dtn_philox4x32_10")
     return out.cpu().numpy().view(np.uint32)
+
+
+def philox_fields21(ctr, seed: int, stream=None):
+    """dtn_philox_fields21 on a (n, 4) uint32 counter array -> numpy (fields (n, 6)
+    uint32, uniforms (n, 6) float32, directions (n, 3, 3) float32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    cd = torch.from_numpy(c.view(np.int32)).to("cuda")
+    n = c.shape[0]
+    f = torch.empty(n, 6, dtype=torch.int32, device="cuda")
+    u = torch.empty(n, 6, dtype=torch.float32, device="cuda")
+    d = torch.empty(n, 3, 3, dtype=torch.float32, device="cuda")
+    _check(load().dtn_philox_fields21(n, _ptr(cd), int(seed), _ptr(f), _ptr(u), _ptr(d), _stream(stream)),
+           "dtn_philox_fields21")
+    return f.cpu().numpy().view(np.uint32), u.cpu().numpy(), d.cpu().numpy()
 
 
 def eval_dirichlet(geom: Geometry, x, stream=None):

@@ -21,6 +21,11 @@ std::atomic<int32_t> g_last_cuda_error{0};
 
 void set_cuda_error(cudaError_t e) { g_last_cuda_error.store((int32_t)e); }
 
+bool wrong_device(const dtn_geometry *g) {
+    int dev = -1;
+    return cudaGetDevice(&dev) != cudaSuccess || dev != g->device;
+}
+
 cudaError_t DevBuf::reserve(size_t n) {
     if (n <= bytes && p) return cudaSuccess;
     if (p) {
@@ -540,7 +545,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
-                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp};
+                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp, &g->ws.capflag};
     for (DevBuf *b : bufs) b->release();
     fmm_release(g);
     for (int k = 0; k < 5; ++k)
@@ -553,6 +558,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
 
 dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
     if (!g || !d) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
     DData &dd = g->dd;
     if (d->kind == DTN_DATA_HARMONIC_SH) {
@@ -638,6 +644,7 @@ dtn_status dtn_query_patch_sizes(const dtn_patch_batch *b, int64_t *panels_total
 dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dtn_solve_opts *o,
                              dtn_patch_result *r, void *stream) {
     if (!g || !b || !o || !r) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (b->n_patches < 0) return DTN_E_INVALID_ARG;
     if (b->n_patches == 0) return DTN_OK;
     if (!b->centers || !b->radius || !b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors) return DTN_E_INVALID_ARG;
@@ -670,7 +677,8 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         (e = W.gamma_xyz.reserve(G * 3 * 8)) != cudaSuccess || (e = W.panel_loc.reserve(Pn * 3 * 8)) != cudaSuccess ||
         (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
         (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.rhs.reserve(Pn * 8)) != cudaSuccess ||
-        (e = W.se_tmp.reserve(G * 8)) != cudaSuccess)
+        (e = W.se_tmp.reserve(G * 8)) != cudaSuccess ||
+        (e = W.capflag.reserve((size_t)L.n_patches * sizeof(int32_t))) != cudaSuccess)
         return to_status(e);
     const bool shared = (o->prec == DTN_PREC_MIXED);
     if (shared) {
@@ -718,7 +726,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                                 &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
-                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec};
+                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.capflag};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
@@ -803,8 +811,14 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         w.se = r->u_gamma_se ? r->u_gamma_se : W.se_tmp.as<double>();
         w.steps = r->gamma_steps;
         w.capped = r->gamma_capped;
+        w.group_capped = W.capflag.as<int32_t>();
         if ((e = launch_wos(g, w, s)) != cudaSuccess) return e;
     }
+    // after the solve: DTN_E_WALK_CAP where a patch had walks cut and no other error
+    auto walk_cap = [&]() -> cudaError_t {
+        return o->u_provided ? cudaSuccess
+                             : launch_walk_cap_status(L.n_patches, W.capflag.as<int32_t>(), r->patch_status, s);
+    };
     if ((e = mark(2)) != cudaSuccess) return e;
     const bool caps = (g->dg.kind == kBall || g->dg.kind == kBallExterior);
     // 3-4. second kind (Eq. bw55-bw59) on disk patches: q = 2b row by row, no system
@@ -812,6 +826,7 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         e = launch_second_kind(g, L, D, W.panel_loc.as<double>(), pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                o->ring_order > 0 ? o->ring_order : 20, r->neumann, r->rhs, r->refine_iters,
                                r->residual, r->patch_status, s);
+        if (e == cudaSuccess) e = walk_cap();
         if (e == cudaSuccess) e = mark(3);
         if (e == cudaSuccess) e = mark(4);
         return e;
@@ -862,6 +877,7 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     else
         e = launch_lu_solve(g, L, D, o->prec, A, rhs, r->neumann, iters, tol, r->refine_iters, r->residual,
                             r->patch_status, s);
+    if (e == cudaSuccess) e = walk_cap();
     if (e == cudaSuccess) e = mark(4);
     return e;
 }
@@ -874,6 +890,7 @@ extern "C" {
 dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const dtn_solve_opts *o, dtn_tuning *out,
                               void *stream) {
     if (!g || !b || !o || b->n_patches < 1 || !b->centers || !b->radius || !b->walks_per_point) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (!b->n_theta || !b->n_phi || !b->n_rings || !b->n_sectors || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
     if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
     if (!g->has_data) return DTN_E_INVALID_ARG;
@@ -983,6 +1000,7 @@ dtn_status dtn_eval_potential(const dtn_geometry *g, int64_t np, const double *x
                               const int64_t *n_index, int64_t nt, const double *t, double *out, int32_t prec,
                               void *stream) {
     if (!g || np < 0 || nt < 0) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (nt == 0) return DTN_OK;
     if (!t || !out || (np > 0 && (!xyz || !nrm || !area || !q))) return DTN_E_INVALID_ARG;
     if (prec != DTN_PREC_FP64 && prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
@@ -1012,6 +1030,7 @@ dtn_status dtn_wos_points(const dtn_geometry *gc, int64_t n, const double *y, co
                           double *se, uint64_t *steps, uint32_t *capped, void *stream) {
     dtn_geometry *g = const_cast<dtn_geometry *>(gc);
     if (!g || n < 0 || !o) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (n == 0) return DTN_OK;
     if (!y || !point_ids || !patch_ids || !walks || !mean || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
     if (o->prec != DTN_PREC_FP64 && o->prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
@@ -1081,6 +1100,7 @@ dtn_status dtn_single_point_neumann(dtn_geometry *g, int64_t n, const double *x,
                                     const dtn_solve_opts *o, double *sigma1, double *sigma2, double *q, double *se,
                                     int32_t *status, double *U, void *stream) {
     if (!g || n < 0 || !o) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (n == 0) return DTN_OK;
     if (!x || !walks || !q || !(a > 0) || !(delta >= 0) || !(delta < a)) return DTN_E_INVALID_ARG;
     if (ng1 < 1 || ng1 > kMaxGauss || ng2 < 1 || ng2 > kMaxGauss || !(o->epsilon > 0)) return DTN_E_INVALID_ARG;
@@ -1170,6 +1190,7 @@ dtn_status dtn_single_point_neumann(dtn_geometry *g, int64_t n, const double *x,
 dtn_status dtn_distance(const dtn_geometry *g, int64_t n, const double *x, double *d, double *nearest, int32_t prec,
                         void *stream) {
     if (!g || n < 0 || (n > 0 && !x)) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (prec != DTN_PREC_FP64 && prec != DTN_PREC_MIXED) return DTN_E_INVALID_ARG;
     return to_status(launch_distance(g, n, x, d, nearest, prec, (cudaStream_t)stream));
 }
@@ -1179,8 +1200,16 @@ dtn_status dtn_philox4x32_10(int64_t n, const uint32_t *ctr, uint64_t seed, uint
     return to_status(launch_philox(n, ctr, seed, out, (cudaStream_t)stream));
 }
 
+dtn_status dtn_philox_fields21(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *fields, float *uniforms,
+                               float *directions, void *stream) {
+    if (n < 0 || (n > 0 && !ctr)) return DTN_E_INVALID_ARG;
+    if (n > 0 && !fields && !uniforms && !directions) return DTN_E_INVALID_ARG;
+    return to_status(launch_fields21(n, ctr, seed, fields, uniforms, directions, (cudaStream_t)stream));
+}
+
 dtn_status dtn_eval_dirichlet(const dtn_geometry *g, int64_t n, const double *x, double *out, void *stream) {
     if (!g || n < 0 || (n > 0 && (!x || !out))) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (!g->has_data) return DTN_E_INVALID_ARG;
     return to_status(launch_dirichlet(g, n, x, out, (cudaStream_t)stream));
 }

@@ -97,6 +97,7 @@ struct Workspace {
     DevBuf gw;              // right-side weights per weight group (FP32)
     DevBuf vec;             // per-patch samples (data at panel points, walk estimates), FP32
     DevBuf sp;              // single-point method: frames, nodes, weights, estimates, walk layout
+    DevBuf capflag;         // n_patches int32: 1 where a walk of the patch was cut at max_steps
 };
 
 struct GeometryHost {
@@ -152,6 +153,9 @@ void set_cuda_error(cudaError_t e);
 // n(n-1)/2, nodes ascending on [-1, 1].
 constexpr int kMaxGauss = 64;
 cudaError_t ensure_tables();
+// 1 when the current device is not the geometry's (the entry points then return
+// DTN_E_INVALID_ARG: every launch goes to the current device)
+bool wrong_device(const dtn_geometry *g);
 const double *gl_x_dev();
 const double *gl_w_dev();
 const ShTables *sh_tables_dev();
@@ -201,10 +205,12 @@ struct WosLaunch {
     double *mean, *se;
     uint64_t *steps;
     uint32_t *capped;
+    int32_t *group_capped;       // per group or nullptr: set to 1 where a walk was cut (cleared first)
 };
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s);
 size_t wos_scratch_bytes(int64_t nodes);
 cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s);
+cudaError_t launch_walk_cap_status(int64_t n, const int32_t *group_capped, int32_t *status, cudaStream_t s);
 
 // mode 0: per patch, A and b (FP64 rules, or FP32 far field in mixed precision);
 // mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off
@@ -260,6 +266,8 @@ cudaError_t launch_gather(int64_t np, const double *x, const int64_t *owner, int
                           const double *cent, uint8_t *keep, int64_t *kept, int64_t *n_kept,
                           cudaStream_t s);
 
+cudaError_t launch_fields21(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *fields, float *uni, float *dir,
+                            cudaStream_t s);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out,
                           cudaStream_t s);
 cudaError_t launch_distance(const dtn_geometry *g, int64_t n, const double *x, double *d,

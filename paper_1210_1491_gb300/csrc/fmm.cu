@@ -1284,6 +1284,7 @@ extern "C" dtn_status dtn_eval_potential_fmm(dtn_geometry *g, int64_t np, const 
                                              dtn_fmm_stats *st, void *stream) {
     using namespace dtn;
     if (!g || !o || np < 0 || nt < 0) return DTN_E_INVALID_ARG;
+    if (wrong_device(g)) return DTN_E_INVALID_ARG;
     if (o->order < 1 || o->order > kFmmMaxOrder || !(o->theta > 0.0 && o->theta < 1.0) || o->leaf_sources < 1 ||
         o->leaf_sources > 4096 || o->leaf_targets < 1 || o->leaf_targets > 4096 || o->max_level < 1 ||
         o->max_level > kMortonBits)

@@ -9,10 +9,19 @@
 namespace dtn {
 
 namespace {
+// Gauss-Legendre and spherical-harmonic tables, one copy per device (uploaded
+// with that device current, together with every unit's __constant__ copy)
+constexpr int kMaxTableDevices = 64;
 std::mutex g_tab_mu;
-bool g_tab_ready = false;
-double *g_glx = nullptr, *g_glw = nullptr;
-ShTables *g_sh = nullptr;
+bool g_tab_ready[kMaxTableDevices] = {false};
+double *g_glx[kMaxTableDevices] = {nullptr}, *g_glw[kMaxTableDevices] = {nullptr};
+ShTables *g_sh[kMaxTableDevices] = {nullptr};
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxTableDevices) return -1;
+    return dev;
+}
 }  // namespace
 
 // Gauss-Legendre by Newton iteration on P_n from its three-term recurrence,
@@ -50,18 +59,20 @@ void gauss_legendre_host(int n, double *x, double *w) {
 }
 
 cudaError_t ensure_tables() {
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_tab_mu);
-    if (g_tab_ready) return cudaSuccess;
+    if (g_tab_ready[dev]) return cudaSuccess;
     const int total = kMaxGauss * (kMaxGauss + 1) / 2;
     std::vector<double> hx(total), hw(total);
     for (int n = 1; n <= kMaxGauss; ++n) gauss_legendre_host(n, &hx[n * (n - 1) / 2], &hw[n * (n - 1) / 2]);
-    cudaError_t e = cudaMalloc(&g_glx, total * sizeof(double));
+    cudaError_t e = cudaMalloc(&g_glx[dev], total * sizeof(double));
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&g_glw, total * sizeof(double));
+    e = cudaMalloc(&g_glw[dev], total * sizeof(double));
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(g_glx, hx.data(), total * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(g_glx[dev], hx.data(), total * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(g_glw, hw.data(), total * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(g_glw[dev], hw.data(), total * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     ShTables t{};
     for (int l = 0; l <= kMaxL; ++l) {
@@ -82,22 +93,33 @@ cudaError_t ensure_tables() {
     }
     for (int m = 0; m <= kMaxL; ++m)
         for (int l = m + 2; l <= kMaxL; ++l) t.beta[sh_pair(l, m)] = (float)(t.B[l][m] / t.A[l - 1][m]);
-    e = cudaMalloc(&g_sh, sizeof(ShTables));
+    e = cudaMalloc(&g_sh[dev], sizeof(ShTables));
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(g_sh, &t, sizeof(t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(g_sh[dev], &t, sizeof(t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     if ((e = upload_sh_tables_here(t)) != cudaSuccess) return e;
     if ((e = upload_sh_wos(t)) != cudaSuccess) return e;
     if ((e = upload_sh_assemble(t)) != cudaSuccess) return e;
     if ((e = upload_sh_second_kind(t)) != cudaSuccess) return e;
     if ((e = upload_sh_single_point(t)) != cudaSuccess) return e;
-    g_tab_ready = true;
+    g_tab_ready[dev] = true;
     return cudaSuccess;
 }
 
-const double *gl_x_dev() { return g_glx; }
-const double *gl_w_dev() { return g_glw; }
-const ShTables *sh_tables_dev() { return g_sh; }
+// the tables of the current device (every launch goes to the current device,
+// which the entry points check is the geometry's)
+const double *gl_x_dev() {
+    const int d = current_device();
+    return d < 0 ? nullptr : g_glx[d];
+}
+const double *gl_w_dev() {
+    const int d = current_device();
+    return d < 0 ? nullptr : g_glw[d];
+}
+const ShTables *sh_tables_dev() {
+    const int d = current_device();
+    return d < 0 ? nullptr : g_sh[d];
+}
 
 namespace {
 

@@ -227,14 +227,37 @@ __device__ __forceinline__ void score_batch(const WosDev &P, const T *sb, const 
 // in (-pi, pi) up to one rounding (a constant shift of the angle), by the SFU
 // sine/cosine; s = sqrt(1 - z^2) by the SFU reciprocal square root
 // (1 - z^2 >= 2^-20 > 0 for these uniforms).  d = 0 leaves x unchanged.
-__device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
+// The six 21-bit fields of one Philox block: the top 21 bits of each word, then
+// the low 11 bits of words 0 and 2 with the low 10 bits of words 1 and 3 above
+// them (126 of the block's 128 bits, each used once).
+__device__ __forceinline__ void fields21(const uint4 &w, uint32_t f[6]) {
+    f[0] = w.x >> 11;
+    f[1] = w.y >> 11;
+    f[2] = w.z >> 11;
+    f[3] = w.w >> 11;
+    f[4] = (w.x & 0x7ffu) | ((w.y & 0x3ffu) << 11);
+    f[5] = (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11);
+}
+
+// v = 1 + u for the uniform u = (2f + 1) 2^-22 of a 21-bit field f: the
+// significand of 1.0 plus 4f + 2 units of 2^-23 (exact, no conversion)
+__device__ __forceinline__ float one_plus_u21(uint32_t f) { return __uint_as_float(0x3F800002u + 4u * f); }
+
+// The pieces of the jump direction from two fields: z = 1 - 2 u1 = 3 - 2 v1
+// (exact), s = sqrt(1 - z^2), and the sine and cosine of the azimuth
+// 2 pi (u2 - 1/2) = 2 pi v2 - 3 pi
+__device__ __forceinline__ void direction21(uint32_t f1, uint32_t f2, float &zz, float &s, float &sn, float &cs) {
     constexpr float kTwoPi = 6.2831853071795865f, kAz0 = 1.5f * kTwoPi;
-    const float v1 = __uint_as_float(0x3F800002u + 4u * f1), v2 = __uint_as_float(0x3F800002u + 4u * f2);
-    const float zz = fmaf(-2.0f, v1, 3.0f);
+    const float v1 = one_plus_u21(f1), v2 = one_plus_u21(f2);
+    zz = fmaf(-2.0f, v1, 3.0f);
     const float t = fmaf(-zz, zz, 1.0f);   // 1 - z^2, one rounding
-    const float s = t * rsqrtf(t);
-    float sn, cs;
+    s = t * rsqrtf(t);
     __sincosf(fmaf(kTwoPi, v2, -kAz0), &sn, &cs);
+}
+
+__device__ __forceinline__ void jump(float &x, float &y, float &z, float d, uint32_t f1, uint32_t f2) {
+    float zz, s, sn, cs;
+    direction21(f1, f2, zz, s, sn, cs);
     x = fmaf(d * s, cs, x);
     y = fmaf(d * s, sn, y);
     z = fmaf(d, zz, z);
@@ -388,9 +411,8 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
                 // three jumps from one Philox block; idle lanes run it too and
                 // jump by 0, so the block needs no branch around it
                 const uint4 w = philox4x32_10_rk(make_uint4(walk, step / 3u, ppt, ppid), P.rk0, P.rk1);
-                const uint32_t f[6] = {w.x >> 11, w.y >> 11, w.z >> 11, w.w >> 11,
-                                       (w.x & 0x7ffu) | ((w.y & 0x3ffu) << 11),
-                                       (w.z & 0x7ffu) | ((w.w & 0x3ffu) << 11)};
+                uint32_t f[6];
+                fields21(w, f);
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
                     if (unbounded(GK) && active && (kRel ? ball_escaped_rel(P.g, x, y, z) : geo_escaped<T>(P.g, x, y, z))) {
@@ -461,20 +483,34 @@ __global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int
                                     const unsigned long long *__restrict__ st,
                                     const unsigned int *__restrict__ done, int lgM1, int lgM2,
                                     double *__restrict__ mean, double *__restrict__ se,
-                                    uint64_t *__restrict__ steps, uint32_t *__restrict__ capped) {
+                                    uint64_t *__restrict__ steps, uint32_t *__restrict__ capped,
+                                    int32_t *__restrict__ group_capped) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_nodes) return;
     const int64_t grp = find_group(node_off, n_groups, i);
     const double N = (double)done[i];   // walks not cut at max_steps
     const double inv1 = pow2(-fixed_exponent(walks[grp], lgM1));
     const double inv2 = pow2(-fixed_exponent(walks[grp], lgM2));
-    const double m1 = (double)(long long)s1[i] * inv1 / N;
+    // a node with no walk left has no estimate (NaN); with one, no standard
+    // error (+inf)
+    const double m1 = N > 0.0 ? (double)(long long)s1[i] * inv1 / N : __longlong_as_double(0x7ff8000000000000ll);
     const double e2 = (double)(long long)s2[i] * inv2;
-    const double var = (e2 - N * m1 * m1) / (N * (N - 1.0));
+    const double var = N > 1.0 ? fmax((e2 - N * m1 * m1) / (N * (N - 1.0)), 0.0) : __longlong_as_double(0x7ff0000000000000ll);
     mean[i] = m1;
-    if (se) se[i] = sqrt(fmax(var, 0.0));
+    if (se) se[i] = sqrt(var);
     if (steps) steps[i] = st[i];
-    if (capped) capped[i] = (uint32_t)(walks[grp] - (int64_t)done[i]);
+    const uint32_t cut = (uint32_t)(walks[grp] - (int64_t)done[i]);
+    if (capped) capped[i] = cut;
+    if (group_capped && cut) group_capped[grp] = 1;   // every writer stores 1
+}
+
+// DTN_E_WALK_CAP for the solved patches that had walks cut at max_steps (it
+// replaces DTN_E_NOT_CONVERGED: a node without walks makes the system NaN)
+__global__ void walk_cap_status_kernel(int64_t n, const int32_t *__restrict__ group_capped,
+                                       int32_t *__restrict__ status) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n && group_capped[p] && (status[p] == DTN_OK || status[p] == DTN_E_NOT_CONVERGED))
+        status[p] = DTN_E_WALK_CAP;
 }
 
 template <typename T>
@@ -489,25 +525,40 @@ void *wos_kernel_ptr(int gk) {
 
 }  // namespace
 
+// Accumulator bytes of a walk launch over `nodes` nodes: s1, s2, st (u64) and
+// done (u32) per node, after a 64-byte slot for the work counter.
+size_t wos_scratch_bytes(int64_t nodes) {
+    return (size_t)nodes * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
+}
+
+// The walk launch with its accumulators in the geometry's workspace.
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
+    if (w.total_nodes == 0) return cudaSuccess;
+    cudaError_t e = g->ws.acc.reserve(wos_scratch_bytes(w.total_nodes));
+    if (e != cudaSuccess) return e;
+    return launch_wos_into(g, w, g->ws.acc.p, s);
+}
+
+// The walk launch with the accumulators and the work counter in `acc` (at least
+// wos_scratch_bytes(nodes) bytes, 256-byte aligned, device): walks, then the
+// estimates of Eq. bw87.
+cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s) {
     if (w.total_nodes == 0) return cudaSuccess;
     if (w.total_nodes > 0x7fffffffll) return cudaErrorInvalidValue;   // node ids are 32-bit in the kernel
     cudaError_t e;
-    // accumulators: s1, s2, st (u64) and done (u32) per node, plus the counter
     const size_t n = (size_t)w.total_nodes;
-    const size_t bytes = n * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
-    if ((e = g->ws.acc.reserve(bytes)) != cudaSuccess) return e;
-    char *base = g->ws.acc.as<char>();
+    const size_t bytes = wos_scratch_bytes(w.total_nodes);
+    char *base = (char *)acc;
     unsigned long long *counter = (unsigned long long *)base;
     unsigned long long *s1 = (unsigned long long *)(base + 64);
     unsigned long long *s2 = s1 + n, *st = s2 + n;
     unsigned int *done = (unsigned int *)(st + n);
     if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
-
+    if (w.group_capped && (e = cudaMemsetAsync(w.group_capped, 0, (size_t)w.n_groups * sizeof(int32_t), s)) != cudaSuccess)
+        return e;
     // fixed-point scales follow the bound on |g| (per node walk count on the device)
     const double M = g->score_bound > 0 ? g->score_bound : 1.0;
     const int lgM1 = (int)std::ceil(std::log2(M)), lgM2 = (int)std::ceil(std::log2(M * M));
-
     WosDev P;
     P.g = g->dg;
     P.dat = g->dd;
@@ -530,7 +581,6 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     P.eps_f = (float)w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
     philox_round_keys(w.seed, P.rk0, P.rk1);
-
     const int gk = g->dg.kind;
     const bool fp32 = (w.prec == DTN_PREC_MIXED);
     void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
@@ -539,8 +589,8 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
         if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
     }
-    // persistent grid: never more blocks per SM than can be resident at once
     int resident = 1;
+    // persistent grid: never more blocks per SM than can be resident at once
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, kWosThreads, smem)) != cudaSuccess)
         return e;
     resident = std::max(resident, 1);
@@ -555,77 +605,15 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
         return e;
     const int T = 256;
     wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
-        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped,
+        w.group_capped);
     return cudaGetLastError();
 }
 
-// Same launch as launch_wos, but the accumulators and the work counter live in
-// caller-provided device memory (`acc`, at least wos_scratch_bytes(nodes)
-// bytes, 256-byte aligned) instead of the geometry's workspace, so nothing is
-// allocated here.
-size_t wos_scratch_bytes(int64_t nodes) {
-    return (size_t)nodes * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64;
-}
-
-cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s) {
-    if (w.total_nodes == 0) return cudaSuccess;
-    if (w.total_nodes > 0x7fffffffll) return cudaErrorInvalidValue;   // node ids are 32-bit in the kernel
-    cudaError_t e;
-    const size_t n = (size_t)w.total_nodes;
-    const size_t bytes = wos_scratch_bytes(w.total_nodes);
-    char *base = (char *)acc;
-    unsigned long long *counter = (unsigned long long *)base;
-    unsigned long long *s1 = (unsigned long long *)(base + 64);
-    unsigned long long *s2 = s1 + n, *st = s2 + n;
-    unsigned int *done = (unsigned int *)(st + n);
-    if ((e = cudaMemsetAsync(base, 0, bytes, s)) != cudaSuccess) return e;
-    const double M = g->score_bound > 0 ? g->score_bound : 1.0;
-    const int lgM1 = (int)std::ceil(std::log2(M)), lgM2 = (int)std::ceil(std::log2(M * M));
-    WosDev P;
-    P.g = g->dg;
-    P.dat = g->dd;
-    P.y = w.y;
-    P.node_off = w.node_off;
-    P.walks = w.walks;
-    P.pid = w.pid;
-    P.point_id = w.point_id;
-    P.chunk_off = w.chunk_off;
-    P.cpn = w.cpn;
-    P.n_groups = w.n_groups;
-    P.total_chunks = w.total_chunks;
-    P.chunk = w.chunk;
-    P.refill = w.refill > 0 ? std::min(w.refill, 32) : 8;
-    P.counter = counter;
-    P.s1 = s1; P.s2 = s2; P.st = st; P.done = done;
-    P.lgM1 = lgM1;
-    P.lgM2 = lgM2;
-    P.eps = w.eps;
-    P.eps_f = (float)w.eps;
-    P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
-    philox_round_keys(w.seed, P.rk0, P.rk1);
-    const int gk = g->dg.kind;
-    const bool fp32 = (w.prec == DTN_PREC_MIXED);
-    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
-    const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
-    if (smem > 48 * 1024) {
-        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-    }
-    int resident = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, kWosThreads, smem)) != cudaSuccess)
-        return e;
-    resident = std::max(resident, 1);
-    const int bps = w.blocks_per_sm > 0 ? std::min(w.blocks_per_sm, resident) : resident;
-    int64_t blocks = (int64_t)g->num_sms * bps;
-    const int64_t max_blocks = (w.total_chunks + (kWosThreads / 32) - 1) / (kWosThreads / 32);
-    if (blocks > max_blocks) blocks = max_blocks;
-    if (blocks < 1) blocks = 1;
-    void *args[] = {&P};
-    if ((e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kWosThreads), args, smem, s)) != cudaSuccess)
-        return e;
+cudaError_t launch_walk_cap_status(int64_t n, const int32_t *group_capped, int32_t *status, cudaStream_t s) {
+    if (n == 0 || !status || !group_capped) return cudaSuccess;
     const int T = 256;
-    wos_finalize_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
-        w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped);
+    walk_cap_status_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(n, group_capped, status);
     return cudaGetLastError();
 }
 
@@ -642,6 +630,31 @@ __global__ void philox_kernel(int64_t n, const uint32_t *__restrict__ ctr, uint3
     const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
     const uint4 r = philox4x32_10(c, k0, k1);
     out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+// The draws of FP32 walks for n Philox blocks: the six fields, their uniforms
+// (v - 1, exact) and the unit directions of the block's three jumps (the jump
+// of a walk at the origin by d = 1), by the walk kernel's own functions.
+__global__ void fields21_kernel(int64_t n, const uint32_t *__restrict__ ctr, uint32_t k0, uint32_t k1,
+                                uint32_t *__restrict__ fields, float *__restrict__ uni, float *__restrict__ dir) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 w = philox4x32_10(c, k0, k1);
+    uint32_t f[6];
+    fields21(w, f);
+    for (int k = 0; k < 6; ++k) {
+        if (fields) fields[6 * i + k] = f[k];
+        if (uni) uni[6 * i + k] = one_plus_u21(f[k]) - 1.0f;
+    }
+    if (dir)
+        for (int h = 0; h < 3; ++h) {
+            float x = 0.f, y = 0.f, z = 0.f;
+            jump(x, y, z, 1.0f, f[2 * h], f[2 * h + 1]);
+            dir[9 * i + 3 * h] = x;
+            dir[9 * i + 3 * h + 1] = y;
+            dir[9 * i + 3 * h + 2] = z;
+        }
 }
 
 template <typename T>
@@ -685,6 +698,15 @@ cudaError_t launch_philox(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_
     const int T = 256;
     philox_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(n, ctr, (uint32_t)(seed & 0xFFFFFFFFull),
                                                             (uint32_t)(seed >> 32), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields21(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *fields, float *uni, float *dir,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int T = 256;
+    fields21_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(n, ctr, (uint32_t)(seed & 0xFFFFFFFFull),
+                                                              (uint32_t)(seed >> 32), fields, uni, dir);
     return cudaGetLastError();
 }
 

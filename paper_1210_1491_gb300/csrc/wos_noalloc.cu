@@ -82,9 +82,13 @@ extern "C" dtn_status dtn_wos_points_noalloc(const dtn_geometry *gc, int64_t n, 
         if (walks[i] < 2 || walks[i] > 0xFFFFFFFFll) return DTN_E_INVALID_ARG;
         maxw = std::max(maxw, walks[i]);
     }
-    void *scratch = nullptr;
-    cudaError_t e = scratch_on_current_device(&scratch);
+    // the geometry's device copies and the scratch address must be of one device
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return to_status(e);
+    if (dev != g->device) return DTN_E_INVALID_ARG;
+    void *scratch = nullptr;
+    if ((e = scratch_on_current_device(&scratch)) != cudaSuccess) return to_status(e);
     const int32_t chunk = o->walk_chunk > 0 ? o->walk_chunk : 256;
     // private copy of the walk counts, so that every host array the copies
     // below read is pageable memory of this call

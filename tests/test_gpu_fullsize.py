@@ -39,7 +39,8 @@ def test_unit_ball_full_size_sampled():
                           O.wos_opts(eps=wl.epsilon, seed=wl.seed, stream=O.STREAM_F32))
         Uo, SEo = O.wos_estimates(ro, 4096)
         z = (U[sl][nodes] - Uo) / np.sqrt(SE[sl][nodes] ** 2 + SEo ** 2)
-        assert np.all(np.abs(z) <= 4.5)
+        print(f"patch {p}: max |z| = {np.max(np.abs(z)):.2f}")
+        assert np.all(np.abs(z) <= 4.0)
         # solve: the oracle's assembly and LU with the GPU's node values
         rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], 0.1, 16, 32, 8, 16, 0, 0, O.wos_opts(),
                            U_in=U[sl], rtol=1e-11)
@@ -76,7 +77,7 @@ def test_wire_patches_vs_oracle():
         ro = O.wos_points(wl.geometry, wl.data, yg[sl], np.arange(64), p, 1024,
                           O.wos_opts(eps=1e-4, seed=2, stream=O.STREAM_F32))
         Uo, SEo = O.wos_estimates(ro, 1024)
-        assert np.all(np.abs(U[sl] - Uo) <= 4.5 * np.sqrt(SE[sl] ** 2 + SEo ** 2))
+        assert np.all(np.abs(U[sl] - Uo) <= 4.0 * np.sqrt(SE[sl] ** 2 + SEo ** 2))
         rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], 0.3, 8, 8, 4, 8, 0, 0, O.wos_opts(), U_in=U[sl],
                            rtol=1e-11)
         assert np.linalg.norm(q[p * 32:(p + 1) * 32] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4
@@ -135,7 +136,7 @@ def test_wires_full_size_uneven_batch_graph_replay():
     (16^2..32^2 nodes, 32..512 panels, 2048 walks) in one mixed-precision call,
     captured as a CUDA graph and replayed; the replay gives the same results bit
     for bit, and sampled patches of each size match the oracle (walk means
-    within 4.5 standard errors on the same Philox streams; the collocation solve
+    within 4 standard errors on the same Philox streams; the collocation solve
     within 1e-4 with the GPU's node values)."""
     wl = W.wires()
     b = wl.batch
@@ -168,7 +169,7 @@ def test_wires_full_size_uneven_batch_graph_replay():
         ro = O.wos_points(wl.geometry, wl.data, yg[gs][nodes], nodes, p, int(b.walks[p]),
                           O.wos_opts(eps=wl.epsilon, seed=wl.seed, stream=O.STREAM_F32))
         Uo, SEo = O.wos_estimates(ro, int(b.walks[p]))
-        assert np.all(np.abs(U[gs][nodes] - Uo) <= 4.5 * np.sqrt(SE[gs][nodes] ** 2 + SEo ** 2))
+        assert np.all(np.abs(U[gs][nodes] - Uo) <= 4.0 * np.sqrt(SE[gs][nodes] ** 2 + SEo ** 2))
         rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], float(b.radius[p]), int(b.n_theta[p]),
                            int(b.n_phi[p]), int(b.n_rings[p]), int(b.n_sectors[p]), 0, 0, O.wos_opts(),
                            U_in=U[gs], rtol=1e-10)

@@ -43,6 +43,33 @@ def test_philox_bit_exact():
     assert list(kat[0]) == [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
 
 
+def test_fp32_draws_bit_exact():
+    """The FP32 walks' fields and uniforms equal the oracle's stream 1 bit for
+    bit; their jump directions agree with the oracle's FP64 directions from the
+    same uniforms to the FP32 sine/cosine accuracy."""
+    rng = np.random.default_rng(3)
+    n = 5003
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    seed = 0x0123456789ABCDEF
+    f, u, d = dtn.philox_fields21(ctr, seed)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    worst = 0.0
+    for i in list(range(0, n, 11)) + [1, n - 1]:
+        w = O.philox(ctr[i], key)
+        fo = O.fields21(w)
+        assert f[i].tolist() == fo.tolist()
+        uo = np.array([O.u01_21(int(v)) for v in fo])
+        assert np.array_equal(u[i].astype(np.float64), uo)   # exact: 22-bit odd multiples of 2^-22
+        for h in range(3):
+            om = O.direction(uo[2 * h], uo[2 * h + 1], O.STREAM_F32)
+            worst = max(worst, float(np.max(np.abs(d[i, h].astype(np.float64) - om))))
+    # FP32 z is exact; the SFU sine/cosine of an argument in (-pi, pi) and the
+    # reciprocal square root are good to a few 1e-7
+    assert worst < 4e-6, worst
+
+
 def _wire_geometry():
     boxes = np.array([[0.3, 0.3, 0.3, 0.6, 0.5, 0.45], [0.1, 0.6, 0.6, 0.9, 0.8, 0.7],
                       [0.7, 0.1, 0.1, 0.9, 0.2, 0.9]])
@@ -156,6 +183,34 @@ def test_wos_fp64_matches_oracle_streams(kind):
         assert close.mean() >= 0.9
         st = _np(r["steps"]).astype(np.int64)
         assert np.mean(np.abs(st - ro["steps"].astype(np.int64)) <= 2) >= 0.9
+
+
+@pytest.mark.parametrize("kind", ["cube", "ball"])
+def test_wos_fp32_follows_oracle_stream1(kind):
+    """FP32 walks draw the oracle's stream-1 numbers, so with two walks per node
+    nearly every node's walks are the oracle's: the same number of steps, and a
+    mean that differs by the FP32 rounding of the positions and the score only.
+    (Walks part where an FP32 distance falls on the other side of epsilon from
+    the FP64 one, about once per 1e2 walks.)"""
+    wl, _ = _wos_case(kind)
+    if kind == "cube":
+        y = W.points_in_box(3000, (0.05, 0.05, 0.05), (0.95, 0.95, 0.95), margin=0.0, seed=21)
+        scale = 1.0 / (4 * math.pi * 0.3)
+    else:
+        y = W.targets_in_ball(3000, 1.0, 0.02, seed=22)
+        scale = float(np.max(np.abs(O.dirichlet(wl.data, y))))
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    N = 2
+    r = dtn.wos_points(g, y, np.arange(len(y)), 41, N, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=6))
+    ro = O.wos_points(wl.geometry, wl.data, y, np.arange(len(y)), 41, N,
+                      O.wos_opts(eps=1e-4, seed=6, stream=O.STREAM_F32))
+    Uo, _ = O.wos_estimates(ro, N)
+    U = _np(r["mean"])
+    same = _np(r["steps"]).astype(np.int64) == ro["steps"].astype(np.int64)
+    assert same.mean() >= 0.9, same.mean()
+    close = np.abs(U - Uo) <= 1e-4 * scale
+    assert np.mean(close[same]) >= 0.99
+    assert np.all(_np(r["capped"]) == 0)
 
 
 @pytest.mark.parametrize("kind", ["cube", "ball", "wires"])

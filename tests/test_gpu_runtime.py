@@ -99,3 +99,60 @@ def test_capped_walks_counted_and_excluded():
         assert st[1] == 200
         # a cut walk made exactly 3 steps, every other one 1 to 3
         assert 3 * cap[0] + (200 - cap[0]) <= st[0] <= 600
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_walk_cap_status_and_nodes_without_estimates(prec):
+    """max_steps = 2: nearly every walk is cut.  Each patch reports
+    DTN_E_WALK_CAP; a node keeping no walk has mean NaN and standard error
+    +inf, a node keeping one walk a finite mean and +inf, and the counts add
+    up (kept + cut = walks)."""
+    wl = W.unit_ball(n_patches=3, walks=6, n_theta=8, n_phi=8, n_rings=4, n_sectors=8)
+    b = wl.batch
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks)
+    p = dtn.PREC_MIXED if prec == "mixed" else dtn.PREC_FP64
+    r = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=p, epsilon=1e-4, max_steps=2))
+    torch.cuda.synchronize()
+    assert np.all(r["patch_status"].cpu().numpy() == 7)   # DTN_E_WALK_CAP
+    cut = r["gamma_capped"].cpu().numpy().astype(np.int64)
+    kept = 6 - cut
+    U = r["u_gamma_mean"].cpu().numpy()
+    SE = r["u_gamma_se"].cpu().numpy()
+    assert np.all((cut >= 0) & (cut <= 6)) and cut.sum() > 0
+    assert np.all(np.isnan(U[kept == 0])) and np.all(np.isposinf(SE[kept == 0]))
+    assert np.all(np.isfinite(U[kept == 1])) and np.all(np.isposinf(SE[kept == 1]))
+    assert np.all(np.isfinite(U[kept >= 2])) and np.all(np.isfinite(SE[kept >= 2]))
+    # without a cap the same batch solves cleanly
+    r2 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=p, epsilon=1e-4))
+    torch.cuda.synchronize()
+    assert np.all(r2["patch_status"].cpu().numpy() == 0)
+    assert np.all(r2["gamma_capped"].cpu().numpy() == 0)
+
+
+def test_not_converged_status():
+    """One refinement sweep against an unreachable tolerance: every patch
+    reports DTN_E_NOT_CONVERGED with its residual and sweep count."""
+    wl = W.unit_ball(n_patches=3, walks=2, n_theta=8, n_phi=8, n_rings=4, n_sectors=8)
+    b = wl.batch
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks)
+    for p in (dtn.PREC_MIXED, dtn.PREC_FP64):
+        res = dtn.alloc_result(hb)
+        r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=p, u_provided=True), result=res)
+        torch.cuda.synchronize()
+        res["u_gamma_mean"].copy_(torch.from_numpy(O_exact(wl, r0)))
+        dtn.solve_patches(g, b.centers, b.radius, hb,
+                          dtn.solve_opts(prec=p, u_provided=True, max_refine_iters=1, refine_tol=1e-300), result=res)
+        torch.cuda.synchronize()
+        assert np.all(res["patch_status"].cpu().numpy() == 4), p   # DTN_E_NOT_CONVERGED
+        assert np.all(res["residual"].cpu().numpy() > 0)
+        assert np.all(res["refine_iters"].cpu().numpy() <= 1)
+        dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=p, u_provided=True), result=res)
+        torch.cuda.synchronize()
+        assert np.all(res["patch_status"].cpu().numpy() == 0), p
+
+
+def O_exact(wl, r):
+    import oracle as O
+    return O.dirichlet(wl.data, r["gamma_xyz"].cpu().numpy())

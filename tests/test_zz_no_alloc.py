@@ -53,3 +53,37 @@ def test_noalloc_rejects_oversized_requests():
     rc = L.dtn_wos_points_noalloc(g.handle, n, dummy, dummy, dummy, walks.ctypes.data_as(C.c_void_p),
                                   C.byref(opts), dummy, None, None, None, None)
     assert rc == 1
+
+
+def test_noalloc_call_takes_no_device_memory():
+    """With the caller's tensors made beforehand, a call (after the first one on
+    the device, which may load the library's module and its scratch array)
+    leaves the free device memory unchanged: nothing is allocated."""
+    g, y = _case()
+    L = dtn.load()
+    opts = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=2)
+    n = len(y)
+    yd = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    ids = torch.arange(n, dtype=torch.int32, device="cuda")
+    pid = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    walks = np.full(n, 500, dtype=np.int64)
+    outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(2)]
+    st = torch.empty(n, dtype=torch.int64, device="cuda")
+    cp = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def call():
+        rc = L.dtn_wos_points_noalloc(g.handle, n, C.c_void_p(yd.data_ptr()), C.c_void_p(ids.data_ptr()),
+                                      C.c_void_p(pid.data_ptr()), walks.ctypes.data_as(C.c_void_p), C.byref(opts),
+                                      C.c_void_p(outs[0].data_ptr()), C.c_void_p(outs[1].data_ptr()),
+                                      C.c_void_p(st.data_ptr()), C.c_void_p(cp.data_ptr()), None)
+        assert rc == 0
+        torch.cuda.synchronize()
+
+    call()
+    first = outs[0].clone()
+    free0 = torch.cuda.mem_get_info()[0]
+    call()
+    call()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    assert torch.equal(outs[0], first)
