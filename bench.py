@@ -39,9 +39,19 @@ N_TARGETS = 100_000
 # the per-m sums) 216 + fixed-point terms 11: 235.
 OPS_PER_STEP = 45
 OPS_PER_WALK = 235
+# The same count for the walk in the wire region (box minus 200 boxes), as a
+# lower bound: the step without the ball distance (45 - 6 = 39), the outer box
+# (6 differences, 5 minima) 11, the lookup-grid cell (3 x (difference, scale,
+# floor, conversion, two clamps) + index) 20, the cell's cap 2, and 17 more per
+# listed box (3 x (2 differences, 2 maxima), |e|^2, sqrt, minimum), counted as
+# none: 72.  Per walk: nearest point on the outer box 12, the grid cell 20,
+# point-source data (3 differences, |r|^2, reciprocal square root, scale) 8,
+# fixed-point terms 11, listed boxes again counted as none: 51.
+OPS_PER_STEP_WIRES_MIN = 72
+OPS_PER_WALK_WIRES_MIN = 51
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
-# per-node sums): ncu capture of the 64-patch case, 1,768,704 bytes for 32,768
-# nodes (profiles/wos_kernel_unit_ball_64p.md), scaled to the launch's nodes
+# per-node sums): an ncu capture of the 64-patch unit-ball case read and wrote
+# 1,768,704 bytes for its 32,768 nodes; scaled to the launch's nodes
 DRAM_BYTES_PER_NODE = 1768704 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
 NCU_ISSUE_ACTIVE = 0.727        # ncu, same capture: issue slots busy
@@ -173,34 +183,49 @@ def run_reference(args):
 # ------------------------------------------------------------------ our arm
 
 def cpu_baseline_sample(wl):
-    """The oracle on a bounded sample (2 patches) on this host's cores."""
+    """The oracle on a bounded sample on this host's cores: 2 patches with every
+    core, then 1 patch on one core."""
     import oracle as O
     b = wl.batch
     o = O.wos_opts(eps=wl.epsilon, seed=wl.seed, stream=O.STREAM_F64)
-    t0 = time.perf_counter()
-    steps = 0
-    n = 2
-    for i in range(n):
-        r = O.solve_patch(wl.geometry, wl.data, b.centers[i], float(b.radius[i]), int(b.n_theta[i]),
-                          int(b.n_phi[i]), int(b.n_rings[i]), int(b.n_sectors[i]), int(b.walks[i]), i, o,
-                          rtol=1e-12)
-        steps += r["steps"]
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "patches/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"first {n} patches of the workload, full walks, assembly and solve",
-            "walk_steps_per_s": steps / dt}
+
+    def run(n):
+        t0 = time.perf_counter()
+        steps = 0
+        for i in range(n):
+            r = O.solve_patch(wl.geometry, wl.data, b.centers[i], float(b.radius[i]), int(b.n_theta[i]),
+                              int(b.n_phi[i]), int(b.n_rings[i]), int(b.n_sectors[i]), int(b.walks[i]), i, o,
+                              rtol=1e-12)
+            steps += r["steps"]
+        dt = time.perf_counter() - t0
+        return n / dt, steps / dt
+
+    cores = O.num_threads()
+    v, sps = run(2)
+    O.set_num_threads(1)
+    try:
+        v1, sps1 = run(1)
+    finally:
+        O.set_num_threads(cores)
+    return {"value": v, "unit": "patches/s", "cores": cores, "kind": "oracle",
+            "sample": "first 2 patches of the workload, full walks, assembly and solve",
+            "walk_steps_per_s": sps,
+            "one_core": {"value": v1, "unit": "patches/s", "cores": 1, "walk_steps_per_s": sps1,
+                         "sample": "first patch of the workload, full walks, assembly and solve"}}
 
 
-def run_serving(dtn, n_queries=32, seed=7, load=0.8, n_targets=100_000):
+def run_serving(dtn, n_queries=600, seed=7, load=0.8, n_targets=100_000):
     """Continuous-batching server on the 200-wire geometry (resident on the device).
 
     Each query asks for the Neumann data at 1..4096 boundary points (log-uniform),
     served by wire-face patches taken in turn until their panels cover that many
     points, with 1024..16384 walks per hemisphere point (log-uniform).  The queries
     are submitted first all at once (saturated throughput), then as Poisson
-    arrivals at `load` x that rate (p50/p99 submit-to-result latency), with an
-    8 GB device-memory admission budget.  Then the potential at 10^5 targets
-    outside the wires, by the integral representation over all served panels."""
+    arrivals at `load` x that rate (p50/p99 submit-to-result latency).  Admission
+    by device memory: the server's budget is the free device memory at its
+    creation less a reserve; three slots share the SMs.  Then the potential at
+    10^5 targets outside the wires, by the integral representation over all
+    served panels."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     wl = W.wires(n_patches=4096, walks=2048)
@@ -223,7 +248,7 @@ def run_serving(dtn, n_queries=32, seed=7, load=0.8, n_targets=100_000):
         queries.append(dict(centers=b.centers[idx], radius=b.radius[idx], n_theta=b.n_theta[idx],
                             n_phi=b.n_phi[idx], n_rings=b.n_rings[idx], n_sectors=b.n_sectors[idx],
                             walks=np.full(len(idx), walks, np.int64), patch_ids=idx.astype(np.uint32)))
-    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, memory_budget=8 << 30)
+    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, split_sms=True)
     # warm-up (first-use costs)
     srv.submit(**queries[0])
     srv.drain()
@@ -243,7 +268,9 @@ def run_serving(dtn, n_queries=32, seed=7, load=0.8, n_targets=100_000):
     t_poisson = time.perf_counter() - t0
     served = [srv.poll(t) for t in tickets]
     lat = np.array([r["latency_s"] for r in served]) * 1e3
+    info = srv.stats()
     srv.close()
+    n_bad = sum(1 for r in served if r["status"] != 0)
     # potential at targets outside the wires, over every served panel: the panel
     # geometry and data of the served patches (no walks), their served Neumann data
     allq = {k: np.concatenate([q[k] for q in queries]) for k in queries[0]}
@@ -278,7 +305,14 @@ def run_serving(dtn, n_queries=32, seed=7, load=0.8, n_targets=100_000):
             "walks_per_node": "1024..16384 log-uniform per query",
             "saturated_queries_per_s": n_queries / t_sat, "saturated_patches_per_s": len(allq["radius"]) / t_sat,
             "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "poisson_queries_per_s": n_queries / t_poisson,
+            "poisson_queries_per_s": n_queries / t_poisson, "queries_not_ok": n_bad,
+            "admission": {"rule": "free device memory at creation less max(1 GiB, 5%), slot workspaces + "
+                                  "each starting batch's workspace within it",
+                          "budget_bytes": info["budget_bytes"], "peak_held_bytes": info["peak_held_bytes"],
+                          "rejected": info["rejected"]},
+            "slots": 3, "split_sms": True,
+            "device_overlap": {"batches": info["batches"], "max_concurrent": info["max_concurrent"],
+                               "busy_ms": info["busy_ms"], "overlap_ms": info["overlap_ms"]},
             "potential": {"targets": int(tgt.shape[0]), "panels": n_pan, "ms": pot_ms,
                           "targets_per_s": tgt.shape[0] / (pot_ms / 1e3),
                           "pair_terms_per_s": tgt.shape[0] * n_pan / (pot_ms / 1e3)}}
@@ -368,6 +402,77 @@ def run_potential_fmm(dtn, n_panels=1_000_000, n_targets=1_000_000, order=10, th
         out.update({"direct_ms": direct_s * 1e3, "speedup_vs_direct": direct_s / fmm_s,
                     "rel_l2_fp32_direct_vs_fp64_sample": float((ud[samp] - ref).norm() / ref.norm())})
     return out
+
+
+def run_batch_leg(dtn, wl, ops_step, ops_walk, reps=2, n_plain=8, capture=False, exact_ops=True):
+    """One workload solved in one mixed-precision call (captured as a CUDA graph
+    and replayed when `capture`), walk launch autotuned: device time of the call
+    (CUDA events, mean of `reps` after a warm-up), patches/s, walk-steps/s from
+    a separate call with stage events, the walk kernel's ALU roofline, and the
+    plain FP64 path (FP64 walks, assembly and LU, one patch per launch) on the
+    first n_plain patches."""
+    import torch
+    b = wl.batch
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks)
+    centers = torch.from_numpy(b.centers).cuda()
+    radius = np.ascontiguousarray(b.radius)
+    stream = torch.cuda.current_stream()
+    base = dict(prec=dtn.PREC_MIXED, epsilon=wl.epsilon, seed=wl.seed)
+    tuning = dtn.autotune_walks(g, centers, radius, hb, dtn.solve_opts(**base))
+    res = dtn.alloc_result(hb)
+    # walk time and walk-steps from one call with stage events (not captured)
+    dtn.solve_patches(g, centers, radius, hb, dtn.solve_opts(record_stages=True, **base), result=res)
+    torch.cuda.synchronize()
+    walk_ms = g.stage_times()[1]
+    steps = int(res["gamma_steps"].sum().item())
+    status_ok = bool((res["patch_status"] == 0).all().item())
+    o = dtn.solve_opts(graph_capture=capture, **base)
+    times = []
+    for k in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dtn.solve_patches(g, centers, radius, hb, o, result=res)
+        e1.record(stream)
+        e1.synchronize()
+        if k:   # the first call captures (or warms up)
+            times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    walks = int(np.sum(b.walks * (b.n_theta * b.n_phi)))
+    peaks = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = (steps * ops_step + walks * ops_walk) / (walk_ms / 1e3) / 1e12
+    # the plain FP64 path, one patch per launch
+    o64 = dtn.solve_opts(prec=dtn.PREC_FP64, epsilon=wl.epsilon, seed=wl.seed)
+    hb1 = [dtn.HostBatch(b.n_theta[i:i + 1], b.n_phi[i:i + 1], b.n_rings[i:i + 1], b.n_sectors[i:i + 1],
+                         b.walks[i:i + 1], patch_id_base=i) for i in range(n_plain)]
+    r1 = [dtn.alloc_result(h) for h in hb1]
+    dtn.solve_patches(g, centers[0:1], radius[0:1], hb1[0], o64, result=r1[0])
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n_plain):
+        dtn.solve_patches(g, centers[i:i + 1], radius[i:i + 1], hb1[i], o64, result=r1[i])
+    e1.record(stream)
+    e1.synchronize()
+    plain = n_plain / (e0.elapsed_time(e1) / 1e3)
+    value = b.n / (ms / 1e3)
+    return {"workload": wl.name, "patches": b.n,
+            "nodes_per_patch": sorted(set(int(v) for v in b.n_theta * b.n_phi)),
+            "panels_per_patch": [int(np.min(b.n_rings * b.n_sectors)), int(np.max(b.n_rings * b.n_sectors))],
+            "walks_per_node": int(b.walks[0]), "graph_capture": capture, "ms": ms, "patches_per_s": value,
+            "walk_ms": walk_ms, "walk_steps": steps, "walk_steps_per_s": steps / (walk_ms / 1e3),
+            "status_ok": status_ok, "walk_tuning": tuning,
+            "roofline": {"bound": "alu", "kernel": "wos_kernel<float>", "achieved": achieved, "peak": alu_peak,
+                         "unit": "Tops/s", "frac": achieved / alu_peak, "ops_per_walk_step": ops_step,
+                         "ops_per_walk": ops_walk,
+                         "ops_basis": "algorithmic count" if exact_ops else
+                         "lower bound: listed obstacle boxes counted as none"},
+            "fp64_path": {"value": plain, "unit": "patches/s", "sample": f"first {n_plain} patches, one per launch",
+                          "speedup": value / plain}}
 
 
 def run_second_kind(dtn, g, centers, radius, hb, opts_kw):
@@ -561,6 +666,14 @@ def run_ours(args):
         line["potential_fmm"] = run_potential_fmm(dtn)
         line["second_kind"] = run_second_kind(dtn, g, centers, radius, hb,
                                               dict(prec=prec, epsilon=wl.epsilon, seed=wl.seed))
+        del res, keep, flush
+        torch.cuda.empty_cache()
+        # the batching workload (1e4 uneven wire patches, one captured launch) and
+        # the precision study's size (2e4 patches x 1024 nodes x 8192 walks)
+        line["wires_batch"] = run_batch_leg(dtn, W.wires(), OPS_PER_STEP_WIRES_MIN, OPS_PER_WALK_WIRES_MIN,
+                                            capture=True, exact_ops=False)
+        line["unit_ball_scaled"] = run_batch_leg(dtn, W.unit_ball_scaled(), OPS_PER_STEP, OPS_PER_WALK, reps=1,
+                                                 n_plain=4)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(wl)
     if rank == 0:

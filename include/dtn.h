@@ -199,6 +199,14 @@ dtn_status dtn_create_geometry(const dtn_geometry_desc *desc, dtn_geometry **out
 /* Releases the geometry object and every device buffer it owns (synchronises). */
 dtn_status dtn_destroy_geometry(dtn_geometry *geom);
 
+/* Frees the device workspaces the geometry's calls have grown (they grow again,
+ * stream-ordered, on the next call) and drops a captured solve graph.
+ * Synchronises the device.  The calls that grow a workspace do so with
+ * cudaMallocAsync on their stream, by at least half its size each time, and
+ * keep it: a workload of recurring sizes settles at a high-water mark and then
+ * allocates nothing. */
+dtn_status dtn_release_workspace(dtn_geometry *geom);
+
 /* Sets the Dirichlet data g of Eq. bw01 (copied to the device). */
 dtn_status dtn_set_dirichlet(dtn_geometry *geom, const dtn_dirichlet_desc *data);
 
@@ -427,19 +435,49 @@ int32_t dtn_last_cuda_error(void);
 
 /* ---------------------------------------------------------------- serving */
 /* Continuous-batching request server (not in the paper: a serving layer over
- * dtn_solve_patches).  Queries are sets of patches with their own walk
- * budgets; they are admitted while in-flight slots and workspace memory
- * allow, run concurrently on separate streams, and complete independently.
- * Results depend only on the query (its patch ids fix every random number),
- * so a query gives the same answer alone or in a mix. */
+ * dtn_solve_patches, which relies on the independence of the patch solves,
+ * Sec. 6).  Queries are sets of patches with their own walk budgets.  A worker
+ * thread merges queued queries into batches and runs each batch on one of
+ * max_inflight slots (a stream and a private copy of the geometry's
+ * workspace); queries that arrive while batches run are admitted as slots and
+ * device memory free up, so batches of different requests overlap on the
+ * device.  Results depend only on the query (its patch ids fix every random
+ * number), so a query gives the same answer alone or in a mix.
+ * Admission by device memory: the budget is the free device memory at
+ * creation (cudaMemGetInfo) less a reserve of max(1 GiB, 5% of the device),
+ * or memory_budget if that is smaller.  A batch starts only if the slots'
+ * workspaces (what each holds now, and for the starting batch the workspace
+ * its solve reserves) stay within the budget; idle slots give theirs back when
+ * a batch would not fit otherwise, and a query that cannot fit in an empty
+ * server finishes with DTN_E_OUT_OF_MEMORY.  Slot workspaces grow
+ * stream-ordered and are kept, so a steady stream of similar queries neither
+ * frees nor allocates. */
 typedef struct dtn_server dtn_server;
 
 typedef struct {
     int32_t max_inflight;        /* concurrent batches (streams), >= 1 */
     int64_t max_batch_patches;   /* patches merged into one launch */
-    int64_t memory_budget;       /* bytes of workspace the server may hold in flight */
+    int64_t memory_budget;       /* upper limit in bytes of the budget above (0: none) */
     dtn_solve_opts opts;         /* solve options for every query */
+    int32_t split_sms;           /* 1: when opts.wos_blocks_per_sm is 0, each slot's walk launch
+                                    takes 1/max_inflight of the resident walk blocks per SM, so the
+                                    walks of several slots run side by side; 0: every walk launch
+                                    may fill the GPU (batches then overlap at kernel boundaries) */
 } dtn_server_config;
+
+/* Counters of a server (dtn_server_stats). */
+typedef struct {
+    int64_t budget_bytes;        /* admission budget */
+    int64_t device_free_bytes;   /* free device memory at creation */
+    int64_t held_bytes;          /* slot workspaces now (and batches in flight) */
+    int64_t peak_held_bytes;     /* the most the ledger has held */
+    int64_t batches;             /* finished batches */
+    int64_t queries;             /* finished queries (any status) */
+    int64_t rejected;            /* queries that could not fit the budget */
+    int32_t max_concurrent;      /* most batches in flight on the device at one time */
+    double busy_ms;              /* device time with at least one batch in flight */
+    double overlap_ms;           /* device time with two or more batches in flight */
+} dtn_server_info;
 
 /* One query: host arrays, copied at submission.  Node/panel layout as in
  * dtn_patch_batch. */
@@ -455,13 +493,22 @@ typedef struct {
 dtn_status dtn_server_create(dtn_geometry *geom, const dtn_server_config *cfg, dtn_server **out);
 /* Enqueues a query; *ticket identifies it.  Never blocks on the GPU. */
 dtn_status dtn_server_submit(dtn_server *srv, const dtn_query *q, int64_t *ticket);
-/* Non-blocking: *done = 1 once the query has finished; then neumann (host,
- * its panels_total) and, if not NULL, u_mean (host, its gamma_total) are
- * filled, and latency_s gets submit-to-completion seconds. */
+/* Non-blocking: *done = 1 once the query has finished; then latency_s (may be
+ * NULL) gets submit-to-completion seconds and the call returns the query's
+ * status: DTN_OK, or the first non-OK patch status of its patches
+ * (DTN_E_UNSUPPORTED, DTN_E_WALK_CAP, DTN_E_NOT_CONVERGED), or DTN_E_CUDA /
+ * DTN_E_OUT_OF_MEMORY when the query did not run.  Unless the query did not
+ * run, neumann (host, its panels_total; may be NULL), u_mean (host, its
+ * gamma_total; may be NULL) and patch_status (host, its n_patches; may be
+ * NULL) receive its results.  DTN_OK with *done = 0 while it runs. */
 dtn_status dtn_server_poll(dtn_server *srv, int64_t ticket, int32_t *done, double *neumann,
-                           double *u_mean, double *latency_s);
-/* Blocks until every submitted query has completed. */
+                           double *u_mean, double *latency_s, int32_t *patch_status);
+/* Blocks until every submitted query has completed; returns DTN_E_CUDA if a
+ * batch failed on the device, else DTN_OK. */
 dtn_status dtn_server_drain(dtn_server *srv);
+/* Counters and device intervals of the finished batches (CUDA events recorded
+ * on the slot streams around each batch). */
+dtn_status dtn_server_stats(dtn_server *srv, dtn_server_info *out);
 dtn_status dtn_server_destroy(dtn_server *srv);
 
 #ifdef __cplusplus

@@ -1452,6 +1452,16 @@ void or_owned(int64_t npan, const double *x, const int64_t *owner_patch, int64_t
     }
 }
 
+/* Host threads of the OpenMP loops (timing the oracle on one core). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP

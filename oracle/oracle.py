@@ -61,6 +61,7 @@ def lib():
         L.or_u01_53.argtypes = [C.c_uint32, C.c_uint32]
         L.or_u01_53.restype = C.c_double
         L.or_direction.argtypes = [C.c_double, C.c_double, C.c_int, _f64p]
+        L.or_set_num_threads.argtypes = [C.c_int]
         L.or_set_sk_self_order.argtypes = [C.c_int]
         L.or_set_sk_self_order.restype = C.c_int
         L.or_gauss_legendre.argtypes = [C.c_int, _f64p, _f64p]
@@ -403,6 +404,10 @@ def owned(x, owner_patch, centers) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().or_set_num_threads(int(n))
 
 
 def single_point(geom, data, x, a, ng1, ng2, delta, walks=0, patch=0, opts=None, U_in=None):

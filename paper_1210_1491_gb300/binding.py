@@ -81,7 +81,17 @@ class PatchResult(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("max_batch_patches", C.c_int64),
-                ("memory_budget", C.c_int64), ("opts", SolveOpts)]
+                ("memory_budget", C.c_int64), ("opts", SolveOpts), ("split_sms", C.c_int32)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("device_free_bytes", C.c_int64), ("held_bytes", C.c_int64),
+                ("peak_held_bytes", C.c_int64), ("batches", C.c_int64), ("queries", C.c_int64),
+                ("rejected", C.c_int64), ("max_concurrent", C.c_int32), ("busy_ms", C.c_double),
+                ("overlap_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Query(C.Structure):
@@ -110,7 +120,7 @@ EXPORTS = ["dtn_create_geometry", "dtn_destroy_geometry", "dtn_set_dirichlet", "
            "dtn_last_cuda_error", "dtn_server_create", "dtn_server_submit", "dtn_server_poll",
            "dtn_server_drain", "dtn_server_destroy", "dtn_stage_times", "dtn_autotune_walks",
            "dtn_wos_points_noalloc", "dtn_single_point_neumann", "dtn_eval_potential_fmm",
-           "dtn_philox_fields21"]
+           "dtn_philox_fields21", "dtn_release_workspace", "dtn_server_stats"]
 
 _lib = None
 
@@ -141,7 +151,9 @@ def load(path: str = LIB_PATH):
         "dtn_last_cuda_error": ([], i32),
         "dtn_server_create": ([vp, C.POINTER(ServerConfig), C.POINTER(vp)], i32),
         "dtn_server_submit": ([vp, C.POINTER(Query), C.POINTER(i64)], i32),
-        "dtn_server_poll": ([vp, i64, C.POINTER(i32), vp, vp, C.POINTER(dbl)], i32),
+        "dtn_server_poll": ([vp, i64, C.POINTER(i32), vp, vp, C.POINTER(dbl), vp], i32),
+        "dtn_server_stats": ([vp, C.POINTER(ServerInfo)], i32),
+        "dtn_release_workspace": ([vp], i32),
         "dtn_server_drain": ([vp], i32),
         "dtn_server_destroy": ([vp], i32),
         "dtn_stage_times": ([vp, C.POINTER(C.c_float)], i32),
@@ -275,6 +287,10 @@ class Geometry:
         ms = (C.c_float * 4)()
         _check(load().dtn_stage_times(self.handle, ms), "dtn_stage_times")
         return [float(v) for v in ms]
+
+    def release_workspace(self):
+        """dtn_release_workspace: free the device workspaces the calls have grown."""
+        _check(load().dtn_release_workspace(self.handle), "dtn_release_workspace")
 
     def close(self):
         if getattr(self, "handle", None):
@@ -537,10 +553,11 @@ class Server:
     """dtn_server_*: continuous-batching request server (host arrays in, host arrays out)."""
 
     def __init__(self, geom: Geometry, opts: SolveOpts, max_inflight=2, max_batch_patches=4096,
-                 memory_budget=0):
+                 memory_budget=0, split_sms=True):
         cfg = ServerConfig()
         cfg.max_inflight, cfg.max_batch_patches, cfg.memory_budget = int(max_inflight), int(max_batch_patches), int(memory_budget)
         cfg.opts = opts
+        cfg.split_sms = 1 if split_sms else 0
         h = C.c_void_p()
         _check(load().dtn_server_create(geom.handle, C.byref(cfg), C.byref(h)), "dtn_server_create")
         self.handle = h
@@ -560,20 +577,30 @@ class Server:
         t = C.c_int64()
         _check(load().dtn_server_submit(self.handle, C.byref(q), C.byref(t)), "dtn_server_submit")
         self._sizes[t.value] = (int(np.sum(arrs[4].astype(np.int64) * arrs[5])),
-                                int(np.sum(arrs[2].astype(np.int64) * arrs[3])))
+                                int(np.sum(arrs[2].astype(np.int64) * arrs[3])), q.n_patches)
         return t.value
 
     def poll(self, ticket: int):
-        npan, nnode = self._sizes[ticket]
+        """None while the query runs; then a dict with its status, latency and (unless
+        it did not run: DTN_E_CUDA, DTN_E_OUT_OF_MEMORY) neumann, u and patch_status."""
+        npan, nnode, npat = self._sizes[ticket]
         q = np.zeros(npan)
         u = np.zeros(nnode)
+        ps = np.zeros(npat, dtype=np.int32)
         done = C.c_int32()
         lat = C.c_double()
-        _check(load().dtn_server_poll(self.handle, ticket, C.byref(done), _ptr(q), _ptr(u), C.byref(lat)),
-               "dtn_server_poll")
+        st = load().dtn_server_poll(self.handle, ticket, C.byref(done), _ptr(q), _ptr(u), C.byref(lat), _ptr(ps))
         if not done.value:
+            _check(st, "dtn_server_poll")
             return None
-        return dict(neumann=q, u=u, latency_s=lat.value)
+        if st in (1, 2, 3):   # invalid ticket, out of memory, CUDA: no result
+            return dict(status=st, latency_s=lat.value, neumann=None, u=None, patch_status=None)
+        return dict(status=st, neumann=q, u=u, patch_status=ps, latency_s=lat.value)
+
+    def stats(self) -> dict:
+        info = ServerInfo()
+        _check(load().dtn_server_stats(self.handle, C.byref(info)), "dtn_server_stats")
+        return info.as_dict()
 
     def drain(self):
         _check(load().dtn_server_drain(self.handle), "dtn_server_drain")

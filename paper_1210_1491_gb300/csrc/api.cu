@@ -41,13 +41,43 @@ cudaError_t DevBuf::reserve(size_t n) {
         return e;
     }
     bytes = want;
+    pooled = false;
+    return cudaSuccess;
+}
+
+cudaError_t DevBuf::reserve(size_t n, cudaStream_t s) {
+    if (n <= bytes && p) return cudaSuccess;
+    const size_t want = std::max<size_t>({n, bytes + bytes / 2, 256});
+    if (p) {
+        cudaError_t e = pooled ? cudaFreeAsync(p, s) : cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMallocAsync(&p, want, s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return e;
+    }
+    bytes = want;
+    pooled = true;
     return cudaSuccess;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (pooled) {
+            // stream-ordered memory: free it once nothing on the device can use it
+            cudaDeviceSynchronize();
+            cudaFreeAsync(p, nullptr);
+            cudaStreamSynchronize(nullptr);
+        } else {
+            cudaFree(p);
+        }
+    }
     p = nullptr;
     bytes = 0;
+    pooled = false;
 }
 
 dtn_status to_status(cudaError_t e) {
@@ -323,7 +353,7 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     const size_t o_tof = off; off = al(off + (nw + 1) * 8);
     const size_t host_bytes = off;
     const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
-    cudaError_t e = g->ws.layout.reserve(off);
+    cudaError_t e = g->ws.layout.reserve(off, s);
     if (e != cudaSuccess) return e;
     std::vector<unsigned char> h(host_bytes, 0);
     std::memcpy(&h[o_goff], L.gamma_off.data(), (n + 1) * 8);
@@ -382,6 +412,41 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     D.frames = (PatchFrame *)(base + o_fr);
     return cudaSuccess;
 }
+
+}  // namespace
+
+// Device bytes a dtn_solve_patches call on this batch reserves in a fresh
+// geometry workspace (the buffers the call grows; an upper bound for a batch
+// merged from several queries, whose shape groups are shared).
+size_t solve_workspace_bytes(const dtn_patch_batch *b, const dtn_solve_opts *o, bool caps) {
+    BatchLayout L;
+    if (build_layout(b, L, caps) != DTN_OK) return 0;
+    const size_t G = (size_t)L.gamma_total, Pn = (size_t)L.panels_total, n = (size_t)L.n_patches;
+    size_t t = 40 * 256 + n * (200 + sizeof(PatchFrame)) + (size_t)(L.n_groups + L.n_wgroups) * 64;   // layout
+    t += G * (3 + 1 + 3 + 1) * 8 + Pn * (3 + 6 + 4 + 1 + 1) * 8 + n * 4;   // nodes, panels, flags
+    if (!o->u_provided) t += wos_scratch_bytes(L.gamma_total);
+    if (o->prec == DTN_PREC_MIXED) {
+        const size_t w = o->bie_kind == 1 ? 8 : 4;
+        t += (size_t)L.gmat_total * 8 + lu_shared_scratch_bytes(L) + (size_t)L.grows_total * 4 +
+             (size_t)(L.gw_total + L.vec_total) * w;
+    } else {
+        t += (size_t)L.matrix_total * 8 + lu_scratch_bytes(L, o->prec);
+    }
+    return t;
+}
+
+// Device bytes the geometry's workspaces hold now.
+size_t workspace_bytes(const dtn_geometry *g) {
+    const Workspace &W = g->ws;
+    const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
+                            &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter,
+                            &W.se_tmp, &W.tune, &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag};
+    size_t t = 0;
+    for (const DevBuf *d : bufs) t += d->bytes;
+    return t;
+}
+
+namespace {
 
 // Walk-kernel launch parameters: explicit opts fields win; fields left at 0 come
 // from the autotuner's cache for (device name, region kind, precision), else
@@ -556,6 +621,23 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
     return DTN_OK;
 }
 
+dtn_status dtn_release_workspace(dtn_geometry *g) {
+    if (!g) return DTN_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaDeviceSynchronize();
+    Workspace &W = g->ws;
+    DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm, &W.panel_aux,
+                      &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter, &W.se_tmp, &W.tune,
+                      &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag};
+    for (DevBuf *b : bufs) b->release();
+    if (g->graph_exec) {   // a captured graph holds the old pointers
+        cudaGraphExecDestroy(g->graph_exec);
+        g->graph_exec = nullptr;
+        g->graph_key.clear();
+    }
+    return DTN_OK;
+}
+
 dtn_status dtn_set_dirichlet(dtn_geometry *g, const dtn_dirichlet_desc *d) {
     if (!g || !d) return DTN_E_INVALID_ARG;
     if (wrong_device(g)) return DTN_E_INVALID_ARG;
@@ -673,26 +755,30 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     if (e != cudaSuccess) return to_status(e);
     Workspace &W = g->ws;
     const size_t G = (size_t)L.gamma_total, Pn = (size_t)L.panels_total;
-    if ((e = W.gamma_loc.reserve(G * 3 * 8)) != cudaSuccess || (e = W.gamma_w.reserve(G * 8)) != cudaSuccess ||
-        (e = W.gamma_xyz.reserve(G * 3 * 8)) != cudaSuccess || (e = W.panel_loc.reserve(Pn * 3 * 8)) != cudaSuccess ||
-        (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
-        (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.rhs.reserve(Pn * 8)) != cudaSuccess ||
-        (e = W.se_tmp.reserve(G * 8)) != cudaSuccess ||
-        (e = W.capflag.reserve((size_t)L.n_patches * sizeof(int32_t))) != cudaSuccess)
+    if ((e = W.gamma_loc.reserve(G * 3 * 8, s)) != cudaSuccess || (e = W.gamma_w.reserve(G * 8, s)) != cudaSuccess ||
+        (e = W.gamma_xyz.reserve(G * 3 * 8, s)) != cudaSuccess ||
+        (e = W.panel_loc.reserve(Pn * 3 * 8, s)) != cudaSuccess ||
+        (e = W.panel_prm.reserve(Pn * 6 * 8, s)) != cudaSuccess ||
+        (e = W.panel_aux.reserve(Pn * 4 * 8, s)) != cudaSuccess || (e = W.panel_g.reserve(Pn * 8, s)) != cudaSuccess ||
+        (e = W.rhs.reserve(Pn * 8, s)) != cudaSuccess || (e = W.se_tmp.reserve(G * 8, s)) != cudaSuccess ||
+        (e = W.capflag.reserve((size_t)L.n_patches * sizeof(int32_t), s)) != cudaSuccess ||
+        (!o->u_provided && (e = W.acc.reserve(wos_scratch_bytes(L.gamma_total), s)) != cudaSuccess))
         return to_status(e);
     const bool shared = (o->prec == DTN_PREC_MIXED);
     if (shared) {
-        if ((e = W.gmat.reserve((size_t)L.gmat_total * 8)) != cudaSuccess ||
-            (e = W.gfac.reserve(lu_shared_scratch_bytes(L))) != cudaSuccess ||
-            (e = W.gpiv.reserve((size_t)L.grows_total * 4)) != cudaSuccess ||
-            (e = W.gw.reserve((size_t)L.gw_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)))) !=
+        if ((e = W.gmat.reserve((size_t)L.gmat_total * 8, s)) != cudaSuccess ||
+            (e = W.gfac.reserve(lu_shared_scratch_bytes(L), s)) != cudaSuccess ||
+            (e = W.gpiv.reserve((size_t)L.grows_total * 4, s)) != cudaSuccess ||
+            (e = W.gw.reserve((size_t)L.gw_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)), s)) !=
                 cudaSuccess ||
-            (e = W.vec.reserve((size_t)L.vec_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)))) !=
+            (e = W.vec.reserve((size_t)L.vec_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)), s)) !=
                 cudaSuccess)
             return to_status(e);
 
-    } else if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8)) != cudaSuccess) {
-        return to_status(e);
+    } else {
+        if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8, s)) != cudaSuccess) return to_status(e);
+        const size_t lus = lu_scratch_bytes(L, o->prec);
+        if (lus && (e = W.lu64.reserve(lus, s)) != cudaSuccess) return to_status(e);
     }
     double *gxyz = r->gamma_xyz ? r->gamma_xyz : W.gamma_xyz.as<double>();
     double *gw = r->gamma_w ? r->gamma_w : W.gamma_w.as<double>();
@@ -706,13 +792,10 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         g->stages_recorded = true;
     }
     if (o->graph_capture) {
-        // every buffer the device part touches is reserved before capture, so the
-        // captured graph allocates nothing and its pointers stay valid while the
-        // key (shapes, pointers, options, data version) repeats
-        if ((e = W.acc.reserve(G * (3 * sizeof(unsigned long long) + sizeof(unsigned int)) + 64)) != cudaSuccess)
-            return to_status(e);
-        const size_t lus = shared ? 0 : lu_scratch_bytes(L, o->prec);
-        if (lus && (e = W.lu64.reserve(lus)) != cudaSuccess) return to_status(e);
+        // every buffer the device part touches is reserved above, before capture,
+        // so the captured graph allocates nothing and its pointers stay valid
+        // while the key (shapes, pointers, options, data version) repeats
+        if ((e = W.acc.reserve(wos_scratch_bytes(L.gamma_total), s)) != cudaSuccess) return to_status(e);
         std::vector<unsigned char> key;
         auto put = [&key](const void *p, size_t n) {
             const unsigned char *c = (const unsigned char *)p;

@@ -17,7 +17,14 @@ namespace dtn {
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool pooled = false;   // allocated stream-ordered (cudaMallocAsync)
+    // grow to at least n bytes (contents are not kept): cudaFree + cudaMalloc,
+    // which may synchronise the device
     cudaError_t reserve(size_t n);
+    // grow stream-ordered on s (cudaFreeAsync + cudaMallocAsync: no device-wide
+    // synchronisation), to at least 1.5x the old size, so that a workload whose
+    // sizes vary settles at a high-water mark and then allocates nothing
+    cudaError_t reserve(size_t n, cudaStream_t s);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
@@ -156,6 +163,9 @@ cudaError_t ensure_tables();
 // 1 when the current device is not the geometry's (the entry points then return
 // DTN_E_INVALID_ARG: every launch goes to the current device)
 bool wrong_device(const dtn_geometry *g);
+// workspace bytes a solve of this batch reserves, and what a geometry holds now
+size_t solve_workspace_bytes(const dtn_patch_batch *b, const dtn_solve_opts *o, bool caps);
+size_t workspace_bytes(const dtn_geometry *g);
 const double *gl_x_dev();
 const double *gl_w_dev();
 const ShTables *sh_tables_dev();
@@ -211,6 +221,8 @@ cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s);
 size_t wos_scratch_bytes(int64_t nodes);
 cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cudaStream_t s);
 cudaError_t launch_walk_cap_status(int64_t n, const int32_t *group_capped, int32_t *status, cudaStream_t s);
+// resident 128-thread walk blocks per SM of the walk kernel for this geometry and precision
+int wos_resident_blocks(const dtn_geometry *g, int prec);
 
 // mode 0: per patch, A and b (FP64 rules, or FP32 far field in mixed precision);
 // mode 1: A of each shape group's representative (FP64 rules) into A + gmat_off

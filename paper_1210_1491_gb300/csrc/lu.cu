@@ -304,7 +304,7 @@ cudaError_t launch_lu_solve(dtn_geometry *g, const BatchLayout &L, const DevLayo
         smem = head + fac;
     } else {
         DevBuf &buf = fp32 ? g->ws.lu32 : g->ws.lu64;
-        if ((e = buf.reserve(lu_scratch_bytes(L, prec))) != cudaSuccess) return e;
+        if ((e = buf.reserve(lu_scratch_bytes(L, prec), s)) != cudaSuccess) return e;
         P.scratch = buf.p;
     }
     void *fn = fp32 ? (void *)lu_kernel<float> : (void *)lu_kernel<double>;

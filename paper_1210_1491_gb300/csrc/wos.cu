@@ -534,7 +534,7 @@ size_t wos_scratch_bytes(int64_t nodes) {
 // The walk launch with its accumulators in the geometry's workspace.
 cudaError_t launch_wos(dtn_geometry *g, const WosLaunch &w, cudaStream_t s) {
     if (w.total_nodes == 0) return cudaSuccess;
-    cudaError_t e = g->ws.acc.reserve(wos_scratch_bytes(w.total_nodes));
+    cudaError_t e = g->ws.acc.reserve(wos_scratch_bytes(w.total_nodes), s);
     if (e != cudaSuccess) return e;
     return launch_wos_into(g, w, g->ws.acc.p, s);
 }
@@ -608,6 +608,24 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
         w.total_nodes, w.n_groups, w.node_off, w.walks, s1, s2, st, done, lgM1, lgM2, w.mean, w.se, w.steps, w.capped,
         w.group_capped);
     return cudaGetLastError();
+}
+
+int wos_resident_blocks(const dtn_geometry *g, int prec) {
+    const int gk = g->dg.kind;
+    const bool fp32 = (prec == DTN_PREC_MIXED);
+    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
+    const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int resident = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, kWosThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(resident, 1);
 }
 
 cudaError_t launch_walk_cap_status(int64_t n, const int32_t *group_capped, int32_t *status, cudaStream_t s) {

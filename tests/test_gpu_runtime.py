@@ -131,8 +131,11 @@ def test_walk_cap_status_and_nodes_without_estimates(prec):
 
 
 def test_not_converged_status():
-    """One refinement sweep against an unreachable tolerance: every patch
-    reports DTN_E_NOT_CONVERGED with its residual and sweep count."""
+    """Mixed precision (FP32 factors, FP64-residual refinement), one sweep
+    against an unreachable tolerance: every patch reports DTN_E_NOT_CONVERGED
+    with its residual and sweep count, and solves cleanly with the defaults.
+    The FP64 path factors in FP64 and does not refine: its status stays
+    DTN_OK with 0 sweeps whatever the tolerance."""
     wl = W.unit_ball(n_patches=3, walks=2, n_theta=8, n_phi=8, n_rings=4, n_sectors=8)
     b = wl.batch
     g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
@@ -145,9 +148,14 @@ def test_not_converged_status():
         dtn.solve_patches(g, b.centers, b.radius, hb,
                           dtn.solve_opts(prec=p, u_provided=True, max_refine_iters=1, refine_tol=1e-300), result=res)
         torch.cuda.synchronize()
-        assert np.all(res["patch_status"].cpu().numpy() == 4), p   # DTN_E_NOT_CONVERGED
-        assert np.all(res["residual"].cpu().numpy() > 0)
-        assert np.all(res["refine_iters"].cpu().numpy() <= 1)
+        st = res["patch_status"].cpu().numpy()
+        it = res["refine_iters"].cpu().numpy()
+        if p == dtn.PREC_MIXED:
+            assert np.all(st == 4), st   # DTN_E_NOT_CONVERGED
+            assert np.all(res["residual"].cpu().numpy() > 0)
+            assert np.all(it == 1)
+        else:
+            assert np.all(st == 0) and np.all(it == 0)
         dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=p, u_provided=True), result=res)
         torch.cuda.synchronize()
         assert np.all(res["patch_status"].cpu().numpy() == 0), p
