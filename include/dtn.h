@@ -411,7 +411,7 @@ dtn_status dtn_eval_dirichlet(const dtn_geometry *geom, int64_t n, const double 
 /* Autotuner (not in the paper): times the walk kernel on a sample of the batch
  * (its first 96 patches at most, at most 4096 walks per node) for every combination of
  * walk chunk {64, 128, 256, 512}, resident 128-thread blocks per SM
- * {4, 5, 6, 7} (each capped at the occupancy limit) and refill threshold
+ * {5, 6, 7, 8, 9} (each capped at the occupancy limit) and refill threshold
  * {4, 8, 12, 16}, and keeps the fastest per
  * (device name, region kind, precision) in a process-wide cache that
  * dtn_solve_patches and dtn_wos_points consult for every opts field left at 0.

@@ -1012,10 +1012,10 @@ dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const d
     if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return to_status(e); }
     dtn_tuning best{256, 0, 8, 1e30f};
     uint64_t total_steps = 0;
-    const int chunks[4] = {64, 128, 256, 512}, bpss[4] = {4, 5, 6, 7}, refills[4] = {4, 8, 12, 16};
+    const int chunks[4] = {64, 128, 256, 512}, bpss[5] = {5, 6, 7, 8, 9}, refills[4] = {4, 8, 12, 16};
     for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
         if ((e = upload_layout(g, L, chunks[ci], D, total_chunks, s)) != cudaSuccess) break;
-        for (int bi = 0; bi < 4 && e == cudaSuccess; ++bi)
+        for (int bi = 0; bi < 5 && e == cudaSuccess; ++bi)
             for (int ri = 0; ri < 4 && e == cudaSuccess; ++ri) {
                 WosLaunch w{};
                 w.n_groups = L.n_patches;

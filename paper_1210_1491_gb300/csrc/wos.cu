@@ -54,6 +54,7 @@ struct WosDev {
     double eps;
     float eps_f;           // eps rounded to FP32 on the host (FP32 walks)
     uint32_t max_steps;
+    uint32_t blk_fast;     // FP32 walks: blocks of three jumps below this index cannot reach max_steps
     uint32_t rk0[10], rk1[10];   // Philox round keys from the seed
 };
 
@@ -477,6 +478,201 @@ __global__ void __launch_bounds__(kWosThreads, 7) wos_kernel(WosDev P) {
     }
 }
 
+// FP32 walks in the bounded regions (ball, box, box minus boxes): the same
+// walks as wos_kernel<float, GK>, bit for bit, with the bookkeeping of a jump
+// moved from predicates, selects and integer counters (the int/logic pipe,
+// which throttles issue in this kernel) to FP32 arithmetic on the FMA pipe.
+// A walk carries af = 1 while it goes on and 0 once it has ended: a jump first
+// counts the distance evaluation (lst += af), then af *= sat((d - eps) 1e30),
+// which is exactly 1 for d > eps and 0 for d <= eps (d - eps rounds to the sign
+// of the difference, and any nonzero difference of these normal floats times
+// 1e30 saturates), and the walk moves by d af.  The Philox counter is the
+// block index itself.  The max_steps cap is tested once per block: a block in
+// which no lane can reach it runs the arithmetic above; one that can (rare)
+// runs the exact per-jump test.  An ended walk is absorbed unless it was cut.
+// MINB: resident blocks per SM the registers are budgeted for (8: 64 registers,
+// no spills; 9: 56 registers, a few spilled values of the refill rounds).
+template <int GK, int MINB>
+__global__ void __launch_bounds__(kWosThreads, MINB) wos_kernel_f32(WosDev P) {
+    extern __shared__ float s_boxes[];
+    __shared__ ScoreQueue<float> s_queue[kWosThreads / 32];
+    __shared__ float2 s_cs[kShPairs];
+    const float *sb = nullptr;
+    if (GK == kBoxMinusBoxes && P.g.nb <= kMaxSmemBoxes) {
+        for (int i = threadIdx.x; i < 6 * P.g.nb; i += blockDim.x) s_boxes[i] = P.g.boxes_f[i];
+        sb = s_boxes;
+    }
+    if (P.dat.kind == kHarmonicSH)
+        for (int i = threadIdx.x; i < kShPairs; i += blockDim.x) s_cs[i] = P.dat.cart[i];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const float eps = P.eps_f;
+    ScoreQueue<float> &Q = s_queue[threadIdx.x >> 5];
+    constexpr bool kRel = (GK == kBall);
+    const float ox = kRel ? P.g.c_f[0] : 0.f, oy = kRel ? P.g.c_f[1] : 0.f, oz = kRel ? P.g.c_f[2] : 0.f;
+    int qhead = 0, qcount = 0;   // warp-uniform
+    WarpScore ws;
+
+    // warp-uniform chunk state
+    int cnode = -1;
+    uint32_t cnext = 0, cend = 0;
+    uint32_t cpid = 0, cpt = 0;
+    int cf1 = 0, cf2 = 0;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    bool no_more = false;
+
+    // lane state
+    bool hw = false;     // the lane holds a walk whose end has not been handled
+    bool cut = false;    // that walk was cut at max_steps
+    float af = 0.f;      // 1 while the walk goes on, 0 once it has ended
+    float lst = 0.f;     // distance evaluations of the walk (exact below 2^24)
+    float x = 0.f, y = 0.f, z = 0.f;
+    uint32_t walk = 0, blk = 0, ppid = 0, ppt = 0;
+    int f1 = 0, f2 = 0;
+    LaneAcc acc;
+
+    for (;;) {
+        // ended walks: absorbed ones go to the queue with their absorption
+        // point, cut ones are only released
+        const bool ended = hw && af == 0.f;
+        const bool pend = ended && !cut;
+        const unsigned pm = __ballot_sync(FULL, pend);
+        if (pm) {
+            if (pend) {
+                const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
+                Q.x[e] = x + ox;
+                Q.y[e] = y + oy;
+                Q.z[e] = z + oz;
+                Q.node[e] = acc.node;
+                Q.f1[e] = (short)f1;
+                Q.f2[e] = (short)f2;
+            }
+            qcount += __popc(pm);
+            __syncwarp();
+            if (qcount >= 32) score_batch<float, GK>(P, sb, s_cs, Q, qhead, qcount, 32, lane, ws);
+        }
+        if (ended) {
+            hw = false;
+            cut = false;
+        }
+        // hand out walks to idle lanes
+        unsigned idle = __ballot_sync(FULL, !hw);
+        while (idle != 0u && !no_more) {
+            if (cnext >= cend) {
+                unsigned long long c = 0;
+                if (lane == 0) c = atomicAdd(P.counter, 1ull);
+                c = __shfl_sync(FULL, c, 0);
+                if (c >= (unsigned long long)P.total_chunks) {
+                    no_more = true;
+                    break;
+                }
+                const int64_t grp = find_group(P.chunk_off, P.n_groups, (int64_t)c);
+                const int64_t local = (int64_t)c - P.chunk_off[grp];
+                const int64_t cp = P.cpn[grp];
+                const int64_t k = local / cp, j = local - k * cp;
+                cnode = (int)(P.node_off[grp] + k);
+                cnext = (uint32_t)(j * P.chunk);
+                cend = (uint32_t)min(P.walks[grp], (j + 1) * (int64_t)P.chunk);
+                cpid = P.pid[grp];
+                cf1 = fixed_exponent(P.walks[grp], P.lgM1);
+                cf2 = fixed_exponent(P.walks[grp], P.lgM2);
+                cpt = P.point_id ? P.point_id[cnode] : (uint32_t)k;
+                const double *yc = P.y + 3 * (int64_t)cnode;
+                cx = (float)(yc[0] - (kRel ? P.g.c[0] : 0.0));
+                cy = (float)(yc[1] - (kRel ? P.g.c[1] : 0.0));
+                cz = (float)(yc[2] - (kRel ? P.g.c[2] : 0.0));
+            }
+            const int nidle = __popc(idle);
+            const int take = (int)min((uint32_t)nidle, cend - cnext);
+            const int rank = __popc(idle & lt_mask);
+            if (!hw && rank < take) {
+                acc.st += (uint32_t)lst;   // the length of the lane's previous walk (0 before the first)
+                if (acc.node != cnode) {
+                    acc.flush(P);
+                    acc.node = cnode;
+                }
+                walk = cnext + (uint32_t)rank;
+                blk = 0;
+                lst = 0.f;
+                ppid = cpid;
+                ppt = cpt;
+                f1 = cf1;
+                f2 = cf2;
+                x = cx;
+                y = cy;
+                z = cz;
+                af = 1.f;
+                hw = true;
+            }
+            cnext += (uint32_t)take;
+            if (take == nidle) {   // every idle lane has a walk
+                idle = 0u;
+                break;
+            }
+            idle = __ballot_sync(FULL, !hw);
+        }
+        if (idle == FULL) break;   // no lane holds a walk and no walk is left
+        const int thresh = no_more ? 32 : P.refill;
+        for (;;) {
+            // three jumps from one Philox block; lanes without a walk run it too
+            // and move by 0
+            const uint4 w = philox4x32_10_rk(make_uint4(walk, blk, ppt, ppid), P.rk0, P.rk1);
+            uint32_t f[6];
+            fields21(w, f);
+            if (!__any_sync(FULL, hw && blk >= P.blk_fast)) {
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const float d = kRel ? ball_dist_rel<GK>(P.g, x, y, z) : geo_dist<float, GK>(P.g, sb, x, y, z);
+                    lst += af;
+                    af *= __saturatef((d - eps) * 1e30f);
+                    jump(x, y, z, d * af, f[2 * h], f[2 * h + 1]);
+                }
+            } else {
+                // a lane may reach max_steps in this block: the exact test
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    const float d = kRel ? ball_dist_rel<GK>(P.g, x, y, z) : geo_dist<float, GK>(P.g, sb, x, y, z);
+                    const bool active = af != 0.f;
+                    const bool absorbed = active && d <= eps;
+                    const bool go = active && !absorbed && 3u * blk + (uint32_t)h + 1u < P.max_steps;
+                    cut = cut || (active && !absorbed && !go);
+                    lst += af;
+                    af = go ? 1.f : 0.f;
+                    jump(x, y, z, go ? d : 0.f, f[2 * h], f[2 * h + 1]);
+                }
+            }
+            ++blk;
+            if (__popc(__ballot_sync(FULL, af == 0.f)) >= thresh) break;
+        }
+    }
+    acc.st += (uint32_t)lst;   // the lane's last walk
+    acc.flush(P);
+    // the last absorbed walks (fewer than 32)
+    {
+        const bool pend = hw && af == 0.f && !cut;
+        const unsigned pm = __ballot_sync(FULL, pend);
+        if (pend) {
+            const int e = (qhead + qcount + __popc(pm & lt_mask)) & (kQueue - 1);
+            Q.x[e] = x + ox;
+            Q.y[e] = y + oy;
+            Q.z[e] = z + oz;
+            Q.node[e] = acc.node;
+            Q.f1[e] = (short)f1;
+            Q.f2[e] = (short)f2;
+        }
+        qcount += __popc(pm);
+        __syncwarp();
+        while (qcount > 0) score_batch<float, GK>(P, sb, s_cs, Q, qhead, qcount, min(qcount, 32), lane, ws);
+    }
+    if (ws.node >= 0 && lane == 0) {
+        atomicAdd(P.s1 + ws.node, (unsigned long long)ws.a1);
+        atomicAdd(P.s2 + ws.node, (unsigned long long)ws.a2);
+        atomicAdd(P.done + ws.node, ws.n);
+    }
+}
+
 __global__ void wos_finalize_kernel(int64_t n_nodes, int64_t n_groups, const int64_t *__restrict__ node_off,
                                     const int64_t *__restrict__ walks, const unsigned long long *__restrict__ s1,
                                     const unsigned long long *__restrict__ s2,
@@ -513,8 +709,21 @@ __global__ void walk_cap_status_kernel(int64_t n, const int32_t *__restrict__ gr
         status[p] = DTN_E_WALK_CAP;
 }
 
+// FP32 walks in bounded regions take wos_kernel_f32 while the float step count
+// of a walk stays exact (max_steps <= 2^24), budgeted for 9 resident blocks
+// per SM when 9 or more are asked for, else for 8
+template <int GK>
+void *wos_kernel_f32_ptr(int bps) {
+    return bps >= 9 ? (void *)wos_kernel_f32<GK, 9> : (void *)wos_kernel_f32<GK, 8>;
+}
+
 template <typename T>
-void *wos_kernel_ptr(int gk) {
+void *wos_kernel_ptr(int gk, uint64_t max_steps, int bps) {
+    if (std::is_same<T, float>::value && max_steps <= (1ull << 24)) {
+        if (gk == kBall) return wos_kernel_f32_ptr<kBall>(bps);
+        if (gk == kBox) return wos_kernel_f32_ptr<kBox>(bps);
+        if (gk == kBoxMinusBoxes) return wos_kernel_f32_ptr<kBoxMinusBoxes>(bps);
+    }
     if (gk == kBall) return (void *)wos_kernel<T, kBall>;
     if (gk == kBox) return (void *)wos_kernel<T, kBox>;
     if (gk == kHalfSpace) return (void *)wos_kernel<T, kHalfSpace>;
@@ -580,10 +789,13 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
     P.eps = w.eps;
     P.eps_f = (float)w.eps;
     P.max_steps = (uint32_t)std::min<uint64_t>(w.max_steps, 0xFFFFFFFFull);
+    // a block of jumps 3 blk + 1 .. 3 blk + 3 can reach max_steps once 3 blk + 3 >= max_steps
+    P.blk_fast = P.max_steps >= 3u ? (P.max_steps - 1u) / 3u : 0u;
     philox_round_keys(w.seed, P.rk0, P.rk1);
     const int gk = g->dg.kind;
     const bool fp32 = (w.prec == DTN_PREC_MIXED);
-    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
+    void *fn = fp32 ? wos_kernel_ptr<float>(gk, P.max_steps, w.blocks_per_sm)
+                    : wos_kernel_ptr<double>(gk, P.max_steps, w.blocks_per_sm);
     const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
     if (smem > 48 * 1024) {
         if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -613,7 +825,7 @@ cudaError_t launch_wos_into(dtn_geometry *g, const WosLaunch &w, void *acc, cuda
 int wos_resident_blocks(const dtn_geometry *g, int prec) {
     const int gk = g->dg.kind;
     const bool fp32 = (prec == DTN_PREC_MIXED);
-    void *fn = fp32 ? wos_kernel_ptr<float>(gk) : wos_kernel_ptr<double>(gk);
+    void *fn = fp32 ? wos_kernel_ptr<float>(gk, 1000000, 0) : wos_kernel_ptr<double>(gk, 1000000, 0);
     const size_t smem = (gk == kBoxMinusBoxes && fp32 && g->dg.nb <= kMaxSmemBoxes) ? 6 * sizeof(float) * g->dg.nb : 0;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
