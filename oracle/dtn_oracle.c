@@ -436,17 +436,45 @@ void or_wos_points(const or_geom *g, const or_data *dat, int64_t n, const double
 
 /* ================================================================ patches */
 /* Patch kinds: 0 flat disk (S lies in one plane face), 1 spherical cap (S lies
- * on the boundary sphere of a ball domain).  Local frame (t1, t2, n): n is the
+ * on the boundary sphere of a ball domain), 2 wrapped box patch (the ball
+ * about a point of an obstacle box's face meets several faces of that box: S
+ * is made of face pieces, reading R15).  Local frame (t1, t2, n): n is the
  * outward normal of the region at c; t1 = normalised projection of the
  * coordinate axis least aligned with n (lowest index on ties); t2 = n x t1. */
+#define OR_MAX_PIECES 6
+#define OR_MAX_SUB 16
+
+/* One piece of a wrapped patch: a face rectangle of the box cut by the ball,
+ * i.e. rectangle intersect disk (the ball's slice of the face plane), a convex
+ * region described in polar coordinates (rho, phi) about P, its point nearest
+ * the disk centre: rho <= rho_max(phi) for phi in [sub[0], sub[nsub]].  The
+ * angle range is cut at the angles where rho_max changes from one rectangle
+ * side or the circle to another, so rho_max is smooth between cuts. */
+typedef struct {
+    int ax, side;             /* the face: coordinate axis, 0 the lo face, 1 the hi face */
+    int ua, va;               /* in-plane axes, ua < va */
+    double fv;                /* the plane's coordinate along ax */
+    double rlo[2], rhi[2];    /* the face rectangle in (ua, va) */
+    double cf[2], rf;         /* the ball's slice of the plane: centre, radius */
+    double P[2];              /* polar origin */
+    int onlo[2], onhi[2];     /* P lies on the rectangle side u = rlo / rhi (then that side
+                                 bounds no ray of the range) */
+    int nsub;                 /* sub-ranges of the angle */
+    double sub[OR_MAX_SUB + 1];
+    double area;
+} or_piece;
+
 typedef struct {
     int kind;
     double c[3], n[3], t1[3], t2[3];
     double a;
     double R, sc[3];   /* cap: signed sphere radius (the sphere's centre is at c - R n:
                           R > 0 for a ball region, R < 0 outside a sphere) and centre */
-    double theta_max;  /* hemisphere polar range measured from -n */
+    double theta_max;  /* hemisphere polar range measured from -n (kinds 0, 1) */
     double umax;       /* panel radial parameter range: a (disk) or psi_max (cap) */
+    double blo[3], bhi[3];   /* wrapped patch: the obstacle box */
+    int npiece;
+    or_piece piece[OR_MAX_PIECES];
 } or_patch;
 
 static void cross3(const double a[3], const double b[3], double c[3])
@@ -468,6 +496,169 @@ static void frame_from_normal(or_patch *p)
     double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     for (int i = 0; i < 3; ++i) p->t1[i] = t[i] / tn;
     cross3(p->n, p->t1, p->t2);
+}
+
+/* ----------------------------------------------------- wrapped box patches */
+/* rho_max(phi) of a piece: the distance from P along (cos phi, sin phi) to the
+ * circle, or to a rectangle side if one is nearer (sides through P excepted). */
+static double piece_rho(const or_piece *q, double ph)
+{
+    const double e[2] = {cos(ph), sin(ph)};
+    const double w0 = q->P[0] - q->cf[0], w1 = q->P[1] - q->cf[1];
+    const double we = w0 * e[0] + w1 * e[1], ww = w0 * w0 + w1 * w1;
+    double r = -we + sqrt(fmax(0.0, we * we - ww + q->rf * q->rf));
+    for (int k = 0; k < 2; ++k) {
+        if (e[k] > 0.0 && !q->onhi[k]) r = fmin(r, (q->rhi[k] - q->P[k]) / e[k]);
+        if (e[k] < 0.0 && !q->onlo[k]) r = fmin(r, (q->rlo[k] - q->P[k]) / e[k]);
+    }
+    return r;
+}
+
+static int cmp_double(const void *x, const void *y)
+{
+    const double a = *(const double *)x, b = *(const double *)y;
+    return (a > b) - (a < b);
+}
+
+/* The piece of box face f (axis f/2, lo face for f even) inside the ball
+ * B(c, a); 0 if the ball does not meet the closed face rectangle. */
+static int make_piece(const double lo[3], const double hi[3], int f, const double c[3], double a,
+                      or_piece *q)
+{
+    memset(q, 0, sizeof(*q));
+    q->ax = f / 2;
+    q->side = f % 2;
+    q->fv = q->side ? hi[q->ax] : lo[q->ax];
+    const double d = c[q->ax] - q->fv;
+    if (!(fabs(d) < a)) return 0;
+    q->ua = (q->ax == 0) ? 1 : 0;
+    q->va = (q->ax == 2) ? 1 : 2;
+    const int ax2[2] = {q->ua, q->va};
+    for (int k = 0; k < 2; ++k) {
+        q->rlo[k] = lo[ax2[k]];
+        q->rhi[k] = hi[ax2[k]];
+        q->cf[k] = c[ax2[k]];
+        q->P[k] = fmin(fmax(q->cf[k], q->rlo[k]), q->rhi[k]);
+        q->onlo[k] = (q->P[k] == q->rlo[k]);
+        q->onhi[k] = (q->P[k] == q->rhi[k]);
+    }
+    q->rf = sqrt(a * a - d * d);
+    const double dP = hypot(q->P[0] - q->cf[0], q->P[1] - q->cf[1]);
+    if (!(dP < q->rf)) return 0;
+    /* the angles of the rays from P into the rectangle: every side through P
+     * halves the range (quarter at a corner) */
+    double ph0 = 0.0, ph1 = 2.0 * OR_PI;
+    if (q->onlo[0] && q->onlo[1]) { ph0 = 0.0; ph1 = 0.5 * OR_PI; }
+    else if (q->onhi[0] && q->onlo[1]) { ph0 = 0.5 * OR_PI; ph1 = OR_PI; }
+    else if (q->onhi[0] && q->onhi[1]) { ph0 = OR_PI; ph1 = 1.5 * OR_PI; }
+    else if (q->onlo[0] && q->onhi[1]) { ph0 = 1.5 * OR_PI; ph1 = 2.0 * OR_PI; }
+    else if (q->onlo[0]) { ph0 = -0.5 * OR_PI; ph1 = 0.5 * OR_PI; }
+    else if (q->onhi[0]) { ph0 = 0.5 * OR_PI; ph1 = 1.5 * OR_PI; }
+    else if (q->onlo[1]) { ph0 = 0.0; ph1 = OR_PI; }
+    else if (q->onhi[1]) { ph0 = OR_PI; ph1 = 2.0 * OR_PI; }
+    /* cuts: the directions of the rectangle corners inside the disk and of the
+     * points where the circle crosses a rectangle side */
+    double cut[12];
+    int nc = 0;
+    double pts[12][2];
+    int np = 0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const double Q[2] = {i ? q->rhi[0] : q->rlo[0], j ? q->rhi[1] : q->rlo[1]};
+            if (hypot(Q[0] - q->cf[0], Q[1] - q->cf[1]) < q->rf) { pts[np][0] = Q[0]; pts[np][1] = Q[1]; ++np; }
+        }
+    for (int k = 0; k < 2; ++k) {        /* sides u_k = const */
+        const int o = 1 - k;
+        for (int sd = 0; sd < 2; ++sd) {
+            const double uk = sd ? q->rhi[k] : q->rlo[k];
+            const double h2 = q->rf * q->rf - (uk - q->cf[k]) * (uk - q->cf[k]);
+            if (!(h2 > 0.0)) continue;
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double vo = q->cf[o] + sg * sqrt(h2);
+                if (vo > q->rlo[o] && vo < q->rhi[o]) {
+                    pts[np][k] = uk; pts[np][o] = vo; ++np;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < np; ++i) {
+        const double dx = pts[i][0] - q->P[0], dy = pts[i][1] - q->P[1];
+        if (hypot(dx, dy) < 1e-12 * q->rf) continue;
+        double ang = atan2(dy, dx);
+        while (ang < ph0) ang += 2.0 * OR_PI;
+        while (ang >= ph0 + 2.0 * OR_PI) ang -= 2.0 * OR_PI;
+        if (ang > ph0 + 1e-12 && ang < ph1 - 1e-12) cut[nc++] = ang;
+    }
+    qsort(cut, nc, sizeof(double), cmp_double);
+    q->sub[0] = ph0;
+    q->nsub = 0;
+    for (int i = 0; i < nc; ++i)
+        if (cut[i] - q->sub[q->nsub] > 1e-12) q->sub[++q->nsub] = cut[i];
+    if (ph1 - q->sub[q->nsub] > 1e-12) q->sub[++q->nsub] = ph1;
+    else q->sub[q->nsub] = ph1;
+    /* area: int 1/2 rho_max^2 dphi, 32-point Gauss per sub-range */
+    double gx[32], gw[32];
+    or_gauss_legendre(32, gx, gw);
+    q->area = 0.0;
+    for (int j = 0; j < q->nsub; ++j) {
+        const double h = 0.5 * (q->sub[j + 1] - q->sub[j]), m = 0.5 * (q->sub[j + 1] + q->sub[j]);
+        for (int i = 0; i < 32; ++i) {
+            const double r = piece_rho(q, m + h * gx[i]);
+            q->area += gw[i] * h * 0.5 * r * r;
+        }
+    }
+    return 1;
+}
+
+/* Point of the hemisphere Gamma at polar angle th (from -n) and azimuth ph. */
+static void arc_point(const or_patch *p, double th, double ph, double y[3])
+{
+    const double L[3] = {p->a * sin(th) * cos(ph), p->a * sin(th) * sin(ph), -p->a * cos(th)};
+    for (int i = 0; i < 3; ++i) y[i] = p->c[i] + L[0] * p->t1[i] + L[1] * p->t2[i] + L[2] * p->n[i];
+}
+
+static int in_box(const double lo[3], const double hi[3], const double y[3])
+{
+    return y[0] >= lo[0] && y[0] <= hi[0] && y[1] >= lo[1] && y[1] <= hi[1] && y[2] >= lo[2] && y[2] <= hi[2];
+}
+
+/* Wrapped patch (R4): theta_max(ph) is where the great-circle arc from the
+ * pole -n at azimuth ph first leaves the region, i.e. enters the box.  The
+ * arc lies outside the box for theta < pi/2 (the box is on the +n side of the
+ * face plane); on [pi/2, pi] it is sampled at 4096 points and the first entry
+ * bracketed and bisected to 1e-15.  *star = 0 if a later sample is outside the
+ * box again (the arc re-enters the region: Gamma is not star-shaped about the
+ * pole, and the patch is not supported). */
+static double theta_max_box(const or_patch *p, double ph, int *star)
+{
+    const int M = 4096;
+    double y[3];
+    double th_in = -1.0, th_out = 0.5 * OR_PI;
+    for (int m = 0; m <= M; ++m) {
+        const double th = 0.5 * OR_PI * (1.0 + (double)m / M);
+        arc_point(p, th, ph, y);
+        const int in = in_box(p->blo, p->bhi, y);
+        if (th_in < 0.0) {
+            if (in) th_in = th;
+            else th_out = th;
+        } else if (!in) {
+            *star = 0;
+        }
+    }
+    if (th_in < 0.0) {   /* never enters the box: the arc runs out of the ball's reach */
+        *star = 0;
+        return OR_PI;
+    }
+    if (th_in == 0.5 * OR_PI) return th_in;
+    double lo = th_out, hi = th_in;   /* lo outside, hi inside */
+    while (hi - lo > 1e-15) {
+        const double mid = 0.5 * (lo + hi);
+        arc_point(p, mid, ph, y);
+        if (in_box(p->blo, p->bhi, y)) hi = mid;
+        else lo = mid;
+        if (mid == lo && mid == hi) break;
+    }
+    return hi;
 }
 
 /* Returns 0 on success, -1 if the ball about c meets more than one plane face
@@ -561,14 +752,33 @@ int or_patch_frame(const or_geom *g, const double c[3], double a, or_patch *p)
         }
     } else {
         const double *lo = g->boxes + 6 * bw, *hi = lo + 3;
-        for (int i = 0; i < 3; ++i)
-            if (i != ax && (c[i] - lo[i] <= a || hi[i] - c[i] <= a)) return -1;
-        /* the ball must not reach the opposite face of the same box */
-        if (hi[ax] - lo[ax] <= a) return -1;
+        /* the ball must not reach the outer box (another conductor) */
         for (int f = 0; f < 6; ++f) {
             int fx = f / 2;
             double d = (f % 2 == 0) ? c[fx] - g->lo[fx] : g->hi[fx] - c[fx];
             if (d <= a) return -1;
+        }
+        int wrap = (hi[ax] - lo[ax] <= a);
+        for (int i = 0; i < 3; ++i)
+            if (i != ax && (c[i] - lo[i] <= a || hi[i] - c[i] <= a)) wrap = 1;
+        if (wrap) {
+            /* the ball meets further faces of this box: a wrapped patch made of
+             * the face pieces inside the ball (R15), with Gamma star-shaped about
+             * the pole */
+            p->kind = 2;
+            for (int i = 0; i < 3; ++i) { p->blo[i] = lo[i]; p->bhi[i] = hi[i]; }
+            p->npiece = 0;
+            for (int f = 0; f < 6; ++f) {
+                /* the face containing c first, then the others in face order */
+                int ff = (f == 0) ? bf : (f <= bf ? f - 1 : f);
+                or_piece q;
+                if (make_piece(lo, hi, ff, c, a, &q)) {
+                    if (q.nsub > OR_MAX_SUB) return -1;
+                    p->piece[p->npiece++] = q;
+                }
+            }
+            p->theta_max = 0.0;
+            p->umax = 0.0;
         }
     }
     if (g->kind == 2) {
@@ -583,6 +793,12 @@ int or_patch_frame(const or_geom *g, const double c[3], double a, or_patch *p)
             if (sqrt(s) <= a) return -1;
         }
     }
+    if (p->kind == 2) {
+        /* Gamma must be star-shaped about the pole: probe 256 azimuths */
+        int star = 1;
+        for (int j = 0; j < 256 && star; ++j) theta_max_box(p, 2.0 * OR_PI * (j + 0.5) / 256, &star);
+        if (!star) return -1;
+    }
     return 0;
 }
 
@@ -591,7 +807,8 @@ static void local_to_global(const or_patch *p, const double L[3], double y[3])
     for (int i = 0; i < 3; ++i) y[i] = p->c[i] + L[0] * p->t1[i] + L[1] * p->t2[i] + L[2] * p->n[i];
 }
 
-/* Hemisphere nodes (Eq. bw85 generalised to theta in [0, theta_max]):
+/* Hemisphere nodes (Eq. bw85 generalised to theta in [0, theta_max]; on a
+ * wrapped patch theta_max depends on the azimuth, reading R4):
  * theta_i = (theta_max/2)(xi_i + 1), phi_j = pi (xi_j + 1), node index i*nphi + j,
  * local position a (sin th cos ph, sin th sin ph, -cos th), weight
  * w_i w_j (theta_max/2) pi a^2 sin th_i (the area element of Eq. bw83). */
@@ -601,26 +818,52 @@ void or_gamma_nodes(const or_patch *p, int nt, int nph, double *Yloc, double *yg
     double *xp = malloc(sizeof(double) * nph), *wp = malloc(sizeof(double) * nph);
     or_gauss_legendre(nt, xt, wt);
     or_gauss_legendre(nph, xp, wp);
-    for (int i = 0; i < nt; ++i) {
-        double th = 0.5 * p->theta_max * (xt[i] + 1.0);
-        for (int j = 0; j < nph; ++j) {
-            double ph = OR_PI * (xp[j] + 1.0);
+    for (int j = 0; j < nph; ++j) {
+        double ph = OR_PI * (xp[j] + 1.0);
+        /* polar range of this azimuth: fixed (kinds 0, 1) or theta_max(ph) (kind 2) */
+        int star = 1;
+        double tmax = (p->kind == 2) ? theta_max_box(p, ph, &star) : p->theta_max;
+        for (int i = 0; i < nt; ++i) {
+            double th = 0.5 * tmax * (xt[i] + 1.0);
             int k = i * nph + j;
             double L[3] = {p->a * sin(th) * cos(ph), p->a * sin(th) * sin(ph), -p->a * cos(th)};
             if (Yloc) { Yloc[3 * k] = L[0]; Yloc[3 * k + 1] = L[1]; Yloc[3 * k + 2] = L[2]; }
             if (yglob) local_to_global(p, L, yglob + 3 * k);
-            W[k] = wt[i] * wp[j] * 0.5 * p->theta_max * OR_PI * p->a * p->a * sin(th);
+            W[k] = wt[i] * wp[j] * 0.5 * tmax * OR_PI * p->a * p->a * sin(th);
         }
     }
     free(xt); free(wt); free(xp); free(wp);
 }
 
-/* Point of the patch at parameters (u, v), local coordinates, its unit normal
- * (local) and the area Jacobian.  Disk: Y = u (cos v, sin v, 0), J = u.
+/* Point of the patch at parameters (u, v) (of piece `piece` on a wrapped patch),
+ * local coordinates, its unit normal (local) and the area Jacobian.  Disk:
+ * Y = u (cos v, sin v, 0), J = u.
  * Cap: Y = (R sin u cos v, R sin u sin v, -2R sin^2(u/2)), n = (sin u cos v,
  * sin u sin v, cos u), J = R^2 sin u. */
-static void patch_point(const or_patch *p, double u, double v, double Y[3], double nl[3], double *J)
+static void patch_point(const or_patch *p, int piece, double u, double v, double Y[3], double nl[3], double *J)
 {
+    if (p->kind == 2) {
+        /* piece of a wrapped patch: u = rho / rho_max(v), v = phi; the point
+         * P + u rho_max(v) (cos v, sin v) of the face plane; J = u rho_max(v)^2;
+         * the normal points into the box (outward of the region) */
+        const or_piece *q = &p->piece[piece];
+        const double r = piece_rho(q, v);
+        double y[3], ng[3] = {0.0, 0.0, 0.0};
+        y[q->ax] = q->fv;
+        y[q->ua] = q->P[0] + u * r * cos(v);
+        y[q->va] = q->P[1] + u * r * sin(v);
+        ng[q->ax] = q->side ? -1.0 : 1.0;
+        const double d[3] = {y[0] - p->c[0], y[1] - p->c[1], y[2] - p->c[2]};
+        Y[0] = d[0] * p->t1[0] + d[1] * p->t1[1] + d[2] * p->t1[2];
+        Y[1] = d[0] * p->t2[0] + d[1] * p->t2[1] + d[2] * p->t2[2];
+        Y[2] = d[0] * p->n[0] + d[1] * p->n[1] + d[2] * p->n[2];
+        nl[0] = ng[0] * p->t1[0] + ng[1] * p->t1[1] + ng[2] * p->t1[2];
+        nl[1] = ng[0] * p->t2[0] + ng[1] * p->t2[1] + ng[2] * p->t2[2];
+        nl[2] = ng[0] * p->n[0] + ng[1] * p->n[1] + ng[2] * p->n[2];
+        *J = u * r * r;
+        return;
+    }
+    (void)piece;
     if (p->kind == 0) {
         Y[0] = u * cos(v); Y[1] = u * sin(v); Y[2] = 0.0;
         nl[0] = 0.0; nl[1] = 0.0; nl[2] = 1.0;
@@ -636,10 +879,76 @@ static void patch_point(const or_patch *p, double u, double v, double Y[3], doub
 /* Panels: ring r in [0,nr), sector s in [0,ns), index r*ns + s; parameter box
  * u in [r umax/nr, (r+1) umax/nr], v in [s 2pi/ns, (s+1) 2pi/ns].
  * Collocation point = the panel's area centroid (disk), or the radial projection
- * of its area centroid onto the sphere (cap).  prm = (u0, u1, v0, v1, uc, vc). */
-void or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, double *nglob,
-               double *area, double *prm)
+ * of its area centroid onto the sphere (cap).  prm = (u0, u1, v0, v1, uc, vc,
+ * piece), OR_PRM values per panel.
+ * Wrapped patch (kind 2, R8): the ns sectors are shared among the sub-ranges of
+ * all pieces (pieces in order, sub-ranges by angle): one each, then one at a
+ * time to the sub-range with the largest area per sector (lowest index on
+ * ties), and a sub-range's sectors split its angle evenly; rings split u =
+ * rho / rho_max in [0, 1] evenly; the collocation point is the image of the
+ * parameter box's midpoint.  Returns -1 if ns is below the number of
+ * sub-ranges. */
+#define OR_PRM 7
+int or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, double *nglob,
+              double *area, double *prm)
 {
+    if (p->kind == 2) {
+        int nsr = 0, pc[OR_MAX_PIECES * OR_MAX_SUB], sj[OR_MAX_PIECES * OR_MAX_SUB], cnt[OR_MAX_PIECES * OR_MAX_SUB];
+        double sa[OR_MAX_PIECES * OR_MAX_SUB];
+        double gx[32], gw[32];
+        or_gauss_legendre(32, gx, gw);
+        for (int k = 0; k < p->npiece; ++k)
+            for (int j = 0; j < p->piece[k].nsub; ++j) {
+                const or_piece *q = &p->piece[k];
+                const double h = 0.5 * (q->sub[j + 1] - q->sub[j]), m = 0.5 * (q->sub[j + 1] + q->sub[j]);
+                double A = 0.0;
+                for (int i = 0; i < 32; ++i) {
+                    const double r = piece_rho(q, m + h * gx[i]);
+                    A += gw[i] * h * 0.5 * r * r;
+                }
+                pc[nsr] = k; sj[nsr] = j; sa[nsr] = A; cnt[nsr] = 1; ++nsr;
+            }
+        if (ns < nsr) return -1;
+        for (int extra = ns - nsr; extra > 0; --extra) {
+            int best = 0;
+            for (int t = 1; t < nsr; ++t)
+                if (sa[t] / cnt[t] > sa[best] / cnt[best]) best = t;
+            cnt[best] += 1;
+        }
+        int sector = 0;
+        for (int t = 0; t < nsr; ++t) {
+            const or_piece *q = &p->piece[pc[t]];
+            const double a0 = q->sub[sj[t]], a1 = q->sub[sj[t] + 1];
+            for (int m = 0; m < cnt[t]; ++m, ++sector) {
+                const double v0 = a0 + (a1 - a0) * m / cnt[t], v1 = a0 + (a1 - a0) * (m + 1) / cnt[t];
+                const double vc = 0.5 * (v0 + v1);
+                /* int_{v0}^{v1} rho_max^2 dv, for the panel areas */
+                const double h = 0.5 * (v1 - v0);
+                double R2 = 0.0;
+                for (int i = 0; i < 32; ++i) {
+                    const double r = piece_rho(q, vc + h * gx[i]);
+                    R2 += gw[i] * h * r * r;
+                }
+                for (int r = 0; r < nr; ++r) {
+                    const int k = r * ns + sector;
+                    const double u0 = (double)r / nr, u1 = (double)(r + 1) / nr, uc = 0.5 * (u0 + u1);
+                    double Y[3], nl[3], J;
+                    patch_point(p, pc[t], uc, vc, Y, nl, &J);
+                    if (Xloc) { Xloc[3 * k] = Y[0]; Xloc[3 * k + 1] = Y[1]; Xloc[3 * k + 2] = Y[2]; }
+                    if (xglob) local_to_global(p, Y, xglob + 3 * k);
+                    if (nglob)
+                        for (int i = 0; i < 3; ++i)
+                            nglob[3 * k + i] = nl[0] * p->t1[i] + nl[1] * p->t2[i] + nl[2] * p->n[i];
+                    area[k] = 0.5 * (u1 * u1 - u0 * u0) * R2;
+                    if (prm) {
+                        double *w = prm + OR_PRM * k;
+                        w[0] = u0; w[1] = u1; w[2] = v0; w[3] = v1; w[4] = uc; w[5] = vc; w[6] = pc[t];
+                    }
+                }
+            }
+        }
+        return 0;
+    }
     double du = p->umax / nr, dv = 2.0 * OR_PI / ns;
     double sinc = sin(0.5 * dv) / (0.5 * dv);
     for (int r = 0; r < nr; ++r) {
@@ -658,7 +967,7 @@ void or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, d
                 A = p->R * p->R * (cos(u0) - cos(u1)) * dv;
             }
             double Y[3], nl[3], J;
-            patch_point(p, uc, vc, Y, nl, &J);
+            patch_point(p, 0, uc, vc, Y, nl, &J);
             if (Xloc) { Xloc[3 * k] = Y[0]; Xloc[3 * k + 1] = Y[1]; Xloc[3 * k + 2] = Y[2]; }
             if (xglob) local_to_global(p, Y, xglob + 3 * k);
             if (nglob)
@@ -666,11 +975,12 @@ void or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, d
                     nglob[3 * k + i] = nl[0] * p->t1[i] + nl[1] * p->t2[i] + nl[2] * p->n[i];
             area[k] = A;
             if (prm) {
-                double *q = prm + 6 * k;
-                q[0] = u0; q[1] = u1; q[2] = v0; q[3] = v1; q[4] = uc; q[5] = vc;
+                double *q = prm + OR_PRM * k;
+                q[0] = u0; q[1] = u1; q[2] = v0; q[3] = v1; q[4] = uc; q[5] = vc; q[6] = 0.0;
             }
         }
     }
+    return 0;
 }
 
 /* ======================================================= Green's functions */
@@ -845,6 +1155,7 @@ typedef struct {
     double gx;          /* g at the collocation point (kinds 1, 4) */
     double nx[3];       /* normal at X (kinds 4, 5) */
     double ga[3];       /* tangential gradient of g at X, l(Y) = gx + ga.(Y - X) (kind 4) */
+    int piece;          /* wrapped patch: the piece the panel lies on */
 } quad_ctx;
 
 static double gl10_x[10], gl10_w[10];
@@ -861,7 +1172,7 @@ static void gl10_init(void)
 static double integrand(const quad_ctx *c, double u, double v)
 {
     double Y[3], nl[3], J;
-    patch_point(c->p, u, v, Y, nl, &J);
+    patch_point(c->p, c->piece, u, v, Y, nl, &J);
     if (c->kind == 0) return or_green(c->p->a, c->X, Y) * J;
     if (c->kind == 4 || c->kind == 5) {
         /* dG/dn_x(X, Y) = n_x . grad_X G(X, Y) = n_x . (grad_y G)(Y, X), G symmetric */
@@ -1006,7 +1317,7 @@ static double duffy_triangle(const quad_ctx *c, const double S[2], const double 
  * collocation point lies on this panel) the box is cut into four triangles
  * from the singular parameter point and each is integrated through the Duffy
  * map.  `rtol` is relative to area / (4 pi max(distance, diameter)). */
-static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *sing, double rtol);
+static double panel_integral_ctx(quad_ctx c, const double prm[7], const double *sing, double rtol);
 
 /* Gauss order per direction of the self-panel rule of the second-kind
  * integrands (see panel_integral_ctx).  Set before calls, not during them. */
@@ -1020,7 +1331,7 @@ int or_set_sk_self_order(int n)
 }
 
 double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const double X[3],
-                         const double prm[6], const double *sing, double rtol)
+                         const double prm[7], const double *sing, double rtol)
 {
     quad_ctx c;
     memset(&c, 0, sizeof(c));
@@ -1034,18 +1345,35 @@ double or_panel_integral(const or_patch *p, const or_data *dat, int kind, const 
     return panel_integral_ctx(c, prm, sing, rtol);
 }
 
-static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *sing, double rtol)
+static double panel_integral_ctx(quad_ctx c, const double prm[7], const double *sing, double rtol)
 {
     gl10_init();
     const or_patch *p = c.p;
     const double *X = c.X;
     double u0 = prm[0], u1 = prm[1], v0 = prm[2], v1 = prm[3];
+    c.piece = (p->kind == 2) ? (int)prm[6] : 0;
     double Yc[3], nl[3], J;
-    patch_point(p, prm[4], prm[5], Yc, nl, &J);
+    patch_point(p, c.piece, prm[4], prm[5], Yc, nl, &J);
     double d = sqrt((X[0] - Yc[0]) * (X[0] - Yc[0]) + (X[1] - Yc[1]) * (X[1] - Yc[1]) +
                     (X[2] - Yc[2]) * (X[2] - Yc[2]));
     double diam, area;
-    if (p->kind == 0) {
+    if (p->kind == 2) {
+        /* the largest distance between the panel's corners and edge midpoints,
+         * and an upper bound of its area */
+        double pts[8][3], nn[3], Jd;
+        const double us[3] = {u0, 0.5 * (u0 + u1), u1}, vs[3] = {v0, 0.5 * (v0 + v1), v1};
+        int m = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (!(i == 1 && j == 1)) patch_point(p, c.piece, us[i], vs[j], pts[m++], nn, &Jd);
+        diam = 0.0;
+        for (int i = 0; i < 8; ++i)
+            for (int j = i + 1; j < 8; ++j)
+                diam = fmax(diam, sqrt((pts[i][0] - pts[j][0]) * (pts[i][0] - pts[j][0]) +
+                                       (pts[i][1] - pts[j][1]) * (pts[i][1] - pts[j][1]) +
+                                       (pts[i][2] - pts[j][2]) * (pts[i][2] - pts[j][2])));
+        area = diam * diam;
+    } else if (p->kind == 0) {
         diam = (u1 - u0) + u1 * (v1 - v0);
         area = 0.5 * (u1 * u1 - u0 * u0) * (v1 - v0);
     } else {
@@ -1073,12 +1401,12 @@ static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *
         double gxs[64], gws[64];
         or_gauss_legendre(NQ, gxs, gws);
         double PS[3], nn[3], Jd;
-        patch_point(p, S[0], S[1], PS, nn, &Jd);
+        patch_point(p, c.piece, S[0], S[1], PS, nn, &Jd);
         for (int e = 0; e < 4; ++e) {
           /* the far edge cut into m pieces no longer than the triangle's height */
           double PA[3], PB[3];
-          patch_point(p, cor[e][0], cor[e][1], PA, nn, &Jd);
-          patch_point(p, cor[e + 1][0], cor[e + 1][1], PB, nn, &Jd);
+          patch_point(p, c.piece, cor[e][0], cor[e][1], PA, nn, &Jd);
+          patch_point(p, c.piece, cor[e + 1][0], cor[e + 1][1], PB, nn, &Jd);
           double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
           double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
           double cr[3];
@@ -1128,14 +1456,17 @@ static double panel_integral_ctx(quad_ctx c, const double prm[6], const double *
  * over the hemisphere nodes and U_k are the walk estimates of u there.  On a
  * plane through c both terms of dG/dn_y vanish, so the S integral is zero for
  * flat patches. */
-void or_assemble(const or_patch *p, const or_data *dat, int nr, int ns, int nt, int nph,
-                 const double *U, double rtol, double *A, double *b)
+int or_assemble(const or_patch *p, const or_data *dat, int nr, int ns, int nt, int nph,
+                const double *U, double rtol, double *A, double *b)
 {
     int n = nr * ns, P = nt * nph;
     double *Xl = malloc(sizeof(double) * 3 * n), *xg = malloc(sizeof(double) * 3 * n);
-    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * 6 * n);
+    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * OR_PRM * n);
     double *Yl = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
-    or_panels(p, nr, ns, Xl, xg, NULL, ar, prm);
+    if (or_panels(p, nr, ns, Xl, xg, NULL, ar, prm) != 0) {
+        free(Xl); free(xg); free(ar); free(prm); free(Yl); free(W);
+        return -1;
+    }
     or_gamma_nodes(p, nt, nph, Yl, NULL, W);
     gl10_init();
 #pragma omp parallel for schedule(dynamic, 1)
@@ -1143,16 +1474,19 @@ void or_assemble(const or_patch *p, const or_data *dat, int nr, int ns, int nt, 
         double gxi = or_dirichlet(dat, xg + 3 * i);
         double bi = 0.0;
         for (int j = 0; j < n; ++j) {
-            const double *sing = (i == j) ? prm + 6 * i + 4 : NULL;
-            A[(int64_t)i * n + j] = or_panel_integral(p, dat, 0, Xl + 3 * i, prm + 6 * j, sing, rtol);
-            if (p->kind == 1)
-                bi += or_panel_integral(p, dat, 1, Xl + 3 * i, prm + 6 * j, sing, rtol);
+            const double *sing = (i == j) ? prm + OR_PRM * i + 4 : NULL;
+            A[(int64_t)i * n + j] = or_panel_integral(p, dat, 0, Xl + 3 * i, prm + OR_PRM * j, sing, rtol);
+            /* dG/dn_y vanishes on a plane through c (disk patches, and the
+             * wrapped patch's first piece, where it is integrated anyway) */
+            if (p->kind == 1 || p->kind == 2)
+                bi += or_panel_integral(p, dat, 1, Xl + 3 * i, prm + OR_PRM * j, sing, rtol);
         }
         for (int k = 0; k < P; ++k)
             bi -= W[k] * or_poisson(p->a, Xl + 3 * i, Yl + 3 * k) * (U[k] - gxi);
         b[i] = bi;
     }
     free(Xl); free(xg); free(ar); free(prm); free(Yl); free(W);
+    return 0;
 }
 
 /* ============================================= second kind, any patch */
@@ -1179,10 +1513,11 @@ int or_lu_solve(int n, double *A, double *b, double *x);
 int or_second_kind(const or_patch *p, const or_data *dat, int nt, int nph, int nr, int ns, const double *U,
                    double rtol, double *A_out, double *b_out, double *q)
 {
+    if (p->kind == 2) return -2;   /* the second kind is written for disk and cap patches */
     const int n = nr * ns, P = nt * nph;
     const double a = p->a;
     double *Xl = malloc(sizeof(double) * 3 * n), *xg = malloc(sizeof(double) * 3 * n);
-    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * 6 * n);
+    double *ar = malloc(sizeof(double) * n), *prm = malloc(sizeof(double) * OR_PRM * n);
     double *Yl = malloc(sizeof(double) * 3 * P), *W = malloc(sizeof(double) * P);
     double *A = malloc(sizeof(double) * (size_t)n * n), *b = malloc(sizeof(double) * n);
     or_panels(p, nr, ns, Xl, xg, NULL, ar, prm);
@@ -1192,9 +1527,9 @@ int or_second_kind(const or_patch *p, const or_data *dat, int nt, int nph, int n
     for (int i = 0; i < n; ++i) {
         const double *X = Xl + 3 * i;
         double Yc[3], nx[3], J;
-        patch_point(p, prm[6 * i + 4], prm[6 * i + 5], Yc, nx, &J);
+        patch_point(p, 0, prm[OR_PRM * i + 4], prm[OR_PRM * i + 5], Yc, nx, &J);
         /* unit tangents at the collocation point: along u and along v */
-        const double uc = prm[6 * i + 4], vc = prm[6 * i + 5];
+        const double uc = prm[OR_PRM * i + 4], vc = prm[OR_PRM * i + 5];
         double e1[3], e2[3] = {-sin(vc), cos(vc), 0.0};
         if (p->kind == 0) { e1[0] = cos(vc); e1[1] = sin(vc); e1[2] = 0.0; }
         else { e1[0] = cos(uc) * cos(vc); e1[1] = cos(uc) * sin(vc); e1[2] = -sin(uc); }
@@ -1216,12 +1551,12 @@ int or_second_kind(const or_patch *p, const or_data *dat, int nt, int nph, int n
         c.gx = or_dirichlet(dat, xg + 3 * i);
         double bi = 0.0;
         for (int j = 0; j < n; ++j) {
-            const double *sing = (i == j) ? prm + 6 * i + 4 : NULL;
+            const double *sing = (i == j) ? prm + OR_PRM * i + 4 : NULL;
             c.kind = 5;
-            const double dij = panel_integral_ctx(c, prm + 6 * j, sing, rtol);
+            const double dij = panel_integral_ctx(c, prm + OR_PRM * j, sing, rtol);
             A[(int64_t)i * n + j] = (i == j ? 0.5 : 0.0) - dij;
             c.kind = 4;
-            bi -= panel_integral_ctx(c, prm + 6 * j, sing, rtol);
+            bi -= panel_integral_ctx(c, prm + OR_PRM * j, sing, rtol);
         }
         for (int k = 0; k < P; ++k) {
             const double *Y = Yl + 3 * k;
@@ -1313,8 +1648,8 @@ int or_solve_patch(const or_geom *g, const or_data *dat, const double c[3], doub
     }
     if (U_out) memcpy(U_out, U, sizeof(double) * P);
     double *A = malloc(sizeof(double) * n * n), *b = malloc(sizeof(double) * n);
-    or_assemble(&p, dat, nr, ns, nt, nph, U, rtol, A, b);
-    int rc = or_lu_solve(n, A, b, q_out);
+    int rc = or_assemble(&p, dat, nr, ns, nt, nph, U, rtol, A, b);
+    if (rc == 0) rc = or_lu_solve(n, A, b, q_out);
     free(A); free(b); free(U);
     return rc;
 }

@@ -38,11 +38,24 @@ class OrWosOpts(C.Structure):
                 ("stream", C.c_int), ("score", C.c_int)]
 
 
+class OrPiece(C.Structure):
+    _fields_ = [("ax", C.c_int), ("side", C.c_int), ("ua", C.c_int), ("va", C.c_int), ("fv", C.c_double),
+                ("rlo", C.c_double * 2), ("rhi", C.c_double * 2), ("cf", C.c_double * 2), ("rf", C.c_double),
+                ("P", C.c_double * 2), ("onlo", C.c_int * 2), ("onhi", C.c_int * 2), ("nsub", C.c_int),
+                ("sub", C.c_double * 17), ("area", C.c_double)]
+
+
 class OrPatch(C.Structure):
     _fields_ = [("kind", C.c_int), ("c", C.c_double * 3), ("n", C.c_double * 3),
                 ("t1", C.c_double * 3), ("t2", C.c_double * 3), ("a", C.c_double),
                 ("R", C.c_double), ("sc", C.c_double * 3), ("theta_max", C.c_double),
-                ("umax", C.c_double)]
+                ("umax", C.c_double), ("blo", C.c_double * 3), ("bhi", C.c_double * 3),
+                ("npiece", C.c_int), ("piece", OrPiece * 6)]
+
+    def pieces(self):
+        """Wrapped patch: (face axis, side, area, sub-range cuts) of each piece."""
+        return [(self.piece[k].ax, self.piece[k].side, self.piece[k].area,
+                 list(self.piece[k].sub[: self.piece[k].nsub + 1])) for k in range(self.npiece)]
 
 
 STREAM_F64 = 0   # one Philox call per jump, 53-bit uniforms
@@ -301,8 +314,10 @@ def gamma_nodes(p: OrPatch, nt: int, nph: int):
 def panels(p: OrPatch, nr: int, ns: int):
     n = nr * ns
     Xl = np.zeros((n, 3)); xg = np.zeros((n, 3)); ng = np.zeros((n, 3))
-    ar = np.zeros(n); prm = np.zeros((n, 6))
-    lib().or_panels(C.byref(p), nr, ns, Xl, xg, ng, ar, prm)
+    ar = np.zeros(n); prm = np.zeros((n, 7))
+    rc = lib().or_panels(C.byref(p), nr, ns, Xl, xg, ng, ar, prm)
+    if rc != 0:
+        raise ValueError("or_panels: fewer sectors than the wrapped patch's sub-ranges")
     return dict(Xloc=Xl, x=xg, normal=ng, area=ar, prm=prm)
 
 
@@ -338,8 +353,10 @@ def assemble(p: OrPatch, data, nr, ns, nt, nph, U, rtol=1e-13):
     od, keep = make_data(data)
     n = nr * ns
     A = np.zeros((n, n)); b = np.zeros(n)
-    lib().or_assemble(C.byref(p), C.byref(od), nr, ns, nt, nph,
-                      np.ascontiguousarray(U, dtype=np.float64), rtol, A, b)
+    rc = lib().or_assemble(C.byref(p), C.byref(od), nr, ns, nt, nph,
+                           np.ascontiguousarray(U, dtype=np.float64), rtol, A, b)
+    if rc != 0:
+        raise ValueError("or_assemble: fewer sectors than the wrapped patch's sub-ranges")
     return A, b
 
 
