@@ -214,18 +214,19 @@ def cpu_baseline_sample(wl):
                          "sample": "first patch of the workload, full walks, assembly and solve"}}
 
 
-def run_serving(dtn, n_queries=600, seed=7, load=0.8, n_targets=100_000):
+def run_serving(dtn, n_queries=600, seed=7, loads=(0.5, 0.8), n_targets=100_000):
     """Continuous-batching server on the 200-wire geometry (resident on the device).
 
     Each query asks for the Neumann data at 1..4096 boundary points (log-uniform),
     served by wire-face patches taken in turn until their panels cover that many
     points, with 1024..16384 walks per hemisphere point (log-uniform).  The queries
     are submitted first all at once (saturated throughput), then as Poisson
-    arrivals at `load` x that rate (p50/p99 submit-to-result latency).  Admission
-    by device memory: the server's budget is the free device memory at its
-    creation less a reserve; three slots share the SMs.  Then the potential at
-    10^5 targets outside the wires, by the integral representation over all
-    served panels."""
+    arrivals at each of `loads` x that rate (p50/p99 submit-to-result latency).
+    Admission by device memory: the server's budget is the free device memory at
+    its creation less a reserve.  Three slots; each batch's walk launch may fill
+    the GPU (the lowest latency), and the saturated run is repeated with the
+    slots sharing the SMs.  Then the potential at 10^5 targets outside the wires,
+    by the integral representation over all served panels."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     wl = W.wires(n_patches=4096, walks=2048)
@@ -248,29 +249,41 @@ def run_serving(dtn, n_queries=600, seed=7, load=0.8, n_targets=100_000):
         queries.append(dict(centers=b.centers[idx], radius=b.radius[idx], n_theta=b.n_theta[idx],
                             n_phi=b.n_phi[idx], n_rings=b.n_rings[idx], n_sectors=b.n_sectors[idx],
                             walks=np.full(len(idx), walks, np.int64), patch_ids=idx.astype(np.uint32)))
-    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, split_sms=True)
-    # warm-up (first-use costs)
-    srv.submit(**queries[0])
-    srv.drain()
-    t0 = time.perf_counter()
-    for q in queries:
-        srv.submit(**q)
-    srv.drain()
-    t_sat = time.perf_counter() - t0
-    rate = load * n_queries / t_sat
-    gaps = rng.exponential(1.0 / rate, n_queries)
-    tickets = []
-    t0 = time.perf_counter()
-    for q, gap in zip(queries, gaps):
-        time.sleep(gap)
-        tickets.append(srv.submit(**q))
-    srv.drain()
-    t_poisson = time.perf_counter() - t0
-    served = [srv.poll(t) for t in tickets]
-    lat = np.array([r["latency_s"] for r in served]) * 1e3
+
+    def saturated(srv):
+        srv.submit(**queries[0])   # warm-up (first-use costs)
+        srv.drain()
+        t0 = time.perf_counter()
+        for q in queries:
+            srv.submit(**q)
+        srv.drain()
+        return time.perf_counter() - t0
+
+    split = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, split_sms=True)
+    t_split = saturated(split)
+    split_info = split.stats()
+    split.close()
+    srv = dtn.Server(g, opts, max_inflight=3, max_batch_patches=1024, split_sms=False)
+    t_sat = saturated(srv)
+    poisson = []
+    served = []
+    for load in loads:
+        rate = load * n_queries / t_sat
+        gaps = rng.exponential(1.0 / rate, n_queries)
+        tickets = []
+        t0 = time.perf_counter()
+        for q, gap in zip(queries, gaps):
+            time.sleep(gap)
+            tickets.append(srv.submit(**q))
+        srv.drain()
+        t_poisson = time.perf_counter() - t0
+        served = [srv.poll(t) for t in tickets]
+        lat = np.array([r["latency_s"] for r in served]) * 1e3
+        poisson.append({"offered_load": load, "offered_queries_per_s": rate, "queries_per_s": n_queries / t_poisson,
+                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                        "queries_not_ok": sum(1 for r in served if r["status"] != 0)})
     info = srv.stats()
     srv.close()
-    n_bad = sum(1 for r in served if r["status"] != 0)
     # potential at targets outside the wires, over every served panel: the panel
     # geometry and data of the served patches (no walks), their served Neumann data
     allq = {k: np.concatenate([q[k] for q in queries]) for k in queries[0]}
@@ -302,17 +315,18 @@ def run_serving(dtn, n_queries=600, seed=7, load=0.8, n_targets=100_000):
     n_pan = int(q_served.shape[0])
     return {"geometry": "box [0,64]^2x[0,16] minus 200 wires", "queries": n_queries, "points": points,
             "patches": int(len(allq["radius"])), "panels": n_pan,
-            "walks_per_node": "1024..16384 log-uniform per query",
+            "walks_per_node": "1024..16384 log-uniform per query", "slots": 3,
             "saturated_queries_per_s": n_queries / t_sat, "saturated_patches_per_s": len(allq["radius"]) / t_sat,
-            "offered_load": load, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "poisson_queries_per_s": n_queries / t_poisson, "queries_not_ok": n_bad,
-            "admission": {"rule": "free device memory at creation less max(1 GiB, 5%), slot workspaces + "
+            "poisson": poisson,
+            "admission": {"rule": "free device memory at creation less max(1 GiB, 5%); slot workspaces plus "
                                   "each starting batch's workspace within it",
                           "budget_bytes": info["budget_bytes"], "peak_held_bytes": info["peak_held_bytes"],
                           "rejected": info["rejected"]},
-            "slots": 3, "split_sms": True,
             "device_overlap": {"batches": info["batches"], "max_concurrent": info["max_concurrent"],
                                "busy_ms": info["busy_ms"], "overlap_ms": info["overlap_ms"]},
+            "split_sms": {"saturated_queries_per_s": n_queries / t_split, "batches": split_info["batches"],
+                          "max_concurrent": split_info["max_concurrent"], "busy_ms": split_info["busy_ms"],
+                          "overlap_ms": split_info["overlap_ms"]},
             "potential": {"targets": int(tgt.shape[0]), "panels": n_pan, "ms": pot_ms,
                           "targets_per_s": tgt.shape[0] / (pot_ms / 1e3),
                           "pair_terms_per_s": tgt.shape[0] * n_pan / (pot_ms / 1e3)}}
