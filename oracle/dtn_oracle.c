@@ -848,12 +848,14 @@ static void patch_point(const or_patch *p, int piece, double u, double v, double
          * the normal points into the box (outward of the region) */
         const or_piece *q = &p->piece[piece];
         const double r = piece_rho(q, v);
-        double y[3], ng[3] = {0.0, 0.0, 0.0};
-        y[q->ax] = q->fv;
-        y[q->ua] = q->P[0] + u * r * cos(v);
-        y[q->va] = q->P[1] + u * r * sin(v);
+        /* y - c formed from (P - c) and the offset, never from y itself: far
+         * from the origin the global coordinates' spacing (1e-14 at 50) would
+         * round a point next to the collocation point onto it */
+        double d[3], ng[3] = {0.0, 0.0, 0.0};
+        d[q->ax] = q->fv - p->c[q->ax];
+        d[q->ua] = (q->P[0] - p->c[q->ua]) + u * r * cos(v);
+        d[q->va] = (q->P[1] - p->c[q->va]) + u * r * sin(v);
         ng[q->ax] = q->side ? -1.0 : 1.0;
-        const double d[3] = {y[0] - p->c[0], y[1] - p->c[1], y[2] - p->c[2]};
         Y[0] = d[0] * p->t1[0] + d[1] * p->t1[1] + d[2] * p->t1[2];
         Y[1] = d[0] * p->t2[0] + d[1] * p->t2[1] + d[2] * p->t2[2];
         Y[2] = d[0] * p->n[0] + d[1] * p->n[1] + d[2] * p->n[2];
@@ -883,8 +885,9 @@ static void patch_point(const or_patch *p, int piece, double u, double v, double
  * piece), OR_PRM values per panel.
  * Wrapped patch (kind 2, R8): the ns sectors are shared among the sub-ranges of
  * all pieces (pieces in order, sub-ranges by angle): one each, then one at a
- * time to the sub-range with the largest area per sector (lowest index on
- * ties), and a sub-range's sectors split its angle evenly; rings split u =
+ * time to the sub-range with the largest area per sector (a larger ratio wins
+ * only by more than 1e-12 relative, else the lowest index), and a sub-range's
+ * sectors split its angle evenly; rings split u =
  * rho / rho_max in [0, 1] evenly; the collocation point is the image of the
  * parameter box's midpoint.  Returns -1 if ns is below the number of
  * sub-ranges. */
@@ -912,7 +915,7 @@ int or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, do
         for (int extra = ns - nsr; extra > 0; --extra) {
             int best = 0;
             for (int t = 1; t < nsr; ++t)
-                if (sa[t] / cnt[t] > sa[best] / cnt[best]) best = t;
+                if (sa[t] / cnt[t] > sa[best] / cnt[best] * (1.0 + 1e-12)) best = t;
             cnt[best] += 1;
         }
         int sector = 0;
