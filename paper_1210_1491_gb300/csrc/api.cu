@@ -203,7 +203,11 @@ double score_bound(const dtn_geometry_desc &gd, const dtn_dirichlet_desc &dd) {
     return std::fabs(dd.constant);
 }
 
-dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap) {
+// Batch layout: per-patch offsets, shape groups (one matrix per region kind,
+// a, rings, sectors) and weight groups (also node orders).  A wrapped patch
+// (wrapped[p] != 0) is congruent to no other: it gets groups of its own, and
+// its weight group no columns (its right side is assembled directly).
+dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap, const uint8_t *wrapped = nullptr) {
     const int64_t n = b->n_patches;
     L.n_patches = n;
     L.gamma_off.assign(n + 1, 0);
@@ -214,8 +218,9 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap) {
     L.group_of.assign(n, 0);
     L.rep.clear();
     L.max_panels = 0; L.max_nodes = 0; L.max_walks = 0;
-    std::map<std::tuple<uint64_t, int32_t, int32_t>, int64_t> groups;
-    std::map<std::tuple<uint64_t, int32_t, int32_t, int32_t, int32_t>, int64_t> wgroups;
+    std::map<std::tuple<uint64_t, int32_t, int32_t, int64_t>, int64_t> groups;
+    std::map<std::tuple<uint64_t, int32_t, int32_t, int32_t, int32_t, int64_t>, int64_t> wgroups;
+    L.wrapped.assign(n, 0);
     L.wgroup_of.assign(n, 0);
     L.wrep.clear();
     for (int64_t p = 0; p < n; ++p) {
@@ -231,14 +236,16 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap) {
         }
         uint64_t abits;
         std::memcpy(&abits, &L.radius[p], sizeof(abits));
-        auto key = std::make_tuple(abits, nr, ns);
+        const int64_t uniq = (wrapped && wrapped[p]) ? p : -1;
+        L.wrapped[p] = (uniq >= 0) ? 1 : 0;
+        auto key = std::make_tuple(abits, nr, ns, uniq);
         auto it = groups.find(key);
         if (it == groups.end()) {
             it = groups.emplace(key, (int64_t)L.rep.size()).first;
             L.rep.push_back(p);
         }
         L.group_of[p] = it->second;
-        auto wkey = std::make_tuple(abits, nr, ns, nt, nph);
+        auto wkey = std::make_tuple(abits, nr, ns, nt, nph, uniq);
         auto wit = wgroups.find(wkey);
         if (wit == wgroups.end()) {
             wit = wgroups.emplace(wkey, (int64_t)L.wrep.size()).first;
@@ -283,7 +290,7 @@ dtn_status build_layout(const dtn_patch_batch *b, BatchLayout &L, bool cap) {
         const int64_t r = L.wrep[k];
         const int64_t np = (int64_t)L.nr[r] * L.ns[r];
         L.wrows_off[k + 1] = L.wrows_off[k] + np;
-        L.kcols[k] = (cap ? (int64_t)kSamplesPerPanel * np : 0) + (int64_t)L.nt[r] * L.nph[r];
+        L.kcols[k] = L.wrapped[r] ? 0 : (cap ? (int64_t)kSamplesPerPanel * np : 0) + (int64_t)L.nt[r] * L.nph[r];
         L.gw_off[k + 1] = L.gw_off[k] + np * L.kcols[k];
         L.max_wgroup_rows = std::max<int32_t>(L.max_wgroup_rows, (int32_t)np);
     }
@@ -353,6 +360,9 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     const size_t o_tof = off; off = al(off + (nw + 1) * 8);
     const size_t host_bytes = off;
     const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
+    // pieces of wrapped patches (obstacle regions only)
+    const bool wrapped_possible = (g->dg.kind == kBoxMinusBoxes);
+    const size_t o_pc = off; off = al(off + (wrapped_possible ? n * kMaxPieces * sizeof(Piece) : 0));
     cudaError_t e = g->ws.layout.reserve(off, s);
     if (e != cudaSuccess) return e;
     std::vector<unsigned char> h(host_bytes, 0);
@@ -410,6 +420,7 @@ cudaError_t upload_layout(dtn_geometry *g, const BatchLayout &L, int32_t chunk, 
     D.mem_off = (int64_t *)(base + o_mof);
     D.tile_off = (int64_t *)(base + o_tof);
     D.frames = (PatchFrame *)(base + o_fr);
+    D.pieces = wrapped_possible ? (Piece *)(base + o_pc) : nullptr;
     return cudaSuccess;
 }
 
@@ -440,7 +451,8 @@ size_t workspace_bytes(const dtn_geometry *g) {
     const Workspace &W = g->ws;
     const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                             &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter,
-                            &W.se_tmp, &W.tune, &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag};
+                            &W.se_tmp, &W.tune, &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag,
+                            &W.panel_piece, &W.kinds};
     size_t t = 0;
     for (const DevBuf *d : bufs) t += d->bytes;
     return t;
@@ -610,7 +622,8 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.layout, &g->ws.gamma_loc, &g->ws.gamma_w, &g->ws.gamma_xyz, &g->ws.panel_loc,
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
-                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp, &g->ws.capflag};
+                      &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp, &g->ws.capflag,
+                      &g->ws.panel_piece, &g->ws.kinds};
     for (DevBuf *b : bufs) b->release();
     fmm_release(g);
     for (int k = 0; k < 5; ++k)
@@ -628,7 +641,7 @@ dtn_status dtn_release_workspace(dtn_geometry *g) {
     Workspace &W = g->ws;
     DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm, &W.panel_aux,
                       &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter, &W.se_tmp, &W.tune,
-                      &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag};
+                      &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag, &W.panel_piece, &W.kinds};
     for (DevBuf *b : bufs) b->release();
     if (g->graph_exec) {   // a captured graph holds the old pointers
         cudaGraphExecDestroy(g->graph_exec);
@@ -745,7 +758,33 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
     std::lock_guard<std::mutex> lk(g->mu);
     cudaStream_t s = (cudaStream_t)stream;
     BatchLayout L;
-    dtn_status st = build_layout(b, L, g->dg.kind == kBall || g->dg.kind == kBallExterior);
+    // Mixed precision shares one matrix among congruent patches; on an obstacle
+    // region a wrapped patch (the ball meets several faces of a box) is
+    // congruent to no other.  Which patches wrap is read back from a frames
+    // pass on the device before the batch is grouped (this synchronises s).
+    std::vector<uint8_t> wrapped;
+    if (g->dg.kind == kBoxMinusBoxes && o->prec == DTN_PREC_MIXED && o->bie_kind == 0) {
+        const int64_t n = b->n_patches;
+        for (int64_t p = 0; p < n; ++p)
+            if (!(b->radius[p] > 0.0)) return DTN_E_INVALID_ARG;
+        cudaError_t e;
+        const size_t fbytes = ((size_t)n * sizeof(PatchFrame) + 255) & ~(size_t)255;
+        if ((e = g->ws.kinds.reserve(fbytes + (size_t)n * sizeof(double), s)) != cudaSuccess) return to_status(e);
+        PatchFrame *fr = g->ws.kinds.as<PatchFrame>();
+        double *rad = (double *)(g->ws.kinds.as<char>() + fbytes);
+        std::vector<int32_t> kinds(n);
+        if ((e = cudaMemcpyAsync(rad, b->radius, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = launch_patch_frames(g, n, b->centers, rad, fr, s)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(kinds.data(), sizeof(int32_t), &fr->kind, sizeof(PatchFrame), sizeof(int32_t),
+                                   (size_t)n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return to_status(e);
+        wrapped.resize(n);
+        for (int64_t p = 0; p < n; ++p) wrapped[p] = (kinds[p] == kWrapped) ? 1 : 0;
+    }
+    dtn_status st = build_layout(b, L, g->dg.kind == kBall || g->dg.kind == kBallExterior,
+                                 wrapped.empty() ? nullptr : wrapped.data());
     if (st != DTN_OK) return st;
     const WalkParams wp = walk_params(g, o);
     const int32_t chunk = wp.chunk;
@@ -762,6 +801,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         (e = W.panel_aux.reserve(Pn * 4 * 8, s)) != cudaSuccess || (e = W.panel_g.reserve(Pn * 8, s)) != cudaSuccess ||
         (e = W.rhs.reserve(Pn * 8, s)) != cudaSuccess || (e = W.se_tmp.reserve(G * 8, s)) != cudaSuccess ||
         (e = W.capflag.reserve((size_t)L.n_patches * sizeof(int32_t), s)) != cudaSuccess ||
+        (e = W.panel_piece.reserve(Pn * sizeof(int32_t), s)) != cudaSuccess ||
         (!o->u_provided && (e = W.acc.reserve(wos_scratch_bytes(L.gamma_total), s)) != cudaSuccess))
         return to_status(e);
     const bool shared = (o->prec == DTN_PREC_MIXED);
@@ -805,11 +845,12 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(L.nr.data(), L.nr.size() * 4); put(L.ns.data(), L.ns.size() * 4);
         put(L.walks.data(), L.walks.size() * 8); put(L.pid.data(), L.pid.size() * 4);
         put(L.radius.data(), L.radius.size() * 8);
+        put(L.wrapped.data(), L.wrapped.size());
         put(&wp, sizeof(wp)); put(o, sizeof(*o)); put(&b->centers, sizeof(void *));
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                                 &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
-                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.capflag};
+                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.capflag, &W.panel_piece};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
@@ -866,7 +907,7 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
     // 1. patch setup
     e = launch_patch_setup(g, L, D, b->centers, gxyz, gw, W.gamma_loc.as<double>(), r->colloc_xyz,
                            r->normals, r->areas, W.panel_loc.as<double>(), W.panel_prm.as<double>(),
-                           W.panel_aux.as<double>(), pg, s);
+                           W.panel_aux.as<double>(), pg, W.panel_piece.as<int32_t>(), s);
     if (e != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
     // 2. walks at the hemisphere nodes (step 1 of the BIE-WOS algorithm)
@@ -944,6 +985,10 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         if (e == cudaSuccess)
             e = launch_rhs_shared(g, L, D, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                   W.gw.as<float>(), W.vec.as<float>(), rhs, s);
+        // wrapped patches: their right sides by the FP64 panel rules, row by row
+        if (e == cudaSuccess && std::find(L.wrapped.begin(), L.wrapped.end(), 1) != L.wrapped.end())
+            e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
+                                nullptr, rhs, s, 0, 1);
         if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
     } else {
         e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,
@@ -999,11 +1044,13 @@ dtn_status dtn_autotune_walks(dtn_geometry *g, const dtn_patch_batch *b, const d
     if ((e = W.gamma_loc.reserve(G * 3 * 8)) != cudaSuccess || (e = W.gamma_w.reserve(G * 8)) != cudaSuccess ||
         (e = W.gamma_xyz.reserve(G * 3 * 8)) != cudaSuccess || (e = W.panel_loc.reserve(Pn * 3 * 8)) != cudaSuccess ||
         (e = W.panel_prm.reserve(Pn * 6 * 8)) != cudaSuccess || (e = W.panel_aux.reserve(Pn * 4 * 8)) != cudaSuccess ||
-        (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.tune.reserve(G * 8 * 3)) != cudaSuccess)
+        (e = W.panel_g.reserve(Pn * 8)) != cudaSuccess || (e = W.tune.reserve(G * 8 * 3)) != cudaSuccess ||
+        (e = W.panel_piece.reserve(Pn * sizeof(int32_t))) != cudaSuccess)
         return to_status(e);
     e = launch_patch_setup(g, L, D, b->centers, W.gamma_xyz.as<double>(), W.gamma_w.as<double>(),
                            W.gamma_loc.as<double>(), nullptr, nullptr, nullptr, W.panel_loc.as<double>(),
-                           W.panel_prm.as<double>(), W.panel_aux.as<double>(), W.panel_g.as<double>(), s);
+                           W.panel_prm.as<double>(), W.panel_aux.as<double>(), W.panel_g.as<double>(),
+                           W.panel_piece.as<int32_t>(), s);
     if (e != cudaSuccess) return to_status(e);
     double *mean = W.tune.as<double>(), *se = mean + G;
     uint64_t *steps = (uint64_t *)(se + G);
@@ -1220,6 +1267,9 @@ dtn_status dtn_single_point_neumann(dtn_geometry *g, int64_t n, const double *x,
     const size_t o_rad = off; off = al(off + n * 8);
     const size_t host_bytes = off;
     const size_t o_fr = off; off = al(off + n * sizeof(PatchFrame));
+    // pieces of wrapped patches (obstacle regions only)
+    const bool wrapped_possible = (g->dg.kind == kBoxMinusBoxes);
+    const size_t o_pc = off; off = al(off + (wrapped_possible ? n * kMaxPieces * sizeof(Piece) : 0));
     const size_t o_y = off; off = al(off + nodes * 24);
     const size_t o_wk = off; off = al(off + nodes * 8);
     const size_t o_U = off; off = al(off + nodes * 8);

@@ -64,7 +64,24 @@ struct Ctx {
     // right-side integrand K (g - l) + dG/dn_x a.n_y, l(Y) = gx + ga.(Y - X)
     bool sk;
     T nx[3], ga[3];
+    const Piece *pc;   // wrapped patch: the piece of the panel being integrated ...
+    int sub;           // ... and its sub-range (the panel's quadrature parameters)
 };
+
+// point of the panel's quadrature parameters for any patch kind
+template <typename T>
+__device__ __forceinline__ void ctx_point(const Ctx<T> &c, T u, T v, T *Y, T *nl, T &J) {
+    if (c.kind == kWrapped) wrapped_point_q<T>(*c.pc, c.sub, u, v, Y, nl, J);
+    else patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+}
+
+// the piece and sub-range of a wrapped patch's panel (panel_piece = piece * kMaxSub + sub)
+template <typename T>
+__device__ __forceinline__ void ctx_panel(Ctx<T> &c, const Piece *pcs, int32_t code) {
+    if (!pcs) return;
+    c.pc = pcs + code / kMaxSub;
+    c.sub = code % kMaxSub;
+}
 
 // One quadrature point of the second-kind integrands (FP64 only).
 __device__ __forceinline__ void sk_point(const Ctx<double> &c, const double *Y, const double *nl, double wj,
@@ -89,7 +106,7 @@ __device__ __forceinline__ void sk_point(const Ctx<T> &, const T *, const T *, T
 template <typename T>
 __device__ __forceinline__ void eval_point(const Ctx<T> &c, T u, T v, T w, T &sa, T &sd) {
     T Y[3], nl[3], J;
-    patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+    ctx_point<T>(c, u, v, Y, nl, J);
     const T wj = w * J;
     if (c.sk) {
         sk_point(c, Y, nl, wj, sa, sd);
@@ -136,6 +153,36 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
     const T he = (T)0.5 * (e1 - e0), me = (T)0.5 * (e0 + e1);
     const T du = (T)R.p[1], dv = (T)R.p[3];
     const T jac = du * dv;
+    if (c.kind == kWrapped) {
+        // piece of a wrapped patch: Y = Pl + u B(w), J = u Jf(w), the lines in w
+        // taken once each
+        T Bs[kMaxRule][3], Jfs[kMaxRule];
+        for (int j = 0; j < n; ++j) {
+            double B[3], Jf;
+            wrapped_line(*c.pc, c.sub, (double)((T)R.p[2] + (me + he * (T)gx[j]) * dv), B, Jf);
+            for (int d = 0; d < 3; ++d) Bs[j][d] = (T)B[d];
+            Jfs[j] = (T)Jf;
+        }
+        const T nl[3] = {(T)c.pc->nl[0], (T)c.pc->nl[1], (T)c.pc->nl[2]};
+        const T Pl[3] = {(T)c.pc->Pl[0], (T)c.pc->Pl[1], (T)c.pc->Pl[2]};
+        for (int i = 0; i < n; ++i) {
+            const T u = (T)R.p[0] + (mx + hx * (T)gx[i]) * du;
+            const T wi = (T)gw[i] * hx * he * jac;
+            for (int j = 0; j < n; ++j) {
+                const T Y[3] = {Pl[0] + u * Bs[j][0], Pl[1] + u * Bs[j][1], Pl[2] + u * Bs[j][2]};
+                const T wj = wi * (T)gw[j] * u * Jfs[j];
+                if (c.needA) sa += wj * green_ball<T>(c.a, c.X, c.xn, Y);
+                if (c.needD) {
+                    const T yx = c.c[0] + Y[0] * c.t1[0] + Y[1] * c.t2[0] + Y[2] * c.n[0];
+                    const T yy = c.c[1] + Y[0] * c.t1[1] + Y[1] * c.t2[1] + Y[2] * c.n[1];
+                    const T yz = c.c[2] + Y[0] * c.t1[2] + Y[1] * c.t2[2] + Y[2] * c.n[2];
+                    const T gy = dirichlet_eval<T>(*c.dat, yx, yy, yz);
+                    sd += wj * green_ball_dny<T>(c.a, c.X, c.xn, Y, nl) * (gy - c.gx);
+                }
+            }
+        }
+        return;
+    }
     T cvs[kMaxRule], svs[kMaxRule];
     for (int j = 0; j < n; ++j) {
         const T v = (T)R.p[2] + (me + he * (T)gx[j]) * dv;
@@ -194,7 +241,7 @@ template <typename T>
 __device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T e1, bool withX, T &lx, T &le) {
     T uc, vc, jac, Yc[3], nl[3], J;
     map_uv<T>(R, (T)0.5 * (x0 + x1), (T)0.5 * (e0 + e1), uc, vc, jac);
-    patch_point<T>(c.kind, c.R, uc, vc, Yc, nl, J);
+    ctx_point<T>(c, uc, vc, Yc, nl, J);
     T rad = (T)0;
     T P[3][3][3];
     for (int a = 0; a < 3; ++a)
@@ -205,7 +252,7 @@ __device__ T square_ratio(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T 
             }
             T u, v, Y[3];
             map_uv<T>(R, x0 + (T)0.5 * a * (x1 - x0), e0 + (T)0.5 * b * (e1 - e0), u, v, jac);
-            patch_point<T>(c.kind, c.R, u, v, Y, nl, J);
+            ctx_point<T>(c, u, v, Y, nl, J);
             P[a][b][0] = Y[0]; P[a][b][1] = Y[1]; P[a][b][2] = Y[2];
             const T d2 = (Y[0] - Yc[0]) * (Y[0] - Yc[0]) + (Y[1] - Yc[1]) * (Y[1] - Yc[1]) +
                          (Y[2] - Yc[2]) * (Y[2] - Yc[2]);
@@ -288,11 +335,15 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
     c.img = xx > 0.0;
     if (c.img)
         for (int d = 0; d < 3; ++d) c.Xs[d] = (T)(f.a * f.a * X[d] / xx);
-    c.needD = (f.kind == kCap);
+    // dG/dn_y vanishes on a plane through c: the S integral of the right side
+    // is needed on caps and on a wrapped patch's other faces
+    c.needD = (f.kind == kCap || f.kind == kWrapped);
     c.needA = true;
     c.gx = (T)gx;
     c.dat = dat;
     c.sk = false;
+    c.pc = nullptr;
+    c.sub = 0;
 }
 
 struct AsmDev {
@@ -308,7 +359,10 @@ struct AsmDev {
     int prec;
     int mode;   // 0 matrix and right side per patch, 1 matrix per shape group, 2 right side only
     int sk;     // second-kind system (1/2 I - D) q = b instead of Eq. bw49-bw51
+    int only_wrapped;   // mode 2: the rows of wrapped patches only (the others are left untouched)
     const double *glx, *glw;
+    const Piece *pieces;        // n_patches x kMaxPieces, or nullptr
+    const int32_t *panel_piece; // per panel
 };
 
 // self panel: triangles from the collocation point (uc, vc) to each side, each
@@ -317,22 +371,27 @@ struct AsmDev {
 // smooth for thin panels)
 // (fn(R) integrates over one triangle R)
 template <typename Fn>
-__device__ void self_triangles(const PatchFrame &f, const double *prm, Fn &&fn) {
+__device__ void self_triangles(const Ctx<double> &c, const double *prm, Fn &&fn) {
     const double S[2] = {prm[4], prm[5]};
     const double cu[5] = {prm[0], prm[1], prm[1], prm[0], prm[0]};
     const double cv[5] = {prm[2], prm[2], prm[3], prm[3], prm[2]};
     double PS[3], nl[3], J;
-    patch_point<double>(f.kind, f.R, S[0], S[1], PS, nl, J);
+    ctx_point<double>(c, S[0], S[1], PS, nl, J);
     for (int e = 0; e < 4; ++e) {
         double PA[3], PB[3];
-        patch_point<double>(f.kind, f.R, cu[e], cv[e], PA, nl, J);
-        patch_point<double>(f.kind, f.R, cu[e + 1], cv[e + 1], PB, nl, J);
+        ctx_point<double>(c, cu[e], cv[e], PA, nl, J);
+        ctx_point<double>(c, cu[e + 1], cv[e + 1], PB, nl, J);
         const double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
         const double as[3] = {PS[0] - PA[0], PS[1] - PA[1], PS[2] - PA[2]};
         const double cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2], ab[0] * as[1] - ab[1] * as[0]};
         const double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
         const double h = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmax(L, 1e-300);
-        const int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
+        int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
+        // a side that maps to one point (the polar origin of a ring-0 panel):
+        // the triangle is a sliver whose angular factor still varies across the
+        // side's parameter range; four pieces
+        const double sa = sqrt(as[0] * as[0] + as[1] * as[1] + as[2] * as[2]);
+        if (L <= 1e-9 * sa) m = 4;
         for (int k = 0; k < m; ++k) {
             const double ua = cu[e] + (cu[e + 1] - cu[e]) * k / m, va = cv[e] + (cv[e + 1] - cv[e]) * k / m;
             const double ub = cu[e] + (cu[e + 1] - cu[e]) * (k + 1) / m;
@@ -401,6 +460,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const PatchFrame f = P.frames[p];
     const int64_t poff = P.panel_off[p];
     __shared__ double red[2][kAsmThreads / 32];
+    if (P.only_wrapped && f.kind != kWrapped) return;
+    const Piece *pcs = (f.kind == kWrapped) ? P.pieces + p * kMaxPieces : nullptr;
     if (P.mode != 1 && f.status != DTN_OK) {
         if (Arow)
             for (int j = threadIdx.x; j < n; j += blockDim.x) Arow[j] = (i == j) ? 1.0 : 0.0;
@@ -412,6 +473,16 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     Ctx<double> c64;
     make_ctx<double>(c64, f, X, gx, &P.dat);
     if (P.mode == 1) c64.needD = false;
+    if (P.mode == 2) c64.needA = false;
+    // mixed precision on a wrapped patch (a matrix of its own): far panels by
+    // FP32 rules, near, self and image-near panels by the FP64 ones
+    const bool far32 = (P.prec == DTN_PREC_MIXED && f.kind == kWrapped && !SK);
+    Ctx<float> c32;
+    if (far32) {
+        make_ctx<float>(c32, f, X, gx, &P.dat);
+        c32.needA = c64.needA;
+        c32.needD = c64.needD;
+    }
     __shared__ int near_list[1024];
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
@@ -454,22 +525,43 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const double dsign = SK ? -1.0 : 1.0;   // second kind: A = 1/2 I - D
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double dsum = 0.0;
-    // far panels (r >= 2): one thread each, separable Gauss rule
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        if (j == i) continue;
+    // far panels (r >= 2): one thread each, separable Gauss rule.  The near
+    // panels are listed in panel order (ballots and a prefix over the warps),
+    // so that the warps sum their right-side parts in the same order on every
+    // run.
+    __shared__ int warp_near[kAsmThreads / 32];
+    for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const bool near = (j < n && j != i) && panel_ratio(c64, X, P.panel_aux + 4 * (poff + j)) < 2.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, near);
+        if (lane == 0) warp_near[warp] = __popc(bal);
+        __syncthreads();
+        int base = near_count;
+        for (int w = 0; w < warp; ++w) base += warp_near[w];
+        if (near) near_list[base + __popc(bal & ((1u << lane) - 1u))] = j;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kAsmThreads / 32; ++w) near_count += warp_near[w];
+        __syncthreads();
+        if (j >= n || j == i || near) continue;
         const int64_t pj = poff + j;
         const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
-        if (r < 2.0) {
-            near_list[atomicAdd(&near_count, 1)] = j;
-            continue;
-        }
         const double *prm = P.panel_prm + 6 * pj;
         Region R;
         R.tri = false;
         R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
-        gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
+        if (far32) {
+            ctx_panel(c32, pcs, P.panel_piece[pj]);
+            float sa32 = 0.f, sd32 = 0.f;
+            gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order64(r), P.glx, P.glw, sa32, sd32);
+            sa = sa32;
+            sd = sd32;
+        } else {
+            ctx_panel(c64, pcs, P.panel_piece[pj]);
+            gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
+        }
         if (Arow) Arow[j] = dsign * sa;
         dsum += sd;
     }
@@ -478,7 +570,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     {
         double sa = 0.0, sd = 0.0;
         int tri = 0;
-        self_triangles(f, P.panel_prm + 6 * row, [&](const Region &R) {
+        ctx_panel(c64, pcs, P.panel_piece[row]);
+        self_triangles(c64, P.panel_prm + 6 * row, [&](const Region &R) {
             if ((tri++ % (kAsmThreads / 32)) != warp) return;
             adaptive_squares<double>(c64, R, false, 16, [&](double x0, double x1, double e0, double e1, int nq) {
                 coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
@@ -513,6 +606,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         R.p[0] = prm[0]; R.p[1] = prm[1] - prm[0]; R.p[2] = prm[2]; R.p[3] = prm[3] - prm[2];
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
+        ctx_panel(c64, pcs, P.panel_piece[poff + j]);
         adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
             coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
         });
@@ -641,7 +735,7 @@ __global__ void __launch_bounds__(kWtThreads) rhs_far_weights_kernel(WtDev P) {
     __shared__ Basis8 B;
     if (threadIdx.x == 0) basis8_init(B, P.glx, P.glw);
     __syncthreads();
-    if (r.dcols == 0 || t >= r.n * kSampleN) return;
+    if (r.kc == 0 || r.dcols == 0 || t >= r.n * kSampleN) return;   // (no columns: a wrapped patch's row)
     const int j = t / kSampleN, a = t - j * kSampleN;
     if (j == r.i) return;
     const PatchFrame f = P.frames[r.p];
@@ -728,7 +822,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev
         near_count = 0;
     }
     __syncthreads();
-    if (r.dcols == 0) return;
+    if (r.kc == 0 || r.dcols == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const PatchFrame f = P.frames[r.p];
     Ctx<double> c;
@@ -743,7 +837,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev
         const double u0 = prm[0], du = prm[1] - prm[0], v0 = prm[2], dv = prm[3] - prm[2];
         double acc0 = 0.0, acc1 = 0.0;
         int tri = 0;
-        self_triangles(f, prm, [&](const Region &R) {
+        self_triangles(c, prm, [&](const Region &R) {
             if ((tri++ % kNearWarps) != warp) return;
             adaptive_squares<double>(c, R, false, kSelfOrderW, [&](double x0, double x1, double e0, double e1, int nq) {
                 coop_square(c, f, B, R, u0, du, v0, dv, x0, x1, e0, e1, nq, P.glx, P.glw, pbuf[warp], lane, acc0,
@@ -784,7 +878,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev
 __global__ void __launch_bounds__(kWtThreads) rhs_walk_weights_kernel(WtDev P) {
     const WtRow r = wt_row(P, blockIdx.x);
     const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= r.m) return;
+    if (r.kc == 0 || k >= r.m) return;   // no columns: a wrapped patch's row (its right side is assembled directly)
     const double a = P.frames[r.p].a;
     const int64_t gk = P.gamma_off[r.p] + k;
     const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
@@ -922,7 +1016,7 @@ __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
-                            const double *U, double *A, double *b, cudaStream_t s, int sk) {
+                            const double *U, double *A, double *b, cudaStream_t s, int sk, int only_wrapped) {
     const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
     if (rows == 0) return cudaSuccess;
     AsmDev P;
@@ -948,8 +1042,11 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.prec = prec;
     P.mode = mode;
     P.sk = sk;
+    P.only_wrapped = only_wrapped;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
+    P.pieces = D.pieces;
+    P.panel_piece = g->ws.panel_piece.as<int32_t>();
     if (sk) assemble_kernel<true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     else assemble_kernel<false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();

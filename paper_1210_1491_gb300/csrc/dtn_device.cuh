@@ -519,7 +519,7 @@ __device__ __forceinline__ T poisson_ball(T a, const T *X, const T *Y) {
 }
 
 // ------------------------------------------------------------------ patches
-enum PatchKind : int { kDisk = 0, kCap = 1 };
+enum PatchKind : int { kDisk = 0, kCap = 1, kWrapped = 2 };
 
 // Local frame of a patch: n = outward normal of D at c; t1 = normalised
 // projection of the coordinate axis least aligned with n (lowest index on
@@ -528,7 +528,106 @@ struct PatchFrame {
     double c[3], n[3], t1[3], t2[3];
     double a, R, theta_max, umax;
     int kind, status;
+    double blo[3], bhi[3];   // wrapped patch: the obstacle box
+    int npiece;              // wrapped patch: pieces (kMaxPieces per patch in the pieces array)
 };
+
+// A piece of a wrapped patch (the ball about a point of an obstacle face meets
+// further faces of that box): a face rectangle cut by the ball's slice of the
+// face plane, in polar coordinates about P (the point of the rectangle nearest
+// the slice centre cf): rho <= rho_max(phi), phi in [sub[0], sub[nsub]], the
+// angle cut where rho_max changes from one rectangle side or the circle to
+// another.  Panels: rings in u = rho / rho_max, cnt[j] sectors in sub-range j.
+constexpr int kMaxPieces = 6, kMaxSub = 16;
+struct Piece {
+    double P[2], cf[2], rlo[2], rhi[2], rf, fv;
+    double Pl[3], Ul[3], Vl[3], nl[3];   // in the patch frame: P, the in-plane axes, the normal
+    double sub[kMaxSub + 1];
+    // what bounds a sub-range: the circle (stype 0), or a rectangle side (stype
+    // 1) at distance sdist from P along the direction of angle svn
+    double svn[kMaxSub], sdist[kMaxSub];
+    double en[kMaxSub][3], et[kMaxSub][3];   // side-bounded: e(svn), e(svn + pi/2) in the patch frame, times sdist
+    int stype[kMaxSub];
+    int centred;   // P is the slice centre (rho_max = rf on circle-bounded sub-ranges)
+    int ax, side, ua, va, onlo[2], onhi[2], nsub;
+    int cnt[kMaxSub];
+};
+
+// rho_max(phi): from P along (cos phi, sin phi) to the circle, or to a
+// rectangle side if nearer (the sides through P bound no ray of the range)
+__device__ __forceinline__ double piece_rho(const Piece &q, double ph) {
+    double e0, e1;
+    sincos(ph, &e1, &e0);
+    const double w0 = q.P[0] - q.cf[0], w1 = q.P[1] - q.cf[1];
+    const double we = w0 * e0 + w1 * e1, ww = w0 * w0 + w1 * w1;
+    double r = -we + sqrt(fmax(0.0, we * we - ww + q.rf * q.rf));
+    if (e0 > 0.0 && !q.onhi[0]) r = fmin(r, (q.rhi[0] - q.P[0]) / e0);
+    if (e0 < 0.0 && !q.onlo[0]) r = fmin(r, (q.rlo[0] - q.P[0]) / e0);
+    if (e1 > 0.0 && !q.onhi[1]) r = fmin(r, (q.rhi[1] - q.P[1]) / e1);
+    if (e1 < 0.0 && !q.onlo[1]) r = fmin(r, (q.rlo[1] - q.P[1]) / e1);
+    return r;
+}
+
+// point of a piece at (u, v) = (rho / rho_max, phi), in the patch frame:
+// Y = Pl + u rho_max(v) (cos v Ul + sin v Vl), its normal, J = u rho_max(v)^2
+template <typename T>
+__device__ __forceinline__ void wrapped_point(const Piece &q, T u, T v, T *Y, T *nl, T &J) {
+    const double r = piece_rho(q, (double)v);
+    double sv, cv;
+    sincos((double)v, &sv, &cv);
+    const double ur = (double)u * r;
+    for (int d = 0; d < 3; ++d) {
+        Y[d] = (T)(q.Pl[d] + ur * (cv * q.Ul[d] + sv * q.Vl[d]));
+        nl[d] = (T)q.nl[d];
+    }
+    J = (T)((double)u * r * r);
+}
+
+// The quadrature parameters of a panel of sub-range j: (u, v) on a sub-range
+// bounded by the circle (rho_max constant there), (u, t) with t = tan(v -
+// svn) on one bounded by a rectangle side, where the point P + u sdist (e_n +
+// t e_t) is bilinear in (u, t) (J = sdist^2 u): the same panel, but the
+// integrands stay smooth however close the side's pole angle svn +- pi/2
+// comes to the sub-range.
+template <typename T>
+__device__ __forceinline__ void wrapped_point_q(const Piece &q, int j, T u, T w, T *Y, T *nl, T &J) {
+    if (q.stype[j] == 0) {
+        if (!q.centred) {
+            wrapped_point<T>(q, u, w, Y, nl, J);
+            return;
+        }
+        double sv, cv;
+        sincos((double)w, &sv, &cv);
+        const double ur = (double)u * q.rf;
+        for (int d = 0; d < 3; ++d) {
+            Y[d] = (T)(q.Pl[d] + ur * (cv * q.Ul[d] + sv * q.Vl[d]));
+            nl[d] = (T)q.nl[d];
+        }
+        J = (T)((double)u * q.rf * q.rf);
+        return;
+    }
+    const double ud = (double)u, wt = (double)w;
+    for (int d = 0; d < 3; ++d) {
+        Y[d] = (T)(q.Pl[d] + ud * (q.en[j][d] + wt * q.et[j][d]));
+        nl[d] = (T)q.nl[d];
+    }
+    J = (T)(q.sdist[j] * q.sdist[j] * ud);
+}
+
+// the direction of a wrapped panel's quadrature line at parameter w (the point
+// is Pl + u B, the Jacobian u Jf): separable in (u, w)
+__device__ __forceinline__ void wrapped_line(const Piece &q, int j, double w, double *B, double &Jf) {
+    if (q.stype[j] == 0) {
+        const double r = q.centred ? q.rf : piece_rho(q, w);
+        double sv, cv;
+        sincos(w, &sv, &cv);
+        for (int d = 0; d < 3; ++d) B[d] = r * (cv * q.Ul[d] + sv * q.Vl[d]);
+        Jf = r * r;
+    } else {
+        for (int d = 0; d < 3; ++d) B[d] = q.en[j][d] + w * q.et[j][d];
+        Jf = q.sdist[j] * q.sdist[j];
+    }
+}
 
 // point of the patch at parameters (u, v), local coordinates (t1, t2, n),
 // its local unit normal and the area Jacobian.  Disk: Y = u (cos v, sin v, 0),

@@ -37,6 +37,7 @@ struct BatchLayout {
     int32_t max_panels = 0, max_nodes = 0;
     int64_t max_walks = 0;
     std::vector<int64_t> gamma_off, panel_off, mat_off;   // n+1
+    std::vector<uint8_t> wrapped;                         // n: a wrapped patch (groups of its own)
     std::vector<int32_t> nt, nph, nr, ns;                 // n
     std::vector<int64_t> walks;                           // n
     std::vector<uint32_t> pid;                            // n
@@ -79,6 +80,7 @@ struct DevLayout {
     int64_t *group_of, *rep, *grows_off, *gmat_off, *gfac_off;
     int64_t *wrep, *wrows_off, *kcols, *gw_off, *vec_off, *members, *mem_off, *tile_off;
     PatchFrame *frames;
+    Piece *pieces;          // n_patches x kMaxPieces (box-minus-boxes regions), else nullptr
 };
 
 struct Workspace {
@@ -105,6 +107,8 @@ struct Workspace {
     DevBuf vec;             // per-patch samples (data at panel points, walk estimates), FP32
     DevBuf sp;              // single-point method: frames, nodes, weights, estimates, walk layout
     DevBuf capflag;         // n_patches int32: 1 where a walk of the patch was cut at max_steps
+    DevBuf panel_piece;     // panels_total int32: the piece of a wrapped patch's panel
+    DevBuf kinds;           // n_patches frames + kinds of the classification pre-pass (mixed, wires)
 };
 
 struct GeometryHost {
@@ -181,7 +185,7 @@ cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, cons
                                const double *centers, double *gamma_xyz,
                                double *gamma_w, double *gamma_loc, double *colloc, double *normals,
                                double *areas, double *panel_loc, double *panel_prm, double *panel_aux,
-                               double *panel_g, cudaStream_t s);
+                               double *panel_g, int32_t *panel_piece, cudaStream_t s);
 
 cudaError_t launch_patch_frames(const dtn_geometry *g, int64_t n, const double *centers, const double *radius,
                                 PatchFrame *frames, cudaStream_t s);
@@ -230,7 +234,7 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
                             int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
                             const double *gamma_w, const double *U, double *A, double *b, cudaStream_t s,
-                            int sk = 0);
+                            int sk = 0, int only_wrapped = 0);
 
 // mixed precision right sides: FP64 weights per shape group (product rules of
 // the double layer against the panel interpolants of the data, and the walk

@@ -57,12 +57,14 @@ __global__ void __launch_bounds__(kSkThreads) second_kind_kernel(SkDev P) {
     const PatchFrame f = P.frames[p];
     __shared__ double red[kSkThreads / 32];
     __shared__ double grad[2];
+    // the second-kind rows are written for disk patches: a wrapped patch is not supported
+    const int st = (f.status == DTN_OK && f.kind != kDisk) ? DTN_E_UNSUPPORTED : f.status;
     if (i == 0 && threadIdx.x == 0) {
         if (P.iters) P.iters[p] = 0;
         if (P.resid) P.resid[p] = 0.0;
-        if (P.status) P.status[p] = f.status;
+        if (P.status) P.status[p] = st;
     }
-    if (f.status != DTN_OK) {
+    if (st != DTN_OK) {
         if (threadIdx.x == 0) {
             P.q[row] = 0.0;
             if (P.b) P.b[row] = 0.0;

@@ -48,7 +48,7 @@ def test_rows_match_oracle_with_exact_values():
 
 
 def test_with_walks_on_wire_patches():
-    wl = W.wires(n_patches=6, walks=400)
+    wl = W.wires(n_patches=6, walks=400, allow_wrapped=False)
     g, b, hb = _setup(wl)
     res = dtn.solve_patches(g, b.centers, b.radius, hb,
                             dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=2, bie_kind=1, ring_order=16))

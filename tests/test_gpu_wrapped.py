@@ -1,0 +1,160 @@
+"""GPU parity on wrapped wire patches (a ball about a point of a wire face that
+meets further faces of that wire, reading R15): the patch setup (hemisphere
+nodes with theta_max(phi), the face pieces' panels), the assembly of Eq.
+bw49-bw51 and the solve with exact values at the nodes (FP64 and mixed
+precision, in a batch that mixes flat and wrapped patches), and the walks, all
+against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+dtn = pytest.importorskip("paper_1210_1491_gb300")
+
+A = 0.3
+BOX = np.array([1.0, 1.0, 1.0, 3.0, 1.8, 1.7])
+
+
+def _case():
+    geo = W.Geometry(W.GEOM_BOX_MINUS_BOXES, lo=(0, 0, 0), hi=(4, 3, 3), boxes=np.array([BOX]))
+    data = W.Dirichlet(W.DATA_POINT_SOURCE, x0=(2.0, 1.4, 1.35), strength=1.0)
+    centers = np.array([[2.0, 1.4, 1.7],              # flat (top face)
+                        [2.0, 1.1, 1.7],              # edge
+                        [2.88, 1.65, 1.7],            # corner
+                        [1.15, 1.0, 1.35],            # side face, near the end face
+                        [2.4, 1.8, 1.05]])            # side face, near the bottom edge
+    n = len(centers)
+    batch = W.PatchBatch(centers=centers, radius=np.full(n, A), n_theta=np.full(n, 12, np.int32),
+                         n_phi=np.full(n, 24, np.int32), n_rings=np.full(n, 3, np.int32),
+                         n_sectors=np.full(n, 16, np.int32), walks=np.full(n, 2, np.int64))
+    return W.Workload("one_wire", geo, data, batch)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _setup(wl):
+    g = dtn.Geometry.from_spec(wl.geometry).set_data_spec(wl.data)
+    b = wl.batch
+    hb = dtn.HostBatch(b.n_theta, b.n_phi, b.n_rings, b.n_sectors, b.walks)
+    return g, b, hb
+
+
+def test_wrapped_setup_matches_oracle():
+    wl = _case()
+    g, b, hb = _setup(wl)
+    r = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
+    torch.cuda.synchronize()
+    assert np.all(_np(r["patch_status"]) == 0)
+    P, n = 12 * 24, 3 * 16
+    kinds = []
+    for p in range(b.n):
+        pf = O.patch_frame(wl.geometry, b.centers[p], A)
+        kinds.append(pf.kind)
+        _, yg, Wg = O.gamma_nodes(pf, 12, 24)
+        pan = O.panels(pf, 3, 16)
+        assert np.max(np.abs(_np(r["gamma_xyz"])[p * P:(p + 1) * P] - yg)) < 1e-13
+        assert np.max(np.abs(_np(r["gamma_w"])[p * P:(p + 1) * P] - Wg)) < 1e-14
+        assert np.max(np.abs(_np(r["colloc_xyz"])[p * n:(p + 1) * n] - pan["x"])) < 1e-13
+        assert np.max(np.abs(_np(r["normals"])[p * n:(p + 1) * n] - pan["normal"])) < 1e-14
+        assert np.max(np.abs(_np(r["areas"])[p * n:(p + 1) * n] - pan["area"])) < 1e-14
+    assert kinds == [0, 2, 2, 2, 2]
+
+
+def test_wrapped_assembly_and_solve_given_exact_values():
+    """Matrix and right side against the oracle's adaptive integrals, and q:
+    FP64 within relative L2 1e-10; mixed precision (a wrapped patch has a
+    matrix of its own: far panels by FP32 rules, near and self panels by the
+    FP64 ones; the same for its right side) entries within 2e-5 of the
+    largest, q within 1e-4."""
+    wl = _case()
+    g, b, hb = _setup(wl)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
+    torch.cuda.synchronize()
+    U = O.dirichlet(wl.data, _np(r0["gamma_xyz"]))
+    P, n = 12 * 24, 3 * 16
+    ref = []
+    for p in range(b.n):
+        pf = O.patch_frame(wl.geometry, b.centers[p], A)
+        Ao, bo = O.assemble(pf, wl.data, 3, 16, 12, 24, U[p * P:(p + 1) * P], rtol=1e-12)
+        ref.append((Ao, bo, np.linalg.solve(Ao, bo)))
+    for prec, tol in [(dtn.PREC_FP64, 1e-10), (dtn.PREC_MIXED, 1e-4)]:
+        res = dtn.alloc_result(hb, want_matrix=True)
+        res["u_gamma_mean"].copy_(torch.from_numpy(U))
+        dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=prec, u_provided=True), result=res)
+        torch.cuda.synchronize()
+        assert np.all(_np(res["patch_status"]) == 0)
+        for p in range(b.n):
+            Ao, bo, qo = ref[p]
+            Am = _np(res["matrix"])[p * n * n:(p + 1) * n * n].reshape(n, n)
+            bm = _np(res["rhs"])[p * n:(p + 1) * n]
+            fp64 = (prec == dtn.PREC_FP64)
+            atol = 1e-10 if (fp64 or p == 0) else 2e-5          # patch 0 is flat: a shared FP64 matrix
+            btol = 1e-10 if fp64 else (1e-6 if p == 0 else 2e-5)
+            print(f"prec {prec} patch {p}: A {np.max(np.abs(Am - Ao)) / np.max(np.abs(Ao)):.1e}, "
+                  f"b {np.max(np.abs(bm - bo)) / np.max(np.abs(bo)):.1e}")
+            assert np.max(np.abs(Am - Ao)) <= atol * np.max(np.abs(Ao)), (prec, p)
+            assert np.max(np.abs(bm - bo)) <= btol * np.max(np.abs(bo)), (prec, p)
+            q = _np(res["neumann"])[p * n:(p + 1) * n]
+            rel = np.linalg.norm(q - qo) / np.linalg.norm(qo)
+            print(f"prec {prec} patch {p}: q rel-L2 {rel:.2e}")
+            assert rel <= tol, (prec, p, rel)
+
+
+def test_wrapped_walks_and_full_solve_vs_oracle():
+    """Walk means at the wrapped hemisphere's nodes within 4 standard errors of
+    the oracle's (FP32 walks), and the solve with the GPU's node values within
+    1e-4 of the oracle's."""
+    wl = _case()
+    b = wl.batch
+    b.walks[:] = 2000
+    g, b, hb = _setup(wl)
+    r = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=1e-4, seed=3))
+    torch.cuda.synchronize()
+    assert np.all(_np(r["patch_status"]) == 0)
+    U, SE, yg = _np(r["u_gamma_mean"]), _np(r["u_gamma_se"]), _np(r["gamma_xyz"])
+    q = _np(r["neumann"])
+    P, n = 12 * 24, 3 * 16
+    for p in (1, 2):
+        sl = slice(p * P, (p + 1) * P)
+        nodes = np.arange(0, P, 6)
+        ro = O.wos_points(wl.geometry, wl.data, yg[sl][nodes], nodes, p, 2000,
+                          O.wos_opts(eps=1e-4, seed=3, stream=O.STREAM_F32))
+        Uo, SEo = O.wos_estimates(ro, 2000)
+        assert np.all(np.abs(U[sl][nodes] - Uo) <= 4.0 * np.sqrt(SE[sl][nodes] ** 2 + SEo ** 2))
+        rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], A, 12, 24, 3, 16, 0, 0, O.wos_opts(), U_in=U[sl],
+                           rtol=1e-10)
+        assert np.linalg.norm(q[p * n:(p + 1) * n] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4
+
+
+def test_wire_layout_batch_mixed_flat_and_wrapped_graph_replay():
+    """The wire workload's own patches (mostly wrapped), in one mixed-precision
+    call captured as a CUDA graph: the replay is bit-equal, every patch solves,
+    and sampled wrapped patches match the oracle's solve with the GPU's node
+    values within 1e-4."""
+    wl = W.wires(n_patches=64, walks=256)
+    g, b, hb = _setup(wl)
+    o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=wl.epsilon, seed=wl.seed, graph_capture=True)
+    r1 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+    torch.cuda.synchronize()
+    q1 = _np(r1["neumann"]).copy()
+    r2 = dtn.solve_patches(g, b.centers, b.radius, hb, o)
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(r2["neumann"]), q1)
+    assert np.all(_np(r2["patch_status"]) == 0)
+    assert np.sum(wl.faces_met > 1) > 32
+    U = _np(r2["u_gamma_mean"])
+    Pn = (b.n_theta * b.n_phi).astype(np.int64)
+    nn = (b.n_rings * b.n_sectors).astype(np.int64)
+    goff, poff = np.r_[0, np.cumsum(Pn)], np.r_[0, np.cumsum(nn)]
+    for p in [int(i) for i in np.nonzero(wl.faces_met > 1)[0][:3]]:
+        rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], A, int(b.n_theta[p]), int(b.n_phi[p]),
+                           int(b.n_rings[p]), int(b.n_sectors[p]), 0, 0, O.wos_opts(), U_in=U[goff[p]:goff[p + 1]],
+                           rtol=1e-10)
+        qq = q1[poff[p]:poff[p + 1]]
+        assert np.linalg.norm(qq - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4, p

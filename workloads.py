@@ -207,12 +207,15 @@ def wire_layout(n_wires: int = 200, seed: int = 0, outer_lo=(0.0, 0.0, 0.0),
 
 def wire_patch_centers(boxes: np.ndarray, n: int, a: float, seed: int = 1,
                        margin: float = 1e-9, max_tries: int = 5_000_000,
-                       outer_lo=(0.0, 0.0, 0.0), outer_hi=(64.0, 64.0, 16.0)):
-    """Area-uniform patch centres on wire faces whose ball meets one face only.
+                       outer_lo=(0.0, 0.0, 0.0), outer_hi=(64.0, 64.0, 16.0), allow_wrapped: bool = True):
+    """Area-uniform patch centres on the wire faces (reading R15).
 
-    A centre c on face f of wire w is kept when the disk of radius a around c
-    lies inside the face rectangle and no other wire, face or the outer box
-    comes within a of c.  Returns (centres (n,3), wire index (n,), rejected).
+    A centre c on face f of wire w is kept when no other wire and no face of the
+    outer box comes within a of c (the ball meets one conductor only) and the
+    wire is at least a thick along the face normal (the hemisphere is then
+    star-shaped about its pole).  The ball may meet further faces of wire w (a
+    wrapped patch); with allow_wrapped=False such centres are rejected too.
+    Returns (centres (n,3), wire index (n,), faces met (n,), rejected).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     ext = boxes[:, 3:] - boxes[:, :3]
@@ -224,7 +227,7 @@ def wire_patch_centers(boxes: np.ndarray, n: int, a: float, seed: int = 1,
     prob = flat / flat.sum()
     olo = np.asarray(outer_lo)
     ohi = np.asarray(outer_hi)
-    out, owner = [], []
+    out, owner, nfaces = [], [], []
     rejected = 0
     tries = 0
     while len(out) < n:
@@ -237,17 +240,18 @@ def wire_patch_centers(boxes: np.ndarray, n: int, a: float, seed: int = 1,
         lo, hi = boxes[w, :3], boxes[w, 3:]
         c = rng.uniform(lo, hi)
         c[axis] = lo[axis] if side == 0 else hi[axis]
-        good = ext[w, axis] > a + margin   # the ball must not reach the opposite face
+        good = ext[w, axis] >= a + margin     # star-shaped hemisphere
+        # faces of wire w the ball reaches besides f
+        met = 1
         for ax in range(3):
             if ax == axis:
                 continue
-            if c[ax] - lo[ax] < a + margin or hi[ax] - c[ax] < a + margin:
-                good = False
-        # other wires and the outer box must stay farther than a
-        if good:
-            d_out = np.min(np.minimum(c - olo, ohi - c))
-            if d_out <= a + margin:
-                good = False
+            met += int(c[ax] - lo[ax] < a) + int(hi[ax] - c[ax] < a)
+        if met > 1 and not allow_wrapped:
+            good = False
+        # the outer box and the other wires must stay farther than a
+        if good and np.min(np.minimum(c - olo, ohi - c)) <= a + margin:
+            good = False
         if good:
             e = np.maximum(np.maximum(boxes[:, :3] - c, 0.0), c - boxes[:, 3:])
             d = np.sqrt((e * e).sum(axis=1))
@@ -259,35 +263,79 @@ def wire_patch_centers(boxes: np.ndarray, n: int, a: float, seed: int = 1,
             continue
         out.append(c)
         owner.append(w)
-    return np.array(out), np.array(owner, dtype=np.int64), rejected
+        nfaces.append(met)
+    return np.array(out), np.array(owner, dtype=np.int64), np.array(nfaces, dtype=np.int64), rejected
+
+
+def _rect_disk_area(lo_u, hi_u, lo_v, hi_v, cu, cv, r, m=256):
+    """Area of the rectangle [lo_u, hi_u] x [lo_v, hi_v] inside the disk of radius
+    r about (cu, cv) (midpoint rule over u of the clipped chord)."""
+    u0, u1 = max(lo_u, cu - r), min(hi_u, cu + r)
+    if u1 <= u0:
+        return 0.0
+    u = u0 + (np.arange(m) + 0.5) * (u1 - u0) / m
+    h = np.sqrt(np.maximum(r * r - (u - cu) ** 2, 0.0))
+    chord = np.clip(np.minimum(hi_v, cv + h) - np.maximum(lo_v, cv - h), 0.0, None)
+    return float(chord.sum() * (u1 - u0) / m)
+
+
+def patch_area_on_box(box: np.ndarray, c: np.ndarray, a: float) -> float:
+    """Area of the box surface inside the ball B(c, a) (all six faces)."""
+    lo, hi = box[:3], box[3:]
+    tot = 0.0
+    for ax in range(3):
+        o = [i for i in range(3) if i != ax]
+        for fv in (lo[ax], hi[ax]):
+            d = c[ax] - fv
+            if abs(d) >= a:
+                continue
+            r = np.sqrt(a * a - d * d)
+            tot += _rect_disk_area(lo[o[0]], hi[o[0]], lo[o[1]], hi[o[1]], c[o[0]], c[o[1]], r)
+    return tot
 
 
 def wires(n_patches: int = 10_000, walks: int = 2048, a: float = 0.3,
-          seed: int = 0) -> Workload:
+          seed: int = 0, allow_wrapped: bool = True) -> Workload:
     """200-wire layout in the grounded box [0,64]^2 x [0,16].
 
-    Data: point source at the centre of wire 0 (outside the region).  Patch
-    sizes vary by patch: node orders 16^2, 24^2 or 32^2 and panel counts
-    4x8 .. 16x32, drawn per patch, so that one batch carries uneven systems
-    (32 .. 512 collocation points).
+    Data: point source at the centre of wire 0 (outside the region).  Centres
+    area-uniform on the wire faces (R15); a ball that reaches further faces of
+    its wire gives a wrapped patch.  Collocation points by the intersected area
+    (R8): n_p = clamp(round(area(S) / h^2), 32, 512), h = a / 8, as rings x
+    sectors with rings = round(sqrt(n_p / pi)); hemisphere nodes by area bucket
+    (R19): 16^2 on a flat patch, 24^2 up to 1.4 times its area, 32^2 above.
+    The generator's rejected-centre count is kept in `rejected`.
     """
     boxes = wire_layout(seed=seed)
     geom = Geometry(GEOM_BOX_MINUS_BOXES, lo=(0.0, 0.0, 0.0), hi=(64.0, 64.0, 16.0),
                     boxes=boxes)
     x0 = tuple(0.5 * (boxes[0, :3] + boxes[0, 3:]))
     data = Dirichlet(DATA_POINT_SOURCE, x0=x0, strength=1.0)
-    centers, _, _ = wire_patch_centers(boxes, n_patches, a, seed=seed + 1)
-    rng = np.random.Generator(np.random.PCG64(seed + 2))
-    # uneven collocation sizes: rings x sectors in {4..16} x {8..32}
-    rings = rng.choice(np.array([4, 8, 12, 16], dtype=np.int32), size=n_patches)
-    sectors = rng.choice(np.array([8, 16, 24, 32], dtype=np.int32), size=n_patches)
-    nodes = rng.choice(np.array([16, 24, 32], dtype=np.int32), size=n_patches)
+    centers, owner, nfaces, rejected = wire_patch_centers(boxes, n_patches, a, seed=seed + 1,
+                                                          allow_wrapped=allow_wrapped)
+    h = a / 8.0
+    flat_area = np.pi * a * a
+    rings = np.zeros(n_patches, np.int32)
+    sectors = np.zeros(n_patches, np.int32)
+    nodes = np.zeros(n_patches, np.int32)
+    for p in range(n_patches):
+        area = patch_area_on_box(boxes[owner[p]], centers[p], a) if nfaces[p] > 1 else flat_area
+        n_p = int(min(max(round(area / (h * h)), 32), 512))
+        nr = max(2, int(round(np.sqrt(n_p / np.pi))))
+        ns = max(8, int(round(n_p / nr)))
+        while nr * ns > 512:
+            ns -= 1
+        rings[p], sectors[p] = nr, ns
+        nodes[p] = 16 if area <= 1.0001 * flat_area else (24 if area <= 1.4 * flat_area else 32)
     batch = PatchBatch(centers=centers.astype(np.float64),
                        radius=np.full(n_patches, a),
                        n_theta=nodes.copy(), n_phi=nodes.copy(),
                        n_rings=rings, n_sectors=sectors,
                        walks=np.full(n_patches, walks, dtype=np.int64))
-    return Workload(f"wires200_{n_patches}p_uneven", geom, data, batch)
+    wl = Workload(f"wires200_{n_patches}p_by_area", geom, data, batch)
+    wl.rejected = rejected
+    wl.faces_met = nfaces
+    return wl
 
 
 def half_space_charge(depth: float = 1.0, truncation: float = 1e5) -> tuple:
