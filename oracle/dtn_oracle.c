@@ -1384,6 +1384,20 @@ static double panel_integral_ctx(quad_ctx c, const double prm[7], const double *
         area = p->R * p->R * (cos(u0) - cos(u1)) * (v1 - v0);
     }
     double tol = rtol * area / (4.0 * OR_PI * (d > diam ? d : diam));
+    if (c.kind >= 1 && c.kind <= 3) {
+        /* integrands that carry the data: relative to the integral of |f| (a
+         * 10 x 10 Gauss estimate), since area / (4 pi d) is the size of G alone
+         * and far from the data's own scale (a source far away makes g(y) -
+         * g(x) small) */
+        gl10_init();
+        const double hu = 0.5 * (u1 - u0), hv = 0.5 * (v1 - v0);
+        double mabs = 0.0;
+        for (int i = 0; i < 10; ++i)
+            for (int j = 0; j < 10; ++j)
+                mabs += gl10_w[i] * gl10_w[j] *
+                        fabs(integrand(&c, u0 + hu * (gl10_x[i] + 1.0), v0 + hv * (gl10_x[j] + 1.0)));
+        tol = rtol * mabs * hu * hv;
+    }
     if (!sing) return rect_integral(&c, u0, u1, v0, v1, tol);
     double S[2] = {sing[0], sing[1]};
     double cor[5][2] = {{u0, v0}, {u1, v0}, {u1, v1}, {u0, v1}, {u0, v0}};

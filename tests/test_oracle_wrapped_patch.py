@@ -156,3 +156,21 @@ def test_wrapped_solve_with_exact_values_away_from_edges():
     assert far.sum() >= 20
     err = np.abs(r["q"] - qe)[far] / np.max(np.abs(qe[far]))
     assert np.max(err) < 0.03, np.max(err)
+
+
+def test_right_side_converged_with_a_distant_source():
+    """The right side's data integrals are refined relative to their own size:
+    with the source of the wire workload 30 units away (g(y) - g(x) ~ 1e-4 of
+    the kernel's scale) the right side at rtol 1e-10 agrees with rtol 1e-12 to
+    1e-11 of max|b| (with the tolerance taken from the size of G alone they
+    differed by 1e-8)."""
+    wl = W.wires(n_patches=16, walks=2)
+    b = wl.batch
+    p = int(np.nonzero(wl.faces_met == 3)[0][0])
+    pf = O.patch_frame(wl.geometry, b.centers[p], float(b.radius[p]))
+    nt, nph, nr, ns = int(b.n_theta[p]), int(b.n_phi[p]), int(b.n_rings[p]), int(b.n_sectors[p])
+    _, yg, _ = O.gamma_nodes(pf, nt, nph)
+    U = O.dirichlet(wl.data, yg)
+    _, b10 = O.assemble(pf, wl.data, nr, ns, nt, nph, U, rtol=1e-10)
+    _, b12 = O.assemble(pf, wl.data, nr, ns, nt, nph, U, rtol=1e-12)
+    assert np.max(np.abs(b10 - b12)) <= 1e-11 * np.max(np.abs(b12))
