@@ -447,7 +447,8 @@ void or_wos_points(const or_geom *g, const or_data *dat, int64_t n, const double
 /* One piece of a wrapped patch: a face rectangle of the box cut by the ball,
  * i.e. rectangle intersect disk (the ball's slice of the face plane), a convex
  * region described in polar coordinates (rho, phi) about P, its point nearest
- * the disk centre: rho <= rho_max(phi) for phi in [sub[0], sub[nsub]].  The
+ * the disk centre (moved onto a rectangle side closer than rf/4, see
+ * make_piece): rho <= rho_max(phi) for phi in [sub[0], sub[nsub]].  The
  * angle range is cut at the angles where rho_max changes from one rectangle
  * side or the circle to another, so rho_max is smooth between cuts. */
 typedef struct {
@@ -539,10 +540,29 @@ static int make_piece(const double lo[3], const double hi[3], int f, const doubl
         q->rhi[k] = hi[ax2[k]];
         q->cf[k] = c[ax2[k]];
         q->P[k] = fmin(fmax(q->cf[k], q->rlo[k]), q->rhi[k]);
+    }
+    q->rf = sqrt(a * a - d * d);
+    {
+        /* a polar origin closer than rf/4 to a rectangle side moves onto that
+         * side (onto the corner when near two), as long as it stays well inside
+         * the disk: the rays from P would otherwise cross a thin strip between
+         * P and the side, whose rings are sliver panels (aspect ratios in the
+         * thousands, collocation systems with condition numbers 1e3 and more) */
+        const double snap = 0.25 * q->rf;
+        for (int k = 0; k < 2; ++k) {
+            const double dl = q->P[k] - q->rlo[k], dh = q->rhi[k] - q->P[k];
+            const double t = dl <= dh ? q->rlo[k] : q->rhi[k];
+            if ((dl <= dh ? dl : dh) < snap) {
+                double Pt[2] = {q->P[0], q->P[1]};
+                Pt[k] = t;
+                if (hypot(Pt[0] - q->cf[0], Pt[1] - q->cf[1]) < 0.9 * q->rf) q->P[k] = t;
+            }
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
         q->onlo[k] = (q->P[k] == q->rlo[k]);
         q->onhi[k] = (q->P[k] == q->rhi[k]);
     }
-    q->rf = sqrt(a * a - d * d);
     const double dP = hypot(q->P[0] - q->cf[0], q->P[1] - q->cf[1]);
     if (!(dP < q->rf)) return 0;
     /* the angles of the rays from P into the rectangle: every side through P

@@ -174,7 +174,9 @@ def load(path: str = LIB_PATH):
 
 def _check(code: int, what: str):
     if code != 0:
-        raise DtnError(code, what)
+        # a failed CUDA runtime call: name it (cudaError_t value)
+        cu = load().dtn_last_cuda_error() if code in (2, 3) else 0
+        raise DtnError(code, what + (f" [cudaError {cu}]" if cu else ""))
 
 
 def _ptr(t):

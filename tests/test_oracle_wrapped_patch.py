@@ -174,3 +174,27 @@ def test_right_side_converged_with_a_distant_source():
     _, b10 = O.assemble(pf, wl.data, nr, ns, nt, nph, U, rtol=1e-10)
     _, b12 = O.assemble(pf, wl.data, nr, ns, nt, nph, U, rtol=1e-12)
     assert np.max(np.abs(b10 - b12)) <= 1e-11 * np.max(np.abs(b12))
+
+
+def test_polar_origin_moves_onto_a_near_side():
+    """A centre 0.002 from the long edge of the top face: the top piece's polar
+    origin moves onto that edge (0.002 < rf/4); left where it was, the rings of
+    the strip between it and the edge would be panels 0.6 long and 0.0005 wide.
+    The pieces keep their closed-form areas and the collocation matrix stays
+    well conditioned."""
+    d = 0.002
+    geo, data = _geo(), _data()
+    p = O.patch_frame(geo, (2.0, 1.0 + d, 1.7), A)
+    q = p.piece[0]
+    assert q.ax == 2 and q.onlo[1] == 1 and q.P[1] == 1.0 and q.P[0] == 2.0
+    seg = A * A * math.acos(d / A) - d * math.sqrt(A * A - d * d)
+    areas = [pc[2] for pc in p.pieces()]
+    assert abs(areas[0] - (math.pi * A * A - seg)) < 1e-13
+    assert abs(areas[1] - 0.5 * math.pi * (A * A - d * d)) < 1e-13
+    nt, nph, nr, ns = 12, 24, 4, 24
+    _, yg, _ = O.gamma_nodes(p, nt, nph)
+    Am, _ = O.assemble(p, data, nr, ns, nt, nph, O.dirichlet(data, yg), rtol=1e-8)
+    pan = O.panels(p, nr, ns)
+    assert abs(pan["area"].sum() - sum(areas)) < 1e-12
+    assert pan["area"].max() / pan["area"].min() < 20
+    assert np.linalg.cond(Am) < 100
