@@ -985,10 +985,11 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         if (e == cudaSuccess)
             e = launch_rhs_shared(g, L, D, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
                                   W.gw.as<float>(), W.vec.as<float>(), rhs, s);
-        // wrapped patches: their right sides by the FP64 panel rules, row by row
+        // wrapped patches (groups of their own): matrix rows and right sides by
+        // the panel rules, row by row
         if (e == cudaSuccess && std::find(L.wrapped.begin(), L.wrapped.end(), 1) != L.wrapped.end())
             e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                                nullptr, rhs, s, 0, 1);
+                                gA, rhs, s, 0, 1);
         if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
     } else {
         e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,

@@ -221,6 +221,162 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
     }
 }
 
+// FP32 tensor rule on a wrapped patch's panel or part of one (mixed
+// precision).  A wrapped patch lies anywhere in the box, and the data of a
+// distant source vary little over it, so the points' coordinates and g(y) -
+// g(x) would lose most of FP32's digits to cancellation.  Instead every
+// quantity is built from offsets: the rectangle centre's offsets from X, from
+// its Kelvin image X* and (global axes) the data difference are formed in FP64
+// once, and a Gauss point adds its in-plane offset from the centre, (u - uc)
+// B(w) + uc (B(w) - B(wc)), whose parts are small and exact to FP32 rounding.
+// On the flat piece n_y.(X - Y) and |X|^2 n_y.Y - a^2 n_y.X do not depend on
+// the point.  G and dG/dn_y then keep FP32's relative accuracy; a point-source
+// difference is taken as -q d.(2e + d) / (|e + d| |e| (|e + d| + |e|)), e = x -
+// x0, d = y - x; other data are differenced in FP64 at the point.
+struct WF32 {
+    float Dc[3], Ds[3], e[3], ne, gi, g0, k1, k2, qf;
+    double xg[3];
+    bool point, img, needA, needD;
+};
+
+// G = (1/r - gi / rs - g0) / 4pi;  dG/dn_y = (k1 / r^3 + k2 / rs^3) / 4pi
+__device__ void wf32_setup(const Ctx<double> &c, double uc, double wc, double Bc[3], WF32 &W) {
+    const Piece &q = *c.pc;
+    double Jc;
+    wrapped_line(q, c.sub, wc, Bc, Jc);
+    double Dl[3], Dsl[3];
+    for (int d = 0; d < 3; ++d) {
+        const double yc = q.Pl[d] + uc * Bc[d];
+        Dl[d] = yc - c.X[d];
+        Dsl[d] = c.img ? yc - c.Xs[d] : 0.0;
+    }
+    const double xx = c.xn * c.xn;
+    double nyX = 0.0, nyP = 0.0, nyXP = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        nyX += q.nl[d] * c.X[d];
+        nyP += q.nl[d] * q.Pl[d];
+        nyXP += q.nl[d] * (c.X[d] - q.Pl[d]);
+        W.xg[d] = c.c[d] + c.X[0] * c.t1[d] + c.X[1] * c.t2[d] + c.X[2] * c.n[d];
+        W.Dc[d] = (float)(Dl[0] * c.t1[d] + Dl[1] * c.t2[d] + Dl[2] * c.n[d]);
+        W.Ds[d] = (float)(Dsl[0] * c.t1[d] + Dsl[1] * c.t2[d] + Dsl[2] * c.n[d]);
+    }
+    W.img = c.img;
+    W.gi = c.img ? (float)(c.a / c.xn) : 0.f;
+    W.g0 = c.img ? 0.f : (float)(1.0 / c.a);
+    W.k1 = (float)nyXP;
+    W.k2 = c.img ? (float)(c.a * (xx * nyP - c.a * c.a * nyX) / (xx * c.xn)) : 0.f;
+    const int dk = c.dat->kind;
+    W.point = (dk == kPointSource);
+    W.needA = c.needA;
+    W.needD = c.needD && dk != kConstant;
+    W.ne = 0.f;
+    W.qf = c.dat->q_f;
+    W.e[0] = W.e[1] = W.e[2] = 0.f;
+    if (W.point) {
+        double sq = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double ed = W.xg[d] - c.dat->x0[d];
+            sq += ed * ed;
+            W.e[d] = (float)ed;
+        }
+        W.ne = (float)sqrt(sq);
+    }
+}
+
+// line w of the rule: B(w) and uc (B(w) - B(wc)) in global axes, the Jacobian factor
+__device__ __forceinline__ void wf32_line(const Ctx<double> &c, double w, double uc, const double Bc[3], float *Bg,
+                                          float *dBg, float &Jf) {
+    double B[3], J;
+    wrapped_line(*c.pc, c.sub, w, B, J);
+    const double dB[3] = {uc * (B[0] - Bc[0]), uc * (B[1] - Bc[1]), uc * (B[2] - Bc[2])};
+    for (int d = 0; d < 3; ++d) {
+        Bg[d] = (float)(B[0] * c.t1[d] + B[1] * c.t2[d] + B[2] * c.n[d]);
+        dBg[d] = (float)(dB[0] * c.t1[d] + dB[1] * c.t2[d] + dB[2] * c.n[d]);
+    }
+    Jf = (float)J;
+}
+
+// one point: offset dui = u - uc along B, weight w (Gauss weights, u, Jf)
+__device__ __forceinline__ void wf32_point(const Ctx<double> &c, const WF32 &W, float dui, const float *Bg,
+                                           const float *dBg, float w, float &la, float &ld) {
+    const float ox = fmaf(dui, Bg[0], dBg[0]), oy = fmaf(dui, Bg[1], dBg[1]), oz = fmaf(dui, Bg[2], dBg[2]);
+    const float dx = ox + W.Dc[0], dy = oy + W.Dc[1], dz = oz + W.Dc[2];
+    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float irs = 0.f;
+    if (W.img) {
+        const float sx = ox + W.Ds[0], sy = oy + W.Ds[1], sz = oz + W.Ds[2];
+        irs = rsqrtf(sx * sx + sy * sy + sz * sz);
+    }
+    if (W.needA) la += w * (ir - W.gi * irs - W.g0);
+    if (W.needD) {
+        float dg;
+        if (W.point) {
+            const float px = W.e[0] + dx, py = W.e[1] + dy, pz = W.e[2] + dz;
+            const float rp = sqrtf(px * px + py * py + pz * pz);
+            const float num = dx * (W.e[0] + px) + dy * (W.e[1] + py) + dz * (W.e[2] + pz);
+            dg = -W.qf * __fdividef(num, rp * W.ne * (rp + W.ne));
+        } else {
+            dg = (float)(dirichlet_eval<double>(*c.dat, W.xg[0] + (double)dx, W.xg[1] + (double)dy,
+                                               W.xg[2] + (double)dz) - c.gx);
+        }
+        ld += w * (W.k1 * ir * ir * ir + W.k2 * irs * irs * irs) * dg;
+    }
+}
+
+// a whole far panel (box prm, order n) by one thread
+__device__ void far_wrapped_f32(const Ctx<double> &c, const double *prm, int n, const double *__restrict__ glx,
+                                const double *__restrict__ glw, double &sa_out, double &sd_out) {
+    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
+    const double u0 = prm[0], du = prm[1] - prm[0], w0 = prm[2], dw = prm[3] - prm[2], uc = prm[4], wc = prm[5];
+    WF32 W;
+    double Bc[3];
+    wf32_setup(c, uc, wc, Bc, W);
+    float Bg[kMaxRule][3], dBg[kMaxRule][3], Jf[kMaxRule];
+    for (int jj = 0; jj < n; ++jj) wf32_line(c, w0 + (0.5 + 0.5 * gx[jj]) * dw, uc, Bc, Bg[jj], dBg[jj], Jf[jj]);
+    float sa = 0.f, sd = 0.f;
+    for (int i = 0; i < n; ++i) {
+        const double ud = u0 + (0.5 + 0.5 * gx[i]) * du;
+        const float u = (float)ud, dui = (float)(ud - uc);
+        float la = 0.f, ld = 0.f;
+        for (int jj = 0; jj < n; ++jj) wf32_point(c, W, dui, Bg[jj], dBg[jj], (float)gw[jj] * u * Jf[jj], la, ld);
+        const float wi = (float)(gw[i] * 0.25 * du * dw);
+        sa += wi * la;
+        sd += wi * ld;
+    }
+    sa_out = (double)sa * (0.25 / kPi);
+    sd_out = (double)sd * (0.25 / kPi);
+}
+
+// Line data of one warp's current rectangle (warp-cooperative rule below).
+struct WLines {
+    float Bg[kMaxRule][3], dBg[kMaxRule][3], Jf[kMaxRule];
+};
+
+// the rectangle [ua, ub] x [wa, wb] of a panel's quadrature parameters, order
+// n, by the lanes of a warp (points dealt in turn); each lane adds its part,
+// times 1/4pi, to sa and sd
+__device__ void rect_wrapped_f32_warp(const Ctx<double> &c, double ua, double ub, double wa, double wb, int n,
+                                      const double *__restrict__ glx, const double *__restrict__ glw, WLines &Ls,
+                                      int lane, double &sa, double &sd) {
+    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
+    const double uc = 0.5 * (ua + ub), wc = 0.5 * (wa + wb), hu = 0.5 * (ub - ua), hw = 0.5 * (wb - wa);
+    WF32 W;
+    double Bc[3];
+    wf32_setup(c, uc, wc, Bc, W);
+    __syncwarp();
+    if (lane < n) wf32_line(c, wc + hw * gx[lane], uc, Bc, Ls.Bg[lane], Ls.dBg[lane], Ls.Jf[lane]);
+    __syncwarp();
+    float la = 0.f, ld = 0.f;
+    for (int k = lane; k < n * n; k += 32) {
+        const int i = k / n, jj = k - i * n;
+        const double ud = uc + hu * gx[i];
+        const float w = (float)(gw[i] * gw[jj] * hu * hw) * (float)ud * Ls.Jf[jj];
+        wf32_point(c, W, (float)(ud - uc), Ls.Bg[jj], Ls.dBg[jj], w, la, ld);
+    }
+    sa += (double)la * (0.25 / kPi);
+    sd += (double)ld * (0.25 / kPi);
+}
+
 // Gauss order from the distance ratio r (0: split further), aiming at 1e-15
 // relative for a singularity next to the middle of a panel edge.
 __device__ __forceinline__ int order64(double r) {
@@ -360,6 +516,7 @@ struct AsmDev {
     int mode;   // 0 matrix and right side per patch, 1 matrix per shape group, 2 right side only
     int sk;     // second-kind system (1/2 I - D) q = b instead of Eq. bw49-bw51
     int only_wrapped;   // mode 2: the rows of wrapped patches only (the others are left untouched)
+    const int64_t *group_of;   // mode 2: a wrapped patch's group (its matrix in A, gmat_off)
     const double *glx, *glw;
     const Piece *pieces;        // n_patches x kMaxPieces, or nullptr
     const int32_t *panel_piece; // per panel
@@ -408,6 +565,89 @@ __device__ void self_triangles(const Ctx<double> &c, const double *prm, Fn &&fn)
     }
 }
 
+
+// Self panel of a wrapped patch, whose panels can be long and thin (a sector of
+// a strip along a box edge): the parameter box is cut at the singular point
+// into four quadrants, and a quadrant whose physical sides differ by more than
+// 2:1 is cut along its long side at lengths l, 2l, 4l, ... from the point (l the
+// short side), so that every piece is about as long as its distance from the
+// point.  The piece at the point takes two Duffy triangles from it, their far
+// sides cut as in self_triangles (fn(R, false, 16)); the others the adaptive
+// cover with the point as a singular point (fn(R, true, 0)).
+template <typename Fn>
+__device__ void self_regions(const Ctx<double> &c, const double *prm, Fn &&fn) {
+    const double us = prm[4], ws = prm[5];
+    const double ucs[2] = {prm[0], prm[1]}, wcs[2] = {prm[2], prm[3]};
+    double X[3], nl[3], J;
+    ctx_point<double>(c, us, ws, X, nl, J);
+    auto dist = [](const double *A, const double *B) {
+        return sqrt((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]));
+    };
+    for (int qu = 0; qu < 2; ++qu)
+        for (int qw = 0; qw < 2; ++qw) {
+            const double uC = ucs[qu], wC = wcs[qw];
+            if (uC == us || wC == ws) continue;
+            double Pa[3], Pm[3], Pb[3];
+            ctx_point<double>(c, uC, ws, Pa, nl, J);
+            ctx_point<double>(c, us, ws + 0.5 * (wC - ws), Pm, nl, J);
+            ctx_point<double>(c, us, wC, Pb, nl, J);
+            const double lu = dist(Pa, X), lw = dist(Pm, X) + dist(Pb, Pm);
+            // graded direction (1: u, 2: w) and the first cut as a fraction
+            int along = 0;
+            double f0 = 1.0;
+            if (lw > 2.0 * lu) { along = 2; f0 = lu / lw; }
+            else if (lu > 2.0 * lw) { along = 1; f0 = lw / lu; }
+            f0 = fmax(f0, 1.0 / 1048576.0);
+            double fa = 0.0, fb = f0;
+            for (int k = 0;; ++k) {
+                double a1 = uC, b1 = wC, a0 = us, b0 = ws;
+                if (along == 1) { a0 = us + fa * (uC - us); a1 = us + fb * (uC - us); }
+                if (along == 2) { b0 = ws + fa * (wC - ws); b1 = ws + fb * (wC - ws); }
+                if (k == 0) {
+                    // Duffy triangles (S, (a1, ws), (a1, b1)) and (S, (a1, b1), (us, b1)),
+                    // each far side cut into pieces no longer than the triangle's
+                    // height (four if it maps to one point)
+                    const double ta[2][2] = {{a1, ws}, {a1, b1}}, tb[2][2] = {{a1, b1}, {us, b1}};
+                    for (int t = 0; t < 2; ++t) {
+                        double PA[3], PB[3];
+                        ctx_point<double>(c, ta[t][0], ta[t][1], PA, nl, J);
+                        ctx_point<double>(c, tb[t][0], tb[t][1], PB, nl, J);
+                        const double ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
+                        const double as[3] = {X[0] - PA[0], X[1] - PA[1], X[2] - PA[2]};
+                        const double cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2],
+                                              ab[0] * as[1] - ab[1] * as[0]};
+                        const double L = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+                        const double h = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmax(L, 1e-300);
+                        int m = (int)fmin(64.0, fmax(1.0, ceil(L / fmax(h, 1e-300))));
+                        if (L <= 1e-9 * sqrt(as[0] * as[0] + as[1] * as[1] + as[2] * as[2])) m = 4;
+                        for (int e = 0; e < m; ++e) {
+                            const double Au = ta[t][0] + (tb[t][0] - ta[t][0]) * e / m;
+                            const double Aw = ta[t][1] + (tb[t][1] - ta[t][1]) * e / m;
+                            const double Bu = ta[t][0] + (tb[t][0] - ta[t][0]) * (e + 1) / m;
+                            const double Bw = ta[t][1] + (tb[t][1] - ta[t][1]) * (e + 1) / m;
+                            Region R;
+                            R.tri = true;
+                            R.p[0] = us; R.p[1] = ws;
+                            R.p[2] = Au - us; R.p[3] = Aw - ws;
+                            R.p[4] = Bu - Au; R.p[5] = Bw - Aw;
+                            R.det = fabs(R.p[2] * R.p[5] - R.p[3] * R.p[4]);
+                            if (R.det > 0.0) fn(R, false, 16);
+                        }
+                    }
+                } else {
+                    Region R;
+                    R.tri = false;
+                    R.p[0] = fmin(a0, a1); R.p[1] = fabs(a1 - a0);
+                    R.p[2] = fmin(b0, b1); R.p[3] = fabs(b1 - b0);
+                    R.det = 0.0;
+                    fn(R, true, 0);
+                }
+                if (along == 0 || fb >= 1.0) break;
+                fa = fb;
+                fb = fmin(1.0, 2.0 * fb);
+            }
+        }
+}
 
 // The Gauss rule of order nq on one sub-square of a region, its points dealt
 // to the lanes of a warp in turn (each lane sums its own points).
@@ -461,6 +701,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const int64_t poff = P.panel_off[p];
     __shared__ double red[2][kAsmThreads / 32];
     if (P.only_wrapped && f.kind != kWrapped) return;
+    // a wrapped patch is a group of its own: its matrix rows and right side are
+    // assembled together by the mode-2 pass, into its group matrix
+    if (P.mode == 1 && f.kind == kWrapped) return;
+    if (P.mode == 2 && P.A) Arow = P.A + P.gmat_off[P.group_of[p]] + (int64_t)i * n;
     const Piece *pcs = (f.kind == kWrapped) ? P.pieces + p * kMaxPieces : nullptr;
     if (P.mode != 1 && f.status != DTN_OK) {
         if (Arow)
@@ -473,19 +717,15 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     Ctx<double> c64;
     make_ctx<double>(c64, f, X, gx, &P.dat);
     if (P.mode == 1) c64.needD = false;
-    if (P.mode == 2) c64.needA = false;
-    // mixed precision on a wrapped patch (a matrix of its own): far panels by
-    // FP32 rules, near, self and image-near panels by the FP64 ones
+    if (P.mode == 2) c64.needA = (Arow != nullptr);
+    // mixed precision on a wrapped patch (a matrix of its own): far panels and
+    // the rectangles of the near panels' covers by the FP32 rule in offset
+    // form (far_wrapped_f32), the self panel by the FP64 rules
     const bool far32 = (P.prec == DTN_PREC_MIXED && f.kind == kWrapped && !SK);
-    Ctx<float> c32;
-    if (far32) {
-        make_ctx<float>(c32, f, X, gx, &P.dat);
-        c32.needA = c64.needA;
-        c32.needD = c64.needD;
-    }
     __shared__ int near_list[1024];
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
+    __shared__ WLines wlines[kAsmThreads / 32];
     __shared__ double sk_grad[2];
     double e1[3] = {0.0, 0.0, 0.0}, e2[3] = {0.0, 0.0, 0.0};
     if (SK) {
@@ -553,11 +793,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
         if (far32) {
-            ctx_panel(c32, pcs, P.panel_piece[pj]);
-            float sa32 = 0.f, sd32 = 0.f;
-            gauss_rect<float>(c32, R, 0.f, 1.f, 0.f, 1.f, order64(r), P.glx, P.glw, sa32, sd32);
-            sa = sa32;
-            sd = sd32;
+            ctx_panel(c64, pcs, P.panel_piece[pj]);
+            far_wrapped_f32(c64, prm, order64(r), P.glx, P.glw, sa, sd);
         } else {
             ctx_panel(c64, pcs, P.panel_piece[pj]);
             gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
@@ -571,12 +808,14 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         double sa = 0.0, sd = 0.0;
         int tri = 0;
         ctx_panel(c64, pcs, P.panel_piece[row]);
-        self_triangles(c64, P.panel_prm + 6 * row, [&](const Region &R) {
+        auto region = [&](const Region &R, bool withX, int min_order) {
             if ((tri++ % (kAsmThreads / 32)) != warp) return;
-            adaptive_squares<double>(c64, R, false, 16, [&](double x0, double x1, double e0, double e1, int nq) {
+            adaptive_squares<double>(c64, R, withX, min_order, [&](double x0, double x1, double e0, double e1, int nq) {
                 coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
             });
-        });
+        };
+        if (f.kind == kWrapped) self_regions(c64, P.panel_prm + 6 * row, region);
+        else self_triangles(c64, P.panel_prm + 6 * row, [&](const Region &R) { region(R, false, 16); });
         for (int o = 16; o > 0; o >>= 1) {
             sa += __shfl_xor_sync(0xffffffffu, sa, o);
             sd += __shfl_xor_sync(0xffffffffu, sd, o);
@@ -607,9 +846,17 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
         ctx_panel(c64, pcs, P.panel_piece[poff + j]);
-        adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
-            coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
-        });
+        if (far32) {
+            // mixed precision on a wrapped patch: the cover's rectangles by the FP32 rule
+            adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
+                rect_wrapped_f32_warp(c64, R.p[0] + x0 * R.p[1], R.p[0] + x1 * R.p[1], R.p[2] + e0 * R.p[3],
+                                      R.p[2] + e1 * R.p[3], nq, P.glx, P.glw, wlines[warp], lane, sa, sd);
+            });
+        } else {
+            adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
+                coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
+            });
+        }
         for (int o = 16; o > 0; o >>= 1) {
             sa += __shfl_xor_sync(0xffffffffu, sa, o);
             sd += __shfl_xor_sync(0xffffffffu, sd, o);
@@ -944,6 +1191,7 @@ __global__ void __launch_bounds__(kGemmThreads) rhs_product_kernel(RhsDev P) {
     const int row0 = rt * kGemmM;
     if (row0 >= n) return;
     const int64_t kc = P.kcols[grp];
+    if (kc == 0) return;   // a wrapped patch's group: its right side is assembled directly
     const float *W = P.gw + P.gw_off[grp];
     const int64_t m0 = P.mem_off[grp] + (tile - P.tile_off[grp]) * kRhsTileN;
     const int mcount = (int)min((int64_t)kRhsTileN, P.mem_off[grp + 1] - m0);
@@ -1043,6 +1291,7 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.mode = mode;
     P.sk = sk;
     P.only_wrapped = only_wrapped;
+    P.group_of = D.group_of;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
     P.pieces = D.pieces;
@@ -1082,9 +1331,12 @@ cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const
     }
     rhs_walk_weights_kernel<<<dim3(rows, (unsigned)((L.max_nodes + kWtThreads - 1) / kWtThreads)), kWtThreads, 0, s>>>(Wd);
     const int T = 256;
-    rhs_samples_kernel<<<(unsigned)((L.vec_total + T - 1) / T), T, 0, s>>>(
-        g->dd, L.n_patches, L.vec_total, D.vec_off, D.panel_off, D.gamma_off, D.frames, panel_prm, panel_g, U,
-        Wd.glx, vec);
+    // (a batch of wrapped patches only has weight rows without columns: their
+    // right sides are assembled directly, and there are no samples)
+    if (L.vec_total > 0)
+        rhs_samples_kernel<<<(unsigned)((L.vec_total + T - 1) / T), T, 0, s>>>(
+            g->dd, L.n_patches, L.vec_total, D.vec_off, D.panel_off, D.gamma_off, D.frames, panel_prm, panel_g, U,
+            Wd.glx, vec);
     RhsDev R;
     R.frames = D.frames;
     R.panel_off = D.panel_off;

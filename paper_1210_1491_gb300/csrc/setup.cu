@@ -155,10 +155,23 @@ __device__ bool make_piece(const double *lo, const double *hi, int fc, const dou
         q.rhi[k] = hi[ax2[k]];
         q.cf[k] = c[ax2[k]];
         q.P[k] = fmin(fmax(q.cf[k], q.rlo[k]), q.rhi[k]);
+    }
+    q.rf = sqrt(a * a - d * d);
+    // a polar origin closer than rf/4 to a rectangle side moves onto it (onto
+    // the corner when near two) if it stays well inside the disk: otherwise the
+    // rings of the thin strip between it and the side are sliver panels
+    for (int k = 0; k < 2; ++k) {
+        const double dl = q.P[k] - q.rlo[k], dh = q.rhi[k] - q.P[k];
+        if (fmin(dl, dh) < 0.25 * q.rf) {
+            const double t = dl <= dh ? q.rlo[k] : q.rhi[k];
+            const double e0 = (k == 0 ? t : q.P[0]) - q.cf[0], e1 = (k == 1 ? t : q.P[1]) - q.cf[1];
+            if (hypot(e0, e1) < 0.9 * q.rf) q.P[k] = t;
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
         q.onlo[k] = (q.P[k] == q.rlo[k]);
         q.onhi[k] = (q.P[k] == q.rhi[k]);
     }
-    q.rf = sqrt(a * a - d * d);
     if (!(hypot(q.P[0] - q.cf[0], q.P[1] - q.cf[1]) < q.rf)) return false;
     // angle range: halved by each rectangle side through P
     double ph0 = 0.0, ph1 = 2.0 * kPi;
