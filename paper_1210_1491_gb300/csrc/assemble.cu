@@ -296,10 +296,10 @@ __device__ __forceinline__ void wf32_line(const Ctx<double> &c, double w, double
     Jf = (float)J;
 }
 
-// one point: offset dui = u - uc along B, weight w (Gauss weights, u, Jf)
-__device__ __forceinline__ void wf32_point(const Ctx<double> &c, const WF32 &W, float dui, const float *Bg,
-                                           const float *dBg, float w, float &la, float &ld) {
-    const float ox = fmaf(dui, Bg[0], dBg[0]), oy = fmaf(dui, Bg[1], dBg[1]), oz = fmaf(dui, Bg[2], dBg[2]);
+// one point given by its offset (ox, oy, oz) from the rectangle centre (global
+// axes), weight w (Gauss weights, Jacobians)
+__device__ __forceinline__ void wf32_eval(const Ctx<double> &c, const WF32 &W, float ox, float oy, float oz, float w,
+                                          float &la, float &ld) {
     const float dx = ox + W.Dc[0], dy = oy + W.Dc[1], dz = oz + W.Dc[2];
     const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
     float irs = 0.f;
@@ -321,6 +321,129 @@ __device__ __forceinline__ void wf32_point(const Ctx<double> &c, const WF32 &W, 
         }
         ld += w * (W.k1 * ir * ir * ir + W.k2 * irs * irs * irs) * dg;
     }
+}
+
+// one point of a tensor rule: offset dui = u - uc along B(w), line data Bg, dBg
+__device__ __forceinline__ void wf32_point(const Ctx<double> &c, const WF32 &W, float dui, const float *Bg,
+                                           const float *dBg, float w, float &la, float &ld) {
+    wf32_eval(c, W, fmaf(dui, Bg[0], dBg[0]), fmaf(dui, Bg[1], dBg[1]), fmaf(dui, Bg[2], dBg[2]), w, la, ld);
+}
+
+// Gauss order of the FP32 rules for a ratio order n of order64: the orders
+// that order64 takes for 1e-15 give about 1e-10 at two thirds of the points
+// per direction, far below FP32 rounding
+__device__ __forceinline__ int order32(int n) {
+    return n >= 20 ? 14 : n >= 12 ? 8 : n >= 9 ? 6 : 4;
+}
+
+// The self panel of a wrapped patch in FP32 (mixed precision): a point's
+// offset from the collocation point S is built from its parameter offsets
+// (du, dw) from S, which are exact, through the sub-range's map: on a side-
+// bounded sub-range B(w) = en + w et (so B(w) - B(ws) = dw et); on a circle-
+// bounded one B(v) = rho(v) e(v) with e(v) - e(vs) = 2 sin(dv/2) e'(vs + dv/2)
+// and, when P is not the slice centre, rho(v) - rho(vs) = (p - ps) (-1 + (p +
+// ps) / (sqrt D + sqrt Ds)), p = (P - cf).e, D = p^2 - |P - cf|^2 + rf^2.  The
+// offset is du B(w) + us (B(w) - B(ws)): the 1/r singularity at S is met with
+// FP32's relative accuracy, and the Duffy factor removes it as in FP64.
+struct SelfF32 {
+    WF32 W;
+    int type;          // 1: rectangle side, 0: circle about P, 2: circle, P off the slice centre
+    float us, ws;
+    double usd, wsd;                     // S exactly (the offsets of a box's points are taken from it)
+    float eg[3], tg[3], js;              // side: B(w) = eg + w tg, Jf = js
+    float Ug[3], Vg[3], rf;              // circle
+    float w2[2], ww, ps, sDs, rhos;      // off-centre circle
+};
+
+__device__ void self_f32_setup(const Ctx<double> &c, const double *prm, SelfF32 &S) {
+    const Piece &q = *c.pc;
+    const int j = c.sub;
+    double Bc[3];
+    wf32_setup(c, prm[4], prm[5], Bc, S.W);
+    S.us = (float)prm[4];
+    S.ws = (float)prm[5];
+    S.usd = prm[4];
+    S.wsd = prm[5];
+    for (int d = 0; d < 3; ++d) {
+        S.eg[d] = (float)(q.en[j][0] * c.t1[d] + q.en[j][1] * c.t2[d] + q.en[j][2] * c.n[d]);
+        S.tg[d] = (float)(q.et[j][0] * c.t1[d] + q.et[j][1] * c.t2[d] + q.et[j][2] * c.n[d]);
+        S.Ug[d] = (float)(q.Ul[0] * c.t1[d] + q.Ul[1] * c.t2[d] + q.Ul[2] * c.n[d]);
+        S.Vg[d] = (float)(q.Vl[0] * c.t1[d] + q.Vl[1] * c.t2[d] + q.Vl[2] * c.n[d]);
+    }
+    S.js = (float)(q.sdist[j] * q.sdist[j]);
+    S.rf = (float)q.rf;
+    S.type = q.stype[j] ? 1 : (q.centred ? 0 : 2);
+    const double w0 = q.P[0] - q.cf[0], w1 = q.P[1] - q.cf[1];
+    double sv, cv;
+    sincos(prm[5], &sv, &cv);
+    const double ps = w0 * cv + w1 * sv, ww = w0 * w0 + w1 * w1;
+    const double sDs = sqrt(fmax(0.0, ps * ps - ww + q.rf * q.rf));
+    S.w2[0] = (float)w0;
+    S.w2[1] = (float)w1;
+    S.ww = (float)ww;
+    S.ps = (float)ps;
+    S.sDs = (float)sDs;
+    S.rhos = (float)(-ps + sDs);
+}
+
+// a point at parameter offsets (du, dw) from S, weight wt (Gauss weights, region Jacobian)
+__device__ __forceinline__ void self_f32_point(const Ctx<double> &c, const SelfF32 &S, float du, float dw, float wt,
+                                               float &la, float &ld) {
+    const float u = S.us + du;
+    float o[3], J;
+    if (S.type == 1) {
+        const float w = S.ws + dw;
+        for (int d = 0; d < 3; ++d) o[d] = du * fmaf(w, S.tg[d], S.eg[d]) + S.us * (dw * S.tg[d]);
+        J = S.js * u;
+    } else {
+        float sv, cv, sm, cm;
+        sincosf(S.ws + dw, &sv, &cv);
+        sincosf(S.ws + 0.5f * dw, &sm, &cm);
+        const float h = 2.f * sinf(0.5f * dw);
+        const float de0 = -h * sm, de1 = h * cm;   // e(v) - e(vs) in (U, V)
+        float rho = S.rf, drho = 0.f;
+        if (S.type == 2) {
+            const float pv = S.w2[0] * cv + S.w2[1] * sv;
+            const float dp = S.w2[0] * de0 + S.w2[1] * de1;
+            const float sD = sqrtf(fmaxf(0.f, pv * pv - S.ww + S.rf * S.rf));
+            rho = -pv + sD;
+            drho = dp * (-1.f + __fdividef(pv + S.ps, sD + S.sDs));
+        }
+        const float rs = (S.type == 2) ? S.rhos : S.rf;
+        for (int d = 0; d < 3; ++d) {
+            const float e = cv * S.Ug[d] + sv * S.Vg[d];
+            const float dB = drho * e + rs * (de0 * S.Ug[d] + de1 * S.Vg[d]);
+            o[d] = du * (rho * e) + S.us * dB;
+        }
+        J = rho * rho * u;
+    }
+    wf32_eval(c, S.W, o[0], o[1], o[2], wt * J, la, ld);
+}
+
+// one accepted sub-square of a self region, its points dealt to the lanes
+__device__ void self_f32_square(const Ctx<double> &c, const SelfF32 &S, const Region &R, double x0, double x1,
+                                double e0, double e1, int nq, const double *__restrict__ glx,
+                                const double *__restrict__ glw, int lane, double &sa, double &sd) {
+    const double *gx = glx + nq * (nq - 1) / 2, *gw = glw + nq * (nq - 1) / 2;
+    const double hx = 0.5 * (x1 - x0), mx = 0.5 * (x0 + x1), he = 0.5 * (e1 - e0), me = 0.5 * (e0 + e1);
+    float la = 0.f, ld = 0.f;
+    for (int k = lane; k < nq * nq; k += 32) {
+        const int qi = k / nq, qj = k - qi * nq;
+        const double xi = mx + hx * gx[qi], eta = me + he * gx[qj];
+        double du, dw, jac;
+        if (R.tri) {
+            du = xi * (R.p[2] + eta * R.p[4]);
+            dw = xi * (R.p[3] + eta * R.p[5]);
+            jac = xi * R.det;
+        } else {
+            du = (R.p[0] - S.usd) + xi * R.p[1];
+            dw = (R.p[2] - S.wsd) + eta * R.p[3];
+            jac = R.p[1] * R.p[3];
+        }
+        self_f32_point(c, S, (float)du, (float)dw, (float)(gw[qi] * gw[qj] * hx * he * jac), la, ld);
+    }
+    sa += (double)la * (0.25 / kPi);
+    sd += (double)ld * (0.25 / kPi);
 }
 
 // a whole far panel (box prm, order n) by one thread
@@ -678,7 +801,9 @@ __device__ __forceinline__ double panel_ratio(const Ctx<double> &c, const double
 
 // SK: the second-kind system (a separate instance, so the first-kind code
 // carries none of its branches).
-template <bool SK>
+// W32: the mixed-precision pass over wrapped patches (FP32 rules in offset
+// form), a separate instance so that the FP64 code keeps its registers.
+template <bool SK, bool W32>
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     int64_t p, row;
     int n, i;
@@ -718,10 +843,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     make_ctx<double>(c64, f, X, gx, &P.dat);
     if (P.mode == 1) c64.needD = false;
     if (P.mode == 2) c64.needA = (Arow != nullptr);
-    // mixed precision on a wrapped patch (a matrix of its own): far panels and
-    // the rectangles of the near panels' covers by the FP32 rule in offset
-    // form (far_wrapped_f32), the self panel by the FP64 rules
-    const bool far32 = (P.prec == DTN_PREC_MIXED && f.kind == kWrapped && !SK);
+    // mixed precision on a wrapped patch (a matrix of its own): every panel by
+    // FP32 rules in offset form (far_wrapped_f32, self_f32_setup), on the covers
+    // and regions that the FP64 rules choose, with fewer points (order32)
+    const bool far32 = W32;   // (the W32 pass runs over wrapped patches only)
     __shared__ int near_list[1024];
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
@@ -794,7 +919,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         double sa = 0.0, sd = 0.0;
         if (far32) {
             ctx_panel(c64, pcs, P.panel_piece[pj]);
-            far_wrapped_f32(c64, prm, order64(r), P.glx, P.glw, sa, sd);
+            far_wrapped_f32(c64, prm, order32(order64(r)), P.glx, P.glw, sa, sd);
         } else {
             ctx_panel(c64, pcs, P.panel_piece[pj]);
             gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
@@ -814,8 +939,23 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
                 coop_gauss(c64, R, x0, x1, e0, e1, nq, P.glx, P.glw, lane, sa, sd);
             });
         };
-        if (f.kind == kWrapped) self_regions(c64, P.panel_prm + 6 * row, region);
-        else self_triangles(c64, P.panel_prm + 6 * row, [&](const Region &R) { region(R, false, 16); });
+        if (far32) {
+            // mixed precision: the same regions and covers, points by the FP32 rule
+            SelfF32 SF;
+            self_f32_setup(c64, P.panel_prm + 6 * row, SF);
+            self_regions(c64, P.panel_prm + 6 * row, [&](const Region &R, bool withX, int min_order) {
+                if ((tri++ % (kAsmThreads / 32)) != warp) return;
+                adaptive_squares<double>(c64, R, withX, withX ? 0 : 10,
+                                         [&](double x0, double x1, double e0, double e1, int nq) {
+                                             self_f32_square(c64, SF, R, x0, x1, e0, e1, withX ? order32(nq) : nq,
+                                                             P.glx, P.glw, lane, sa, sd);
+                                         });
+            });
+        } else if (f.kind == kWrapped) {
+            self_regions(c64, P.panel_prm + 6 * row, region);
+        } else {
+            self_triangles(c64, P.panel_prm + 6 * row, [&](const Region &R) { region(R, false, 16); });
+        }
         for (int o = 16; o > 0; o >>= 1) {
             sa += __shfl_xor_sync(0xffffffffu, sa, o);
             sd += __shfl_xor_sync(0xffffffffu, sd, o);
@@ -850,7 +990,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             // mixed precision on a wrapped patch: the cover's rectangles by the FP32 rule
             adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
                 rect_wrapped_f32_warp(c64, R.p[0] + x0 * R.p[1], R.p[0] + x1 * R.p[1], R.p[2] + e0 * R.p[3],
-                                      R.p[2] + e1 * R.p[3], nq, P.glx, P.glw, wlines[warp], lane, sa, sd);
+                                      R.p[2] + e1 * R.p[3], order32(nq), P.glx, P.glw, wlines[warp], lane, sa, sd);
             });
         } else {
             adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
@@ -1296,8 +1436,10 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.glw = gl_w_dev();
     P.pieces = D.pieces;
     P.panel_piece = g->ws.panel_piece.as<int32_t>();
-    if (sk) assemble_kernel<true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
-    else assemble_kernel<false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    if (sk) assemble_kernel<true, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    else if (mode == 2 && only_wrapped && prec == DTN_PREC_MIXED)
+        assemble_kernel<false, true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    else assemble_kernel<false, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -69,9 +69,10 @@ def test_wrapped_setup_matches_oracle():
 def test_wrapped_assembly_and_solve_given_exact_values():
     """Matrix and right side against the oracle's adaptive integrals, and q:
     FP64 within relative L2 1e-10; mixed precision (a wrapped patch has a
-    matrix of its own: far panels by FP32 rules, near and self panels by the
-    FP64 ones; the same for its right side) entries within 2e-5 of the
-    largest, q within 1e-4."""
+    matrix of its own: far panels and the near panels' covers by the FP32 rule
+    in offset form, the self panel by the FP64 rules; the same for its right
+    side) matrix entries within 2e-7 of the largest, right side within 1e-6,
+    q within 1e-5."""
     wl = _case()
     g, b, hb = _setup(wl)
     r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
@@ -83,7 +84,7 @@ def test_wrapped_assembly_and_solve_given_exact_values():
         pf = O.patch_frame(wl.geometry, b.centers[p], A)
         Ao, bo = O.assemble(pf, wl.data, 3, 16, 12, 24, U[p * P:(p + 1) * P], rtol=1e-12)
         ref.append((Ao, bo, np.linalg.solve(Ao, bo)))
-    for prec, tol in [(dtn.PREC_FP64, 1e-10), (dtn.PREC_MIXED, 1e-4)]:
+    for prec, tol in [(dtn.PREC_FP64, 1e-10), (dtn.PREC_MIXED, 1e-5)]:
         res = dtn.alloc_result(hb, want_matrix=True)
         res["u_gamma_mean"].copy_(torch.from_numpy(U))
         dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=prec, u_provided=True), result=res)
@@ -94,8 +95,8 @@ def test_wrapped_assembly_and_solve_given_exact_values():
             Am = _np(res["matrix"])[p * n * n:(p + 1) * n * n].reshape(n, n)
             bm = _np(res["rhs"])[p * n:(p + 1) * n]
             fp64 = (prec == dtn.PREC_FP64)
-            atol = 1e-10 if (fp64 or p == 0) else 2e-5          # patch 0 is flat: a shared FP64 matrix
-            btol = 1e-10 if fp64 else (1e-6 if p == 0 else 2e-5)
+            atol = 1e-10 if (fp64 or p == 0) else 2e-7          # patch 0 is flat: a shared FP64 matrix
+            btol = 1e-10 if fp64 else 1e-6
             print(f"prec {prec} patch {p}: A {np.max(np.abs(Am - Ao)) / np.max(np.abs(Ao)):.1e}, "
                   f"b {np.max(np.abs(bm - bo)) / np.max(np.abs(bo)):.1e}")
             assert np.max(np.abs(Am - Ao)) <= atol * np.max(np.abs(Ao)), (prec, p)
@@ -109,7 +110,7 @@ def test_wrapped_assembly_and_solve_given_exact_values():
 def test_wrapped_walks_and_full_solve_vs_oracle():
     """Walk means at the wrapped hemisphere's nodes within 4 standard errors of
     the oracle's (FP32 walks), and the solve with the GPU's node values within
-    1e-4 of the oracle's."""
+    1e-5 of the oracle's."""
     wl = _case()
     b = wl.batch
     b.walks[:] = 2000
@@ -129,14 +130,14 @@ def test_wrapped_walks_and_full_solve_vs_oracle():
         assert np.all(np.abs(U[sl][nodes] - Uo) <= 4.0 * np.sqrt(SE[sl][nodes] ** 2 + SEo ** 2))
         rq = O.solve_patch(wl.geometry, wl.data, b.centers[p], A, 12, 24, 3, 16, 0, 0, O.wos_opts(), U_in=U[sl],
                            rtol=1e-10)
-        assert np.linalg.norm(q[p * n:(p + 1) * n] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4
+        assert np.linalg.norm(q[p * n:(p + 1) * n] - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-5
 
 
 def test_wire_layout_batch_mixed_flat_and_wrapped_graph_replay():
     """The wire workload's own patches (mostly wrapped), in one mixed-precision
     call captured as a CUDA graph: the replay is bit-equal, every patch solves,
     and sampled wrapped patches match the oracle's solve with the GPU's node
-    values within 1e-4."""
+    values within 1e-5."""
     wl = W.wires(n_patches=64, walks=256)
     g, b, hb = _setup(wl)
     o = dtn.solve_opts(prec=dtn.PREC_MIXED, epsilon=wl.epsilon, seed=wl.seed, graph_capture=True)
@@ -157,4 +158,28 @@ def test_wire_layout_batch_mixed_flat_and_wrapped_graph_replay():
                            int(b.n_rings[p]), int(b.n_sectors[p]), 0, 0, O.wos_opts(), U_in=U[goff[p]:goff[p + 1]],
                            rtol=1e-10)
         qq = q1[poff[p]:poff[p + 1]]
-        assert np.linalg.norm(qq - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-4, p
+        assert np.linalg.norm(qq - rq["q"]) / np.linalg.norm(rq["q"]) <= 1e-5, p
+
+
+def test_mixed_batch_of_wrapped_patches_only():
+    """A mixed-precision batch of wrapped patches only (no flat patch, so no
+    shared right-side weights at all) solves, and gives each patch the same q,
+    bit for bit, as the batch that also holds a flat patch."""
+    wl = _case()
+    g, b, hb = _setup(wl)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
+    torch.cuda.synchronize()
+    U = O.dirichlet(wl.data, _np(r0["gamma_xyz"]))
+    o = dtn.solve_opts(prec=dtn.PREC_MIXED, u_provided=True)
+    res = dtn.alloc_result(hb)
+    res["u_gamma_mean"].copy_(torch.from_numpy(U))
+    dtn.solve_patches(g, b.centers, b.radius, hb, o, result=res)
+    P, n = 12 * 24, 3 * 16
+    idx = np.arange(1, b.n)
+    hb2 = dtn.HostBatch(b.n_theta[idx], b.n_phi[idx], b.n_rings[idx], b.n_sectors[idx], b.walks[idx])
+    res2 = dtn.alloc_result(hb2)
+    res2["u_gamma_mean"].copy_(torch.from_numpy(U[P:]))
+    dtn.solve_patches(g, b.centers[idx], b.radius[idx], hb2, o, result=res2)
+    torch.cuda.synchronize()
+    assert np.all(_np(res2["patch_status"]) == 0)
+    assert np.array_equal(_np(res2["neumann"]), _np(res["neumann"])[n:])
