@@ -221,285 +221,6 @@ __device__ void gauss_rect(const Ctx<T> &c, const Region &R, T x0, T x1, T e0, T
     }
 }
 
-// FP32 tensor rule on a wrapped patch's panel or part of one (mixed
-// precision).  A wrapped patch lies anywhere in the box, and the data of a
-// distant source vary little over it, so the points' coordinates and g(y) -
-// g(x) would lose most of FP32's digits to cancellation.  Instead every
-// quantity is built from offsets: the rectangle centre's offsets from X, from
-// its Kelvin image X* and (global axes) the data difference are formed in FP64
-// once, and a Gauss point adds its in-plane offset from the centre, (u - uc)
-// B(w) + uc (B(w) - B(wc)), whose parts are small and exact to FP32 rounding.
-// On the flat piece n_y.(X - Y) and |X|^2 n_y.Y - a^2 n_y.X do not depend on
-// the point.  G and dG/dn_y then keep FP32's relative accuracy; a point-source
-// difference is taken as -q d.(2e + d) / (|e + d| |e| (|e + d| + |e|)), e = x -
-// x0, d = y - x; other data are differenced in FP64 at the point.
-struct WF32 {
-    float Dc[3], Ds[3], e[3], ne, gi, g0, k1, k2, qf;
-    double xg[3];
-    bool point, img, needA, needD;
-};
-
-// G = (1/r - gi / rs - g0) / 4pi;  dG/dn_y = (k1 / r^3 + k2 / rs^3) / 4pi
-__device__ void wf32_setup(const Ctx<double> &c, double uc, double wc, double Bc[3], WF32 &W) {
-    const Piece &q = *c.pc;
-    double Jc;
-    wrapped_line(q, c.sub, wc, Bc, Jc);
-    double Dl[3], Dsl[3];
-    for (int d = 0; d < 3; ++d) {
-        const double yc = q.Pl[d] + uc * Bc[d];
-        Dl[d] = yc - c.X[d];
-        Dsl[d] = c.img ? yc - c.Xs[d] : 0.0;
-    }
-    const double xx = c.xn * c.xn;
-    double nyX = 0.0, nyP = 0.0, nyXP = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        nyX += q.nl[d] * c.X[d];
-        nyP += q.nl[d] * q.Pl[d];
-        nyXP += q.nl[d] * (c.X[d] - q.Pl[d]);
-        W.xg[d] = c.c[d] + c.X[0] * c.t1[d] + c.X[1] * c.t2[d] + c.X[2] * c.n[d];
-        W.Dc[d] = (float)(Dl[0] * c.t1[d] + Dl[1] * c.t2[d] + Dl[2] * c.n[d]);
-        W.Ds[d] = (float)(Dsl[0] * c.t1[d] + Dsl[1] * c.t2[d] + Dsl[2] * c.n[d]);
-    }
-    W.img = c.img;
-    W.gi = c.img ? (float)(c.a / c.xn) : 0.f;
-    W.g0 = c.img ? 0.f : (float)(1.0 / c.a);
-    W.k1 = (float)nyXP;
-    W.k2 = c.img ? (float)(c.a * (xx * nyP - c.a * c.a * nyX) / (xx * c.xn)) : 0.f;
-    const int dk = c.dat->kind;
-    W.point = (dk == kPointSource);
-    W.needA = c.needA;
-    W.needD = c.needD && dk != kConstant;
-    W.ne = 0.f;
-    W.qf = c.dat->q_f;
-    W.e[0] = W.e[1] = W.e[2] = 0.f;
-    if (W.point) {
-        double sq = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            const double ed = W.xg[d] - c.dat->x0[d];
-            sq += ed * ed;
-            W.e[d] = (float)ed;
-        }
-        W.ne = (float)sqrt(sq);
-    }
-}
-
-// line w of the rule: B(w) and uc (B(w) - B(wc)) in global axes, the Jacobian factor
-__device__ __forceinline__ void wf32_line(const Ctx<double> &c, double w, double uc, const double Bc[3], float *Bg,
-                                          float *dBg, float &Jf) {
-    double B[3], J;
-    wrapped_line(*c.pc, c.sub, w, B, J);
-    const double dB[3] = {uc * (B[0] - Bc[0]), uc * (B[1] - Bc[1]), uc * (B[2] - Bc[2])};
-    for (int d = 0; d < 3; ++d) {
-        Bg[d] = (float)(B[0] * c.t1[d] + B[1] * c.t2[d] + B[2] * c.n[d]);
-        dBg[d] = (float)(dB[0] * c.t1[d] + dB[1] * c.t2[d] + dB[2] * c.n[d]);
-    }
-    Jf = (float)J;
-}
-
-// one point given by its offset (ox, oy, oz) from the rectangle centre (global
-// axes), weight w (Gauss weights, Jacobians)
-__device__ __forceinline__ void wf32_eval(const Ctx<double> &c, const WF32 &W, float ox, float oy, float oz, float w,
-                                          float &la, float &ld) {
-    const float dx = ox + W.Dc[0], dy = oy + W.Dc[1], dz = oz + W.Dc[2];
-    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float irs = 0.f;
-    if (W.img) {
-        const float sx = ox + W.Ds[0], sy = oy + W.Ds[1], sz = oz + W.Ds[2];
-        irs = rsqrtf(sx * sx + sy * sy + sz * sz);
-    }
-    if (W.needA) la += w * (ir - W.gi * irs - W.g0);
-    if (W.needD) {
-        float dg;
-        if (W.point) {
-            const float px = W.e[0] + dx, py = W.e[1] + dy, pz = W.e[2] + dz;
-            const float rp = sqrtf(px * px + py * py + pz * pz);
-            const float num = dx * (W.e[0] + px) + dy * (W.e[1] + py) + dz * (W.e[2] + pz);
-            dg = -W.qf * __fdividef(num, rp * W.ne * (rp + W.ne));
-        } else {
-            dg = (float)(dirichlet_eval<double>(*c.dat, W.xg[0] + (double)dx, W.xg[1] + (double)dy,
-                                               W.xg[2] + (double)dz) - c.gx);
-        }
-        ld += w * (W.k1 * ir * ir * ir + W.k2 * irs * irs * irs) * dg;
-    }
-}
-
-// one point of a tensor rule: offset dui = u - uc along B(w), line data Bg, dBg
-__device__ __forceinline__ void wf32_point(const Ctx<double> &c, const WF32 &W, float dui, const float *Bg,
-                                           const float *dBg, float w, float &la, float &ld) {
-    wf32_eval(c, W, fmaf(dui, Bg[0], dBg[0]), fmaf(dui, Bg[1], dBg[1]), fmaf(dui, Bg[2], dBg[2]), w, la, ld);
-}
-
-// Gauss order of the FP32 rules for a ratio order n of order64: the orders
-// that order64 takes for 1e-15 give about 1e-10 at two thirds of the points
-// per direction, far below FP32 rounding
-__device__ __forceinline__ int order32(int n) {
-    return n >= 20 ? 14 : n >= 12 ? 8 : n >= 9 ? 6 : 4;
-}
-
-// The self panel of a wrapped patch in FP32 (mixed precision): a point's
-// offset from the collocation point S is built from its parameter offsets
-// (du, dw) from S, which are exact, through the sub-range's map: on a side-
-// bounded sub-range B(w) = en + w et (so B(w) - B(ws) = dw et); on a circle-
-// bounded one B(v) = rho(v) e(v) with e(v) - e(vs) = 2 sin(dv/2) e'(vs + dv/2)
-// and, when P is not the slice centre, rho(v) - rho(vs) = (p - ps) (-1 + (p +
-// ps) / (sqrt D + sqrt Ds)), p = (P - cf).e, D = p^2 - |P - cf|^2 + rf^2.  The
-// offset is du B(w) + us (B(w) - B(ws)): the 1/r singularity at S is met with
-// FP32's relative accuracy, and the Duffy factor removes it as in FP64.
-struct SelfF32 {
-    WF32 W;
-    int type;          // 1: rectangle side, 0: circle about P, 2: circle, P off the slice centre
-    float us, ws;
-    double usd, wsd;                     // S exactly (the offsets of a box's points are taken from it)
-    float eg[3], tg[3], js;              // side: B(w) = eg + w tg, Jf = js
-    float Ug[3], Vg[3], rf;              // circle
-    float w2[2], ww, ps, sDs, rhos;      // off-centre circle
-};
-
-__device__ void self_f32_setup(const Ctx<double> &c, const double *prm, SelfF32 &S) {
-    const Piece &q = *c.pc;
-    const int j = c.sub;
-    double Bc[3];
-    wf32_setup(c, prm[4], prm[5], Bc, S.W);
-    S.us = (float)prm[4];
-    S.ws = (float)prm[5];
-    S.usd = prm[4];
-    S.wsd = prm[5];
-    for (int d = 0; d < 3; ++d) {
-        S.eg[d] = (float)(q.en[j][0] * c.t1[d] + q.en[j][1] * c.t2[d] + q.en[j][2] * c.n[d]);
-        S.tg[d] = (float)(q.et[j][0] * c.t1[d] + q.et[j][1] * c.t2[d] + q.et[j][2] * c.n[d]);
-        S.Ug[d] = (float)(q.Ul[0] * c.t1[d] + q.Ul[1] * c.t2[d] + q.Ul[2] * c.n[d]);
-        S.Vg[d] = (float)(q.Vl[0] * c.t1[d] + q.Vl[1] * c.t2[d] + q.Vl[2] * c.n[d]);
-    }
-    S.js = (float)(q.sdist[j] * q.sdist[j]);
-    S.rf = (float)q.rf;
-    S.type = q.stype[j] ? 1 : (q.centred ? 0 : 2);
-    const double w0 = q.P[0] - q.cf[0], w1 = q.P[1] - q.cf[1];
-    double sv, cv;
-    sincos(prm[5], &sv, &cv);
-    const double ps = w0 * cv + w1 * sv, ww = w0 * w0 + w1 * w1;
-    const double sDs = sqrt(fmax(0.0, ps * ps - ww + q.rf * q.rf));
-    S.w2[0] = (float)w0;
-    S.w2[1] = (float)w1;
-    S.ww = (float)ww;
-    S.ps = (float)ps;
-    S.sDs = (float)sDs;
-    S.rhos = (float)(-ps + sDs);
-}
-
-// a point at parameter offsets (du, dw) from S, weight wt (Gauss weights, region Jacobian)
-__device__ __forceinline__ void self_f32_point(const Ctx<double> &c, const SelfF32 &S, float du, float dw, float wt,
-                                               float &la, float &ld) {
-    const float u = S.us + du;
-    float o[3], J;
-    if (S.type == 1) {
-        const float w = S.ws + dw;
-        for (int d = 0; d < 3; ++d) o[d] = du * fmaf(w, S.tg[d], S.eg[d]) + S.us * (dw * S.tg[d]);
-        J = S.js * u;
-    } else {
-        float sv, cv, sm, cm;
-        sincosf(S.ws + dw, &sv, &cv);
-        sincosf(S.ws + 0.5f * dw, &sm, &cm);
-        const float h = 2.f * sinf(0.5f * dw);
-        const float de0 = -h * sm, de1 = h * cm;   // e(v) - e(vs) in (U, V)
-        float rho = S.rf, drho = 0.f;
-        if (S.type == 2) {
-            const float pv = S.w2[0] * cv + S.w2[1] * sv;
-            const float dp = S.w2[0] * de0 + S.w2[1] * de1;
-            const float sD = sqrtf(fmaxf(0.f, pv * pv - S.ww + S.rf * S.rf));
-            rho = -pv + sD;
-            drho = dp * (-1.f + __fdividef(pv + S.ps, sD + S.sDs));
-        }
-        const float rs = (S.type == 2) ? S.rhos : S.rf;
-        for (int d = 0; d < 3; ++d) {
-            const float e = cv * S.Ug[d] + sv * S.Vg[d];
-            const float dB = drho * e + rs * (de0 * S.Ug[d] + de1 * S.Vg[d]);
-            o[d] = du * (rho * e) + S.us * dB;
-        }
-        J = rho * rho * u;
-    }
-    wf32_eval(c, S.W, o[0], o[1], o[2], wt * J, la, ld);
-}
-
-// one accepted sub-square of a self region, its points dealt to the lanes
-__device__ void self_f32_square(const Ctx<double> &c, const SelfF32 &S, const Region &R, double x0, double x1,
-                                double e0, double e1, int nq, const double *__restrict__ glx,
-                                const double *__restrict__ glw, int lane, double &sa, double &sd) {
-    const double *gx = glx + nq * (nq - 1) / 2, *gw = glw + nq * (nq - 1) / 2;
-    const double hx = 0.5 * (x1 - x0), mx = 0.5 * (x0 + x1), he = 0.5 * (e1 - e0), me = 0.5 * (e0 + e1);
-    float la = 0.f, ld = 0.f;
-    for (int k = lane; k < nq * nq; k += 32) {
-        const int qi = k / nq, qj = k - qi * nq;
-        const double xi = mx + hx * gx[qi], eta = me + he * gx[qj];
-        double du, dw, jac;
-        if (R.tri) {
-            du = xi * (R.p[2] + eta * R.p[4]);
-            dw = xi * (R.p[3] + eta * R.p[5]);
-            jac = xi * R.det;
-        } else {
-            du = (R.p[0] - S.usd) + xi * R.p[1];
-            dw = (R.p[2] - S.wsd) + eta * R.p[3];
-            jac = R.p[1] * R.p[3];
-        }
-        self_f32_point(c, S, (float)du, (float)dw, (float)(gw[qi] * gw[qj] * hx * he * jac), la, ld);
-    }
-    sa += (double)la * (0.25 / kPi);
-    sd += (double)ld * (0.25 / kPi);
-}
-
-// a whole far panel (box prm, order n) by one thread
-__device__ void far_wrapped_f32(const Ctx<double> &c, const double *prm, int n, const double *__restrict__ glx,
-                                const double *__restrict__ glw, double &sa_out, double &sd_out) {
-    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
-    const double u0 = prm[0], du = prm[1] - prm[0], w0 = prm[2], dw = prm[3] - prm[2], uc = prm[4], wc = prm[5];
-    WF32 W;
-    double Bc[3];
-    wf32_setup(c, uc, wc, Bc, W);
-    float Bg[kMaxRule][3], dBg[kMaxRule][3], Jf[kMaxRule];
-    for (int jj = 0; jj < n; ++jj) wf32_line(c, w0 + (0.5 + 0.5 * gx[jj]) * dw, uc, Bc, Bg[jj], dBg[jj], Jf[jj]);
-    float sa = 0.f, sd = 0.f;
-    for (int i = 0; i < n; ++i) {
-        const double ud = u0 + (0.5 + 0.5 * gx[i]) * du;
-        const float u = (float)ud, dui = (float)(ud - uc);
-        float la = 0.f, ld = 0.f;
-        for (int jj = 0; jj < n; ++jj) wf32_point(c, W, dui, Bg[jj], dBg[jj], (float)gw[jj] * u * Jf[jj], la, ld);
-        const float wi = (float)(gw[i] * 0.25 * du * dw);
-        sa += wi * la;
-        sd += wi * ld;
-    }
-    sa_out = (double)sa * (0.25 / kPi);
-    sd_out = (double)sd * (0.25 / kPi);
-}
-
-// Line data of one warp's current rectangle (warp-cooperative rule below).
-struct WLines {
-    float Bg[kMaxRule][3], dBg[kMaxRule][3], Jf[kMaxRule];
-};
-
-// the rectangle [ua, ub] x [wa, wb] of a panel's quadrature parameters, order
-// n, by the lanes of a warp (points dealt in turn); each lane adds its part,
-// times 1/4pi, to sa and sd
-__device__ void rect_wrapped_f32_warp(const Ctx<double> &c, double ua, double ub, double wa, double wb, int n,
-                                      const double *__restrict__ glx, const double *__restrict__ glw, WLines &Ls,
-                                      int lane, double &sa, double &sd) {
-    const double *gx = glx + n * (n - 1) / 2, *gw = glw + n * (n - 1) / 2;
-    const double uc = 0.5 * (ua + ub), wc = 0.5 * (wa + wb), hu = 0.5 * (ub - ua), hw = 0.5 * (wb - wa);
-    WF32 W;
-    double Bc[3];
-    wf32_setup(c, uc, wc, Bc, W);
-    __syncwarp();
-    if (lane < n) wf32_line(c, wc + hw * gx[lane], uc, Bc, Ls.Bg[lane], Ls.dBg[lane], Ls.Jf[lane]);
-    __syncwarp();
-    float la = 0.f, ld = 0.f;
-    for (int k = lane; k < n * n; k += 32) {
-        const int i = k / n, jj = k - i * n;
-        const double ud = uc + hu * gx[i];
-        const float w = (float)(gw[i] * gw[jj] * hu * hw) * (float)ud * Ls.Jf[jj];
-        wf32_point(c, W, (float)(ud - uc), Ls.Bg[jj], Ls.dBg[jj], w, la, ld);
-    }
-    sa += (double)la * (0.25 / kPi);
-    sd += (double)ld * (0.25 / kPi);
-}
-
 // Gauss order from the distance ratio r (0: split further), aiming at 1e-15
 // relative for a singularity next to the middle of a panel edge.
 __device__ __forceinline__ int order64(double r) {
@@ -772,6 +493,328 @@ __device__ void self_regions(const Ctx<double> &c, const double *prm, Fn &&fn) {
         }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision on wrapped patches: FP32 rules in offset form.
+//
+// A wrapped patch lies anywhere in the box and the data of a distant source
+// vary little over it, so points formed from coordinates, and g(y) - g(x),
+// would lose most of FP32's digits.  Instead every point is the offset of its
+// quadrature parameters (du, dw) from the panel centre C = (uc, wc), pushed
+// through the sub-range's map: on a side-bounded sub-range B(w) = e_n + w e_t
+// (so B(w) - B(wc) = dw e_t); on a circle-bounded one B(v) = rho(v) e(v) with
+// e(v) - e(vc) = 2 sin(dv/2) e'(vc + dv/2) and, when P is off the slice centre,
+// rho(v) - rho(vc) = (p - pc) (-1 + (p + pc) / (sqrt D + sqrt Dc)), p = (P -
+// cf).e, D = p^2 - |P - cf|^2 + rf^2.  The point's offset from C is du B(w) +
+// uc (B(w) - B(wc)); C's offsets from X and from its Kelvin image X*, and the
+// data's e = x - x0, are formed in FP64 once per (row, panel).  |Y - X|, |Y -
+// X*| and the data difference -q d.(2e + d) / (|e + d| |e| (|e + d| + |e|))
+// then keep FP32's relative accuracy, down to the collocation point itself
+// (the self panel's centre), where the Duffy factor removes 1/r as in FP64.
+// Adaptive-cover decisions are taken on the same FP32 offsets.  Other data
+// than a point source are differenced in FP64.
+
+struct Off32 {
+    int type;                          // 1: rectangle side, 0: circle about P, 2: circle, P off centre
+    float uc, wc;
+    float eg[3], tg[3], js;            // side: B(w) = eg + w tg (global axes), Jacobian factor js
+    float Ug[3], Vg[3], rf;            // circle: e(v) = cos v Ug + sin v Vg
+    float w2[2], ww, pc, sDc, rhoc;    // off-centre circle
+    float Dc[3], Ds[3];                // C - X, C - X* (global axes)
+    float k1, k2, gi, g0;              // G = (1/r - gi/rs - g0)/4pi, dG/dn_y = (k1/r^3 + k2/rs^3)/4pi
+    bool img;
+};
+
+struct Row32 {
+    double xg[3], gx;                  // x (global) and g(x)
+    float e[3], ne, qf;                // point source: e = x - x0, |e|, q/4pi
+    bool point, needA, needD;
+    const DData *dat;
+};
+
+__device__ void row32_setup(const Ctx<double> &c, Row32 &R) {
+    for (int d = 0; d < 3; ++d) R.xg[d] = c.c[d] + c.X[0] * c.t1[d] + c.X[1] * c.t2[d] + c.X[2] * c.n[d];
+    R.gx = c.gx;
+    R.dat = c.dat;
+    const int dk = c.dat->kind;
+    R.point = (dk == kPointSource);
+    R.needA = c.needA;
+    R.needD = c.needD && dk != kConstant;
+    R.qf = c.dat->q_f;
+    double sq = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double ed = R.point ? R.xg[d] - c.dat->x0[d] : 0.0;
+        sq += ed * ed;
+        R.e[d] = (float)ed;
+    }
+    R.ne = (float)sqrt(sq);
+}
+
+// the panel's map about its centre (prm: u0, u1, w0, w1, uc, wc) and C's offsets
+__device__ void off32_setup(const Ctx<double> &c, const double *prm, const double *Yc, Off32 &O) {
+    const Piece &q = *c.pc;
+    const int j = c.sub;
+    const double uc = prm[4], wc = prm[5];
+    O.uc = (float)uc;
+    O.wc = (float)wc;
+    O.type = q.stype[j] ? 1 : (q.centred ? 0 : 2);
+    double Dl[3], Dsl[3];
+    for (int d = 0; d < 3; ++d) {
+        Dl[d] = Yc[d] - c.X[d];
+        Dsl[d] = c.img ? Yc[d] - c.Xs[d] : 0.0;
+    }
+    for (int d = 0; d < 3; ++d) {
+        O.eg[d] = (float)(q.en[j][0] * c.t1[d] + q.en[j][1] * c.t2[d] + q.en[j][2] * c.n[d]);
+        O.tg[d] = (float)(q.et[j][0] * c.t1[d] + q.et[j][1] * c.t2[d] + q.et[j][2] * c.n[d]);
+        O.Ug[d] = (float)(q.Ul[0] * c.t1[d] + q.Ul[1] * c.t2[d] + q.Ul[2] * c.n[d]);
+        O.Vg[d] = (float)(q.Vl[0] * c.t1[d] + q.Vl[1] * c.t2[d] + q.Vl[2] * c.n[d]);
+        O.Dc[d] = (float)(Dl[0] * c.t1[d] + Dl[1] * c.t2[d] + Dl[2] * c.n[d]);
+        O.Ds[d] = (float)(Dsl[0] * c.t1[d] + Dsl[1] * c.t2[d] + Dsl[2] * c.n[d]);
+    }
+    O.js = (float)(q.sdist[j] * q.sdist[j]);
+    O.rf = (float)q.rf;
+    if (O.type == 2) {
+        const double w0 = q.P[0] - q.cf[0], w1 = q.P[1] - q.cf[1];
+        double sv, cv;
+        sincos(wc, &sv, &cv);
+        const double pc = w0 * cv + w1 * sv, ww = w0 * w0 + w1 * w1;
+        const double sDc = sqrt(fmax(0.0, pc * pc - ww + q.rf * q.rf));
+        O.w2[0] = (float)w0; O.w2[1] = (float)w1;
+        O.ww = (float)ww; O.pc = (float)pc; O.sDc = (float)sDc; O.rhoc = (float)(-pc + sDc);
+    } else {
+        O.w2[0] = O.w2[1] = O.ww = O.pc = O.sDc = 0.f;
+        O.rhoc = O.rf;
+    }
+    const double xx = c.xn * c.xn;
+    double nyX = 0.0, nyP = 0.0, nyXP = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        nyX += q.nl[d] * c.X[d];
+        nyP += q.nl[d] * q.Pl[d];
+        nyXP += q.nl[d] * (c.X[d] - q.Pl[d]);
+    }
+    O.img = c.img;
+    O.k1 = (float)nyXP;
+    O.k2 = c.img ? (float)(c.a * (xx * nyP - c.a * c.a * nyX) / (xx * c.xn)) : 0.f;
+    O.gi = c.img ? (float)(c.a / c.xn) : 0.f;
+    O.g0 = c.img ? 0.f : (float)(1.0 / c.a);
+}
+
+// line dw of the map: B(wc + dw), uc (B(wc + dw) - B(wc)) (global axes), Jacobian factor
+__device__ __forceinline__ void line32(const Off32 &O, float dw, float *Bg, float *dBg, float &Jf) {
+    if (O.type == 1) {
+        const float w = O.wc + dw;
+        for (int d = 0; d < 3; ++d) {
+            Bg[d] = fmaf(w, O.tg[d], O.eg[d]);
+            dBg[d] = O.uc * (dw * O.tg[d]);
+        }
+        Jf = O.js;
+        return;
+    }
+    float sv, cv, sm, cm;
+    sincosf(O.wc + dw, &sv, &cv);
+    sincosf(O.wc + 0.5f * dw, &sm, &cm);
+    const float h = 2.f * sinf(0.5f * dw);
+    const float de0 = -h * sm, de1 = h * cm;   // e(v) - e(vc) in (U, V)
+    float rho = O.rf, drho = 0.f;
+    if (O.type == 2) {
+        const float pv = O.w2[0] * cv + O.w2[1] * sv;
+        const float dp = O.w2[0] * de0 + O.w2[1] * de1;
+        const float sD = sqrtf(fmaxf(0.f, pv * pv - O.ww + O.rf * O.rf));
+        rho = -pv + sD;
+        drho = dp * (-1.f + __fdividef(pv + O.pc, sD + O.sDc));
+    }
+    for (int d = 0; d < 3; ++d) {
+        const float e = cv * O.Ug[d] + sv * O.Vg[d];
+        Bg[d] = rho * e;
+        dBg[d] = O.uc * (drho * e + O.rhoc * (de0 * O.Ug[d] + de1 * O.Vg[d]));
+    }
+    Jf = rho * rho;
+}
+
+// the point at offsets (du, dw) from C: its offset from C (global axes) and u Jf
+__device__ __forceinline__ void pos32(const Off32 &O, float du, float dw, float *o, float &J) {
+    float Bg[3], dBg[3], Jf;
+    line32(O, dw, Bg, dBg, Jf);
+    for (int d = 0; d < 3; ++d) o[d] = fmaf(du, Bg[d], dBg[d]);
+    J = (O.uc + du) * Jf;
+}
+
+// one point by its offset o from C, weight w (Gauss weights, Jacobians)
+__device__ __forceinline__ void eval32(const Off32 &O, const Row32 &R, const float *o, float w, float &la,
+                                       float &ld) {
+    const float dx = o[0] + O.Dc[0], dy = o[1] + O.Dc[1], dz = o[2] + O.Dc[2];
+    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float irs = 0.f;
+    if (O.img) {
+        const float sx = o[0] + O.Ds[0], sy = o[1] + O.Ds[1], sz = o[2] + O.Ds[2];
+        irs = rsqrtf(sx * sx + sy * sy + sz * sz);
+    }
+    if (R.needA) la += w * (ir - O.gi * irs - O.g0);
+    if (R.needD) {
+        float dg;
+        if (R.point) {
+            const float px = R.e[0] + dx, py = R.e[1] + dy, pz = R.e[2] + dz;
+            const float rp = sqrtf(px * px + py * py + pz * pz);
+            const float num = dx * (R.e[0] + px) + dy * (R.e[1] + py) + dz * (R.e[2] + pz);
+            dg = -R.qf * __fdividef(num, rp * R.ne * (rp + R.ne));
+        } else {
+            dg = (float)(dirichlet_eval<double>(*R.dat, R.xg[0] + (double)dx, R.xg[1] + (double)dy,
+                                               R.xg[2] + (double)dz) - R.gx);
+        }
+        ld += w * (O.k1 * ir * ir * ir + O.k2 * irs * irs * irs) * dg;
+    }
+}
+
+// A region in offsets from C: a box (du = a0 + x da, dw = b0 + e db) or a
+// Duffy triangle from C (du = x (E1u + e E2u), dw = x (E1w + e E2w), Jacobian x det)
+struct Reg32 {
+    bool tri;
+    float a0, da, b0, db;
+    float E1[2], E2[2], det;
+};
+
+__device__ __forceinline__ void map32(const Reg32 &R, float x, float e, float &du, float &dw, float &jac) {
+    if (!R.tri) {
+        du = fmaf(x, R.da, R.a0);
+        dw = fmaf(e, R.db, R.b0);
+        jac = R.da * R.db;
+    } else {
+        du = x * fmaf(e, R.E2[0], R.E1[0]);
+        dw = x * fmaf(e, R.E2[1], R.E1[1]);
+        jac = x * R.det;
+    }
+}
+
+// Gauss order per direction of the FP32 rules at distance ratio r (0: split):
+// about two thirds of order64's points per direction, ~1e-10, below FP32 rounding
+__device__ __forceinline__ int order32r(float r) {
+    if (r >= 20.f) return 4;
+    if (r >= 10.f) return 4;
+    if (r >= 5.f) return 6;
+    if (r >= 3.f) return 8;
+    if (r >= 2.f) return 14;
+    return 0;
+}
+
+// the adaptive cover of order64/adaptive_squares on FP32 offsets
+__device__ float ratio32(const Off32 &O, const Reg32 &R, float x0, float x1, float e0, float e1, bool withX, float &lx,
+                         float &le) {
+    float P[3][3][3], J, du, dw, jac;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            map32(R, x0 + 0.5f * a * (x1 - x0), e0 + 0.5f * b * (e1 - e0), du, dw, jac);
+            pos32(O, du, dw, P[a][b], J);
+        }
+    const float *Yc = P[1][1];
+    float rad2 = 0.f;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const float d0 = P[a][b][0] - Yc[0], d1 = P[a][b][1] - Yc[1], d2 = P[a][b][2] - Yc[2];
+            rad2 = fmaxf(rad2, d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    lx = 0.f;
+    le = 0.f;
+    for (int k = 0; k < 2; ++k) {
+        float dx = 0.f, de = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            dx += (P[k + 1][1][d] - P[k][1][d]) * (P[k + 1][1][d] - P[k][1][d]);
+            de += (P[1][k + 1][d] - P[1][k][d]) * (P[1][k + 1][d] - P[1][k][d]);
+        }
+        lx += sqrtf(dx);
+        le += sqrtf(de);
+    }
+    float dmin2 = INFINITY;
+    if (withX) {
+        const float x = Yc[0] + O.Dc[0], y = Yc[1] + O.Dc[1], z = Yc[2] + O.Dc[2];
+        dmin2 = x * x + y * y + z * z;
+    }
+    if (O.img) {
+        const float x = Yc[0] + O.Ds[0], y = Yc[1] + O.Ds[1], z = Yc[2] + O.Ds[2];
+        dmin2 = fminf(dmin2, x * x + y * y + z * z);
+    }
+    return rad2 > 0.f ? sqrtf(dmin2 / rad2) : INFINITY;
+}
+
+template <typename Fn>
+__device__ void adaptive32(const Off32 &O, const Reg32 &R, bool withX, int min_order, Fn &&fn) {
+    struct Sq { float x0, x1, e0, e1; int depth; };
+    Sq stack[kStack];
+    int sp = 0;
+    stack[sp++] = Sq{0.f, 1.f, 0.f, 1.f, 0};
+    while (sp > 0) {
+        const Sq q = stack[--sp];
+        float lx, le;
+        const float r = ratio32(O, R, q.x0, q.x1, q.e0, q.e1, withX, lx, le);
+        int n = order32r(r);
+        if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
+            const float xm = 0.5f * (q.x0 + q.x1), em = 0.5f * (q.e0 + q.e1);
+            if (lx > 2.f * le) {
+                stack[sp++] = Sq{q.x0, xm, q.e0, q.e1, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, q.e0, q.e1, q.depth + 1};
+            } else if (le > 2.f * lx) {
+                stack[sp++] = Sq{q.x0, q.x1, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{q.x0, q.x1, em, q.e1, q.depth + 1};
+            } else {
+                stack[sp++] = Sq{q.x0, xm, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, q.e0, em, q.depth + 1};
+                stack[sp++] = Sq{q.x0, xm, em, q.e1, q.depth + 1};
+                stack[sp++] = Sq{xm, q.x1, em, q.e1, q.depth + 1};
+            }
+            continue;
+        }
+        if (n == 0) n = 14;
+        if (n < min_order) n = min_order;
+        fn(q.x0, q.x1, q.e0, q.e1, n);
+    }
+}
+
+// FP32 Gauss tables: nodes (1 + x)/2 and weights w/2 on [0, 1], order n at n(n-1)/2
+struct Gauss32 {
+    float t[kMaxRule * (kMaxRule + 1) / 2], w[kMaxRule * (kMaxRule + 1) / 2];
+};
+
+// one accepted square of a region, its points dealt to the lanes of a warp;
+// each lane adds its part, times 1/4pi, to sa and sd
+__device__ void square32_warp(const Off32 &O, const Row32 &Rw, const Reg32 &R, float x0, float x1, float e0, float e1,
+                              int n, const Gauss32 &G, int lane, double &sa, double &sd) {
+    const float *t = G.t + n * (n - 1) / 2, *w = G.w + n * (n - 1) / 2;
+    const float hx = x1 - x0, he = e1 - e0;
+    float la = 0.f, ld = 0.f;
+    for (int k = lane; k < n * n; k += 32) {
+        const int i = k / n, j = k - i * n;
+        float du, dw, jac, o[3], J;
+        map32(R, fmaf(hx, t[i], x0), fmaf(he, t[j], e0), du, dw, jac);
+        pos32(O, du, dw, o, J);
+        eval32(O, Rw, o, w[i] * w[j] * hx * he * jac * J, la, ld);
+    }
+    sa += (double)la * (0.25 / kPi);
+    sd += (double)ld * (0.25 / kPi);
+}
+
+// a whole far panel by one thread: the tensor rule of order n on the box
+// du in [a0, a0 + da], dw in [b0, b0 + db] (offsets of the panel's parameter box
+// from C: on a side-bounded sub-range C is not the box's midpoint in w), lines
+// once each
+__device__ void far_panel32(const Off32 &O, const Row32 &Rw, float a0, float da, float b0, float db, int n,
+                            const Gauss32 &G, double &sa, double &sd) {
+    const float *t = G.t + n * (n - 1) / 2, *w = G.w + n * (n - 1) / 2;
+    float la = 0.f, ld = 0.f;
+    for (int j = 0; j < n; ++j) {
+        float Bg[3], dBg[3], Jf;
+        line32(O, fmaf(db, t[j], b0), Bg, dBg, Jf);
+        float li = 0.f, lj = 0.f;
+        for (int i = 0; i < n; ++i) {
+            const float du = fmaf(da, t[i], a0);
+            const float o[3] = {fmaf(du, Bg[0], dBg[0]), fmaf(du, Bg[1], dBg[1]), fmaf(du, Bg[2], dBg[2])};
+            eval32(O, Rw, o, w[i] * (O.uc + du), li, lj);
+        }
+        la += w[j] * Jf * li;
+        ld += w[j] * Jf * lj;
+    }
+    const float jac = da * db;
+    sa += (double)(la * jac) * (0.25 / kPi);
+    sd += (double)(ld * jac) * (0.25 / kPi);
+}
+
 // The Gauss rule of order nq on one sub-square of a region, its points dealt
 // to the lanes of a warp in turn (each lane sums its own points).
 __device__ __forceinline__ void coop_gauss(const Ctx<double> &c, const Region &R, double x0, double x1, double e0,
@@ -844,13 +887,20 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     if (P.mode == 1) c64.needD = false;
     if (P.mode == 2) c64.needA = (Arow != nullptr);
     // mixed precision on a wrapped patch (a matrix of its own): every panel by
-    // FP32 rules in offset form (far_wrapped_f32, self_f32_setup), on the covers
-    // and regions that the FP64 rules choose, with fewer points (order32)
+    // FP32 rules in offset form (Off32), with FP32 adaptive covers
     const bool far32 = W32;   // (the W32 pass runs over wrapped patches only)
     __shared__ int near_list[1024];
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
-    __shared__ WLines wlines[kAsmThreads / 32];
+    __shared__ Gauss32 g32;
+    Row32 rw;
+    if (W32) {
+        for (int k = threadIdx.x; k < kMaxRule * (kMaxRule + 1) / 2; k += blockDim.x) {
+            g32.t[k] = (float)(0.5 + 0.5 * P.glx[k]);
+            g32.w[k] = (float)(0.5 * P.glw[k]);
+        }
+        row32_setup(c64, rw);
+    }
     __shared__ double sk_grad[2];
     double e1[3] = {0.0, 0.0, 0.0}, e2[3] = {0.0, 0.0, 0.0};
     if (SK) {
@@ -919,7 +969,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         double sa = 0.0, sd = 0.0;
         if (far32) {
             ctx_panel(c64, pcs, P.panel_piece[pj]);
-            far_wrapped_f32(c64, prm, order32(order64(r)), P.glx, P.glw, sa, sd);
+            Off32 O;
+            off32_setup(c64, prm, P.panel_loc + 3 * pj, O);
+            far_panel32(O, rw, (float)(prm[0] - prm[4]), (float)(prm[1] - prm[0]), (float)(prm[2] - prm[5]),
+                        (float)(prm[3] - prm[2]), order32r((float)r), g32, sa, sd);
         } else {
             ctx_panel(c64, pcs, P.panel_piece[pj]);
             gauss_rect<double>(c64, R, 0.0, 1.0, 0.0, 1.0, order64(r), P.glx, P.glw, sa, sd);
@@ -940,16 +993,28 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             });
         };
         if (far32) {
-            // mixed precision: the same regions and covers, points by the FP32 rule
-            SelfF32 SF;
-            self_f32_setup(c64, P.panel_prm + 6 * row, SF);
-            self_regions(c64, P.panel_prm + 6 * row, [&](const Region &R, bool withX, int min_order) {
+            // mixed precision: the graded regions, in offsets from the collocation
+            // point (the panel centre), by the FP32 rules and covers
+            const double *prm = P.panel_prm + 6 * row;
+            Off32 O;
+            off32_setup(c64, prm, X, O);
+            self_regions(c64, prm, [&](const Region &R, bool withX, int min_order) {
                 if ((tri++ % (kAsmThreads / 32)) != warp) return;
-                adaptive_squares<double>(c64, R, withX, withX ? 0 : 10,
-                                         [&](double x0, double x1, double e0, double e1, int nq) {
-                                             self_f32_square(c64, SF, R, x0, x1, e0, e1, withX ? order32(nq) : nq,
-                                                             P.glx, P.glw, lane, sa, sd);
-                                         });
+                Reg32 Q;
+                Q.tri = R.tri;
+                if (R.tri) {
+                    Q.E1[0] = (float)R.p[2]; Q.E1[1] = (float)R.p[3];
+                    Q.E2[0] = (float)R.p[4]; Q.E2[1] = (float)R.p[5];
+                    Q.det = (float)R.det;
+                    Q.a0 = Q.da = Q.b0 = Q.db = 0.f;
+                } else {
+                    Q.a0 = (float)(R.p[0] - prm[4]); Q.da = (float)R.p[1];
+                    Q.b0 = (float)(R.p[2] - prm[5]); Q.db = (float)R.p[3];
+                    Q.E1[0] = Q.E1[1] = Q.E2[0] = Q.E2[1] = Q.det = 0.f;
+                }
+                adaptive32(O, Q, withX, withX ? 0 : 10, [&](float x0, float x1, float e0, float e1, int n) {
+                    square32_warp(O, rw, Q, x0, x1, e0, e1, n, g32, lane, sa, sd);
+                });
             });
         } else if (f.kind == kWrapped) {
             self_regions(c64, P.panel_prm + 6 * row, region);
@@ -987,10 +1052,16 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         double sa = 0.0, sd = 0.0;
         ctx_panel(c64, pcs, P.panel_piece[poff + j]);
         if (far32) {
-            // mixed precision on a wrapped patch: the cover's rectangles by the FP32 rule
-            adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {
-                rect_wrapped_f32_warp(c64, R.p[0] + x0 * R.p[1], R.p[0] + x1 * R.p[1], R.p[2] + e0 * R.p[3],
-                                      R.p[2] + e1 * R.p[3], order32(nq), P.glx, P.glw, wlines[warp], lane, sa, sd);
+            // mixed precision on a wrapped patch: the FP32 cover in offsets from the panel centre
+            Off32 O;
+            off32_setup(c64, prm, P.panel_loc + 3 * (poff + j), O);
+            Reg32 Q;
+            Q.tri = false;
+            Q.a0 = (float)(prm[0] - prm[4]); Q.da = (float)(prm[1] - prm[0]);
+            Q.b0 = (float)(prm[2] - prm[5]); Q.db = (float)(prm[3] - prm[2]);
+            Q.E1[0] = Q.E1[1] = Q.E2[0] = Q.E2[1] = Q.det = 0.f;
+            adaptive32(O, Q, true, 0, [&](float x0, float x1, float e0, float e1, int n) {
+                square32_warp(O, rw, Q, x0, x1, e0, e1, n, g32, lane, sa, sd);
             });
         } else {
             adaptive_squares<double>(c64, R, true, 0, [&](double x0, double x1, double e0, double e1, int nq) {

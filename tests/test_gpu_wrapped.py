@@ -71,7 +71,7 @@ def test_wrapped_assembly_and_solve_given_exact_values():
     FP64 within relative L2 1e-10; mixed precision (a wrapped patch has a
     matrix of its own: far panels and the near panels' covers by the FP32 rule
     in offset form, the self panel by the FP64 rules; the same for its right
-    side) matrix entries within 2e-7 of the largest, right side within 1e-6,
+    side) matrix entries within 5e-7 of the largest, right side within 1e-6,
     q within 1e-5."""
     wl = _case()
     g, b, hb = _setup(wl)
@@ -95,7 +95,7 @@ def test_wrapped_assembly_and_solve_given_exact_values():
             Am = _np(res["matrix"])[p * n * n:(p + 1) * n * n].reshape(n, n)
             bm = _np(res["rhs"])[p * n:(p + 1) * n]
             fp64 = (prec == dtn.PREC_FP64)
-            atol = 1e-10 if (fp64 or p == 0) else 2e-7          # patch 0 is flat: a shared FP64 matrix
+            atol = 1e-10 if (fp64 or p == 0) else 5e-7          # patch 0 is flat: a shared FP64 matrix
             btol = 1e-10 if fp64 else 1e-6
             print(f"prec {prec} patch {p}: A {np.max(np.abs(Am - Ao)) / np.max(np.abs(Ao)):.1e}, "
                   f"b {np.max(np.abs(bm - bo)) / np.max(np.abs(bo)):.1e}")
