@@ -52,10 +52,10 @@ OPS_PER_WALK_WIRES_MIN = 51
 # DRAM bytes of the walk kernel per hemisphere node (node coordinates and the
 # per-node sums): an ncu capture of the 64-patch unit-ball case read and wrote
 # 1,768,704 bytes for its 32,768 nodes; scaled to the launch's nodes
-DRAM_BYTES_PER_NODE = 1768704 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
+DRAM_BYTES_PER_NODE = 1772800 / 32768   # ncu, 64-patch capture (32,768 nodes), read + write
 # the same capture's issue-slot utilisation and active lanes per warp instruction
-NCU_ISSUE_ACTIVE = 0.727        # ncu, same capture: issue slots busy
-NCU_LANES_PER_INST = 30.73      # ncu, same capture: active lanes per warp instruction
+NCU_ISSUE_ACTIVE = 0.765        # ncu, same capture: issue slots busy
+NCU_LANES_PER_INST = 30.65      # ncu, same capture: active lanes per warp instruction
 SM_COUNT = 152
 LANES_PER_SM = 128
 
@@ -480,7 +480,7 @@ def run_batch_leg(dtn, wl, ops_step, ops_walk, reps=2, n_plain=8, capture=False,
             "walks_per_node": int(b.walks[0]), "graph_capture": capture, "ms": ms, "patches_per_s": value,
             "walk_ms": walk_ms, "walk_steps": steps, "walk_steps_per_s": steps / (walk_ms / 1e3),
             "status_ok": status_ok, "walk_tuning": tuning,
-            "roofline": {"bound": "alu", "kernel": "wos_kernel<float>", "achieved": achieved, "peak": alu_peak,
+            "roofline": {"bound": "alu", "kernel": "wos_kernel_f32", "achieved": achieved, "peak": alu_peak,
                          "unit": "Tops/s", "frac": achieved / alu_peak, "ops_per_walk_step": ops_step,
                          "ops_per_walk": ops_walk,
                          "ops_basis": "algorithmic count" if exact_ops else
@@ -639,14 +639,14 @@ def run_ours(args):
     alu_peak = SM_COUNT * LANES_PER_SM * sm_mhz * 1e6 / 1e12   # Tops/s
     n_walks = int(np.sum(b.walks * (b.n_theta * b.n_phi)))
     achieved = (walk_steps * OPS_PER_STEP + n_walks * OPS_PER_WALK) / (wos / 1e3) / 1e12
-    # setup 3, walks + estimates 2; mixed: group matrices 1, right-side weights 3
+    # setup 3, walks + estimates + walk-cap statuses 3; mixed: group matrices 1, right-side weights 3
     # (far, near, walk term), samples 1, products 1, group factors + solves 2;
     # FP64: matrices and right sides 1, factor + solve 1; gather 4, potential 1
     # the potential adds a split-order reduction when the targets alone fill fewer than
     # 8 CTAs of 256 threads per SM (its panel list is then split across CTAs)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pot_reduce = 1 if sms * 8 // ((N_TARGETS + 255) // 256) > 1 else 0
-    kernels_per_step = 3 + 2 + (1 + 3 + 1 + 1 + 2 if prec == dtn.PREC_MIXED else 1 + 1) + 4 + 1 + pot_reduce
+    kernels_per_step = 3 + 3 + (1 + 3 + 1 + 1 + 2 if prec == dtn.PREC_MIXED else 1 + 1) + 4 + 1 + pot_reduce
     line = {
         "metric": METRIC, "value": value, "unit": "patches/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -661,7 +661,7 @@ def run_ours(args):
                      "gather_and_potential": ms - sum(statistics.mean(s[k] for s in stage) for k in range(4))},
         "fp64_path": {"value": plain, "unit": "patches/s", "sample": f"{nplain} patches, one patch per launch",
                       "speedup": value / plain},
-        "roofline": {"bound": "alu", "kernel": "wos_kernel<float, ball>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "wos_kernel_f32<ball>", "achieved": achieved,
                      "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
                      "traffic": DRAM_BYTES_PER_NODE * int(np.sum(b.n_theta * b.n_phi)),
                      "traffic_basis": "ncu dram bytes of the 64-patch capture, scaled by hemisphere nodes",

@@ -599,7 +599,9 @@ __device__ void off32_setup(const Ctx<double> &c, const double *prm, const doubl
 }
 
 // line dw of the map: B(wc + dw), uc (B(wc + dw) - B(wc)) (global axes), Jacobian factor
-__device__ __forceinline__ void line32(const Off32 &O, float dw, float *Bg, float *dBg, float &Jf) {
+// (not inlined: one copy of the sine and cosine code keeps the kernel within the
+// instruction cache, whose misses otherwise stalled it most)
+__device__ __noinline__ void line32(const Off32 &O, float dw, float *Bg, float *dBg, float &Jf) {
     if (O.type == 1) {
         const float w = O.wc + dw;
         for (int d = 0; d < 3; ++d) {
@@ -699,11 +701,12 @@ __device__ __forceinline__ int order32r(float r) {
 __device__ float ratio32(const Off32 &O, const Reg32 &R, float x0, float x1, float e0, float e1, bool withX, float &lx,
                          float &le) {
     float P[3][3][3], J, du, dw, jac;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            map32(R, x0 + 0.5f * a * (x1 - x0), e0 + 0.5f * b * (e1 - e0), du, dw, jac);
-            pos32(O, du, dw, P[a][b], J);
-        }
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) {
+        const int a = k / 3, b = k - 3 * (k / 3);
+        map32(R, x0 + 0.5f * a * (x1 - x0), e0 + 0.5f * b * (e1 - e0), du, dw, jac);
+        pos32(O, du, dw, P[a][b], J);
+    }
     const float *Yc = P[1][1];
     float rad2 = 0.f;
     for (int a = 0; a < 3; ++a)
