@@ -440,6 +440,7 @@ size_t solve_workspace_bytes(const dtn_patch_batch *b, const dtn_solve_opts *o, 
         const size_t w = o->bie_kind == 1 ? 8 : 4;
         t += (size_t)L.gmat_total * 8 + lu_shared_scratch_bytes(L) + (size_t)L.grows_total * 4 +
              (size_t)(L.gw_total + L.vec_total) * w;
+        if (!caps && o->bie_kind == 0) t += wrapped_static_bytes(L.panels_total);   // wrapped patches (box regions)
     } else {
         t += (size_t)L.matrix_total * 8 + lu_scratch_bytes(L, o->prec);
     }
@@ -452,7 +453,7 @@ size_t workspace_bytes(const dtn_geometry *g) {
     const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                             &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter,
                             &W.se_tmp, &W.tune, &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag,
-                            &W.panel_piece, &W.kinds};
+                            &W.panel_piece, &W.kinds, &W.pstat};
     size_t t = 0;
     for (const DevBuf *d : bufs) t += d->bytes;
     return t;
@@ -623,7 +624,7 @@ dtn_status dtn_destroy_geometry(dtn_geometry *g) {
                       &g->ws.panel_prm, &g->ws.panel_aux, &g->ws.panel_g, &g->ws.mat, &g->ws.lu32, &g->ws.lu64,
                       &g->ws.rhs, &g->ws.acc, &g->ws.counter, &g->ws.se_tmp, &g->ws.tune, &g->ws.gmat,
                       &g->ws.gfac, &g->ws.gpiv, &g->ws.gw, &g->ws.vec, &g->ws.sp, &g->ws.capflag,
-                      &g->ws.panel_piece, &g->ws.kinds};
+                      &g->ws.panel_piece, &g->ws.kinds, &g->ws.pstat};
     for (DevBuf *b : bufs) b->release();
     fmm_release(g);
     for (int k = 0; k < 5; ++k)
@@ -641,7 +642,8 @@ dtn_status dtn_release_workspace(dtn_geometry *g) {
     Workspace &W = g->ws;
     DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm, &W.panel_aux,
                       &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.counter, &W.se_tmp, &W.tune,
-                      &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag, &W.panel_piece, &W.kinds};
+                      &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.sp, &W.capflag, &W.panel_piece, &W.kinds,
+                      &W.pstat};
     for (DevBuf *b : bufs) b->release();
     if (g->graph_exec) {   // a captured graph holds the old pointers
         cudaGraphExecDestroy(g->graph_exec);
@@ -814,6 +816,9 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
             (e = W.vec.reserve((size_t)L.vec_total * (o->bie_kind == 1 ? sizeof(double) : sizeof(float)), s)) !=
                 cudaSuccess)
             return to_status(e);
+        if (std::find(L.wrapped.begin(), L.wrapped.end(), 1) != L.wrapped.end() &&
+            (e = W.pstat.reserve(wrapped_static_bytes(L.panels_total), s)) != cudaSuccess)
+            return to_status(e);
 
     } else {
         if (!r->matrix && (e = W.mat.reserve((size_t)L.matrix_total * 8, s)) != cudaSuccess) return to_status(e);
@@ -850,7 +855,7 @@ dtn_status dtn_solve_patches(dtn_geometry *g, const dtn_patch_batch *b, const dt
         put(r, sizeof(*r)); put(&g->data_version, sizeof(g->data_version));
         const DevBuf *bufs[] = {&W.layout, &W.gamma_loc, &W.gamma_w, &W.gamma_xyz, &W.panel_loc, &W.panel_prm,
                                 &W.panel_aux, &W.panel_g, &W.mat, &W.lu32, &W.lu64, &W.rhs, &W.acc, &W.se_tmp,
-                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.capflag, &W.panel_piece};
+                                &W.gmat, &W.gfac, &W.gpiv, &W.gw, &W.vec, &W.capflag, &W.panel_piece, &W.pstat};
         for (const DevBuf *d : bufs) put(&d->p, sizeof(void *));
         if (!(g->graph_exec && key == g->graph_key)) {
             if (g->graph_exec) {
@@ -989,7 +994,7 @@ cudaError_t enqueue_solve(dtn_geometry *g, const BatchLayout &L, const DevLayout
         // the panel rules, row by row
         if (e == cudaSuccess && std::find(L.wrapped.begin(), L.wrapped.end(), 1) != L.wrapped.end())
             e = launch_assemble(g, L, D, o->prec, 2, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean,
-                                gA, rhs, s, 0, 1);
+                                gA, rhs, s, 0, 1, W.pstat.p);
         if (e == cudaSuccess && r->matrix) e = launch_expand_matrices(L, D, gA, r->matrix, s);
     } else {
         e = launch_assemble(g, L, D, o->prec, 0, pl, pp, pa, pg, W.gamma_loc.as<double>(), gw, r->u_gamma_mean, A,

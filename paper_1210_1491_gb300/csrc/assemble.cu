@@ -346,6 +346,8 @@ __device__ void make_ctx(Ctx<T> &c, const PatchFrame &f, const double *X, double
     c.sub = 0;
 }
 
+struct PanelStatic32;
+
 struct AsmDev {
     const PatchFrame *frames;
     const int64_t *panel_off, *gamma_off, *mat_off;
@@ -361,6 +363,7 @@ struct AsmDev {
     int sk;     // second-kind system (1/2 I - D) q = b instead of Eq. bw49-bw51
     int only_wrapped;   // mode 2: the rows of wrapped patches only (the others are left untouched)
     const int64_t *group_of;   // mode 2: a wrapped patch's group (its matrix in A, gmat_off)
+    const PanelStatic32 *pstat;   // mixed-precision wrapped pass: per-panel FP32 maps
     const double *glx, *glw;
     const Piece *pieces;        // n_patches x kMaxPieces, or nullptr
     const int32_t *panel_piece; // per panel
@@ -549,53 +552,134 @@ __device__ void row32_setup(const Ctx<double> &c, Row32 &R) {
     R.ne = (float)sqrt(sq);
 }
 
-// the panel's map about its centre (prm: u0, u1, w0, w1, uc, wc) and C's offsets
-__device__ void off32_setup(const Ctx<double> &c, const double *prm, const double *Yc, Off32 &O) {
-    const Piece &q = *c.pc;
-    const int j = c.sub;
+// Per wrapped panel, once per call (`wrapped_static_kernel`): its map about its
+// centre C in FP32, C in global axes (FP64, from the ball centre), and its
+// bounding sphere's centre as an FP32 offset from C.
+struct PanelStatic32 {
+    double Ycg[3];
+    float uc, wc;
+    float eg[3], tg[3], js;
+    float Ug[3], Vg[3], rf;
+    float w2[2], ww, pc, sDc, rhoc;
+    float Ao[3], arad;
+    int type, piece;
+};
+
+// local (t1, t2, n) to global axes, one expression wherever it is used, so
+// that the same local point gives the same global offsets bit for bit
+__device__ __forceinline__ void to_global(const PatchFrame &f, const double *v, double *g) {
+    for (int d = 0; d < 3; ++d) g[d] = v[0] * f.t1[d] + v[1] * f.t2[d] + v[2] * f.n[d];
+}
+
+__device__ void panel_static32(const PatchFrame &f, const Piece &q, int k, int j, const double *prm, const double *Yc,
+                               const double *aux, PanelStatic32 &S) {
+    S.piece = k;
+    to_global(f, Yc, S.Ycg);
     const double uc = prm[4], wc = prm[5];
-    O.uc = (float)uc;
-    O.wc = (float)wc;
-    O.type = q.stype[j] ? 1 : (q.centred ? 0 : 2);
-    double Dl[3], Dsl[3];
-    for (int d = 0; d < 3; ++d) {
-        Dl[d] = Yc[d] - c.X[d];
-        Dsl[d] = c.img ? Yc[d] - c.Xs[d] : 0.0;
-    }
-    for (int d = 0; d < 3; ++d) {
-        O.eg[d] = (float)(q.en[j][0] * c.t1[d] + q.en[j][1] * c.t2[d] + q.en[j][2] * c.n[d]);
-        O.tg[d] = (float)(q.et[j][0] * c.t1[d] + q.et[j][1] * c.t2[d] + q.et[j][2] * c.n[d]);
-        O.Ug[d] = (float)(q.Ul[0] * c.t1[d] + q.Ul[1] * c.t2[d] + q.Ul[2] * c.n[d]);
-        O.Vg[d] = (float)(q.Vl[0] * c.t1[d] + q.Vl[1] * c.t2[d] + q.Vl[2] * c.n[d]);
-        O.Dc[d] = (float)(Dl[0] * c.t1[d] + Dl[1] * c.t2[d] + Dl[2] * c.n[d]);
-        O.Ds[d] = (float)(Dsl[0] * c.t1[d] + Dsl[1] * c.t2[d] + Dsl[2] * c.n[d]);
-    }
-    O.js = (float)(q.sdist[j] * q.sdist[j]);
-    O.rf = (float)q.rf;
-    if (O.type == 2) {
+    S.uc = (float)uc;
+    S.wc = (float)wc;
+    S.type = q.stype[j] ? 1 : (q.centred ? 0 : 2);
+    double g[3];
+    to_global(f, q.en[j], g);
+    for (int d = 0; d < 3; ++d) S.eg[d] = (float)g[d];
+    to_global(f, q.et[j], g);
+    for (int d = 0; d < 3; ++d) S.tg[d] = (float)g[d];
+    to_global(f, q.Ul, g);
+    for (int d = 0; d < 3; ++d) S.Ug[d] = (float)g[d];
+    to_global(f, q.Vl, g);
+    for (int d = 0; d < 3; ++d) S.Vg[d] = (float)g[d];
+    S.js = (float)(q.sdist[j] * q.sdist[j]);
+    S.rf = (float)q.rf;
+    if (S.type == 2) {
         const double w0 = q.P[0] - q.cf[0], w1 = q.P[1] - q.cf[1];
         double sv, cv;
         sincos(wc, &sv, &cv);
         const double pc = w0 * cv + w1 * sv, ww = w0 * w0 + w1 * w1;
         const double sDc = sqrt(fmax(0.0, pc * pc - ww + q.rf * q.rf));
-        O.w2[0] = (float)w0; O.w2[1] = (float)w1;
-        O.ww = (float)ww; O.pc = (float)pc; O.sDc = (float)sDc; O.rhoc = (float)(-pc + sDc);
+        S.w2[0] = (float)w0; S.w2[1] = (float)w1;
+        S.ww = (float)ww; S.pc = (float)pc; S.sDc = (float)sDc; S.rhoc = (float)(-pc + sDc);
     } else {
-        O.w2[0] = O.w2[1] = O.ww = O.pc = O.sDc = 0.f;
-        O.rhoc = O.rf;
+        S.w2[0] = S.w2[1] = S.ww = S.pc = S.sDc = 0.f;
+        S.rhoc = S.rf;
     }
+    const double ao[3] = {aux[0] - Yc[0], aux[1] - Yc[1], aux[2] - Yc[2]};
+    to_global(f, ao, g);
+    for (int d = 0; d < 3; ++d) S.Ao[d] = (float)g[d];
+    S.arad = (float)aux[3];
+}
+
+// Per row (shared memory): X and its Kelvin image in global axes, and the
+// normal-derivative constants of each piece
+struct RowStatic32 {
+    double Xg[3], Xsg[3];
+    float k1[kMaxPieces], k2[kMaxPieces], gi, g0;
+    int img;
+};
+
+__device__ void row_static32(const Ctx<double> &c, const PatchFrame &f, const Piece *pcs, RowStatic32 &R) {
+    to_global(f, c.X, R.Xg);
+    const double zero[3] = {0.0, 0.0, 0.0};
+    to_global(f, c.img ? c.Xs : zero, R.Xsg);
     const double xx = c.xn * c.xn;
-    double nyX = 0.0, nyP = 0.0, nyXP = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        nyX += q.nl[d] * c.X[d];
-        nyP += q.nl[d] * q.Pl[d];
-        nyXP += q.nl[d] * (c.X[d] - q.Pl[d]);
+    for (int k = 0; k < f.npiece && k < kMaxPieces; ++k) {
+        const Piece &q = pcs[k];
+        double nyX = 0.0, nyP = 0.0, nyXP = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            nyX += q.nl[d] * c.X[d];
+            nyP += q.nl[d] * q.Pl[d];
+            nyXP += q.nl[d] * (c.X[d] - q.Pl[d]);
+        }
+        R.k1[k] = (float)nyXP;
+        R.k2[k] = c.img ? (float)(c.a * (xx * nyP - c.a * c.a * nyX) / (xx * c.xn)) : 0.f;
     }
-    O.img = c.img;
-    O.k1 = (float)nyXP;
-    O.k2 = c.img ? (float)(c.a * (xx * nyP - c.a * c.a * nyX) / (xx * c.xn)) : 0.f;
-    O.gi = c.img ? (float)(c.a / c.xn) : 0.f;
-    O.g0 = c.img ? 0.f : (float)(1.0 / c.a);
+    R.img = c.img;
+    R.gi = c.img ? (float)(c.a / c.xn) : 0.f;
+    R.g0 = c.img ? 0.f : (float)(1.0 / c.a);
+}
+
+// the panel's map about C and C's offsets from X and X*: the FP64 work of a
+// (row, panel) pair is six subtractions
+__device__ __forceinline__ void off32_make(const PanelStatic32 &S, const RowStatic32 &R, Off32 &O) {
+    O.type = S.type;
+    O.uc = S.uc;
+    O.wc = S.wc;
+    for (int d = 0; d < 3; ++d) {
+        O.eg[d] = S.eg[d]; O.tg[d] = S.tg[d]; O.Ug[d] = S.Ug[d]; O.Vg[d] = S.Vg[d];
+        O.Dc[d] = (float)(S.Ycg[d] - R.Xg[d]);
+        O.Ds[d] = R.img ? (float)(S.Ycg[d] - R.Xsg[d]) : 0.f;
+    }
+    O.js = S.js; O.rf = S.rf;
+    O.w2[0] = S.w2[0]; O.w2[1] = S.w2[1];
+    O.ww = S.ww; O.pc = S.pc; O.sDc = S.sDc; O.rhoc = S.rhoc;
+    O.k1 = R.k1[S.piece]; O.k2 = R.k2[S.piece];
+    O.gi = R.gi; O.g0 = R.g0;
+    O.img = R.img != 0;
+}
+
+// distance ratio of the panel (its bounding sphere) to X and X*, in FP32
+__device__ __forceinline__ float ratio_panel32(const PanelStatic32 &S, const Off32 &O) {
+    const float ax = O.Dc[0] + S.Ao[0], ay = O.Dc[1] + S.Ao[1], az = O.Dc[2] + S.Ao[2];
+    float d2 = ax * ax + ay * ay + az * az;
+    if (O.img) {
+        const float bx = O.Ds[0] + S.Ao[0], by = O.Ds[1] + S.Ao[1], bz = O.Ds[2] + S.Ao[2];
+        d2 = fminf(d2, bx * bx + by * by + bz * bz);
+    }
+    return sqrtf(d2) / S.arad;
+}
+
+__global__ void wrapped_static_kernel(int64_t n_patches, int64_t total, const int64_t *__restrict__ panel_off,
+                                      const PatchFrame *__restrict__ frames, const Piece *__restrict__ pieces,
+                                      const int32_t *__restrict__ panel_piece, const double *__restrict__ prm,
+                                      const double *__restrict__ loc, const double *__restrict__ aux,
+                                      PanelStatic32 *__restrict__ out) {
+    const int64_t gidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gidx >= total) return;
+    const int64_t p = find_group(panel_off, n_patches, gidx);
+    const PatchFrame &f = frames[p];
+    if (f.kind != kWrapped || f.status != DTN_OK) return;
+    const int code = panel_piece[gidx];
+    const int k = code / kMaxSub, j = code - k * kMaxSub;
+    panel_static32(f, pieces[p * kMaxPieces + k], k, j, prm + 6 * gidx, loc + 3 * gidx, aux + 4 * gidx, out[gidx]);
 }
 
 // line dw of the map: B(wc + dw), uc (B(wc + dw) - B(wc)) (global axes), Jacobian factor
@@ -818,6 +902,83 @@ __device__ void far_panel32(const Off32 &O, const Row32 &Rw, float a0, float da,
     sd += (double)(ld * jac) * (0.25 / kPi);
 }
 
+// self_regions on FP32 offsets from the collocation point (the panel centre C
+// of the Off32 map), for the mixed-precision pass: the same quadrants, graded
+// pieces and Duffy triangles, measured on pos32 (a side that maps to one point
+// is recognised at 1e-5 of its distance, above FP32 rounding of the offsets).
+template <typename Fn>
+__device__ void self_regions32(const Off32 &O, const double *prm, Fn &&fn) {
+    const double ucs[2] = {prm[0], prm[1]}, wcs[2] = {prm[2], prm[3]};
+    auto len = [](const float *A, const float *B) {
+        return sqrtf((A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]));
+    };
+    const float Z[3] = {0.f, 0.f, 0.f};
+    float J;
+#pragma unroll 1
+    for (int qd = 0; qd < 4; ++qd) {
+        const float Du = (float)(ucs[qd >> 1] - prm[4]), Dw = (float)(wcs[qd & 1] - prm[5]);
+        if (Du == 0.f || Dw == 0.f) continue;
+        float Pa[3], Pm[3], Pb[3];
+        pos32(O, Du, 0.f, Pa, J);
+        pos32(O, 0.f, 0.5f * Dw, Pm, J);
+        pos32(O, 0.f, Dw, Pb, J);
+        const float lu = len(Pa, Z), lw = len(Pm, Z) + len(Pb, Pm);
+        int along = 0;
+        float f0 = 1.f;
+        if (lw > 2.f * lu) { along = 2; f0 = lu / lw; }
+        else if (lu > 2.f * lw) { along = 1; f0 = lw / lu; }
+        f0 = fmaxf(f0, 1.f / 1048576.f);
+        float fa = 0.f, fb = f0;
+        for (int k = 0;; ++k) {
+            float a1 = Du, b1 = Dw, a0 = 0.f, b0 = 0.f;
+            if (along == 1) { a0 = fa * Du; a1 = fb * Du; }
+            if (along == 2) { b0 = fa * Dw; b1 = fb * Dw; }
+            if (k == 0) {
+                // Duffy triangles (C, (a1, 0), (a1, b1)) and (C, (a1, b1), (0, b1)), far
+                // sides cut to the triangle's height (four pieces on a degenerate side)
+                const float ta[2][2] = {{a1, 0.f}, {a1, b1}}, tb[2][2] = {{a1, b1}, {0.f, b1}};
+#pragma unroll 1
+                for (int t = 0; t < 2; ++t) {
+                    float PA[3], PB[3];
+                    pos32(O, ta[t][0], ta[t][1], PA, J);
+                    pos32(O, tb[t][0], tb[t][1], PB, J);
+                    const float ab[3] = {PB[0] - PA[0], PB[1] - PA[1], PB[2] - PA[2]};
+                    const float as[3] = {-PA[0], -PA[1], -PA[2]};
+                    const float cr[3] = {ab[1] * as[2] - ab[2] * as[1], ab[2] * as[0] - ab[0] * as[2],
+                                         ab[0] * as[1] - ab[1] * as[0]};
+                    const float L = sqrtf(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+                    const float h = sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / fmaxf(L, 1e-30f);
+                    int m = (int)fminf(64.f, fmaxf(1.f, ceilf(L / fmaxf(h, 1e-30f))));
+                    if (L <= 1e-5f * sqrtf(as[0] * as[0] + as[1] * as[1] + as[2] * as[2])) m = 4;
+                    for (int e = 0; e < m; ++e) {
+                        const float Au = ta[t][0] + (tb[t][0] - ta[t][0]) * e / m;
+                        const float Aw = ta[t][1] + (tb[t][1] - ta[t][1]) * e / m;
+                        const float Bu = ta[t][0] + (tb[t][0] - ta[t][0]) * (e + 1) / m;
+                        const float Bw = ta[t][1] + (tb[t][1] - ta[t][1]) * (e + 1) / m;
+                        Reg32 R;
+                        R.tri = true;
+                        R.a0 = R.da = R.b0 = R.db = 0.f;
+                        R.E1[0] = Au; R.E1[1] = Aw;
+                        R.E2[0] = Bu - Au; R.E2[1] = Bw - Aw;
+                        R.det = fabsf(R.E1[0] * R.E2[1] - R.E1[1] * R.E2[0]);
+                        if (R.det > 0.f) fn(R, false, 10);
+                    }
+                }
+            } else {
+                Reg32 R;
+                R.tri = false;
+                R.a0 = fminf(a0, a1); R.da = fabsf(a1 - a0);
+                R.b0 = fminf(b0, b1); R.db = fabsf(b1 - b0);
+                R.E1[0] = R.E1[1] = R.E2[0] = R.E2[1] = R.det = 0.f;
+                fn(R, true, 0);
+            }
+            if (along == 0 || fb >= 1.f) break;
+            fa = fb;
+            fb = fminf(1.f, 2.f * fb);
+        }
+    }
+}
+
 // The Gauss rule of order nq on one sub-square of a region, its points dealt
 // to the lanes of a warp in turn (each lane sums its own points).
 __device__ __forceinline__ void coop_gauss(const Ctx<double> &c, const Region &R, double x0, double x1, double e0,
@@ -896,12 +1057,14 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     __shared__ int near_count;
     __shared__ double self_part[2][kAsmThreads / 32];
     __shared__ Gauss32 g32;
+    __shared__ RowStatic32 rs32;
     Row32 rw;
     if (W32) {
         for (int k = threadIdx.x; k < kMaxRule * (kMaxRule + 1) / 2; k += blockDim.x) {
             g32.t[k] = (float)(0.5 + 0.5 * P.glx[k]);
             g32.w[k] = (float)(0.5 * P.glw[k]);
         }
+        if (threadIdx.x == 0) row_static32(c64, f, pcs, rs32);
         row32_setup(c64, rw);
     }
     __shared__ double sk_grad[2];
@@ -950,7 +1113,15 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     __shared__ int warp_near[kAsmThreads / 32];
     for (int j0 = 0; j0 < n; j0 += blockDim.x) {
         const int j = j0 + threadIdx.x;
-        const bool near = (j < n && j != i) && panel_ratio(c64, X, P.panel_aux + 4 * (poff + j)) < 2.0;
+        Off32 O;
+        float r32 = 0.f;
+        if (W32 && j < n && j != i) {
+            const PanelStatic32 &S = P.pstat[poff + j];
+            off32_make(S, rs32, O);
+            r32 = ratio_panel32(S, O);
+        }
+        const bool near = (j < n && j != i) &&
+                          (W32 ? r32 < 2.f : panel_ratio(c64, X, P.panel_aux + 4 * (poff + j)) < 2.0);
         const unsigned bal = __ballot_sync(0xffffffffu, near);
         if (lane == 0) warp_near[warp] = __popc(bal);
         __syncthreads();
@@ -963,7 +1134,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         __syncthreads();
         if (j >= n || j == i || near) continue;
         const int64_t pj = poff + j;
-        const double r = panel_ratio(c64, X, P.panel_aux + 4 * pj);
+        const double r = W32 ? (double)r32 : panel_ratio(c64, X, P.panel_aux + 4 * pj);
         const double *prm = P.panel_prm + 6 * pj;
         Region R;
         R.tri = false;
@@ -971,9 +1142,6 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         R.det = 0.0;
         double sa = 0.0, sd = 0.0;
         if (far32) {
-            ctx_panel(c64, pcs, P.panel_piece[pj]);
-            Off32 O;
-            off32_setup(c64, prm, P.panel_loc + 3 * pj, O);
             far_panel32(O, rw, (float)(prm[0] - prm[4]), (float)(prm[1] - prm[0]), (float)(prm[2] - prm[5]),
                         (float)(prm[3] - prm[2]), order32r((float)r), g32, sa, sd);
         } else {
@@ -1000,22 +1168,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             // point (the panel centre), by the FP32 rules and covers
             const double *prm = P.panel_prm + 6 * row;
             Off32 O;
-            off32_setup(c64, prm, X, O);
-            self_regions(c64, prm, [&](const Region &R, bool withX, int min_order) {
+            off32_make(P.pstat[row], rs32, O);
+            self_regions32(O, prm, [&](const Reg32 &Q, bool withX, int min_order) {
                 if ((tri++ % (kAsmThreads / 32)) != warp) return;
-                Reg32 Q;
-                Q.tri = R.tri;
-                if (R.tri) {
-                    Q.E1[0] = (float)R.p[2]; Q.E1[1] = (float)R.p[3];
-                    Q.E2[0] = (float)R.p[4]; Q.E2[1] = (float)R.p[5];
-                    Q.det = (float)R.det;
-                    Q.a0 = Q.da = Q.b0 = Q.db = 0.f;
-                } else {
-                    Q.a0 = (float)(R.p[0] - prm[4]); Q.da = (float)R.p[1];
-                    Q.b0 = (float)(R.p[2] - prm[5]); Q.db = (float)R.p[3];
-                    Q.E1[0] = Q.E1[1] = Q.E2[0] = Q.E2[1] = Q.det = 0.f;
-                }
-                adaptive32(O, Q, withX, withX ? 0 : 10, [&](float x0, float x1, float e0, float e1, int n) {
+                adaptive32(O, Q, withX, min_order, [&](float x0, float x1, float e0, float e1, int n) {
                     square32_warp(O, rw, Q, x0, x1, e0, e1, n, g32, lane, sa, sd);
                 });
             });
@@ -1057,7 +1213,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         if (far32) {
             // mixed precision on a wrapped patch: the FP32 cover in offsets from the panel centre
             Off32 O;
-            off32_setup(c64, prm, P.panel_loc + 3 * (poff + j), O);
+            off32_make(P.pstat[poff + j], rs32, O);
             Reg32 Q;
             Q.tri = false;
             Q.a0 = (float)(prm[0] - prm[4]); Q.da = (float)(prm[1] - prm[0]);
@@ -1478,7 +1634,8 @@ __global__ void expand_kernel(int64_t n_patches, const int64_t *__restrict__ mat
 cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D, int prec, int mode,
                             const double *panel_loc, const double *panel_prm, const double *panel_aux,
                             const double *panel_g, const double *gamma_loc, const double *gamma_w,
-                            const double *U, double *A, double *b, cudaStream_t s, int sk, int only_wrapped) {
+                            const double *U, double *A, double *b, cudaStream_t s, int sk, int only_wrapped,
+                            void *pstat) {
     const int64_t rows = (mode == 1) ? L.grows_total : L.panels_total;
     if (rows == 0) return cudaSuccess;
     AsmDev P;
@@ -1506,16 +1663,24 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.sk = sk;
     P.only_wrapped = only_wrapped;
     P.group_of = D.group_of;
+    P.pstat = (const PanelStatic32 *)pstat;
     P.glx = gl_x_dev();
     P.glw = gl_w_dev();
     P.pieces = D.pieces;
     P.panel_piece = g->ws.panel_piece.as<int32_t>();
     if (sk) assemble_kernel<true, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
-    else if (mode == 2 && only_wrapped && prec == DTN_PREC_MIXED)
+    else if (mode == 2 && only_wrapped && prec == DTN_PREC_MIXED) {
+        if (!pstat) return cudaErrorInvalidValue;
+        wrapped_static_kernel<<<(unsigned)((L.panels_total + 255) / 256), 256, 0, s>>>(
+            L.n_patches, L.panels_total, D.panel_off, D.frames, D.pieces, P.panel_piece, panel_prm, panel_loc,
+            panel_aux, (PanelStatic32 *)pstat);
         assemble_kernel<false, true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    }
     else assemble_kernel<false, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
+
+size_t wrapped_static_bytes(int64_t panels) { return (size_t)panels * sizeof(PanelStatic32); }
 
 cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const DevLayout &D,
                               const double *panel_loc, const double *panel_prm, const double *panel_aux,

@@ -109,6 +109,7 @@ struct Workspace {
     DevBuf capflag;         // n_patches int32: 1 where a walk of the patch was cut at max_steps
     DevBuf panel_piece;     // panels_total int32: the piece of a wrapped patch's panel
     DevBuf kinds;           // n_patches frames + kinds of the classification pre-pass (mixed, wires)
+    DevBuf pstat;           // panels_total per-panel FP32 maps (mixed precision, wrapped patches)
 };
 
 struct GeometryHost {
@@ -234,7 +235,9 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
                             int prec, int mode, const double *panel_loc, const double *panel_prm,
                             const double *panel_aux, const double *panel_g, const double *gamma_loc,
                             const double *gamma_w, const double *U, double *A, double *b, cudaStream_t s,
-                            int sk = 0, int only_wrapped = 0);
+                            int sk = 0, int only_wrapped = 0, void *pstat = nullptr);
+// bytes of the per-panel FP32 maps of the mixed-precision wrapped pass
+size_t wrapped_static_bytes(int64_t panels);
 
 // mixed precision right sides: FP64 weights per shape group (product rules of
 // the double layer against the panel interpolants of the data, and the walk
