@@ -579,6 +579,35 @@ __device__ inline bool m2l_task(int t, int P, int &n, int &m0) {
     return false;
 }
 
+// The geometry of each accepted pair, once per pair (the M2L kernel's lanes would
+// otherwise each redo it, on GB300's narrow FP64 pipe): the translation z - c
+// in units of the finer cell's half-width, that scale, and the two cells'
+// level offsets from the finer level.
+struct M2lGeo {
+    float v[3], fr;
+    int bt, bs;
+};
+
+__global__ void fmm_m2lgeo_kernel(int64_t n, const uint64_t *__restrict__ list, const FCell *__restrict__ tc,
+                                  const FCell *__restrict__ sc, double half_w0, M2lGeo *__restrict__ geo) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const uint64_t key = list[e];
+    const FCell &T = tc[(int64_t)(key >> 32)];
+    const FCell &Sc = sc[(int64_t)(uint32_t)(key & 0xffffffffu)];
+    const int lt = T.level, ls = Sc.level;
+    const int lr = min(lt, ls);
+    const double irho = ldexp(1.0 / half_w0, lr);
+    M2lGeo G;
+    G.v[0] = (float)((T.c[0] - Sc.c[0]) * irho);
+    G.v[1] = (float)((T.c[1] - Sc.c[1]) * irho);
+    G.v[2] = (float)((T.c[2] - Sc.c[2]) * irho);
+    G.fr = (float)irho;
+    G.bt = lt - lr;
+    G.bs = ls - lr;
+    geo[e] = G;
+}
+
 // Persistent warps: each takes the next target cell from *queue (L is zeroed
 // before the launch, so cells without M2L pairs are skipped).
 // PT > 0: the order is the compile-time PT (the j and k loops unroll fully;
@@ -587,8 +616,8 @@ __device__ inline bool m2l_task(int t, int P, int &n, int &m0) {
 template <int PT>
 __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     const FCell *__restrict__ tc, int64_t ntc, const FCell *__restrict__ sc, const int64_t *__restrict__ off,
-    const uint64_t *__restrict__ list, double half_w0, int P, const float2 *__restrict__ M, float2 *__restrict__ L,
-    unsigned long long *__restrict__ queue) {
+    const uint64_t *__restrict__ list, const M2lGeo *__restrict__ geo, int P, const float2 *__restrict__ M,
+    float2 *__restrict__ L, unsigned long long *__restrict__ queue) {
     if (PT > 0) P = PT;
     __shared__ M2lShared sh[kCellWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -604,7 +633,6 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     float *S = sh[wid].s + kSPad;
     float2 *Mf = sh[wid].m;
     if (lane < kSPad) sh[wid].s[lane] = 0.0f;
-    const double ihw = 1.0 / half_w0;
     for (;;) {
     unsigned long long qi = 0;
     if (lane == 0) qi = atomicAdd(queue, 1ull);
@@ -612,7 +640,6 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
     if (ti >= ntc) break;
     const int64_t e0 = off[ti], e1 = off[ti + 1];
     if (e0 == e1) continue;
-    const FCell T = tc[ti];
     float2 acc[kM2lTasksMax][kM2lBlock];
 #pragma unroll
     for (int r = 0; r < kM2lTasksMax; ++r)
@@ -620,13 +647,9 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
         for (int d = 0; d < kM2lBlock; ++d) acc[r][d] = make_float2(0.0f, 0.0f);
     for (int64_t e = e0; e < e1; ++e) {
         const int64_t si = (int64_t)(uint32_t)(list[e] & 0xffffffffu);
-        const FCell &Sc = sc[si];
-        const int lt = T.level, ls = Sc.level;
-        const int lr = min(lt, ls);
-        const double irho = ldexp(ihw, lr);
-        const float vx = (float)((T.c[0] - Sc.c[0]) * irho), vy = (float)((T.c[1] - Sc.c[1]) * irho),
-                    vz = (float)((T.c[2] - Sc.c[2]) * irho);
-        const int bt = lt - lr, bs = ls - lr;
+        const M2lGeo G = geo[e];
+        const float vx = G.v[0], vy = G.v[1], vz = G.v[2];
+        const int bt = G.bt, bs = G.bs;
         // azimuth of z - c taken out: S_N^l(v) = e^{i l phi} s_N^l with s the (real)
         // singular harmonics at (rho_xy, 0, vz); the source's coefficients are
         // turned by e^{i k phi} and each output by e^{-i m phi}
@@ -662,7 +685,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) fmm_m2l_kernel(
             if (m) Mf[n * n + n - m] = make_float2(sg * w.x, -sg * w.y);
         }
         __syncwarp();
-        const float fr = (float)irho;
+        const float fr = G.fr;
 #pragma unroll
         for (int r = 0; r < kM2lTasksMax; ++r) {
             if (r == 1 && !round2) break;
@@ -966,7 +989,7 @@ inline int64_t nblk(int64_t n, int t) { return (n + t - 1) / t; }
 
 struct FmmWorkspace {
     DevBuf part, kin, kout, vin, sval, tval, flag, pos, lo, hi, cub, scell, tcell, tparent;
-    DevBuf spos, sdat, srel, M, L, front, next, m2l, m2l_s, p2p, p2p_s, m2l_off, p2p_off, cnt, gtmp, queue;
+    DevBuf spos, sdat, srel, M, L, front, next, m2l, m2l_s, p2p, p2p_s, m2l_off, p2p_off, cnt, gtmp, queue, m2lgeo;
     DttCounters *host_cnt = nullptr;   // pinned
     int64_t cap_front = 0, cap_m2l = 0, cap_p2p = 0;
     int64_t grid_m2l = 0, grid_leaf = 0;   // persistent grids (resident CTAs x SMs)
@@ -978,7 +1001,7 @@ void fmm_release(dtn_geometry *g) {
     DevBuf *bufs[] = {&w->part, &w->kin, &w->kout, &w->vin, &w->sval, &w->tval, &w->flag, &w->pos, &w->lo,
                       &w->hi, &w->cub, &w->scell, &w->tcell, &w->tparent, &w->spos, &w->sdat, &w->srel, &w->M, &w->L,
                       &w->front, &w->next, &w->m2l, &w->m2l_s, &w->p2p, &w->p2p_s, &w->m2l_off, &w->p2p_off,
-                      &w->cnt, &w->gtmp, &w->queue};
+                      &w->cnt, &w->gtmp, &w->queue, &w->m2lgeo};
     for (DevBuf *b : bufs) b->release();
     if (w->host_cnt) cudaFreeHost(w->host_cnt);
     delete w;
@@ -1221,6 +1244,10 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
     FMM_TRY(w.m2l_off.reserve((ntc + 1) * 8));
     FMM_TRY(w.p2p_off.reserve((ntc + 1) * 8));
     fmm_csr_kernel<<<nblk(ntc + 1, 256), 256, 0, s>>>(ntc, w.m2l_s.as<uint64_t>(), n_m2l, w.m2l_off.as<int64_t>());
+    FMM_TRY(w.m2lgeo.reserve(std::max<int64_t>(n_m2l, 1) * sizeof(M2lGeo)));
+    if (n_m2l > 0)
+        fmm_m2lgeo_kernel<<<nblk(n_m2l, 256), 256, 0, s>>>(n_m2l, w.m2l_s.as<uint64_t>(), w.tcell.as<FCell>(),
+                                                           w.scell.as<FCell>(), half_w0, w.m2lgeo.as<M2lGeo>());
     fmm_csr_kernel<<<nblk(ntc + 1, 256), 256, 0, s>>>(ntc, w.p2p_s.as<uint64_t>(), n_p2p, w.p2p_off.as<int64_t>());
     FMM_TRY(cudaGetLastError());
 
@@ -1241,7 +1268,7 @@ cudaError_t fmm_evaluate(dtn_geometry *g, int64_t np, int64_t np_total, const do
         const int grid = (int)std::min<int64_t>(w.grid_m2l, nblk(ntc, kCellWarps));
         auto kern = P == 8 ? fmm_m2l_kernel<8> : P == 10 ? fmm_m2l_kernel<10> : fmm_m2l_kernel<0>;
         kern<<<grid, 32 * kCellWarps, 0, s>>>(w.tcell.as<FCell>(), ntc, w.scell.as<FCell>(), w.m2l_off.as<int64_t>(),
-                                              w.m2l_s.as<uint64_t>(), half_w0, P, w.M.as<float2>(),
+                                              w.m2l_s.as<uint64_t>(), w.m2lgeo.as<M2lGeo>(), P, w.M.as<float2>(),
                                               w.L.as<float2>(), queue);
     }
     FMM_TRY(cudaGetLastError());
