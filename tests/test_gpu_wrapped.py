@@ -183,3 +183,48 @@ def test_mixed_batch_of_wrapped_patches_only():
     torch.cuda.synchronize()
     assert np.all(_np(res2["patch_status"]) == 0)
     assert np.array_equal(_np(res2["neumann"]), _np(res["neumann"])[n:])
+
+
+def test_wire_layout_wrapped_patches_match_oracle_entrywise():
+    """Wrapped patches of the wire workload itself (2 to 4 faces, polar origins
+    moved onto near sides among them), solved with the exact values at the GPU's
+    hemisphere nodes: FP64 matrix and right side within 1e-10 of their largest
+    entries and q within relative L2 1e-10 of the oracle's adaptive integrals
+    and solve; mixed precision within 5e-7 (matrix), 1e-6 (right side) and
+    1e-5 (q)."""
+    wl = W.wires(n_patches=64, walks=64)
+    idx = [int(i) for i in np.nonzero(wl.faces_met > 1)[0][:6]]
+    b0 = wl.batch
+    sub = W.PatchBatch(centers=b0.centers[idx], radius=b0.radius[idx], n_theta=b0.n_theta[idx],
+                       n_phi=b0.n_phi[idx], n_rings=b0.n_rings[idx], n_sectors=b0.n_sectors[idx],
+                       walks=b0.walks[idx])
+    wl = W.Workload("wire_sub", wl.geometry, wl.data, sub)
+    g, b, hb = _setup(wl)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
+    torch.cuda.synchronize()
+    U = O.dirichlet(wl.data, _np(r0["gamma_xyz"]))
+    Pn = (b.n_theta * b.n_phi).astype(np.int64)
+    nn = (b.n_rings * b.n_sectors).astype(np.int64)
+    goff, poff, moff = np.r_[0, np.cumsum(Pn)], np.r_[0, np.cumsum(nn)], np.r_[0, np.cumsum(nn * nn)]
+    ref = []
+    for p in range(b.n):
+        pf = O.patch_frame(wl.geometry, b.centers[p], float(b.radius[p]))
+        assert pf.kind == 2
+        Ao, bo = O.assemble(pf, wl.data, int(b.n_rings[p]), int(b.n_sectors[p]), int(b.n_theta[p]),
+                            int(b.n_phi[p]), U[goff[p]:goff[p + 1]], rtol=1e-12)
+        ref.append((Ao, bo, np.linalg.solve(Ao, bo)))
+    for prec, ta, tb, tq in [(dtn.PREC_FP64, 1e-10, 1e-10, 1e-10), (dtn.PREC_MIXED, 5e-7, 1e-6, 1e-5)]:
+        res = dtn.alloc_result(hb, want_matrix=True)
+        res["u_gamma_mean"].copy_(torch.from_numpy(U))
+        dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=prec, u_provided=True), result=res)
+        torch.cuda.synchronize()
+        assert np.all(_np(res["patch_status"]) == 0)
+        for p in range(b.n):
+            Ao, bo, qo = ref[p]
+            n = int(nn[p])
+            Am = _np(res["matrix"])[moff[p]:moff[p + 1]].reshape(n, n)
+            bm = _np(res["rhs"])[poff[p]:poff[p + 1]]
+            q = _np(res["neumann"])[poff[p]:poff[p + 1]]
+            assert np.max(np.abs(Am - Ao)) <= ta * np.max(np.abs(Ao)), (prec, p)
+            assert np.max(np.abs(bm - bo)) <= tb * np.max(np.abs(bo)), (prec, p)
+            assert np.linalg.norm(q - qo) / np.linalg.norm(qo) <= tq, (prec, p)
