@@ -228,3 +228,39 @@ def test_wire_layout_wrapped_patches_match_oracle_entrywise():
             assert np.max(np.abs(Am - Ao)) <= ta * np.max(np.abs(Ao)), (prec, p)
             assert np.max(np.abs(bm - bo)) <= tb * np.max(np.abs(bo)), (prec, p)
             assert np.linalg.norm(q - qo) / np.linalg.norm(qo) <= tq, (prec, p)
+
+
+@pytest.mark.parametrize("data", ["harmonic", "constant"])
+def test_wrapped_patches_with_other_data(data):
+    """The wrapped patches of the single-wire case with harmonic-polynomial data
+    (the mixed pass differences them in FP64 at each point) and with constant
+    data (no data integral): FP64 and mixed-precision solves with the exact
+    values at the GPU's nodes against the oracle's adaptive integrals and solve;
+    constant data give q = 0."""
+    wl = _case()
+    if data == "harmonic":
+        wl = W.Workload("one_wire_sh", wl.geometry,
+                        W.Dirichlet(W.DATA_HARMONIC_SH, lmax=4, clm=W.random_clm(4, 5), center=(2.0, 1.5, 1.5),
+                                    scale=2.0), wl.batch)
+    else:
+        wl = W.Workload("one_wire_const", wl.geometry, W.Dirichlet(W.DATA_CONSTANT, constant=2.0), wl.batch)
+    g, b, hb = _setup(wl)
+    r0 = dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=dtn.PREC_FP64, u_provided=True))
+    torch.cuda.synchronize()
+    U = O.dirichlet(wl.data, _np(r0["gamma_xyz"]))
+    P, n = 12 * 24, 3 * 16
+    for prec, tq in [(dtn.PREC_FP64, 1e-10), (dtn.PREC_MIXED, 1e-5)]:
+        res = dtn.alloc_result(hb)
+        res["u_gamma_mean"].copy_(torch.from_numpy(U))
+        dtn.solve_patches(g, b.centers, b.radius, hb, dtn.solve_opts(prec=prec, u_provided=True), result=res)
+        torch.cuda.synchronize()
+        assert np.all(_np(res["patch_status"]) == 0)
+        for p in range(1, b.n):
+            q = _np(res["neumann"])[p * n:(p + 1) * n]
+            if data == "constant":
+                assert np.max(np.abs(q)) < 1e-9, (prec, p)
+                continue
+            pf = O.patch_frame(wl.geometry, b.centers[p], A)
+            Ao, bo = O.assemble(pf, wl.data, 3, 16, 12, 24, U[p * P:(p + 1) * P], rtol=1e-12)
+            qo = np.linalg.solve(Ao, bo)
+            assert np.linalg.norm(q - qo) / np.linalg.norm(qo) <= tq, (prec, p)
