@@ -1113,15 +1113,15 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     __shared__ int warp_near[kAsmThreads / 32];
     for (int j0 = 0; j0 < n; j0 += blockDim.x) {
         const int j = j0 + threadIdx.x;
+        const bool mine = j < n && j != i;
         Off32 O;
         float r32 = 0.f;
-        if (W32 && j < n && j != i) {
+        if (W32 && mine) {
             const PanelStatic32 &S = P.pstat[poff + j];
             off32_make(S, rs32, O);
             r32 = ratio_panel32(S, O);
         }
-        const bool near = (j < n && j != i) &&
-                          (W32 ? r32 < 2.f : panel_ratio(c64, X, P.panel_aux + 4 * (poff + j)) < 2.0);
+        const bool near = mine && (W32 ? r32 < 2.f : panel_ratio(c64, X, P.panel_aux + 4 * (poff + j)) < 2.0);
         const unsigned bal = __ballot_sync(0xffffffffu, near);
         if (lane == 0) warp_near[warp] = __popc(bal);
         __syncthreads();
@@ -1132,7 +1132,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
         if (threadIdx.x == 0)
             for (int w = 0; w < kAsmThreads / 32; ++w) near_count += warp_near[w];
         __syncthreads();
-        if (j >= n || j == i || near) continue;
+        if (!mine || near) continue;
         const int64_t pj = poff + j;
         const double r = W32 ? (double)r32 : panel_ratio(c64, X, P.panel_aux + 4 * pj);
         const double *prm = P.panel_prm + 6 * pj;
@@ -1444,12 +1444,14 @@ __global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev
     const PatchFrame f = P.frames[r.p];
     Ctx<double> c;
     make_ctx<double>(c, f, r.X, 0.0, nullptr);
-    // near panels of this row
+    // near panels of this row: the row's CTAs (gridDim.y) take the panels j with
+    // j mod gridDim.y = blockIdx.y; the own panel is the first CTA's
     for (int j = threadIdx.x; j < r.n; j += blockDim.x)
-        if (j != r.i && panel_ratio(c, r.X, P.panel_aux + 4 * (r.poff + j)) < kFarRatio)
+        if (j != r.i && (j % (int)gridDim.y) == (int)blockIdx.y &&
+            panel_ratio(c, r.X, P.panel_aux + 4 * (r.poff + j)) < kFarRatio)
             near_list[atomicAdd(&near_count, 1)] = j;
     // own panel
-    {
+    if (blockIdx.y == 0) {
         const double *prm = P.panel_prm + 6 * (r.poff + r.i);
         const double u0 = prm[0], du = prm[1] - prm[0], v0 = prm[2], dv = prm[3] - prm[2];
         double acc0 = 0.0, acc1 = 0.0;
@@ -1466,7 +1468,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) rhs_near_weights_kernel(WtDev
         part[warp][o + 1] = acc1;
     }
     __syncthreads();
-    if (threadIdx.x < kSamplesPerPanel) {
+    if (blockIdx.y == 0 && threadIdx.x < kSamplesPerPanel) {
         double t = 0.0;
         for (int w = 0; w < kNearWarps; ++w) t += part[w][threadIdx.x];
         r.W[(int64_t)r.i * kSamplesPerPanel + threadIdx.x] = (float)t;
@@ -1505,37 +1507,56 @@ __global__ void __launch_bounds__(kWtThreads) rhs_walk_weights_kernel(WtDev P) {
 // Per-patch sample vectors: the data at the 8 x 8 Gauss points of every panel
 // (FP32 evaluation) and the walk estimates, each minus c = g at the first
 // collocation point, stored FP32.  One thread per sample.
-__global__ void rhs_samples_kernel(DData dat, int64_t n_patches, int64_t total, const int64_t *__restrict__ vec_off,
-                                   const int64_t *__restrict__ panel_off, const int64_t *__restrict__ gamma_off,
-                                   const PatchFrame *__restrict__ frames, const double *__restrict__ panel_prm,
-                                   const double *__restrict__ panel_g, const double *__restrict__ U,
-                                   const double *__restrict__ glx, float *__restrict__ vec) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int64_t p = find_group(vec_off, n_patches, idx);
-    const int64_t q = idx - vec_off[p];
-    const int64_t m = gamma_off[p + 1] - gamma_off[p];
-    const int64_t dcols = vec_off[p + 1] - vec_off[p] - m;
-    const double c0 = panel_g[panel_off[p]];
-    double val;
+// Per-patch sample vectors: the data at the 8 x 8 Gauss points of every panel
+// and the walk estimates, less c = g at the patch's first collocation point.
+// The members of a weight group are congruent, so a sample's point in the patch
+// frame is the same for all of them: a thread places its sample once (FP64
+// trigonometry) and then, for a chunk of the group's patches, only rotates it
+// into each patch's frame and evaluates the data (grid: samples x member chunks
+// x weight groups).  The values are those of placing it per patch, bit for bit.
+__global__ void rhs_samples_kernel(DData dat, const int64_t *__restrict__ wrep, const int64_t *__restrict__ mem_off,
+                                   const int64_t *__restrict__ members, int chunk, int64_t gbase,
+                                   const int64_t *__restrict__ vec_off, const int64_t *__restrict__ panel_off,
+                                   const int64_t *__restrict__ gamma_off, const PatchFrame *__restrict__ frames,
+                                   const double *__restrict__ panel_prm, const double *__restrict__ panel_g,
+                                   const double *__restrict__ U, const double *__restrict__ glx,
+                                   float *__restrict__ vec) {
+    const int64_t grp = gbase + blockIdx.z;
+    const int64_t rep = wrep[grp];
+    const int64_t kc = vec_off[rep + 1] - vec_off[rep];
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= kc) return;
+    const int64_t m = gamma_off[rep + 1] - gamma_off[rep];
+    const int64_t dcols = kc - m;
+    const int64_t k0 = mem_off[grp] + (int64_t)blockIdx.y * chunk;
+    const int64_t k1 = min(mem_off[grp + 1], k0 + chunk);
+    if (k0 >= k1) return;
     if (q < dcols) {
         const int64_t j = q / kSamplesPerPanel;
         const int a = (int)(q - j * kSamplesPerPanel) / kSampleN, b = (int)(q % kSampleN);
         const double *gx = glx + kSampleN * (kSampleN - 1) / 2;
-        const double *prm = panel_prm + 6 * (panel_off[p] + j);
+        const double *prm = panel_prm + 6 * (panel_off[rep] + j);
         const double u = prm[0] + 0.5 * (1.0 + gx[a]) * (prm[1] - prm[0]);
         const double v = prm[2] + 0.5 * (1.0 + gx[b]) * (prm[3] - prm[2]);
-        const PatchFrame &f = frames[p];
+        const PatchFrame &fr = frames[rep];
         double Y[3], nl[3], J;
-        patch_point<double>(f.kind, f.R, u, v, Y, nl, J);
-        const double y0 = f.c[0] + Y[0] * f.t1[0] + Y[1] * f.t2[0] + Y[2] * f.n[0];
-        const double y1 = f.c[1] + Y[0] * f.t1[1] + Y[1] * f.t2[1] + Y[2] * f.n[1];
-        const double y2 = f.c[2] + Y[0] * f.t1[2] + Y[1] * f.t2[2] + Y[2] * f.n[2];
-        val = (double)dirichlet_eval<float>(dat, (float)y0, (float)y1, (float)y2) - c0;
+        patch_point<double>(fr.kind, fr.R, u, v, Y, nl, J);
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t p = members[k];
+            const PatchFrame &f = frames[p];
+            const double y0 = f.c[0] + Y[0] * f.t1[0] + Y[1] * f.t2[0] + Y[2] * f.n[0];
+            const double y1 = f.c[1] + Y[0] * f.t1[1] + Y[1] * f.t2[1] + Y[2] * f.n[1];
+            const double y2 = f.c[2] + Y[0] * f.t1[2] + Y[1] * f.t2[2] + Y[2] * f.n[2];
+            const double val = (double)dirichlet_eval<float>(dat, (float)y0, (float)y1, (float)y2) -
+                               panel_g[panel_off[p]];
+            vec[vec_off[p] + q] = (float)val;
+        }
     } else {
-        val = U[gamma_off[p] + (q - dcols)] - c0;
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t p = members[k];
+            vec[vec_off[p] + q] = (float)(U[gamma_off[p] + (q - dcols)] - panel_g[panel_off[p]]);
+        }
     }
-    vec[idx] = (float)val;
 }
 
 constexpr int kGemmM = 32, kGemmK = 32, kGemmThreads = 256;
@@ -1668,7 +1689,8 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
     P.glw = gl_w_dev();
     P.pieces = D.pieces;
     P.panel_piece = g->ws.panel_piece.as<int32_t>();
-    if (sk) assemble_kernel<true, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    const dim3 grid((unsigned)rows);
+    if (sk) assemble_kernel<true, false><<<grid, kAsmThreads, 0, s>>>(P);
     else if (mode == 2 && only_wrapped && prec == DTN_PREC_MIXED) {
         if (!pstat) return cudaErrorInvalidValue;
         wrapped_static_kernel<<<(unsigned)((L.panels_total + 255) / 256), 256, 0, s>>>(
@@ -1676,7 +1698,7 @@ cudaError_t launch_assemble(const dtn_geometry *g, const BatchLayout &L, const D
             panel_aux, (PanelStatic32 *)pstat);
         assemble_kernel<false, true><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
     }
-    else assemble_kernel<false, false><<<(unsigned)rows, kAsmThreads, 0, s>>>(P);
+    else assemble_kernel<false, false><<<grid, kAsmThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -1708,16 +1730,29 @@ cudaError_t launch_rhs_shared(const dtn_geometry *g, const BatchLayout &L, const
     if (g->dg.kind == kBall || g->dg.kind == kBallExterior) {
         const unsigned tb = (unsigned)((L.max_wgroup_rows * kSampleN + kWtThreads - 1) / kWtThreads);
         rhs_far_weights_kernel<<<dim3(rows, tb), kWtThreads, 0, s>>>(Wd);
-        rhs_near_weights_kernel<<<rows, 32 * kNearWarps, 0, s>>>(Wd);
+        // four CTAs per row: the FP64 quadrature of one weight group's rows spread
+        // over every SM (a single group has as few as 128 rows)
+        rhs_near_weights_kernel<<<dim3(rows, 4), 32 * kNearWarps, 0, s>>>(Wd);
     }
     rhs_walk_weights_kernel<<<dim3(rows, (unsigned)((L.max_nodes + kWtThreads - 1) / kWtThreads)), kWtThreads, 0, s>>>(Wd);
     const int T = 256;
     // (a batch of wrapped patches only has weight rows without columns: their
     // right sides are assembled directly, and there are no samples)
-    if (L.vec_total > 0)
-        rhs_samples_kernel<<<(unsigned)((L.vec_total + T - 1) / T), T, 0, s>>>(
-            g->dd, L.n_patches, L.vec_total, D.vec_off, D.panel_off, D.gamma_off, D.frames, panel_prm, panel_g, U,
-            Wd.glx, vec);
+    if (L.vec_total > 0) {
+        int64_t max_kc = 0, max_mem = 0;
+        for (int64_t k = 0; k < L.n_wgroups; ++k) {
+            max_kc = std::max(max_kc, L.kcols[k]);
+            max_mem = std::max(max_mem, L.mem_off[k + 1] - L.mem_off[k]);
+        }
+        const int chunk = (int)std::max<int64_t>(16, (max_mem + 65534) / 65535);
+        for (int64_t g0 = 0; g0 < L.n_wgroups; g0 += 65535) {   // grid z holds at most 65535 groups
+            const dim3 grid((unsigned)((max_kc + T - 1) / T), (unsigned)((max_mem + chunk - 1) / chunk),
+                            (unsigned)std::min<int64_t>(65535, L.n_wgroups - g0));
+            rhs_samples_kernel<<<grid, T, 0, s>>>(g->dd, D.wrep, D.mem_off, D.members, chunk, g0, D.vec_off,
+                                                  D.panel_off, D.gamma_off, D.frames, panel_prm, panel_g, U, Wd.glx,
+                                                  vec);
+        }
+    }
     RhsDev R;
     R.frames = D.frames;
     R.panel_off = D.panel_off;
