@@ -904,8 +904,10 @@ static void patch_point(const or_patch *p, int piece, double u, double v, double
  * of its area centroid onto the sphere (cap).  prm = (u0, u1, v0, v1, uc, vc,
  * piece), OR_PRM values per panel.
  * Wrapped patch (kind 2, R8): the ns sectors are shared among the sub-ranges of
- * all pieces (pieces in order, sub-ranges by angle): one each, then one at a
- * time to the sub-range with the largest area per sector (a larger ratio wins
+ * all pieces (pieces in order, sub-ranges by angle) whose area is at least
+ * area(S) / (nr^2 ns) (smaller ones get none and are left out of S): one
+ * each, then one at a time to the sub-range with the largest area per sector
+ * (a larger ratio wins
  * only by more than 1e-12 relative, else the lowest index), and a sub-range's
  * sectors split its angle evenly; rings split u =
  * rho / rho_max in [0, 1] evenly; the collocation point is the image of the
@@ -931,11 +933,24 @@ int or_panels(const or_patch *p, int nr, int ns, double *Xloc, double *xglob, do
                 }
                 pc[nsr] = k; sj[nsr] = j; sa[nsr] = A; cnt[nsr] = 1; ++nsr;
             }
-        if (ns < nsr) return -1;
-        for (int extra = ns - nsr; extra > 0; --extra) {
-            int best = 0;
-            for (int t = 1; t < nsr; ++t)
-                if (sa[t] / cnt[t] > sa[best] / cnt[best] * (1.0 + 1e-12)) best = t;
+        /* a sub-range whose area is below As / (nr^2 ns), less than a ring-0
+         * panel of the patch split evenly, gets no sector: it is below the
+         * layout's resolution (a ball that grazes a face, or a direction cut
+         * next to a rectangle corner) and its rings would be slivers */
+        double As = 0.0;
+        for (int t = 0; t < nsr; ++t) As += sa[t];
+        const double thr = As / ((double)nr * nr * ns);
+        int used = 0, first = -1;
+        for (int t = 0; t < nsr; ++t) {
+            cnt[t] = sa[t] >= thr ? 1 : 0;
+            used += cnt[t];
+            if (cnt[t] && first < 0) first = t;
+        }
+        if (ns < used || first < 0) return -1;
+        for (int extra = ns - used; extra > 0; --extra) {
+            int best = first;
+            for (int t = first + 1; t < nsr; ++t)
+                if (cnt[t] && sa[t] / cnt[t] > sa[best] / cnt[best] * (1.0 + 1e-12)) best = t;
             cnt[best] += 1;
         }
         int sector = 0;

@@ -281,6 +281,7 @@ __device__ double rho2_integral(const Piece &q, double v0, double v1, const doub
 __global__ void patch_frame_kernel(DGeom g, int64_t n, const double *__restrict__ centers,
                                    const double *__restrict__ radius, PatchFrame *__restrict__ out,
                                    Piece *__restrict__ pieces, const int32_t *__restrict__ nsec,
+                                   const int32_t *__restrict__ nring,
                                    const double *__restrict__ glx, const double *__restrict__ glw) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -372,7 +373,7 @@ __global__ void patch_frame_kernel(DGeom g, int64_t n, const double *__restrict_
                 // Gamma is star-shaped about the pole iff the box is at least a
                 // thick along n: the arc from the pole enters the box once and
                 // stays in it through theta = pi
-                if (hi[ax] - lo[ax] < a || !pieces || !nsec) f.status = DTN_E_UNSUPPORTED;
+                if (hi[ax] - lo[ax] < a || !pieces || !nsec || !nring) f.status = DTN_E_UNSUPPORTED;
                 wbox = bw;
                 wface = bf;
                 for (int i = 0; i < 3; ++i) { f.blo[i] = lo[i]; f.bhi[i] = hi[i]; }
@@ -432,24 +433,33 @@ __global__ void patch_frame_kernel(DGeom g, int64_t n, const double *__restrict_
             pc[np++] = q;
         }
         f.npiece = np;
-        // the sectors: one per sub-range, the rest by the largest area per sector
-        int nsr = 0;
-        for (int k = 0; k < np; ++k) nsr += pc[k].nsub;
-        const int ns = nsec[p];
-        if (ns < nsr) {
+        // the sectors: one per sub-range of area at least area(S) / (nr^2 ns)
+        // (smaller ones, below the layout's resolution, get none and are left
+        // out of S), the rest by the largest area per sector
+        const int ns = nsec[p], nrg = nring[p];
+        double area[kMaxPieces][kMaxSub], As = 0.0;
+        for (int k = 0; k < np; ++k)
+            for (int j = 0; j < pc[k].nsub; ++j) {
+                area[k][j] = 0.5 * rho2_integral(pc[k], pc[k].sub[j], pc[k].sub[j + 1], glx, glw);
+                As += area[k][j];
+            }
+        const double thr = As / ((double)nrg * nrg * ns);
+        int used = 0, fk = -1, fj = -1;
+        for (int k = 0; k < np; ++k)
+            for (int j = 0; j < pc[k].nsub; ++j) {
+                pc[k].cnt[j] = area[k][j] >= thr ? 1 : 0;
+                used += pc[k].cnt[j];
+                if (pc[k].cnt[j] && fk < 0) { fk = k; fj = j; }
+            }
+        if (ns < used || fk < 0) {
             f.status = DTN_E_UNSUPPORTED;
         } else {
-            double area[kMaxPieces][kMaxSub];
-            for (int k = 0; k < np; ++k)
-                for (int j = 0; j < pc[k].nsub; ++j) {
-                    area[k][j] = 0.5 * rho2_integral(pc[k], pc[k].sub[j], pc[k].sub[j + 1], glx, glw);
-                    pc[k].cnt[j] = 1;
-                }
-            for (int extra = ns - nsr; extra > 0; --extra) {
-                int bk = 0, bj = 0;
+            for (int extra = ns - used; extra > 0; --extra) {
+                int bk = fk, bj = fj;
                 for (int k = 0; k < np; ++k)
                     for (int j = 0; j < pc[k].nsub; ++j)
-                        if (area[k][j] / pc[k].cnt[j] > area[bk][bj] / pc[bk].cnt[bj] * (1.0 + 1e-12)) { bk = k; bj = j; }
+                        if (pc[k].cnt[j] && (k > fk || (k == fk && j > fj)) &&
+                            area[k][j] / pc[k].cnt[j] > area[bk][bj] / pc[bk].cnt[bj] * (1.0 + 1e-12)) { bk = k; bj = j; }
                 pc[bk].cnt[bj] += 1;
             }
         }
@@ -652,7 +662,7 @@ cudaError_t launch_patch_frames(const dtn_geometry *g, int64_t n, const double *
     if (n == 0) return cudaSuccess;
     const int T = 128;
     patch_frame_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dg, n, centers, radius, frames, nullptr, nullptr,
-                                                                 gl_x_dev(), gl_w_dev());
+                                                                 nullptr, gl_x_dev(), gl_w_dev());
     return cudaGetLastError();
 }
 
@@ -664,7 +674,7 @@ cudaError_t launch_patch_setup(const dtn_geometry *g, const BatchLayout &L, cons
     const int T = 128;
     const int64_t n = L.n_patches;
     patch_frame_kernel<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(g->dg, n, centers, D.radius, D.frames, D.pieces,
-                                                                 D.ns, gl_x_dev(), gl_w_dev());
+                                                                 D.ns, D.nr, gl_x_dev(), gl_w_dev());
     if (L.gamma_total > 0)
         gamma_nodes_kernel<<<(unsigned)((L.gamma_total + T - 1) / T), T, 0, s>>>(
             n, L.gamma_total, D.gamma_off, D.nt, D.nph, D.frames, gl_x_dev(), gl_w_dev(), gamma_xyz,

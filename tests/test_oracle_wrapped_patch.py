@@ -198,3 +198,27 @@ def test_polar_origin_moves_onto_a_near_side():
     assert abs(pan["area"].sum() - sum(areas)) < 1e-12
     assert pan["area"].max() / pan["area"].min() < 20
     assert np.linalg.cond(Am) < 100
+
+
+def test_piece_below_layout_resolution_gets_no_panels():
+    """A ball that grazes a second face (centre 0.2999 from it: a slice of
+    radius 0.0077, area about 1e-4) has two pieces, but the grazed one is
+    smaller than area(S) / (nr^2 ns) and gets no sector: every panel lies on
+    the top face, the panels' area is the top piece's closed-form area, and the
+    collocation matrix stays well conditioned (its rings would otherwise be
+    slivers of 1e-7 in area)."""
+    d = 0.2999
+    geo, data = _geo(), _data()
+    p = O.patch_frame(geo, (2.0, 1.0 + d, 1.7), A)
+    assert p.kind == 2 and p.npiece == 2
+    seg = A * A * math.acos(d / A) - d * math.sqrt(A * A - d * d)
+    areas = [pc[2] for pc in p.pieces()]
+    assert abs(areas[0] - (math.pi * A * A - seg)) < 1e-13
+    nr, ns, nt, nph = 4, 24, 12, 24
+    pan = O.panels(p, nr, ns)
+    assert areas[1] < sum(areas) / (nr * nr * ns)
+    assert abs(pan["area"].sum() - areas[0]) < 1e-12
+    assert {tuple(np.round(v, 12)) for v in pan["normal"]} == {(0.0, 0.0, -1.0)}
+    _, yg, _ = O.gamma_nodes(p, nt, nph)
+    Am, _ = O.assemble(p, data, nr, ns, nt, nph, O.dirichlet(data, yg), rtol=1e-8)
+    assert np.linalg.cond(Am) < 100
