@@ -781,16 +781,23 @@ __device__ __forceinline__ int order32r(float r) {
     return 0;
 }
 
-// the adaptive cover of order64/adaptive_squares on FP32 offsets
-__device__ float ratio32(const Off32 &O, const Reg32 &R, float x0, float x1, float e0, float e1, bool withX, float &lx,
-                         float &le) {
-    float P[3][3][3], J, du, dw, jac;
-#pragma unroll 1
-    for (int k = 0; k < 9; ++k) {
-        const int a = k / 3, b = k - 3 * (k / 3);
+// the adaptive cover of order64/adaptive_squares on FP32 offsets, taken by a
+// whole warp: the square's nine points (corners, edge midpoints, centre) are
+// placed by lanes 0-8, one each, and shared by shuffles, so that every lane
+// takes the same decision on the same values
+__device__ float ratio32(const Off32 &O, const Reg32 &R, float x0, float x1, float e0, float e1, bool withX, int lane,
+                         float &lx, float &le) {
+    float P[3][3][3], mine[3] = {0.f, 0.f, 0.f};
+    if (lane < 9) {
+        const int a = lane / 3, b = lane - 3 * (lane / 3);
+        float J, du, dw, jac;
         map32(R, x0 + 0.5f * a * (x1 - x0), e0 + 0.5f * b * (e1 - e0), du, dw, jac);
-        pos32(O, du, dw, P[a][b], J);
+        pos32(O, du, dw, mine, J);
     }
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) P[k / 3][k % 3][d] = __shfl_sync(0xffffffffu, mine[d], k);
     const float *Yc = P[1][1];
     float rad2 = 0.f;
     for (int a = 0; a < 3; ++a)
@@ -821,8 +828,9 @@ __device__ float ratio32(const Off32 &O, const Reg32 &R, float x0, float x1, flo
     return rad2 > 0.f ? sqrtf(dmin2 / rad2) : INFINITY;
 }
 
+// (called by whole warps: the cover's measures are shared by shuffles)
 template <typename Fn>
-__device__ void adaptive32(const Off32 &O, const Reg32 &R, bool withX, int min_order, Fn &&fn) {
+__device__ void adaptive32(const Off32 &O, const Reg32 &R, bool withX, int min_order, int lane, Fn &&fn) {
     struct Sq { float x0, x1, e0, e1; int depth; };
     Sq stack[kStack];
     int sp = 0;
@@ -830,7 +838,7 @@ __device__ void adaptive32(const Off32 &O, const Reg32 &R, bool withX, int min_o
     while (sp > 0) {
         const Sq q = stack[--sp];
         float lx, le;
-        const float r = ratio32(O, R, q.x0, q.x1, q.e0, q.e1, withX, lx, le);
+        const float r = ratio32(O, R, q.x0, q.x1, q.e0, q.e1, withX, lane, lx, le);
         int n = order32r(r);
         if (n == 0 && q.depth < kMaxDepth && sp + 4 <= kStack) {
             const float xm = 0.5f * (q.x0 + q.x1), em = 0.5f * (q.e0 + q.e1);
@@ -860,12 +868,41 @@ struct Gauss32 {
 };
 
 // one accepted square of a region, its points dealt to the lanes of a warp;
-// each lane adds its part, times 1/4pi, to sa and sd
+// each lane adds its part, times 1/4pi, to sa and sd.  On a box the map's
+// line (dw) depends on the point's second index alone: lane j maps line j once
+// and the points take its values by shuffles (the same values pos32 forms).
 __device__ void square32_warp(const Off32 &O, const Row32 &Rw, const Reg32 &R, float x0, float x1, float e0, float e1,
                               int n, const Gauss32 &G, int lane, double &sa, double &sd) {
     const float *t = G.t + n * (n - 1) / 2, *w = G.w + n * (n - 1) / 2;
     const float hx = x1 - x0, he = e1 - e0;
     float la = 0.f, ld = 0.f;
+    if (!R.tri && n <= 32) {
+        const unsigned FULL = 0xffffffffu;
+        float Bl[3] = {0.f, 0.f, 0.f}, dBl[3] = {0.f, 0.f, 0.f}, Jl = 0.f;
+        if (lane < n) line32(O, fmaf(fmaf(he, t[lane], e0), R.db, R.b0), Bl, dBl, Jl);
+        const float jac = R.da * R.db;
+        for (int k0 = 0; k0 < n * n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool ok = k < n * n;
+            const int i = ok ? k / n : 0, j = ok ? k - (k / n) * n : 0;
+            float Bg[3], dBg[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Bg[d] = __shfl_sync(FULL, Bl[d], j);
+                dBg[d] = __shfl_sync(FULL, dBl[d], j);
+            }
+            const float Jf = __shfl_sync(FULL, Jl, j);
+            if (ok) {
+                const float du = fmaf(fmaf(hx, t[i], x0), R.da, R.a0);
+                const float o[3] = {fmaf(du, Bg[0], dBg[0]), fmaf(du, Bg[1], dBg[1]), fmaf(du, Bg[2], dBg[2])};
+                const float J = (O.uc + du) * Jf;
+                eval32(O, Rw, o, w[i] * w[j] * hx * he * jac * J, la, ld);
+            }
+        }
+        sa += (double)la * (0.25 / kPi);
+        sd += (double)ld * (0.25 / kPi);
+        return;
+    }
     for (int k = lane; k < n * n; k += 32) {
         const int i = k / n, j = k - i * n;
         float du, dw, jac, o[3], J;
@@ -1171,7 +1208,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             off32_make(P.pstat[row], rs32, O);
             self_regions32(O, prm, [&](const Reg32 &Q, bool withX, int min_order) {
                 if ((tri++ % (kAsmThreads / 32)) != warp) return;
-                adaptive32(O, Q, withX, min_order, [&](float x0, float x1, float e0, float e1, int n) {
+                adaptive32(O, Q, withX, min_order, lane, [&](float x0, float x1, float e0, float e1, int n) {
                     square32_warp(O, rw, Q, x0, x1, e0, e1, n, g32, lane, sa, sd);
                 });
             });
@@ -1219,7 +1256,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
             Q.a0 = (float)(prm[0] - prm[4]); Q.da = (float)(prm[1] - prm[0]);
             Q.b0 = (float)(prm[2] - prm[5]); Q.db = (float)(prm[3] - prm[2]);
             Q.E1[0] = Q.E1[1] = Q.E2[0] = Q.E2[1] = Q.det = 0.f;
-            adaptive32(O, Q, true, 0, [&](float x0, float x1, float e0, float e1, int n) {
+            adaptive32(O, Q, true, 0, lane, [&](float x0, float x1, float e0, float e1, int n) {
                 square32_warp(O, rw, Q, x0, x1, e0, e1, n, g32, lane, sa, sd);
             });
         } else {
@@ -1241,7 +1278,23 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(AsmDev P) {
     const int64_t goff = P.gamma_off[p];
     const int nk = (int)(P.gamma_off[p + 1] - goff);
     double gsum = 0.0;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    if (W32) {
+        // mixed precision: FP32 terms W_k (U_k - g(x)) / |x - y_k|^3 from FP64
+        // differences, summed per thread in FP32, times the row's
+        // (a^2 - |x|^2) / (4 pi a)
+        const double xx = X[0] * X[0] + X[1] * X[1] + X[2] * X[2];
+        const float cp = (float)((f.a * f.a - xx) / (4.0 * kPi * f.a));
+        float gs = 0.f;
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const int64_t gk = goff + k;
+            const float dx = (float)(X[0] - P.gamma_loc[3 * gk]), dy = (float)(X[1] - P.gamma_loc[3 * gk + 1]),
+                        dz = (float)(X[2] - P.gamma_loc[3 * gk + 2]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            gs += (float)P.gamma_w[gk] * (float)(P.U[gk] - gx) / (r2 * sqrtf(r2));
+        }
+        gsum = (double)(gs * cp);
+    }
+    for (int k = threadIdx.x; k < nk && !W32; k += blockDim.x) {
         const int64_t gk = goff + k;
         const double Y[3] = {P.gamma_loc[3 * gk], P.gamma_loc[3 * gk + 1], P.gamma_loc[3 * gk + 2]};
         if (SK) {
