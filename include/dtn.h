@@ -101,9 +101,11 @@ typedef struct {
 
 typedef enum {
     DTN_PREC_FP64 = 0,   /* FP64 walks, FP64 assembly, FP64 LU (the plain path) */
-    DTN_PREC_MIXED = 1   /* FP32 walks with FP64 sums; FP32 far-field assembly with FP64
-                            singular / near-singular / rim entries; FP32 LU with FP64-residual
-                            iterative refinement */
+    DTN_PREC_MIXED = 1   /* FP32 walks with FP64 sums; patches of one shape share one
+                            FP64-rule matrix, their right sides by FP32 weights and products
+                            summed in FP64; a wrapped patch (its own shape) by FP32 rules in
+                            offset form, FP32 hemisphere terms from FP64 differences; FP32 LU
+                            with FP64-residual iterative refinement */
 } dtn_precision;
 
 typedef struct {
@@ -223,9 +225,13 @@ dtn_status dtn_query_patch_sizes(const dtn_patch_batch *batch, int64_t *panels_t
  * A (assembled with the FP64 rules) and one FP32 factorisation, and each patch
  * gets its own right side and FP64-residual refinement.  DTN_PREC_FP64 (the
  * plain path) assembles and factors every patch separately.  Per-patch failures land in patch_status
- * (DTN_E_UNSUPPORTED: the ball meets more than one plane face, or the centre
- * is not on the boundary; DTN_E_NOT_CONVERGED: refinement stopped above
- * refine_tol; DTN_E_WALK_CAP: some walks were cut at max_steps). */
+ * (DTN_E_UNSUPPORTED: the centre is not on the boundary; or the ball meets a
+ * second smooth piece, except further faces of the obstacle box the centre
+ * lies on (a wrapped patch), which is then unsupported if the ball also reaches
+ * another conductor or the outer box, if the box is thinner than a along the
+ * face normal, or if its face pieces need more sectors than n_sectors holds;
+ * DTN_E_NOT_CONVERGED: refinement stopped above refine_tol; DTN_E_WALK_CAP:
+ * some walks were cut at max_steps). */
 dtn_status dtn_solve_patches(dtn_geometry *geom, const dtn_patch_batch *batch,
                              const dtn_solve_opts *opts, dtn_patch_result *result, void *stream);
 
